@@ -1,0 +1,210 @@
+/*
+ * rbc.h -- C ABI of the B300 Random Ball Cover library (librbc.so).
+ *
+ * Exact and one-shot nearest-neighbour search with the Random Ball Cover of
+ * Cayton, "Accelerating Nearest Neighbor Search on Manycore Systems": every
+ * search and build step is a call of the brute-force primitive BF(Q, X)
+ * (Section 3), run by hand-written sm_103a CUDA kernels.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * Pointers.  Every array argument may be a DEVICE pointer (cudaMalloc /
+ *   torch CUDA tensor on the current device) or a HOST pointer (pageable or
+ *   pinned).  The library inspects each pointer; host inputs are copied to the
+ *   device and host outputs are filled by a device-to-host copy, inside the
+ *   call, on the given stream.  Arrays are dense row-major: X [n, d],
+ *   Q [m, d] float32; out_ids [m, k] int64; out_dist [m, k] float32.
+ * Streams.  `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   With device outputs the call is asynchronous: results are valid once the
+ *   stream has drained.  With host outputs the call returns after they are
+ *   written.  Calls synchronise the stream internally when the amount of
+ *   stage-two work must be read back (exact search) -- see rbc_search.
+ * Results.  Row i of out_ids / out_dist holds the k nearest database points
+ *   of query i in increasing (rho, id) order: equal distances are ordered by
+ *   the smaller database id.  out_dist holds rho itself (Euclidean distance,
+ *   not its square, for RBC_L2; the l1 sum for RBC_L1).  When k exceeds the
+ *   number of points the tail holds id -1 and distance +inf.
+ * Exactness.  Low-precision storage (RBC_BF16 / RBC_F16) is used for the
+ *   tensor-core distance pass only; candidates are re-ranked in FP32
+ *   difference form, the candidate set is certified with a rounding-error
+ *   bound, queries that fail certification are re-searched in FP32, and
+ *   near-ties are decided in FP64.  Results agree with an FP64 brute force up
+ *   to ties closer than the FP32 rounding bound (about 1e-6 relative).
+ * Errors.  Every int-returning call returns RBC_OK (0) or a negative code;
+ *   rbc_last_error() then returns a message for the calling thread.  On error
+ *   no output is guaranteed.  Inputs containing NaN or Inf are undefined.
+ * Threads.  Different indexes may be used from different threads.  One index
+ *   may be searched concurrently from several threads on different streams
+ *   (the index is read-only after build; each call owns its workspace).
+ */
+#ifndef RBC_H_
+#define RBC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define RBC_OK 0
+#define RBC_ERR_ARG (-1)         /* invalid argument (sizes, k, n_r, null pointer) */
+#define RBC_ERR_OOM (-2)         /* device allocation failed */
+#define RBC_ERR_CUDA (-3)        /* a CUDA runtime call or kernel failed */
+#define RBC_ERR_TIMEOUT (-4)     /* a bounded device-side wait expired */
+#define RBC_ERR_UNSUPPORTED (-5) /* combination not supported (e.g. d > 1024) */
+
+/* ---- enumerations ---- */
+typedef enum {
+  RBC_L2 = 0, /* Euclidean distance (Section 7: used for every experiment) */
+  RBC_L1 = 1  /* sum of absolute differences (Section 6, lattice example) */
+} rbc_metric;
+
+typedef enum {
+  RBC_EXACT = 0,  /* exact search: lists are a partition, Section 5.2 */
+  RBC_ONESHOT = 1 /* one-shot search: lists are the s-NN of each rep, Section 5.1 */
+} rbc_mode;
+
+typedef enum {
+  RBC_F32 = 0,  /* FP32 CUDA-core distance kernels throughout */
+  RBC_BF16 = 1, /* bf16 tensor-core pass (L2), FP32 re-rank, FP64 ties */
+  RBC_F16 = 2   /* fp16 tensor-core pass (L2), FP32 re-rank, FP64 ties */
+} rbc_storage;
+
+typedef struct rbc_index rbc_index; /* opaque; owned by the library */
+
+/* Build options.  Zero-initialised (or rbc_default_opts) means: seed 0,
+ * RBC_EXACT, RBC_F32, default re-rank width, sampled representatives. */
+typedef struct {
+  uint64_t seed;          /* seed of the representative sampler */
+  int32_t mode;           /* rbc_mode */
+  int32_t storage;        /* rbc_storage used by the search and the build */
+  int32_t rerank_c;       /* candidates per query kept by the low-precision
+                             pass before re-ranking; 0 = automatic */
+  int32_t reserved;       /* must be 0 */
+  const int64_t* rep_ids; /* optional HOST array of n_r distinct ids in
+                             [0, n), ascending; NULL = sample them */
+} rbc_opts;
+
+void rbc_default_opts(rbc_opts* opts);
+
+/*
+ * rbc_sample_reps -- the representative set R (Section 4).
+ *   The paper selects each point independently with probability n_r / n; this
+ *   library draws exactly n_r distinct ids uniformly without replacement: a
+ *   partial Fisher-Yates shuffle of [0, n) whose swap positions come from
+ *   SplitMix64(seed) (Steele, Lea & Flood 2014) with rejection of the top
+ *   2^64 mod (n - i) values, and returns them sorted ascending.  Host-only
+ *   (no device work).  out: HOST array of n_r int64.
+ *   Errors: RBC_ERR_ARG if n < 1, n_r < 1, n_r > n or out is NULL.
+ */
+int rbc_sample_reps(int64_t n, int32_t n_r, uint64_t seed, int64_t* out);
+
+/*
+ * rbc_build -- build a Random Ball Cover over X (Sections 4 and 5).
+ *   X [n, d] float32 (device or host).  n_r representatives are sampled with
+ *   rbc_sample_reps(n, n_r, opts->seed) unless opts->rep_ids is given.
+ *   Exact mode: BF(X, R) assigns every point to its nearest representative
+ *   (ties to the smaller id), each representative's list L_r is the set of
+ *   points it owns and psi_r = max over L_r of rho(x, r).  `s` is ignored.
+ *   One-shot mode: BF(R, X) with k = s gives each L_r = the s nearest points
+ *   of r (ties by id) and psi_r = the s-th distance.
+ *   The index keeps its own copies (FP32 rows in list order, the
+ *   low-precision copy, norms, rounding residuals, radii); X may be freed
+ *   after the call returns and the stream has drained.
+ *   out: receives the new index; free with rbc_free.
+ *   Errors: RBC_ERR_ARG if n < 1, d < 1, n_r < 1, n_r > n, n >= 2^31,
+ *   one-shot with s < 1 or s > n, bad enum, or NULL X/out;
+ *   RBC_ERR_UNSUPPORTED if d > 1024; RBC_ERR_OOM; RBC_ERR_CUDA.
+ */
+int rbc_build(const float* X, int64_t n, int32_t d, int32_t n_r, int32_t s, int32_t metric,
+              const rbc_opts* opts, void* stream, rbc_index** out);
+
+/*
+ * rbc_search -- k nearest neighbours of every query (Section 5).
+ *   Exact mode (Section 5.2, generalised to k): stage one is BF(Q, R) keeping
+ *   every distance; gamma_1 / gamma_k are the distances to the nearest / k-th
+ *   nearest representative; representative r survives iff
+ *   rho(q, r) <= gamma_k + psi_r and rho(q, r) <= 2 gamma_k + gamma_1 (both
+ *   evaluated with certified rounding bounds); stage two is BF over the union
+ *   of the surviving lists.  Queries are processed in tiles of nearby queries
+ *   (ordered by nearest representative) and each tile searches the union of
+ *   its queries' surviving lists -- a superset, so results are unchanged.
+ *   One-shot mode (Section 5.1): BF(q, R) picks the nearest representative r
+ *   and BF(q, X[L_r]) gives the answer; requires k <= s.
+ *   Q [m, d] float32; out_ids [m, k] int64; out_dist [m, k] float32 (device
+ *   or host).  m may be 0 (no work).  The call reads back one small counter
+ *   (the stage-two work size) and so synchronises `stream` once.
+ *   Errors: RBC_ERR_ARG if idx/Q/outputs NULL, m < 0, k < 1, k > n, or
+ *   one-shot with k > s; RBC_ERR_OOM; RBC_ERR_CUDA; RBC_ERR_TIMEOUT.
+ */
+int rbc_search(const rbc_index* idx, const float* Q, int64_t m, int32_t k, int64_t* out_ids,
+               float* out_dist, void* stream);
+
+/*
+ * bf_search -- the brute-force primitive BF(Q, X) (Section 3): all m x n
+ *   distances fused with a per-query top-k; no distance matrix is stored.
+ *   storage RBC_F32: FP32 CUDA-core kernel.  RBC_BF16 / RBC_F16 with RBC_L2:
+ *   tcgen05 tensor-core pass over the expansion |x|^2 - 2 q.x, then the FP32
+ *   re-rank / certification / FP64 tie steps described above.  RBC_L1 always
+ *   runs in FP32 on CUDA cores.
+ *   Errors: RBC_ERR_ARG (m < 0, n < 1, d < 1, k < 1, n >= 2^31, bad enum,
+ *   NULL pointers); RBC_ERR_UNSUPPORTED (d > 1024); RBC_ERR_OOM; RBC_ERR_CUDA.
+ */
+int bf_search(const float* Q, int64_t m, const float* X, int64_t n, int32_t d, int32_t k,
+              int32_t metric, int32_t storage, int64_t* out_ids, float* out_dist, void* stream);
+
+/* Index description. */
+typedef struct {
+  int64_t n;
+  int32_t d;
+  int32_t n_r;
+  int32_t s;
+  int32_t metric;
+  int32_t mode;
+  int32_t storage;
+  int64_t list_entries;  /* total entries over all lists (n in exact mode) */
+  int64_t device_bytes;  /* device memory held by the index */
+} rbc_index_desc;
+
+/* rbc_index_info -- fills *out.  Errors: RBC_ERR_ARG on NULL. */
+int rbc_index_info(const rbc_index* idx, rbc_index_desc* out);
+
+/*
+ * rbc_index_export -- copies the built structure to HOST arrays (each may be
+ *   NULL to skip it): reps [n_r] representative ids (ascending);
+ *   offsets [n_r + 1] start of each list in `members`; members
+ *   [list_entries] database ids, list by list (ascending id within a list);
+ *   psi [n_r] radii as float32 (for exact mode an upper bound of
+ *   max_{x in L_r} rho(x, r) within the FP32 rounding bound).
+ *   Synchronises the index's build stream.  Errors: RBC_ERR_ARG, RBC_ERR_CUDA.
+ */
+int rbc_index_export(const rbc_index* idx, int64_t* reps, int64_t* offsets, int64_t* members,
+                     float* psi);
+
+/* Statistics of the most recent rbc_search / bf_search on this thread. */
+typedef struct {
+  int64_t queries;
+  int64_t kept_reps;         /* sum over queries of surviving representatives */
+  int64_t tile_points;       /* sum over query tiles of union list points x tile rows */
+  int64_t stage2_items;      /* stage-two work items launched */
+  int64_t uncertified;       /* queries whose low-precision candidate set failed
+                                certification and were re-searched in FP32 */
+  int64_t fp64_ties;         /* queries whose order needed the FP64 tie step */
+  int64_t boundary_ties;     /* queries with an FP32 near-tie at the k-th place */
+} rbc_search_stats;
+
+/* rbc_last_stats -- statistics of this thread's last search call (host only). */
+int rbc_last_stats(rbc_search_stats* out);
+
+/* rbc_free -- releases the index (waits for its outstanding work). NULL ok. */
+void rbc_free(rbc_index* idx);
+
+/* rbc_last_error -- message of the last failing call on this thread ("" if none). */
+const char* rbc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBC_H_ */

@@ -1,0 +1,248 @@
+"""Python binding of librbc.so: exact nearest-neighbour search with the
+Random Ball Cover on one B300 (sm_103a).
+
+Argument marshalling only.  Every step of every search runs in the library's
+CUDA kernels; this module passes pointers, sizes and the caller's stream.
+
+Arrays may be torch CUDA tensors (device pointers; the call is stream-ordered
+on ``torch.cuda.current_stream()`` unless a stream is given) or numpy arrays
+(host pointers; the library copies to and from the device inside the call).
+
+    import paper_1103_2635_b300 as rbc
+    ids, dist = rbc.bf_search(Q, X, k=10)                       # BF(Q, X)
+    index = rbc.rbc_build(X, n_r=1024, storage=rbc.BF16)        # R, lists, radii
+    ids, dist = rbc.rbc_search(index, Q, k=10)                  # exact search
+
+The library must have been built (``python -m paper_1103_2635_b300.build_lib``
+or ``__graft_entry__.build()``); importing without it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "L2", "L1", "EXACT", "ONESHOT", "F32", "BF16", "F16",
+    "RbcError", "bf_search", "rbc_build", "rbc_search", "rbc_sample_reps",
+    "RbcIndex", "last_stats", "library_path", "load",
+]
+
+L2, L1 = 0, 1
+EXACT, ONESHOT = 0, 1
+F32, BF16, F16 = 0, 1, 2
+_STATUS = {0: "ok", -1: "invalid argument", -2: "out of device memory", -3: "CUDA error",
+           -4: "device wait timed out", -5: "unsupported"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "librbc.so")
+_lib = None
+
+
+class RbcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("mode", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("rerank_c", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("rep_ids", ctypes.c_void_p)]
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("n_r", ctypes.c_int32),
+                ("s", ctypes.c_int32), ("metric", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("storage", ctypes.c_int32), ("list_entries", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "queries", "kept_reps", "tile_points", "stage2_items", "uncertified", "fp64_ties",
+        "boundary_ties")]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load librbc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(
+            f"{_LIB_PATH} is missing: build it with `python -m paper_1103_2635_b300.build_lib`"
+        )
+    lib = ctypes.CDLL(_LIB_PATH)
+    P, I64, I32, U64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
+    lib.rbc_sample_reps.argtypes = [I64, I32, U64, P]
+    lib.bf_search.argtypes = [P, I64, P, I64, I32, I32, I32, I32, P, P, P]
+    lib.rbc_build.argtypes = [P, I64, I32, I32, I32, I32, ctypes.POINTER(_Opts), P,
+                              ctypes.POINTER(ctypes.c_void_p)]
+    lib.rbc_search.argtypes = [P, P, I64, I32, P, P, P]
+    lib.rbc_index_info.argtypes = [P, ctypes.POINTER(_Desc)]
+    lib.rbc_index_export.argtypes = [P, P, P, P, P]
+    lib.rbc_last_stats.argtypes = [ctypes.POINTER(_Stats)]
+    lib.rbc_free.argtypes = [P]
+    lib.rbc_free.restype = None
+    lib.rbc_last_error.restype = ctypes.c_char_p
+    lib.rbc_default_opts.argtypes = [ctypes.POINTER(_Opts)]
+    lib.rbc_default_opts.restype = None
+    for f in ("rbc_sample_reps", "bf_search", "rbc_build", "rbc_search", "rbc_index_info",
+              "rbc_index_export", "rbc_last_stats"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise RbcError(rc, load().rbc_last_error().decode())
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _arg(a, dtype):
+    """(pointer, keepalive, is_device) for a torch tensor or a numpy-compatible array."""
+    if _is_torch(a):
+        import torch
+
+        want = {np.float32: torch.float32, np.int64: torch.int64}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {want} tensor")
+        return a.data_ptr(), a, a.is_cuda
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data, arr, False
+
+
+def _stream_of(stream, device_side: bool):
+    if stream is not None:
+        return getattr(stream, "cuda_stream", stream)
+    if device_side:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    return 0
+
+
+def _outputs(m: int, k: int, like_device, out_ids, out_dist):
+    if out_ids is None:
+        if like_device is not None:
+            import torch
+
+            out_ids = torch.empty((m, k), dtype=torch.int64, device=like_device)
+            out_dist = torch.empty((m, k), dtype=torch.float32, device=like_device)
+        else:
+            out_ids = np.empty((m, k), dtype=np.int64)
+            out_dist = np.empty((m, k), dtype=np.float32)
+    return out_ids, out_dist
+
+
+def rbc_sample_reps(n: int, n_r: int, seed: int = 0) -> np.ndarray:
+    """The library's representative set: n_r distinct ids of [0, n), ascending."""
+    out = np.empty(n_r, dtype=np.int64)
+    _check(load().rbc_sample_reps(n, n_r, seed, out.ctypes.data))
+    return out
+
+
+def bf_search(Q, X, k: int, metric: int = L2, storage: int = F32, out_ids=None, out_dist=None,
+              stream=None):
+    """BF(Q, X): ids [m, k] int64 and rho [m, k] float32, sorted by (rho, id)."""
+    qp, qk, qdev = _arg(Q, np.float32)
+    xp, xk, xdev = _arg(X, np.float32)
+    m, d = qk.shape
+    n = xk.shape[0]
+    if xk.shape[1] != d:
+        raise ValueError("Q and X differ in dimension")
+    out_ids, out_dist = _outputs(m, k, qk.device if qdev else None, out_ids, out_dist)
+    ip, _, idev = _arg(out_ids, np.int64)
+    dp, _, ddev = _arg(out_dist, np.float32)
+    st = _stream_of(stream, qdev or xdev or idev)
+    _check(load().bf_search(qp, m, xp, n, d, k, metric, storage, ip, dp, st))
+    return out_ids, out_dist
+
+
+class RbcIndex:
+    """A built Random Ball Cover (library-owned device memory)."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        d = _Desc()
+        _check(load().rbc_index_info(self._h, ctypes.byref(d)))
+        return {f: getattr(d, f) for f, _ in _Desc._fields_}
+
+    def export(self) -> dict:
+        """reps, list offsets, list members (ids), radii -- host numpy arrays."""
+        inf = self.info()
+        reps = np.empty(inf["n_r"], np.int64)
+        off = np.empty(inf["n_r"] + 1, np.int64)
+        mem = np.empty(inf["list_entries"], np.int64)
+        psi = np.empty(inf["n_r"], np.float32)
+        _check(load().rbc_index_export(self._h, reps.ctypes.data, off.ctypes.data, mem.ctypes.data,
+                                       psi.ctypes.data))
+        return {"reps": reps, "offsets": off, "members": mem, "psi": psi}
+
+    def search(self, Q, k: int, out_ids=None, out_dist=None, stream=None):
+        return rbc_search(self, Q, k, out_ids=out_ids, out_dist=out_dist, stream=stream)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().rbc_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rbc_build(X, n_r: int, metric: int = L2, seed: int = 0, mode: int = EXACT,
+              storage: int = F32, s: int = 0, rerank_c: int = 0, rep_ids=None,
+              stream=None) -> RbcIndex:
+    """Build the Random Ball Cover of X (Sections 4-5 of the paper)."""
+    xp, xk, xdev = _arg(X, np.float32)
+    n, d = xk.shape
+    opts = _Opts()
+    load().rbc_default_opts(ctypes.byref(opts))
+    opts.seed, opts.mode, opts.storage, opts.rerank_c = seed, mode, storage, rerank_c
+    keep = None
+    if rep_ids is not None:
+        keep = np.ascontiguousarray(rep_ids, dtype=np.int64)
+        opts.rep_ids = keep.ctypes.data
+    h = ctypes.c_void_p()
+    st = _stream_of(stream, xdev)
+    _check(load().rbc_build(xp, n, d, n_r, s, metric, ctypes.byref(opts), st, ctypes.byref(h)))
+    return RbcIndex(h.value)
+
+
+def rbc_search(index: RbcIndex, Q, k: int, out_ids=None, out_dist=None, stream=None):
+    """Exact k-NN of every query with the index: ids [m, k], rho [m, k]."""
+    qp, qk, qdev = _arg(Q, np.float32)
+    m = qk.shape[0]
+    out_ids, out_dist = _outputs(m, k, qk.device if qdev else None, out_ids, out_dist)
+    ip, _, idev = _arg(out_ids, np.int64)
+    dp, _, _ = _arg(out_dist, np.float32)
+    st = _stream_of(stream, qdev or idev)
+    _check(load().rbc_search(index.handle, qp, m, k, ip, dp, st))
+    return out_ids, out_dist
+
+
+def last_stats() -> dict:
+    """Counters of this thread's last search call (waits for its stream)."""
+    s = _Stats()
+    _check(load().rbc_last_stats(ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in _Stats._fields_}

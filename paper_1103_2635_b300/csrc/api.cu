@@ -1,0 +1,986 @@
+// C ABI of librbc.so and the host-side orchestration of the kernels.
+//
+// Every search is a sequence of BF calls (Section 3) on the device:
+//   bf_search   : BF(Q, X)                                     (Section 3)
+//   rbc_build   : BF(X, R) -> owners -> lists, radii            (Sections 4, 5.2)
+//   rbc_search  : BF(Q, R) keeping all distances, pruning, then BF over the
+//                 union of surviving lists per query tile        (Section 5.2)
+// Host code only validates arguments, allocates stream-ordered workspace and
+// launches kernels; every arithmetic step of the search runs on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rbc {
+
+namespace {
+thread_local char g_err[512] = "";
+}
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  set_error("%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  return e == cudaErrorMemoryAllocation ? RBC_ERR_OOM : RBC_ERR_CUDA;
+}
+
+const char* last_error_text() { return g_err; }
+
+}  // namespace rbc
+
+// ---------------------------------------------------------------------------
+// the index object (opaque to callers)
+// ---------------------------------------------------------------------------
+struct rbc_index {
+  int64_t n = 0;
+  int32_t d = 0, n_r = 0, s = 0, metric = 0, mode = 0, storage = 0, rerank_c = 0;
+  int64_t list_entries = 0;
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  int64_t* reps = nullptr;    // [n_r] representative ids
+  float* R32 = nullptr;       // [n_r, d] representative rows
+  int* offsets = nullptr;     // [n_r + 1] list starts (entries)
+  int* members = nullptr;     // [list_entries] database id of each entry
+  float* X32 = nullptr;       // [list_entries, d] rows in list order
+  float* psi = nullptr;       // [n_r] radius upper bounds
+  int dpad = 0;               // low-precision row length (multiple of 64)
+  void* Xlp = nullptr;        // [list_entries, dpad]
+  float* xnorm = nullptr;     // [list_entries] |x~|^2
+  unsigned* lp_max = nullptr; // [4] float bits: max|x-x~|, max|x~|, max|r-r~|, max|r~|
+  void* Rlp = nullptr;        // [n_r, dpad]
+  float* rnorm = nullptr;     // [n_r]
+
+  template <typename T>
+  int alloc(T** out, int64_t count) {
+    void* p = nullptr;
+    if (count <= 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, (size_t)count * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      rbc::set_error("index allocation of %lld bytes failed: %s",
+                     (long long)(count * (int64_t)sizeof(T)), cudaGetErrorString(e));
+      return RBC_ERR_OOM;
+    }
+    allocs.push_back(p);
+    bytes += count * (int64_t)sizeof(T);
+    *out = static_cast<T*>(p);
+    return RBC_OK;
+  }
+  ~rbc_index() {
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
+namespace rbc {
+namespace {
+
+#define RBC_TRY(x)               \
+  do {                           \
+    int _r = (x);                \
+    if (_r != RBC_OK) return _r; \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// representative sampler (Section 4, fixed-size reading): partial
+// Fisher-Yates over [0, n) driven by SplitMix64 (Steele, Lea & Flood 2014)
+// ---------------------------------------------------------------------------
+struct SplitMix64 {
+  uint64_t state;
+  uint64_t next() {
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  // uniform in [0, bound): draws >= 2^64 - (2^64 mod bound) are rejected
+  uint64_t below(uint64_t bound) {
+    uint64_t rem = (0 - bound) % bound;  // 2^64 mod bound
+    for (;;) {
+      uint64_t x = next();
+      if (rem == 0 || x < (0 - rem)) return x % bound;
+    }
+  }
+};
+
+std::vector<int64_t> sample_reps_host(int64_t n, int32_t n_r, uint64_t seed) {
+  SplitMix64 g{seed};
+  std::unordered_map<int64_t, int64_t> moved;  // positions no longer holding their own index
+  moved.reserve((size_t)n_r * 2 + 1);
+  auto at = [&](int64_t p) {
+    auto it = moved.find(p);
+    return it == moved.end() ? p : it->second;
+  };
+  std::vector<int64_t> out((size_t)n_r);
+  for (int32_t i = 0; i < n_r; ++i) {
+    int64_t j = i + (int64_t)g.below((uint64_t)(n - i));
+    int64_t vi = at(i), vj = at(j);
+    moved[i] = vj;
+    moved[j] = vi;
+    out[(size_t)i] = vj;
+  }
+  std::sort(out.begin(), out.end());
+  return out;
+}
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cached[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = v > 0 ? v : 1;
+  }
+  return cached[dev];
+}
+
+// Stream-ordered scratch released when the arena goes out of scope.
+struct Arena {
+  cudaStream_t st;
+  std::vector<void*> ptrs;
+  explicit Arena(cudaStream_t s) : st(s) {}
+  ~Arena() {
+    for (void* p : ptrs) cudaFreeAsync(p, st);
+  }
+  template <typename T>
+  int alloc(T** out, int64_t count) {
+    *out = nullptr;
+    if (count <= 0) count = 1;
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, (size_t)count * sizeof(T), st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("workspace allocation of %lld bytes failed: %s",
+                (long long)((size_t)count * sizeof(T)), cudaGetErrorString(e));
+      return RBC_ERR_OOM;
+    }
+    ptrs.push_back(p);
+    *out = static_cast<T*>(p);
+    return RBC_OK;
+  }
+};
+
+constexpr float U32 = 5.9604645e-08f;
+// relative bound of rho from the FP32 tile kernel (sequential fused sums)
+float simt_eps(int d) { return (float)(d + 8) * U32; }
+// relative bound of rho from the FP32 re-rank (interleaved partial sums)
+float rerank_eps_host(int d) { return (0.25f * d + 8.0f) * U32; }
+int pad64(int d) { return (d + 63) / 64 * 64; }
+
+// ---- per-thread statistics ----
+struct StatsBlock {
+  unsigned long long v[8];
+};
+thread_local StatsBlock* t_stats_host = nullptr;
+thread_local cudaStream_t t_stats_stream = nullptr;
+thread_local bool t_stats_pending = false;
+thread_local rbc_search_stats t_stats_fixed;
+
+// device counters: ints [0] uncertified [1] fp64 ties [2] boundary ties,
+// [4..6] the same for the FP32 re-search; u64 sums [0] kept reps [1] tile points
+struct Counters {
+  int* c = nullptr;
+  unsigned long long* sums = nullptr;
+};
+
+__global__ void stats_pack_kernel(const int* c, const unsigned long long* sums,
+                                  unsigned long long* out) {
+  if (threadIdx.x == 0) {
+    out[0] = sums[0];
+    out[1] = sums[1];
+    out[2] = (unsigned long long)c[0];
+    out[3] = (unsigned long long)(c[1] + c[5]);
+    out[4] = (unsigned long long)(c[2] + c[6]);
+    out[5] = (unsigned long long)c[4];
+    out[6] = 0;
+    out[7] = 0;
+  }
+}
+
+int counters_alloc(Counters& cn, Arena& ar, cudaStream_t st) {
+  RBC_TRY(ar.alloc(&cn.c, 8));
+  RBC_TRY(ar.alloc(&cn.sums, 2));
+  RBC_CUDA(cudaMemsetAsync(cn.c, 0, 8 * sizeof(int), st));
+  RBC_CUDA(cudaMemsetAsync(cn.sums, 0, 2 * sizeof(unsigned long long), st));
+  return RBC_OK;
+}
+
+int stats_publish(const Counters& cn, int64_t queries, int64_t items, Arena& ar,
+                  cudaStream_t st) {
+  if (!t_stats_host) {
+    void* p = nullptr;
+    RBC_CUDA(cudaMallocHost(&p, sizeof(StatsBlock)));
+    t_stats_host = static_cast<StatsBlock*>(p);
+  }
+  unsigned long long* packed;
+  RBC_TRY(ar.alloc(&packed, 8));
+  stats_pack_kernel<<<1, 32, 0, st>>>(cn.c, cn.sums, packed);
+  RBC_LAUNCH_CHECK("stats_pack_kernel");
+  RBC_CUDA(cudaMemcpyAsync(t_stats_host->v, packed, sizeof(StatsBlock), cudaMemcpyDeviceToHost,
+                           st));
+  memset(&t_stats_fixed, 0, sizeof(t_stats_fixed));
+  t_stats_fixed.queries = queries;
+  t_stats_fixed.stage2_items = items;
+  t_stats_stream = st;
+  t_stats_pending = true;
+  return RBC_OK;
+}
+
+// ---- inputs / outputs that may live in host memory ----
+struct IoPlan {
+  const float* Qdev = nullptr;
+  int64_t* ids_dev = nullptr;
+  float* dist_dev = nullptr;
+  bool ids_host = false, dist_host = false;
+};
+
+int io_prepare(const float* Q, int64_t m, int d, int k, int64_t* out_ids, float* out_dist,
+               IoPlan& io, Arena& ar, cudaStream_t st) {
+  if (m > 0 && !is_device_ptr(Q)) {
+    float* q;
+    RBC_TRY(ar.alloc(&q, m * d));
+    RBC_CUDA(cudaMemcpyAsync(q, Q, (size_t)m * d * sizeof(float), cudaMemcpyHostToDevice, st));
+    io.Qdev = q;
+  } else {
+    io.Qdev = Q;
+  }
+  io.ids_host = m > 0 && !is_device_ptr(out_ids);
+  io.dist_host = m > 0 && !is_device_ptr(out_dist);
+  if (io.ids_host) {
+    RBC_TRY(ar.alloc(&io.ids_dev, m * k));
+  } else {
+    io.ids_dev = out_ids;
+  }
+  if (io.dist_host) {
+    RBC_TRY(ar.alloc(&io.dist_dev, m * k));
+  } else {
+    io.dist_dev = out_dist;
+  }
+  return RBC_OK;
+}
+
+int io_finish(int64_t m, int k, int64_t* out_ids, float* out_dist, const IoPlan& io,
+              cudaStream_t st) {
+  if (m == 0) return RBC_OK;
+  if (io.ids_host)
+    RBC_CUDA(cudaMemcpyAsync(out_ids, io.ids_dev, (size_t)m * k * sizeof(int64_t),
+                             cudaMemcpyDeviceToHost, st));
+  if (io.dist_host)
+    RBC_CUDA(cudaMemcpyAsync(out_dist, io.dist_dev, (size_t)m * k * sizeof(float),
+                             cudaMemcpyDeviceToHost, st));
+  if (io.ids_host || io.dist_host) RBC_CUDA(cudaStreamSynchronize(st));
+  return RBC_OK;
+}
+
+int valid_enums(int metric, int storage) {
+  if (metric != RBC_L2 && metric != RBC_L1) {
+    set_error("unknown metric %d", metric);
+    return RBC_ERR_ARG;
+  }
+  if (storage != RBC_F32 && storage != RBC_BF16 && storage != RBC_F16) {
+    set_error("unknown storage %d", storage);
+    return RBC_ERR_ARG;
+  }
+  return RBC_OK;
+}
+
+bool uses_lp(int storage, int metric) { return storage != RBC_F32 && metric == RBC_L2; }
+
+int choose_c(int k, bool lp, int rerank_c) {
+  int c = k + 1;
+  if (lp) c = rerank_c > 0 ? std::max(rerank_c, k + 1) : (k <= 1 ? 16 : 32);
+  return std::min(c, MAX_C);
+}
+
+int lp_width(int c) {
+  for (int w : {8, 16, 32})
+    if (w >= c) return w;
+  return -1;
+}
+
+// ---------------------------------------------------------------------------
+// database views for the BF core
+// ---------------------------------------------------------------------------
+struct DbView {
+  const float* X32 = nullptr;  // [rows, d] FP32 rows
+  const int* xid = nullptr;    // row -> original id (nullptr = identity)
+  int64_t rows = 0;
+  const void* Xlp = nullptr;   // [rows, dpad]
+  const float* xnorm = nullptr;
+  int dpad = 0;
+  const unsigned* lp_max = nullptr;  // [0] max |x - x~|, [1] max |x~| (float bits)
+};
+
+// Dense BF(Q, DB) with the FP32 CUDA-core kernel; results for query row i go
+// to output row qorig[i] (identity when null).  `cnt` = 3 counters.
+int bf_dense_f32(const float* Qdev, int64_t m, const DbView& db, int d, int k, int metric,
+                 const int* qorig, int64_t* out_ids, float* out_dist, int* cnt, Arena& ar,
+                 cudaStream_t st) {
+  if (m == 0) return RBC_OK;
+  const int c_out = choose_c(k, false, 0);
+  const int C = simt_list_width(c_out);
+  const int64_t tiles = (m + TQ - 1) / TQ;
+  const int sms = sm_count();
+  int64_t splits = (8LL * sms + tiles - 1) / tiles;
+  splits = std::max<int64_t>(1, std::min<int64_t>(splits, std::max<int64_t>(1, db.rows / 512)));
+  int64_t chunk = (db.rows + splits - 1) / splits;
+  splits = (db.rows + chunk - 1) / chunk;
+  const int64_t items = tiles * splits;
+  float* ps;
+  int* pi;
+  RBC_TRY(ar.alloc(&ps, items * TQ * 2 * C));
+  RBC_TRY(ar.alloc(&pi, items * TQ * 2 * C));
+  TileWork w{};
+  w.num_items = (int)items;
+  w.m = m;
+  w.n = db.rows;
+  w.dense_splits = (int)splits;
+  w.dense_chunk = chunk;
+  int grid = (int)std::min<int64_t>(items, (int64_t)sms * 2 * 16);
+  RBC_TRY(launch_bf_simt_topc(Qdev, db.X32, d, metric, C, w, TopOut{ps, pi}, grid, st));
+  SelectArgs a{};
+  a.part_score = ps;
+  a.part_idx = pi;
+  a.C = C;
+  a.nsub = 2;
+  a.dense_splits = (int)splits;
+  a.m = m;
+  a.Q32 = Qdev;
+  a.d = d;
+  a.metric = metric;
+  a.qorig = qorig;
+  a.X32 = db.X32;
+  a.xid = db.xid;
+  a.lp = 0;
+  a.simt_eps = simt_eps(d);
+  a.k = k;
+  a.c_out = c_out;
+  a.out_ids = out_ids;
+  a.out_dist = out_dist;
+  a.counters = cnt;
+  return launch_select(a, st);
+}
+
+// Rows of a query buffer that failed certification are searched again with
+// the FP32 kernel over every row of `db` (a superset of what they needed).
+int fallback_f32(const float* Qbuf, const int* rows_dev, int nrows, const int* qorig,
+                 const DbView& db, int d, int k, int metric, int64_t* out_ids, float* out_dist,
+                 int* cnt, Arena& ar, cudaStream_t st) {
+  if (nrows <= 0) return RBC_OK;
+  float* Qf;
+  int* forig;
+  RBC_TRY(ar.alloc(&Qf, (int64_t)nrows * d));
+  RBC_TRY(ar.alloc(&forig, nrows));
+  RBC_TRY(launch_gather_rows(Qbuf, nullptr, rows_dev, nrows, d, Qf, st));
+  RBC_TRY(launch_map_rows(rows_dev, nullptr, nrows, qorig, forig, st));
+  return bf_dense_f32(Qf, nrows, db, d, k, metric, forig, out_ids, out_dist, cnt, ar, st);
+}
+
+// Low-precision copy of a query buffer.
+struct LpQueries {
+  void* lp = nullptr;
+  float* norm = nullptr;
+  float* err = nullptr;
+};
+
+int lp_queries(const float* Qdev, int64_t m, int d, int dpad, int storage, LpQueries& q,
+               Arena& ar, cudaStream_t st) {
+  uint16_t* buf;
+  RBC_TRY(ar.alloc(&buf, std::max<int64_t>(m, 1) * dpad));
+  RBC_TRY(ar.alloc(&q.norm, m));
+  RBC_TRY(ar.alloc(&q.err, m));
+  q.lp = buf;
+  return launch_to_lowp(Qdev, m, d, dpad, storage, buf, q.norm, q.err, nullptr, nullptr, st);
+}
+
+// Select (merge + re-rank + certification) for the low-precision pass, then
+// the FP32 re-search of uncertified rows (one host read of their count).
+int select_lp_and_fallback(const float* ps, const int* pi, int C, const int* tile_slot_off,
+                           int dense_splits, int64_t m, const float* Qbuf, const LpQueries& ql,
+                           const DbView& db, int d, int k, int c_out, const int* qorig,
+                           int64_t* out_ids, float* out_dist, int* cnt, Arena& ar,
+                           cudaStream_t st) {
+  int* fb_rows;
+  RBC_TRY(ar.alloc(&fb_rows, m));
+  SelectArgs a{};
+  a.part_score = ps;
+  a.part_idx = pi;
+  a.C = C;
+  a.nsub = 1;
+  a.tile_slot_off = tile_slot_off;
+  a.dense_splits = dense_splits;
+  a.m = m;
+  a.Q32 = Qbuf;
+  a.d = d;
+  a.metric = RBC_L2;
+  a.qorig = qorig;
+  a.X32 = db.X32;
+  a.xid = db.xid;
+  a.lp = 1;
+  a.q_lpnorm = ql.norm;
+  a.q_err = ql.err;
+  a.x_err_max_bits = db.lp_max;
+  a.x_norm_max_bits = db.lp_max + 1;
+  a.k = k;
+  a.c_out = c_out;
+  a.out_ids = out_ids;
+  a.out_dist = out_dist;
+  a.fallback_rows = fb_rows;
+  a.counters = cnt;
+  RBC_TRY(launch_select(a, st));
+  int nfb = 0;
+  RBC_CUDA(cudaMemcpyAsync(&nfb, cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RBC_CUDA(cudaStreamSynchronize(st));
+  if (nfb > 0)
+    RBC_TRY(fallback_f32(Qbuf, fb_rows, nfb, qorig, db, d, k, RBC_L2, out_ids, out_dist, cnt + 4,
+                         ar, st));
+  return RBC_OK;
+}
+
+// Dense BF(Q, DB) on the tensor cores (L2, bf16 / fp16).
+int bf_dense_lp(const float* Qdev, int64_t m, const DbView& db, int d, int k, int storage,
+                int rerank_c, int64_t* out_ids, float* out_dist, int* cnt, Arena& ar,
+                cudaStream_t st) {
+  if (m == 0) return RBC_OK;
+  const int c_out = choose_c(k, true, rerank_c);
+  const int C = lp_width(c_out);
+  LpQueries ql;
+  RBC_TRY(lp_queries(Qdev, m, d, db.dpad, storage, ql, ar, st));
+  const int64_t tiles = (m + TQ - 1) / TQ;
+  const int sms = sm_count();
+  int64_t splits = (4LL * sms + tiles - 1) / tiles;
+  splits = std::max<int64_t>(1, std::min<int64_t>(splits, std::max<int64_t>(1, db.rows / 2048)));
+  int64_t chunk = (db.rows + splits - 1) / splits;
+  chunk = (chunk + 255) / 256 * 256;
+  splits = (db.rows + chunk - 1) / chunk;
+  const int64_t items = tiles * splits;
+  float* ps;
+  int* pi;
+  RBC_TRY(ar.alloc(&ps, items * TQ * C));
+  RBC_TRY(ar.alloc(&pi, items * TQ * C));
+  TileWork w{};
+  w.num_items = (int)items;
+  w.m = m;
+  w.n = db.rows;
+  w.dense_splits = (int)splits;
+  w.dense_chunk = chunk;
+  LpMatrix Qm{ql.lp, ql.norm, m, db.dpad, storage};
+  LpMatrix Xm{db.Xlp, db.xnorm, db.rows, db.dpad, storage};
+  uint32_t* dev_err;
+  RBC_TRY(ar.alloc(&dev_err, 1));
+  RBC_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(uint32_t), st));
+  int grid = (int)std::min<int64_t>(items, (int64_t)sms);
+  RBC_TRY(launch_bf_tc_topc(Qm, Xm, C, w, TopOut{ps, pi}, grid, st, dev_err));
+  RBC_TRY(select_lp_and_fallback(ps, pi, C, nullptr, (int)splits, m, Qdev, ql, db, d, k, c_out,
+                                 nullptr, out_ids, out_dist, cnt, ar, st));
+  uint32_t herr = 0;
+  RBC_CUDA(cudaMemcpyAsync(&herr, dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  RBC_CUDA(cudaStreamSynchronize(st));
+  if (herr) {
+    set_error("tensor-core kernel reported device error flags 0x%x", herr);
+    return (herr & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
+  }
+  return RBC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// build (Sections 4, 5.2)
+// ---------------------------------------------------------------------------
+int build_exact(rbc_index* ix, const float* Xdev, const std::vector<int64_t>& reps,
+                cudaStream_t st) {
+  const int64_t n = ix->n;
+  const int d = ix->d, n_r = ix->n_r, metric = ix->metric;
+  Arena ar(st);
+  RBC_TRY(ix->alloc(&ix->reps, n_r));
+  RBC_CUDA(cudaMemcpyAsync(ix->reps, reps.data(), n_r * sizeof(int64_t), cudaMemcpyHostToDevice,
+                           st));
+  RBC_TRY(ix->alloc(&ix->R32, (int64_t)n_r * d));
+  RBC_TRY(launch_gather_rows(Xdev, ix->reps, nullptr, n_r, d, ix->R32, st));
+  // BF(X, R): owner = nearest representative ordinal (ties to the smaller
+  // ordinal = smaller id since R is sorted), owner distance
+  int64_t* owner;
+  float* odist;
+  RBC_TRY(ar.alloc(&owner, n));
+  RBC_TRY(ar.alloc(&odist, n));
+  Counters cn;
+  RBC_TRY(counters_alloc(cn, ar, st));
+  DbView dbR;
+  dbR.X32 = ix->R32;
+  dbR.rows = n_r;
+  RBC_TRY(bf_dense_f32(Xdev, n, dbR, d, 1, metric, nullptr, owner, odist, cn.c, ar, st));
+  // lists: stable counting sort by owner
+  ix->list_entries = n;
+  RBC_TRY(ix->alloc(&ix->offsets, n_r + 1));
+  RBC_TRY(ix->alloc(&ix->members, n));
+  int* scratch;
+  RBC_TRY(ar.alloc(&scratch, counting_sort_scratch_ints(n, n_r)));
+  RBC_TRY(launch_counting_sort(owner, n, n_r, ix->members, ix->offsets, scratch, st));
+  RBC_TRY(ix->alloc(&ix->X32, n * d));
+  RBC_TRY(launch_gather_rows(Xdev, nullptr, ix->members, n, d, ix->X32, st));
+  // radii psi_r, inflated by the FP32 bound of the owner distances
+  RBC_TRY(ix->alloc(&ix->psi, n_r));
+  RBC_TRY(launch_list_radii(odist, ix->members, ix->offsets, n_r, 2.0f * rerank_eps_host(d),
+                            ix->psi, st));
+  if (ix->storage != RBC_F32 && metric == RBC_L2) {
+    ix->dpad = pad64(d);
+    uint16_t* xl;
+    uint16_t* rl;
+    RBC_TRY(ix->alloc(&xl, n * ix->dpad));
+    RBC_TRY(ix->alloc(&ix->xnorm, n));
+    RBC_TRY(ix->alloc(&ix->lp_max, 4));
+    RBC_TRY(ix->alloc(&rl, (int64_t)n_r * ix->dpad));
+    RBC_TRY(ix->alloc(&ix->rnorm, n_r));
+    RBC_CUDA(cudaMemsetAsync(ix->lp_max, 0, 4 * sizeof(unsigned), st));
+    RBC_TRY(launch_to_lowp(ix->X32, n, d, ix->dpad, ix->storage, xl, ix->xnorm, nullptr,
+                           ix->lp_max, ix->lp_max + 1, st));
+    RBC_TRY(launch_to_lowp(ix->R32, n_r, d, ix->dpad, ix->storage, rl, ix->rnorm, nullptr,
+                           ix->lp_max + 2, ix->lp_max + 3, st));
+    ix->Xlp = xl;
+    ix->Rlp = rl;
+  }
+  RBC_CUDA(cudaStreamSynchronize(st));
+  return RBC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// exact search (Section 5.2)
+// ---------------------------------------------------------------------------
+constexpr int64_t MAX_BATCH = 131072;  // queries per internal batch (bounds workspace)
+
+int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, int64_t* ids,
+                       float* dist, const Counters& cn, int64_t* items_total, Arena& ar,
+                       cudaStream_t st) {
+  const int d = ix->d, n_r = ix->n_r, metric = ix->metric;
+  const int64_t n = ix->list_entries;
+  const int sms = sm_count();
+  const bool lp = uses_lp(ix->storage, metric) && ix->Xlp != nullptr;
+  const int64_t tiles = (mb + TQ - 1) / TQ;
+
+  // stage 1: BF(Q, R) keeping every distance
+  float* D;
+  RBC_TRY(ar.alloc(&D, mb * n_r));
+  TileWork w1{};
+  w1.num_items = (int)tiles;
+  w1.m = mb;
+  w1.n = n_r;
+  w1.dense_splits = 1;
+  w1.dense_chunk = n_r;
+  RBC_TRY(launch_bf_simt_store(Qb, ix->R32, d, metric, w1, D, n_r,
+                               (int)std::min<int64_t>(tiles, (int64_t)sms * 2 * 16), st));
+  float *g1, *gk;
+  int64_t* nearest;
+  RBC_TRY(ar.alloc(&g1, mb));
+  RBC_TRY(ar.alloc(&gk, mb));
+  RBC_TRY(ar.alloc(&nearest, mb));
+  RBC_TRY(launch_row_stats(D, mb, n_r, k, g1, gk, nearest, st));
+  // queries ordered by nearest representative, so each tile holds nearby queries
+  int *qperm, *qoff, *scratch;
+  RBC_TRY(ar.alloc(&qperm, mb));
+  RBC_TRY(ar.alloc(&qoff, n_r + 1));
+  RBC_TRY(ar.alloc(&scratch, counting_sort_scratch_ints(mb, n_r)));
+  RBC_TRY(launch_counting_sort(nearest, mb, n_r, qperm, qoff, scratch, st));
+  float* Qp;
+  RBC_TRY(ar.alloc(&Qp, mb * d));
+  RBC_TRY(launch_gather_rows(Qb, nullptr, qperm, mb, d, Qp, st));
+  // pruning -> per tile union of surviving lists
+  const int words = (n_r + 31) / 32;
+  uint32_t* tmask;
+  int64_t* tpts;
+  int* qkept;
+  RBC_TRY(ar.alloc(&tmask, tiles * words));
+  RBC_TRY(ar.alloc(&tpts, tiles));
+  RBC_TRY(ar.alloc(&qkept, mb));
+  RBC_TRY(launch_prune(D, qperm, mb, n_r, g1, gk, ix->psi, ix->offsets, simt_eps(d), tmask, tpts,
+                       qkept, st));
+  RBC_TRY(launch_sum_i32(qkept, mb, cn.sums, st));
+  RBC_TRY(launch_sum_i64(tpts, tiles, cn.sums + 1, st));
+  // work items
+  int64_t W = (tiles * n + 16LL * sms - 1) / (16LL * sms);
+  W = std::max<int64_t>(W, 4096);
+  W = std::min<int64_t>(W, std::max<int64_t>(n, 1));
+  W = (W + 255) / 256 * 256;
+  const int item_cap = (int)((n + W - 1) / W) + 1;
+  const int seg_cap = n_r + item_cap + 1;
+  int *toff, *tcnt;
+  RBC_TRY(ar.alloc(&toff, tiles + 1));
+  RBC_TRY(ar.alloc(&tcnt, tiles));
+  RBC_TRY(launch_item_offsets(tpts, (int)tiles, (int)W, tcnt, toff, st));
+  WorkItem* items;
+  Seg* segs;
+  uint32_t* dev_err;
+  RBC_TRY(ar.alloc(&items, tiles * item_cap));
+  RBC_TRY(ar.alloc(&segs, tiles * seg_cap));
+  RBC_TRY(ar.alloc(&dev_err, 1));
+  RBC_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(uint32_t), st));
+  RBC_TRY(launch_workgen_items(tmask, ix->offsets, n_r, mb, (int)W, item_cap, seg_cap, toff, items,
+                               segs, dev_err, st));
+  *items_total += tiles * item_cap;
+  TileWork w2{};
+  w2.items = items;
+  w2.num_items_dev = toff + tiles;
+  w2.num_items = (int)(tiles * item_cap);
+  w2.segs = segs;
+  w2.m = mb;
+  w2.n = n;
+  DbView db;
+  db.X32 = ix->X32;
+  db.xid = ix->members;
+  db.rows = n;
+  db.Xlp = ix->Xlp;
+  db.xnorm = ix->xnorm;
+  db.dpad = ix->dpad;
+  db.lp_max = ix->lp_max;
+  const int64_t cap_items = tiles * item_cap;
+  if (!lp) {
+    const int c_out = choose_c(k, false, 0);
+    const int C = simt_list_width(c_out);
+    float* ps;
+    int* pi;
+    RBC_TRY(ar.alloc(&ps, cap_items * TQ * 2 * C));
+    RBC_TRY(ar.alloc(&pi, cap_items * TQ * 2 * C));
+    RBC_TRY(launch_bf_simt_topc(Qp, ix->X32, d, metric, C, w2, TopOut{ps, pi},
+                                (int)std::min<int64_t>(cap_items, (int64_t)sms * 2 * 8), st));
+    SelectArgs a{};
+    a.part_score = ps;
+    a.part_idx = pi;
+    a.C = C;
+    a.nsub = 2;
+    a.tile_slot_off = toff;
+    a.m = mb;
+    a.Q32 = Qp;
+    a.d = d;
+    a.metric = metric;
+    a.qorig = qperm;
+    a.X32 = ix->X32;
+    a.xid = ix->members;
+    a.simt_eps = simt_eps(d);
+    a.k = k;
+    a.c_out = c_out;
+    a.out_ids = ids;
+    a.out_dist = dist;
+    a.counters = cn.c;
+    RBC_TRY(launch_select(a, st));
+  } else {
+    const int c_out = choose_c(k, true, ix->rerank_c);
+    const int C = lp_width(c_out);
+    LpQueries ql;
+    RBC_TRY(lp_queries(Qp, mb, d, ix->dpad, ix->storage, ql, ar, st));
+    float* ps;
+    int* pi;
+    RBC_TRY(ar.alloc(&ps, cap_items * TQ * C));
+    RBC_TRY(ar.alloc(&pi, cap_items * TQ * C));
+    LpMatrix Qm{ql.lp, ql.norm, mb, ix->dpad, ix->storage};
+    LpMatrix Xm{ix->Xlp, ix->xnorm, n, ix->dpad, ix->storage};
+    RBC_TRY(launch_bf_tc_topc(Qm, Xm, C, w2, TopOut{ps, pi}, sms, st, dev_err));
+    RBC_TRY(select_lp_and_fallback(ps, pi, C, toff, 0, mb, Qp, ql, db, d, k, c_out, qperm, ids,
+                                   dist, cn.c, ar, st));
+  }
+  uint32_t herr = 0;
+  RBC_CUDA(cudaMemcpyAsync(&herr, dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  RBC_CUDA(cudaStreamSynchronize(st));
+  if (herr) {
+    set_error("stage-two work generation / kernel reported device error flags 0x%x", herr);
+    return (herr & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
+  }
+  return RBC_OK;
+}
+
+}  // namespace
+}  // namespace rbc
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+using namespace rbc;
+
+extern "C" {
+
+void rbc_default_opts(rbc_opts* o) {
+  if (o) memset(o, 0, sizeof(*o));
+}
+
+const char* rbc_last_error(void) { return last_error_text(); }
+
+int rbc_sample_reps(int64_t n, int32_t n_r, uint64_t seed, int64_t* out) {
+  if (n < 1 || n_r < 1 || n_r > n || !out) {
+    set_error("rbc_sample_reps: need 1 <= n_r <= n and out != NULL (n=%lld n_r=%d)",
+              (long long)n, n_r);
+    return RBC_ERR_ARG;
+  }
+  std::vector<int64_t> r = sample_reps_host(n, n_r, seed);
+  memcpy(out, r.data(), r.size() * sizeof(int64_t));
+  return RBC_OK;
+}
+
+int rbc_last_stats(rbc_search_stats* out) {
+  if (!out) {
+    set_error("rbc_last_stats: NULL");
+    return RBC_ERR_ARG;
+  }
+  if (t_stats_pending) {
+    cudaError_t e = cudaStreamSynchronize(t_stats_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+    const unsigned long long* v = t_stats_host->v;
+    t_stats_fixed.kept_reps = (int64_t)v[0];
+    t_stats_fixed.tile_points = (int64_t)v[1];
+    t_stats_fixed.uncertified = (int64_t)v[2];
+    t_stats_fixed.fp64_ties = (int64_t)v[3];
+    t_stats_fixed.boundary_ties = (int64_t)v[4];
+    t_stats_pending = false;
+  }
+  *out = t_stats_fixed;
+  return RBC_OK;
+}
+
+int bf_search(const float* Q, int64_t m, const float* X, int64_t n, int32_t d, int32_t k,
+              int32_t metric, int32_t storage, int64_t* out_ids, float* out_dist, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (m < 0 || n < 1 || d < 1 || k < 1 || n >= (1LL << 31) || m >= (1LL << 31)) {
+    set_error("bf_search: bad sizes m=%lld n=%lld d=%d k=%d", (long long)m, (long long)n, d, k);
+    return RBC_ERR_ARG;
+  }
+  RBC_TRY(valid_enums(metric, storage));
+  if (!X || (m > 0 && (!Q || !out_ids || !out_dist))) {
+    set_error("bf_search: NULL pointer");
+    return RBC_ERR_ARG;
+  }
+  if (k > MAX_C - 1) {
+    set_error("bf_search: k=%d exceeds the supported maximum %d", k, MAX_C - 1);
+    return RBC_ERR_UNSUPPORTED;
+  }
+  if (d > MAX_D) {
+    set_error("bf_search: d=%d exceeds %d", d, MAX_D);
+    return RBC_ERR_UNSUPPORTED;
+  }
+  Arena ar(st);
+  IoPlan io;
+  RBC_TRY(io_prepare(Q, m, d, k, out_ids, out_dist, io, ar, st));
+  const float* Xdev = X;
+  if (!is_device_ptr(X)) {
+    float* x;
+    RBC_TRY(ar.alloc(&x, n * d));
+    RBC_CUDA(cudaMemcpyAsync(x, X, (size_t)n * d * sizeof(float), cudaMemcpyHostToDevice, st));
+    Xdev = x;
+  }
+  Counters cn;
+  RBC_TRY(counters_alloc(cn, ar, st));
+  DbView db;
+  db.X32 = Xdev;
+  db.rows = n;
+  if (!uses_lp(storage, metric)) {
+    RBC_TRY(bf_dense_f32(io.Qdev, m, db, d, k, metric, nullptr, io.ids_dev, io.dist_dev, cn.c,
+                         ar, st));
+  } else {
+    db.dpad = pad64(d);
+    uint16_t* xl;
+    float* xn;
+    unsigned* mx;
+    RBC_TRY(ar.alloc(&xl, n * db.dpad));
+    RBC_TRY(ar.alloc(&xn, n));
+    RBC_TRY(ar.alloc(&mx, 2));
+    RBC_CUDA(cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned), st));
+    RBC_TRY(launch_to_lowp(Xdev, n, d, db.dpad, storage, xl, xn, nullptr, mx, mx + 1, st));
+    db.Xlp = xl;
+    db.xnorm = xn;
+    db.lp_max = mx;
+    RBC_TRY(bf_dense_lp(io.Qdev, m, db, d, k, storage, 0, io.ids_dev, io.dist_dev, cn.c, ar, st));
+  }
+  RBC_TRY(stats_publish(cn, m, 0, ar, st));
+  RBC_TRY(io_finish(m, k, out_ids, out_dist, io, st));
+  return RBC_OK;
+}
+
+int rbc_build(const float* X, int64_t n, int32_t d, int32_t n_r, int32_t s, int32_t metric,
+              const rbc_opts* opts, void* stream, rbc_index** out) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!out || !X) {
+    set_error("rbc_build: NULL pointer");
+    return RBC_ERR_ARG;
+  }
+  *out = nullptr;
+  rbc_opts o;
+  rbc_default_opts(&o);
+  if (opts) o = *opts;
+  if (n < 1 || d < 1 || n_r < 1 || n_r > n || n >= (1LL << 31)) {
+    set_error("rbc_build: bad sizes n=%lld d=%d n_r=%d", (long long)n, d, n_r);
+    return RBC_ERR_ARG;
+  }
+  RBC_TRY(valid_enums(metric, o.storage));
+  if (o.mode != RBC_EXACT && o.mode != RBC_ONESHOT) {
+    set_error("rbc_build: unknown mode %d", o.mode);
+    return RBC_ERR_ARG;
+  }
+  if (o.mode == RBC_ONESHOT && (s < 1 || s > n)) {
+    set_error("rbc_build: one-shot needs 1 <= s <= n (s=%d)", s);
+    return RBC_ERR_ARG;
+  }
+  if (o.rerank_c < 0 || o.rerank_c > MAX_C || o.reserved != 0) {
+    set_error("rbc_build: rerank_c must be in [0, %d] and reserved 0", MAX_C);
+    return RBC_ERR_ARG;
+  }
+  if (d > MAX_D) {
+    set_error("rbc_build: d=%d exceeds %d", d, MAX_D);
+    return RBC_ERR_UNSUPPORTED;
+  }
+  if (o.mode == RBC_ONESHOT) {
+    set_error("rbc_build: one-shot mode is not available in this build");
+    return RBC_ERR_UNSUPPORTED;
+  }
+  std::vector<int64_t> reps;
+  if (o.rep_ids) {
+    reps.assign(o.rep_ids, o.rep_ids + n_r);
+    for (int i = 0; i < n_r; ++i)
+      if (reps[i] < 0 || reps[i] >= n || (i && reps[i] <= reps[i - 1])) {
+        set_error("rbc_build: rep_ids must be ascending, distinct and inside [0, n)");
+        return RBC_ERR_ARG;
+      }
+  } else {
+    reps = sample_reps_host(n, n_r, o.seed);
+  }
+  rbc_index* ix = new (std::nothrow) rbc_index();
+  if (!ix) {
+    set_error("rbc_build: host allocation failed");
+    return RBC_ERR_OOM;
+  }
+  ix->n = n;
+  ix->d = d;
+  ix->n_r = n_r;
+  ix->s = s;
+  ix->metric = metric;
+  ix->mode = o.mode;
+  ix->storage = o.storage;
+  ix->rerank_c = o.rerank_c;
+  int rc;
+  {
+    Arena ar(st);
+    const float* Xdev = X;
+    rc = RBC_OK;
+    if (!is_device_ptr(X)) {
+      float* x = nullptr;
+      rc = ar.alloc(&x, n * d);
+      if (rc == RBC_OK) {
+        cudaError_t e =
+            cudaMemcpyAsync(x, X, (size_t)n * d * sizeof(float), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__);
+      }
+      Xdev = x;
+    }
+    if (rc == RBC_OK) rc = build_exact(ix, Xdev, reps, st);
+  }
+  if (rc != RBC_OK) {
+    cudaStreamSynchronize(st);
+    delete ix;
+    return rc;
+  }
+  *out = ix;
+  return RBC_OK;
+}
+
+int rbc_search(const rbc_index* ix, const float* Q, int64_t m, int32_t k, int64_t* out_ids,
+               float* out_dist, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!ix || (m > 0 && (!Q || !out_ids || !out_dist))) {
+    set_error("rbc_search: NULL pointer");
+    return RBC_ERR_ARG;
+  }
+  if (m < 0 || k < 1 || k > ix->n || m >= (1LL << 31)) {
+    set_error("rbc_search: bad sizes m=%lld k=%d (n=%lld)", (long long)m, k, (long long)ix->n);
+    return RBC_ERR_ARG;
+  }
+  if (k > MAX_C - 1) {
+    set_error("rbc_search: k=%d exceeds the supported maximum %d", k, MAX_C - 1);
+    return RBC_ERR_UNSUPPORTED;
+  }
+  Arena ar(st);
+  IoPlan io;
+  RBC_TRY(io_prepare(Q, m, ix->d, k, out_ids, out_dist, io, ar, st));
+  Counters cn;
+  RBC_TRY(counters_alloc(cn, ar, st));
+  int64_t items = 0;
+  for (int64_t b0 = 0; b0 < m; b0 += MAX_BATCH) {
+    int64_t mb = std::min<int64_t>(MAX_BATCH, m - b0);
+    Arena bar(st);
+    RBC_TRY(search_exact_batch(ix, io.Qdev + b0 * ix->d, mb, k, io.ids_dev + b0 * k,
+                               io.dist_dev + b0 * k, cn, &items, bar, st));
+  }
+  RBC_TRY(stats_publish(cn, m, items, ar, st));
+  RBC_TRY(io_finish(m, k, out_ids, out_dist, io, st));
+  return RBC_OK;
+}
+
+int rbc_index_info(const rbc_index* ix, rbc_index_desc* out) {
+  if (!ix || !out) {
+    set_error("rbc_index_info: NULL");
+    return RBC_ERR_ARG;
+  }
+  out->n = ix->n;
+  out->d = ix->d;
+  out->n_r = ix->n_r;
+  out->s = ix->s;
+  out->metric = ix->metric;
+  out->mode = ix->mode;
+  out->storage = ix->storage;
+  out->list_entries = ix->list_entries;
+  out->device_bytes = ix->bytes;
+  return RBC_OK;
+}
+
+int rbc_index_export(const rbc_index* ix, int64_t* reps, int64_t* offsets, int64_t* members,
+                     float* psi) {
+  if (!ix) {
+    set_error("rbc_index_export: NULL index");
+    return RBC_ERR_ARG;
+  }
+  // the build synchronised its stream before returning, so the index is complete
+  if (reps)
+    RBC_CUDA(cudaMemcpy(reps, ix->reps, ix->n_r * sizeof(int64_t), cudaMemcpyDeviceToHost));
+  if (offsets) {
+    std::vector<int> o(ix->n_r + 1);
+    RBC_CUDA(cudaMemcpy(o.data(), ix->offsets, o.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < o.size(); ++i) offsets[i] = o[i];
+  }
+  if (members) {
+    std::vector<int> mm((size_t)ix->list_entries);
+    RBC_CUDA(cudaMemcpy(mm.data(), ix->members, mm.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < mm.size(); ++i) members[i] = mm[i];
+  }
+  if (psi) RBC_CUDA(cudaMemcpy(psi, ix->psi, ix->n_r * sizeof(float), cudaMemcpyDeviceToHost));
+  return RBC_OK;
+}
+
+void rbc_free(rbc_index* ix) {
+  // cudaFree waits for outstanding device work that may still read the index
+  delete ix;
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// Shared device/host definitions for the RBC library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cfloat>
+#include <cmath>
+
+#include "../../include/rbc.h"
+
+namespace rbc {
+
+// Query tile height: every distance kernel processes queries in tiles of this
+// many rows, and the exact search forms one union of kept lists per tile.
+constexpr int TQ = 128;
+
+// One contiguous run of database rows [x_begin, x_end) in a database buffer.
+struct Seg {
+  int32_t x_begin;
+  int32_t x_end;
+};
+
+// A unit of distance work: queries [q_row0, q_row0 + nq) of the query buffer
+// against the union of segs[seg_begin .. seg_end); results go to partial slot
+// `slot`.
+struct WorkItem {
+  int32_t q_row0;
+  int32_t nq;
+  int32_t seg_begin;
+  int32_t seg_end;
+  int32_t slot;
+  int32_t tile;
+};
+
+// Ordering used by every selection: (score, index) lexicographic.
+__device__ __forceinline__ bool pair_lt(float a, int ia, float b, int ib) {
+  return a < b || (a == b && ia < ib);
+}
+
+// Sorted register list of C (score, index) pairs, ascending.  Insert walks the
+// list once, carrying the larger element of each compare-swap downwards; the
+// last element falls off.  Fully unrolled so the arrays stay in registers.
+template <int C>
+struct TopList {
+  float s[C];
+  int i[C];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      s[j] = INFINITY;
+      i[j] = INT32_MAX;
+    }
+  }
+  __device__ __forceinline__ float worst() const { return s[C - 1]; }
+  __device__ __forceinline__ bool admits(float v, int id) const {
+    return pair_lt(v, id, s[C - 1], i[C - 1]);
+  }
+  __device__ __forceinline__ void insert(float v, int id) {
+    float cv = v;
+    int ci = id;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      bool lt = pair_lt(cv, ci, s[j], i[j]);
+      float ts = lt ? s[j] : cv;
+      int ti = lt ? i[j] : ci;
+      s[j] = lt ? cv : s[j];
+      i[j] = lt ? ci : i[j];
+      cv = ts;
+      ci = ti;
+    }
+  }
+};
+
+// Device-side error flags (bit mask), read back by the host after a call.
+enum : uint32_t {
+  DEV_ERR_TIMEOUT = 1u,      // a bounded wait gave up
+  DEV_ERR_BOUNDS = 2u,       // an index check failed (access skipped)
+  DEV_ERR_CAPACITY = 4u,     // a worst-case buffer bound was exceeded
+};
+
+}  // namespace rbc
+
+// ---------------------------------------------------------------------------
+// Host-side error plumbing shared by the .cu files.
+// ---------------------------------------------------------------------------
+namespace rbc {
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+}  // namespace rbc
+
+#define RBC_CUDA(call)                                                                \
+  do {                                                                                \
+    cudaError_t _e = (call);                                                          \
+    if (_e != cudaSuccess) return ::rbc::cuda_fail(_e, #call, __FILE__, __LINE__);    \
+  } while (0)
+
+#define RBC_LAUNCH_CHECK(what)                                                        \
+  do {                                                                                \
+    cudaError_t _e = cudaGetLastError();                                              \
+    if (_e != cudaSuccess) return ::rbc::cuda_fail(_e, what, __FILE__, __LINE__);     \
+  } while (0)

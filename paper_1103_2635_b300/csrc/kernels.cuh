@@ -1,0 +1,133 @@
+// Launch interfaces shared by the host orchestration and the kernel files.
+#pragma once
+
+#include "common.cuh"
+
+namespace rbc {
+
+constexpr int MAX_D = 256;       // largest supported dimension
+constexpr int SIMT_MAX_D = 256;  // FP32 tile kernel limit (query tile in shared memory)
+constexpr int MAX_C = 32;        // largest candidate list per query
+
+// Where a tile kernel finds its work.  items == nullptr selects the dense
+// form: item = tile * dense_splits + split, query rows [tile*TQ, +TQ) of an
+// m-row buffer against database rows [split*dense_chunk, +dense_chunk) of n.
+struct TileWork {
+  const WorkItem* items;
+  const int* num_items_dev;  // list form: device-side item count (or nullptr)
+  int num_items;             // dense form / host-known count
+  const Seg* segs;           // list form: segment table
+  int64_t m;
+  int64_t n;
+  int dense_splits;
+  int64_t dense_chunk;
+};
+
+// Per-(slot, query row, sub-list) top-C output of a tile kernel.
+struct TopOut {
+  float* score;
+  int* idx;
+};
+
+int simt_list_width(int c_needed);
+int launch_bf_simt_topc(const float* Q, const float* X, int d, int metric, int C,
+                        const TileWork& w, const TopOut& out, int grid, cudaStream_t st);
+int launch_bf_simt_store(const float* Q, const float* X, int d, int metric, const TileWork& w,
+                         float* store, int64_t store_ld, int grid, cudaStream_t st);
+
+// ---- low-precision (tensor-core) path ----
+struct LpMatrix {
+  const void* data;  // [rows, dpad] bf16 / f16, row-major, rows 16-byte aligned
+  const float* norm; // [rows] |x~|^2 in FP32
+  int64_t rows;
+  int dpad;          // multiple of 64
+  int storage;       // RBC_BF16 / RBC_F16
+};
+
+bool tc_available();
+int launch_bf_tc_topc(const LpMatrix& Qm, const LpMatrix& Xm, int C, const TileWork& w,
+                      const TopOut& out, int grid, cudaStream_t st, uint32_t* dev_err);
+
+// ---- merge + re-rank + certification ----
+struct SelectArgs {
+  const float* part_score;
+  const int* part_idx;
+  int C;       // entries per sub-list
+  int nsub;    // sub-lists per (slot, row)
+  const int* tile_slot_off;  // list form: slots of tile t are [off[t], off[t+1])
+  int dense_splits;          // dense form: slots of tile t are [t*splits, (t+1)*splits)
+  const int* rows;           // optional: buffer rows to process (fallback); else 0..m-1
+  const int* num_rows_dev;   // with `rows`: device-side count
+  int64_t m;                 // number of query rows (buffer rows) when rows == nullptr
+  const float* Q32;          // [m, d] buffer queries FP32
+  int d;
+  int metric;
+  const int* qorig;          // buffer row -> original query index (nullptr = identity)
+  const float* X32;          // database buffer rows FP32
+  const int* xid;            // buffer row -> original id (nullptr = identity)
+  int lp;                    // 1: scores are |x~|^2 - 2 q~.x~ (low precision)
+  const float* q_lpnorm;     // [m] |q~|^2 (lp)
+  const float* q_err;        // [m] |q - q~| rounded up (lp)
+  const unsigned* x_err_max_bits;   // max |x - x~| rounded up, float bits (lp)
+  const unsigned* x_norm_max_bits;  // max |x~| rounded up, float bits (lp)
+  float simt_eps;            // FP32 path: relative bound of the tile kernel's rho
+  int k;
+  int c_out;
+  int64_t* out_ids;
+  float* out_dist;
+  int* fallback_rows;        // uncertified rows are appended here (lp)
+  int* counters;             // [0] uncertified, [1] fp64 ties, [2] boundary ties
+};
+int launch_select(const SelectArgs& a, cudaStream_t st);
+
+}  // namespace rbc
+
+namespace rbc {
+
+// ---- data movement and preparation (prep.cu) ----
+int launch_gather_rows(const float* src, const int64_t* idx64, const int* idx32, int64_t rows,
+                       int d, float* dst, cudaStream_t st);
+// FP32 rows -> low-precision rows [rows, dpad] (zero padded), |x~|^2, |x - x~|
+// (FP64, rounded up); global maxima of |x - x~| and |x~| as float bits.
+int launch_to_lowp(const float* src, int64_t rows, int d, int dpad, int storage, void* dst,
+                   float* norm, float* err, unsigned* err_max_bits, unsigned* norm_max_bits,
+                   cudaStream_t st);
+// out[i] = qorig ? qorig[rows[i]] : rows[i], for i < *n_dev (or n when n_dev is null)
+int launch_map_rows(const int* rows, const int* n_dev, int n, const int* qorig, int* out,
+                    cudaStream_t st);
+
+// ---- index construction / exact-search helpers (rbc_kernels.cu) ----
+// counting sort of `key[i]` in [0, nbins): stable positions.  perm[pos] = i,
+// offsets[nbins + 1].  `scratch` needs counting_sort_scratch_ints() ints.
+int64_t counting_sort_scratch_ints(int64_t n, int nbins);
+int launch_counting_sort(const int64_t* key, int64_t n, int nbins, int* perm, int* offsets,
+                         int* scratch, cudaStream_t st);
+// psi_plus[r] = max over list r of dist[perm[pos]] * (1 + rel) (0 if empty)
+int launch_list_radii(const float* dist_by_id, const int* perm, const int* offsets, int n_r,
+                      float rel, float* psi_plus, cudaStream_t st);
+// Per query of D [m, n_r]: gamma_1, gamma_k (k-th smallest), nearest ordinal.
+int launch_row_stats(const float* D, int64_t m, int n_r, int k, float* g1, float* gk,
+                     int64_t* nearest, cudaStream_t st);
+// Exact-search pruning per query tile (tile t = positions [t*TQ, +TQ)):
+// representative r is kept for query q iff
+//   D_lo(q,r) <= gk_hi(q) + psi_plus[r]  and  D_lo(q,r) <= 2 gk_hi(q) + g1_hi(q)
+// with D_lo = D (1 - rel) and gamma_hi = gamma (1 + rel).  Writes the tile's
+// union bitmask [tiles][words], the tile's point count (sum of kept list
+// sizes) and per-query kept counts.
+int launch_prune(const float* D, const int* qperm, int64_t m, int n_r, const float* g1,
+                 const float* gk, const float* psi_plus, const int* offsets, float rel,
+                 uint32_t* tile_mask, int64_t* tile_points, int* q_kept, cudaStream_t st);
+// Work generation: item counts per tile (ceil(points / W)) and their
+// exclusive scan -> tile_item_off [tiles + 1] (last entry = total items).
+int launch_item_offsets(const int64_t* tile_points, int tiles, int W, int* counts_scratch,
+                        int* tile_item_off, cudaStream_t st);
+// Each tile's kept lists (merged where adjacent) cut into items of at most W
+// points; segments of tile t live at [t * seg_cap_per_tile, ...).
+int launch_workgen_items(const uint32_t* tile_mask, const int* offsets, int n_r, int64_t m, int W,
+                         int item_cap_per_tile, int seg_cap_per_tile, const int* tile_item_off,
+                         WorkItem* items, Seg* segs, uint32_t* dev_err, cudaStream_t st);
+// reduce helpers for statistics
+int launch_sum_i32(const int* v, int64_t n, unsigned long long* out, cudaStream_t st);
+int launch_sum_i64(const int64_t* v, int64_t n, unsigned long long* out, cudaStream_t st);
+
+}  // namespace rbc

@@ -1,0 +1,136 @@
+// Data movement and storage preparation.
+//
+// gather_rows: dst[i] = src[idx[i]] for FP32 rows (representatives, lists in
+//   permuted order, queries in tile order).  One warp per row, float4 when the
+//   row length allows it.
+// to_lowp: FP32 rows -> bf16 / fp16 rows padded with zeros to `dpad` columns
+//   (a multiple of 64, the tensor-core K block), plus per row the FP32 norm
+//   |x~|^2 of the rounded row and the rounding residual |x - x~| computed in
+//   FP64 and rounded up to float.  The residual bounds how far any distance
+//   can move under rounding (triangle inequality of the metric:
+//   |rho(q~, x~) - rho(q, x)| <= |q - q~| + |x - x~|), which the exact search
+//   needs to stay exact with low-precision storage.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rbc {
+
+namespace {
+
+__global__ void gather_rows_kernel(const float* __restrict__ src, const int64_t* __restrict__ idx64,
+                                   const int* __restrict__ idx32, int64_t rows, int d,
+                                   float* __restrict__ dst) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= rows) return;
+  const int64_t s = idx64 ? idx64[w] : (int64_t)idx32[w];
+  const float* a = src + s * d;
+  float* b = dst + w * d;
+  if ((d & 3) == 0) {
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    float4* b4 = reinterpret_cast<float4*>(b);
+    for (int i = lane; i < (d >> 2); i += 32) b4[i] = a4[i];
+  } else {
+    for (int i = lane; i < d; i += 32) b[i] = a[i];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T to_lp(float v);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_lp<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+template <>
+__device__ __forceinline__ __half to_lp<__half>(float v) {
+  return __float2half_rn(v);
+}
+__device__ __forceinline__ float from_lp(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float from_lp(__half v) { return __half2float(v); }
+
+template <typename T>
+__global__ void to_lowp_kernel(const float* __restrict__ src, int64_t rows, int d, int dpad,
+                               T* __restrict__ dst, float* __restrict__ norm,
+                               float* __restrict__ err, unsigned* err_max_bits,
+                               unsigned* norm_max_bits) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= rows) return;
+  const float* a = src + w * d;
+  T* b = dst + w * dpad;
+  float nrm = 0.f;
+  double e2 = 0.0;
+  for (int i = lane; i < dpad; i += 32) {
+    float v = i < d ? a[i] : 0.f;
+    T lv = to_lp<T>(v);
+    b[i] = lv;
+    float r = from_lp(lv);
+    nrm = fmaf(r, r, nrm);
+    double diff = (double)v - (double)r;
+    e2 += diff * diff;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+  }
+  if (lane == 0) {
+    float e = __double2float_ru(sqrt(e2));
+    norm[w] = nrm;
+    if (err) err[w] = e;
+    // non-negative floats order like their bit patterns
+    if (err_max_bits) atomicMax(err_max_bits, __float_as_uint(e));
+    if (norm_max_bits) atomicMax(norm_max_bits, __float_as_uint(__fsqrt_ru(nrm)));
+  }
+}
+
+__global__ void map_rows_kernel(const int* __restrict__ rows, const int* __restrict__ n_dev, int n,
+                                const int* __restrict__ qorig, int* __restrict__ out) {
+  int lim = n_dev ? *n_dev : n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < lim; i += gridDim.x * blockDim.x)
+    out[i] = qorig ? qorig[rows[i]] : rows[i];
+}
+
+}  // namespace
+
+int launch_map_rows(const int* rows, const int* n_dev, int n, const int* qorig, int* out,
+                    cudaStream_t st) {
+  if (n <= 0) return RBC_OK;
+  map_rows_kernel<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, st>>>(rows, n_dev, n,
+                                                                                  qorig, out);
+  RBC_LAUNCH_CHECK("map_rows_kernel");
+  return RBC_OK;
+}
+
+int launch_gather_rows(const float* src, const int64_t* idx64, const int* idx32, int64_t rows,
+                       int d, float* dst, cudaStream_t st) {
+  if (rows <= 0) return RBC_OK;
+  int64_t threads = rows * 32;
+  gather_rows_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(src, idx64, idx32, rows,
+                                                                       d, dst);
+  RBC_LAUNCH_CHECK("gather_rows_kernel");
+  return RBC_OK;
+}
+
+int launch_to_lowp(const float* src, int64_t rows, int d, int dpad, int storage, void* dst,
+                   float* norm, float* err, unsigned* err_max_bits, unsigned* norm_max_bits,
+                   cudaStream_t st) {
+  if (rows <= 0) return RBC_OK;
+  int64_t threads = rows * 32;
+  unsigned blocks = (unsigned)((threads + 255) / 256);
+  if (storage == RBC_BF16)
+    to_lowp_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(
+        src, rows, d, dpad, reinterpret_cast<__nv_bfloat16*>(dst), norm, err, err_max_bits,
+        norm_max_bits);
+  else
+    to_lowp_kernel<__half><<<blocks, 256, 0, st>>>(src, rows, d, dpad,
+                                                   reinterpret_cast<__half*>(dst), norm, err,
+                                                   err_max_bits, norm_max_bits);
+  RBC_LAUNCH_CHECK("to_lowp_kernel");
+  return RBC_OK;
+}
+
+}  // namespace rbc

@@ -1,0 +1,433 @@
+// Index construction and exact-search bookkeeping around the BF calls.
+//
+// * counting sort   -- forms the ownership lists L_r (Sections 4, 5.2): a
+//                      stable counting sort of the points by owner, so each
+//                      list is one contiguous run of the permuted database.
+// * list radii      -- psi_r = max_{x in L_r} rho(x, r) (Section 4).
+// * row stats       -- gamma_1 and gamma_k of every query from its retained
+//                      representative distances (Section 5.2).
+// * prune           -- the two pruning rules of Section 5.2 (rule (1) with
+//                      gamma_k, Lemma 1 generalised to 2 gamma_k + gamma_1),
+//                      evaluated with rounding slack so that no surviving
+//                      representative is dropped; per query tile the union
+//                      of survivors is kept as a bitmask.
+// * workgen         -- cuts each tile's union of lists into work items for
+//                      the stage-two BF kernel.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rbc {
+
+namespace {
+
+constexpr int CS_CHUNK = 2048;  // keys per counting-sort block
+
+__global__ void cs_hist_kernel(const int64_t* __restrict__ key, int64_t n, int nbins,
+                               int* __restrict__ counts) {
+  extern __shared__ int h[];
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * CS_CHUNK;
+  for (int i = threadIdx.x; i < CS_CHUNK; i += blockDim.x) {
+    int64_t j = base + i;
+    if (j < n) atomicAdd(&h[(int)key[j]], 1);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+    counts[(int64_t)blockIdx.x * nbins + b] = h[b];
+}
+
+// per bin: exclusive prefix over blocks in place; totals[bin] = sum
+__global__ void cs_colscan_kernel(int* __restrict__ counts, int nblocks, int nbins,
+                                  int* __restrict__ totals) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbins) return;
+  int run = 0;
+  for (int k = 0; k < nblocks; ++k) {
+    int64_t o = (int64_t)k * nbins + b;
+    int c = counts[o];
+    counts[o] = run;
+    run += c;
+  }
+  totals[b] = run;
+}
+
+// single block exclusive scan of n ints: out[i] = sum_{j<i} in[j], out[n] = total
+__global__ void exclusive_scan_kernel(const int* __restrict__ in, int n, int* __restrict__ out) {
+  __shared__ int warp_sums[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int base = 0; base < n; base += blockDim.x) {
+    int i = base + threadIdx.x;
+    int v = i < n ? in[i] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int s = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += y;
+      }
+      warp_sums[lane] = s;  // inclusive over warps
+    }
+    __syncthreads();
+    int warp_off = wid ? warp_sums[wid - 1] : 0;
+    if (i < n) out[i] = carry + warp_off + x - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[n] = carry;
+}
+
+// one warp per block walks its chunk in order; equal keys within a group of
+// 32 are ranked by lane, so the scatter is stable
+__global__ void cs_scatter_kernel(const int64_t* __restrict__ key, int64_t n, int nbins,
+                                  const int* __restrict__ counts, const int* __restrict__ offsets,
+                                  int* __restrict__ perm) {
+  extern __shared__ int run[];
+  const int lane = threadIdx.x;
+  for (int b = lane; b < nbins; b += 32)
+    run[b] = offsets[b] + counts[(int64_t)blockIdx.x * nbins + b];
+  __syncwarp();
+  int64_t base = (int64_t)blockIdx.x * CS_CHUNK;
+  for (int g = 0; g < CS_CHUNK; g += 32) {
+    int64_t j = base + g + lane;
+    bool act = j < n;
+    unsigned active = __ballot_sync(0xffffffffu, act);
+    if (!active) break;
+    int kv = act ? (int)key[j] : -1 - lane;  // inactive lanes get unique dummy keys
+    unsigned same = __match_any_sync(0xffffffffu, kv);
+    int rank = __popc(same & ((1u << lane) - 1u));
+    int pos = act ? run[kv] + rank : 0;
+    __syncwarp();
+    if (act) {
+      perm[pos] = (int)j;
+      if (rank == 0) run[kv] += __popc(same);
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void list_radii_kernel(const float* __restrict__ dist_by_id, const int* __restrict__ perm,
+                                  const int* __restrict__ offsets, int n_r, float rel,
+                                  float* __restrict__ psi_plus) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n_r) return;
+  float mx = 0.f;
+  for (int p = offsets[w] + lane; p < offsets[w + 1]; p += 32) mx = fmaxf(mx, dist_by_id[perm[p]]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) psi_plus[w] = mx * (1.0f + rel);
+}
+
+template <int KW>
+__global__ void row_stats_kernel(const float* __restrict__ D, int64_t m, int n_r, int k,
+                                 float* __restrict__ g1, float* __restrict__ gk,
+                                 int64_t* __restrict__ nearest) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= m) return;
+  const float* row = D + w * n_r;
+  TopList<KW> lst;
+  lst.init();
+  for (int c = lane; c < n_r; c += 32) {
+    float v = row[c];
+    if (lst.admits(v, c)) lst.insert(v, c);
+  }
+  // k rounds of warp arg-min over the lane heads (lists live in registers:
+  // the head is selected with a fully unrolled scan)
+  int head = 0;
+  float first = INFINITY, kth = INFINITY;
+  int first_id = 0;
+  const int rounds = min(k, n_r);
+  for (int j = 0; j < rounds; ++j) {
+    float hv = INFINITY;
+    int hi = INT32_MAX;
+#pragma unroll
+    for (int t = 0; t < KW; ++t)
+      if (t == head) {
+        hv = lst.s[t];
+        hi = lst.i[t];
+      }
+    float bv = hv;
+    int bi = hi;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (pair_lt(ov, oi, bv, bi)) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    if (hi == bi && hv == bv) ++head;
+    if (j == 0) {
+      first = bv;
+      first_id = bi;
+    }
+    kth = bv;
+  }
+  if (lane == 0) {
+    g1[w] = first;
+    gk[w] = (k <= n_r) ? kth : INFINITY;
+    nearest[w] = first_id;
+  }
+}
+
+constexpr int PRUNE_WARPS = 8;
+
+__global__ void __launch_bounds__(PRUNE_WARPS * 32)
+prune_kernel(const float* __restrict__ D, const int* __restrict__ qperm, int64_t m, int n_r,
+             const float* __restrict__ g1, const float* __restrict__ gk,
+             const float* __restrict__ psi_plus, const int* __restrict__ offsets, float rel,
+             uint32_t* __restrict__ tile_mask, int64_t* __restrict__ tile_points,
+             int* __restrict__ q_kept) {
+  extern __shared__ uint32_t mask[];
+  const int words = (n_r + 31) / 32;
+  const int tile = blockIdx.x;
+  for (int i = threadIdx.x; i < words; i += blockDim.x) mask[i] = 0;
+  __syncthreads();
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float up = 1.0f + rel, lo = 1.0f - rel, slack = 1.0f + 2.4e-7f;
+  for (int r = wid; r < TQ; r += PRUNE_WARPS) {
+    int64_t pos = (int64_t)tile * TQ + r;
+    if (pos >= m) break;
+    int q = qperm ? qperm[pos] : (int)pos;
+    float gkh = gk[q] * up, g1h = g1[q] * up;
+    float lemma = (2.0f * gkh + g1h) * slack;
+    const float* row = D + (int64_t)q * n_r;
+    int kept = 0;
+    for (int c0 = 0; c0 < n_r; c0 += 32) {
+      int c = c0 + lane;
+      bool keep = false;
+      if (c < n_r) {
+        float dl = row[c] * lo;
+        keep = dl <= (gkh + psi_plus[c]) * slack && dl <= lemma;
+      }
+      unsigned bits = __ballot_sync(0xffffffffu, keep);
+      kept += __popc(bits);
+      if (lane == 0 && bits) atomicOr(&mask[c0 >> 5], bits);
+    }
+    if (lane == 0 && q_kept) q_kept[q] = kept;
+  }
+  __syncthreads();
+  // tile point count = sum of kept list sizes
+  long long pts = 0;
+  for (int r = threadIdx.x; r < n_r; r += blockDim.x)
+    if (mask[r >> 5] & (1u << (r & 31))) pts += offsets[r + 1] - offsets[r];
+  for (int o = 16; o > 0; o >>= 1) pts += __shfl_xor_sync(0xffffffffu, pts, o);
+  __shared__ long long part[PRUNE_WARPS];
+  if (lane == 0) part[wid] = pts;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long s = 0;
+    for (int i = 0; i < PRUNE_WARPS; ++i) s += part[i];
+    tile_points[tile] = s;
+  }
+  for (int i = threadIdx.x; i < words; i += blockDim.x)
+    tile_mask[(int64_t)tile * words + i] = mask[i];
+}
+
+__global__ void item_count_kernel(const int64_t* __restrict__ tile_points, int tiles, int W,
+                                  int* __restrict__ counts) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < tiles) counts[t] = (int)((tile_points[t] + W - 1) / W);
+}
+
+// one thread per tile: walk the kept representatives in order, merge adjacent
+// lists into runs, cut runs so that every item holds at most W points
+__global__ void workgen_kernel(const uint32_t* __restrict__ tile_mask, const int* __restrict__ offsets,
+                               int n_r, int64_t m, int W, int item_cap, int seg_cap,
+                               const int* __restrict__ tile_item_off, WorkItem* __restrict__ items,
+                               Seg* __restrict__ segs, uint32_t* dev_err) {
+  const int tiles = (int)((m + TQ - 1) / TQ);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tiles) return;
+  const int words = (n_r + 31) / 32;
+  const uint32_t* mk = tile_mask + (int64_t)t * words;
+  const int q0 = t * TQ;
+  const int nq = (int)min((int64_t)TQ, m - q0);
+  int item = tile_item_off[t];
+  const int item_end = tile_item_off[t + 1];
+  if (item_end - item > item_cap) {
+    atomicOr(dev_err, DEV_ERR_CAPACITY);
+    return;
+  }
+  const int seg0 = t * seg_cap;
+  int seg = seg0;
+  int acc = 0;          // points in the open item
+  int item_seg0 = seg;  // first segment of the open item
+  auto close_item = [&]() {
+    if (item < item_end) items[item] = WorkItem{q0, nq, item_seg0, seg, item, t};
+    ++item;
+    item_seg0 = seg;
+    acc = 0;
+  };
+  for (int r = 0; r < n_r; ++r) {
+    if (!(mk[r >> 5] & (1u << (r & 31)))) continue;
+    int b = offsets[r], e = offsets[r + 1];
+    while (b < e) {
+      int take = min(e - b, W - acc);
+      if (seg > item_seg0 && segs[seg - 1].x_end == b) {
+        segs[seg - 1].x_end = b + take;  // extend the previous run
+      } else {
+        if (seg - seg0 >= seg_cap) {
+          atomicOr(dev_err, DEV_ERR_CAPACITY);
+          return;
+        }
+        segs[seg++] = Seg{b, b + take};
+      }
+      acc += take;
+      b += take;
+      if (acc == W) close_item();
+    }
+  }
+  if (acc > 0) close_item();
+}
+
+__global__ void sum_i32_kernel(const int* __restrict__ v, int64_t n, unsigned long long* out) {
+  unsigned long long s = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += (unsigned long long)v[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+__global__ void sum_i64_kernel(const int64_t* __restrict__ v, int64_t n, unsigned long long* out) {
+  unsigned long long s = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += (unsigned long long)v[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+}  // namespace
+
+int64_t counting_sort_scratch_ints(int64_t n, int nbins) {
+  int64_t blocks = (n + CS_CHUNK - 1) / CS_CHUNK;
+  return blocks * nbins + nbins + 1;
+}
+
+int launch_counting_sort(const int64_t* key, int64_t n, int nbins, int* perm, int* offsets,
+                         int* scratch, cudaStream_t st) {
+  if (nbins > 12000) {
+    set_error("counting sort: %d bins exceed the shared-memory histogram", nbins);
+    return RBC_ERR_UNSUPPORTED;
+  }
+  int blocks = (int)((n + CS_CHUNK - 1) / CS_CHUNK);
+  int* counts = scratch;
+  int* totals = scratch + (int64_t)blocks * nbins;
+  if (blocks > 0) {
+    cs_hist_kernel<<<blocks, 256, nbins * sizeof(int), st>>>(key, n, nbins, counts);
+    RBC_LAUNCH_CHECK("cs_hist_kernel");
+    cs_colscan_kernel<<<(nbins + 255) / 256, 256, 0, st>>>(counts, blocks, nbins, totals);
+    RBC_LAUNCH_CHECK("cs_colscan_kernel");
+  } else {
+    RBC_CUDA(cudaMemsetAsync(totals, 0, nbins * sizeof(int), st));
+  }
+  exclusive_scan_kernel<<<1, 1024, 0, st>>>(totals, nbins, offsets);
+  RBC_LAUNCH_CHECK("exclusive_scan_kernel");
+  if (blocks > 0) {
+    cs_scatter_kernel<<<blocks, 32, nbins * sizeof(int), st>>>(key, n, nbins, counts, offsets,
+                                                                perm);
+    RBC_LAUNCH_CHECK("cs_scatter_kernel");
+  }
+  return RBC_OK;
+}
+
+int launch_list_radii(const float* dist_by_id, const int* perm, const int* offsets, int n_r,
+                      float rel, float* psi_plus, cudaStream_t st) {
+  list_radii_kernel<<<(n_r * 32 + 255) / 256, 256, 0, st>>>(dist_by_id, perm, offsets, n_r, rel,
+                                                           psi_plus);
+  RBC_LAUNCH_CHECK("list_radii_kernel");
+  return RBC_OK;
+}
+
+int launch_row_stats(const float* D, int64_t m, int n_r, int k, float* g1, float* gk,
+                     int64_t* nearest, cudaStream_t st) {
+  if (m <= 0) return RBC_OK;
+  unsigned blocks = (unsigned)((m * 32 + 255) / 256);
+  int kk = k < n_r ? k : n_r;
+  if (kk <= 1)
+    row_stats_kernel<1><<<blocks, 256, 0, st>>>(D, m, n_r, k, g1, gk, nearest);
+  else if (kk <= 2)
+    row_stats_kernel<2><<<blocks, 256, 0, st>>>(D, m, n_r, k, g1, gk, nearest);
+  else if (kk <= 4)
+    row_stats_kernel<4><<<blocks, 256, 0, st>>>(D, m, n_r, k, g1, gk, nearest);
+  else if (kk <= 8)
+    row_stats_kernel<8><<<blocks, 256, 0, st>>>(D, m, n_r, k, g1, gk, nearest);
+  else if (kk <= 16)
+    row_stats_kernel<16><<<blocks, 256, 0, st>>>(D, m, n_r, k, g1, gk, nearest);
+  else if (kk <= 32)
+    row_stats_kernel<32><<<blocks, 256, 0, st>>>(D, m, n_r, k, g1, gk, nearest);
+  else {
+    set_error("row_stats: k = %d too large", k);
+    return RBC_ERR_UNSUPPORTED;
+  }
+  RBC_LAUNCH_CHECK("row_stats_kernel");
+  // when n_r < k every representative is kept: gamma_k = +inf
+  return RBC_OK;
+}
+
+int launch_prune(const float* D, const int* qperm, int64_t m, int n_r, const float* g1,
+                 const float* gk, const float* psi_plus, const int* offsets, float rel,
+                 uint32_t* tile_mask, int64_t* tile_points, int* q_kept, cudaStream_t st) {
+  int tiles = (int)((m + TQ - 1) / TQ);
+  if (tiles == 0) return RBC_OK;
+  int words = (n_r + 31) / 32;
+  prune_kernel<<<tiles, PRUNE_WARPS * 32, words * sizeof(uint32_t), st>>>(
+      D, qperm, m, n_r, g1, gk, psi_plus, offsets, rel, tile_mask, tile_points, q_kept);
+  RBC_LAUNCH_CHECK("prune_kernel");
+  return RBC_OK;
+}
+
+int launch_item_offsets(const int64_t* tile_points, int tiles, int W, int* counts_scratch,
+                        int* tile_item_off, cudaStream_t st) {
+  if (tiles == 0) return RBC_OK;
+  item_count_kernel<<<(tiles + 255) / 256, 256, 0, st>>>(tile_points, tiles, W, counts_scratch);
+  RBC_LAUNCH_CHECK("item_count_kernel");
+  exclusive_scan_kernel<<<1, 1024, 0, st>>>(counts_scratch, tiles, tile_item_off);
+  RBC_LAUNCH_CHECK("exclusive_scan_kernel");
+  return RBC_OK;
+}
+
+int launch_workgen_items(const uint32_t* tile_mask, const int* offsets, int n_r, int64_t m, int W,
+                         int item_cap_per_tile, int seg_cap_per_tile, const int* tile_item_off,
+                         WorkItem* items, Seg* segs, uint32_t* dev_err, cudaStream_t st) {
+  int tiles = (int)((m + TQ - 1) / TQ);
+  if (tiles == 0) return RBC_OK;
+  workgen_kernel<<<(tiles + 127) / 128, 128, 0, st>>>(tile_mask, offsets, n_r, m, W,
+                                                       item_cap_per_tile, seg_cap_per_tile,
+                                                       tile_item_off, items, segs, dev_err);
+  RBC_LAUNCH_CHECK("workgen_kernel");
+  return RBC_OK;
+}
+
+int launch_sum_i32(const int* v, int64_t n, unsigned long long* out, cudaStream_t st) {
+  if (n <= 0) return RBC_OK;
+  sum_i32_kernel<<<64, 256, 0, st>>>(v, n, out);
+  RBC_LAUNCH_CHECK("sum_i32_kernel");
+  return RBC_OK;
+}
+
+int launch_sum_i64(const int64_t* v, int64_t n, unsigned long long* out, cudaStream_t st) {
+  if (n <= 0) return RBC_OK;
+  sum_i64_kernel<<<64, 256, 0, st>>>(v, n, out);
+  RBC_LAUNCH_CHECK("sum_i64_kernel");
+  return RBC_OK;
+}
+
+}  // namespace rbc

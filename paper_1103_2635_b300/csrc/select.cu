@@ -1,0 +1,283 @@
+// Merge, re-rank and certification: the comparison step of BF(Q, X)
+// (Section 3) finished per query, plus the exactness machinery for the
+// low-precision distance pass.
+//
+// One warp per query row:
+//  1. merge the top-C partial lists of every work item of the row's tile
+//     (each lane keeps a sorted register list of its share, then c_out rounds
+//     of a warp-wide arg-min over the lane heads) -> c_out candidates, one per
+//     lane, and the boundary score B of the c_out-th candidate;
+//  2. re-rank: each lane recomputes its candidate's distance in FP32
+//     difference form sqrt(sum (q_i - x_i)^2) (or sum |q_i - x_i|) from the
+//     FP32 rows, four interleaved partial sums combined pairwise;
+//  3. bitonic sort of the 32 lanes by (rho, id);
+//  4. certification: every point outside the candidate set has a score >= B;
+//     its true distance is at least lower(B), a rounding-error bound of the
+//     pass that produced B.  The candidate set holds the true k nearest if
+//     lower(B) > rho_(k) * (1 + eps), eps the re-rank's relative bound;
+//     otherwise the row is queued for an FP32 re-search;
+//  5. near-ties: if two neighbouring ranks among the first k+1 lie within the
+//     FP32 bound of each other, every candidate is recomputed in FP64 and the
+//     candidates re-sorted by (rho64, id);
+//  6. the first k (id, rho) pairs are written at the query's original row.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rbc {
+
+namespace {
+
+constexpr int WARPS = 4;
+constexpr float U32 = 5.9604645e-08f;  // 2^-24, unit roundoff of float
+
+__device__ __forceinline__ bool key_lt(float a, int ia, int la, float b, int ib, int lb) {
+  return a < b || (a == b && (ia < ib || (ia == ib && la < lb)));
+}
+
+// Relative error bound of the re-rank's FP32 rho (see header comment):
+// each term carries <= 3u, each of the four partial sums adds (d/4 - 1)u,
+// the pairwise combination 2u; halving for the square root and adding its
+// rounding, (d/8 + 3)u suffices; twice that is used.
+__device__ __forceinline__ float rerank_eps(int d) { return (0.25f * d + 8.0f) * U32; }
+
+template <int CW>
+__global__ void __launch_bounds__(WARPS * 32) select_kernel(SelectArgs a) {
+  __shared__ float sh_s[WARPS][32][CW + 1];
+  __shared__ int sh_i[WARPS][32][CW + 1];
+  const int wib = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * WARPS + wib;
+  const int64_t nrows = a.rows ? (int64_t)*a.num_rows_dev : a.m;
+  if (gw >= nrows) return;
+  const int row = a.rows ? a.rows[gw] : (int)gw;
+  const int tile = row / TQ;
+  const int r = row - tile * TQ;
+  int sb, se;
+  if (a.tile_slot_off) {
+    sb = a.tile_slot_off[tile];
+    se = a.tile_slot_off[tile + 1];
+  } else {
+    sb = tile * a.dense_splits;
+    se = sb + a.dense_splits;
+  }
+  const int per_slot = a.nsub * a.C;
+
+  // ---- 1. merge ----
+  TopList<CW> lst;
+  lst.init();
+  const int total = (se - sb) * per_slot;
+  for (int e = lane; e < total; e += 32) {
+    int s = sb + e / per_slot;
+    int j = e - (e / per_slot) * per_slot;
+    int64_t off = ((int64_t)s * TQ + r) * per_slot + j;
+    int id = a.part_idx[off];
+    float v = a.part_score[off];
+    if (id >= 0 && lst.admits(v, id)) lst.insert(v, id);
+  }
+#pragma unroll
+  for (int j = 0; j < CW; ++j) {
+    sh_s[wib][lane][j] = lst.s[j];
+    sh_i[wib][lane][j] = lst.i[j];
+  }
+  __syncwarp();
+  int head = 0;
+  float cs = INFINITY;  // this lane's candidate (rank = lane) score
+  int ci = INT32_MAX;   // its database buffer row
+  for (int j = 0; j < a.c_out; ++j) {
+    float hv = head < CW ? sh_s[wib][lane][head] : INFINITY;
+    int hi = head < CW ? sh_i[wib][lane][head] : INT32_MAX;
+    float bv = hv;
+    int bi = hi, bl = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+      if (key_lt(ov, oi, ol, bv, bi, bl)) {
+        bv = ov;
+        bi = oi;
+        bl = ol;
+      }
+    }
+    if (lane == bl) ++head;
+    if (lane == j) {
+      cs = bv;
+      ci = bi;
+    }
+  }
+  const float B = __shfl_sync(0xffffffffu, cs, a.c_out - 1);
+  const bool valid = lane < a.c_out && ci != INT32_MAX && cs != INFINITY;
+
+  // ---- 2. FP32 re-rank ----
+  const int d = a.d;
+  const float* qr = a.Q32 + (int64_t)row * d;
+  float rho = INFINITY;
+  int oid = INT32_MAX;
+  if (valid) {
+    const float* xr = a.X32 + (int64_t)ci * d;
+    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+    int i = 0;
+    for (; i + 4 <= d; i += 4) {
+      float t0 = qr[i] - xr[i], t1 = qr[i + 1] - xr[i + 1];
+      float t2 = qr[i + 2] - xr[i + 2], t3 = qr[i + 3] - xr[i + 3];
+      if (a.metric == RBC_L2) {
+        p0 = fmaf(t0, t0, p0);
+        p1 = fmaf(t1, t1, p1);
+        p2 = fmaf(t2, t2, p2);
+        p3 = fmaf(t3, t3, p3);
+      } else {
+        p0 += fabsf(t0);
+        p1 += fabsf(t1);
+        p2 += fabsf(t2);
+        p3 += fabsf(t3);
+      }
+    }
+    for (; i < d; ++i) {
+      float t0 = qr[i] - xr[i];
+      if (a.metric == RBC_L2) p0 = fmaf(t0, t0, p0); else p0 += fabsf(t0);
+    }
+    float sum = (p0 + p1) + (p2 + p3);
+    rho = a.metric == RBC_L2 ? sqrtf(sum) : sum;
+    oid = a.xid ? a.xid[ci] : ci;
+  }
+  int brow = valid ? ci : -1;  // buffer row carried through the sort
+
+  // ---- 3. sort lanes by (rho, id) ----
+  auto bitonic = [&](float& v, int& id, int& br) {
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        float ov = __shfl_xor_sync(0xffffffffu, v, stride);
+        int oi = __shfl_xor_sync(0xffffffffu, id, stride);
+        int ob = __shfl_xor_sync(0xffffffffu, br, stride);
+        bool up = (lane & size) == 0 || size == 32;
+        bool lower = (lane & stride) == 0;
+        bool other_less = pair_lt(ov, oi, v, id);
+        bool take = (lower == up) ? other_less : (!other_less && !(ov == v && oi == id));
+        if (take) {
+          v = ov;
+          id = oi;
+          br = ob;
+        }
+      }
+    }
+  };
+  bitonic(rho, oid, brow);
+
+  // ---- 4. certification ----
+  const float eps = rerank_eps(d);
+  const int k = a.k;
+  const float rk = __shfl_sync(0xffffffffu, rho, k - 1);
+  bool certified;
+  if (B == INFINITY) {
+    certified = true;  // every point of the searched set is a candidate
+  } else {
+    float lower;
+    if (!a.lp) {
+      float rb = a.metric == RBC_L2 ? sqrtf(B) : B;
+      lower = rb * (1.0f - a.simt_eps) * (1.0f - 4.0f * U32);
+    } else {
+      float qn = a.q_lpnorm[row];
+      float nq = sqrtf(qn);
+      float span = nq + __uint_as_float(*a.x_norm_max_bits);
+      // FP32 evaluation bound of |x~|^2 - 2 q~.x~ (tensor-core products are
+      // exact, accumulation allowed 2^-20 relative per term): (d+4) 2^-19 span^2
+      float ef = (float)(d + 4) * 1.9073486e-06f * span * span;
+      float t = B + qn - ef;
+      lower = (t > 0.f ? sqrtf(t) * (1.0f - 4.0f * U32) : 0.f) - a.q_err[row] -
+              __uint_as_float(*a.x_err_max_bits);
+      lower *= (1.0f - 8.0f * U32);
+    }
+    float upper = rk * (1.0f + eps) * (1.0f + 4.0f * U32);
+    certified = lower > upper;
+  }
+
+  // ---- 5. near-ties among the first k+1 ranks -> FP64 ----
+  float nxt = __shfl_down_sync(0xffffffffu, rho, 1);
+  bool tie = lane < k && lane + 1 < a.c_out && rho != INFINITY && nxt != INFINITY &&
+             (nxt - rho) <= eps * (nxt + rho) * 2.0f;
+  unsigned tie_mask = __ballot_sync(0xffffffffu, tie);
+  if (tie_mask) {
+    double r64 = INFINITY;
+    if (brow >= 0) {
+      const float* xr = a.X32 + (int64_t)brow * d;
+      double s = 0.0;
+      for (int i = 0; i < d; ++i) {
+        double t0 = (double)qr[i] - (double)xr[i];
+        s += a.metric == RBC_L2 ? t0 * t0 : fabs(t0);
+      }
+      r64 = a.metric == RBC_L2 ? sqrt(s) : s;
+    }
+    // sort by (rho64, id): reuse the float sort on the double's ordering by
+    // sorting with a two-stage key; keys are non-negative doubles, so their
+    // bit patterns order like the values.
+    long long key = brow >= 0 ? __double_as_longlong(r64) : LLONG_MAX;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        long long ok = __shfl_xor_sync(0xffffffffu, key, stride);
+        int oi = __shfl_xor_sync(0xffffffffu, oid, stride);
+        int ob = __shfl_xor_sync(0xffffffffu, brow, stride);
+        bool up = (lane & size) == 0 || size == 32;
+        bool lower = (lane & stride) == 0;
+        bool other_less = ok < key || (ok == key && oi < oid);
+        bool same = ok == key && oi == oid;
+        bool take = (lower == up) ? other_less : (!other_less && !same);
+        if (take) {
+          key = ok;
+          oid = oi;
+          brow = ob;
+        }
+      }
+    }
+    rho = key == LLONG_MAX ? INFINITY : (float)__longlong_as_double(key);
+  }
+
+  // ---- 6. output ----
+  const int64_t orow = a.qorig ? (int64_t)a.qorig[row] : (int64_t)row;
+  if (lane < k) {
+    bool ok = rho != INFINITY && brow >= 0;
+    a.out_ids[orow * k + lane] = ok ? (int64_t)oid : (int64_t)-1;
+    a.out_dist[orow * k + lane] = ok ? rho : INFINITY;
+  }
+  if (lane == 0) {
+    if (!certified) {
+      int pos = atomicAdd(&a.counters[0], 1);
+      if (a.fallback_rows) a.fallback_rows[pos] = row;
+    }
+    if (tie_mask) atomicAdd(&a.counters[1], 1);
+    if (tie_mask & (1u << (k - 1))) atomicAdd(&a.counters[2], 1);
+  }
+}
+
+template <int CW>
+int launch_cw(const SelectArgs& a, int64_t grid_rows, cudaStream_t st) {
+  int64_t blocks = (grid_rows + WARPS - 1) / WARPS;
+  if (blocks == 0) return RBC_OK;
+  select_kernel<CW><<<(unsigned)blocks, WARPS * 32, 0, st>>>(a);
+  RBC_LAUNCH_CHECK("select_kernel");
+  return RBC_OK;
+}
+
+}  // namespace
+
+int launch_select(const SelectArgs& a, cudaStream_t st) {
+  if (a.k < 1 || a.c_out < a.k || a.c_out > 32) {
+    set_error("select: bad k=%d c_out=%d", a.k, a.c_out);
+    return RBC_ERR_ARG;
+  }
+  // with a device-side row count the grid covers the worst case (a.m rows)
+  int64_t grid_rows = a.m;
+  int cw = a.c_out <= 2 ? 2 : a.c_out <= 4 ? 4 : a.c_out <= 8 ? 8 : a.c_out <= 16 ? 16 : 32;
+  switch (cw) {
+    case 2: return launch_cw<2>(a, grid_rows, st);
+    case 4: return launch_cw<4>(a, grid_rows, st);
+    case 8: return launch_cw<8>(a, grid_rows, st);
+    case 16: return launch_cw<16>(a, grid_rows, st);
+    default: return launch_cw<32>(a, grid_rows, st);
+  }
+}
+
+}  // namespace rbc

@@ -1,0 +1,117 @@
+"""Parity of the CUDA Random Ball Cover with the FP64 oracle (Sections 4-5):
+the build (representatives, lists, radii) against the oracle's build, and the
+exact search against the oracle's brute force (the exact algorithm returns
+exactly the brute-force neighbours)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import check_knn
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1103_2635_b300 as rbc  # noqa: E402
+
+MET = {"l2": rbc.L2, "l1": rbc.L1}
+
+
+def build(X, n_r, metric="l2", seed=2, storage=rbc.F32, **kw):
+    return rbc.rbc_build(torch.from_numpy(X).cuda(), n_r, metric=MET[metric], seed=seed, storage=storage, **kw)
+
+
+def search(idx, Q, k):
+    ids, dist = rbc.rbc_search(idx, torch.from_numpy(Q).cuda(), k)
+    torch.cuda.synchronize()
+    return ids.cpu().numpy(), dist.cpu().numpy()
+
+
+@pytest.mark.parametrize("metric", ["l2", "l1"])
+def test_build_matches_oracle(metric):
+    X, _ = synth.make_workload("iid-n16k-d16", seed=0)
+    idx = build(X, 128, metric)
+    ex = idx.export()
+    reps = oracle.sample_reps(len(X), 128, 2)
+    np.testing.assert_array_equal(ex["reps"], reps)
+    o = oracle.build_exact(X, reps, metric)
+    sizes = np.array([len(l) for l in o.lists])
+    np.testing.assert_array_equal(np.diff(ex["offsets"]), sizes)
+    for r in range(128):
+        got = ex["members"][ex["offsets"][r] : ex["offsets"][r + 1]]
+        np.testing.assert_array_equal(got, o.lists[r])  # stable: ascending ids
+    # radii: an upper bound within the FP32 rounding allowance
+    assert np.all(ex["psi"] >= o.psi * (1 - 1e-6))
+    assert np.all(ex["psi"] <= o.psi * (1 + 2e-5) + 1e-6)
+
+
+@pytest.mark.parametrize("metric", ["l2", "l1"])
+@pytest.mark.parametrize("k", [1, 10])
+def test_exact_search_iid_n16k_d16(metric, k):
+    X, Q = synth.make_workload("iid-n16k-d16", seed=0)
+    idx = build(X, 128, metric)
+    ids, dist = search(idx, Q, k)
+    o_ids, o_rho = oracle.bf(Q, X, k, metric)
+    check_knn(Q, X, ids, dist, o_ids, o_rho, metric)
+    st = rbc.last_stats()
+    assert st["queries"] == len(Q) and st["kept_reps"] >= len(Q)
+
+
+@pytest.mark.parametrize("metric", ["l2", "l1"])
+@pytest.mark.parametrize("n,m,d,n_r,k", [(5000, 300, 5, 71, 3), (2049, 129, 33, 1, 2), (3001, 77, 12, 3001, 4), (20000, 513, 8, 141, 7), (1000, 1, 64, 30, 31)])
+def test_exact_search_ragged(metric, n, m, d, n_r, k):
+    X = synth.iid_normal(n, d, 10 + n)
+    Q = synth.iid_normal(m, d, 20 + m)
+    idx = build(X, n_r, metric, seed=n_r)
+    ids, dist = search(idx, Q, k)
+    o_ids, o_rho = oracle.bf(Q, X, k, metric)
+    check_knn(Q, X, ids, dist, o_ids, o_rho, metric)
+
+
+def test_exact_search_subspace_workload_small():
+    mod = synth.SubspaceModel(d=64, k=8, noise_var=0.01, seed=0)
+    X = mod.sample(60000, 0)
+    Q = mod.sample(700, 1)
+    idx = build(X, 245)
+    for k in (1, 10):
+        ids, dist = search(idx, Q, k)
+        o_ids, o_rho = oracle.bf(Q, X, k, "l2")
+        check_knn(Q, X, ids, dist, o_ids, o_rho)
+
+
+def test_exact_search_with_duplicates():
+    base = synth.iid_normal(60, 4, 30)
+    X = np.concatenate([base, base, base[:25], base[:5]])
+    Q = np.concatenate([base[:15], synth.iid_normal(40, 4, 31)])
+    for n_r in (1, 9, 60, len(X)):
+        idx = build(X, n_r, seed=n_r)
+        ids, dist = search(idx, Q, 5)
+        o_ids, o_rho = oracle.bf(Q, X, 5, "l2")
+        np.testing.assert_array_equal(ids, o_ids)
+
+
+def test_given_representatives():
+    X = synth.iid_normal(3000, 6, 40)
+    Q = synth.iid_normal(100, 6, 41)
+    reps = np.arange(0, 3000, 37)
+    idx = build(X, len(reps), rep_ids=reps)
+    np.testing.assert_array_equal(idx.export()["reps"], reps)
+    ids, dist = search(idx, Q, 3)
+    o_ids, o_rho = oracle.bf(Q, X, 3, "l2")
+    check_knn(Q, X, ids, dist, o_ids, o_rho)
+
+
+def test_host_buffer_search():
+    X = synth.iid_normal(4000, 10, 50)
+    Q = synth.iid_normal(200, 10, 51)
+    idx = rbc.rbc_build(X, 63, seed=3)  # numpy database
+    ids, dist = rbc.rbc_search(idx, Q, 4)  # numpy queries and outputs
+    o_ids, o_rho = oracle.bf(Q, X, 4, "l2")
+    check_knn(Q, X, ids, dist, o_ids, o_rho)
+
+
+def test_empty_query_batch():
+    X = synth.iid_normal(500, 4, 60)
+    idx = build(X, 22)
+    ids, dist = search(idx, np.zeros((0, 4), np.float32), 2)
+    assert ids.shape == (0, 2)
