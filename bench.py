@@ -1,0 +1,379 @@
+"""Benchmark: exact k-NN queries/s of the Random Ball Cover on one B300.
+
+One step = one exact search (rbc_search) of the whole query batch of the
+8-dim-subspace workload (n = 1,048,576 points in R^64, N(0, 0.01) noise,
+m = 100,000 queries, n_r = 1024, k = 10, l2): stage one BF(Q, R), pruning,
+the tensor-core stage-two BF over the surviving lists, FP32 re-rank with
+certification and FP64 near-ties.  The index is built once before timing.
+
+Printed JSON line (rank 0): value = queries/s with inputs resident on the
+device; e2e = the same call with host (pinned) buffers, copies inside the
+timed region; roofline of the dominant kernel (stage-two tcgen05 BF);
+cpu_baseline = the FP64 CPU oracle on a bounded query sample; the FP32
+CUDA-core brute force over the same queries for comparison.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="subspace8-n1m-d64")
+    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--storage", default="bf16", choices=["bf16", "f16", "f32"])
+    ap.add_argument("--cpu-sample", type=int, default=1000)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-sample", type=int, default=200)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return FALLBACK_PEAKS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload_arrays(name: str, seed: int, m: int | None = None, query_seed: int | None = None):
+    w = synth.WORKLOADS[name]
+    X, Q = synth.make_workload(w, seed=seed, m=m, query_seed=query_seed)
+    return w, X, Q
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle (as it stands) on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+
+    w, X, Q = workload_arrays(args.workload, 0)
+    reps = oracle.sample_reps(len(X), w.n_r, 2)
+    idx = oracle.build_exact(X, reps, "l2")
+    cores = oracle.num_threads()
+    S = args.ref_sample
+    g = np.random.default_rng(7)
+    times = []
+    for step in range(args.warmup + args.steps):
+        sel = np.sort(g.choice(len(Q), S, replace=False))
+        t0 = time.perf_counter()
+        oracle.search_exact(idx, Q[sel], args.k)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    qps = S * len(times) / total
+    out = {
+        "impl": "reference",
+        "metric": "exact k-NN queries/s", "value": qps, "unit": "queries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": w.n, "m": w.m, "d": w.d, "n_r": w.n_r, "k": args.k,
+                   "metric": "l2", "method": "exact RBC (oracle, FP64 CPU)"},
+        "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{S} random queries of {w.m} per step, full {w.n}-point database"},
+        "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local):
+    import torch
+
+    import paper_1103_2635_b300 as rbc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    storage = {"bf16": rbc.BF16, "f16": rbc.F16, "f32": rbc.F32}[args.storage]
+    # each rank holds its own replica and its own query batch (weak scaling)
+    w, X, Q = workload_arrays(args.workload, 0, query_seed=1 + 1000 * rank)
+    Xd = torch.from_numpy(X).to(dev)
+    Qd = torch.from_numpy(Q).to(dev)
+    m, d, k = Q.shape[0], Q.shape[1], args.k
+    st = torch.cuda.current_stream(dev)
+
+    t0 = time.perf_counter()
+    idx = rbc.rbc_build(Xd, w.n_r, metric=rbc.L2, seed=2, storage=storage)
+    torch.cuda.synchronize(dev)
+    build_s = time.perf_counter() - t0
+
+    ids = torch.empty((m, k), dtype=torch.int64, device=dev)
+    dist_ = torch.empty((m, k), dtype=torch.float32, device=dev)
+
+    def step():
+        rbc.rbc_search(idx, Qd, k, out_ids=ids, out_dist=dist_)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    launches_per_step = rbc.last_stats()["kernel_launches"]
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    # ---- device-resident timed region ----
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize(dev)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        evs[0].record(st)
+        for i in range(args.steps):
+            step()
+            evs[i + 1].record(st)
+        torch.cuda.synchronize(dev)
+        barrier()
+    launches = launches_per_step * args.steps
+    elapsed_ms = evs[0].elapsed_time(evs[-1])
+    step_ms = sorted(evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps))
+    lat = {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+           "unit": "ms per batch of %d queries" % m}
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    stats = rbc.last_stats()
+    qps = world * m * args.steps / (elapsed_ms / 1000.0)
+
+    # ---- phase timing (separate pass: events around each phase) ----
+    rbc.set_timing(True)
+    ph = {"stage1_ms": 0.0, "stage2_ms": 0.0, "select_ms": 0.0, "fallback_ms": 0.0}
+    pairs = 0
+    nt = max(3, min(args.steps, 5))
+    for _ in range(nt):
+        step()
+        s = rbc.last_stats()
+        for key in ph:
+            ph[key] += s[key] / nt
+        pairs = s["pairs"]
+    rbc.set_timing(False)
+
+    # ---- end-to-end through the C ABI with host buffers ----
+    Qh = torch.from_numpy(Q).pin_memory()
+    ids_h = torch.empty((m, k), dtype=torch.int64).pin_memory()
+    dist_h = torch.empty((m, k), dtype=torch.float32).pin_memory()
+    Qh_np, ids_np, dist_np = Qh.numpy(), ids_h.numpy(), dist_h.numpy()
+    for _ in range(2):
+        rbc.rbc_search(idx, Qh_np, k, out_ids=ids_np, out_dist=dist_np)
+    torch.cuda.synchronize(dev)
+    e2e_steps = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        rbc.rbc_search(idx, Qh_np, k, out_ids=ids_np, out_dist=dist_np)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    e2e_qps = world * m * e2e_steps / e2e_s
+    same = bool((ids_h.numpy() == ids.cpu().numpy()).all())
+
+    # ---- plain FP32 CUDA-core brute force on the same queries ----
+    fp32_m = min(m, 20000)
+    Qs = Qd[:fp32_m].contiguous()
+    rbc.bf_search(Qs, Xd, k, metric=rbc.L2, storage=rbc.F32)
+    torch.cuda.synchronize(dev)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(st)
+    bf_ids, bf_dist = rbc.bf_search(Qs, Xd, k, metric=rbc.L2, storage=rbc.F32)
+    f1.record(st)
+    torch.cuda.synchronize(dev)
+    fp32_qps = fp32_m / (f0.elapsed_time(f1) / 1000.0)
+    agree = float((bf_ids.cpu().numpy() == ids[:fp32_m].cpu().numpy()).all(axis=1).mean())
+
+    # ---- dense BF16 brute force (tensor cores) on the same queries ----
+    rbc.set_timing(True)
+    bf16_ids, _ = rbc.bf_search(Qd, Xd, k, metric=rbc.L2, storage=rbc.BF16)
+    torch.cuda.synchronize(dev)
+    b0 = torch.cuda.Event(enable_timing=True)
+    b1 = torch.cuda.Event(enable_timing=True)
+    b0.record(st)
+    rbc.bf_search(Qd, Xd, k, metric=rbc.L2, storage=rbc.BF16)
+    b1.record(st)
+    bst = rbc.last_stats()
+    rbc.set_timing(False)
+    torch.cuda.synchronize(dev)
+    bf16_qps = m / (b0.elapsed_time(b1) / 1000.0)
+
+    peaks, peak_src = load_peaks()
+    flops_per_pair = 2 * d
+    # dominant kernel: stage-two tcgen05 BF (timed with events on its stream)
+    tflops = pairs * flops_per_pair / (ph["stage2_ms"] / 1000.0) / 1e12 if ph["stage2_ms"] > 0 else None
+    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    dense_tflops = m * len(X) * flops_per_pair / (bst["stage2_ms"] / 1000.0) / 1e12 if bst["stage2_ms"] else None
+    roofline = {
+        "bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+        "frac": (tflops / peak) if tflops else None, "traffic": None,
+        "kernel": "bf_tc_kernel (stage-two BF over surviving lists)",
+        "peak_source": f"{peak_src} bf16 sustained (cuBLAS), of {peak_src}",
+        "flops_per_launch": pairs * flops_per_pair, "launch_ms": ph["stage2_ms"],
+        "dense_bf16_bf": {"achieved": dense_tflops, "frac": (dense_tflops / peak) if dense_tflops else None,
+                          "launch_ms": bst["stage2_ms"]},
+    }
+
+    # ---- CPU oracle baseline on a bounded sample (rank 0, N = 1) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+
+        S = min(args.cpu_sample, m)
+        g = np.random.default_rng(11)
+        sel = np.sort(g.choice(m, S, replace=False))
+        reps = oracle.sample_reps(len(X), w.n_r, 2)
+        oidx = oracle.build_exact(X, reps, "l2")
+        t0 = time.perf_counter()
+        o_ids, o_rho, _ = oracle.search_exact(oidx, Q[sel], k)
+        cpu_s = time.perf_counter() - t0
+        g_ids = ids.cpu().numpy()[sel]
+        g_d = dist_.cpu().numpy()[sel].astype(np.float64)
+        rel = np.abs(g_d - o_rho) / np.maximum(o_rho, 1e-30)
+        cpu = {"value": S / cpu_s, "unit": "queries/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{S} random queries of {m} (seed 11), exact RBC search (FP64) against the full "
+                         f"{len(X)}-point database; index built outside the timed region",
+               "parity_on_sample": {"rows_ids_equal": float((g_ids == o_ids).all(axis=1).mean()),
+                                    "max_rel_dist_err": float(rel.max())}}
+
+    out = {
+        "metric": "exact k-NN queries/s (RBC BF16+rerank vs FP32 brute force), p50/p99 latency",
+        "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / args.steps, "latency": lat, "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+        "config": {"workload": args.workload, "n": len(X), "m": m, "d": d, "n_r": w.n_r, "k": k,
+                   "metric": "l2", "storage": args.storage, "noise_var": w.params.get("noise_var"),
+                   "intrinsic_dim": w.params.get("k"), "parallelism": f"replicas{world}",
+                   "l2_flush": "inputs larger than L2 (bf16 database 128 MiB + FP32 copy 256 MiB)"},
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": m * d * 4,
+                "d2h_bytes_per_step": m * k * 12, "matches_device_run": same},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "fp32_bruteforce": {"value": fp32_qps, "unit": "queries/s", "queries": fp32_m,
+                            "rows_equal_to_rbc": agree},
+        "bf16_bruteforce": {"value": bf16_qps, "unit": "queries/s",
+                            "rows_equal_to_rbc": float((bf16_ids.cpu().numpy() == ids.cpu().numpy()).all(axis=1).mean())},
+        "speedup_vs_fp32_bruteforce": qps / fp32_qps,
+        "phases_ms": ph,
+        "stats": {"kept_reps_per_query": stats["kept_reps"] / m,
+                  "examined_per_query": pairs / m if pairs else None,
+                  "uncertified": stats["uncertified"], "fp64_ties": stats["fp64_ties"],
+                  "boundary_ties": stats["boundary_ties"]},
+        "build_s": build_s,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -186,16 +186,33 @@ int rbc_index_export(const rbc_index* idx, int64_t* reps, int64_t* offsets, int6
 typedef struct {
   int64_t queries;
   int64_t kept_reps;         /* sum over queries of surviving representatives */
-  int64_t tile_points;       /* sum over query tiles of union list points x tile rows */
-  int64_t stage2_items;      /* stage-two work items launched */
+  int64_t tile_points;       /* sum over query tiles of the points in the tile's
+                                union of surviving lists */
+  int64_t stage2_items;      /* stage-two work-item capacity launched */
   int64_t uncertified;       /* queries whose low-precision candidate set failed
                                 certification and were re-searched in FP32 */
   int64_t fp64_ties;         /* queries whose order needed the FP64 tie step */
   int64_t boundary_ties;     /* queries with an FP32 near-tie at the k-th place */
+  int64_t pairs;             /* (query, point) distances of the main BF pass:
+                                dense BF m*n; exact search sum over tiles of
+                                tile rows x union points */
+  int64_t kernel_launches;   /* CUDA kernels this call launched */
+  double stage1_ms;          /* device time per phase, filled only while
+                                rbc_set_timing(1) is in effect: preparation and */
+  double stage2_ms;          /*   stage one / the main BF distance kernel / */
+  double select_ms;          /*   merge + re-rank + certification / */
+  double fallback_ms;        /*   FP32 re-search of uncertified queries */
 } rbc_search_stats;
 
-/* rbc_last_stats -- statistics of this thread's last search call (host only). */
+/* rbc_last_stats -- statistics of this thread's last search call (host only;
+ * waits for that call's stream). */
 int rbc_last_stats(rbc_search_stats* out);
+
+/* rbc_set_timing -- on != 0: later searches on this thread record CUDA events
+ * around their phases (one extra stream synchronisation per call) so that
+ * rbc_last_stats reports per-phase device times.  Off by default.  Returns
+ * the previous setting. */
+int rbc_set_timing(int on);
 
 /* rbc_free -- releases the index (waits for its outstanding work). NULL ok. */
 void rbc_free(rbc_index* idx);

@@ -26,7 +26,7 @@ import numpy as np
 __all__ = [
     "L2", "L1", "EXACT", "ONESHOT", "F32", "BF16", "F16",
     "RbcError", "bf_search", "rbc_build", "rbc_search", "rbc_sample_reps",
-    "RbcIndex", "last_stats", "library_path", "load",
+    "RbcIndex", "last_stats", "set_timing", "library_path", "load",
 ]
 
 L2, L1 = 0, 1
@@ -62,7 +62,8 @@ class _Desc(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "queries", "kept_reps", "tile_points", "stage2_items", "uncertified", "fp64_ties",
-        "boundary_ties")]
+        "boundary_ties", "pairs", "kernel_launches")] + [
+        (name, ctypes.c_double) for name in ("stage1_ms", "stage2_ms", "select_ms", "fallback_ms")]
 
 
 def library_path() -> str:
@@ -88,6 +89,8 @@ def load():
     lib.rbc_index_info.argtypes = [P, ctypes.POINTER(_Desc)]
     lib.rbc_index_export.argtypes = [P, P, P, P, P]
     lib.rbc_last_stats.argtypes = [ctypes.POINTER(_Stats)]
+    lib.rbc_set_timing.argtypes = [ctypes.c_int]
+    lib.rbc_set_timing.restype = ctypes.c_int
     lib.rbc_free.argtypes = [P]
     lib.rbc_free.restype = None
     lib.rbc_last_error.restype = ctypes.c_char_p
@@ -239,6 +242,11 @@ def rbc_search(index: RbcIndex, Q, k: int, out_ids=None, out_dist=None, stream=N
     st = _stream_of(stream, qdev or idev)
     _check(load().rbc_search(index.handle, qp, m, k, ip, dp, st))
     return out_ids, out_dist
+
+
+def set_timing(on: bool) -> bool:
+    """Per-phase device timing of later searches on this thread (see last_stats)."""
+    return bool(load().rbc_set_timing(1 if on else 0))
 
 
 def last_stats() -> dict:

@@ -26,6 +26,8 @@ namespace {
 thread_local char g_err[512] = "";
 }
 
+thread_local long long t_launches = 0;
+
 void set_error(const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
@@ -196,6 +198,8 @@ float simt_eps(int d) { return (float)(d + 8) * U32; }
 // relative bound of rho from the FP32 re-rank (interleaved partial sums)
 float rerank_eps_host(int d) { return (0.25f * d + 8.0f) * U32; }
 int pad64(int d) { return (d + 63) / 64 * 64; }
+// the tensor-core kernel reads whole tiles of norms past the last row
+constexpr int64_t NORM_PAD = 512;
 
 // ---- per-thread statistics ----
 struct StatsBlock {
@@ -207,11 +211,44 @@ thread_local bool t_stats_pending = false;
 thread_local rbc_search_stats t_stats_fixed;
 
 // device counters: ints [0] uncertified [1] fp64 ties [2] boundary ties,
-// [4..6] the same for the FP32 re-search; u64 sums [0] kept reps [1] tile points
+// [4..6] the same for the FP32 re-search; u64 sums [0] kept reps
+// [1] tile points [2] (query, point) pairs of the main pass
 struct Counters {
   int* c = nullptr;
   unsigned long long* sums = nullptr;
 };
+
+// Optional per-phase device timing (rbc_set_timing).  Marks 0..4 bound the
+// phases: [0,1) preparation + stage one, [1,2) main BF kernel, [2,3) merge +
+// re-rank + certification, [3,4) FP32 re-search.
+struct Timing {
+  bool on = false;
+  bool ready = false;
+  cudaEvent_t ev[5];
+  double ms[4] = {0, 0, 0, 0};
+};
+thread_local Timing t_timing;
+
+void tmark(int i, cudaStream_t st) {
+  if (!t_timing.on) return;
+  if (!t_timing.ready) {
+    for (auto& e : t_timing.ev) cudaEventCreate(&e);
+    t_timing.ready = true;
+  }
+  cudaEventRecord(t_timing.ev[i], st);
+}
+
+// after the stream has passed mark 4: add the phase times
+void taccumulate() {
+  if (!t_timing.on || !t_timing.ready) return;
+  cudaEventSynchronize(t_timing.ev[4]);
+  for (int i = 0; i < 4; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t_timing.ev[i], t_timing.ev[i + 1]) == cudaSuccess)
+      t_timing.ms[i] += ms;
+  }
+  cudaGetLastError();
+}
 
 __global__ void stats_pack_kernel(const int* c, const unsigned long long* sums,
                                   unsigned long long* out) {
@@ -222,20 +259,22 @@ __global__ void stats_pack_kernel(const int* c, const unsigned long long* sums,
     out[3] = (unsigned long long)(c[1] + c[5]);
     out[4] = (unsigned long long)(c[2] + c[6]);
     out[5] = (unsigned long long)c[4];
-    out[6] = 0;
+    out[6] = sums[2];
     out[7] = 0;
   }
 }
 
 int counters_alloc(Counters& cn, Arena& ar, cudaStream_t st) {
   RBC_TRY(ar.alloc(&cn.c, 8));
-  RBC_TRY(ar.alloc(&cn.sums, 2));
+  RBC_TRY(ar.alloc(&cn.sums, 3));
   RBC_CUDA(cudaMemsetAsync(cn.c, 0, 8 * sizeof(int), st));
-  RBC_CUDA(cudaMemsetAsync(cn.sums, 0, 2 * sizeof(unsigned long long), st));
+  RBC_CUDA(cudaMemsetAsync(cn.sums, 0, 3 * sizeof(unsigned long long), st));
+  t_launches = 0;
+  for (double& v : t_timing.ms) v = 0;
   return RBC_OK;
 }
 
-int stats_publish(const Counters& cn, int64_t queries, int64_t items, Arena& ar,
+int stats_publish(const Counters& cn, int64_t queries, int64_t items, int64_t host_pairs, Arena& ar,
                   cudaStream_t st) {
   if (!t_stats_host) {
     void* p = nullptr;
@@ -251,6 +290,12 @@ int stats_publish(const Counters& cn, int64_t queries, int64_t items, Arena& ar,
   memset(&t_stats_fixed, 0, sizeof(t_stats_fixed));
   t_stats_fixed.queries = queries;
   t_stats_fixed.stage2_items = items;
+  t_stats_fixed.pairs = host_pairs;
+  t_stats_fixed.kernel_launches = t_launches;
+  t_stats_fixed.stage1_ms = t_timing.ms[0];
+  t_stats_fixed.stage2_ms = t_timing.ms[1];
+  t_stats_fixed.select_ms = t_timing.ms[2];
+  t_stats_fixed.fallback_ms = t_timing.ms[3];
   t_stats_stream = st;
   t_stats_pending = true;
   return RBC_OK;
@@ -367,7 +412,9 @@ int bf_dense_f32(const float* Qdev, int64_t m, const DbView& db, int d, int k, i
   w.dense_splits = (int)splits;
   w.dense_chunk = chunk;
   int grid = (int)std::min<int64_t>(items, (int64_t)sms * 2 * 16);
+  tmark(1, st);
   RBC_TRY(launch_bf_simt_topc(Qdev, db.X32, d, metric, C, w, TopOut{ps, pi}, grid, st));
+  tmark(2, st);
   SelectArgs a{};
   a.part_score = ps;
   a.part_idx = pi;
@@ -388,7 +435,10 @@ int bf_dense_f32(const float* Qdev, int64_t m, const DbView& db, int d, int k, i
   a.out_ids = out_ids;
   a.out_dist = out_dist;
   a.counters = cnt;
-  return launch_select(a, st);
+  RBC_TRY(launch_select(a, st));
+  tmark(3, st);
+  tmark(4, st);
+  return RBC_OK;
 }
 
 // Rows of a query buffer that failed certification are searched again with
@@ -436,7 +486,7 @@ int select_lp_and_fallback(const float* ps, const int* pi, int C, const int* til
   a.part_score = ps;
   a.part_idx = pi;
   a.C = C;
-  a.nsub = 1;
+  a.nsub = 2;
   a.tile_slot_off = tile_slot_off;
   a.dense_splits = dense_splits;
   a.m = m;
@@ -457,13 +507,16 @@ int select_lp_and_fallback(const float* ps, const int* pi, int C, const int* til
   a.out_dist = out_dist;
   a.fallback_rows = fb_rows;
   a.counters = cnt;
+  tmark(2, st);
   RBC_TRY(launch_select(a, st));
+  tmark(3, st);
   int nfb = 0;
   RBC_CUDA(cudaMemcpyAsync(&nfb, cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
   RBC_CUDA(cudaStreamSynchronize(st));
   if (nfb > 0)
     RBC_TRY(fallback_f32(Qbuf, fb_rows, nfb, qorig, db, d, k, RBC_L2, out_ids, out_dist, cnt + 4,
                          ar, st));
+  tmark(4, st);
   return RBC_OK;
 }
 
@@ -476,6 +529,7 @@ int bf_dense_lp(const float* Qdev, int64_t m, const DbView& db, int d, int k, in
   const int C = lp_width(c_out);
   LpQueries ql;
   RBC_TRY(lp_queries(Qdev, m, d, db.dpad, storage, ql, ar, st));
+  tmark(1, st);
   const int64_t tiles = (m + TQ - 1) / TQ;
   const int sms = sm_count();
   int64_t splits = (4LL * sms + tiles - 1) / tiles;
@@ -486,8 +540,8 @@ int bf_dense_lp(const float* Qdev, int64_t m, const DbView& db, int d, int k, in
   const int64_t items = tiles * splits;
   float* ps;
   int* pi;
-  RBC_TRY(ar.alloc(&ps, items * TQ * C));
-  RBC_TRY(ar.alloc(&pi, items * TQ * C));
+  RBC_TRY(ar.alloc(&ps, items * TQ * 2 * C));
+  RBC_TRY(ar.alloc(&pi, items * TQ * 2 * C));
   TileWork w{};
   w.num_items = (int)items;
   w.m = m;
@@ -503,6 +557,7 @@ int bf_dense_lp(const float* Qdev, int64_t m, const DbView& db, int d, int k, in
   RBC_TRY(launch_bf_tc_topc(Qm, Xm, C, w, TopOut{ps, pi}, grid, st, dev_err));
   RBC_TRY(select_lp_and_fallback(ps, pi, C, nullptr, (int)splits, m, Qdev, ql, db, d, k, c_out,
                                  nullptr, out_ids, out_dist, cnt, ar, st));
+  taccumulate();
   uint32_t herr = 0;
   RBC_CUDA(cudaMemcpyAsync(&herr, dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   RBC_CUDA(cudaStreamSynchronize(st));
@@ -556,7 +611,8 @@ int build_exact(rbc_index* ix, const float* Xdev, const std::vector<int64_t>& re
     uint16_t* xl;
     uint16_t* rl;
     RBC_TRY(ix->alloc(&xl, n * ix->dpad));
-    RBC_TRY(ix->alloc(&ix->xnorm, n));
+    RBC_TRY(ix->alloc(&ix->xnorm, n + NORM_PAD));
+    RBC_CUDA(cudaMemsetAsync(ix->xnorm + n, 0, NORM_PAD * sizeof(float), st));
     RBC_TRY(ix->alloc(&ix->lp_max, 4));
     RBC_TRY(ix->alloc(&rl, (int64_t)n_r * ix->dpad));
     RBC_TRY(ix->alloc(&ix->rnorm, n_r));
@@ -586,6 +642,7 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
   const bool lp = uses_lp(ix->storage, metric) && ix->Xlp != nullptr;
   const int64_t tiles = (mb + TQ - 1) / TQ;
 
+  tmark(0, st);
   // stage 1: BF(Q, R) keeping every distance
   float* D;
   RBC_TRY(ar.alloc(&D, mb * n_r));
@@ -624,6 +681,7 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
                        qkept, st));
   RBC_TRY(launch_sum_i32(qkept, mb, cn.sums, st));
   RBC_TRY(launch_sum_i64(tpts, tiles, cn.sums + 1, st));
+  RBC_TRY(launch_sum_pairs(tpts, mb, cn.sums + 2, st));
   // work items
   int64_t W = (tiles * n + 16LL * sms - 1) / (16LL * sms);
   W = std::max<int64_t>(W, 4096);
@@ -668,8 +726,10 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
     int* pi;
     RBC_TRY(ar.alloc(&ps, cap_items * TQ * 2 * C));
     RBC_TRY(ar.alloc(&pi, cap_items * TQ * 2 * C));
+    tmark(1, st);
     RBC_TRY(launch_bf_simt_topc(Qp, ix->X32, d, metric, C, w2, TopOut{ps, pi},
                                 (int)std::min<int64_t>(cap_items, (int64_t)sms * 2 * 8), st));
+    tmark(2, st);
     SelectArgs a{};
     a.part_score = ps;
     a.part_idx = pi;
@@ -690,6 +750,8 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
     a.out_dist = dist;
     a.counters = cn.c;
     RBC_TRY(launch_select(a, st));
+    tmark(3, st);
+    tmark(4, st);
   } else {
     const int c_out = choose_c(k, true, ix->rerank_c);
     const int C = lp_width(c_out);
@@ -697,10 +759,11 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
     RBC_TRY(lp_queries(Qp, mb, d, ix->dpad, ix->storage, ql, ar, st));
     float* ps;
     int* pi;
-    RBC_TRY(ar.alloc(&ps, cap_items * TQ * C));
-    RBC_TRY(ar.alloc(&pi, cap_items * TQ * C));
+    RBC_TRY(ar.alloc(&ps, cap_items * TQ * 2 * C));
+    RBC_TRY(ar.alloc(&pi, cap_items * TQ * 2 * C));
     LpMatrix Qm{ql.lp, ql.norm, mb, ix->dpad, ix->storage};
     LpMatrix Xm{ix->Xlp, ix->xnorm, n, ix->dpad, ix->storage};
+    tmark(1, st);
     RBC_TRY(launch_bf_tc_topc(Qm, Xm, C, w2, TopOut{ps, pi}, sms, st, dev_err));
     RBC_TRY(select_lp_and_fallback(ps, pi, C, toff, 0, mb, Qp, ql, db, d, k, c_out, qperm, ids,
                                    dist, cn.c, ar, st));
@@ -708,6 +771,7 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
   uint32_t herr = 0;
   RBC_CUDA(cudaMemcpyAsync(&herr, dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   RBC_CUDA(cudaStreamSynchronize(st));
+  taccumulate();
   if (herr) {
     set_error("stage-two work generation / kernel reported device error flags 0x%x", herr);
     return (herr & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
@@ -756,6 +820,7 @@ int rbc_last_stats(rbc_search_stats* out) {
     t_stats_fixed.uncertified = (int64_t)v[2];
     t_stats_fixed.fp64_ties = (int64_t)v[3];
     t_stats_fixed.boundary_ties = (int64_t)v[4];
+    if (v[6]) t_stats_fixed.pairs = (int64_t)v[6];
     t_stats_pending = false;
   }
   *out = t_stats_fixed;
@@ -797,16 +862,19 @@ int bf_search(const float* Q, int64_t m, const float* X, int64_t n, int32_t d, i
   DbView db;
   db.X32 = Xdev;
   db.rows = n;
+  tmark(0, st);
   if (!uses_lp(storage, metric)) {
     RBC_TRY(bf_dense_f32(io.Qdev, m, db, d, k, metric, nullptr, io.ids_dev, io.dist_dev, cn.c,
                          ar, st));
+    taccumulate();
   } else {
     db.dpad = pad64(d);
     uint16_t* xl;
     float* xn;
     unsigned* mx;
     RBC_TRY(ar.alloc(&xl, n * db.dpad));
-    RBC_TRY(ar.alloc(&xn, n));
+    RBC_TRY(ar.alloc(&xn, n + NORM_PAD));
+    RBC_CUDA(cudaMemsetAsync(xn + n, 0, NORM_PAD * sizeof(float), st));
     RBC_TRY(ar.alloc(&mx, 2));
     RBC_CUDA(cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned), st));
     RBC_TRY(launch_to_lowp(Xdev, n, d, db.dpad, storage, xl, xn, nullptr, mx, mx + 1, st));
@@ -815,9 +883,15 @@ int bf_search(const float* Q, int64_t m, const float* X, int64_t n, int32_t d, i
     db.lp_max = mx;
     RBC_TRY(bf_dense_lp(io.Qdev, m, db, d, k, storage, 0, io.ids_dev, io.dist_dev, cn.c, ar, st));
   }
-  RBC_TRY(stats_publish(cn, m, 0, ar, st));
+  RBC_TRY(stats_publish(cn, m, 0, m * n, ar, st));
   RBC_TRY(io_finish(m, k, out_ids, out_dist, io, st));
   return RBC_OK;
+}
+
+int rbc_set_timing(int on) {
+  int prev = t_timing.on ? 1 : 0;
+  t_timing.on = on != 0;
+  return prev;
 }
 
 int rbc_build(const float* X, int64_t n, int32_t d, int32_t n_r, int32_t s, int32_t metric,
@@ -933,7 +1007,7 @@ int rbc_search(const rbc_index* ix, const float* Q, int64_t m, int32_t k, int64_
     RBC_TRY(search_exact_batch(ix, io.Qdev + b0 * ix->d, mb, k, io.ids_dev + b0 * k,
                                io.dist_dev + b0 * k, cn, &items, bar, st));
   }
-  RBC_TRY(stats_publish(cn, m, items, ar, st));
+  RBC_TRY(stats_publish(cn, m, items, 0, ar, st));
   RBC_TRY(io_finish(m, k, out_ids, out_dist, io, st));
   return RBC_OK;
 }

@@ -1,15 +1,635 @@
-// tcgen05 tensor-core BF kernel (placeholder until the kernel lands).
+// Tensor-core brute-force tile kernel (sm_103a): BF(Q, X[segments]) for the
+// l2 metric, fused with a per-query top-C (Section 3: the distance step is a
+// matrix product, the comparison step a per-query reduction).
+//
+// For l2, rho(q, x)^2 = |q|^2 - 2 q.x + |x|^2; |q|^2 does not change the
+// order for a fixed query, so the kernel ranks points by the score
+//     s(q, x) = |x~|^2 - 2 q~.x~
+// of the low-precision (bf16 / fp16) rows q~, x~.  The products q~.x~ come
+// from tcgen05.mma (kind::f16, FP32 accumulation in tensor memory); the
+// score and the selection run in the epilogue, so no distance matrix is ever
+// written to global memory.  Candidates are re-ranked in FP32 and certified
+// afterwards (select.cu).
+//
+// Structure (one CTA per SM, persistent over work items):
+//   warp 0     TMA producer: the 128-row query tile once per item, database
+//              tiles of BN rows into an S-stage ring (128-byte swizzle, K-major),
+//              and each tile's row norms (+inf past the segment end, which
+//              masks those columns without a per-element test).
+//   warp 1     allocates 2*BN tensor-memory columns and issues the MMAs
+//              (M = 128, N = BN, K = 16 per instruction) into a double-buffered
+//              accumulator.
+//   warps 2-9  epilogue: warp w reads tensor-memory lanes 32*(w%4) .. +31 (one
+//              query row per thread) for half of the tile's columns, forms
+//              the scores two at a time (fma.f32x2), takes a running minimum
+//              over each 32-column chunk (three-input min) and only when that
+//              minimum beats the row's current C-th best walks the chunk and
+//              inserts into a sorted register list.
+// Every wait on an mbarrier is bounded; on expiry the kernel raises
+// DEV_ERR_TIMEOUT, stops issuing work, waits (bounded) for its own TMA copies
+// and frees its tensor memory before returning.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace rbc {
 
-bool tc_available() { return false; }
+namespace {
 
-int launch_bf_tc_topc(const LpMatrix&, const LpMatrix&, int, const TileWork&, const TopOut&, int,
-                      cudaStream_t, uint32_t*) {
-  set_error("tensor-core BF kernel not built");
-  return RBC_ERR_UNSUPPORTED;
+constexpr int NUM_THREADS = 320;   // 10 warps
+constexpr int EPI_WARP0 = 2;       // first epilogue warp
+constexpr int BM = TQ;             // query rows per tile (MMA M)
+constexpr uint64_t WAIT_NS = 2000000000ull;  // bounded waits: 2 s
+
+#define RBC_TRY_TC(x)            \
+  do {                           \
+    int _r = (x);                \
+    if (_r != RBC_OK) return _r; \
+  } while (0)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity.  Returns false (and sets
+// the CTA's abort flag and the device error word) if the wait expired or
+// another role already aborted.
+__device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag,
+                                       uint32_t* dev_err) {
+  if (mbar_try_wait(b, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try_wait(b, parity)) return true;
+    if ((i & 63) == 63) {
+      if (*abort_flag) return false;
+      if (global_ns() - t0 > WAIT_NS) {
+        *abort_flag = 1;
+        atomicOr(dev_err, DEV_ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                            int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// core groups 1024 bytes apart (SBO); start address in 16-byte units.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, A/B both bf16 (1) or
+// both fp16 (0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_f16(int ab_fmt, int M, int N) {
+  return (1u << 4) | ((uint32_t)ab_fmt << 7) | ((uint32_t)ab_fmt << 10) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                        uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 32 lanes x 32 consecutive 32-bit columns -> 32 registers per thread
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// (d0, d1) = (a0, a1) * (b, b) + (c0, c1) as one packed FP32 instruction
+__device__ __forceinline__ void fma2(float& d0, float& d1, float a0, float a1, float b, float c0,
+                                     float c1) {
+  uint64_t a, bb, c, d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(a) : "f"(a0), "f"(a1));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(bb) : "f"(b), "f"(b));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(c) : "f"(c0), "f"(c1));
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(bb), "l"(c));
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d0), "=f"(d1) : "l"(d));
+}
+
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+struct TcParams {
+  TileWork w;
+  TopOut out;
+  const float* xnorm;  // [rows + pad] |x~|^2, readable up to row index rows + BN
+  int64_t x_rows;
+  int q_rows;
+  uint32_t* dev_err;
+};
+
+__device__ __forceinline__ void item_info(const TileWork& w, int item, int& q0, int& nq, int& sb,
+                                          int& se, int& slot) {
+  if (w.items) {
+    const WorkItem it = w.items[item];
+    q0 = it.q_row0;
+    nq = it.nq;
+    sb = it.seg_begin;
+    se = it.seg_end;
+    slot = it.slot;
+  } else {
+    int tile = item / w.dense_splits;
+    int s = item - tile * w.dense_splits;
+    q0 = tile * TQ;
+    nq = min(TQ, (int)(w.m - (int64_t)q0));
+    sb = s;
+    se = s + 1;
+    slot = item;
+  }
+}
+
+__device__ __forceinline__ Seg seg_at(const TileWork& w, int si) {
+  if (w.segs) return w.segs[si];
+  int64_t b = (int64_t)si * w.dense_chunk;
+  int64_t e = min(w.n, b + w.dense_chunk);
+  return Seg{(int32_t)b, (int32_t)e};
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory layout.  Database tiles start at a row index rounded down to
+// a multiple of 4 so that the tile's norms (BN floats) can be fetched with
+// one 16-byte-aligned bulk copy; the columns before the segment start and
+// past its end are masked to +inf in the epilogue.
+template <int C, int KB, int BN, int S, int QCAP>
+struct TcSmem {
+  static constexpr int Q_BYTES = KB * BM * 128;  // query tile, KB K-blocks of 64 elements
+  static constexpr int X_STAGE = KB * BN * 128;  // one database tile
+  static constexpr int NORM_STAGE = BN * 4;
+  static constexpr int NEPI_THREADS = NUM_THREADS - EPI_WARP0 * 32;
+  static constexpr int OFF_Q = 0;
+  static constexpr int OFF_X = OFF_Q + Q_BYTES;
+  static constexpr int OFF_NORM = OFF_X + S * X_STAGE;
+  static constexpr int OFF_QS = OFF_NORM + S * NORM_STAGE;         // hit queues: scores
+  static constexpr int OFF_QI = OFF_QS + QCAP * NEPI_THREADS * 4;  // hit queues: columns
+  static constexpr int OFF_BAR = OFF_QI + QCAP * NEPI_THREADS * 4;
+  // barriers: full[S], empty[S], tfull[2], tempty[2], qfull, qempty
+  static constexpr int NBAR = 2 * S + 6;
+  static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;  // tmem base, abort flag
+  static constexpr int BYTES = OFF_MISC + 16;
+  static constexpr int ALLOC = BYTES + 1024;  // slack for 1024-byte alignment
+  static_assert(ALLOC <= 232448, "shared memory budget");
+};
+
+template <int C, int KB, int BN, int S, int QCAP>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap xmap,
+             TcParams p, uint32_t idesc) {
+  using L = TcSmem<C, KB, BN, S, QCAP>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~(uintptr_t)1023);
+  uint8_t* sQ = smem + L::OFF_Q;
+  uint8_t* sX = smem + L::OFF_X;
+  float* sNorm = reinterpret_cast<float*>(smem + L::OFF_NORM);
+  float* sQs = reinterpret_cast<float*>(smem + L::OFF_QS);
+  int* sQi = reinterpret_cast<int*>(smem + L::OFF_QI);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + S;
+  uint64_t* tfull = bars + 2 * S;
+  uint64_t* tempty = bars + 2 * S + 2;
+  uint64_t* qfull = bars + 2 * S + 4;
+  uint64_t* qempty = bars + 2 * S + 5;
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(smem + L::OFF_MISC);
+  volatile int* sAbort = reinterpret_cast<volatile int*>(smem + L::OFF_MISC + 4);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  constexpr int NEPI = NUM_THREADS / 32 - EPI_WARP0;  // 8 epilogue warps
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1 + NEPI);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], NEPI);
+    }
+    mbar_init(qfull, 1);
+    mbar_init(qempty, 1);
+    *sAbort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(sTmem)),
+                 "r"(2 * BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *sTmem;
+
+  const TileWork& w = p.w;
+  const int n_items = w.num_items_dev ? *w.num_items_dev : w.num_items;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    uint32_t it = 0, qi = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x, ++qi) {
+      int q0, nq, sb, se, slot;
+      item_info(w, item, q0, nq, sb, se, slot);
+      if (!__all_sync(0xffffffffu, mbar_wait(qempty, (qi & 1) ^ 1, sAbort, p.dev_err))) {
+        ok = false;
+        break;
+      }
+      if (lane == 0) {
+        mbar_arrive_expect_tx(qfull, L::Q_BYTES);
+#pragma unroll
+        for (int kb = 0; kb < KB; ++kb) tma_load_2d(sQ + kb * BM * 128, &qmap, qfull, kb * 64, q0);
+      }
+      for (int si = sb; ok && si < se; ++si) {
+        const Seg sg = seg_at(w, si);
+        for (int x = sg.x_begin & ~3; x < sg.x_end; x += BN, ++it) {
+          const int s = it % S;
+          const uint32_t ph = (it / S) & 1;
+          if (!__all_sync(0xffffffffu, mbar_wait(&empty[s], ph ^ 1, sAbort, p.dev_err))) {
+            ok = false;
+            break;
+          }
+          if (lane == 0) {
+            mbar_arrive_expect_tx(&full[s], L::X_STAGE + L::NORM_STAGE);
+#pragma unroll
+            for (int kb = 0; kb < KB; ++kb)
+              tma_load_2d(sX + s * L::X_STAGE + kb * BN * 128, &xmap, &full[s], kb * 64, x);
+            bulk_load(sNorm + s * BN, p.xnorm + x, L::NORM_STAGE, &full[s]);
+          }
+          __syncwarp();
+        }
+      }
+    }
+    // drain: every issued stage must have landed before the CTA exits
+    if (lane == 0) {
+      for (uint32_t j = (it > (uint32_t)S ? it - S : 0); j < it; ++j)
+        mbar_wait(&full[j % S], (j / S) & 1, sAbort, p.dev_err);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    uint32_t it = 0, qi = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x, ++qi) {
+      int q0, nq, sb, se, slot;
+      item_info(w, item, q0, nq, sb, se, slot);
+      if (!__all_sync(0xffffffffu, mbar_wait(qfull, qi & 1, sAbort, p.dev_err))) {
+        ok = false;
+        break;
+      }
+      for (int si = sb; ok && si < se; ++si) {
+        const Seg sg = seg_at(w, si);
+        for (int x = sg.x_begin & ~3; x < sg.x_end; x += BN, ++it) {
+          const int s = it % S;
+          const uint32_t ph = (it / S) & 1;
+          const int buf = it & 1;
+          const uint32_t aph = (it >> 1) & 1;
+          bool got = mbar_wait(&full[s], ph, sAbort, p.dev_err) &&
+                     mbar_wait(&tempty[buf], aph ^ 1, sAbort, p.dev_err);
+          if (!__all_sync(0xffffffffu, got)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          if (lane == 0) {
+            const uint32_t d_tmem = tmem + buf * BN;
+            const uint32_t qa = smem_u32(sQ);
+            const uint32_t xb = smem_u32(sX + s * L::X_STAGE);
+#pragma unroll
+            for (int kb = 0; kb < KB; ++kb)
+#pragma unroll
+              for (int k16 = 0; k16 < 4; ++k16) {
+                uint64_t ad = smem_desc_sw128(qa + kb * BM * 128 + k16 * 32);
+                uint64_t bd = smem_desc_sw128(xb + kb * BN * 128 + k16 * 32);
+                mma_f16(d_tmem, ad, bd, idesc, (kb | k16) != 0);
+              }
+            mma_commit(&empty[s]);
+            mma_commit(&tfull[buf]);
+          }
+          __syncwarp();
+        }
+      }
+      if (lane == 0) mma_commit(qempty);
+      __syncwarp();
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    // thread = one query row (TMEM lane) x one half of each tile's columns.
+    // Hits (score below the row's current C-th best) are queued in shared
+    // memory; when any lane's queue might overflow, the whole warp merges its
+    // queues into the register lists in lock-step, so the O(C) insertions of
+    // different lanes share issue slots instead of serialising.
+    const int quarter = warp & 3;
+    const int half = (warp - EPI_WARP0) / 4;
+    const int row = quarter * 32 + lane;
+    const int et = threadIdx.x - EPI_WARP0 * 32;  // epilogue thread index
+    float* qs = sQs + et;
+    int* qix = sQi + et;
+    constexpr int HALF = BN / 2;
+    constexpr int NT = L::NEPI_THREADS;
+    uint32_t it = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
+      int q0, nq, sb, se, slot;
+      item_info(w, item, q0, nq, sb, se, slot);
+      TopList<C> top;
+      top.init();
+      float tau = INFINITY;
+      int qcnt = 0;
+      auto merge = [&]() {
+        const int qmax = __reduce_max_sync(0xffffffffu, qcnt);
+#pragma unroll 1
+        for (int e = 0; e < qmax; ++e) {
+          if (e < qcnt) {
+            float vv = qs[e * NT];
+            int ii = qix[e * NT];
+            if (top.admits(vv, ii)) top.insert(vv, ii);
+          }
+        }
+        qcnt = 0;
+        tau = top.worst();
+        __syncwarp();
+      };
+      for (int si = sb; ok && si < se; ++si) {
+        const Seg sg = seg_at(w, si);
+        for (int x = sg.x_begin & ~3; x < sg.x_end; x += BN, ++it) {
+          const int s = it % S;
+          const uint32_t ph = (it / S) & 1;
+          const int buf = it & 1;
+          const uint32_t aph = (it >> 1) & 1;
+          bool got = mbar_wait(&full[s], ph, sAbort, p.dev_err) &&
+                     mbar_wait(&tfull[buf], aph, sAbort, p.dev_err);
+          if (!__all_sync(0xffffffffu, got)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const float* nrm = sNorm + s * BN + half * HALF;
+          const int lo = sg.x_begin - x - half * HALF;  // first valid column of this half
+          const int hi = sg.x_end - x - half * HALF;    // one past the last valid column
+          const bool partial = lo > 0 || hi < HALF;
+          const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + buf * BN + half * HALF;
+#pragma unroll 1
+          for (int ch = 0; ch < HALF / 32; ++ch) {
+            float v[32];
+            tmem_ld32(tbase + ch * 32, v);
+            const float4* n4 = reinterpret_cast<const float4*>(nrm + ch * 32);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              float4 nn = n4[j];
+              fma2(v[4 * j], v[4 * j + 1], v[4 * j], v[4 * j + 1], -2.0f, nn.x, nn.y);
+              fma2(v[4 * j + 2], v[4 * j + 3], v[4 * j + 2], v[4 * j + 3], -2.0f, nn.z, nn.w);
+            }
+            if (partial) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                int c = ch * 32 + j;
+                if (c < lo || c >= hi) v[j] = INFINITY;
+              }
+            }
+            float ma = min3f(v[0], v[1], v[2]);
+            float mb = min3f(v[3], v[4], v[5]);
+#pragma unroll
+            for (int j = 6; j < 30; j += 4) {
+              ma = min3f(ma, v[j], v[j + 1]);
+              mb = min3f(mb, v[j + 2], v[j + 3]);
+            }
+            const float mn = min3f(ma, mb, fminf(v[30], v[31]));
+            const bool hit = mn < tau;
+            if (__any_sync(0xffffffffu, hit)) {
+              if (__any_sync(0xffffffffu, qcnt > QCAP - 32)) merge();
+              if (hit) {
+                const int cb = x + half * HALF + ch * 32;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                  if (v[j] < tau) {
+                    qs[qcnt * NT] = v[j];
+                    qix[qcnt * NT] = cb + j;
+                    ++qcnt;
+                  }
+                }
+              }
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) {
+            mbar_arrive(&tempty[buf]);
+            mbar_arrive(&empty[s]);
+          }
+        }
+      }
+      merge();
+      if (ok && row < nq) {
+        int64_t base = (((int64_t)slot * TQ + row) * 2 + half) * C;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          p.out.score[base + j] = top.s[j];
+          p.out.idx[base + j] = top.s[j] == INFINITY ? -1 : top.i[j];
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN)
+                 : "memory");
+  }
+}
+
+// ---- host side ----
+// cuTensorMapEncodeTiled is taken from the driver at run time, so the library
+// loads on machines without a driver (argument checks, the host sampler).
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+int encode_map(CUtensorMap* map, const void* base, int64_t rows, int dpad, int storage,
+               int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return RBC_ERR_CUDA;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)dpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)dpad * 2};
+  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(
+      map, storage == RBC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+      2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d): rows=%lld dpad=%d", (int)r, (long long)rows,
+              dpad);
+    return RBC_ERR_CUDA;
+  }
+  return RBC_OK;
+}
+
+template <int C, int KB, int BN, int S, int QCAP>
+int launch_tc(const LpMatrix& Qm, const LpMatrix& Xm, const TileWork& w, const TopOut& out,
+              int grid, cudaStream_t st, uint32_t* dev_err) {
+  using L = TcSmem<C, KB, BN, S, QCAP>;
+  CUtensorMap qmap, xmap;
+  RBC_TRY_TC(encode_map(&qmap, Qm.data, Qm.rows, Qm.dpad, Qm.storage, BM));
+  RBC_TRY_TC(encode_map(&xmap, Xm.data, Xm.rows, Xm.dpad, Xm.storage, BN));
+  auto kern = bf_tc_kernel<C, KB, BN, S, QCAP>;
+  RBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC));
+  TcParams p{w, out, Xm.norm, Xm.rows, (int)Qm.rows, dev_err};
+  uint32_t idesc = idesc_f16(Qm.storage == RBC_BF16 ? 1 : 0, BM, BN);
+  kern<<<grid, NUM_THREADS, L::ALLOC, st>>>(qmap, xmap, p, idesc);
+  RBC_LAUNCH_CHECK("bf_tc_kernel");
+  return RBC_OK;
+}
+
+template <int C>
+int dispatch_kb(const LpMatrix& Qm, const LpMatrix& Xm, const TileWork& w, const TopOut& out,
+                int grid, cudaStream_t st, uint32_t* dev_err) {
+  switch (Qm.dpad / 64) {
+    case 1: return launch_tc<C, 1, 256, 3, 40>(Qm, Xm, w, out, grid, st, dev_err);
+    case 2: return launch_tc<C, 2, 128, 3, 40>(Qm, Xm, w, out, grid, st, dev_err);
+    case 3: return launch_tc<C, 3, 64, 3, 40>(Qm, Xm, w, out, grid, st, dev_err);
+    case 4: return launch_tc<C, 4, 64, 2, 40>(Qm, Xm, w, out, grid, st, dev_err);
+    default:
+      set_error("tensor-core BF: padded dimension %d unsupported", Qm.dpad);
+      return RBC_ERR_UNSUPPORTED;
+  }
+}
+
+}  // namespace
+
+bool tc_available() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3;
+}
+
+int launch_bf_tc_topc(const LpMatrix& Qm, const LpMatrix& Xm, int C, const TileWork& w,
+                      const TopOut& out, int grid, cudaStream_t st, uint32_t* dev_err) {
+  if (!tc_available()) {
+    set_error("tensor-core BF kernel needs an sm_103 device");
+    return RBC_ERR_UNSUPPORTED;
+  }
+  if (Qm.dpad != Xm.dpad || Qm.storage != Xm.storage) {
+    set_error("tensor-core BF: operand layouts differ");
+    return RBC_ERR_ARG;
+  }
+  switch (C) {
+    case 8: return dispatch_kb<8>(Qm, Xm, w, out, grid, st, dev_err);
+    case 16: return dispatch_kb<16>(Qm, Xm, w, out, grid, st, dev_err);
+    case 32: return dispatch_kb<32>(Qm, Xm, w, out, grid, st, dev_err);
+    default:
+      set_error("tensor-core BF: list width %d unsupported", C);
+      return RBC_ERR_UNSUPPORTED;
+  }
 }
 
 }  // namespace rbc

@@ -86,6 +86,7 @@ enum : uint32_t {
 namespace rbc {
 void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+extern thread_local long long t_launches;  // kernels launched by this thread
 }  // namespace rbc
 
 #define RBC_CUDA(call)                                                                \
@@ -96,6 +97,7 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 
 #define RBC_LAUNCH_CHECK(what)                                                        \
   do {                                                                                \
+    ++::rbc::t_launches;                                                              \
     cudaError_t _e = cudaGetLastError();                                              \
     if (_e != cudaSuccess) return ::rbc::cuda_fail(_e, what, __FILE__, __LINE__);     \
   } while (0)

@@ -314,7 +314,26 @@ __global__ void sum_i64_kernel(const int64_t* __restrict__ v, int64_t n, unsigne
   if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
 }
 
+__global__ void sum_pairs_kernel(const int64_t* __restrict__ tpts, int64_t m,
+                                 unsigned long long* out) {
+  const int64_t tiles = (m + TQ - 1) / TQ;
+  unsigned long long s = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tiles;
+       t += (int64_t)gridDim.x * blockDim.x)
+    s += (unsigned long long)tpts[t] * (unsigned long long)min((int64_t)TQ, m - t * TQ);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
 }  // namespace
+
+int launch_sum_pairs(const int64_t* tile_points, int64_t m, unsigned long long* out,
+                     cudaStream_t st) {
+  if (m <= 0) return RBC_OK;
+  sum_pairs_kernel<<<16, 256, 0, st>>>(tile_points, m, out);
+  RBC_LAUNCH_CHECK("sum_pairs_kernel");
+  return RBC_OK;
+}
 
 int64_t counting_sort_scratch_ints(int64_t n, int nbins) {
   int64_t blocks = (n + CS_CHUNK - 1) / CS_CHUNK;

@@ -179,15 +179,21 @@ WORKLOADS = {
 
 
 def make_workload(
-    w: Workload | str, seed: int = 0, n: int | None = None, m: int | None = None
+    w: Workload | str,
+    seed: int = 0,
+    n: int | None = None,
+    m: int | None = None,
+    query_seed: int | None = None,
 ) -> tuple[np.ndarray, np.ndarray]:
-    """(X [n,d], Q [m,d]) float32 for a named workload; ``n``/``m`` override sizes."""
+    """(X [n,d], Q [m,d]) float32 for a named workload; ``n``/``m`` override
+    sizes; queries use ``query_seed`` (default seed + 1) with the same model."""
     if isinstance(w, str):
         w = WORKLOADS[w]
     n = w.n if n is None else n
     m = w.m if m is None else m
+    qs = seed + 1 if query_seed is None else query_seed
     if w.generator == "iid":
-        return iid_normal(n, w.d, seed), iid_normal(m, w.d, seed + 1)
+        return iid_normal(n, w.d, seed), iid_normal(m, w.d, qs)
     if w.generator == "subspace":
         mod = SubspaceModel(d=w.d, seed=seed, **w.params)
     elif w.generator == "clusters":
@@ -196,4 +202,4 @@ def make_workload(
         mod = SincosModel(d=w.d, seed=seed, **w.params)
     else:  # pragma: no cover
         raise ValueError(w.generator)
-    return mod.sample(n, seed), mod.sample(m, seed + 1)
+    return mod.sample(n, seed), mod.sample(m, qs)

@@ -99,3 +99,58 @@ def test_bf_on_a_side_stream():
     s.synchronize()
     o_ids, o_rho = oracle.bf(Q, X, 3, "l2")
     check_knn(Q, X, ids.cpu().numpy(), dist.cpu().numpy(), o_ids, o_rho)
+
+
+# ---- tensor-core (tcgen05) path: bf16 / fp16 storage, FP32 re-rank, certified ----
+
+LP = {"bf16": rbc.BF16, "f16": rbc.F16}
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("k", [1, 10])
+def test_bf_tc_iid_n16k_d16(storage, k):
+    X, Q = synth.make_workload("iid-n16k-d16", seed=0)
+    ids, dist = run_bf(Q, X, k, "l2", LP[storage])
+    o_ids, o_rho = oracle.bf(Q, X, k, "l2")
+    check_knn(Q, X, ids, dist, o_ids, o_rho)
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("n,m,d,k", [(1000, 1, 3, 1), (4099, 129, 33, 5), (3000, 127, 100, 31), (2500, 257, 128, 3), (70000, 300, 64, 10), (5000, 200, 200, 4), (600, 130, 256, 2)])
+def test_bf_tc_ragged(storage, n, m, d, k):
+    X = synth.iid_normal(n, d, 3000 + n)
+    Q = synth.iid_normal(m, d, 4000 + m)
+    ids, dist = run_bf(Q, X, k, "l2", LP[storage])
+    o_ids, o_rho = oracle.bf(Q, X, k, "l2")
+    check_knn(Q, X, ids, dist, o_ids, o_rho)
+
+
+def test_bf_tc_subspace_workload():
+    mod = synth.SubspaceModel(d=64, k=8, noise_var=0.01, seed=0)
+    X = mod.sample(200000, 0)
+    Q = mod.sample(1000, 1)
+    for k in (1, 10):
+        ids, dist = run_bf(Q, X, k, "l2", rbc.BF16)
+        st = rbc.last_stats()
+        o_ids, o_rho = oracle.bf(Q, X, k, "l2")
+        check_knn(Q, X, ids, dist, o_ids, o_rho)
+        assert st["uncertified"] <= 0.05 * len(Q), st
+
+
+def test_bf_tc_duplicates_and_ties():
+    base = synth.iid_normal(40, 6, 3)
+    X = np.concatenate([base, base, base[:10], np.zeros((30, 6), np.float32)])
+    Q = np.concatenate([base[:20], np.zeros((3, 6), np.float32), synth.iid_normal(20, 6, 4)])
+    ids, dist = run_bf(Q, X, 6, "l2", rbc.BF16)
+    o_ids, o_rho = oracle.bf(Q, X, 6, "l2")
+    np.testing.assert_array_equal(ids, o_ids)
+
+
+def test_bf_tc_k_exceeds_n_and_empty():
+    X = synth.iid_normal(5, 8, 1)
+    Q = synth.iid_normal(9, 8, 2)
+    ids, dist = run_bf(Q, X, 8, "l2", rbc.BF16)
+    o_ids, o_rho = oracle.bf(Q, X, 8, "l2")
+    check_knn(Q, X, ids, dist, o_ids, o_rho)
+    ids, dist = run_bf(np.zeros((0, 8), np.float32), X, 2, "l2", rbc.BF16)
+    assert ids.shape == (0, 2)

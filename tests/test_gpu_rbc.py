@@ -115,3 +115,47 @@ def test_empty_query_batch():
     idx = build(X, 22)
     ids, dist = search(idx, np.zeros((0, 4), np.float32), 2)
     assert ids.shape == (0, 2)
+
+
+# ---- low-precision storage: tensor-core stage two, certified re-rank ----
+
+@pytest.mark.parametrize("storage", [rbc.BF16, rbc.F16])
+@pytest.mark.parametrize("k", [1, 10])
+def test_exact_search_tc_iid_n16k_d16(storage, k):
+    X, Q = synth.make_workload("iid-n16k-d16", seed=0)
+    idx = build(X, 128, storage=storage)
+    ids, dist = search(idx, Q, k)
+    o_ids, o_rho = oracle.bf(Q, X, k, "l2")
+    check_knn(Q, X, ids, dist, o_ids, o_rho)
+
+
+@pytest.mark.parametrize("n,m,d,n_r,k", [(5000, 300, 5, 71, 3), (2049, 129, 33, 1, 2), (3001, 77, 12, 3001, 4), (20000, 513, 100, 141, 7), (1000, 1, 64, 30, 31)])
+def test_exact_search_tc_ragged(n, m, d, n_r, k):
+    X = synth.iid_normal(n, d, 10 + n)
+    Q = synth.iid_normal(m, d, 20 + m)
+    idx = build(X, n_r, seed=n_r, storage=rbc.BF16)
+    ids, dist = search(idx, Q, k)
+    o_ids, o_rho = oracle.bf(Q, X, k, "l2")
+    check_knn(Q, X, ids, dist, o_ids, o_rho)
+
+
+def test_exact_search_tc_subspace_workload_small():
+    mod = synth.SubspaceModel(d=64, k=8, noise_var=0.01, seed=0)
+    X = mod.sample(60000, 0)
+    Q = mod.sample(700, 1)
+    idx = build(X, 245, storage=rbc.BF16)
+    for k in (1, 10):
+        ids, dist = search(idx, Q, k)
+        o_ids, o_rho = oracle.bf(Q, X, k, "l2")
+        check_knn(Q, X, ids, dist, o_ids, o_rho)
+
+
+def test_exact_search_tc_duplicates():
+    base = synth.iid_normal(60, 4, 30)
+    X = np.concatenate([base, base, base[:25], base[:5]])
+    Q = np.concatenate([base[:15], synth.iid_normal(40, 4, 31)])
+    for n_r in (1, 9, 60, len(X)):
+        idx = build(X, n_r, seed=n_r, storage=rbc.BF16)
+        ids, dist = search(idx, Q, 5)
+        o_ids, o_rho = oracle.bf(Q, X, 5, "l2")
+        np.testing.assert_array_equal(ids, o_ids)
