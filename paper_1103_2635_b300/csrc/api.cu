@@ -367,11 +367,8 @@ int choose_c(int k, bool lp, int rerank_c) {
   return std::min(c, MAX_C);
 }
 
-int lp_width(int c) {
-  for (int w : {8, 16, 32})
-    if (w >= c) return w;
-  return -1;
-}
+// candidates kept per (row, half) by the tensor-core kernel
+int lp_width(int c) { return c <= 16 ? 16 : 32; }
 
 // ---------------------------------------------------------------------------
 // database views for the BF core

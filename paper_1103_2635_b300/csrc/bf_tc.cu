@@ -157,22 +157,30 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// 32 lanes x 32 consecutive 32-bit columns -> 32 registers per thread
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+// Wide tensor-memory loads: 32 lanes x N consecutive 32-bit columns, N registers
+// per thread; tcgen05.wait::ld must follow before the registers are used.
+__device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-      "%30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld_x64(uint32_t taddr, uint32_t (&r)[64]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void tmem_load_cols(uint32_t taddr, float (&v)[N]) {
+  uint32_t r[N];
+  if constexpr (N == 64) tmem_ld_x64(taddr, r);
+  else tmem_ld_x32(taddr, r);
+  tmem_wait_ld();
 #pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+  for (int j = 0; j < N; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 // (d0, d1) = (a0, a1) * (b, b) + (c0, c1) as one packed FP32 instruction
@@ -240,46 +248,92 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 // a multiple of 4 so that the tile's norms (BN floats) can be fetched with
 // one 16-byte-aligned bulk copy; the columns before the segment start and
 // past its end are masked to +inf in the epilogue.
-template <int C, int KB, int BN, int S, int QCAP>
+// Each (row, half) keeps C candidates (C = 16 or 32).
+
+// Order-preserving map of a float to an unsigned int (negative values
+// reversed), so (score, column) pairs compare as one 64-bit integer.
+__device__ __forceinline__ uint32_t f2o(float f) {
+  uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float o2f(uint32_t o) {
+  return (o & 0x80000000u) ? __uint_as_float(o & 0x7fffffffu) : __uint_as_float(~o);
+}
+
+// Max-heap of C (score, column) keys, one per epilogue thread, element j of
+// thread t at h[j * NT] (consecutive threads use consecutive banks).
+// Replaces the root (the current C-th best) by `key` and sifts it down.
+template <int C, int NT>
+__device__ __forceinline__ void heap_replace_root(uint64_t* h, uint64_t key) {
+  int pos = 0;
+#pragma unroll 1
+  while (true) {
+    const int l = 2 * pos + 1;
+    if (l >= C) break;
+    int c = l;
+    uint64_t kc = h[l * NT];
+    if (l + 1 < C) {
+      const uint64_t kr = h[(l + 1) * NT];
+      if (kr > kc) {
+        c = l + 1;
+        kc = kr;
+      }
+    }
+    if (kc <= key) break;
+    h[pos * NT] = kc;
+    pos = c;
+  }
+  h[pos * NT] = key;
+}
+
+template <int C, int KB, int BN, int S, int NR>
 struct TcSmem {
   static constexpr int Q_BYTES = KB * BM * 128;  // query tile, KB K-blocks of 64 elements
   static constexpr int X_STAGE = KB * BN * 128;  // one database tile
   static constexpr int NORM_STAGE = BN * 4;
-  static constexpr int NEPI_THREADS = NUM_THREADS - EPI_WARP0 * 32;
+  static constexpr int NEPI_WARPS = NUM_THREADS / 32 - EPI_WARP0;
   static constexpr int OFF_Q = 0;
   static constexpr int OFF_X = OFF_Q + Q_BYTES;
   static constexpr int OFF_NORM = OFF_X + S * X_STAGE;
-  static constexpr int OFF_QS = OFF_NORM + S * NORM_STAGE;         // hit queues: scores
-  static constexpr int OFF_QI = OFF_QS + QCAP * NEPI_THREADS * 4;  // hit queues: columns
-  static constexpr int OFF_BAR = OFF_QI + QCAP * NEPI_THREADS * 4;
-  // barriers: full[S], empty[S], tfull[2], tempty[2], qfull, qempty
-  static constexpr int NBAR = 2 * S + 6;
+  static constexpr int NEPI_THREADS = NEPI_WARPS * 32;
+  // per epilogue thread: a max-heap of LIST u64 keys, element j at [j][thread]
+  static constexpr int OFF_HEAP = OFF_NORM + NR * NORM_STAGE;
+  // per epilogue thread: one spilled 32-column chunk
+  static constexpr int OFF_SCR = OFF_HEAP + C * NEPI_THREADS * 8;
+  static constexpr int OFF_BAR = OFF_SCR + NEPI_WARPS * 32 * 32 * 4;
+  // barriers: full[S], empty[S], nfull[NR], nempty[NR], tfull[2], tempty[2], qfull, qempty
+  static constexpr int NBAR = 2 * S + 2 * NR + 6;
   static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;  // tmem base, abort flag
   static constexpr int BYTES = OFF_MISC + 16;
   static constexpr int ALLOC = BYTES + 1024;  // slack for 1024-byte alignment
   static_assert(ALLOC <= 232448, "shared memory budget");
 };
 
-template <int C, int KB, int BN, int S, int QCAP>
+// 10 warps: one SM sub-partition hosts three of them, so its 16K-register
+// slice caps a thread at 168 registers (enforced by the launch bound).
+template <int C, int KB, int BN, int S, int NRING>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap xmap,
              TcParams p, uint32_t idesc) {
-  using L = TcSmem<C, KB, BN, S, QCAP>;
+  using L = TcSmem<C, KB, BN, S, NRING>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
   uint8_t* sQ = smem + L::OFF_Q;
   uint8_t* sX = smem + L::OFF_X;
   float* sNorm = reinterpret_cast<float*>(smem + L::OFF_NORM);
-  float* sQs = reinterpret_cast<float*>(smem + L::OFF_QS);
-  int* sQi = reinterpret_cast<int*>(smem + L::OFF_QI);
+  uint64_t* sHeap = reinterpret_cast<uint64_t*>(smem + L::OFF_HEAP);
+  float* sScr = reinterpret_cast<float*>(smem + L::OFF_SCR);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
+  constexpr int NR = NRING;
   uint64_t* full = bars;
   uint64_t* empty = bars + S;
-  uint64_t* tfull = bars + 2 * S;
-  uint64_t* tempty = bars + 2 * S + 2;
-  uint64_t* qfull = bars + 2 * S + 4;
-  uint64_t* qempty = bars + 2 * S + 5;
+  uint64_t* nfull = bars + 2 * S;
+  uint64_t* nempty = bars + 2 * S + NR;
+  uint64_t* tfull = bars + 2 * S + 2 * NR;
+  uint64_t* tempty = bars + 2 * S + 2 * NR + 2;
+  uint64_t* qfull = bars + 2 * S + 2 * NR + 4;
+  uint64_t* qempty = bars + 2 * S + 2 * NR + 5;
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(smem + L::OFF_MISC);
   volatile int* sAbort = reinterpret_cast<volatile int*>(smem + L::OFF_MISC + 4);
 
@@ -290,7 +344,11 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1 + NEPI);
+      mbar_init(&empty[s], 1);
+    }
+    for (int r = 0; r < NR; ++r) {
+      mbar_init(&nfull[r], 1);
+      mbar_init(&nempty[r], NEPI);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -338,16 +396,21 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
         for (int x = sg.x_begin & ~3; x < sg.x_end; x += BN, ++it) {
           const int s = it % S;
           const uint32_t ph = (it / S) & 1;
-          if (!__all_sync(0xffffffffu, mbar_wait(&empty[s], ph ^ 1, sAbort, p.dev_err))) {
+          const int r = it % NR;
+          const uint32_t nph = (it / NR) & 1;
+          bool got = mbar_wait(&empty[s], ph ^ 1, sAbort, p.dev_err) &&
+                     mbar_wait(&nempty[r], nph ^ 1, sAbort, p.dev_err);
+          if (!__all_sync(0xffffffffu, got)) {
             ok = false;
             break;
           }
           if (lane == 0) {
-            mbar_arrive_expect_tx(&full[s], L::X_STAGE + L::NORM_STAGE);
+            mbar_arrive_expect_tx(&full[s], L::X_STAGE);
 #pragma unroll
             for (int kb = 0; kb < KB; ++kb)
               tma_load_2d(sX + s * L::X_STAGE + kb * BN * 128, &xmap, &full[s], kb * 64, x);
-            bulk_load(sNorm + s * BN, p.xnorm + x, L::NORM_STAGE, &full[s]);
+            mbar_arrive_expect_tx(&nfull[r], L::NORM_STAGE);
+            bulk_load(sNorm + r * BN, p.xnorm + x, L::NORM_STAGE, &nfull[r]);
           }
           __syncwarp();
         }
@@ -357,6 +420,8 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
     if (lane == 0) {
       for (uint32_t j = (it > (uint32_t)S ? it - S : 0); j < it; ++j)
         mbar_wait(&full[j % S], (j / S) & 1, sAbort, p.dev_err);
+      for (uint32_t j = (it > (uint32_t)NR ? it - NR : 0); j < it; ++j)
+        mbar_wait(&nfull[j % NR], (j / NR) & 1, sAbort, p.dev_err);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -406,118 +471,121 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
     }
   } else {
     // ---------------- epilogue ----------------
-    // thread = one query row (TMEM lane) x one half of each tile's columns.
-    // Hits (score below the row's current C-th best) are queued in shared
-    // memory; when any lane's queue might overflow, the whole warp merges its
-    // queues into the register lists in lock-step, so the O(C) insertions of
-    // different lanes share issue slots instead of serialising.
+    // Lane l of warp w owns query row 32*(w%4) + l (its TMEM lane) for one
+    // half of each tile's columns.  Each thread keeps the C best
+    // (score, column) keys of its row in a max-heap in shared memory; the
+    // heap root is the threshold tau.  A 32-column chunk whose minimum is not
+    // below tau costs only the scores and the minimum.  Otherwise the thread
+    // spills the chunk to its scratch row, builds the bit mask of the columns
+    // below tau and pushes only those; hitting lanes run the same loop
+    // iterations, so their O(log C) sift-downs overlap.
     const int quarter = warp & 3;
     const int half = (warp - EPI_WARP0) / 4;
     const int row = quarter * 32 + lane;
     const int et = threadIdx.x - EPI_WARP0 * 32;  // epilogue thread index
-    float* qs = sQs + et;
-    int* qix = sQi + et;
-    constexpr int HALF = BN / 2;
     constexpr int NT = L::NEPI_THREADS;
+    uint64_t* heap = sHeap + et;
+    float* scr = sScr + et * 32;
+    constexpr int HALF = BN / 2;
+    constexpr uint64_t EMPTY_KEY = 0xFF800000FFFFFFFFull;  // (+inf, no column)
     uint32_t it = 0;
     bool ok = true;
     for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
       int q0, nq, sb, se, slot;
       item_info(w, item, q0, nq, sb, se, slot);
-      TopList<C> top;
-      top.init();
+#pragma unroll 4
+      for (int j = 0; j < C; ++j) heap[j * NT] = EMPTY_KEY;
       float tau = INFINITY;
-      int qcnt = 0;
-      auto merge = [&]() {
-        const int qmax = __reduce_max_sync(0xffffffffu, qcnt);
-#pragma unroll 1
-        for (int e = 0; e < qmax; ++e) {
-          if (e < qcnt) {
-            float vv = qs[e * NT];
-            int ii = qix[e * NT];
-            if (top.admits(vv, ii)) top.insert(vv, ii);
-          }
-        }
-        qcnt = 0;
-        tau = top.worst();
-        __syncwarp();
-      };
       for (int si = sb; ok && si < se; ++si) {
         const Seg sg = seg_at(w, si);
         for (int x = sg.x_begin & ~3; x < sg.x_end; x += BN, ++it) {
-          const int s = it % S;
-          const uint32_t ph = (it / S) & 1;
+          const int r = it % NR;
+          const uint32_t nph = (it / NR) & 1;
           const int buf = it & 1;
           const uint32_t aph = (it >> 1) & 1;
-          bool got = mbar_wait(&full[s], ph, sAbort, p.dev_err) &&
+          bool got = mbar_wait(&nfull[r], nph, sAbort, p.dev_err) &&
                      mbar_wait(&tfull[buf], aph, sAbort, p.dev_err);
           if (!__all_sync(0xffffffffu, got)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const float* nrm = sNorm + s * BN + half * HALF;
+          const float* nrm = sNorm + r * BN + half * HALF;
           const int lo = sg.x_begin - x - half * HALF;  // first valid column of this half
           const int hi = sg.x_end - x - half * HALF;    // one past the last valid column
           const bool partial = lo > 0 || hi < HALF;
           const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + buf * BN + half * HALF;
 #pragma unroll 1
-          for (int ch = 0; ch < HALF / 32; ++ch) {
-            float v[32];
-            tmem_ld32(tbase + ch * 32, v);
-            const float4* n4 = reinterpret_cast<const float4*>(nrm + ch * 32);
+          for (int c0 = 0; c0 < HALF; c0 += 32) {
+            float u[32];
+            tmem_load_cols<32>(tbase + c0, u);
+            if (c0 + 32 == HALF) {
+              // the whole half is in registers: hand the accumulator back
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&tempty[buf]);
+            }
+            const float4* n4 = reinterpret_cast<const float4*>(nrm + c0);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               float4 nn = n4[j];
-              fma2(v[4 * j], v[4 * j + 1], v[4 * j], v[4 * j + 1], -2.0f, nn.x, nn.y);
-              fma2(v[4 * j + 2], v[4 * j + 3], v[4 * j + 2], v[4 * j + 3], -2.0f, nn.z, nn.w);
+              fma2(u[4 * j], u[4 * j + 1], u[4 * j], u[4 * j + 1], -2.0f, nn.x, nn.y);
+              fma2(u[4 * j + 2], u[4 * j + 3], u[4 * j + 2], u[4 * j + 3], -2.0f, nn.z, nn.w);
             }
             if (partial) {
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
-                int c = ch * 32 + j;
-                if (c < lo || c >= hi) v[j] = INFINITY;
+                int c = c0 + j;
+                if (c < lo || c >= hi) u[j] = INFINITY;
               }
             }
-            float ma = min3f(v[0], v[1], v[2]);
-            float mb = min3f(v[3], v[4], v[5]);
+            float ma = min3f(u[0], u[1], u[2]);
+            float mb = min3f(u[3], u[4], u[5]);
 #pragma unroll
             for (int j = 6; j < 30; j += 4) {
-              ma = min3f(ma, v[j], v[j + 1]);
-              mb = min3f(mb, v[j + 2], v[j + 3]);
+              ma = min3f(ma, u[j], u[j + 1]);
+              mb = min3f(mb, u[j + 2], u[j + 3]);
             }
-            const float mn = min3f(ma, mb, fminf(v[30], v[31]));
-            const bool hit = mn < tau;
-            if (__any_sync(0xffffffffu, hit)) {
-              if (__any_sync(0xffffffffu, qcnt > QCAP - 32)) merge();
-              if (hit) {
-                const int cb = x + half * HALF + ch * 32;
+            const float mn = min3f(ma, mb, fminf(u[30], u[31]));
+            if (mn < tau) {
+              // 16-byte slots rotated by lane so that 8 lanes hit 8 bank groups
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                  if (v[j] < tau) {
-                    qs[qcnt * NT] = v[j];
-                    qix[qcnt * NT] = cb + j;
-                    ++qcnt;
-                  }
+              for (int j = 0; j < 32; j += 4)
+                *reinterpret_cast<float4*>(scr + ((((j >> 2) ^ lane) & 7) << 2)) =
+                    make_float4(u[j], u[j + 1], u[j + 2], u[j + 3]);
+              // hit mask, combined as a tree of 4-bit groups
+              uint32_t g[8];
+#pragma unroll
+              for (int q = 0; q < 8; ++q)
+                g[q] = (u[4 * q] < tau ? 1u : 0u) | (u[4 * q + 1] < tau ? 2u : 0u) |
+                       (u[4 * q + 2] < tau ? 4u : 0u) | (u[4 * q + 3] < tau ? 8u : 0u);
+              uint32_t mask = (g[0] | (g[1] << 4) | (g[2] << 8) | (g[3] << 12)) |
+                              ((g[4] | (g[5] << 4) | (g[6] << 8) | (g[7] << 12)) << 16);
+              const int cb = x + half * HALF + c0;
+              while (mask) {
+                const int j = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const float sv = scr[((((j >> 2) ^ lane) & 7) << 2) | (j & 3)];
+                if (sv < tau) {
+                  heap_replace_root<C, NT>(heap, ((uint64_t)f2o(sv) << 32) | (uint32_t)(cb + j));
+                  tau = o2f((uint32_t)(heap[0] >> 32));
                 }
               }
             }
+            __syncwarp();
           }
-          tc_fence_before();
           __syncwarp();
-          if (lane == 0) {
-            mbar_arrive(&tempty[buf]);
-            mbar_arrive(&empty[s]);
-          }
+          if (lane == 0) mbar_arrive(&nempty[r]);
         }
       }
-      merge();
       if (ok && row < nq) {
         int64_t base = (((int64_t)slot * TQ + row) * 2 + half) * C;
-#pragma unroll
+#pragma unroll 4
         for (int j = 0; j < C; ++j) {
-          p.out.score[base + j] = top.s[j];
-          p.out.idx[base + j] = top.s[j] == INFINITY ? -1 : top.i[j];
+          const uint64_t key = heap[j * NT];
+          const float sc = o2f((uint32_t)(key >> 32));
+          p.out.score[base + j] = sc;
+          p.out.idx[base + j] = sc == INFINITY ? -1 : (int)(uint32_t)key;
         }
       }
     }
@@ -572,34 +640,30 @@ int encode_map(CUtensorMap* map, const void* base, int64_t rows, int dpad, int s
   return RBC_OK;
 }
 
-template <int C, int KB, int BN, int S, int QCAP>
+template <int C, int KB, int BN, int S, int NR>
 int launch_tc(const LpMatrix& Qm, const LpMatrix& Xm, const TileWork& w, const TopOut& out,
               int grid, cudaStream_t st, uint32_t* dev_err) {
-  using L = TcSmem<C, KB, BN, S, QCAP>;
+  using L = TcSmem<C, KB, BN, S, NR>;
   CUtensorMap qmap, xmap;
   RBC_TRY_TC(encode_map(&qmap, Qm.data, Qm.rows, Qm.dpad, Qm.storage, BM));
   RBC_TRY_TC(encode_map(&xmap, Xm.data, Xm.rows, Xm.dpad, Xm.storage, BN));
-  auto kern = bf_tc_kernel<C, KB, BN, S, QCAP>;
+  auto kern = bf_tc_kernel<C, KB, BN, S, NR>;
   RBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC));
   TcParams p{w, out, Xm.norm, Xm.rows, (int)Qm.rows, dev_err};
   uint32_t idesc = idesc_f16(Qm.storage == RBC_BF16 ? 1 : 0, BM, BN);
   kern<<<grid, NUM_THREADS, L::ALLOC, st>>>(qmap, xmap, p, idesc);
-  RBC_LAUNCH_CHECK("bf_tc_kernel");
-  return RBC_OK;
-}
-
-template <int C>
-int dispatch_kb(const LpMatrix& Qm, const LpMatrix& Xm, const TileWork& w, const TopOut& out,
-                int grid, cudaStream_t st, uint32_t* dev_err) {
-  switch (Qm.dpad / 64) {
-    case 1: return launch_tc<C, 1, 256, 3, 40>(Qm, Xm, w, out, grid, st, dev_err);
-    case 2: return launch_tc<C, 2, 128, 3, 40>(Qm, Xm, w, out, grid, st, dev_err);
-    case 3: return launch_tc<C, 3, 64, 3, 40>(Qm, Xm, w, out, grid, st, dev_err);
-    case 4: return launch_tc<C, 4, 64, 2, 40>(Qm, Xm, w, out, grid, st, dev_err);
-    default:
-      set_error("tensor-core BF: padded dimension %d unsupported", Qm.dpad);
-      return RBC_ERR_UNSUPPORTED;
+  ++t_launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, kern);
+    set_error("bf_tc_kernel<C=%d,KB=%d,BN=%d,S=%d> launch failed: %s (regs %d, max threads "
+              "%d, static smem %zu, local %zu, dynamic smem %d)",
+              C, KB, BN, S, cudaGetErrorString(e), fa.numRegs, fa.maxThreadsPerBlock,
+              fa.sharedSizeBytes, fa.localSizeBytes, L::ALLOC);
+    return RBC_ERR_CUDA;
   }
+  return RBC_OK;
 }
 
 }  // namespace
@@ -622,14 +686,28 @@ int launch_bf_tc_topc(const LpMatrix& Qm, const LpMatrix& Xm, int C, const TileW
     set_error("tensor-core BF: operand layouts differ");
     return RBC_ERR_ARG;
   }
-  switch (C) {
-    case 8: return dispatch_kb<8>(Qm, Xm, w, out, grid, st, dev_err);
-    case 16: return dispatch_kb<16>(Qm, Xm, w, out, grid, st, dev_err);
-    case 32: return dispatch_kb<32>(Qm, Xm, w, out, grid, st, dev_err);
-    default:
-      set_error("tensor-core BF: list width %d unsupported", C);
-      return RBC_ERR_UNSUPPORTED;
+  if (C == 16) {
+    switch (Qm.dpad / 64) {
+      case 1: return launch_tc<16, 1, 256, 4, 8>(Qm, Xm, w, out, grid, st, dev_err);
+      case 2: return launch_tc<16, 2, 128, 3, 8>(Qm, Xm, w, out, grid, st, dev_err);
+      case 3: return launch_tc<16, 3, 64, 3, 8>(Qm, Xm, w, out, grid, st, dev_err);
+      case 4: return launch_tc<16, 4, 64, 2, 4>(Qm, Xm, w, out, grid, st, dev_err);
+      default: break;
+    }
+  } else if (C == 32) {
+    switch (Qm.dpad / 64) {
+      case 1: return launch_tc<32, 1, 256, 3, 8>(Qm, Xm, w, out, grid, st, dev_err);
+      case 2: return launch_tc<32, 2, 128, 2, 8>(Qm, Xm, w, out, grid, st, dev_err);
+      case 3: return launch_tc<32, 3, 64, 3, 8>(Qm, Xm, w, out, grid, st, dev_err);
+      case 4: return launch_tc<32, 4, 64, 2, 2>(Qm, Xm, w, out, grid, st, dev_err);
+      default: break;
+    }
+  } else {
+    set_error("tensor-core BF: list width %d unsupported (16 or 32)", C);
+    return RBC_ERR_ARG;
   }
+  set_error("tensor-core BF: padded dimension %d unsupported", Qm.dpad);
+  return RBC_ERR_UNSUPPORTED;
 }
 
 }  // namespace rbc
