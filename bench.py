@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=1000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=200)
+    ap.add_argument("--legs", default="all", choices=["all", "search"],
+                    help="search: only the timed exact-search steps (for profiler launch lists)")
+    ap.add_argument("--n", type=int, default=None, help="override the database size")
+    ap.add_argument("--m", type=int, default=None, help="override the query batch size")
     return ap.parse_args()
 
 
@@ -120,9 +124,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def workload_arrays(name: str, seed: int, m: int | None = None, query_seed: int | None = None):
+def workload_arrays(name: str, seed: int, m: int | None = None, query_seed: int | None = None,
+                    n: int | None = None):
     w = synth.WORKLOADS[name]
-    X, Q = synth.make_workload(w, seed=seed, m=m, query_seed=query_seed)
+    X, Q = synth.make_workload(w, seed=seed, n=n, m=m, query_seed=query_seed)
     return w, X, Q
 
 
@@ -181,7 +186,7 @@ def run_ours(args, rank, world, local):
         dist.init_process_group("nccl", device_id=dev)
     storage = {"bf16": rbc.BF16, "f16": rbc.F16, "f32": rbc.F32}[args.storage]
     # each rank holds its own replica and its own query batch (weak scaling)
-    w, X, Q = workload_arrays(args.workload, 0, query_seed=1 + 1000 * rank)
+    w, X, Q = workload_arrays(args.workload, 0, query_seed=1 + 1000 * rank, n=args.n, m=args.m)
     Xd = torch.from_numpy(X).to(dev)
     Qd = torch.from_numpy(Q).to(dev)
     m, d, k = Q.shape[0], Q.shape[1], args.k
@@ -233,6 +238,12 @@ def run_ours(args, rank, world, local):
         elapsed_ms = float(t.item())
     stats = rbc.last_stats()
     qps = world * m * args.steps / (elapsed_ms / 1000.0)
+    if args.legs == "search":
+        if rank == 0:
+            print(json.dumps({"legs": "search", "value": qps, "unit": "queries/s",
+                              "ms_per_step": elapsed_ms / args.steps, "n": len(X), "m": m, "k": k,
+                              "gpu_launches": launches}), flush=True)
+        return
 
     # ---- phase timing (separate pass: events around each phase) ----
     rbc.set_timing(True)

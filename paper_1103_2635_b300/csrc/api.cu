@@ -410,7 +410,7 @@ int bf_dense_f32(const float* Qdev, int64_t m, const DbView& db, int d, int k, i
   w.dense_chunk = chunk;
   int grid = (int)std::min<int64_t>(items, (int64_t)sms * 2 * 16);
   tmark(1, st);
-  RBC_TRY(launch_bf_simt_topc(Qdev, db.X32, d, metric, C, w, TopOut{ps, pi}, grid, st));
+  RBC_TRY(launch_bf_simt_topc(Qdev, db.X32, d, metric, C, w, TopOut{ps, pi, nullptr}, grid, st));
   tmark(2, st);
   SelectArgs a{};
   a.part_score = ps;
@@ -472,7 +472,8 @@ int lp_queries(const float* Qdev, int64_t m, int d, int dpad, int storage, LpQue
 
 // Select (merge + re-rank + certification) for the low-precision pass, then
 // the FP32 re-search of uncertified rows (one host read of their count).
-int select_lp_and_fallback(const float* ps, const int* pi, int C, const int* tile_slot_off,
+int select_lp_and_fallback(const float* ps, const int* pi, const int* pv, int C,
+                           const int* tile_slot_off,
                            int dense_splits, int64_t m, const float* Qbuf, const LpQueries& ql,
                            const DbView& db, int d, int k, int c_out, const int* qorig,
                            int64_t* out_ids, float* out_dist, int* cnt, Arena& ar,
@@ -482,6 +483,7 @@ int select_lp_and_fallback(const float* ps, const int* pi, int C, const int* til
   SelectArgs a{};
   a.part_score = ps;
   a.part_idx = pi;
+  a.slot_valid = pv;
   a.C = C;
   a.nsub = 2;
   a.tile_slot_off = tile_slot_off;
@@ -529,16 +531,18 @@ int bf_dense_lp(const float* Qdev, int64_t m, const DbView& db, int d, int k, in
   tmark(1, st);
   const int64_t tiles = (m + TQ - 1) / TQ;
   const int sms = sm_count();
-  int64_t splits = (4LL * sms + tiles - 1) / tiles;
-  splits = std::max<int64_t>(1, std::min<int64_t>(splits, std::max<int64_t>(1, db.rows / 2048)));
+  int64_t splits = (16LL * sms + tiles - 1) / tiles;
+  splits = std::max<int64_t>(1, std::min<int64_t>(splits, std::max<int64_t>(1, db.rows / 8192)));
   int64_t chunk = (db.rows + splits - 1) / splits;
   chunk = (chunk + 255) / 256 * 256;
   splits = (db.rows + chunk - 1) / chunk;
   const int64_t items = tiles * splits;
   float* ps;
   int* pi;
+  int* pv;
   RBC_TRY(ar.alloc(&ps, items * TQ * 2 * C));
   RBC_TRY(ar.alloc(&pi, items * TQ * 2 * C));
+  RBC_TRY(ar.alloc(&pv, items));
   TileWork w{};
   w.num_items = (int)items;
   w.m = m;
@@ -551,9 +555,9 @@ int bf_dense_lp(const float* Qdev, int64_t m, const DbView& db, int d, int k, in
   RBC_TRY(ar.alloc(&dev_err, 1));
   RBC_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(uint32_t), st));
   int grid = (int)std::min<int64_t>(items, (int64_t)sms);
-  RBC_TRY(launch_bf_tc_topc(Qm, Xm, C, w, TopOut{ps, pi}, grid, st, dev_err));
-  RBC_TRY(select_lp_and_fallback(ps, pi, C, nullptr, (int)splits, m, Qdev, ql, db, d, k, c_out,
-                                 nullptr, out_ids, out_dist, cnt, ar, st));
+  RBC_TRY(launch_bf_tc_topc(Qm, Xm, C, w, TopOut{ps, pi, pv}, grid, st, dev_err));
+  RBC_TRY(select_lp_and_fallback(ps, pi, pv, C, nullptr, (int)splits, m, Qdev, ql, db, d, k,
+                                 c_out, nullptr, out_ids, out_dist, cnt, ar, st));
   taccumulate();
   uint32_t herr = 0;
   RBC_CUDA(cudaMemcpyAsync(&herr, dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -724,7 +728,7 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
     RBC_TRY(ar.alloc(&ps, cap_items * TQ * 2 * C));
     RBC_TRY(ar.alloc(&pi, cap_items * TQ * 2 * C));
     tmark(1, st);
-    RBC_TRY(launch_bf_simt_topc(Qp, ix->X32, d, metric, C, w2, TopOut{ps, pi},
+    RBC_TRY(launch_bf_simt_topc(Qp, ix->X32, d, metric, C, w2, TopOut{ps, pi, nullptr},
                                 (int)std::min<int64_t>(cap_items, (int64_t)sms * 2 * 8), st));
     tmark(2, st);
     SelectArgs a{};
@@ -756,14 +760,16 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
     RBC_TRY(lp_queries(Qp, mb, d, ix->dpad, ix->storage, ql, ar, st));
     float* ps;
     int* pi;
+    int* pv;
     RBC_TRY(ar.alloc(&ps, cap_items * TQ * 2 * C));
     RBC_TRY(ar.alloc(&pi, cap_items * TQ * 2 * C));
+    RBC_TRY(ar.alloc(&pv, cap_items));
     LpMatrix Qm{ql.lp, ql.norm, mb, ix->dpad, ix->storage};
     LpMatrix Xm{ix->Xlp, ix->xnorm, n, ix->dpad, ix->storage};
     tmark(1, st);
-    RBC_TRY(launch_bf_tc_topc(Qm, Xm, C, w2, TopOut{ps, pi}, sms, st, dev_err));
-    RBC_TRY(select_lp_and_fallback(ps, pi, C, toff, 0, mb, Qp, ql, db, d, k, c_out, qperm, ids,
-                                   dist, cn.c, ar, st));
+    RBC_TRY(launch_bf_tc_topc(Qm, Xm, C, w2, TopOut{ps, pi, pv}, sms, st, dev_err));
+    RBC_TRY(select_lp_and_fallback(ps, pi, pv, C, toff, 0, mb, Qp, ql, db, d, k, c_out, qperm,
+                                   ids, dist, cn.c, ar, st));
   }
   uint32_t herr = 0;
   RBC_CUDA(cudaMemcpyAsync(&herr, dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));

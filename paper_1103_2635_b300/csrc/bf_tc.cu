@@ -374,12 +374,16 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
 
   const TileWork& w = p.w;
   const int n_items = w.num_items_dev ? *w.num_items_dev : w.num_items;
+  // a contiguous range of items per CTA, so that consecutive items of one
+  // query tile stay on one CTA and the epilogue can carry its lists across them
+  const int ib = (int)((int64_t)blockIdx.x * n_items / gridDim.x);
+  const int ie = (int)((int64_t)(blockIdx.x + 1) * n_items / gridDim.x);
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     uint32_t it = 0, qi = 0;
     bool ok = true;
-    for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x, ++qi) {
+    for (int item = ib; ok && item < ie; ++item, ++qi) {
       int q0, nq, sb, se, slot;
       item_info(w, item, q0, nq, sb, se, slot);
       if (!__all_sync(0xffffffffu, mbar_wait(qempty, (qi & 1) ^ 1, sAbort, p.dev_err))) {
@@ -427,7 +431,7 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
     // ---------------- MMA issuer ----------------
     uint32_t it = 0, qi = 0;
     bool ok = true;
-    for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x, ++qi) {
+    for (int item = ib; ok && item < ie; ++item, ++qi) {
       int q0, nq, sb, se, slot;
       item_info(w, item, q0, nq, sb, se, slot);
       if (!__all_sync(0xffffffffu, mbar_wait(qfull, qi & 1, sAbort, p.dev_err))) {
@@ -490,12 +494,19 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
     constexpr uint64_t EMPTY_KEY = 0xFF800000FFFFFFFFull;  // (+inf, no column)
     uint32_t it = 0;
     bool ok = true;
-    for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
+    float tau = INFINITY;
+    for (int item = ib; ok && item < ie; ++item) {
       int q0, nq, sb, se, slot;
       item_info(w, item, q0, nq, sb, se, slot);
+      int pq0 = -1, pnq, psb, pse, pslot;
+      if (item > ib) item_info(w, item - 1, pq0, pnq, psb, pse, pslot);
+      int nq0 = -1, nnq, nsb, nse, nslot;
+      if (item + 1 < ie) item_info(w, item + 1, nq0, nnq, nsb, nse, nslot);
+      if (pq0 != q0) {  // first item of a run of the same query tile
 #pragma unroll 4
-      for (int j = 0; j < C; ++j) heap[j * NT] = EMPTY_KEY;
-      float tau = INFINITY;
+        for (int j = 0; j < C; ++j) heap[j * NT] = EMPTY_KEY;
+        tau = INFINITY;
+      }
       for (int si = sb; ok && si < se; ++si) {
         const Seg sg = seg_at(w, si);
         for (int x = sg.x_begin & ~3; x < sg.x_end; x += BN, ++it) {
@@ -578,7 +589,9 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
           if (lane == 0) mbar_arrive(&nempty[r]);
         }
       }
-      if (ok && row < nq) {
+      const bool carry = nq0 == q0;  // the next item continues this tile's lists
+      if (p.out.slot_valid && threadIdx.x == EPI_WARP0 * 32) p.out.slot_valid[slot] = carry ? 0 : 1;
+      if (ok && !carry && row < nq) {
         int64_t base = (((int64_t)slot * TQ + row) * 2 + half) * C;
 #pragma unroll 4
         for (int j = 0; j < C; ++j) {

@@ -27,6 +27,7 @@ struct TileWork {
 struct TopOut {
   float* score;
   int* idx;
+  int* slot_valid;  // optional: 0 marks a slot whose list was carried into a later slot
 };
 
 int simt_list_width(int c_needed);
@@ -52,6 +53,7 @@ int launch_bf_tc_topc(const LpMatrix& Qm, const LpMatrix& Xm, int C, const TileW
 struct SelectArgs {
   const float* part_score;
   const int* part_idx;
+  const int* slot_valid;     // optional: slots with 0 hold no list
   int C;       // entries per sub-list
   int nsub;    // sub-lists per (slot, row)
   const int* tile_slot_off;  // list form: slots of tile t are [off[t], off[t+1])

@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(WARPS * 32) select_kernel(SelectArgs a) {
   for (int e = lane; e < total; e += 32) {
     int s = sb + e / per_slot;
     int j = e - (e / per_slot) * per_slot;
+    if (a.slot_valid && !a.slot_valid[s]) continue;
     int64_t off = ((int64_t)s * TQ + r) * per_slot + j;
     int id = a.part_idx[off];
     float v = a.part_score[off];
