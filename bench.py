@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+METRIC = "exact k-NN queries/s (RBC BF16+rerank vs FP32 brute force), p50/p99 latency"
 FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
 
 
@@ -157,12 +158,14 @@ def run_reference(args, rank, world):
     qps = S * len(times) / total
     out = {
         "impl": "reference",
-        "metric": "exact k-NN queries/s", "value": qps, "unit": "queries/s", "n_gpus": world,
+        "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "n": w.n, "m": w.m, "d": w.d, "n_r": w.n_r, "k": args.k,
-                   "metric": "l2", "method": "exact RBC (oracle, FP64 CPU)"},
+                   "metric": "l2", "storage": args.storage, "noise_var": w.params.get("noise_var"),
+                   "intrinsic_dim": w.params.get("k"), "parallelism": "replicas1",
+                   "method": "exact RBC search, FP64 CPU oracle"},
         "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
                          "sample": f"{S} random queries of {w.m} per step, full {w.n}-point database"},
         "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -342,7 +345,7 @@ def run_ours(args, rank, world, local):
                                     "max_rel_dist_err": float(rel.max())}}
 
     out = {
-        "metric": "exact k-NN queries/s (RBC BF16+rerank vs FP32 brute force), p50/p99 latency",
+        "metric": METRIC,
         "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / args.steps, "latency": lat, "higher_is_better": True,
         "scaling": "weak",
