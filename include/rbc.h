@@ -154,6 +154,30 @@ int rbc_search(const rbc_index* idx, const float* Q, int64_t m, int32_t k, int64
 int bf_search(const float* Q, int64_t m, const float* X, int64_t n, int32_t d, int32_t k,
               int32_t metric, int32_t storage, int64_t* out_ids, float* out_dist, void* stream);
 
+/*
+ * bf_search_noalloc -- BF(Q, X) like bf_search with storage RBC_F32, for
+ *   callers that cannot allocate device memory (for example a serving engine
+ *   that has reserved the device memory budget for its own pool, or a
+ *   latency-critical path where an allocation, which may synchronise the
+ *   device or fail under memory pressure, is not acceptable).  The paper has
+ *   no counterpart: this is a deployment variant of the brute-force search.
+ *   It makes no allocation: its scratch is one static device array of 32 MiB
+ *   inside the library, held by every GPU that loads the library until the
+ *   process exits.  Q, X, out_ids and out_dist must be DEVICE pointers (host
+ *   buffers are rejected with RBC_ERR_ARG).  Limit: the per-query candidate
+ *   lists of all ceil(m / 128) query tiles must fit in the array, i.e.
+ *   ceil(m / 128) * 128 * 2 * C * 8 bytes <= 32 MiB - 256 with C the smallest
+ *   of 2, 4, 8, 16, 32 that is >= k + 1 (m <= 130,944 for 8 <= k <= 15,
+ *   m <= 65,408 for 16 <= k <= 31); a larger m returns RBC_ERR_UNSUPPORTED with
+ *   the limit in the message.  The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress, once per device, with that device current); make
+ *   that first call before any stream capture.  All calls share the array:
+ *   calls that overlap on the GPU race and must be serialised by the caller.
+ *   Results and errors otherwise as bf_search.
+ */
+int bf_search_noalloc(const float* Q, int64_t m, const float* X, int64_t n, int32_t d, int32_t k,
+                      int32_t metric, int64_t* out_ids, float* out_dist, void* stream);
+
 /* Index description. */
 typedef struct {
   int64_t n;

@@ -25,7 +25,7 @@ import numpy as np
 
 __all__ = [
     "L2", "L1", "EXACT", "ONESHOT", "F32", "BF16", "F16",
-    "RbcError", "bf_search", "rbc_build", "rbc_search", "rbc_sample_reps",
+    "RbcError", "bf_search", "bf_search_noalloc", "rbc_build", "rbc_search", "rbc_sample_reps",
     "RbcIndex", "last_stats", "set_timing", "library_path", "load",
 ]
 
@@ -83,6 +83,7 @@ def load():
     P, I64, I32, U64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
     lib.rbc_sample_reps.argtypes = [I64, I32, U64, P]
     lib.bf_search.argtypes = [P, I64, P, I64, I32, I32, I32, I32, P, P, P]
+    lib.bf_search_noalloc.argtypes = [P, I64, P, I64, I32, I32, I32, P, P, P]
     lib.rbc_build.argtypes = [P, I64, I32, I32, I32, I32, ctypes.POINTER(_Opts), P,
                               ctypes.POINTER(ctypes.c_void_p)]
     lib.rbc_search.argtypes = [P, P, I64, I32, P, P, P]
@@ -96,7 +97,7 @@ def load():
     lib.rbc_last_error.restype = ctypes.c_char_p
     lib.rbc_default_opts.argtypes = [ctypes.POINTER(_Opts)]
     lib.rbc_default_opts.restype = None
-    for f in ("rbc_sample_reps", "bf_search", "rbc_build", "rbc_search", "rbc_index_info",
+    for f in ("rbc_sample_reps", "bf_search", "bf_search_noalloc", "rbc_build", "rbc_search", "rbc_index_info",
               "rbc_index_export", "rbc_last_stats"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
@@ -169,6 +170,20 @@ def bf_search(Q, X, k: int, metric: int = L2, storage: int = F32, out_ids=None, 
     dp, _, ddev = _arg(out_dist, np.float32)
     st = _stream_of(stream, qdev or xdev or idev)
     _check(load().bf_search(qp, m, xp, n, d, k, metric, storage, ip, dp, st))
+    return out_ids, out_dist
+
+
+def bf_search_noalloc(Q, X, k: int, metric: int = L2, out_ids=None, out_dist=None, stream=None):
+    """BF(Q, X) in FP32 without any device allocation (library-owned static
+    scratch; device tensors only; calls must not overlap on the GPU)."""
+    qp, qk, qdev = _arg(Q, np.float32)
+    xp, xk, _ = _arg(X, np.float32)
+    m, d = qk.shape
+    out_ids, out_dist = _outputs(m, k, qk.device if qdev else None, out_ids, out_dist)
+    ip, _, _ = _arg(out_ids, np.int64)
+    dp, _, _ = _arg(out_dist, np.float32)
+    st = _stream_of(stream, qdev)
+    _check(load().bf_search_noalloc(qp, m, xp, xk.shape[0], d, k, metric, ip, dp, st))
     return out_ids, out_dist
 
 
