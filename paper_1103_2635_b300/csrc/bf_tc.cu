@@ -250,40 +250,53 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 // past its end are masked to +inf in the epilogue.
 // Each (row, half) keeps C candidates (C = 16 or 32).
 
-// Order-preserving map of a float to an unsigned int (negative values
-// reversed), so (score, column) pairs compare as one 64-bit integer.
-__device__ __forceinline__ uint32_t f2o(float f) {
-  uint32_t b = __float_as_uint(f);
-  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-__device__ __forceinline__ float o2f(uint32_t o) {
-  return (o & 0x80000000u) ? __uint_as_float(o & 0x7fffffffu) : __uint_as_float(~o);
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
 }
 
-// Max-heap of C (score, column) keys, one per epilogue thread, element j of
-// thread t at h[j * NT] (consecutive threads use consecutive banks).
-// Replaces the root (the current C-th best) by `key` and sifts it down.
-template <int C, int NT>
-__device__ __forceinline__ void heap_replace_root(uint64_t* h, uint64_t key) {
-  int pos = 0;
-#pragma unroll 1
-  while (true) {
-    const int l = 2 * pos + 1;
-    if (l >= C) break;
-    int c = l;
-    uint64_t kc = h[l * NT];
-    if (l + 1 < C) {
-      const uint64_t kr = h[(l + 1) * NT];
-      if (kr > kc) {
-        c = l + 1;
-        kc = kr;
-      }
-    }
-    if (kc <= key) break;
-    h[pos * NT] = kc;
-    pos = c;
+// Largest of C register values (C = 16 or 32): a tree of three-input maxima.
+template <int C>
+__device__ __forceinline__ float max_of(const float (&v)[C]) {
+  float m[C / 2];
+#pragma unroll
+  for (int j = 0; j < C / 2; ++j) m[j] = fmaxf(v[2 * j], v[2 * j + 1]);
+  // C/2 = 8 or 16 partial maxima
+  float a = max3f(m[0], m[1], m[2]);
+  float b = max3f(m[3], m[4], m[5]);
+  float c = fmaxf(m[6], m[7]);
+#pragma unroll
+  for (int j = 8; j < C / 2; j += 4) {
+    a = max3f(a, m[j], m[j + 1]);
+    b = max3f(b, m[j + 2], m[j + 3]);
   }
-  h[pos * NT] = key;
+  return max3f(a, b, c);
+}
+
+// Bit j set iff v[j] == x (C <= 32), OR-combined in groups of four.
+template <int C>
+__device__ __forceinline__ uint32_t eq_mask(const float (&v)[C], float x) {
+  uint32_t g[C / 4];
+#pragma unroll
+  for (int q = 0; q < C / 4; ++q)
+    g[q] = (v[4 * q] == x ? 1u : 0u) | (v[4 * q + 1] == x ? 2u : 0u) |
+           (v[4 * q + 2] == x ? 4u : 0u) | (v[4 * q + 3] == x ? 8u : 0u);
+  uint32_t m = 0;
+#pragma unroll
+  for (int q = 0; q < C / 4; ++q) m |= g[q] << (4 * q);
+  return m;
+}
+
+// Bit j set iff u[j] < t, for a 32-column chunk.
+__device__ __forceinline__ uint32_t hit_mask32(const float (&u)[32], float t) {
+  uint32_t g[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    g[q] = (u[4 * q] < t ? 1u : 0u) | (u[4 * q + 1] < t ? 2u : 0u) | (u[4 * q + 2] < t ? 4u : 0u) |
+           (u[4 * q + 3] < t ? 8u : 0u);
+  return (g[0] | (g[1] << 4) | (g[2] << 8) | (g[3] << 12)) |
+         ((g[4] | (g[5] << 4) | (g[6] << 8) | (g[7] << 12)) << 16);
 }
 
 template <int C, int KB, int BN, int S, int NR>
@@ -296,11 +309,13 @@ struct TcSmem {
   static constexpr int OFF_X = OFF_Q + Q_BYTES;
   static constexpr int OFF_NORM = OFF_X + S * X_STAGE;
   static constexpr int NEPI_THREADS = NEPI_WARPS * 32;
-  // per epilogue thread: a max-heap of LIST u64 keys, element j at [j][thread]
-  static constexpr int OFF_HEAP = OFF_NORM + NR * NORM_STAGE;
+  // per epilogue thread: the columns of its C list entries, entry j at [j][thread]
+  static constexpr int OFF_IDS = OFF_NORM + NR * NORM_STAGE;
   // per epilogue thread: one spilled 32-column chunk
-  static constexpr int OFF_SCR = OFF_HEAP + C * NEPI_THREADS * 8;
-  static constexpr int OFF_BAR = OFF_SCR + NEPI_WARPS * 32 * 32 * 4;
+  static constexpr int OFF_SCR = OFF_IDS + C * NEPI_THREADS * 4;
+  // per (half, query row): the root score of that half's heap
+  static constexpr int OFF_ROOT = OFF_SCR + NEPI_WARPS * 32 * 32 * 4;
+  static constexpr int OFF_BAR = OFF_ROOT + 2 * BM * 4;
   // barriers: full[S], empty[S], nfull[NR], nempty[NR], tfull[2], tempty[2], qfull, qempty
   static constexpr int NBAR = 2 * S + 2 * NR + 6;
   static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;  // tmem base, abort flag
@@ -322,8 +337,9 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
   uint8_t* sQ = smem + L::OFF_Q;
   uint8_t* sX = smem + L::OFF_X;
   float* sNorm = reinterpret_cast<float*>(smem + L::OFF_NORM);
-  uint64_t* sHeap = reinterpret_cast<uint64_t*>(smem + L::OFF_HEAP);
+  int* sIds = reinterpret_cast<int*>(smem + L::OFF_IDS);
   float* sScr = reinterpret_cast<float*>(smem + L::OFF_SCR);
+  float* sRoot = reinterpret_cast<float*>(smem + L::OFF_ROOT);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
   constexpr int NR = NRING;
   uint64_t* full = bars;
@@ -476,25 +492,33 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
   } else {
     // ---------------- epilogue ----------------
     // Lane l of warp w owns query row 32*(w%4) + l (its TMEM lane) for one
-    // half of each tile's columns.  Each thread keeps the C best
-    // (score, column) keys of its row in a max-heap in shared memory; the
-    // heap root is the threshold tau.  A 32-column chunk whose minimum is not
-    // below tau costs only the scores and the minimum.  Otherwise the thread
-    // spills the chunk to its scratch row, builds the bit mask of the columns
-    // below tau and pushes only those; hitting lanes run the same loop
-    // iterations, so their O(log C) sift-downs overlap.
+    // half of each tile's columns.  Each thread keeps the C best scores of its
+    // row so far, unsorted, in registers (their columns in shared memory), and
+    // tracks the largest of them: tau, the row's threshold.  A 32-column chunk
+    // whose minimum is not below tau costs only the scores and the minimum.
+    // Otherwise the thread spills the chunk to its scratch row, builds the bit
+    // mask of the columns below tau and, for each, overwrites the current
+    // largest entry and finds the new largest with a tree of three-input
+    // maxima -- short dependency chains, no memory round trips per level.
+    // The two halves of a row share their thresholds: whichever half has the
+    // smaller maximum holds C candidates below it, so min(max_0, max_1) bounds
+    // the row's C-th best and either half may drop anything at or above it.
     const int quarter = warp & 3;
     const int half = (warp - EPI_WARP0) / 4;
     const int row = quarter * 32 + lane;
     const int et = threadIdx.x - EPI_WARP0 * 32;  // epilogue thread index
     constexpr int NT = L::NEPI_THREADS;
-    uint64_t* heap = sHeap + et;
+    int* lid = sIds + et;  // column of list entry j at lid[j * NT]
     float* scr = sScr + et * 32;
+    float* my_root = sRoot + half * BM + row;
+    const float* other_root = sRoot + (1 - half) * BM + row;
     constexpr int HALF = BN / 2;
-    constexpr uint64_t EMPTY_KEY = 0xFF800000FFFFFFFFull;  // (+inf, no column)
     uint32_t it = 0;
     bool ok = true;
-    float tau = INFINITY;
+    float ls[C];               // the row's best C scores so far (unsorted)
+    int lpos = 0;              // position of the largest entry of ls
+    float tau_own = INFINITY;  // = ls[lpos]
+    float tau = INFINITY;      // effective threshold: min(own max, other half's max)
     for (int item = ib; ok && item < ie; ++item) {
       int q0, nq, sb, se, slot;
       item_info(w, item, q0, nq, sb, se, slot);
@@ -503,9 +527,17 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
       int nq0 = -1, nnq, nsb, nse, nslot;
       if (item + 1 < ie) item_info(w, item + 1, nq0, nnq, nsb, nse, nslot);
       if (pq0 != q0) {  // first item of a run of the same query tile
-#pragma unroll 4
-        for (int j = 0; j < C; ++j) heap[j * NT] = EMPTY_KEY;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          ls[j] = INFINITY;
+          lid[j * NT] = -1;
+        }
+        lpos = 0;
         tau = INFINITY;
+        tau_own = INFINITY;
+        *my_root = INFINITY;
+        // both halves have reset their maxima before either reads the other's
+        asm volatile("bar.sync 1, %0;" ::"r"(NT) : "memory");
       }
       for (int si = sb; ok && si < se; ++si) {
         const Seg sg = seg_at(w, si);
@@ -521,6 +553,7 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
             break;
           }
           tc_fence_after();
+          tau = fminf(tau, *other_root);
           const float* nrm = sNorm + r * BN + half * HALF;
           const int lo = sg.x_begin - x - half * HALF;  // first valid column of this half
           const int hi = sg.x_end - x - half * HALF;    // one past the last valid column
@@ -564,24 +597,25 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
               for (int j = 0; j < 32; j += 4)
                 *reinterpret_cast<float4*>(scr + ((((j >> 2) ^ lane) & 7) << 2)) =
                     make_float4(u[j], u[j + 1], u[j + 2], u[j + 3]);
-              // hit mask, combined as a tree of 4-bit groups
-              uint32_t g[8];
-#pragma unroll
-              for (int q = 0; q < 8; ++q)
-                g[q] = (u[4 * q] < tau ? 1u : 0u) | (u[4 * q + 1] < tau ? 2u : 0u) |
-                       (u[4 * q + 2] < tau ? 4u : 0u) | (u[4 * q + 3] < tau ? 8u : 0u);
-              uint32_t mask = (g[0] | (g[1] << 4) | (g[2] << 8) | (g[3] << 12)) |
-                              ((g[4] | (g[5] << 4) | (g[6] << 8) | (g[7] << 12)) << 16);
+              uint32_t mask = hit_mask32(u, tau);
               const int cb = x + half * HALF + c0;
+              const float tau_in = tau_own;
               while (mask) {
                 const int j = __ffs(mask) - 1;
                 mask &= mask - 1;
                 const float sv = scr[((((j >> 2) ^ lane) & 7) << 2) | (j & 3)];
                 if (sv < tau) {
-                  heap_replace_root<C, NT>(heap, ((uint64_t)f2o(sv) << 32) | (uint32_t)(cb + j));
-                  tau = o2f((uint32_t)(heap[0] >> 32));
+                  // overwrite the largest entry, then find the new largest
+#pragma unroll
+                  for (int t = 0; t < C; ++t)
+                    if (t == lpos) ls[t] = sv;
+                  lid[lpos * NT] = cb + j;
+                  tau_own = max_of<C>(ls);
+                  lpos = __ffs(eq_mask<C>(ls, tau_own)) - 1;
+                  tau = fminf(tau, tau_own);
                 }
               }
+              if (tau_own < tau_in) *my_root = tau_own;
             }
             __syncwarp();
           }
@@ -593,12 +627,10 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
       if (p.out.slot_valid && threadIdx.x == EPI_WARP0 * 32) p.out.slot_valid[slot] = carry ? 0 : 1;
       if (ok && !carry && row < nq) {
         int64_t base = (((int64_t)slot * TQ + row) * 2 + half) * C;
-#pragma unroll 4
+#pragma unroll
         for (int j = 0; j < C; ++j) {
-          const uint64_t key = heap[j * NT];
-          const float sc = o2f((uint32_t)(key >> 32));
-          p.out.score[base + j] = sc;
-          p.out.idx[base + j] = sc == INFINITY ? -1 : (int)(uint32_t)key;
+          p.out.score[base + j] = ls[j];
+          p.out.idx[base + j] = ls[j] == INFINITY ? -1 : lid[j * NT];
         }
       }
     }
@@ -709,7 +741,7 @@ int launch_bf_tc_topc(const LpMatrix& Qm, const LpMatrix& Xm, int C, const TileW
     }
   } else if (C == 32) {
     switch (Qm.dpad / 64) {
-      case 1: return launch_tc<32, 1, 256, 3, 8>(Qm, Xm, w, out, grid, st, dev_err);
+      case 1: return launch_tc<32, 1, 256, 4, 8>(Qm, Xm, w, out, grid, st, dev_err);
       case 2: return launch_tc<32, 2, 128, 2, 8>(Qm, Xm, w, out, grid, st, dev_err);
       case 3: return launch_tc<32, 3, 64, 3, 8>(Qm, Xm, w, out, grid, st, dev_err);
       case 4: return launch_tc<32, 4, 64, 2, 2>(Qm, Xm, w, out, grid, st, dev_err);
