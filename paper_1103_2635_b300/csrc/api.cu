@@ -367,8 +367,10 @@ int choose_c(int k, bool lp, int rerank_c) {
   return std::min(c, MAX_C);
 }
 
-// candidates kept per (row, half) by the tensor-core kernel
-int lp_width(int c) { return c <= 16 ? 16 : 32; }
+// Candidates kept per (row, half) by the tensor-core kernel: half of c_out.
+// The certificate also bounds what full half-lists dropped, so a row's c_out
+// candidates need not fit in one half.
+int lp_width(int c) { return c <= 16 ? 8 : (c <= 32 ? 16 : 32); }
 
 // ---------------------------------------------------------------------------
 // database views for the BF core

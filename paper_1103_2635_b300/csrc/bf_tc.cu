@@ -248,7 +248,7 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 // a multiple of 4 so that the tile's norms (BN floats) can be fetched with
 // one 16-byte-aligned bulk copy; the columns before the segment start and
 // past its end are masked to +inf in the epilogue.
-// Each (row, half) keeps C candidates (C = 16 or 32).
+// Each (row, half) keeps C candidates (C = 8, 16 or 32).
 
 __device__ __forceinline__ float max3f(float a, float b, float c) {
   float r;
@@ -256,22 +256,26 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
   return r;
 }
 
-// Largest of C register values (C = 16 or 32): a tree of three-input maxima.
+// Largest of C register values (C = 8, 16 or 32): pairwise maxima, then a
+// tree of three-input maxima.
 template <int C>
 __device__ __forceinline__ float max_of(const float (&v)[C]) {
   float m[C / 2];
 #pragma unroll
   for (int j = 0; j < C / 2; ++j) m[j] = fmaxf(v[2 * j], v[2 * j + 1]);
-  // C/2 = 8 or 16 partial maxima
-  float a = max3f(m[0], m[1], m[2]);
-  float b = max3f(m[3], m[4], m[5]);
-  float c = fmaxf(m[6], m[7]);
+  if constexpr (C == 8) {
+    return fmaxf(max3f(m[0], m[1], m[2]), m[3]);
+  } else {
+    float a = max3f(m[0], m[1], m[2]);
+    float b = max3f(m[3], m[4], m[5]);
+    float c = fmaxf(m[6], m[7]);
 #pragma unroll
-  for (int j = 8; j < C / 2; j += 4) {
-    a = max3f(a, m[j], m[j + 1]);
-    b = max3f(b, m[j + 2], m[j + 3]);
+    for (int j = 8; j < C / 2; j += 4) {
+      a = max3f(a, m[j], m[j + 1]);
+      b = max3f(b, m[j + 2], m[j + 3]);
+    }
+    return max3f(a, b, c);
   }
-  return max3f(a, b, c);
 }
 
 // Bit j set iff v[j] == x (C <= 32), OR-combined in groups of four.
@@ -731,7 +735,15 @@ int launch_bf_tc_topc(const LpMatrix& Qm, const LpMatrix& Xm, int C, const TileW
     set_error("tensor-core BF: operand layouts differ");
     return RBC_ERR_ARG;
   }
-  if (C == 16) {
+  if (C == 8) {
+    switch (Qm.dpad / 64) {
+      case 1: return launch_tc<8, 1, 256, 4, 8>(Qm, Xm, w, out, grid, st, dev_err);
+      case 2: return launch_tc<8, 2, 128, 3, 8>(Qm, Xm, w, out, grid, st, dev_err);
+      case 3: return launch_tc<8, 3, 64, 3, 8>(Qm, Xm, w, out, grid, st, dev_err);
+      case 4: return launch_tc<8, 4, 64, 2, 4>(Qm, Xm, w, out, grid, st, dev_err);
+      default: break;
+    }
+  } else if (C == 16) {
     switch (Qm.dpad / 64) {
       case 1: return launch_tc<16, 1, 256, 4, 8>(Qm, Xm, w, out, grid, st, dev_err);
       case 2: return launch_tc<16, 2, 128, 3, 8>(Qm, Xm, w, out, grid, st, dev_err);
@@ -748,7 +760,7 @@ int launch_bf_tc_topc(const LpMatrix& Qm, const LpMatrix& Xm, int C, const TileW
       default: break;
     }
   } else {
-    set_error("tensor-core BF: list width %d unsupported (16 or 32)", C);
+    set_error("tensor-core BF: list width %d unsupported (8, 16 or 32)", C);
     return RBC_ERR_ARG;
   }
   set_error("tensor-core BF: padded dimension %d unsupported", Qm.dpad);

@@ -11,9 +11,10 @@
 //     difference form sqrt(sum (q_i - x_i)^2) (or sum |q_i - x_i|) from the
 //     FP32 rows, four interleaved partial sums combined pairwise;
 //  3. bitonic sort of the 32 lanes by (rho, id);
-//  4. certification: every point outside the candidate set has a score >= B;
-//     its true distance is at least lower(B), a rounding-error bound of the
-//     pass that produced B.  The candidate set holds the true k nearest if
+//  4. certification: every point outside the candidate set has a score >= B
+//     (the c_out-th merged score, or less: the smallest maximum of a full
+//     sub-list, which bounds what the tile kernels dropped); its true distance
+//     is at least lower(B), a rounding-error bound of the pass that produced B.  The candidate set holds the true k nearest if
 //     lower(B) > rho_(k) * (1 + eps), eps the re-rank's relative bound;
 //     otherwise the row is queued for an FP32 re-search;
 //  5. near-ties: if two neighbouring ranks among the first k+1 lie within the
@@ -106,7 +107,33 @@ __global__ void __launch_bounds__(WARPS * 32) select_kernel(SelectArgs a) {
       ci = bi;
     }
   }
-  const float B = __shfl_sync(0xffffffffu, cs, a.c_out - 1);
+  // Every point of the searched set that is not a candidate scored at least
+  // B: either it is beyond the c_out-th merged entry, or a tile kernel dropped
+  // or evicted it, in which case it scored at least the final largest entry
+  // of some full sub-list (thresholds only fall).  So B is the smaller of the
+  // c_out-th merged score and the smallest maximum over full sub-lists.
+  float bcap = INFINITY;
+  for (int s = sb; s < se; ++s) {
+    if (a.slot_valid && !a.slot_valid[s]) continue;
+    for (int sub = 0; sub < a.nsub; ++sub) {
+      const int64_t base = (((int64_t)s * TQ + r) * a.nsub + sub) * a.C;
+      float v = -INFINITY;
+      int valid = 0;
+      for (int j = lane; j < a.C; j += 32) {
+        if (a.part_idx[base + j] >= 0) {
+          ++valid;
+          v = fmaxf(v, a.part_score[base + j]);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        valid += __shfl_xor_sync(0xffffffffu, valid, o);
+      }
+      if (valid == a.C) bcap = fminf(bcap, v);
+    }
+  }
+  const float B = fminf(__shfl_sync(0xffffffffu, cs, a.c_out - 1), bcap);
   const bool valid = lane < a.c_out && ci != INT32_MAX && cs != INFINITY;
 
   // ---- 2. FP32 re-rank ----
