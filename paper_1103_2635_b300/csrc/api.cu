@@ -389,7 +389,7 @@ struct DbView {
 // to output row qorig[i] (identity when null).  `cnt` = 3 counters.
 int bf_dense_f32(const float* Qdev, int64_t m, const DbView& db, int d, int k, int metric,
                  const int* qorig, int64_t* out_ids, float* out_dist, int* cnt, Arena& ar,
-                 cudaStream_t st) {
+                 cudaStream_t st, bool marks = true) {
   if (m == 0) return RBC_OK;
   const int c_out = choose_c(k, false, 0);
   const int C = simt_list_width(c_out);
@@ -411,9 +411,9 @@ int bf_dense_f32(const float* Qdev, int64_t m, const DbView& db, int d, int k, i
   w.dense_splits = (int)splits;
   w.dense_chunk = chunk;
   int grid = (int)std::min<int64_t>(items, (int64_t)sms * 2 * 16);
-  tmark(1, st);
+  if (marks) tmark(1, st);
   RBC_TRY(launch_bf_simt_topc(Qdev, db.X32, d, metric, C, w, TopOut{ps, pi, nullptr}, grid, st));
-  tmark(2, st);
+  if (marks) tmark(2, st);
   SelectArgs a{};
   a.part_score = ps;
   a.part_idx = pi;
@@ -435,8 +435,10 @@ int bf_dense_f32(const float* Qdev, int64_t m, const DbView& db, int d, int k, i
   a.out_dist = out_dist;
   a.counters = cnt;
   RBC_TRY(launch_select(a, st));
-  tmark(3, st);
-  tmark(4, st);
+  if (marks) {
+    tmark(3, st);
+    tmark(4, st);
+  }
   return RBC_OK;
 }
 
@@ -452,7 +454,8 @@ int fallback_f32(const float* Qbuf, const int* rows_dev, int nrows, const int* q
   RBC_TRY(ar.alloc(&forig, nrows));
   RBC_TRY(launch_gather_rows(Qbuf, nullptr, rows_dev, nrows, d, Qf, st));
   RBC_TRY(launch_map_rows(rows_dev, nullptr, nrows, qorig, forig, st));
-  return bf_dense_f32(Qf, nrows, db, d, k, metric, forig, out_ids, out_dist, cnt, ar, st);
+  // nested pass: its phases belong to the caller's "re-search" phase
+  return bf_dense_f32(Qf, nrows, db, d, k, metric, forig, out_ids, out_dist, cnt, ar, st, false);
 }
 
 // Low-precision copy of a query buffer.
@@ -460,6 +463,7 @@ struct LpQueries {
   void* lp = nullptr;
   float* norm = nullptr;
   float* err = nullptr;
+  int storage = RBC_BF16;
 };
 
 int lp_queries(const float* Qdev, int64_t m, int d, int dpad, int storage, LpQueries& q,
@@ -469,19 +473,29 @@ int lp_queries(const float* Qdev, int64_t m, int d, int dpad, int storage, LpQue
   RBC_TRY(ar.alloc(&q.norm, m));
   RBC_TRY(ar.alloc(&q.err, m));
   q.lp = buf;
+  q.storage = storage;
   return launch_to_lowp(Qdev, m, d, dpad, storage, buf, q.norm, q.err, nullptr, nullptr, st);
 }
 
+int bf_dense_lp(const float* Qdev, int64_t m, const DbView& db, int d, int k, int storage,
+                int rerank_c, int64_t* out_ids, float* out_dist, int* cnt, Arena& ar,
+                cudaStream_t st, const int* qorig = nullptr, int level = 0);
+
 // Select (merge + re-rank + certification) for the low-precision pass, then
-// the FP32 re-search of uncertified rows (one host read of their count).
+// the re-search of uncertified rows (one host read of their count): first on
+// the tensor cores with the widest candidate lists (level 0 only), then, for
+// rows that still fail, with the FP32 kernel over every row of `db`.
 int select_lp_and_fallback(const float* ps, const int* pi, const int* pv, int C,
                            const int* tile_slot_off,
                            int dense_splits, int64_t m, const float* Qbuf, const LpQueries& ql,
                            const DbView& db, int d, int k, int c_out, const int* qorig,
                            int64_t* out_ids, float* out_dist, int* cnt, Arena& ar,
-                           cudaStream_t st) {
+                           cudaStream_t st, int level = 0) {
   int* fb_rows;
+  int* lc;  // this call's counters: [0] rows appended to fb_rows, [1..2] ties
   RBC_TRY(ar.alloc(&fb_rows, m));
+  RBC_TRY(ar.alloc(&lc, 8));
+  RBC_CUDA(cudaMemsetAsync(lc, 0, 8 * sizeof(int), st));
   SelectArgs a{};
   a.part_score = ps;
   a.part_idx = pi;
@@ -507,30 +521,45 @@ int select_lp_and_fallback(const float* ps, const int* pi, const int* pv, int C,
   a.out_ids = out_ids;
   a.out_dist = out_dist;
   a.fallback_rows = fb_rows;
-  a.counters = cnt;
-  tmark(2, st);
+  a.counters = lc;
+  if (level == 0) tmark(2, st);
   RBC_TRY(launch_select(a, st));
-  tmark(3, st);
+  if (level == 0) tmark(3, st);
+  RBC_TRY(launch_add_ints(cnt, lc, 3, st));
   int nfb = 0;
-  RBC_CUDA(cudaMemcpyAsync(&nfb, cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RBC_CUDA(cudaMemcpyAsync(&nfb, lc, sizeof(int), cudaMemcpyDeviceToHost, st));
   RBC_CUDA(cudaStreamSynchronize(st));
-  if (nfb > 0)
-    RBC_TRY(fallback_f32(Qbuf, fb_rows, nfb, qorig, db, d, k, RBC_L2, out_ids, out_dist, cnt + 4,
-                         ar, st));
-  tmark(4, st);
+  if (nfb > 0) {
+    if (level == 0 && db.Xlp) {
+      float* Qf;
+      int* forig;
+      RBC_TRY(ar.alloc(&Qf, (int64_t)nfb * d));
+      RBC_TRY(ar.alloc(&forig, nfb));
+      RBC_TRY(launch_gather_rows(Qbuf, nullptr, fb_rows, nfb, d, Qf, st));
+      RBC_TRY(launch_map_rows(fb_rows, nullptr, nfb, qorig, forig, st));
+      RBC_TRY(bf_dense_lp(Qf, nfb, db, d, k, ql.storage, MAX_C, out_ids, out_dist, cnt + 4, ar, st,
+                          forig, 1));
+    } else {
+      RBC_TRY(fallback_f32(Qbuf, fb_rows, nfb, qorig, db, d, k, RBC_L2, out_ids, out_dist,
+                           cnt + 4, ar, st));
+    }
+  }
+  if (level == 0) tmark(4, st);
   return RBC_OK;
 }
 
-// Dense BF(Q, DB) on the tensor cores (L2, bf16 / fp16).
+// Dense BF(Q, DB) on the tensor cores (L2, bf16 / fp16).  Level 1 is the
+// re-search of rows that failed certification: the widest lists, output rows
+// mapped through qorig, no phase marks.
 int bf_dense_lp(const float* Qdev, int64_t m, const DbView& db, int d, int k, int storage,
                 int rerank_c, int64_t* out_ids, float* out_dist, int* cnt, Arena& ar,
-                cudaStream_t st) {
+                cudaStream_t st, const int* qorig, int level) {
   if (m == 0) return RBC_OK;
   const int c_out = choose_c(k, true, rerank_c);
-  const int C = lp_width(c_out);
+  const int C = level ? MAX_C : lp_width(c_out);
   LpQueries ql;
   RBC_TRY(lp_queries(Qdev, m, d, db.dpad, storage, ql, ar, st));
-  tmark(1, st);
+  if (level == 0) tmark(1, st);
   const int64_t tiles = (m + TQ - 1) / TQ;
   const int sms = sm_count();
   int64_t splits = (16LL * sms + tiles - 1) / tiles;
@@ -559,8 +588,8 @@ int bf_dense_lp(const float* Qdev, int64_t m, const DbView& db, int d, int k, in
   int grid = (int)std::min<int64_t>(items, (int64_t)sms);
   RBC_TRY(launch_bf_tc_topc(Qm, Xm, C, w, TopOut{ps, pi, pv}, grid, st, dev_err));
   RBC_TRY(select_lp_and_fallback(ps, pi, pv, C, nullptr, (int)splits, m, Qdev, ql, db, d, k,
-                                 c_out, nullptr, out_ids, out_dist, cnt, ar, st));
-  taccumulate();
+                                 c_out, qorig, out_ids, out_dist, cnt, ar, st, level));
+  if (level == 0) taccumulate();
   uint32_t herr = 0;
   RBC_CUDA(cudaMemcpyAsync(&herr, dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   RBC_CUDA(cudaStreamSynchronize(st));
@@ -595,7 +624,7 @@ int build_exact(rbc_index* ix, const float* Xdev, const std::vector<int64_t>& re
   DbView dbR;
   dbR.X32 = ix->R32;
   dbR.rows = n_r;
-  RBC_TRY(bf_dense_f32(Xdev, n, dbR, d, 1, metric, nullptr, owner, odist, cn.c, ar, st));
+  RBC_TRY(bf_dense_f32(Xdev, n, dbR, d, 1, metric, nullptr, owner, odist, cn.c, ar, st, false));
   // lists: stable counting sort by owner
   ix->list_entries = n;
   RBC_TRY(ix->alloc(&ix->offsets, n_r + 1));

@@ -131,6 +131,8 @@ int launch_workgen_items(const uint32_t* tile_mask, const int* offsets, int n_r,
 // reduce helpers for statistics
 int launch_sum_i32(const int* v, int64_t n, unsigned long long* out, cudaStream_t st);
 int launch_sum_i64(const int64_t* v, int64_t n, unsigned long long* out, cudaStream_t st);
+// dst[i] += src[i] for i < n (n <= 32)
+int launch_add_ints(int* dst, const int* src, int n, cudaStream_t st);
 // sum over query tiles of (tile rows) x (tile union points)
 int launch_sum_pairs(const int64_t* tile_points, int64_t m, unsigned long long* out,
                      cudaStream_t st);

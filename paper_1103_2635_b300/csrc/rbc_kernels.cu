@@ -325,7 +325,18 @@ __global__ void sum_pairs_kernel(const int64_t* __restrict__ tpts, int64_t m,
   if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
 }
 
+__global__ void add_ints_kernel(int* __restrict__ dst, const int* __restrict__ src, int n) {
+  int i = threadIdx.x;
+  if (i < n) dst[i] += src[i];
+}
+
 }  // namespace
+
+int launch_add_ints(int* dst, const int* src, int n, cudaStream_t st) {
+  add_ints_kernel<<<1, 32, 0, st>>>(dst, src, n);
+  RBC_LAUNCH_CHECK("add_ints_kernel");
+  return RBC_OK;
+}
 
 int launch_sum_pairs(const int64_t* tile_points, int64_t m, unsigned long long* out,
                      cudaStream_t st) {

@@ -159,3 +159,28 @@ def test_exact_search_tc_duplicates():
         ids, dist = search(idx, Q, 5)
         o_ids, o_rho = oracle.bf(Q, X, 5, "l2")
         np.testing.assert_array_equal(ids, o_ids)
+
+
+def test_exact_search_multi_batch_with_recheck():
+    """More queries than one internal batch (131,072), with 40 exact copies of
+    some points so that queries sitting on them tie far past the candidate
+    width, fail the low-precision certificate and are re-searched: every batch
+    must re-search its own rows only."""
+    base = synth.iid_normal(2000, 16, 90)
+    X = np.concatenate([base] + [base[:100]] * 40)
+    g = np.random.default_rng(91)
+    m = 140_000
+    Q = (X[g.integers(0, len(X), m)] + g.normal(0, 0.05, (m, 16))).astype(np.float32)
+    on = np.arange(0, m, 50)
+    Q[on] = base[g.integers(0, 100, len(on))]  # exactly on a 41-fold point
+    idx = build(X, 80, storage=rbc.BF16)
+    ids, dist = search(idx, Q, 5)
+    st = rbc.last_stats()
+    assert st["uncertified"] > 0  # the recheck path ran
+    ref_ids, ref_dist = rbc.bf_search(torch.from_numpy(Q).cuda(), torch.from_numpy(X).cuda(), 5)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(ids, ref_ids.cpu().numpy())
+    sel = np.unique(np.concatenate([on[:300], g.choice(m, 1200, replace=False)]))
+    o_ids, o_rho = oracle.bf(Q[sel], X, 5, "l2")
+    check_knn(Q[sel], X, ids[sel], dist[sel], o_ids, o_rho)
+    np.testing.assert_array_equal(ids[on[:300]], o_ids[np.searchsorted(sel, on[:300])])
