@@ -250,6 +250,17 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 // past its end are masked to +inf in the epilogue.
 // Each (row, half) keeps C candidates (C = 8, 16 or 32).
 
+// Minimum of 32 values as a depth-4 tree of three-input minima.
+__device__ __forceinline__ float min_of32(const float (&u)[32]) {
+  float a[11];
+#pragma unroll
+  for (int j = 0; j < 10; ++j) a[j] = min3f(u[3 * j], u[3 * j + 1], u[3 * j + 2]);
+  a[10] = fminf(u[30], u[31]);
+  const float b0 = min3f(a[0], a[1], a[2]), b1 = min3f(a[3], a[4], a[5]);
+  const float b2 = min3f(a[6], a[7], a[8]), b3 = fminf(a[9], a[10]);
+  return fminf(min3f(b0, b1, b2), b3);
+}
+
 __device__ __forceinline__ float max3f(float a, float b, float c) {
   float r;
   asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
@@ -305,6 +316,7 @@ __device__ __forceinline__ uint32_t hit_mask32(const float (&u)[32], float t) {
 
 template <int C, int KB, int BN, int S, int NR>
 struct TcSmem {
+  static constexpr int NBUF = (512 / BN) < 4 ? (512 / BN) : 4;  // TMEM accumulator buffers
   static constexpr int Q_BYTES = KB * BM * 128;  // query tile, KB K-blocks of 64 elements
   static constexpr int X_STAGE = KB * BN * 128;  // one database tile
   static constexpr int NORM_STAGE = BN * 4;
@@ -320,8 +332,8 @@ struct TcSmem {
   // per (half, query row): the root score of that half's heap
   static constexpr int OFF_ROOT = OFF_SCR + NEPI_WARPS * 32 * 32 * 4;
   static constexpr int OFF_BAR = OFF_ROOT + 2 * BM * 4;
-  // barriers: full[S], empty[S], nfull[NR], nempty[NR], tfull[2], tempty[2], qfull, qempty
-  static constexpr int NBAR = 2 * S + 2 * NR + 6;
+  // barriers: full[S], empty[S], nfull[NR], nempty[NR], tfull[NBUF], tempty[NBUF], qfull, qempty
+  static constexpr int NBAR = 2 * S + 2 * NR + 2 * NBUF + 2;
   static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;  // tmem base, abort flag
   static constexpr int BYTES = OFF_MISC + 16;
   static constexpr int ALLOC = BYTES + 1024;  // slack for 1024-byte alignment
@@ -350,10 +362,11 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
   uint64_t* empty = bars + S;
   uint64_t* nfull = bars + 2 * S;
   uint64_t* nempty = bars + 2 * S + NR;
+  constexpr int NBUF = L::NBUF;
   uint64_t* tfull = bars + 2 * S + 2 * NR;
-  uint64_t* tempty = bars + 2 * S + 2 * NR + 2;
-  uint64_t* qfull = bars + 2 * S + 2 * NR + 4;
-  uint64_t* qempty = bars + 2 * S + 2 * NR + 5;
+  uint64_t* tempty = bars + 2 * S + 2 * NR + NBUF;
+  uint64_t* qfull = bars + 2 * S + 2 * NR + 2 * NBUF;
+  uint64_t* qempty = bars + 2 * S + 2 * NR + 2 * NBUF + 1;
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(smem + L::OFF_MISC);
   volatile int* sAbort = reinterpret_cast<volatile int*>(smem + L::OFF_MISC + 4);
 
@@ -370,7 +383,7 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
       mbar_init(&nfull[r], 1);
       mbar_init(&nempty[r], NEPI);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NBUF; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], NEPI);
     }
@@ -383,7 +396,7 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(sTmem)),
-                 "r"(2 * BN)
+                 "r"(NBUF * BN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -463,8 +476,8 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
         for (int x = sg.x_begin & ~3; x < sg.x_end; x += BN, ++it) {
           const int s = it % S;
           const uint32_t ph = (it / S) & 1;
-          const int buf = it & 1;
-          const uint32_t aph = (it >> 1) & 1;
+          const int buf = it % NBUF;
+          const uint32_t aph = (it / NBUF) & 1;
           bool got = mbar_wait(&full[s], ph, sAbort, p.dev_err) &&
                      mbar_wait(&tempty[buf], aph ^ 1, sAbort, p.dev_err);
           if (!__all_sync(0xffffffffu, got)) {
@@ -548,8 +561,8 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
         for (int x = sg.x_begin & ~3; x < sg.x_end; x += BN, ++it) {
           const int r = it % NR;
           const uint32_t nph = (it / NR) & 1;
-          const int buf = it & 1;
-          const uint32_t aph = (it >> 1) & 1;
+          const int buf = it % NBUF;
+          const uint32_t aph = (it / NBUF) & 1;
           bool got = mbar_wait(&nfull[r], nph, sAbort, p.dev_err) &&
                      mbar_wait(&tfull[buf], aph, sAbort, p.dev_err);
           if (!__all_sync(0xffffffffu, got)) {
@@ -587,14 +600,7 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
                 if (c < lo || c >= hi) u[j] = INFINITY;
               }
             }
-            float ma = min3f(u[0], u[1], u[2]);
-            float mb = min3f(u[3], u[4], u[5]);
-#pragma unroll
-            for (int j = 6; j < 30; j += 4) {
-              ma = min3f(ma, u[j], u[j + 1]);
-              mb = min3f(mb, u[j + 2], u[j + 3]);
-            }
-            const float mn = min3f(ma, mb, fminf(u[30], u[31]));
+            const float mn = min_of32(u);
             if (mn < tau) {
               // 16-byte slots rotated by lane so that 8 lanes hit 8 bank groups
 #pragma unroll
@@ -644,7 +650,7 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NBUF * BN)
                  : "memory");
   }
 }
