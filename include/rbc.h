@@ -52,7 +52,7 @@ extern "C" {
 #define RBC_ERR_OOM (-2)         /* device allocation failed */
 #define RBC_ERR_CUDA (-3)        /* a CUDA runtime call or kernel failed */
 #define RBC_ERR_TIMEOUT (-4)     /* a bounded device-side wait expired */
-#define RBC_ERR_UNSUPPORTED (-5) /* combination not supported (e.g. d > 1024) */
+#define RBC_ERR_UNSUPPORTED (-5) /* combination not supported (e.g. d > 256) */
 
 /* ---- enumerations ---- */
 typedef enum {
@@ -108,14 +108,20 @@ int rbc_sample_reps(int64_t n, int32_t n_r, uint64_t seed, int64_t* out);
  *   (ties to the smaller id), each representative's list L_r is the set of
  *   points it owns and psi_r = max over L_r of rho(x, r).  `s` is ignored.
  *   One-shot mode: BF(R, X) with k = s gives each L_r = the s nearest points
- *   of r (ties by id) and psi_r = the s-th distance.
+ *   of r in (rho, id) order and psi_r = the s-th distance; lists are stored
+ *   back to back (offsets r * s, n_r * s < 2^31 entries).  The FP32 distances
+ *   are screened per representative by an exact radix select of the s-th
+ *   smallest; every point within the FP32 rounding bound of it is recomputed
+ *   in FP64 and sorted, so the lists are those of FP64 arithmetic.
  *   The index keeps its own copies (FP32 rows in list order, the
  *   low-precision copy, norms, rounding residuals, radii); X may be freed
  *   after the call returns and the stream has drained.
  *   out: receives the new index; free with rbc_free.
  *   Errors: RBC_ERR_ARG if n < 1, d < 1, n_r < 1, n_r > n, n >= 2^31,
  *   one-shot with s < 1 or s > n, bad enum, or NULL X/out;
- *   RBC_ERR_UNSUPPORTED if d > 1024; RBC_ERR_OOM; RBC_ERR_CUDA.
+ *   RBC_ERR_UNSUPPORTED if d > 256, if one-shot n_r * s >= 2^31, or if more
+ *   than 16384 points of a one-shot list tie within FP32 rounding of its
+ *   s-th distance; RBC_ERR_OOM; RBC_ERR_CUDA.
  */
 int rbc_build(const float* X, int64_t n, int32_t d, int32_t n_r, int32_t s, int32_t metric,
               const rbc_opts* opts, void* stream, rbc_index** out);
@@ -131,7 +137,9 @@ int rbc_build(const float* X, int64_t n, int32_t d, int32_t n_r, int32_t s, int3
  *   (ordered by nearest representative) and each tile searches the union of
  *   its queries' surviving lists -- a superset, so results are unchanged.
  *   One-shot mode (Section 5.1): BF(q, R) picks the nearest representative r
- *   and BF(q, X[L_r]) gives the answer; requires k <= s.
+ *   (ties to the smaller id) and BF(q, X[L_r]) gives the answer; requires
+ *   k <= s.  Queries are grouped by representative and each group padded to
+ *   whole 128-query tiles, so every tile searches exactly one list.
  *   Q [m, d] float32; out_ids [m, k] int64; out_dist [m, k] float32 (device
  *   or host).  m may be 0 (no work).  The call reads back one small counter
  *   (the stage-two work size) and so synchronises `stream` once.
@@ -149,7 +157,7 @@ int rbc_search(const rbc_index* idx, const float* Q, int64_t m, int32_t k, int64
  *   re-rank / certification / FP64 tie steps described above.  RBC_L1 always
  *   runs in FP32 on CUDA cores.
  *   Errors: RBC_ERR_ARG (m < 0, n < 1, d < 1, k < 1, n >= 2^31, bad enum,
- *   NULL pointers); RBC_ERR_UNSUPPORTED (d > 1024); RBC_ERR_OOM; RBC_ERR_CUDA.
+ *   NULL pointers); RBC_ERR_UNSUPPORTED (d > 256); RBC_ERR_OOM; RBC_ERR_CUDA.
  */
 int bf_search(const float* Q, int64_t m, const float* X, int64_t n, int32_t d, int32_t k,
               int32_t metric, int32_t storage, int64_t* out_ids, float* out_dist, void* stream);
@@ -198,9 +206,10 @@ int rbc_index_info(const rbc_index* idx, rbc_index_desc* out);
  * rbc_index_export -- copies the built structure to HOST arrays (each may be
  *   NULL to skip it): reps [n_r] representative ids (ascending);
  *   offsets [n_r + 1] start of each list in `members`; members
- *   [list_entries] database ids, list by list (ascending id within a list);
- *   psi [n_r] radii as float32 (for exact mode an upper bound of
- *   max_{x in L_r} rho(x, r) within the FP32 rounding bound).
+ *   [list_entries] database ids, list by list (exact mode: ascending id
+ *   within a list; one-shot: (rho, id) order); psi [n_r] radii as float32
+ *   (exact mode: an upper bound of max_{x in L_r} rho(x, r) within the FP32
+ *   rounding bound; one-shot: the FP64 s-th distance rounded to float).
  *   Synchronises the index's build stream.  Errors: RBC_ERR_ARG, RBC_ERR_CUDA.
  */
 int rbc_index_export(const rbc_index* idx, int64_t* reps, int64_t* offsets, int64_t* members,
@@ -209,9 +218,11 @@ int rbc_index_export(const rbc_index* idx, int64_t* reps, int64_t* offsets, int6
 /* Statistics of the most recent rbc_search / bf_search on this thread. */
 typedef struct {
   int64_t queries;
-  int64_t kept_reps;         /* sum over queries of surviving representatives */
+  int64_t kept_reps;         /* sum over queries of surviving representatives
+                                (one-shot: one per query) */
   int64_t tile_points;       /* sum over query tiles of the points in the tile's
-                                union of surviving lists */
+                                union of surviving lists (one-shot: padded
+                                tiles x s) */
   int64_t stage2_items;      /* stage-two work-item capacity launched */
   int64_t uncertified;       /* queries whose low-precision candidate set failed
                                 certification and were re-searched in FP32 */
@@ -219,7 +230,7 @@ typedef struct {
   int64_t boundary_ties;     /* queries with an FP32 near-tie at the k-th place */
   int64_t pairs;             /* (query, point) distances of the main BF pass:
                                 dense BF m*n; exact search sum over tiles of
-                                tile rows x union points */
+                                tile rows x union points; one-shot m*s */
   int64_t kernel_launches;   /* CUDA kernels this call launched */
   double stage1_ms;          /* device time per phase, filled only while
                                 rbc_set_timing(1) is in effect: preparation and */

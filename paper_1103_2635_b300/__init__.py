@@ -248,7 +248,10 @@ def rbc_build(X, n_r: int, metric: int = L2, seed: int = 0, mode: int = EXACT,
 
 
 def rbc_search(index: RbcIndex, Q, k: int, out_ids=None, out_dist=None, stream=None):
-    """Exact k-NN of every query with the index: ids [m, k], rho [m, k]."""
+    """k-NN of every query with the index: ids [m, k], rho [m, k].  Exact
+    mode returns the exact k nearest neighbours (Section 5.2); one-shot mode
+    the k nearest within the list of the query's nearest representative
+    (Section 5.1)."""
     qp, qk, qdev = _arg(Q, np.float32)
     m = qk.shape[0]
     out_ids, out_dist = _outputs(m, k, qk.device if qdev else None, out_ids, out_dist)

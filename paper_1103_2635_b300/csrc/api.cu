@@ -274,8 +274,10 @@ int counters_alloc(Counters& cn, Arena& ar, cudaStream_t st) {
   return RBC_OK;
 }
 
+thread_local int64_t t_stats_host_kept = -1;  // >= 0: kept_reps known on the host
+
 int stats_publish(const Counters& cn, int64_t queries, int64_t items, int64_t host_pairs, Arena& ar,
-                  cudaStream_t st) {
+                  cudaStream_t st, int64_t host_kept = -1) {
   if (!t_stats_host) {
     void* p = nullptr;
     RBC_CUDA(cudaMallocHost(&p, sizeof(StatsBlock)));
@@ -291,6 +293,7 @@ int stats_publish(const Counters& cn, int64_t queries, int64_t items, int64_t ho
   t_stats_fixed.queries = queries;
   t_stats_fixed.stage2_items = items;
   t_stats_fixed.pairs = host_pairs;
+  t_stats_host_kept = host_kept;
   t_stats_fixed.kernel_launches = t_launches;
   t_stats_fixed.stage1_ms = t_timing.ms[0];
   t_stats_fixed.stage2_ms = t_timing.ms[1];
@@ -603,6 +606,31 @@ int bf_dense_lp(const float* Qdev, int64_t m, const DbView& db, int d, int k, in
 // ---------------------------------------------------------------------------
 // build (Sections 4, 5.2)
 // ---------------------------------------------------------------------------
+// Low-precision copies of the list rows and the representatives (L2 with
+// bf16 / fp16 storage): rows padded to dpad, squared norms, error maxima.
+int make_lp_copies(rbc_index* ix, cudaStream_t st) {
+  if (ix->storage == RBC_F32 || ix->metric != RBC_L2) return RBC_OK;
+  const int64_t n = ix->list_entries;
+  const int d = ix->d, n_r = ix->n_r;
+  ix->dpad = pad64(d);
+  uint16_t* xl;
+  uint16_t* rl;
+  RBC_TRY(ix->alloc(&xl, n * ix->dpad));
+  RBC_TRY(ix->alloc(&ix->xnorm, n + NORM_PAD));
+  RBC_CUDA(cudaMemsetAsync(ix->xnorm + n, 0, NORM_PAD * sizeof(float), st));
+  RBC_TRY(ix->alloc(&ix->lp_max, 4));
+  RBC_TRY(ix->alloc(&rl, (int64_t)n_r * ix->dpad));
+  RBC_TRY(ix->alloc(&ix->rnorm, n_r));
+  RBC_CUDA(cudaMemsetAsync(ix->lp_max, 0, 4 * sizeof(unsigned), st));
+  RBC_TRY(launch_to_lowp(ix->X32, n, d, ix->dpad, ix->storage, xl, ix->xnorm, nullptr,
+                         ix->lp_max, ix->lp_max + 1, st));
+  RBC_TRY(launch_to_lowp(ix->R32, n_r, d, ix->dpad, ix->storage, rl, ix->rnorm, nullptr,
+                         ix->lp_max + 2, ix->lp_max + 3, st));
+  ix->Xlp = xl;
+  ix->Rlp = rl;
+  return RBC_OK;
+}
+
 int build_exact(rbc_index* ix, const float* Xdev, const std::vector<int64_t>& reps,
                 cudaStream_t st) {
   const int64_t n = ix->n;
@@ -638,24 +666,7 @@ int build_exact(rbc_index* ix, const float* Xdev, const std::vector<int64_t>& re
   RBC_TRY(ix->alloc(&ix->psi, n_r));
   RBC_TRY(launch_list_radii(odist, ix->members, ix->offsets, n_r, 2.0f * rerank_eps_host(d),
                             ix->psi, st));
-  if (ix->storage != RBC_F32 && metric == RBC_L2) {
-    ix->dpad = pad64(d);
-    uint16_t* xl;
-    uint16_t* rl;
-    RBC_TRY(ix->alloc(&xl, n * ix->dpad));
-    RBC_TRY(ix->alloc(&ix->xnorm, n + NORM_PAD));
-    RBC_CUDA(cudaMemsetAsync(ix->xnorm + n, 0, NORM_PAD * sizeof(float), st));
-    RBC_TRY(ix->alloc(&ix->lp_max, 4));
-    RBC_TRY(ix->alloc(&rl, (int64_t)n_r * ix->dpad));
-    RBC_TRY(ix->alloc(&ix->rnorm, n_r));
-    RBC_CUDA(cudaMemsetAsync(ix->lp_max, 0, 4 * sizeof(unsigned), st));
-    RBC_TRY(launch_to_lowp(ix->X32, n, d, ix->dpad, ix->storage, xl, ix->xnorm, nullptr,
-                           ix->lp_max, ix->lp_max + 1, st));
-    RBC_TRY(launch_to_lowp(ix->R32, n_r, d, ix->dpad, ix->storage, rl, ix->rnorm, nullptr,
-                           ix->lp_max + 2, ix->lp_max + 3, st));
-    ix->Xlp = xl;
-    ix->Rlp = rl;
-  }
+  RBC_TRY(make_lp_copies(ix, st));
   RBC_CUDA(cudaStreamSynchronize(st));
   return RBC_OK;
 }
@@ -813,6 +824,277 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
   return RBC_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// one-shot build and search (Sections 4 and 5.1)
+// ---------------------------------------------------------------------------
+constexpr int ONESHOT_MAX_CAP = 16384;             // candidates a refine block can sort
+constexpr int64_t ONESHOT_D_BYTES = 4LL << 30;     // distance block of the build
+
+// BF(R, X) with k = s: L_r = the s nearest points of r by (rho, id), psi_r
+// the s-th distance.  Representatives are processed in blocks whose FP32
+// distance rows fit ONESHOT_D_BYTES.
+int build_oneshot(rbc_index* ix, const float* Xdev, const std::vector<int64_t>& reps,
+                  cudaStream_t st) {
+  const int64_t n = ix->n;
+  const int d = ix->d, n_r = ix->n_r, metric = ix->metric, s = ix->s;
+  const int64_t entries = (int64_t)n_r * s;
+  if (entries >= (1LL << 31)) {
+    set_error("rbc_build: one-shot lists hold n_r * s = %lld entries (limit 2^31 - 1)",
+              (long long)entries);
+    return RBC_ERR_UNSUPPORTED;
+  }
+  Arena ar(st);
+  RBC_TRY(ix->alloc(&ix->reps, n_r));
+  RBC_CUDA(cudaMemcpyAsync(ix->reps, reps.data(), n_r * sizeof(int64_t), cudaMemcpyHostToDevice,
+                           st));
+  RBC_TRY(ix->alloc(&ix->R32, (int64_t)n_r * d));
+  RBC_TRY(launch_gather_rows(Xdev, ix->reps, nullptr, n_r, d, ix->R32, st));
+  ix->list_entries = entries;
+  RBC_TRY(ix->alloc(&ix->members, entries));
+  RBC_TRY(ix->alloc(&ix->psi, n_r));
+  RBC_TRY(ix->alloc(&ix->offsets, n_r + 1));
+  {
+    std::vector<int> off((size_t)n_r + 1);
+    for (int r = 0; r <= n_r; ++r) off[(size_t)r] = r * s;
+    RBC_CUDA(cudaMemcpyAsync(ix->offsets, off.data(), off.size() * sizeof(int),
+                             cudaMemcpyHostToDevice, st));
+    RBC_CUDA(cudaStreamSynchronize(st));  // `off` leaves scope
+  }
+  int64_t rb = std::max<int64_t>(1, ONESHOT_D_BYTES / (n * (int64_t)sizeof(float)));
+  rb = std::min<int64_t>(rb, n_r);
+  if (rb > TQ) rb = rb / TQ * TQ;
+  float* D;
+  RBC_TRY(ar.alloc(&D, rb * n));
+  uint32_t* dev_err;
+  RBC_TRY(ar.alloc(&dev_err, 1));
+  const int sms = sm_count();
+  int cap = oneshot_candidate_cap(s);
+  for (;;) {
+    if (cap > ONESHOT_MAX_CAP) {
+      set_error("rbc_build: more than %d points tie within rounding of a representative's s-th "
+                "distance (s=%d)",
+                ONESHOT_MAX_CAP, s);
+      return RBC_ERR_UNSUPPORTED;
+    }
+    Arena car(st);
+    int *cand, *ccnt;
+    RBC_TRY(car.alloc(&cand, rb * cap));
+    RBC_TRY(car.alloc(&ccnt, rb));
+    RBC_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(uint32_t), st));
+    for (int64_t r0 = 0; r0 < n_r; r0 += rb) {
+      const int nb = (int)std::min<int64_t>(rb, n_r - r0);
+      const int64_t tiles = (nb + TQ - 1) / TQ;
+      int64_t splits = (8LL * sms + tiles - 1) / tiles;
+      splits = std::max<int64_t>(1, std::min<int64_t>(splits, std::max<int64_t>(1, n / 512)));
+      int64_t chunk = (n + splits - 1) / splits;
+      splits = (n + chunk - 1) / chunk;
+      TileWork w{};
+      w.num_items = (int)(tiles * splits);
+      w.m = nb;
+      w.n = n;
+      w.dense_splits = (int)splits;
+      w.dense_chunk = chunk;
+      RBC_TRY(launch_bf_simt_store(ix->R32 + r0 * d, Xdev, d, metric, w, D, n,
+                                   (int)std::min<int64_t>(w.num_items, (int64_t)sms * 2 * 16),
+                                   st));
+      RBC_TRY(launch_oneshot_select(D, n, n, nb, s, simt_eps(d), cap, cand, ccnt, dev_err, st));
+      RBC_TRY(launch_oneshot_refine(Xdev, ix->R32, d, metric, s, cap, cand, ccnt, (int)r0, nb,
+                                    ix->members, ix->psi, dev_err, st));
+    }
+    uint32_t herr = 0;
+    RBC_CUDA(cudaMemcpyAsync(&herr, dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    RBC_CUDA(cudaStreamSynchronize(st));
+    if (herr & DEV_ERR_BOUNDS) {
+      set_error("rbc_build: non-finite distances (X holds inf or NaN)");
+      return RBC_ERR_ARG;
+    }
+    if (!(herr & DEV_ERR_CAPACITY)) break;
+    cap = cap < ONESHOT_MAX_CAP ? std::min(ONESHOT_MAX_CAP, cap * 4) : cap * 2;
+  }
+  RBC_TRY(ix->alloc(&ix->X32, entries * d));
+  RBC_TRY(launch_gather_rows(Xdev, nullptr, ix->members, entries, d, ix->X32, st));
+  RBC_TRY(make_lp_copies(ix, st));
+  RBC_CUDA(cudaStreamSynchronize(st));
+  return RBC_OK;
+}
+
+// Stage two of the one-shot search: query rows of `Qsrc` (mq of them) against
+// the list of their representative rep_of[i]; results go to output row
+// orig[i] (i when orig is null).  Queries are grouped by representative and
+// every group padded to whole TQ-row tiles, so each tile is one dense item
+// against exactly one list.  Low-precision rows that fail certification are
+// searched again against their own list with the FP32 kernel.
+int oneshot_stage2(const rbc_index* ix, const float* Qsrc, int64_t mq, const int64_t* rep_of,
+                   const int* orig, bool lp, int k, int64_t* ids, float* dist, int* cnt,
+                   unsigned long long* points_sum, int64_t* items_total, Arena& ar,
+                   cudaStream_t st, bool marks) {
+  if (mq == 0) return RBC_OK;
+  const int d = ix->d, n_r = ix->n_r, s = ix->s, metric = ix->metric;
+  const int64_t entries = ix->list_entries;
+  const int sms = sm_count();
+  int *qperm, *qoff, *scratch;
+  RBC_TRY(ar.alloc(&qperm, mq));
+  RBC_TRY(ar.alloc(&qoff, n_r + 1));
+  RBC_TRY(ar.alloc(&scratch, counting_sort_scratch_ints(mq, n_r)));
+  RBC_TRY(launch_counting_sort(rep_of, mq, n_r, qperm, qoff, scratch, st));
+  const int64_t max_tiles = (mq + TQ - 1) / TQ + std::min<int64_t>(n_r, mq);
+  const int64_t rows_cap = max_tiles * TQ;
+  int *pad_cnt, *pad_off, *qsrc, *qout, *tile_rep;
+  RBC_TRY(ar.alloc(&pad_cnt, n_r));
+  RBC_TRY(ar.alloc(&pad_off, n_r + 1));
+  RBC_TRY(ar.alloc(&qsrc, rows_cap));
+  RBC_TRY(ar.alloc(&qout, rows_cap));
+  RBC_TRY(ar.alloc(&tile_rep, max_tiles));
+  RBC_CUDA(cudaMemsetAsync(qsrc, 0xff, rows_cap * sizeof(int), st));
+  RBC_CUDA(cudaMemsetAsync(qout, 0xff, rows_cap * sizeof(int), st));
+  RBC_TRY(launch_oneshot_layout(qoff, n_r, qperm, orig, pad_cnt, pad_off, qsrc, qout, tile_rep,
+                                st));
+  float* Qp;
+  RBC_TRY(ar.alloc(&Qp, rows_cap * d));
+  RBC_TRY(launch_gather_padded(Qsrc, qsrc, rows_cap, d, Qp, st));
+  WorkItem* items;
+  Seg* segs;
+  int* nitems;
+  RBC_TRY(ar.alloc(&items, max_tiles));
+  RBC_TRY(ar.alloc(&segs, max_tiles));
+  RBC_TRY(ar.alloc(&nitems, 1));
+  RBC_TRY(launch_oneshot_items(pad_off, n_r, tile_rep, qoff, s, items, segs, nitems,
+                               (int)max_tiles, points_sum, st));
+  if (items_total) *items_total += max_tiles;
+  TileWork w{};
+  w.items = items;
+  w.num_items_dev = nitems;
+  w.num_items = (int)max_tiles;
+  w.segs = segs;
+  w.m = rows_cap;
+  w.n = entries;
+  SelectArgs a{};
+  a.nsub = 2;
+  a.dense_splits = 1;  // slot of tile t is t
+  a.m = rows_cap;
+  a.Q32 = Qp;
+  a.d = d;
+  a.metric = metric;
+  a.qorig = qout;
+  a.X32 = ix->X32;
+  a.xid = ix->members;
+  a.k = k;
+  a.out_ids = ids;
+  a.out_dist = dist;
+  if (!lp) {
+    const int c_out = choose_c(k, false, 0);
+    const int C = simt_list_width(c_out);
+    float* ps;
+    int* pi;
+    RBC_TRY(ar.alloc(&ps, max_tiles * TQ * 2 * C));
+    RBC_TRY(ar.alloc(&pi, max_tiles * TQ * 2 * C));
+    if (marks) tmark(1, st);
+    RBC_TRY(launch_bf_simt_topc(Qp, ix->X32, d, metric, C, w, TopOut{ps, pi, nullptr},
+                                (int)std::min<int64_t>(max_tiles, (int64_t)sms * 2 * 8), st));
+    if (marks) tmark(2, st);
+    a.part_score = ps;
+    a.part_idx = pi;
+    a.C = C;
+    a.simt_eps = simt_eps(d);
+    a.c_out = c_out;
+    a.counters = cnt;
+    RBC_TRY(launch_select(a, st));
+    if (marks) {
+      tmark(3, st);
+      tmark(4, st);
+    }
+    return RBC_OK;
+  }
+  const int c_out = choose_c(k, true, ix->rerank_c);
+  const int C = lp_width(c_out);
+  LpQueries ql;
+  RBC_TRY(lp_queries(Qp, rows_cap, d, ix->dpad, ix->storage, ql, ar, st));
+  float* ps;
+  int* pi;
+  int* pv;
+  RBC_TRY(ar.alloc(&ps, max_tiles * TQ * 2 * C));
+  RBC_TRY(ar.alloc(&pi, max_tiles * TQ * 2 * C));
+  RBC_TRY(ar.alloc(&pv, max_tiles));
+  uint32_t* dev_err;
+  RBC_TRY(ar.alloc(&dev_err, 1));
+  RBC_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(uint32_t), st));
+  LpMatrix Qm{ql.lp, ql.norm, rows_cap, ix->dpad, ix->storage};
+  LpMatrix Xm{ix->Xlp, ix->xnorm, entries, ix->dpad, ix->storage};
+  if (marks) tmark(1, st);
+  RBC_TRY(launch_bf_tc_topc(Qm, Xm, C, w, TopOut{ps, pi, pv}, sms, st, dev_err));
+  if (marks) tmark(2, st);
+  int* fb_rows;
+  int* lc;  // [0] rows appended to fb_rows, [1..2] ties
+  RBC_TRY(ar.alloc(&fb_rows, rows_cap));
+  RBC_TRY(ar.alloc(&lc, 8));
+  RBC_CUDA(cudaMemsetAsync(lc, 0, 8 * sizeof(int), st));
+  a.part_score = ps;
+  a.part_idx = pi;
+  a.slot_valid = pv;
+  a.C = C;
+  a.lp = 1;
+  a.q_lpnorm = ql.norm;
+  a.q_err = ql.err;
+  a.x_err_max_bits = ix->lp_max;
+  a.x_norm_max_bits = ix->lp_max + 1;
+  a.c_out = c_out;
+  a.fallback_rows = fb_rows;
+  a.counters = lc;
+  RBC_TRY(launch_select(a, st));
+  if (marks) tmark(3, st);
+  RBC_TRY(launch_add_ints(cnt, lc, 3, st));
+  int nfb = 0;
+  uint32_t herr = 0;
+  RBC_CUDA(cudaMemcpyAsync(&nfb, lc, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RBC_CUDA(cudaMemcpyAsync(&herr, dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  RBC_CUDA(cudaStreamSynchronize(st));
+  if (herr) {
+    set_error("one-shot tensor-core pass reported device error flags 0x%x", herr);
+    return (herr & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
+  }
+  if (nfb > 0) {
+    int64_t* frep;
+    int* forig;
+    float* Qf;
+    RBC_TRY(ar.alloc(&frep, nfb));
+    RBC_TRY(ar.alloc(&forig, nfb));
+    RBC_TRY(ar.alloc(&Qf, (int64_t)nfb * d));
+    RBC_TRY(launch_oneshot_fallback_map(fb_rows, nfb, tile_rep, qout, frep, forig, st));
+    RBC_TRY(launch_gather_rows(Qp, nullptr, fb_rows, nfb, d, Qf, st));
+    RBC_TRY(oneshot_stage2(ix, Qf, nfb, frep, forig, false, k, ids, dist, cnt + 4, nullptr,
+                           nullptr, ar, st, false));
+  }
+  if (marks) tmark(4, st);
+  return RBC_OK;
+}
+
+// One-shot search of one query batch: r(q) = nearest representative by
+// BF(Q, R) (k = 1, ties to the smaller ordinal, i.e. the smaller id), then
+// BF(q, X[L_r(q)]).
+int search_oneshot_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, int64_t* ids,
+                         float* dist, const Counters& cn, int64_t* items_total, Arena& ar,
+                         cudaStream_t st) {
+  tmark(0, st);
+  int64_t* nearest;
+  float* ndist;
+  int* c1;  // stage-one select counters (not part of the search statistics)
+  RBC_TRY(ar.alloc(&nearest, mb));
+  RBC_TRY(ar.alloc(&ndist, mb));
+  RBC_TRY(ar.alloc(&c1, 8));
+  RBC_CUDA(cudaMemsetAsync(c1, 0, 8 * sizeof(int), st));
+  DbView dbR;
+  dbR.X32 = ix->R32;
+  dbR.rows = ix->n_r;
+  RBC_TRY(bf_dense_f32(Qb, mb, dbR, ix->d, 1, ix->metric, nullptr, nearest, ndist, c1, ar, st,
+                       false));
+  const bool lp = uses_lp(ix->storage, ix->metric) && ix->Xlp != nullptr;
+  RBC_TRY(oneshot_stage2(ix, Qb, mb, nearest, nullptr, lp, k, ids, dist, cn.c, cn.sums + 1,
+                         items_total, ar, st, true));
+  taccumulate();
+  return RBC_OK;
+}
+
 }  // namespace
 }  // namespace rbc
 
@@ -849,7 +1131,7 @@ int rbc_last_stats(rbc_search_stats* out) {
     cudaError_t e = cudaStreamSynchronize(t_stats_stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
     const unsigned long long* v = t_stats_host->v;
-    t_stats_fixed.kept_reps = (int64_t)v[0];
+    t_stats_fixed.kept_reps = t_stats_host_kept >= 0 ? t_stats_host_kept : (int64_t)v[0];
     t_stats_fixed.tile_points = (int64_t)v[1];
     t_stats_fixed.uncertified = (int64_t)v[2];
     t_stats_fixed.fp64_ties = (int64_t)v[3];
@@ -960,10 +1242,6 @@ int rbc_build(const float* X, int64_t n, int32_t d, int32_t n_r, int32_t s, int3
     set_error("rbc_build: d=%d exceeds %d", d, MAX_D);
     return RBC_ERR_UNSUPPORTED;
   }
-  if (o.mode == RBC_ONESHOT) {
-    set_error("rbc_build: one-shot mode is not available in this build");
-    return RBC_ERR_UNSUPPORTED;
-  }
   std::vector<int64_t> reps;
   if (o.rep_ids) {
     reps.assign(o.rep_ids, o.rep_ids + n_r);
@@ -1003,7 +1281,9 @@ int rbc_build(const float* X, int64_t n, int32_t d, int32_t n_r, int32_t s, int3
       }
       Xdev = x;
     }
-    if (rc == RBC_OK) rc = build_exact(ix, Xdev, reps, st);
+    if (rc == RBC_OK)
+      rc = o.mode == RBC_ONESHOT ? build_oneshot(ix, Xdev, reps, st)
+                                 : build_exact(ix, Xdev, reps, st);
   }
   if (rc != RBC_OK) {
     cudaStreamSynchronize(st);
@@ -1025,6 +1305,10 @@ int rbc_search(const rbc_index* ix, const float* Q, int64_t m, int32_t k, int64_
     set_error("rbc_search: bad sizes m=%lld k=%d (n=%lld)", (long long)m, k, (long long)ix->n);
     return RBC_ERR_ARG;
   }
+  if (ix->mode == RBC_ONESHOT && k > ix->s) {
+    set_error("rbc_search: one-shot lists hold s=%d points, k=%d", ix->s, k);
+    return RBC_ERR_ARG;
+  }
   if (k > MAX_C - 1) {
     set_error("rbc_search: k=%d exceeds the supported maximum %d", k, MAX_C - 1);
     return RBC_ERR_UNSUPPORTED;
@@ -1038,10 +1322,17 @@ int rbc_search(const rbc_index* ix, const float* Q, int64_t m, int32_t k, int64_
   for (int64_t b0 = 0; b0 < m; b0 += MAX_BATCH) {
     int64_t mb = std::min<int64_t>(MAX_BATCH, m - b0);
     Arena bar(st);
-    RBC_TRY(search_exact_batch(ix, io.Qdev + b0 * ix->d, mb, k, io.ids_dev + b0 * k,
-                               io.dist_dev + b0 * k, cn, &items, bar, st));
+    if (ix->mode == RBC_ONESHOT)
+      RBC_TRY(search_oneshot_batch(ix, io.Qdev + b0 * ix->d, mb, k, io.ids_dev + b0 * k,
+                                   io.dist_dev + b0 * k, cn, &items, bar, st));
+    else
+      RBC_TRY(search_exact_batch(ix, io.Qdev + b0 * ix->d, mb, k, io.ids_dev + b0 * k,
+                                 io.dist_dev + b0 * k, cn, &items, bar, st));
   }
-  RBC_TRY(stats_publish(cn, m, items, 0, ar, st));
+  if (ix->mode == RBC_ONESHOT)
+    RBC_TRY(stats_publish(cn, m, items, m * (int64_t)ix->s, ar, st, m));
+  else
+    RBC_TRY(stats_publish(cn, m, items, 0, ar, st));
   RBC_TRY(io_finish(m, k, out_ids, out_dist, io, st));
   return RBC_OK;
 }

@@ -92,7 +92,9 @@ bf_simt_kernel(const float* __restrict__ Q, const float* __restrict__ X, int d, 
     TopList<C> top;
     if (!STORE) top.init();
 
-    int store_col = 0;  // STORE mode: running column of the output matrix
+    // STORE mode: running column of the output matrix (a dense split starts
+    // at its first database row)
+    int store_col = w.items ? 0 : (int)get_seg(w, sb).x_begin;
     for (int si = sb; si < se; ++si) {
       const Seg sg = get_seg(w, si);
       for (int x0 = sg.x_begin; x0 < sg.x_end; x0 += TX) {

@@ -64,7 +64,8 @@ struct SelectArgs {
   const float* Q32;          // [m, d] buffer queries FP32
   int d;
   int metric;
-  const int* qorig;          // buffer row -> original query index (nullptr = identity)
+  const int* qorig;          // buffer row -> original query index (nullptr = identity;
+                             // rows mapped to -1 are padding and skipped)
   const float* X32;          // database buffer rows FP32
   const int* xid;            // buffer row -> original id (nullptr = identity)
   int lp;                    // 1: scores are |x~|^2 - 2 q~.x~ (low precision)
@@ -81,6 +82,41 @@ struct SelectArgs {
   int* counters;             // [0] uncertified, [1] fp64 ties, [2] boundary ties
 };
 int launch_select(const SelectArgs& a, cudaStream_t st);
+
+
+// ---- one-shot RBC (oneshot.cu) ----
+// candidate capacity per representative for a list of s points
+int oneshot_candidate_cap(int s);
+// per row r < reps of D [reps, ld] (distances to n points): the s-th smallest
+// value t and every column with D <= t (1 + 3 eps) -> cand[r][0 .. cand_cnt[r])
+int launch_oneshot_select(const float* D, int64_t ld, int64_t n, int reps, int s, float eps,
+                          int cap, int* cand, int* cand_cnt, uint32_t* dev_err, cudaStream_t st);
+// FP64 distances of the candidates of representatives r0 .. r0 + reps - 1,
+// sorted by (rho, id): the first s ids -> members[r][0 .. s), psi[r] = the
+// s-th distance rounded to float; DEV_ERR_BOUNDS when a representative had
+// fewer than s candidates (non-finite distances)
+int launch_oneshot_refine(const float* X, const float* R, int d, int metric, int s, int cap,
+                          const int* cand, const int* cand_cnt, int r0, int reps, int* members,
+                          float* psi, uint32_t* dev_err, cudaStream_t st);
+// queries grouped by representative (qperm, qoff from a counting sort), each
+// group padded to a multiple of TQ rows: pad_off [n_r + 1], per padded row
+// the source row (qsrc_pad) and the output row (qout_pad, through `orig` when
+// given), -1 on padding, and per tile its representative
+int launch_oneshot_layout(const int* qoff, int n_r, const int* qperm, const int* orig,
+                          int* counts_scratch, int* pad_off, int* qsrc_pad, int* qout_pad,
+                          int* tile_rep, cudaStream_t st);
+// one work item per padded tile: its rows against list r = [r s, (r + 1) s);
+// adds (tiles x s) to *points_sum when given
+int launch_oneshot_items(const int* pad_off, int n_r, const int* tile_rep, const int* qoff, int s,
+                         WorkItem* items, Seg* segs, int* num_items, int max_tiles,
+                         unsigned long long* points_sum, cudaStream_t st);
+// out[i] = Q[src[i]] (zero row where src[i] < 0), i < rows
+int launch_gather_padded(const float* Q, const int* src, int64_t rows, int d, float* out,
+                         cudaStream_t st);
+// rows[i] (i < n) of a padded layout -> rep64[i] = tile_rep[rows[i] / TQ],
+// out_row[i] = qout_pad[rows[i]]
+int launch_oneshot_fallback_map(const int* rows, int n, const int* tile_rep, const int* qout_pad,
+                                int64_t* rep64, int* out_row, cudaStream_t st);
 
 }  // namespace rbc
 
@@ -131,10 +167,47 @@ int launch_workgen_items(const uint32_t* tile_mask, const int* offsets, int n_r,
 // reduce helpers for statistics
 int launch_sum_i32(const int* v, int64_t n, unsigned long long* out, cudaStream_t st);
 int launch_sum_i64(const int64_t* v, int64_t n, unsigned long long* out, cudaStream_t st);
+// out[i] = sum_{j<i} in[j] for i <= n (out[n] = total), one block
+int launch_exclusive_scan(const int* in, int n, int* out, cudaStream_t st);
 // dst[i] += src[i] for i < n (n <= 32)
 int launch_add_ints(int* dst, const int* src, int n, cudaStream_t st);
 // sum over query tiles of (tile rows) x (tile union points)
 int launch_sum_pairs(const int64_t* tile_points, int64_t m, unsigned long long* out,
                      cudaStream_t st);
+
+
+// ---- one-shot RBC (oneshot.cu) ----
+// candidate capacity per representative for a list of s points
+int oneshot_candidate_cap(int s);
+// per row r < reps of D [reps, ld] (distances to n points): the s-th smallest
+// value t and every column with D <= t (1 + 3 eps) -> cand[r][0 .. cand_cnt[r])
+int launch_oneshot_select(const float* D, int64_t ld, int64_t n, int reps, int s, float eps,
+                          int cap, int* cand, int* cand_cnt, uint32_t* dev_err, cudaStream_t st);
+// FP64 distances of the candidates of representatives r0 .. r0 + reps - 1,
+// sorted by (rho, id): the first s ids -> members[r][0 .. s), psi[r] = the
+// s-th distance rounded to float; DEV_ERR_BOUNDS when a representative had
+// fewer than s candidates (non-finite distances)
+int launch_oneshot_refine(const float* X, const float* R, int d, int metric, int s, int cap,
+                          const int* cand, const int* cand_cnt, int r0, int reps, int* members,
+                          float* psi, uint32_t* dev_err, cudaStream_t st);
+// queries grouped by representative (qperm, qoff from a counting sort), each
+// group padded to a multiple of TQ rows: pad_off [n_r + 1], per padded row
+// the source row (qsrc_pad) and the output row (qout_pad, through `orig` when
+// given), -1 on padding, and per tile its representative
+int launch_oneshot_layout(const int* qoff, int n_r, const int* qperm, const int* orig,
+                          int* counts_scratch, int* pad_off, int* qsrc_pad, int* qout_pad,
+                          int* tile_rep, cudaStream_t st);
+// one work item per padded tile: its rows against list r = [r s, (r + 1) s);
+// adds (tiles x s) to *points_sum when given
+int launch_oneshot_items(const int* pad_off, int n_r, const int* tile_rep, const int* qoff, int s,
+                         WorkItem* items, Seg* segs, int* num_items, int max_tiles,
+                         unsigned long long* points_sum, cudaStream_t st);
+// out[i] = Q[src[i]] (zero row where src[i] < 0), i < rows
+int launch_gather_padded(const float* Q, const int* src, int64_t rows, int d, float* out,
+                         cudaStream_t st);
+// rows[i] (i < n) of a padded layout -> rep64[i] = tile_rep[rows[i] / TQ],
+// out_row[i] = qout_pad[rows[i]]
+int launch_oneshot_fallback_map(const int* rows, int n, const int* tile_rep, const int* qout_pad,
+                                int64_t* rep64, int* out_row, cudaStream_t st);
 
 }  // namespace rbc

@@ -332,6 +332,12 @@ __global__ void add_ints_kernel(int* __restrict__ dst, const int* __restrict__ s
 
 }  // namespace
 
+int launch_exclusive_scan(const int* in, int n, int* out, cudaStream_t st) {
+  exclusive_scan_kernel<<<1, 1024, 0, st>>>(in, n, out);
+  RBC_LAUNCH_CHECK("exclusive_scan_kernel");
+  return RBC_OK;
+}
+
 int launch_add_ints(int* dst, const int* src, int n, cudaStream_t st) {
   add_ints_kernel<<<1, 32, 0, st>>>(dst, src, n);
   RBC_LAUNCH_CHECK("add_ints_kernel");

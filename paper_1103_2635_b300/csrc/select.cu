@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(WARPS * 32) select_kernel(SelectArgs a) {
   const int64_t nrows = a.rows ? (int64_t)*a.num_rows_dev : a.m;
   if (gw >= nrows) return;
   const int row = a.rows ? a.rows[gw] : (int)gw;
+  if (a.qorig && a.qorig[row] < 0) return;  // padding row of a grouped layout
   const int tile = row / TQ;
   const int r = row - tile * TQ;
   int sb, se;
