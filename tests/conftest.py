@@ -10,7 +10,7 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (B300, sm_103a)")
-    config.addinivalue_line("markers", "slow: larger CPU cases (still minutes at most)")
+    config.addinivalue_line("markers", "slow: larger cases (a minute or two at most)")
 
 
 def pytest_collection_modifyitems(config, items):
