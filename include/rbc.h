@@ -71,6 +71,20 @@ typedef enum {
   RBC_F16 = 2   /* fp16 tensor-core pass (L2), FP32 re-rank, FP64 ties */
 } rbc_storage;
 
+/* Stage two of the exact search with bf16 / fp16 storage (L2).
+ *   RBC_PLAN_WINDOW: every query first bounds its k-th neighbour distance by
+ *     g = min(gamma_k, the k-th distance inside its nearest representative's
+ *     list); each surviving list is sorted by rho(x, r), so a query scans only
+ *     the window rho(q, r) - g <= rho(x, r) <= rho(q, r) + g of it (triangle
+ *     inequality).  Queries are grouped per representative, ordered by
+ *     rho(q, r) and cut into chunks of 128; the tensor-core pass emits every
+ *     point whose score can be within g, and the candidates are re-ranked.
+ *   RBC_PLAN_TILE_UNION: tiles of 128 queries ordered by nearest
+ *     representative search the union of their surviving lists, keeping a
+ *     top-c list per query, then re-rank and certify.
+ * FP32 and L1 searches always use the tile-union form on CUDA cores. */
+typedef enum { RBC_PLAN_WINDOW = 0, RBC_PLAN_TILE_UNION = 1 } rbc_plan;
+
 typedef struct rbc_index rbc_index; /* opaque; owned by the library */
 
 /* Build options.  Zero-initialised (or rbc_default_opts) means: seed 0,
@@ -81,7 +95,8 @@ typedef struct {
   int32_t storage;        /* rbc_storage used by the search and the build */
   int32_t rerank_c;       /* candidates per query kept by the low-precision
                              pass before re-ranking; 0 = automatic */
-  int32_t reserved;       /* must be 0 */
+  int32_t plan;           /* exact-search stage two with bf16 / fp16 storage:
+                             RBC_PLAN_WINDOW (0) or RBC_PLAN_TILE_UNION (1) */
   const int64_t* rep_ids; /* optional HOST array of n_r distinct ids in
                              [0, n), ascending; NULL = sample them */
 } rbc_opts;
@@ -206,8 +221,9 @@ int rbc_index_info(const rbc_index* idx, rbc_index_desc* out);
  * rbc_index_export -- copies the built structure to HOST arrays (each may be
  *   NULL to skip it): reps [n_r] representative ids (ascending);
  *   offsets [n_r + 1] start of each list in `members`; members
- *   [list_entries] database ids, list by list (exact mode: ascending id
- *   within a list; one-shot: (rho, id) order); psi [n_r] radii as float32
+ *   [list_entries] database ids, list by list, each list ordered by
+ *   (rho(x, r), id) (exact mode: rho as computed in FP32 by the build;
+ *   one-shot: in FP64); psi [n_r] radii as float32
  *   (exact mode: an upper bound of max_{x in L_r} rho(x, r) within the FP32
  *   rounding bound; one-shot: the FP64 s-th distance rounded to float).
  *   Synchronises the index's build stream.  Errors: RBC_ERR_ARG, RBC_ERR_CUDA.

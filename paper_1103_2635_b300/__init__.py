@@ -24,7 +24,7 @@ import os
 import numpy as np
 
 __all__ = [
-    "L2", "L1", "EXACT", "ONESHOT", "F32", "BF16", "F16",
+    "L2", "L1", "EXACT", "ONESHOT", "F32", "BF16", "F16", "PLAN_WINDOW", "PLAN_TILE_UNION",
     "RbcError", "bf_search", "bf_search_noalloc", "rbc_build", "rbc_search", "rbc_sample_reps",
     "RbcIndex", "last_stats", "set_timing", "library_path", "load",
 ]
@@ -32,6 +32,7 @@ __all__ = [
 L2, L1 = 0, 1
 EXACT, ONESHOT = 0, 1
 F32, BF16, F16 = 0, 1, 2
+PLAN_WINDOW, PLAN_TILE_UNION = 0, 1
 _STATUS = {0: "ok", -1: "invalid argument", -2: "out of device memory", -3: "CUDA error",
            -4: "device wait timed out", -5: "unsupported"}
 
@@ -48,7 +49,7 @@ class RbcError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("mode", ctypes.c_int32), ("storage", ctypes.c_int32),
-                ("rerank_c", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("rerank_c", ctypes.c_int32), ("plan", ctypes.c_int32),
                 ("rep_ids", ctypes.c_void_p)]
 
 
@@ -230,13 +231,15 @@ class RbcIndex:
 
 def rbc_build(X, n_r: int, metric: int = L2, seed: int = 0, mode: int = EXACT,
               storage: int = F32, s: int = 0, rerank_c: int = 0, rep_ids=None,
-              stream=None) -> RbcIndex:
-    """Build the Random Ball Cover of X (Sections 4-5 of the paper)."""
+              plan: int = PLAN_WINDOW, stream=None) -> RbcIndex:
+    """Build the Random Ball Cover of X (Sections 4-5 of the paper).  ``plan``
+    picks the exact search's stage two for bf16 / fp16 storage."""
     xp, xk, xdev = _arg(X, np.float32)
     n, d = xk.shape
     opts = _Opts()
     load().rbc_default_opts(ctypes.byref(opts))
     opts.seed, opts.mode, opts.storage, opts.rerank_c = seed, mode, storage, rerank_c
+    opts.plan = plan
     keep = None
     if rep_ids is not None:
         keep = np.ascontiguousarray(rep_ids, dtype=np.int64)

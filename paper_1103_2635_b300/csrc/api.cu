@@ -49,7 +49,7 @@ const char* last_error_text() { return g_err; }
 // ---------------------------------------------------------------------------
 struct rbc_index {
   int64_t n = 0;
-  int32_t d = 0, n_r = 0, s = 0, metric = 0, mode = 0, storage = 0, rerank_c = 0;
+  int32_t d = 0, n_r = 0, s = 0, metric = 0, mode = 0, storage = 0, rerank_c = 0, plan = 0;
   int64_t list_entries = 0;
   std::vector<void*> allocs;
   int64_t bytes = 0;
@@ -59,6 +59,7 @@ struct rbc_index {
   int* members = nullptr;     // [list_entries] database id of each entry
   float* X32 = nullptr;       // [list_entries, d] rows in list order
   float* psi = nullptr;       // [n_r] radius upper bounds
+  float* xdist = nullptr;     // [list_entries] FP32 rho(x, r) of each entry (exact mode)
   int dpad = 0;               // low-precision row length (multiple of 64)
   void* Xlp = nullptr;        // [list_entries, dpad]
   float* xnorm = nullptr;     // [list_entries] |x~|^2
@@ -657,9 +658,13 @@ int build_exact(rbc_index* ix, const float* Xdev, const std::vector<int64_t>& re
   ix->list_entries = n;
   RBC_TRY(ix->alloc(&ix->offsets, n_r + 1));
   RBC_TRY(ix->alloc(&ix->members, n));
+  // lists by owner, each ordered by (rho(x, r), id): the order the stage-two
+  // window search (Section 5.2's sorted lists) cuts ranges from
   int* scratch;
-  RBC_TRY(ar.alloc(&scratch, counting_sort_scratch_ints(n, n_r)));
-  RBC_TRY(launch_counting_sort(owner, n, n_r, ix->members, ix->offsets, scratch, st));
+  RBC_TRY(ix->alloc(&ix->xdist, n));
+  RBC_TRY(ar.alloc(&scratch, sort_lists_scratch_ints(n, n_r)));
+  RBC_TRY(launch_sort_lists(owner, odist, n, n_r, ix->members, ix->offsets, ix->xdist, scratch,
+                            st));
   RBC_TRY(ix->alloc(&ix->X32, n * d));
   RBC_TRY(launch_gather_rows(Xdev, nullptr, ix->members, n, d, ix->X32, st));
   // radii psi_r, inflated by the FP32 bound of the owner distances
@@ -921,54 +926,80 @@ int build_oneshot(rbc_index* ix, const float* Xdev, const std::vector<int64_t>& 
 
 // Stage two of the one-shot search: query rows of `Qsrc` (mq of them) against
 // the list of their representative rep_of[i]; results go to output row
-// orig[i] (i when orig is null).  Queries are grouped by representative and
+// orig[i] (i when orig is null).  Lists are [r s, (r + 1) s) of the index's
+// list storage, or [list_off[r], list_off[r + 1]) when list_off is given (the
+// exact index's own lists, used by the windowed search for gamma bounds).  Queries are grouped by representative and
 // every group padded to whole TQ-row tiles, so each tile is one dense item
 // against exactly one list.  Low-precision rows that fail certification are
 // searched again against their own list with the FP32 kernel.
-int oneshot_stage2(const rbc_index* ix, const float* Qsrc, int64_t mq, const int64_t* rep_of,
-                   const int* orig, bool lp, int k, int64_t* ids, float* dist, int* cnt,
-                   unsigned long long* points_sum, int64_t* items_total, Arena& ar,
-                   cudaStream_t st, bool marks) {
-  if (mq == 0) return RBC_OK;
-  const int d = ix->d, n_r = ix->n_r, s = ix->s, metric = ix->metric;
-  const int64_t entries = ix->list_entries;
-  const int sms = sm_count();
+// Queries grouped by representative: a counting sort by rep_of, each group
+// padded to whole TQ-row tiles (padded rows map to -1), the gathered FP32
+// query rows, and one work item per tile against its representative's list.
+struct Grouped {
+  int64_t max_tiles = 0, rows_cap = 0;
+  int* qout = nullptr;      // padded row -> output row (or -1)
+  int* tile_rep = nullptr;  // tile -> representative
+  float* Qp = nullptr;      // [rows_cap, d]
+  TileWork w{};             // the tiles as work items
+};
+
+int group_queries(const rbc_index* ix, const float* Qsrc, int64_t mq, const int64_t* rep_of,
+                  const int* orig, const int* list_off, unsigned long long* points_sum, Grouped& gq,
+                  Arena& ar, cudaStream_t st) {
+  const int d = ix->d, n_r = ix->n_r, s = ix->s;
   int *qperm, *qoff, *scratch;
   RBC_TRY(ar.alloc(&qperm, mq));
   RBC_TRY(ar.alloc(&qoff, n_r + 1));
   RBC_TRY(ar.alloc(&scratch, counting_sort_scratch_ints(mq, n_r)));
   RBC_TRY(launch_counting_sort(rep_of, mq, n_r, qperm, qoff, scratch, st));
-  const int64_t max_tiles = (mq + TQ - 1) / TQ + std::min<int64_t>(n_r, mq);
-  const int64_t rows_cap = max_tiles * TQ;
-  int *pad_cnt, *pad_off, *qsrc, *qout, *tile_rep;
+  gq.max_tiles = (mq + TQ - 1) / TQ + std::min<int64_t>(n_r, mq);
+  gq.rows_cap = gq.max_tiles * TQ;
+  int *pad_cnt, *pad_off, *qsrc;
   RBC_TRY(ar.alloc(&pad_cnt, n_r));
   RBC_TRY(ar.alloc(&pad_off, n_r + 1));
-  RBC_TRY(ar.alloc(&qsrc, rows_cap));
-  RBC_TRY(ar.alloc(&qout, rows_cap));
-  RBC_TRY(ar.alloc(&tile_rep, max_tiles));
-  RBC_CUDA(cudaMemsetAsync(qsrc, 0xff, rows_cap * sizeof(int), st));
-  RBC_CUDA(cudaMemsetAsync(qout, 0xff, rows_cap * sizeof(int), st));
-  RBC_TRY(launch_oneshot_layout(qoff, n_r, qperm, orig, pad_cnt, pad_off, qsrc, qout, tile_rep,
-                                st));
-  float* Qp;
-  RBC_TRY(ar.alloc(&Qp, rows_cap * d));
-  RBC_TRY(launch_gather_padded(Qsrc, qsrc, rows_cap, d, Qp, st));
+  RBC_TRY(ar.alloc(&qsrc, gq.rows_cap));
+  RBC_TRY(ar.alloc(&gq.qout, gq.rows_cap));
+  RBC_TRY(ar.alloc(&gq.tile_rep, gq.max_tiles));
+  RBC_CUDA(cudaMemsetAsync(qsrc, 0xff, gq.rows_cap * sizeof(int), st));
+  RBC_CUDA(cudaMemsetAsync(gq.qout, 0xff, gq.rows_cap * sizeof(int), st));
+  RBC_TRY(launch_oneshot_layout(qoff, n_r, qperm, orig, pad_cnt, pad_off, qsrc, gq.qout,
+                                gq.tile_rep, st));
+  RBC_TRY(ar.alloc(&gq.Qp, gq.rows_cap * d));
+  RBC_TRY(launch_gather_padded(Qsrc, qsrc, gq.rows_cap, d, gq.Qp, st));
   WorkItem* items;
   Seg* segs;
   int* nitems;
-  RBC_TRY(ar.alloc(&items, max_tiles));
-  RBC_TRY(ar.alloc(&segs, max_tiles));
+  RBC_TRY(ar.alloc(&items, gq.max_tiles));
+  RBC_TRY(ar.alloc(&segs, gq.max_tiles));
   RBC_TRY(ar.alloc(&nitems, 1));
-  RBC_TRY(launch_oneshot_items(pad_off, n_r, tile_rep, qoff, s, items, segs, nitems,
-                               (int)max_tiles, points_sum, st));
+  RBC_TRY(launch_oneshot_items(pad_off, n_r, gq.tile_rep, qoff, s, list_off, items, segs, nitems,
+                               (int)gq.max_tiles, points_sum, st));
+  gq.w = TileWork{};
+  gq.w.items = items;
+  gq.w.num_items_dev = nitems;
+  gq.w.num_items = (int)gq.max_tiles;
+  gq.w.segs = segs;
+  gq.w.m = gq.rows_cap;
+  gq.w.n = ix->list_entries;
+  return RBC_OK;
+}
+
+int oneshot_stage2(const rbc_index* ix, const float* Qsrc, int64_t mq, const int64_t* rep_of,
+                   const int* orig, bool lp, int k, int64_t* ids, float* dist, int* cnt,
+                   unsigned long long* points_sum, int64_t* items_total, Arena& ar,
+                   cudaStream_t st, bool marks, const int* list_off = nullptr) {
+  if (mq == 0) return RBC_OK;
+  const int d = ix->d, metric = ix->metric;
+  const int64_t entries = ix->list_entries;
+  const int sms = sm_count();
+  Grouped gq;
+  RBC_TRY(group_queries(ix, Qsrc, mq, rep_of, orig, list_off, points_sum, gq, ar, st));
+  const int64_t max_tiles = gq.max_tiles, rows_cap = gq.rows_cap;
+  float* Qp = gq.Qp;
+  int* qout = gq.qout;
+  int* tile_rep = gq.tile_rep;
+  const TileWork& w = gq.w;
   if (items_total) *items_total += max_tiles;
-  TileWork w{};
-  w.items = items;
-  w.num_items_dev = nitems;
-  w.num_items = (int)max_tiles;
-  w.segs = segs;
-  w.m = rows_cap;
-  w.n = entries;
   SelectArgs a{};
   a.nsub = 2;
   a.dense_splits = 1;  // slot of tile t is t
@@ -1063,7 +1094,7 @@ int oneshot_stage2(const rbc_index* ix, const float* Qsrc, int64_t mq, const int
     RBC_TRY(launch_oneshot_fallback_map(fb_rows, nfb, tile_rep, qout, frep, forig, st));
     RBC_TRY(launch_gather_rows(Qp, nullptr, fb_rows, nfb, d, Qf, st));
     RBC_TRY(oneshot_stage2(ix, Qf, nfb, frep, forig, false, k, ids, dist, cnt + 4, nullptr,
-                           nullptr, ar, st, false));
+                           nullptr, ar, st, false, list_off));
   }
   if (marks) tmark(4, st);
   return RBC_OK;
@@ -1091,6 +1122,176 @@ int search_oneshot_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k
   const bool lp = uses_lp(ix->storage, ix->metric) && ix->Xlp != nullptr;
   RBC_TRY(oneshot_stage2(ix, Qb, mb, nearest, nullptr, lp, k, ids, dist, cn.c, cn.sums + 1,
                          items_total, ar, st, true));
+  taccumulate();
+  return RBC_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// windowed exact search (Section 5.2 with lists sorted by rho(x, r))
+// ---------------------------------------------------------------------------
+int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, int64_t* ids,
+                        float* dist, const Counters& cn, int64_t* items_total, Arena& ar,
+                        cudaStream_t st) {
+  const int d = ix->d, n_r = ix->n_r;
+  const int64_t n = ix->list_entries;
+  const int sms = sm_count();
+  tmark(0, st);
+  // stage 1: BF(Q, R) keeping every distance; gamma_1, gamma_k, nearest
+  float* D;
+  RBC_TRY(ar.alloc(&D, mb * n_r));
+  const int64_t tiles = (mb + TQ - 1) / TQ;
+  TileWork w1{};
+  w1.num_items = (int)tiles;
+  w1.m = mb;
+  w1.n = n_r;
+  w1.dense_splits = 1;
+  w1.dense_chunk = n_r;
+  RBC_TRY(launch_bf_simt_store(Qb, ix->R32, d, ix->metric, w1, D, n_r,
+                               (int)std::min<int64_t>(tiles, (int64_t)sms * 2 * 16), st));
+  float *g1, *gk;
+  int64_t* nearest;
+  RBC_TRY(ar.alloc(&g1, mb));
+  RBC_TRY(ar.alloc(&gk, mb));
+  RBC_TRY(ar.alloc(&nearest, mb));
+  RBC_TRY(launch_row_stats(D, mb, n_r, k, g1, gk, nearest, st));
+  // device error flags of both tensor-core passes
+  uint32_t* dev_err;
+  RBC_TRY(ar.alloc(&dev_err, 1));
+  RBC_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(uint32_t), st));
+  // pass A: the k-th distance inside the nearest representative's own list
+  // (tensor-core top-C kernel over the grouped queries; the k-th smallest
+  // score of a row bounds its k-th distance)
+  float* own;
+  RBC_TRY(ar.alloc(&own, mb));
+  {
+    Grouped gq;
+    RBC_TRY(group_queries(ix, Qb, mb, nearest, nullptr, ix->offsets, nullptr, gq, ar, st));
+    LpQueries qa;
+    RBC_TRY(lp_queries(gq.Qp, gq.rows_cap, d, ix->dpad, ix->storage, qa, ar, st));
+    const int C = k <= 8 ? 8 : (k <= 16 ? 16 : 32);
+    float* ps;
+    int* pi;
+    RBC_TRY(ar.alloc(&ps, gq.max_tiles * TQ * 2 * C));
+    RBC_TRY(ar.alloc(&pi, gq.max_tiles * TQ * 2 * C));
+    LpMatrix QmA{qa.lp, qa.norm, gq.rows_cap, ix->dpad, ix->storage};
+    LpMatrix XmA{ix->Xlp, ix->xnorm, n, ix->dpad, ix->storage};
+    RBC_TRY(launch_bf_tc_topc(QmA, XmA, C, gq.w, TopOut{ps, pi, nullptr}, sms, st, dev_err));
+    RBC_TRY(launch_own_kth_lp(ps, pi, C, gq.qout, gq.rows_cap, k, gq.Qp, ix->X32, d, ix->metric,
+                              rerank_eps_host(d) + 8.0f * U32, own, st));
+  }
+  float* g;
+  RBC_TRY(ar.alloc(&g, mb));
+  RBC_TRY(launch_gbound(own, gk, mb, simt_eps(d), g, st));
+  // surviving (q, r) pairs binned by (r, bucket of rho(q, r))
+  const int NB = window_buckets();
+  const int64_t nbins = (int64_t)n_r * NB;
+  unsigned *rmin, *rmax;
+  int *qkept, *counts, *totals, *bin_off;
+  RBC_TRY(ar.alloc(&rmin, n_r));
+  RBC_TRY(ar.alloc(&rmax, n_r));
+  RBC_TRY(ar.alloc(&qkept, mb));
+  RBC_TRY(ar.alloc(&counts, window_pair_blocks(mb) * nbins));
+  RBC_TRY(ar.alloc(&totals, nbins));
+  RBC_TRY(ar.alloc(&bin_off, nbins + 1));
+  RBC_TRY(launch_window_pairs_count(D, mb, n_r, g, g1, ix->psi, simt_eps(d), rmin, rmax, qkept,
+                                    counts, totals, bin_off, st));
+  RBC_TRY(launch_sum_i32(qkept, mb, cn.sums, st));
+  int npairs = 0;
+  RBC_CUDA(cudaMemcpyAsync(&npairs, bin_off + nbins, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RBC_CUDA(cudaStreamSynchronize(st));
+  int* pq;
+  float* pd;
+  RBC_TRY(ar.alloc(&pq, npairs));
+  RBC_TRY(ar.alloc(&pd, npairs));
+  RBC_TRY(launch_window_pairs_scatter(D, mb, n_r, g, g1, ix->psi, simt_eps(d), rmin, rmax, counts,
+                                      bin_off, pq, pd, st));
+  // work items: chunks of TQ pairs, each with the union of its windows
+  const int max_items = (int)std::min<int64_t>((int64_t)npairs / TQ + n_r, INT32_MAX);
+  int *ccount, *choff;
+  EmitItem* items;
+  RBC_TRY(ar.alloc(&ccount, n_r));
+  RBC_TRY(ar.alloc(&choff, n_r + 1));
+  RBC_TRY(ar.alloc(&items, std::max(max_items, 1)));
+  RBC_TRY(launch_window_items(bin_off, NB, n_r, pq, pd, g, ix->offsets, ix->xdist, simt_eps(d),
+                              2.0f * rerank_eps_host(d) + 8.0f * U32, ccount, choff, max_items,
+                              items, cn.sums + 1, st));
+  *items_total += max_items;
+  // thresholds, then the tensor-core pass emitting candidates
+  LpQueries ql;
+  RBC_TRY(lp_queries(Qb, mb, d, ix->dpad, ix->storage, ql, ar, st));
+  float* thr;
+  RBC_TRY(ar.alloc(&thr, mb));
+  RBC_TRY(launch_score_threshold(g, ql.norm, ql.err, ix->lp_max, d, mb, thr, st));
+  float* cs;
+  int *cr, *cc;
+  RBC_TRY(ar.alloc(&cs, mb * CAND_CAP));
+  RBC_TRY(ar.alloc(&cr, mb * CAND_CAP));
+  RBC_TRY(ar.alloc(&cc, mb));
+  RBC_CUDA(cudaMemsetAsync(cc, 0, mb * sizeof(int), st));
+  LpMatrix Qm{ql.lp, ql.norm, mb, ix->dpad, ix->storage};
+  LpMatrix Xm{ix->Xlp, ix->xnorm, n, ix->dpad, ix->storage};
+  EmitOut eo{thr, cs, cr, cc, CAND_CAP};
+  tmark(1, st);
+  RBC_TRY(launch_bf_tc_emit(Qm, Xm, items, choff + n_r, max_items, pq, eo, sms, st, dev_err));
+  tmark(2, st);
+  // exact re-rank of the candidates; overflowing queries go to the FP32 re-search
+  int* fb_rows;
+  int* lc;
+  RBC_TRY(ar.alloc(&fb_rows, mb));
+  RBC_TRY(ar.alloc(&lc, 8));
+  RBC_CUDA(cudaMemsetAsync(lc, 0, 8 * sizeof(int), st));
+  CandSelectArgs a{};
+  a.cand_score = cs;
+  a.cand_row = cr;
+  a.cand_cnt = cc;
+  a.cap = CAND_CAP;
+  a.m = mb;
+  a.Q32 = Qb;
+  a.d = d;
+  a.metric = ix->metric;
+  a.q_lpnorm = ql.norm;
+  a.q_err = ql.err;
+  a.x_err_max_bits = ix->lp_max;
+  a.x_norm_max_bits = ix->lp_max + 1;
+  a.X32 = ix->X32;
+  a.xid = ix->members;
+  a.k = k;
+  a.c_out = std::min(k + 1, MAX_C);
+  a.out_ids = ids;
+  a.out_dist = dist;
+  a.fallback_rows = fb_rows;
+  a.counters = lc;
+  RBC_TRY(launch_select_cands(a, st));
+  tmark(3, st);
+  RBC_TRY(launch_add_ints(cn.c, lc, 3, st));
+  int nfb = 0;
+  uint32_t herr = 0;
+  RBC_CUDA(cudaMemcpyAsync(&nfb, lc, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RBC_CUDA(cudaMemcpyAsync(&herr, dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  RBC_CUDA(cudaStreamSynchronize(st));
+  if (herr) {
+    set_error("windowed stage two reported device error flags 0x%x", herr);
+    return (herr & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
+  }
+  if (nfb > 0) {
+    // queries whose candidate buffer overflowed: dense tensor-core search of
+    // the whole index with the widest lists (certified, FP32 behind it)
+    DbView db;
+    db.X32 = ix->X32;
+    db.xid = ix->members;
+    db.rows = n;
+    db.Xlp = ix->Xlp;
+    db.xnorm = ix->xnorm;
+    db.dpad = ix->dpad;
+    db.lp_max = ix->lp_max;
+    float* Qf;
+    RBC_TRY(ar.alloc(&Qf, (int64_t)nfb * d));
+    RBC_TRY(launch_gather_rows(Qb, nullptr, fb_rows, nfb, d, Qf, st));
+    RBC_TRY(bf_dense_lp(Qf, nfb, db, d, k, ix->storage, MAX_C, ids, dist, cn.c + 4, ar, st,
+                        fb_rows, 1));
+  }
+  tmark(4, st);
   taccumulate();
   return RBC_OK;
 }
@@ -1234,8 +1435,10 @@ int rbc_build(const float* X, int64_t n, int32_t d, int32_t n_r, int32_t s, int3
     set_error("rbc_build: one-shot needs 1 <= s <= n (s=%d)", s);
     return RBC_ERR_ARG;
   }
-  if (o.rerank_c < 0 || o.rerank_c > MAX_C || o.reserved != 0) {
-    set_error("rbc_build: rerank_c must be in [0, %d] and reserved 0", MAX_C);
+  if (o.rerank_c < 0 || o.rerank_c > MAX_C ||
+      (o.plan != RBC_PLAN_WINDOW && o.plan != RBC_PLAN_TILE_UNION)) {
+    set_error("rbc_build: rerank_c must be in [0, %d] and plan RBC_PLAN_WINDOW or "
+              "RBC_PLAN_TILE_UNION", MAX_C);
     return RBC_ERR_ARG;
   }
   if (d > MAX_D) {
@@ -1266,6 +1469,7 @@ int rbc_build(const float* X, int64_t n, int32_t d, int32_t n_r, int32_t s, int3
   ix->mode = o.mode;
   ix->storage = o.storage;
   ix->rerank_c = o.rerank_c;
+  ix->plan = o.plan;
   int rc;
   {
     Arena ar(st);
@@ -1325,6 +1529,9 @@ int rbc_search(const rbc_index* ix, const float* Q, int64_t m, int32_t k, int64_
     if (ix->mode == RBC_ONESHOT)
       RBC_TRY(search_oneshot_batch(ix, io.Qdev + b0 * ix->d, mb, k, io.ids_dev + b0 * k,
                                    io.dist_dev + b0 * k, cn, &items, bar, st));
+    else if (ix->plan == RBC_PLAN_WINDOW && uses_lp(ix->storage, ix->metric) && ix->Xlp)
+      RBC_TRY(search_window_batch(ix, io.Qdev + b0 * ix->d, mb, k, io.ids_dev + b0 * k,
+                                  io.dist_dev + b0 * k, cn, &items, bar, st));
     else
       RBC_TRY(search_exact_batch(ix, io.Qdev + b0 * ix->d, mb, k, io.ids_dev + b0 * k,
                                  io.dist_dev + b0 * k, cn, &items, bar, st));

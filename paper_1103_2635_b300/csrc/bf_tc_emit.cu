@@ -1,0 +1,430 @@
+// Tensor-core windowed BF with candidate emission (sm_103a), the stage two of
+// the windowed exact search (Section 5.2 with sorted lists).
+//
+// A work item is (a chunk of up to 128 queries that all kept representative
+// r, a window [x_begin, x_end) of r's sorted list).  The queries of a chunk
+// are arbitrary rows of the query matrix, so they are gathered, not tiled:
+// a dedicated warp copies them with 16-byte cp.async into the 128-byte-swizzled
+// K-major layout the MMA reads (two query stages, so the next item's rows
+// arrive while the current one computes).  Database windows are contiguous
+// rows and come by TMA as in the top-C kernel.
+//
+// Every query q carries a score threshold T(q) (window.cu): no point whose
+// score |x~|^2 - 2 q~.x~ exceeds T(q) can be within g(q) of q, the bound of
+// its k-th neighbour distance.  So the epilogue keeps no lists at all: per
+// 32-column chunk it forms the scores, takes their minimum, and only when
+// that minimum is <= T(q) appends the qualifying (score, row) pairs to q's
+// candidate buffer in global memory.  The candidates are re-ranked exactly
+// afterwards (select.cu).
+//
+//   warp 0      TMA producer: database tiles of BN rows + their norms
+//   warp 1      tensor-memory allocation, MMA issue (M = 128, N = BN, K = 16)
+//   warp 2      query gather (cp.async), per-row query id and threshold
+//   warp 3      idle (keeps the epilogue warps aligned to TMEM lane quarters)
+//   warps 4-    epilogue: TMEM lane quarter (warp % 4) x column slice; with
+//               no candidate lists to keep, a thread needs ~90 registers, so
+//               up to 16 epilogue warps (four per scheduler) hide the TMEM
+//               load and arithmetic latencies
+// Every mbarrier wait is bounded (2 s); on expiry the kernel raises
+// DEV_ERR_TIMEOUT, stops issuing work, drains its copies and frees TMEM.
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tc_common.cuh"
+
+namespace rbc {
+
+namespace {
+
+using namespace tc;
+
+constexpr int E_GATHER = 2;     // query-gather warp
+constexpr int E_EPI0 = 4;       // first epilogue warp (warp 3 idles)
+constexpr int QSTAGES = 2;      // query stages
+
+// Epilogue parts: the tile's columns are split into NPART slices of BN/NPART
+// (at least 32) columns; each (TMEM lane quarter, slice) is one warp.
+template <int BN>
+struct EpiShape {
+  static constexpr int NPART = BN / 32 < 4 ? BN / 32 : 4;
+  static constexpr int NEPI = 4 * NPART;             // epilogue warps
+  static constexpr int THREADS = 32 * (E_EPI0 + NEPI);
+  static constexpr int COLS = BN / NPART;            // columns per thread per tile
+  static constexpr int CHUNKS = COLS / 32;           // 32-column TMEM loads per tile
+};
+
+struct EmitParams {
+  const EmitItem* items;
+  const int* num_items_dev;
+  int max_items;
+  const int* pair_q;
+  const uint8_t* qlp;  // [q_rows, dpad] 16-bit rows
+  int64_t q_row_bytes;
+  const float* xnorm;  // [rows + pad]
+  EmitOut out;
+  uint32_t* dev_err;
+};
+
+template <int KB, int BN, int S, int NR>
+struct EmitSmem {
+  static constexpr int NBUF = (512 / BN) < 4 ? (512 / BN) : 4;  // TMEM accumulator buffers
+  static constexpr int Q_BYTES = KB * BM * 128;
+  static constexpr int X_STAGE = KB * BN * 128;
+  static constexpr int NORM_STAGE = BN * 4;
+  static constexpr int OFF_Q = 0;
+  static constexpr int OFF_X = OFF_Q + QSTAGES * Q_BYTES;
+  static constexpr int OFF_NORM = OFF_X + S * X_STAGE;
+  static constexpr int OFF_ROWQ = OFF_NORM + NR * NORM_STAGE;  // [QSTAGES][BM] query id or -1
+  static constexpr int OFF_ROWT = OFF_ROWQ + QSTAGES * BM * 4;  // [QSTAGES][BM] threshold
+  static constexpr int OFF_BAR = OFF_ROWT + QSTAGES * BM * 4;
+  // full[S], empty[S], nfull[NR], nempty[NR], tfull[NBUF], tempty[NBUF], qfull[QS], qempty[QS]
+  static constexpr int NBAR = 2 * S + 2 * NR + 2 * NBUF + 2 * QSTAGES;
+  static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;  // tmem base, abort flag
+  static constexpr int BYTES = OFF_MISC + 16;
+  static constexpr int ALLOC = BYTES + 1024;  // slack for 1024-byte alignment
+  static_assert(ALLOC <= 232448, "shared memory budget");
+  static_assert(OFF_X % 1024 == 0 && X_STAGE % 1024 == 0, "swizzled tiles need 1024-byte alignment");
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
+               "l"(reinterpret_cast<uint64_t>(src))
+               : "memory");
+}
+__device__ __forceinline__ void st_shared_zero16(uint32_t dst) {
+  asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(dst), "r"(0) : "memory");
+}
+
+template <int KB, int BN, int S, int NR>
+__global__ void __launch_bounds__(EpiShape<BN>::THREADS, 1)
+bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32_t idesc) {
+  using L = EmitSmem<KB, BN, S, NR>;
+  using E = EpiShape<BN>;
+  constexpr int E_NEPI = E::NEPI;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~(uintptr_t)1023);
+  uint8_t* sQ = smem + L::OFF_Q;
+  uint8_t* sX = smem + L::OFF_X;
+  float* sNorm = reinterpret_cast<float*>(smem + L::OFF_NORM);
+  int* sRowQ = reinterpret_cast<int*>(smem + L::OFF_ROWQ);
+  float* sRowT = reinterpret_cast<float*>(smem + L::OFF_ROWT);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
+  constexpr int NBUF = L::NBUF;
+  uint64_t* full = bars;
+  uint64_t* empty = full + S;
+  uint64_t* nfull = empty + S;
+  uint64_t* nempty = nfull + NR;
+  uint64_t* tfull = nempty + NR;
+  uint64_t* tempty = tfull + NBUF;
+  uint64_t* qfull = tempty + NBUF;
+  uint64_t* qempty = qfull + QSTAGES;
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(smem + L::OFF_MISC);
+  volatile int* sAbort = reinterpret_cast<volatile int*>(smem + L::OFF_MISC + 4);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int r = 0; r < NR; ++r) {
+      mbar_init(&nfull[r], 1);
+      mbar_init(&nempty[r], E_NEPI);
+    }
+    for (int b = 0; b < NBUF; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], E_NEPI);
+    }
+    for (int q = 0; q < QSTAGES; ++q) {
+      mbar_init(&qfull[q], 32);              // every gather lane
+      mbar_init(&qempty[q], 1 + E_NEPI);     // MMA commit + every epilogue warp
+    }
+    *sAbort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(sTmem)),
+                 "r"(NBUF * BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *sTmem;
+
+  int n_items = p.num_items_dev ? *p.num_items_dev : p.max_items;
+  if (n_items > p.max_items) n_items = p.max_items;
+
+  if (warp == 0) {
+    // ---------------- TMA producer (database windows) ----------------
+    uint32_t it = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
+      const EmitItem e = p.items[item];
+      if (e.x_end <= e.x_begin) continue;
+      for (int x = e.x_begin & ~3; x < e.x_end; x += BN, ++it) {
+        const int s = it % S;
+        const uint32_t ph = (it / S) & 1;
+        const int r = it % NR;
+        const uint32_t nph = (it / NR) & 1;
+        bool got = mbar_wait(&empty[s], ph ^ 1, sAbort, p.dev_err) &&
+                   mbar_wait(&nempty[r], nph ^ 1, sAbort, p.dev_err);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        if (lane == 0) {
+          mbar_arrive_expect_tx(&full[s], L::X_STAGE);
+#pragma unroll
+          for (int kb = 0; kb < KB; ++kb)
+            tma_load_2d(sX + s * L::X_STAGE + kb * BN * 128, &xmap, &full[s], kb * 64, x);
+          mbar_arrive_expect_tx(&nfull[r], L::NORM_STAGE);
+          bulk_load(sNorm + r * BN, p.xnorm + x, L::NORM_STAGE, &nfull[r]);
+        }
+        __syncwarp();
+      }
+    }
+    if (lane == 0) {
+      for (uint32_t j = (it > (uint32_t)S ? it - S : 0); j < it; ++j)
+        mbar_wait(&full[j % S], (j / S) & 1, sAbort, p.dev_err);
+      for (uint32_t j = (it > (uint32_t)NR ? it - NR : 0); j < it; ++j)
+        mbar_wait(&nfull[j % NR], (j / NR) & 1, sAbort, p.dev_err);
+    }
+  } else if (warp == E_GATHER) {
+    // ---------------- query gather ----------------
+    uint32_t qi = 0;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+      const EmitItem e = p.items[item];
+      if (e.x_end <= e.x_begin) continue;
+      const int qs = qi % QSTAGES;
+      const uint32_t qph = (qi / QSTAGES) & 1;
+      if (!__all_sync(0xffffffffu, mbar_wait(&qempty[qs], qph ^ 1, sAbort, p.dev_err))) break;
+      const uint32_t qbase = smem_u32(sQ + qs * L::Q_BYTES);
+#pragma unroll
+      for (int t = 0; t < BM / 32; ++t) {
+        const int row = lane + 32 * t;
+        const int src = row < e.nq ? p.pair_q[e.pair_begin + row] : -1;
+        sRowQ[qs * BM + row] = src;
+        sRowT[qs * BM + row] = src >= 0 ? p.out.thr[src] : -INFINITY;
+        const uint8_t* g = p.qlp + (int64_t)(src >= 0 ? src : 0) * p.q_row_bytes;
+#pragma unroll
+        for (int kb = 0; kb < KB; ++kb)
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const uint32_t dst = qbase + kb * BM * 128 + row * 128 + ((c ^ (row & 7)) << 4);
+            if (src >= 0)
+              cp_async16(dst, g + kb * 128 + c * 16);
+            else
+              st_shared_zero16(dst);
+          }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      // this lane's rows are in shared memory: make them visible to the
+      // tensor core (async proxy), then release the stage
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&qfull[qs]);
+      ++qi;
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    uint32_t it = 0, qi = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
+      const EmitItem e = p.items[item];
+      if (e.x_end <= e.x_begin) continue;
+      const int qs = qi % QSTAGES;
+      const uint32_t qph = (qi / QSTAGES) & 1;
+      if (!__all_sync(0xffffffffu, mbar_wait(&qfull[qs], qph, sAbort, p.dev_err))) break;
+      for (int x = e.x_begin & ~3; x < e.x_end; x += BN, ++it) {
+        const int s = it % S;
+        const uint32_t ph = (it / S) & 1;
+        const int buf = it % NBUF;
+        const uint32_t aph = (it / NBUF) & 1;
+        bool got = mbar_wait(&full[s], ph, sAbort, p.dev_err) &&
+                   mbar_wait(&tempty[buf], aph ^ 1, sAbort, p.dev_err);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        if (lane == 0) {
+          const uint32_t d_tmem = tmem + buf * BN;
+          const uint32_t qa = smem_u32(sQ + qs * L::Q_BYTES);
+          const uint32_t xb = smem_u32(sX + s * L::X_STAGE);
+#pragma unroll
+          for (int kb = 0; kb < KB; ++kb)
+#pragma unroll
+            for (int k16 = 0; k16 < 4; ++k16) {
+              uint64_t ad = smem_desc_sw128(qa + kb * BM * 128 + k16 * 32);
+              uint64_t bd = smem_desc_sw128(xb + kb * BN * 128 + k16 * 32);
+              mma_f16(d_tmem, ad, bd, idesc, (kb | k16) != 0);
+            }
+          mma_commit(&empty[s]);
+          mma_commit(&tfull[buf]);
+        }
+        __syncwarp();
+      }
+      if (lane == 0) mma_commit(&qempty[qs]);
+      __syncwarp();
+      ++qi;
+    }
+  } else if (warp >= E_EPI0) {
+    // ---------------- epilogue ----------------
+    // Warp w reads TMEM lane quarter w % 4 (its query rows) and column slice
+    // (w - E_EPI0) / 4 of each tile: all of its CHUNKS loads are issued before
+    // one wait, then the accumulator is handed back and the scores formed.
+    const int quarter = warp & 3;
+    const int part = (warp - E_EPI0) >> 2;
+    const int row = quarter * 32 + lane;
+    constexpr int COLS = E::COLS;
+    constexpr int CH = E::CHUNKS;
+    uint32_t it = 0, qi = 0;
+    bool ok = true;
+    const int cap = p.out.cap;
+    for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
+      const EmitItem e = p.items[item];
+      if (e.x_end <= e.x_begin) continue;
+      const int qs = qi % QSTAGES;
+      const uint32_t qph = (qi / QSTAGES) & 1;
+      if (!__all_sync(0xffffffffu, mbar_wait(&qfull[qs], qph, sAbort, p.dev_err))) break;
+      const int myq = sRowQ[qs * BM + row];
+      const float myT = sRowT[qs * BM + row];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&qempty[qs]);
+      ++qi;
+      float* cs = p.out.cand_score + (int64_t)(myq >= 0 ? myq : 0) * cap;
+      int* cr = p.out.cand_row + (int64_t)(myq >= 0 ? myq : 0) * cap;
+      int* cc = p.out.cand_cnt + (myq >= 0 ? myq : 0);
+      for (int x = e.x_begin & ~3; x < e.x_end; x += BN, ++it) {
+        const int r = it % NR;
+        const uint32_t nph = (it / NR) & 1;
+        const int buf = it % NBUF;
+        const uint32_t aph = (it / NBUF) & 1;
+        bool got = mbar_wait(&nfull[r], nph, sAbort, p.dev_err) &&
+                   mbar_wait(&tfull[buf], aph, sAbort, p.dev_err);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + buf * BN + part * COLS;
+        uint32_t raw[CH][32];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) tmem_ld_x32(tbase + c * 32, raw[c]);
+        tmem_wait_ld();
+        // every column of this slice is in registers: hand the accumulator back
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
+        const float* nrm = sNorm + r * BN + part * COLS;
+        const int lo = e.x_begin - x - part * COLS;  // first valid column of the slice
+        const int hi = e.x_end - x - part * COLS;    // one past the last valid column
+        const bool partial = lo > 0 || hi < COLS;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          float u[32];
+          const float4* n4 = reinterpret_cast<const float4*>(nrm + c * 32);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float4 nn = n4[j];
+            fma2(u[4 * j], u[4 * j + 1], __uint_as_float(raw[c][4 * j]),
+                 __uint_as_float(raw[c][4 * j + 1]), -2.0f, nn.x, nn.y);
+            fma2(u[4 * j + 2], u[4 * j + 3], __uint_as_float(raw[c][4 * j + 2]),
+                 __uint_as_float(raw[c][4 * j + 3]), -2.0f, nn.z, nn.w);
+          }
+          if (partial) {
+            // columns outside the window become NaN: never <= a threshold
+            // (not even an infinite one), and ignored by min.f32
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int col = c * 32 + j;
+              if (col < lo || col >= hi) u[j] = __int_as_float(0x7fffffff);
+            }
+          }
+          if (min_of32(u) <= myT) {
+            const int cb = x + part * COLS + c * 32;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              if (u[j] <= myT) {
+                const int pos = atomicAdd(cc, 1);
+                if (pos < cap) {
+                  cs[pos] = u[j];
+                  cr[pos] = cb + j;
+                }
+              }
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&nempty[r]);
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NBUF * BN)
+                 : "memory");
+  }
+}
+
+template <int KB, int BN, int S, int NR>
+int launch_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
+                const int* num_items_dev, int max_items, const int* pair_q, const EmitOut& out,
+                int grid, cudaStream_t st, uint32_t* dev_err) {
+  using L = EmitSmem<KB, BN, S, NR>;
+  CUtensorMap xmap;
+  RBC_TRY_TC(encode_map(&xmap, Xm.data, Xm.rows, Xm.dpad, Xm.storage, BN));
+  auto kern = bf_tc_emit_kernel<KB, BN, S, NR>;
+  RBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC));
+  EmitParams p{items,   num_items_dev, max_items, pair_q, static_cast<const uint8_t*>(Qm.data),
+               (int64_t)Qm.dpad * 2, Xm.norm, out, dev_err};
+  const uint32_t idesc = idesc_f16(Qm.storage == RBC_BF16 ? 1 : 0, BM, BN);
+  kern<<<grid, EpiShape<BN>::THREADS, L::ALLOC, st>>>(xmap, p, idesc);
+  ++t_launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, kern);
+    set_error("bf_tc_emit_kernel<KB=%d,BN=%d,S=%d> launch failed: %s (regs %d, local %zu, "
+              "dynamic smem %d)",
+              KB, BN, S, cudaGetErrorString(e), fa.numRegs, fa.localSizeBytes, L::ALLOC);
+    return RBC_ERR_CUDA;
+  }
+  return RBC_OK;
+}
+
+}  // namespace
+
+int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
+                      const int* num_items_dev, int max_items, const int* pair_q,
+                      const EmitOut& out, int grid, cudaStream_t st, uint32_t* dev_err) {
+  if (!tc_available()) {
+    set_error("tensor-core BF kernel needs an sm_103 device");
+    return RBC_ERR_UNSUPPORTED;
+  }
+  if (Qm.dpad != Xm.dpad || Qm.storage != Xm.storage) {
+    set_error("tensor-core BF: operand layouts differ");
+    return RBC_ERR_ARG;
+  }
+  if (max_items <= 0) return RBC_OK;
+  switch (Qm.dpad / 64) {
+    case 1: return launch_emit<1, 256, 4, 8>(Qm, Xm, items, num_items_dev, max_items, pair_q, out, grid, st, dev_err);
+    case 2: return launch_emit<2, 128, 3, 8>(Qm, Xm, items, num_items_dev, max_items, pair_q, out, grid, st, dev_err);
+    case 3: return launch_emit<3, 64, 3, 8>(Qm, Xm, items, num_items_dev, max_items, pair_q, out, grid, st, dev_err);
+    case 4: return launch_emit<4, 64, 2, 4>(Qm, Xm, items, num_items_dev, max_items, pair_q, out, grid, st, dev_err);
+    default: break;
+  }
+  set_error("tensor-core BF: padded dimension %d unsupported", Qm.dpad);
+  return RBC_ERR_UNSUPPORTED;
+}
+
+}  // namespace rbc

@@ -71,6 +71,29 @@ struct TopList {
   }
 };
 
+// Largest low-precision score |x~|^2 - 2 q~.x~ that a point within distance
+// g of q can have: (g + |q - q~| + max |x - x~|)^2 - |q~|^2 + E_f, with E_f the
+// FP32 evaluation bound (d + 4) 2^-19 (|q~| + max |x~|)^2 (doubled), rounded up.
+__host__ __device__ __forceinline__ float score_bound(float g, float qn, float qerr, float xerr,
+                                             float xnmax, int d) {
+  if (!(g < INFINITY)) return INFINITY;
+  const float G = (g + qerr + xerr) * (1.0f + 4.8e-7f);
+  const float span = (sqrtf(qn) + xnmax) * (1.0f + 4.8e-7f);
+  const float ef = 2.0f * (float)(d + 4) * 1.9073486e-06f * span * span;
+  return (G * G * (1.0f + 4.8e-7f) - qn * (1.0f - 4.8e-7f) + ef) * (1.0f + 4.8e-7f) + 1e-30f;
+}
+
+// Largest distance a point with low-precision score s can have from q:
+// sqrt(s + |q~|^2 + E_f) + |q - q~| + max |x - x~|, rounded up.
+__host__ __device__ __forceinline__ float dist_upper(float s, float qn, float qerr, float xerr, float xnmax,
+                                            int d) {
+  if (!(s < INFINITY)) return INFINITY;
+  const float span = (sqrtf(qn) + xnmax) * (1.0f + 4.8e-7f);
+  const float ef = 2.0f * (float)(d + 4) * 1.9073486e-06f * span * span;
+  const float t = (s + qn * (1.0f + 4.8e-7f) + ef) * (1.0f + 4.8e-7f);
+  return (sqrtf(fmaxf(t, 0.0f)) * (1.0f + 4.8e-7f) + qerr + xerr) * (1.0f + 4.8e-7f);
+}
+
 // Device-side error flags (bit mask), read back by the host after a call.
 enum : uint32_t {
   DEV_ERR_TIMEOUT = 1u,      // a bounded wait gave up

@@ -49,6 +49,30 @@ bool tc_available();
 int launch_bf_tc_topc(const LpMatrix& Qm, const LpMatrix& Xm, int C, const TileWork& w,
                       const TopOut& out, int grid, cudaStream_t st, uint32_t* dev_err);
 
+// ---- windowed stage two: per (representative, query chunk) work items ----
+// Queries pair_q[pair_begin .. pair_begin + nq) (rows of the query buffer)
+// against database rows [x_begin, x_end) of the list-ordered matrix.
+struct EmitItem {
+  int32_t pair_begin;
+  int32_t nq;
+  int32_t x_begin;
+  int32_t x_end;
+};
+
+// Candidate emission: every (query, row) pair whose score is <= thr[query]
+// is appended to the query's candidate buffer (score, list-ordered row);
+// cand_cnt counts every emission, so a count above cap marks an overflow.
+struct EmitOut {
+  const float* thr;  // [m] score threshold per query
+  float* cand_score; // [m, cap]
+  int* cand_row;     // [m, cap]
+  int* cand_cnt;     // [m]
+  int cap;
+};
+int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
+                      const int* num_items_dev, int max_items, const int* pair_q,
+                      const EmitOut& out, int grid, cudaStream_t st, uint32_t* dev_err);
+
 // ---- merge + re-rank + certification ----
 struct SelectArgs {
   const float* part_score;
@@ -83,6 +107,75 @@ struct SelectArgs {
 };
 int launch_select(const SelectArgs& a, cudaStream_t st);
 
+// Candidate buffers of the windowed search -> exact k-NN per query.
+constexpr int CAND_CAP = 2048;  // candidates per query
+struct CandSelectArgs {
+  const float* cand_score;  // [m, cap]
+  const int* cand_row;      // [m, cap] list-ordered database rows
+  const int* cand_cnt;      // [m] emissions (may exceed cap: overflow)
+  int cap;
+  int64_t m;
+  const float* Q32;  // [m, d] queries FP32
+  int d;
+  int metric;
+  const float* q_lpnorm;            // [m] |q~|^2
+  const float* q_err;               // [m] |q - q~| rounded up
+  const unsigned* x_err_max_bits;   // max |x - x~| rounded up (float bits)
+  const unsigned* x_norm_max_bits;  // max |x~| rounded up (float bits)
+  const float* X32;  // list-ordered rows FP32
+  const int* xid;    // row -> original id
+  int k;
+  int c_out;
+  int64_t* out_ids;  // [m, k]
+  float* out_dist;
+  int* fallback_rows;  // queries sent to the FP32 re-search are appended here
+  int* counters;       // [0] such queries, [1] fp64 ties, [2] boundary ties
+};
+int launch_select_cands(const CandSelectArgs& a, cudaStream_t st);
+
+
+// ---- windowed exact search (window.cu) ----
+// g[q] = min(gk[q] (1 + rel_rep) rounded up, own[q]): an upper bound of q's
+// k-th nearest-neighbour distance
+int launch_gbound(const float* own, const float* gk, int64_t m, float rel_rep, float* g,
+                  cudaStream_t st);
+// own[qout[row]] = the k-th smallest FP32 distance of grouped row `row` from
+// the two sorted sub-lists of the FP32 tile kernel ([tile][TQ][2][C]),
+// rounded up by rel (INF if fewer than k)
+int launch_own_kth(const float* ps, int C, const int* qout, int64_t rows, int k, int metric,
+                   float rel, float* own, cudaStream_t st);
+// the same from the tensor-core top-C lists ([tile][TQ][2][C] unsorted
+// low-precision scores and list-ordered rows, C <= 32): the largest FP32
+// distance of the k best-scored rows, rounded up by rel (Q32: the grouped
+// query rows)
+int launch_own_kth_lp(const float* ps, const int* pi, int C, const int* qout, int64_t rows,
+                      int k, const float* Q32, const float* X32, int d, int metric, float rel,
+                      float* own, cudaStream_t st);
+// Kept (q, r) pairs binned by (r, bucket of rho(q, r)), window_buckets() per
+// r: rmin/rmax [n_r] (float bits), q_kept [m], counts
+// [window_pair_blocks(m)][n_r nb] (per query block, then its prefix within
+// each bin), totals [n_r nb], bin_off [n_r nb + 1]; then the pairs
+// themselves (pair_q, pair_d).
+int window_buckets();
+int64_t window_pair_blocks(int64_t m);
+int launch_window_pairs_count(const float* D, int64_t m, int n_r, const float* g,
+                              const float* g1, const float* psi_plus, float rel, unsigned* rmin,
+                              unsigned* rmax, int* q_kept, int* counts, int* totals, int* bin_off,
+                              cudaStream_t st);
+int launch_window_pairs_scatter(const float* D, int64_t m, int n_r, const float* g,
+                                const float* g1, const float* psi_plus, float rel,
+                                const unsigned* rmin, const unsigned* rmax, int* counts,
+                                const int* bin_off, int* pair_q, float* pair_d, cudaStream_t st);
+// chunks of TQ pairs per representative -> items (the chunk's window in the
+// sorted list); stats[0] += window rows, stats[1] += query x row pairs
+int launch_window_items(const int* bin_off, int nb, int n_r, const int* pair_q,
+                        const float* pair_d, const float* g, const int* offsets,
+                        const float* xdist, float rel, float relx, int* chunk_counts,
+                        int* chunk_off, int max_items, EmitItem* items,
+                        unsigned long long* stats, cudaStream_t st);
+int launch_score_threshold(const float* g, const float* qnorm, const float* qerr,
+                           const unsigned* lp_max, int d, int64_t m, float* thr,
+                           cudaStream_t st);
 
 // ---- one-shot RBC (oneshot.cu) ----
 // candidate capacity per representative for a list of s points
@@ -105,11 +198,12 @@ int launch_oneshot_refine(const float* X, const float* R, int d, int metric, int
 int launch_oneshot_layout(const int* qoff, int n_r, const int* qperm, const int* orig,
                           int* counts_scratch, int* pad_off, int* qsrc_pad, int* qout_pad,
                           int* tile_rep, cudaStream_t st);
-// one work item per padded tile: its rows against list r = [r s, (r + 1) s);
-// adds (tiles x s) to *points_sum when given
+// one work item per padded tile: its rows against list r = [r s, (r + 1) s),
+// or [list_off[r], list_off[r + 1]) when list_off is given; adds each tile's
+// list length to *points_sum when given
 int launch_oneshot_items(const int* pad_off, int n_r, const int* tile_rep, const int* qoff, int s,
-                         WorkItem* items, Seg* segs, int* num_items, int max_tiles,
-                         unsigned long long* points_sum, cudaStream_t st);
+                         const int* list_off, WorkItem* items, Seg* segs, int* num_items,
+                         int max_tiles, unsigned long long* points_sum, cudaStream_t st);
 // out[i] = Q[src[i]] (zero row where src[i] < 0), i < rows
 int launch_gather_padded(const float* Q, const int* src, int64_t rows, int d, float* out,
                          cudaStream_t st);
@@ -140,6 +234,12 @@ int launch_map_rows(const int* rows, const int* n_dev, int n, const int* qorig, 
 int64_t counting_sort_scratch_ints(int64_t n, int nbins);
 int launch_counting_sort(const int64_t* key, int64_t n, int nbins, int* perm, int* offsets,
                          int* scratch, cudaStream_t st);
+// Lists ordered by distance: members[pos] = the point ids sorted by
+// (owner, dist, id), offsets[n_r + 1] the list starts, xdist[pos] =
+// dist[members[pos]] (dist >= 0).  Scratch: sort_lists_scratch_ints() ints.
+int64_t sort_lists_scratch_ints(int64_t n, int n_r);
+int launch_sort_lists(const int64_t* owner, const float* dist, int64_t n, int n_r, int* members,
+                      int* offsets, float* xdist, int* scratch, cudaStream_t st);
 // psi_plus[r] = max over list r of dist[perm[pos]] * (1 + rel) (0 if empty)
 int launch_list_radii(const float* dist_by_id, const int* perm, const int* offsets, int n_r,
                       float rel, float* psi_plus, cudaStream_t st);
@@ -197,11 +297,12 @@ int launch_oneshot_refine(const float* X, const float* R, int d, int metric, int
 int launch_oneshot_layout(const int* qoff, int n_r, const int* qperm, const int* orig,
                           int* counts_scratch, int* pad_off, int* qsrc_pad, int* qout_pad,
                           int* tile_rep, cudaStream_t st);
-// one work item per padded tile: its rows against list r = [r s, (r + 1) s);
-// adds (tiles x s) to *points_sum when given
+// one work item per padded tile: its rows against list r = [r s, (r + 1) s),
+// or [list_off[r], list_off[r + 1]) when list_off is given; adds each tile's
+// list length to *points_sum when given
 int launch_oneshot_items(const int* pad_off, int n_r, const int* tile_rep, const int* qoff, int s,
-                         WorkItem* items, Seg* segs, int* num_items, int max_tiles,
-                         unsigned long long* points_sum, cudaStream_t st);
+                         const int* list_off, WorkItem* items, Seg* segs, int* num_items,
+                         int max_tiles, unsigned long long* points_sum, cudaStream_t st);
 // out[i] = Q[src[i]] (zero row where src[i] < 0), i < rows
 int launch_gather_padded(const float* Q, const int* src, int64_t rows, int d, float* out,
                          cudaStream_t st);

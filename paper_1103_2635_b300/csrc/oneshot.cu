@@ -214,20 +214,25 @@ __global__ void padded_counts_kernel(const int* __restrict__ qoff, int n_r, int*
 
 __global__ void oneshot_items_kernel(const int* __restrict__ pad_off, int n_r,
                                      const int* __restrict__ tile_rep,
-                                     const int* __restrict__ qoff, int s, WorkItem* __restrict__ items,
+                                     const int* __restrict__ qoff, int s,
+                                     const int* __restrict__ list_off,
+                                     WorkItem* __restrict__ items,
                                      Seg* __restrict__ segs, int* __restrict__ num_items,
                                      int max_tiles, unsigned long long* points_sum) {
   const int tiles = pad_off[n_r] / TQ;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *num_items = min(tiles, max_tiles);
-    if (points_sum) atomicAdd(points_sum, (unsigned long long)min(tiles, max_tiles) * s);
+    if (points_sum && !list_off)
+      atomicAdd(points_sum, (unsigned long long)min(tiles, max_tiles) * s);
   }
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles && t < max_tiles;
        t += gridDim.x * blockDim.x) {
     const int r = tile_rep[t];
     const int valid = qoff[r + 1] - qoff[r] - (t * TQ - pad_off[r]);
     items[t] = WorkItem{t * TQ, min(TQ, valid), t, t + 1, t, t};
-    segs[t] = Seg{r * s, (r + 1) * s};
+    const Seg sg = list_off ? Seg{list_off[r], list_off[r + 1]} : Seg{r * s, (r + 1) * s};
+    segs[t] = sg;
+    if (points_sum && list_off) atomicAdd(points_sum, (unsigned long long)(sg.x_end - sg.x_begin));
   }
 }
 
@@ -293,10 +298,10 @@ int launch_oneshot_fallback_map(const int* rows, int n, const int* tile_rep, con
 }
 
 int launch_oneshot_items(const int* pad_off, int n_r, const int* tile_rep, const int* qoff, int s,
-                         WorkItem* items, Seg* segs, int* num_items, int max_tiles,
-                         unsigned long long* points_sum, cudaStream_t st) {
-  oneshot_items_kernel<<<64, 256, 0, st>>>(pad_off, n_r, tile_rep, qoff, s, items, segs, num_items,
-                                           max_tiles, points_sum);
+                         const int* list_off, WorkItem* items, Seg* segs, int* num_items,
+                         int max_tiles, unsigned long long* points_sum, cudaStream_t st) {
+  oneshot_items_kernel<<<64, 256, 0, st>>>(pad_off, n_r, tile_rep, qoff, s, list_off, items, segs,
+                                           num_items, max_tiles, points_sum);
   RBC_LAUNCH_CHECK("oneshot_items_kernel");
   return RBC_OK;
 }

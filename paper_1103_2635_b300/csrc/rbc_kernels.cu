@@ -330,6 +330,44 @@ __global__ void add_ints_kernel(int* __restrict__ dst, const int* __restrict__ s
   if (i < n) dst[i] += src[i];
 }
 
+// ---- lists ordered by distance to their representative ----
+__global__ void iota_kernel(int* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int)i;
+}
+
+// key[j] = 8-bit digit of the float bit pattern of val[cur[j]] (values >= 0,
+// so bit patterns order like the values)
+__global__ void digit_key_kernel(const float* __restrict__ val, const int* __restrict__ cur,
+                                 int64_t n, int shift, int64_t* __restrict__ key) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x)
+    key[j] = (__float_as_uint(val[cur[j]]) >> shift) & 255u;
+}
+
+__global__ void owner_key_kernel(const int64_t* __restrict__ owner, const int* __restrict__ cur,
+                                 int64_t n, int64_t* __restrict__ key) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x)
+    key[j] = owner[cur[j]];
+}
+
+// out[pos] = cur[perm[pos]]
+__global__ void compose_kernel(const int* __restrict__ cur, const int* __restrict__ perm,
+                               int64_t n, int* __restrict__ out) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x)
+    out[j] = cur[perm[j]];
+}
+
+__global__ void gather_f32_kernel(const float* __restrict__ val, const int* __restrict__ idx,
+                                  int64_t n, float* __restrict__ out) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x)
+    out[j] = val[idx[j]];
+}
+
 }  // namespace
 
 int launch_exclusive_scan(const int* in, int n, int* out, cudaStream_t st) {
@@ -381,6 +419,51 @@ int launch_counting_sort(const int64_t* key, int64_t n, int nbins, int* perm, in
                                                                 perm);
     RBC_LAUNCH_CHECK("cs_scatter_kernel");
   }
+  return RBC_OK;
+}
+
+int64_t sort_lists_scratch_ints(int64_t n, int n_r) {
+  // three permutations, 64-bit keys (8-byte aligned), counting-sort scratch,
+  // digit offsets
+  return 5 * n + 2 + counting_sort_scratch_ints(n, n_r > 256 ? n_r : 256) + 257;
+}
+
+int launch_sort_lists(const int64_t* owner, const float* dist, int64_t n, int n_r, int* members,
+                      int* offsets, float* xdist, int* scratch, cudaStream_t st) {
+  if (n <= 0) return RBC_OK;
+  int* cur = scratch;
+  int* tmp = scratch + n;
+  int* perm = scratch + 2 * n;
+  // the keys start at an even int offset: 8-byte aligned for any n
+  const int64_t key_off = (3 * n + 1) & ~(int64_t)1;
+  int64_t* key = reinterpret_cast<int64_t*>(scratch + key_off);
+  int* cs = scratch + key_off + 2 * n;
+  int* digit_off = cs + counting_sort_scratch_ints(n, n_r > 256 ? n_r : 256);
+  const unsigned g = (unsigned)((n + 255) / 256 < 148 * 16 ? (n + 255) / 256 : 148 * 16);
+  iota_kernel<<<g, 256, 0, st>>>(cur, n);
+  RBC_LAUNCH_CHECK("iota_kernel");
+  // least significant digit first; every pass is stable, so equal distances
+  // keep ascending ids
+  for (int shift = 0; shift < 32; shift += 8) {
+    digit_key_kernel<<<g, 256, 0, st>>>(dist, cur, n, shift, key);
+    RBC_LAUNCH_CHECK("digit_key_kernel");
+    int rc = launch_counting_sort(key, n, 256, perm, digit_off, cs, st);
+    if (rc != RBC_OK) return rc;
+    compose_kernel<<<g, 256, 0, st>>>(cur, perm, n, tmp);
+    RBC_LAUNCH_CHECK("compose_kernel");
+    int* t = cur;
+    cur = tmp;
+    tmp = t;
+  }
+  // finally by owner (stable): lists in owner order, each by (distance, id)
+  owner_key_kernel<<<g, 256, 0, st>>>(owner, cur, n, key);
+  RBC_LAUNCH_CHECK("owner_key_kernel");
+  int rc = launch_counting_sort(key, n, n_r, perm, offsets, cs, st);
+  if (rc != RBC_OK) return rc;
+  compose_kernel<<<g, 256, 0, st>>>(cur, perm, n, members);
+  RBC_LAUNCH_CHECK("compose_kernel");
+  gather_f32_kernel<<<g, 256, 0, st>>>(dist, members, n, xdist);
+  RBC_LAUNCH_CHECK("gather_f32_kernel");
   return RBC_OK;
 }
 

@@ -41,6 +41,82 @@ __device__ __forceinline__ bool key_lt(float a, int ia, int la, float b, int ib,
 // rounding, (d/8 + 3)u suffices; twice that is used.
 __device__ __forceinline__ float rerank_eps(int d) { return (0.25f * d + 8.0f) * U32; }
 
+// FP32 difference-form distance with four interleaved partial sums (the
+// re-rank; relative error <= (d/8 + 3) u, see rerank_eps).
+__device__ __forceinline__ float rerank_rho(const float* qr, const float* xr, int d, int metric) {
+  float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+  int i = 0;
+  for (; i + 4 <= d; i += 4) {
+    float t0 = qr[i] - xr[i], t1 = qr[i + 1] - xr[i + 1];
+    float t2 = qr[i + 2] - xr[i + 2], t3 = qr[i + 3] - xr[i + 3];
+    if (metric == RBC_L2) {
+      p0 = fmaf(t0, t0, p0);
+      p1 = fmaf(t1, t1, p1);
+      p2 = fmaf(t2, t2, p2);
+      p3 = fmaf(t3, t3, p3);
+    } else {
+      p0 += fabsf(t0);
+      p1 += fabsf(t1);
+      p2 += fabsf(t2);
+      p3 += fabsf(t3);
+    }
+  }
+  for (; i < d; ++i) {
+    float t0 = qr[i] - xr[i];
+    if (metric == RBC_L2) p0 = fmaf(t0, t0, p0); else p0 += fabsf(t0);
+  }
+  float sum = (p0 + p1) + (p2 + p3);
+  return metric == RBC_L2 ? sqrtf(sum) : sum;
+}
+
+// Near-ties: if two neighbouring ranks among the first k+1 (one rank per
+// lane, sorted by (rho, id)) lie within the FP32 bound of each other, every
+// candidate is recomputed in FP64 and the lanes re-sorted by (rho64, id).
+// Returns the ballot of tied ranks (0: nothing recomputed).
+__device__ __forceinline__ unsigned fp64_ties(const float* qr, const float* X32, int d, int metric,
+                                              int k, int c_out, float eps, int lane, float& rho,
+                                              int& oid, int& brow) {
+  float nxt = __shfl_down_sync(0xffffffffu, rho, 1);
+  bool tie = lane < k && lane + 1 < c_out && rho != INFINITY && nxt != INFINITY &&
+             (nxt - rho) <= eps * (nxt + rho) * 2.0f;
+  unsigned tie_mask = __ballot_sync(0xffffffffu, tie);
+  if (tie_mask) {
+    double r64 = INFINITY;
+    if (brow >= 0) {
+      const float* xr = X32 + (int64_t)brow * d;
+      double s = 0.0;
+      for (int i = 0; i < d; ++i) {
+        double t0 = (double)qr[i] - (double)xr[i];
+        s += metric == RBC_L2 ? t0 * t0 : fabs(t0);
+      }
+      r64 = metric == RBC_L2 ? sqrt(s) : s;
+    }
+    // keys are non-negative doubles, so their bit patterns order like the values
+    long long key = brow >= 0 ? __double_as_longlong(r64) : LLONG_MAX;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        long long ok = __shfl_xor_sync(0xffffffffu, key, stride);
+        int oi = __shfl_xor_sync(0xffffffffu, oid, stride);
+        int ob = __shfl_xor_sync(0xffffffffu, brow, stride);
+        bool up = (lane & size) == 0 || size == 32;
+        bool lower = (lane & stride) == 0;
+        bool other_less = ok < key || (ok == key && oi < oid);
+        bool same = ok == key && oi == oid;
+        bool take = (lower == up) ? other_less : (!other_less && !same);
+        if (take) {
+          key = ok;
+          oid = oi;
+          brow = ob;
+        }
+      }
+    }
+    rho = key == LLONG_MAX ? INFINITY : (float)__longlong_as_double(key);
+  }
+  return tie_mask;
+}
+
 template <int CW>
 __global__ void __launch_bounds__(WARPS * 32) select_kernel(SelectArgs a) {
   __shared__ float sh_s[WARPS][32][CW + 1];
@@ -143,30 +219,7 @@ __global__ void __launch_bounds__(WARPS * 32) select_kernel(SelectArgs a) {
   float rho = INFINITY;
   int oid = INT32_MAX;
   if (valid) {
-    const float* xr = a.X32 + (int64_t)ci * d;
-    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
-    int i = 0;
-    for (; i + 4 <= d; i += 4) {
-      float t0 = qr[i] - xr[i], t1 = qr[i + 1] - xr[i + 1];
-      float t2 = qr[i + 2] - xr[i + 2], t3 = qr[i + 3] - xr[i + 3];
-      if (a.metric == RBC_L2) {
-        p0 = fmaf(t0, t0, p0);
-        p1 = fmaf(t1, t1, p1);
-        p2 = fmaf(t2, t2, p2);
-        p3 = fmaf(t3, t3, p3);
-      } else {
-        p0 += fabsf(t0);
-        p1 += fabsf(t1);
-        p2 += fabsf(t2);
-        p3 += fabsf(t3);
-      }
-    }
-    for (; i < d; ++i) {
-      float t0 = qr[i] - xr[i];
-      if (a.metric == RBC_L2) p0 = fmaf(t0, t0, p0); else p0 += fabsf(t0);
-    }
-    float sum = (p0 + p1) + (p2 + p3);
-    rho = a.metric == RBC_L2 ? sqrtf(sum) : sum;
+    rho = rerank_rho(qr, a.X32 + (int64_t)ci * d, d, a.metric);
     oid = a.xid ? a.xid[ci] : ci;
   }
   int brow = valid ? ci : -1;  // buffer row carried through the sort
@@ -223,46 +276,8 @@ __global__ void __launch_bounds__(WARPS * 32) select_kernel(SelectArgs a) {
   }
 
   // ---- 5. near-ties among the first k+1 ranks -> FP64 ----
-  float nxt = __shfl_down_sync(0xffffffffu, rho, 1);
-  bool tie = lane < k && lane + 1 < a.c_out && rho != INFINITY && nxt != INFINITY &&
-             (nxt - rho) <= eps * (nxt + rho) * 2.0f;
-  unsigned tie_mask = __ballot_sync(0xffffffffu, tie);
-  if (tie_mask) {
-    double r64 = INFINITY;
-    if (brow >= 0) {
-      const float* xr = a.X32 + (int64_t)brow * d;
-      double s = 0.0;
-      for (int i = 0; i < d; ++i) {
-        double t0 = (double)qr[i] - (double)xr[i];
-        s += a.metric == RBC_L2 ? t0 * t0 : fabs(t0);
-      }
-      r64 = a.metric == RBC_L2 ? sqrt(s) : s;
-    }
-    // sort by (rho64, id): reuse the float sort on the double's ordering by
-    // sorting with a two-stage key; keys are non-negative doubles, so their
-    // bit patterns order like the values.
-    long long key = brow >= 0 ? __double_as_longlong(r64) : LLONG_MAX;
-#pragma unroll
-    for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-      for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        long long ok = __shfl_xor_sync(0xffffffffu, key, stride);
-        int oi = __shfl_xor_sync(0xffffffffu, oid, stride);
-        int ob = __shfl_xor_sync(0xffffffffu, brow, stride);
-        bool up = (lane & size) == 0 || size == 32;
-        bool lower = (lane & stride) == 0;
-        bool other_less = ok < key || (ok == key && oi < oid);
-        bool same = ok == key && oi == oid;
-        bool take = (lower == up) ? other_less : (!other_less && !same);
-        if (take) {
-          key = ok;
-          oid = oi;
-          brow = ob;
-        }
-      }
-    }
-    rho = key == LLONG_MAX ? INFINITY : (float)__longlong_as_double(key);
-  }
+  const unsigned tie_mask = fp64_ties(qr, a.X32, d, a.metric, a.k, a.c_out, eps, lane, rho, oid,
+                                      brow);
 
   // ---- 6. output ----
   const int64_t orow = a.qorig ? (int64_t)a.qorig[row] : (int64_t)row;
@@ -281,6 +296,162 @@ __global__ void __launch_bounds__(WARPS * 32) select_kernel(SelectArgs a) {
   }
 }
 
+
+// Windowed search: one warp per query.  The query's candidate buffer holds
+// every point whose low-precision score passed the query's threshold, which
+// includes every point within g(q) >= its k-th neighbour distance -- so the
+// true k nearest are among the candidates and no certificate is needed.
+//  1. s_k = the k-th smallest candidate score (bitwise search over the
+//     order-preserving integer keys of the scores, counting with ballots);
+//     k distinct points score <= s_k, so U = dist_upper(s_k) bounds the k-th
+//     neighbour distance, and only candidates scoring <= score_bound(U) can
+//     be among the k nearest;
+//  2. those (normally k plus a few) are compacted into shared memory,
+//     re-ranked in FP32 and kept per lane sorted by (rho, id);
+//  3. c_out rounds of warp arg-min give ranks 0 .. c_out - 1, one per lane;
+//     near-ties go through the FP64 step.
+// A buffer that overflowed, holds fewer than k entries, or leaves more than
+// RERANK_MAX survivors after step 1 sends the query to the re-search.
+constexpr int RERANK_PL = 8;                    // re-ranked candidates per lane
+constexpr int RERANK_MAX = 32 * RERANK_PL;
+
+__device__ __forceinline__ unsigned score_key(float s) {
+  const unsigned b = __float_as_uint(s);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_score(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+__global__ void __launch_bounds__(WARPS * 32) select_cands_kernel(CandSelectArgs a) {
+  __shared__ int stage[WARPS][RERANK_MAX];
+  const int wib = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t q = (int64_t)blockIdx.x * WARPS + wib;
+  if (q >= a.m) return;
+  const int cnt = a.cand_cnt[q];
+  const int k = a.k;
+  auto to_research = [&]() {
+    if (lane == 0) {
+      const int pos = atomicAdd(&a.counters[0], 1);
+      a.fallback_rows[pos] = (int)q;
+    }
+  };
+  if (cnt > a.cap || cnt < k) {
+    to_research();
+    return;
+  }
+  const float* sc = a.cand_score + q * a.cap;
+  const int* cr = a.cand_row + q * a.cap;
+  // ---- 1. k-th smallest score ----
+  unsigned kth = 0;
+  for (int bit = 31; bit >= 0; --bit) {
+    const unsigned t = kth | (1u << bit);
+    int c = 0;
+    for (int e = lane; e < cnt; e += 32) c += score_key(sc[e]) < t;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (c < k) kth = t;
+  }
+  const float qn = a.q_lpnorm[q], qe = a.q_err[q];
+  const float xe = __uint_as_float(*a.x_err_max_bits), xn = __uint_as_float(*a.x_norm_max_bits);
+  const float smax = score_bound(dist_upper(key_score(kth), qn, qe, xe, xn, a.d), qn, qe, xe, xn,
+                                 a.d);
+  // ---- 2. survivors -> shared memory ----
+  int* stg = stage[wib];
+  int nre = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int e0 = 0; e0 < cnt; e0 += 32) {
+    const int e = e0 + lane;
+    const bool pass = e < cnt && sc[e] <= smax;
+    const unsigned bal = __ballot_sync(0xffffffffu, pass);
+    const int pos = nre + __popc(bal & lt);
+    if (pass && pos < RERANK_MAX) stg[pos] = cr[e];
+    nre += __popc(bal);
+  }
+  if (nre > RERANK_MAX) {
+    to_research();
+    return;
+  }
+  __syncwarp();
+  const int d = a.d;
+  const float* qr = a.Q32 + q * d;
+  float ls[RERANK_PL];
+  int li[RERANK_PL], lr[RERANK_PL];
+#pragma unroll
+  for (int j = 0; j < RERANK_PL; ++j) {
+    ls[j] = INFINITY;
+    li[j] = INT32_MAX;
+    lr[j] = -1;
+  }
+  for (int e = lane; e < nre; e += 32) {
+    const int row = stg[e];
+    float v = rerank_rho(qr, a.X32 + (int64_t)row * d, d, a.metric);
+    int id = a.xid ? a.xid[row] : row;
+    int rw = row;
+#pragma unroll
+    for (int j = 0; j < RERANK_PL; ++j) {
+      const bool lt2 = pair_lt(v, id, ls[j], li[j]);
+      const float ts = lt2 ? ls[j] : v;
+      const int ti = lt2 ? li[j] : id;
+      const int tr = lt2 ? lr[j] : rw;
+      ls[j] = lt2 ? v : ls[j];
+      li[j] = lt2 ? id : li[j];
+      lr[j] = lt2 ? rw : lr[j];
+      v = ts;
+      id = ti;
+      rw = tr;
+    }
+  }
+  // ---- 3. ranks, FP64 ties, output ----
+  int head = 0;
+  float rho = INFINITY;
+  int oid = INT32_MAX, brow = -1;
+  for (int j = 0; j < a.c_out; ++j) {
+    float hv = INFINITY;
+    int hi = INT32_MAX, hr = -1;
+#pragma unroll
+    for (int t = 0; t < RERANK_PL; ++t)
+      if (t == head) {
+        hv = ls[t];
+        hi = li[t];
+        hr = lr[t];
+      }
+    float bv = hv;
+    int bi = hi, bl = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+      if (key_lt(ov, oi, ol, bv, bi, bl)) {
+        bv = ov;
+        bi = oi;
+        bl = ol;
+      }
+    }
+    const int br = __shfl_sync(0xffffffffu, hr, bl);
+    if (lane == bl) ++head;
+    if (lane == j) {
+      rho = bv;
+      oid = bi;
+      brow = bv == INFINITY ? -1 : br;
+    }
+  }
+  const float eps = rerank_eps(d);
+  const unsigned tie_mask = fp64_ties(qr, a.X32, d, a.metric, k, a.c_out, eps, lane, rho, oid,
+                                      brow);
+  if (lane < k) {
+    const bool ok = rho != INFINITY && brow >= 0;
+    a.out_ids[q * k + lane] = ok ? (int64_t)oid : (int64_t)-1;
+    a.out_dist[q * k + lane] = ok ? rho : INFINITY;
+  }
+  if (lane == 0) {
+    if (tie_mask) atomicAdd(&a.counters[1], 1);
+    if (tie_mask & (1u << (k - 1))) atomicAdd(&a.counters[2], 1);
+  }
+}
+
 template <int CW>
 int launch_cw(const SelectArgs& a, int64_t grid_rows, cudaStream_t st) {
   int64_t blocks = (grid_rows + WARPS - 1) / WARPS;
@@ -291,6 +462,18 @@ int launch_cw(const SelectArgs& a, int64_t grid_rows, cudaStream_t st) {
 }
 
 }  // namespace
+
+int launch_select_cands(const CandSelectArgs& a, cudaStream_t st) {
+  if (a.k < 1 || a.c_out < a.k || a.c_out > 32 || a.cap != CAND_CAP) {
+    set_error("select_cands: bad k=%d c_out=%d cap=%d", a.k, a.c_out, a.cap);
+    return RBC_ERR_ARG;
+  }
+  const int64_t blocks = (a.m + WARPS - 1) / WARPS;
+  if (blocks == 0) return RBC_OK;
+  select_cands_kernel<<<(unsigned)blocks, WARPS * 32, 0, st>>>(a);
+  RBC_LAUNCH_CHECK("select_cands_kernel");
+  return RBC_OK;
+}
 
 int launch_select(const SelectArgs& a, cudaStream_t st) {
   if (a.k < 1 || a.c_out < a.k || a.c_out > 32) {

@@ -1,0 +1,508 @@
+// Work generation of the windowed exact search (Section 5.2 with lists sorted
+// by distance to their representative).
+//
+// Every query q first learns g(q), an upper bound of its k-th nearest-neighbour
+// distance: the smaller of gamma_k (its k-th nearest representative, a
+// database point) and the k-th distance inside the list of its nearest
+// representative.  A point x of list L_r can be among q's k nearest only if
+//   (1) rho(q, r) <= g + psi_r           (rule (1) of Section 5.2),
+//   (2) rho(q, r) <= 2 g + gamma_1       (Lemma 1, generalised to k), and
+//   (3) |rho(x, r) - rho(q, r)| <= g     (triangle inequality),
+// so with L_r sorted by rho(x, r), q needs only the window of L_r between
+// rho(q, r) - g and rho(q, r) + g.  All comparisons carry the FP32 rounding
+// bounds of the values involved, so no needed point is ever cut.
+//
+// The surviving (q, r) pairs are binned by (r, bucket of rho(q, r)) -- NB
+// buckets between the smallest and largest kept rho(q, r) of each r -- with a
+// counting sort over the implicit pair list, so each r's group comes out
+// ordered by rho(q, r) up to the bucket width.  Each group is cut into chunks
+// of up to TQ queries: one work item per chunk, against the union of its
+// queries' windows -- queries with close rho(q, r) have close windows.
+//
+// The pair passes read D [m, n_r] in warp tiles of 32 queries x 32
+// representatives through shared memory, so that a lane owns a query and the
+// warp walks the representatives: bin counters are then updated once per
+// (warp, representative, bucket) and the scattered pairs of one bin land in
+// consecutive slots.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rbc {
+
+namespace {
+
+constexpr int WT = 32;           // queries per warp tile
+constexpr int WW = 8;            // warps per block of the pair passes
+constexpr int RSPAN = 64;        // representatives per block (grid.y splits the rest)
+constexpr int NBK = 32;          // distance buckets per representative
+constexpr float SLACK = 1.0f + 2.4e-7f;
+
+__device__ __forceinline__ bool keep_pair(float d, float lo, float gh, float psi, float lemma) {
+  const float dl = d * lo;
+  return dl <= (gh + psi) * SLACK && dl <= lemma;
+}
+
+// g[q] = min(gamma_k (1 + rel_rep), own-list bound), both rounded up
+__global__ void gbound_kernel(const float* __restrict__ own, const float* __restrict__ gk,
+                              int64_t m, float rel_rep, float* __restrict__ g) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= m) return;
+  g[q] = fminf(gk[q] * (1.0f + rel_rep) * SLACK, own[q]);
+}
+
+// k-th smallest FP32 distance of every grouped query row from the two sorted
+// sub-lists its tile kernel left (scores are rho^2 for l2), rounded up by the
+// kernel's bound: an upper bound of the k-th distance inside its list
+__global__ void own_kth_kernel(const float* __restrict__ ps, int C, const int* __restrict__ qout,
+                               int64_t rows, int k, int l2, float rel, float* __restrict__ own) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= rows) return;
+  const int q = qout[row];
+  if (q < 0) return;
+  const int64_t b0 = row * 2 * (int64_t)C;  // slot = tile, [slot][TQ][2][C]
+  const float* a = ps + b0;
+  const float* b = a + C;
+  int i = 0, j = 0;
+  float v = INFINITY;
+  for (int t = 0; t < k; ++t) {
+    const float x = i < C ? a[i] : INFINITY;
+    const float y = j < C ? b[j] : INFINITY;
+    if (x <= y) {
+      v = x;
+      ++i;
+    } else {
+      v = y;
+      ++j;
+    }
+  }
+  own[q] = v < INFINITY ? (l2 ? sqrtf(v) : v) * (1.0f + rel) * SLACK : INFINITY;
+}
+
+// Own-list bound from the tensor-core top-C lists of the grouped rows, one
+// warp per row: the k best-scored candidates of the row's two sub-lists are
+// k distinct points of its list, so the largest of their FP32 distances
+// (rounded up by the re-rank bound) bounds the row's k-th distance.  If the
+// lists hold fewer than k points the bound is infinite.
+__global__ void own_kth_lp_kernel(const float* __restrict__ ps, const int* __restrict__ pi, int C,
+                                  const int* __restrict__ qout, int64_t rows, int k,
+                                  const float* __restrict__ Q32, const float* __restrict__ X32,
+                                  int d, int metric, float rel, float* __restrict__ own) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  const int q = qout[row];
+  if (q < 0) return;
+  const int64_t base = row * 2 * (int64_t)C;  // [slot = tile][TQ][2][C]
+  // up to 2C <= 64 entries, two per lane
+  float s0 = INFINITY, s1 = INFINITY;
+  int c0 = -1, c1 = -1;
+  if (lane < 2 * C) {
+    c0 = pi[base + lane];
+    s0 = c0 >= 0 ? ps[base + lane] : INFINITY;
+  }
+  if (lane + 32 < 2 * C) {
+    c1 = pi[base + lane + 32];
+    s1 = c1 >= 0 ? ps[base + lane + 32] : INFINITY;
+  }
+  if (s1 < s0) {  // each lane's smaller entry first
+    float ts = s0;
+    s0 = s1;
+    s1 = ts;
+    int tc = c0;
+    c0 = c1;
+    c1 = tc;
+  }
+  int mine = -1;  // lane j takes the j-th best-scored column
+  for (int j = 0; j < k; ++j) {
+    float bv = s0;
+    int bl = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+      if (ov < bv || (ov == bv && ol < bl)) {
+        bv = ov;
+        bl = ol;
+      }
+    }
+    const int col = __shfl_sync(0xffffffffu, c0, bl);
+    if (lane == j) mine = bv < INFINITY ? col : -1;
+    if (lane == bl) {
+      s0 = s1;
+      c0 = c1;
+      s1 = INFINITY;
+      c1 = -1;
+    }
+  }
+  float rho = 0.0f;
+  bool missing = lane < k && mine < 0;
+  if (lane < k && mine >= 0) {
+    const float* qr = Q32 + row * d;
+    const float* xr = X32 + (int64_t)mine * d;
+    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+    int i = 0;
+    for (; i + 4 <= d; i += 4) {
+      const float t0 = qr[i] - xr[i], t1 = qr[i + 1] - xr[i + 1];
+      const float t2 = qr[i + 2] - xr[i + 2], t3 = qr[i + 3] - xr[i + 3];
+      if (metric == RBC_L2) {
+        p0 = fmaf(t0, t0, p0);
+        p1 = fmaf(t1, t1, p1);
+        p2 = fmaf(t2, t2, p2);
+        p3 = fmaf(t3, t3, p3);
+      } else {
+        p0 += fabsf(t0);
+        p1 += fabsf(t1);
+        p2 += fabsf(t2);
+        p3 += fabsf(t3);
+      }
+    }
+    for (; i < d; ++i) {
+      const float t0 = qr[i] - xr[i];
+      if (metric == RBC_L2) p0 = fmaf(t0, t0, p0); else p0 += fabsf(t0);
+    }
+    const float sum = (p0 + p1) + (p2 + p3);
+    rho = metric == RBC_L2 ? sqrtf(sum) : sum;
+  }
+  const bool any_missing = __any_sync(0xffffffffu, missing);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) rho = fmaxf(rho, __shfl_xor_sync(0xffffffffu, rho, o));
+  if (lane == 0) own[q] = any_missing ? INFINITY : rho * (1.0f + rel) * SLACK;
+}
+
+// One warp tile: D[q0 .. q0+31][r0 .. r0+31] -> tile[query][r] (padded).
+__device__ __forceinline__ void load_tile(const float* __restrict__ D, int64_t m, int n_r,
+                                          int64_t q0, int r0, float (*tile)[WT + 1], int lane) {
+  const int r = r0 + lane;
+#pragma unroll
+  for (int j = 0; j < WT; ++j) {
+    const int64_t q = q0 + j;
+    tile[j][lane] = (q < m && r < n_r) ? D[q * n_r + r] : INFINITY;
+  }
+  __syncwarp();
+}
+
+// The pair passes: block (x, y) covers queries [x * 256, +256) (one warp tile
+// of 32 queries per warp) and representatives [y * RSPAN, +RSPAN); per-block
+// reductions go through shared memory, so global memory sees one update per
+// (block, representative) or (block, bin).
+struct PairCtx {
+  int64_t q;
+  bool live;
+  float lo, gh, lemma;
+};
+
+__device__ __forceinline__ PairCtx pair_ctx(int64_t q0, int lane, int64_t m,
+                                            const float* __restrict__ g,
+                                            const float* __restrict__ g1, float rel) {
+  PairCtx c;
+  c.q = q0 + lane;
+  c.live = c.q < m;
+  c.lo = 1.0f - rel;
+  c.gh = c.live ? g[c.q] : 0.0f;
+  c.lemma = c.live ? (2.0f * c.gh + g1[c.q] * (1.0f + rel)) * SLACK : -1.0f;
+  return c;
+}
+
+// Pass 1: per representative, the smallest and largest kept rho(q, r) (float
+// bits: distances are >= 0, so integer order is value order); per query its
+// kept count.
+__global__ void __launch_bounds__(WW * 32)
+wrange_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __restrict__ g,
+              const float* __restrict__ g1, const float* __restrict__ psi_plus, float rel,
+              unsigned* __restrict__ rmin, unsigned* __restrict__ rmax, int* __restrict__ q_kept) {
+  __shared__ float tiles[WW][WT][WT + 1];
+  __shared__ unsigned smin[RSPAN], smax[RSPAN];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rb = blockIdx.y * RSPAN, re = min(n_r, rb + RSPAN);
+  for (int i = threadIdx.x; i < RSPAN; i += blockDim.x) {
+    smin[i] = 0x7f7f7f7fu;
+    smax[i] = 0u;
+  }
+  __syncthreads();
+  const int64_t q0 = ((int64_t)blockIdx.x * WW + wid) * WT;
+  if (q0 < m) {
+    const PairCtx c = pair_ctx(q0, lane, m, g, g1, rel);
+    int kept = 0;
+    for (int r0 = rb; r0 < re; r0 += WT) {
+      load_tile(D, m, n_r, q0, r0, tiles[wid], lane);
+      const int nr = min(WT, re - r0);
+      for (int rr = 0; rr < nr; ++rr) {
+        const float v = tiles[wid][lane][rr];
+        if (c.live && keep_pair(v, c.lo, c.gh, psi_plus[r0 + rr], c.lemma)) {
+          ++kept;
+          atomicMin(&smin[r0 + rr - rb], __float_as_uint(v));
+          atomicMax(&smax[r0 + rr - rb], __float_as_uint(v));
+        }
+      }
+      __syncwarp();
+    }
+    if (c.live && kept) atomicAdd(&q_kept[c.q], kept);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < re - rb; i += blockDim.x) {
+    if (smin[i] != 0x7f7f7f7fu) {  // some pair of r kept in this block
+      atomicMin(&rmin[rb + i], smin[i]);
+      atomicMax(&rmax[rb + i], smax[i]);
+    }
+  }
+}
+
+__device__ __forceinline__ int bucket_of(float v, float lo, float scale) {
+  return min(NBK - 1, (int)((v - lo) * scale));
+}
+
+// Passes 2 and 3.  Count: every (r, bucket) bin of the block's pairs ->
+// counts[block x][bin].  Scatter: the pairs, at the bins' offsets plus the
+// block's prefix (off[block x][bin], from the column scan).
+template <bool SCATTER>
+__global__ void __launch_bounds__(WW * 32)
+wbin_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __restrict__ g,
+            const float* __restrict__ g1, const float* __restrict__ psi_plus, float rel,
+            const unsigned* __restrict__ rmin, const unsigned* __restrict__ rmax,
+            int* __restrict__ counts, const int* __restrict__ bin_off, int* __restrict__ pair_q,
+            float* __restrict__ pair_d) {
+  __shared__ float tiles[WW][WT][WT + 1];
+  __shared__ int h[RSPAN * NBK];
+  __shared__ float sblo[RSPAN], sscale[RSPAN];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rb = blockIdx.y * RSPAN, re = min(n_r, rb + RSPAN);
+  const int64_t nbins = (int64_t)n_r * NBK;
+  const int64_t crow = (int64_t)blockIdx.x * nbins;  // this block's row of counts
+  for (int i = threadIdx.x; i < RSPAN * NBK; i += blockDim.x) {
+    const int64_t bin = (int64_t)rb * NBK + i;
+    h[i] = SCATTER ? (bin < nbins ? bin_off[bin] + counts[crow + bin] : 0) : 0;
+  }
+  for (int i = threadIdx.x; i < re - rb; i += blockDim.x) {
+    const float blo = __uint_as_float(rmin[rb + i]);
+    const float bhi = __uint_as_float(rmax[rb + i]);
+    sblo[i] = blo;
+    sscale[i] = bhi > blo ? (float)NBK / (bhi - blo) : 0.0f;
+  }
+  __syncthreads();
+  const int64_t q0 = ((int64_t)blockIdx.x * WW + wid) * WT;
+  if (q0 < m) {
+    const PairCtx c = pair_ctx(q0, lane, m, g, g1, rel);
+    for (int r0 = rb; r0 < re; r0 += WT) {
+      load_tile(D, m, n_r, q0, r0, tiles[wid], lane);
+      const int nr = min(WT, re - r0);
+      for (int rr = 0; rr < nr; ++rr) {
+        const int rl = r0 + rr - rb;
+        const float v = tiles[wid][lane][rr];
+        if (c.live && keep_pair(v, c.lo, c.gh, psi_plus[r0 + rr], c.lemma)) {
+          const int slot = rl * NBK + bucket_of(v, sblo[rl], sscale[rl]);
+          const int pos = atomicAdd(&h[slot], 1);
+          if (SCATTER) {
+            pair_q[pos] = (int)c.q;
+            pair_d[pos] = v;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  if (!SCATTER) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < (re - rb) * NBK; i += blockDim.x)
+      counts[crow + (int64_t)rb * NBK + i] = h[i];
+  }
+}
+
+// per bin: exclusive prefix over the query blocks in place, totals[bin] = sum
+__global__ void bin_colscan_kernel(int* __restrict__ counts, int nblocks, int64_t nbins,
+                                   int* __restrict__ totals) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbins) return;
+  int run = 0;
+  for (int k = 0; k < nblocks; ++k) {
+    const int64_t o = (int64_t)k * nbins + b;
+    const int c = counts[o];
+    counts[o] = run;
+    run += c;
+  }
+  totals[b] = run;
+}
+
+// per representative: chunks of TQ pairs in its group
+__global__ void chunk_count_kernel(const int* __restrict__ bin_off, int nb, int n_r,
+                                   int* __restrict__ out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n_r) out[r] = (bin_off[(r + 1) * nb] - bin_off[r * nb] + TQ - 1) / TQ;
+}
+
+// first index i in [0, n) with a[i] >= v (n if none)
+__device__ __forceinline__ int lower_bound_f(const float* a, int n, float v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+// first index i in [0, n) with a[i] > v (n if none)
+__device__ __forceinline__ int upper_bound_f(const float* a, int n, float v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] <= v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// One warp per chunk: the union of its queries' windows, cut from the sorted
+// list by binary search.
+__global__ void window_items_kernel(const int* __restrict__ chunk_off, int n_r,
+                                    const int* __restrict__ bin_off, int nb,
+                                    const int* __restrict__ pair_q, const float* __restrict__ pair_d,
+                                    const float* __restrict__ g, const int* __restrict__ offsets,
+                                    const float* __restrict__ xdist, float rel, float relx,
+                                    int max_items, EmitItem* __restrict__ items,
+                                    unsigned long long* __restrict__ stats) {
+  const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int total = chunk_off[n_r];
+  if (c >= total || c >= max_items) return;
+  // the group holding chunk c: last r with chunk_off[r] <= c
+  int lo_r = 0, hi_r = n_r;  // invariant: chunk_off[lo_r] <= c < chunk_off[hi_r]
+  while (hi_r - lo_r > 1) {
+    const int mid = (lo_r + hi_r) >> 1;
+    if (chunk_off[mid] <= c) lo_r = mid; else hi_r = mid;
+  }
+  const int r = lo_r;
+  const int begin = bin_off[r * nb] + ((int)c - chunk_off[r]) * TQ;
+  const int end = min(begin + TQ, bin_off[(r + 1) * nb]);
+  float wlo = INFINITY, whi = -INFINITY;
+  const float dlo = 1.0f - rel, dup = 1.0f + rel;
+  const float xlo = (1.0f - relx) * (1.0f - 2.4e-7f), xup = (1.0f + relx) * SLACK;
+  for (int i = begin + lane; i < end; i += 32) {
+    const float d = pair_d[i];
+    const float gq = g[pair_q[i]];
+    wlo = fminf(wlo, (d * dlo - gq * SLACK) * xlo);
+    whi = fmaxf(whi, (d * dup + gq) * xup);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    wlo = fminf(wlo, __shfl_xor_sync(0xffffffffu, wlo, o));
+    whi = fmaxf(whi, __shfl_xor_sync(0xffffffffu, whi, o));
+  }
+  if (lane == 0) {
+    const int ob = offsets[r], oe = offsets[r + 1];
+    const int xb = ob + lower_bound_f(xdist + ob, oe - ob, wlo);
+    const int xe = ob + upper_bound_f(xdist + ob, oe - ob, whi);
+    items[c] = EmitItem{begin, end - begin, xb, xe > xb ? xe : xb};
+    if (stats && xe > xb) {
+      atomicAdd(&stats[0], (unsigned long long)(xe - xb));
+      atomicAdd(&stats[1], (unsigned long long)(end - begin) * (unsigned long long)(xe - xb));
+    }
+  }
+}
+
+// Score threshold of every query: no point within g(q) of q scores above it.
+__global__ void score_threshold_kernel(const float* __restrict__ g, const float* __restrict__ qnorm,
+                                       const float* __restrict__ qerr,
+                                       const unsigned* __restrict__ lp_max, int d, int64_t m,
+                                       float* __restrict__ thr) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= m) return;
+  thr[q] = score_bound(g[q], qnorm[q], qerr[q], __uint_as_float(lp_max[0]),
+                       __uint_as_float(lp_max[1]), d);
+}
+
+}  // namespace
+
+int launch_gbound(const float* own, const float* gk, int64_t m, float rel_rep, float* g,
+                  cudaStream_t st) {
+  if (m <= 0) return RBC_OK;
+  gbound_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(own, gk, m, rel_rep, g);
+  RBC_LAUNCH_CHECK("gbound_kernel");
+  return RBC_OK;
+}
+
+int launch_own_kth(const float* ps, int C, const int* qout, int64_t rows, int k, int metric,
+                   float rel, float* own, cudaStream_t st) {
+  if (rows <= 0) return RBC_OK;
+  own_kth_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(ps, C, qout, rows, k,
+                                                                 metric == RBC_L2, rel, own);
+  RBC_LAUNCH_CHECK("own_kth_kernel");
+  return RBC_OK;
+}
+
+int launch_own_kth_lp(const float* ps, const int* pi, int C, const int* qout, int64_t rows,
+                      int k, const float* Q32, const float* X32, int d, int metric, float rel,
+                      float* own, cudaStream_t st) {
+  if (rows <= 0) return RBC_OK;
+  own_kth_lp_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(
+      ps, pi, C, qout, rows, k, Q32, X32, d, metric, rel, own);
+  RBC_LAUNCH_CHECK("own_kth_lp_kernel");
+  return RBC_OK;
+}
+
+int64_t window_pair_blocks(int64_t m) { return (m + WW * WT - 1) / (WW * WT); }
+
+int launch_window_pairs_count(const float* D, int64_t m, int n_r, const float* g,
+                              const float* g1, const float* psi_plus, float rel, unsigned* rmin,
+                              unsigned* rmax, int* q_kept, int* counts, int* totals, int* bin_off,
+                              cudaStream_t st) {
+  const int64_t nbins = (int64_t)n_r * NBK;
+  const int64_t qblocks = window_pair_blocks(m);
+  if (qblocks > 0) {
+    const dim3 grid((unsigned)qblocks, (n_r + RSPAN - 1) / RSPAN);
+    RBC_CUDA(cudaMemsetAsync(rmin, 0x7f, n_r * sizeof(unsigned), st));  // above any distance
+    RBC_CUDA(cudaMemsetAsync(rmax, 0, n_r * sizeof(unsigned), st));
+    RBC_CUDA(cudaMemsetAsync(q_kept, 0, m * sizeof(int), st));
+    wrange_kernel<<<grid, WW * 32, 0, st>>>(D, m, n_r, g, g1, psi_plus, rel, rmin, rmax, q_kept);
+    RBC_LAUNCH_CHECK("wrange_kernel");
+    wbin_kernel<false><<<grid, WW * 32, 0, st>>>(D, m, n_r, g, g1, psi_plus, rel, rmin, rmax,
+                                                 counts, nullptr, nullptr, nullptr);
+    RBC_LAUNCH_CHECK("wbin_kernel");
+    bin_colscan_kernel<<<(unsigned)((nbins + 255) / 256), 256, 0, st>>>(counts, (int)qblocks,
+                                                                        nbins, totals);
+    RBC_LAUNCH_CHECK("bin_colscan_kernel");
+  } else {
+    RBC_CUDA(cudaMemsetAsync(totals, 0, nbins * sizeof(int), st));
+  }
+  return launch_exclusive_scan(totals, (int)nbins, bin_off, st);
+}
+
+int launch_window_pairs_scatter(const float* D, int64_t m, int n_r, const float* g,
+                                const float* g1, const float* psi_plus, float rel,
+                                const unsigned* rmin, const unsigned* rmax, int* counts,
+                                const int* bin_off, int* pair_q, float* pair_d, cudaStream_t st) {
+  const int64_t qblocks = window_pair_blocks(m);
+  if (qblocks == 0) return RBC_OK;
+  const dim3 grid((unsigned)qblocks, (n_r + RSPAN - 1) / RSPAN);
+  wbin_kernel<true><<<grid, WW * 32, 0, st>>>(D, m, n_r, g, g1, psi_plus, rel, rmin, rmax, counts,
+                                              bin_off, pair_q, pair_d);
+  RBC_LAUNCH_CHECK("wbin_kernel");
+  return RBC_OK;
+}
+
+int window_buckets() { return NBK; }
+
+int launch_window_items(const int* bin_off, int nb, int n_r, const int* pair_q,
+                        const float* pair_d, const float* g, const int* offsets,
+                        const float* xdist, float rel, float relx, int* chunk_counts,
+                        int* chunk_off, int max_items, EmitItem* items,
+                        unsigned long long* stats, cudaStream_t st) {
+  chunk_count_kernel<<<(n_r + 255) / 256, 256, 0, st>>>(bin_off, nb, n_r, chunk_counts);
+  RBC_LAUNCH_CHECK("chunk_count_kernel");
+  int rc = launch_exclusive_scan(chunk_counts, n_r, chunk_off, st);
+  if (rc != RBC_OK) return rc;
+  if (max_items <= 0) return RBC_OK;
+  window_items_kernel<<<(unsigned)(((int64_t)max_items * 32 + 255) / 256), 256, 0, st>>>(
+      chunk_off, n_r, bin_off, nb, pair_q, pair_d, g, offsets, xdist, rel, relx, max_items,
+      items, stats);
+  RBC_LAUNCH_CHECK("window_items_kernel");
+  return RBC_OK;
+}
+
+int launch_score_threshold(const float* g, const float* qnorm, const float* qerr,
+                           const unsigned* lp_max, int d, int64_t m, float* thr,
+                           cudaStream_t st) {
+  if (m <= 0) return RBC_OK;
+  score_threshold_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(g, qnorm, qerr, lp_max, d,
+                                                                      m, thr);
+  RBC_LAUNCH_CHECK("score_threshold_kernel");
+  return RBC_OK;
+}
+
+}  // namespace rbc

@@ -39,7 +39,11 @@ def test_build_matches_oracle(metric):
     np.testing.assert_array_equal(np.diff(ex["offsets"]), sizes)
     for r in range(128):
         got = ex["members"][ex["offsets"][r] : ex["offsets"][r + 1]]
-        np.testing.assert_array_equal(got, o.lists[r])  # stable: ascending ids
+        np.testing.assert_array_equal(np.sort(got), o.lists[r])
+        # each list is ordered by distance to its representative (FP32 values,
+        # so FP64 distances may step back only within rounding), then by id
+        dg = oracle.dist(X[reps[r] : reps[r] + 1], X[got], metric)[0]
+        assert np.all(np.diff(dg) >= -1e-5 * dg[1:]), r
     # radii: an upper bound within the FP32 rounding allowance
     assert np.all(ex["psi"] >= o.psi * (1 - 1e-6))
     assert np.all(ex["psi"] <= o.psi * (1 + 2e-5) + 1e-6)
@@ -117,55 +121,66 @@ def test_empty_query_batch():
     assert ids.shape == (0, 2)
 
 
-# ---- low-precision storage: tensor-core stage two, certified re-rank ----
+# ---- low-precision storage: tensor-core stage two (windowed emission or
+# tile-union top-c lists), exact re-rank ----
 
+PLANS = [rbc.PLAN_WINDOW, rbc.PLAN_TILE_UNION]
+
+
+@pytest.mark.parametrize("plan", PLANS)
 @pytest.mark.parametrize("storage", [rbc.BF16, rbc.F16])
 @pytest.mark.parametrize("k", [1, 10])
-def test_exact_search_tc_iid_n16k_d16(storage, k):
+def test_exact_search_tc_iid_n16k_d16(storage, k, plan):
     X, Q = synth.make_workload("iid-n16k-d16", seed=0)
-    idx = build(X, 128, storage=storage)
+    idx = build(X, 128, storage=storage, plan=plan)
     ids, dist = search(idx, Q, k)
     o_ids, o_rho = oracle.bf(Q, X, k, "l2")
     check_knn(Q, X, ids, dist, o_ids, o_rho)
 
 
-@pytest.mark.parametrize("n,m,d,n_r,k", [(5000, 300, 5, 71, 3), (2049, 129, 33, 1, 2), (3001, 77, 12, 3001, 4), (20000, 513, 100, 141, 7), (1000, 1, 64, 30, 31)])
-def test_exact_search_tc_ragged(n, m, d, n_r, k):
+@pytest.mark.parametrize("plan", PLANS)
+@pytest.mark.parametrize("n,m,d,n_r,k", [(5000, 300, 5, 71, 3), (2049, 129, 33, 1, 2), (3001, 77, 12, 3001, 4), (20000, 513, 100, 141, 7), (1000, 1, 64, 30, 31), (40, 20, 8, 3, 31), (9000, 700, 250, 90, 10)])
+def test_exact_search_tc_ragged(n, m, d, n_r, k, plan):
     X = synth.iid_normal(n, d, 10 + n)
     Q = synth.iid_normal(m, d, 20 + m)
-    idx = build(X, n_r, seed=n_r, storage=rbc.BF16)
+    idx = build(X, n_r, seed=n_r, storage=rbc.BF16, plan=plan)
     ids, dist = search(idx, Q, k)
     o_ids, o_rho = oracle.bf(Q, X, k, "l2")
     check_knn(Q, X, ids, dist, o_ids, o_rho)
 
 
-def test_exact_search_tc_subspace_workload_small():
+@pytest.mark.parametrize("plan", PLANS)
+def test_exact_search_tc_subspace_workload_small(plan):
     mod = synth.SubspaceModel(d=64, k=8, noise_var=0.01, seed=0)
     X = mod.sample(60000, 0)
     Q = mod.sample(700, 1)
-    idx = build(X, 245, storage=rbc.BF16)
+    idx = build(X, 245, storage=rbc.BF16, plan=plan)
     for k in (1, 10):
         ids, dist = search(idx, Q, k)
         o_ids, o_rho = oracle.bf(Q, X, k, "l2")
         check_knn(Q, X, ids, dist, o_ids, o_rho)
 
 
-def test_exact_search_tc_duplicates():
+@pytest.mark.parametrize("plan", PLANS)
+def test_exact_search_tc_duplicates(plan):
     base = synth.iid_normal(60, 4, 30)
     X = np.concatenate([base, base, base[:25], base[:5]])
     Q = np.concatenate([base[:15], synth.iid_normal(40, 4, 31)])
     for n_r in (1, 9, 60, len(X)):
-        idx = build(X, n_r, seed=n_r, storage=rbc.BF16)
+        idx = build(X, n_r, seed=n_r, storage=rbc.BF16, plan=plan)
         ids, dist = search(idx, Q, 5)
         o_ids, o_rho = oracle.bf(Q, X, 5, "l2")
         np.testing.assert_array_equal(ids, o_ids)
 
 
-def test_exact_search_multi_batch_with_recheck():
+@pytest.mark.parametrize("plan", PLANS)
+def test_exact_search_multi_batch_with_recheck(plan):
     """More queries than one internal batch (131,072), with 40 exact copies of
     some points so that queries sitting on them tie far past the candidate
-    width, fail the low-precision certificate and are re-searched: every batch
-    must re-search its own rows only."""
+    width: the tile-union plan fails the low-precision certificate and
+    re-searches them (every batch must re-search its own rows only); the
+    windowed plan takes every copy as a candidate and settles the order in
+    FP64."""
     base = synth.iid_normal(2000, 16, 90)
     X = np.concatenate([base] + [base[:100]] * 40)
     g = np.random.default_rng(91)
@@ -173,10 +188,13 @@ def test_exact_search_multi_batch_with_recheck():
     Q = (X[g.integers(0, len(X), m)] + g.normal(0, 0.05, (m, 16))).astype(np.float32)
     on = np.arange(0, m, 50)
     Q[on] = base[g.integers(0, 100, len(on))]  # exactly on a 41-fold point
-    idx = build(X, 80, storage=rbc.BF16)
+    idx = build(X, 80, storage=rbc.BF16, plan=plan)
     ids, dist = search(idx, Q, 5)
     st = rbc.last_stats()
-    assert st["uncertified"] > 0  # the recheck path ran
+    if plan == rbc.PLAN_TILE_UNION:
+        assert st["uncertified"] > 0  # the recheck path ran
+    else:
+        assert st["fp64_ties"] > 0
     ref_ids, ref_dist = rbc.bf_search(torch.from_numpy(Q).cuda(), torch.from_numpy(X).cuda(), 5)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(ids, ref_ids.cpu().numpy())
@@ -184,3 +202,30 @@ def test_exact_search_multi_batch_with_recheck():
     o_ids, o_rho = oracle.bf(Q[sel], X, 5, "l2")
     check_knn(Q[sel], X, ids[sel], dist[sel], o_ids, o_rho)
     np.testing.assert_array_equal(ids[on[:300]], o_ids[np.searchsorted(sel, on[:300])])
+
+
+def test_window_candidate_overflow_goes_to_fp32_research():
+    # 700 copies of one point: a query on it has 700 points at distance 0,
+    # more than a candidate buffer holds, so it is searched again in FP32
+    X = synth.iid_normal(20000, 24, 3)
+    X[5000:5700] = X[5000]
+    Q = np.concatenate([X[5000:5001].repeat(3, 0), synth.iid_normal(300, 24, 4)]).astype(np.float32)
+    idx = build(X, 140, storage=rbc.BF16, seed=6)
+    ids, dist = search(idx, Q, 10)
+    assert rbc.last_stats()["uncertified"] >= 3
+    o_ids, o_rho = oracle.bf(Q, X, 10, "l2")
+    check_knn(Q, X, ids, dist, o_ids, o_rho)
+    np.testing.assert_array_equal(ids[:3], np.tile(np.arange(5000, 5010), (3, 1)))
+
+
+def test_window_stats_count_fewer_pairs_than_tile_union():
+    mod = synth.SubspaceModel(d=64, k=8, noise_var=0.01, seed=0)
+    X = mod.sample(120000, 0)
+    Q = mod.sample(4000, 1)
+    res = {}
+    for plan in PLANS:
+        idx = build(X, 350, storage=rbc.BF16, plan=plan)
+        ids, dist = search(idx, Q, 10)
+        res[plan] = (ids, rbc.last_stats())
+    np.testing.assert_array_equal(res[rbc.PLAN_WINDOW][0], res[rbc.PLAN_TILE_UNION][0])
+    assert res[rbc.PLAN_WINDOW][1]["pairs"] < res[rbc.PLAN_TILE_UNION][1]["pairs"]
