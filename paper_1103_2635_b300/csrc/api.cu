@@ -568,6 +568,8 @@ int bf_dense_lp(const float* Qdev, int64_t m, const DbView& db, int d, int k, in
   const int sms = sm_count();
   int64_t splits = (16LL * sms + tiles - 1) / tiles;
   splits = std::max<int64_t>(1, std::min<int64_t>(splits, std::max<int64_t>(1, db.rows / 8192)));
+  // a query merges splits x 2C partial entries: keep that within 2048
+  splits = std::min<int64_t>(splits, std::max(1, 2048 / (2 * C)));
   int64_t chunk = (db.rows + splits - 1) / splits;
   chunk = (chunk + 255) / 256 * 256;
   splits = (db.rows + chunk - 1) / chunk;
@@ -937,6 +939,7 @@ int build_oneshot(rbc_index* ix, const float* Xdev, const std::vector<int64_t>& 
 // query rows, and one work item per tile against its representative's list.
 struct Grouped {
   int64_t max_tiles = 0, rows_cap = 0;
+  int* qsrc = nullptr;      // padded row -> source row (or -1)
   int* qout = nullptr;      // padded row -> output row (or -1)
   int* tile_rep = nullptr;  // tile -> representative
   float* Qp = nullptr;      // [rows_cap, d]
@@ -945,7 +948,7 @@ struct Grouped {
 
 int group_queries(const rbc_index* ix, const float* Qsrc, int64_t mq, const int64_t* rep_of,
                   const int* orig, const int* list_off, unsigned long long* points_sum, Grouped& gq,
-                  Arena& ar, cudaStream_t st) {
+                  Arena& ar, cudaStream_t st, bool gather_fp32 = true) {
   const int d = ix->d, n_r = ix->n_r, s = ix->s;
   int *qperm, *qoff, *scratch;
   RBC_TRY(ar.alloc(&qperm, mq));
@@ -954,18 +957,21 @@ int group_queries(const rbc_index* ix, const float* Qsrc, int64_t mq, const int6
   RBC_TRY(launch_counting_sort(rep_of, mq, n_r, qperm, qoff, scratch, st));
   gq.max_tiles = (mq + TQ - 1) / TQ + std::min<int64_t>(n_r, mq);
   gq.rows_cap = gq.max_tiles * TQ;
-  int *pad_cnt, *pad_off, *qsrc;
+  int *pad_cnt, *pad_off;
   RBC_TRY(ar.alloc(&pad_cnt, n_r));
   RBC_TRY(ar.alloc(&pad_off, n_r + 1));
-  RBC_TRY(ar.alloc(&qsrc, gq.rows_cap));
+  RBC_TRY(ar.alloc(&gq.qsrc, gq.rows_cap));
+  int* qsrc = gq.qsrc;
   RBC_TRY(ar.alloc(&gq.qout, gq.rows_cap));
   RBC_TRY(ar.alloc(&gq.tile_rep, gq.max_tiles));
   RBC_CUDA(cudaMemsetAsync(qsrc, 0xff, gq.rows_cap * sizeof(int), st));
   RBC_CUDA(cudaMemsetAsync(gq.qout, 0xff, gq.rows_cap * sizeof(int), st));
   RBC_TRY(launch_oneshot_layout(qoff, n_r, qperm, orig, pad_cnt, pad_off, qsrc, gq.qout,
                                 gq.tile_rep, st));
-  RBC_TRY(ar.alloc(&gq.Qp, gq.rows_cap * d));
-  RBC_TRY(launch_gather_padded(Qsrc, qsrc, gq.rows_cap, d, gq.Qp, st));
+  if (gather_fp32) {
+    RBC_TRY(ar.alloc(&gq.Qp, gq.rows_cap * d));
+    RBC_TRY(launch_gather_padded(Qsrc, qsrc, gq.rows_cap, d, gq.Qp, st));
+  }
   WorkItem* items;
   Seg* segs;
   int* nitems;
@@ -1159,25 +1165,33 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   uint32_t* dev_err;
   RBC_TRY(ar.alloc(&dev_err, 1));
   RBC_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(uint32_t), st));
+  // low-precision copy of the batch (pass A and the emission pass)
+  LpQueries ql;
+  RBC_TRY(lp_queries(Qb, mb, d, ix->dpad, ix->storage, ql, ar, st));
   // pass A: the k-th distance inside the nearest representative's own list
-  // (tensor-core top-C kernel over the grouped queries; the k-th smallest
-  // score of a row bounds its k-th distance)
+  // (tensor-core top-C kernel over the grouped queries, then the FP32
+  // distances of each row's k best-scored candidates)
   float* own;
   RBC_TRY(ar.alloc(&own, mb));
   {
     Grouped gq;
-    RBC_TRY(group_queries(ix, Qb, mb, nearest, nullptr, ix->offsets, nullptr, gq, ar, st));
-    LpQueries qa;
-    RBC_TRY(lp_queries(gq.Qp, gq.rows_cap, d, ix->dpad, ix->storage, qa, ar, st));
+    RBC_TRY(group_queries(ix, Qb, mb, nearest, nullptr, ix->offsets, nullptr, gq, ar, st, false));
+    uint16_t* alp;
+    float *anorm, *aerr;
+    RBC_TRY(ar.alloc(&alp, gq.rows_cap * ix->dpad));
+    RBC_TRY(ar.alloc(&anorm, gq.rows_cap));
+    RBC_TRY(ar.alloc(&aerr, gq.rows_cap));
+    RBC_TRY(launch_gather_lp_rows(ql.lp, ql.norm, ql.err, gq.qsrc, gq.rows_cap, ix->dpad, alp, anorm,
+                                  aerr, st));
     const int C = k <= 8 ? 8 : (k <= 16 ? 16 : 32);
     float* ps;
     int* pi;
     RBC_TRY(ar.alloc(&ps, gq.max_tiles * TQ * 2 * C));
     RBC_TRY(ar.alloc(&pi, gq.max_tiles * TQ * 2 * C));
-    LpMatrix QmA{qa.lp, qa.norm, gq.rows_cap, ix->dpad, ix->storage};
+    LpMatrix QmA{alp, anorm, gq.rows_cap, ix->dpad, ix->storage};
     LpMatrix XmA{ix->Xlp, ix->xnorm, n, ix->dpad, ix->storage};
     RBC_TRY(launch_bf_tc_topc(QmA, XmA, C, gq.w, TopOut{ps, pi, nullptr}, sms, st, dev_err));
-    RBC_TRY(launch_own_kth_lp(ps, pi, C, gq.qout, gq.rows_cap, k, gq.Qp, ix->X32, d, ix->metric,
+    RBC_TRY(launch_own_kth_lp(ps, pi, C, gq.qsrc, gq.rows_cap, k, Qb, ix->X32, d, ix->metric,
                               rerank_eps_host(d) + 8.0f * U32, own, st));
   }
   float* g;
@@ -1218,8 +1232,6 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
                               items, cn.sums + 1, st));
   *items_total += max_items;
   // thresholds, then the tensor-core pass emitting candidates
-  LpQueries ql;
-  RBC_TRY(lp_queries(Qb, mb, d, ix->dpad, ix->storage, ql, ar, st));
   float* thr;
   RBC_TRY(ar.alloc(&thr, mb));
   RBC_TRY(launch_score_threshold(g, ql.norm, ql.err, ix->lp_max, d, mb, thr, st));
@@ -1275,21 +1287,47 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
     return (herr & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
   }
   if (nfb > 0) {
-    // queries whose candidate buffer overflowed: dense tensor-core search of
-    // the whole index with the widest lists (certified, FP32 behind it)
-    DbView db;
-    db.X32 = ix->X32;
-    db.xid = ix->members;
-    db.rows = n;
-    db.Xlp = ix->Xlp;
-    db.xnorm = ix->xnorm;
-    db.dpad = ix->dpad;
-    db.lp_max = ix->lp_max;
-    float* Qf;
-    RBC_TRY(ar.alloc(&Qf, (int64_t)nfb * d));
-    RBC_TRY(launch_gather_rows(Qb, nullptr, fb_rows, nfb, d, Qf, st));
-    RBC_TRY(bf_dense_lp(Qf, nfb, db, d, k, ix->storage, MAX_C, ids, dist, cn.c + 4, ar, st,
-                        fb_rows, 1));
+    // Queries whose candidate buffer overflowed: k of the stored candidates
+    // give a much tighter threshold; emit again for them alone against the
+    // whole list storage, then finish them.  Whatever still overflows (more
+    // than the buffer of points tied within rounding) goes to the FP32 BF.
+    RBC_TRY(launch_overflow_rethreshold(fb_rows, nfb, cs, cc, CAND_CAP, k, ql.norm, ql.err,
+                                        ix->lp_max, d, thr, st));
+    const int xspan = (int)std::max<int64_t>(4096, (n + 2 * sms - 1) / (2 * sms) / 256 * 256);
+    const int64_t nsplit = (n + xspan - 1) / xspan;
+    const int n2 = (int)(((int64_t)nfb + TQ - 1) / TQ * nsplit);
+    EmitItem* items2;
+    RBC_TRY(ar.alloc(&items2, n2));
+    RBC_TRY(launch_dense_emit_items(nfb, n, xspan, items2, st));
+    RBC_TRY(launch_bf_tc_emit(Qm, Xm, items2, nullptr, n2, fb_rows, eo, sms, st, dev_err));
+    int* fb2;
+    int* lc2;
+    RBC_TRY(ar.alloc(&fb2, nfb));
+    RBC_TRY(ar.alloc(&lc2, 8));
+    RBC_CUDA(cudaMemsetAsync(lc2, 0, 8 * sizeof(int), st));
+    CandSelectArgs a2 = a;
+    a2.rows = fb_rows;
+    a2.nrows = nfb;
+    a2.fallback_rows = fb2;
+    a2.counters = lc2;
+    RBC_TRY(launch_select_cands(a2, st));
+    RBC_TRY(launch_add_ints(cn.c + 4, lc2, 3, st));
+    int nfb2 = 0;
+    RBC_CUDA(cudaMemcpyAsync(&nfb2, lc2, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBC_CUDA(cudaMemcpyAsync(&herr, dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    RBC_CUDA(cudaStreamSynchronize(st));
+    if (herr) {
+      set_error("windowed stage two (overflow pass) reported device error flags 0x%x", herr);
+      return (herr & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
+    }
+    if (nfb2 > 0) {
+      DbView db;
+      db.X32 = ix->X32;
+      db.xid = ix->members;
+      db.rows = n;
+      RBC_TRY(fallback_f32(Qb, fb2, nfb2, nullptr, db, d, k, ix->metric, ids, dist, cn.c + 4, ar,
+                           st));
+    }
   }
   tmark(4, st);
   taccumulate();

@@ -39,7 +39,6 @@ using namespace tc;
 
 constexpr int E_GATHER = 2;     // query-gather warp
 constexpr int E_EPI0 = 4;       // first epilogue warp (warp 3 idles)
-constexpr int QSTAGES = 2;      // query stages
 
 // Epilogue parts: the tile's columns are split into NPART slices of BN/NPART
 // (at least 32) columns; each (TMEM lane quarter, slice) is one warp.
@@ -64,7 +63,7 @@ struct EmitParams {
   uint32_t* dev_err;
 };
 
-template <int KB, int BN, int S, int NR>
+template <int KB, int BN, int S, int NR, int QSTAGES>
 struct EmitSmem {
   static constexpr int NBUF = (512 / BN) < 4 ? (512 / BN) : 4;  // TMEM accumulator buffers
   static constexpr int Q_BYTES = KB * BM * 128;
@@ -94,10 +93,12 @@ __device__ __forceinline__ void st_shared_zero16(uint32_t dst) {
   asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(dst), "r"(0) : "memory");
 }
 
-template <int KB, int BN, int S, int NR>
+// QSTAGES query stages: the gather of an item's rows takes a few
+// microseconds, longer than a one-tile item, so several are kept in flight.
+template <int KB, int BN, int S, int NR, int QSTAGES>
 __global__ void __launch_bounds__(EpiShape<BN>::THREADS, 1)
 bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32_t idesc) {
-  using L = EmitSmem<KB, BN, S, NR>;
+  using L = EmitSmem<KB, BN, S, NR, QSTAGES>;
   using E = EpiShape<BN>;
   constexpr int E_NEPI = E::NEPI;
   extern __shared__ uint8_t smem_raw[];
@@ -325,7 +326,6 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32
         const float* nrm = sNorm + r * BN + part * COLS;
         const int lo = e.x_begin - x - part * COLS;  // first valid column of the slice
         const int hi = e.x_end - x - part * COLS;    // one past the last valid column
-        const bool partial = lo > 0 || hi < COLS;
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
           float u[32];
@@ -338,27 +338,29 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32
             fma2(u[4 * j + 2], u[4 * j + 3], __uint_as_float(raw[c][4 * j + 2]),
                  __uint_as_float(raw[c][4 * j + 3]), -2.0f, nn.z, nn.w);
           }
-          if (partial) {
-            // columns outside the window become NaN: never <= a threshold
-            // (not even an infinite one), and ignored by min.f32
+          // The minimum runs over all 32 columns, including any outside the
+          // window (real rows, or zero rows past the matrix end): a false
+          // alarm only costs the slow path, where the in-window mask decides.
+          const bool hit = min_of32(u) <= myT;
+          if (__any_sync(0xffffffffu, hit)) {  // warp-uniform: the rare path
+            if (hit) {
+              const int clo = lo - c * 32, chi = hi - c * 32;
+              const uint32_t below_hi = chi >= 32 ? 0xffffffffu : (chi <= 0 ? 0u : (1u << chi) - 1u);
+              const uint32_t below_lo = clo >= 32 ? 0xffffffffu : (clo <= 0 ? 0u : (1u << clo) - 1u);
+              const uint32_t valid = below_hi & ~below_lo;
+              const int cb = x + part * COLS + c * 32;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int col = c * 32 + j;
-              if (col < lo || col >= hi) u[j] = __int_as_float(0x7fffffff);
-            }
-          }
-          if (min_of32(u) <= myT) {
-            const int cb = x + part * COLS + c * 32;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              if (u[j] <= myT) {
-                const int pos = atomicAdd(cc, 1);
-                if (pos < cap) {
-                  cs[pos] = u[j];
-                  cr[pos] = cb + j;
+              for (int j = 0; j < 32; ++j) {
+                if (((valid >> j) & 1u) && u[j] <= myT) {
+                  const int pos = atomicAdd(cc, 1);
+                  if (pos < cap) {
+                    cs[pos] = u[j];
+                    cr[pos] = cb + j;
+                  }
                 }
               }
             }
+            __syncwarp();
           }
         }
         __syncwarp();
@@ -376,14 +378,14 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32
   }
 }
 
-template <int KB, int BN, int S, int NR>
+template <int KB, int BN, int S, int NR, int QS>
 int launch_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
                 const int* num_items_dev, int max_items, const int* pair_q, const EmitOut& out,
                 int grid, cudaStream_t st, uint32_t* dev_err) {
-  using L = EmitSmem<KB, BN, S, NR>;
+  using L = EmitSmem<KB, BN, S, NR, QS>;
   CUtensorMap xmap;
   RBC_TRY_TC(encode_map(&xmap, Xm.data, Xm.rows, Xm.dpad, Xm.storage, BN));
-  auto kern = bf_tc_emit_kernel<KB, BN, S, NR>;
+  auto kern = bf_tc_emit_kernel<KB, BN, S, NR, QS>;
   RBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC));
   EmitParams p{items,   num_items_dev, max_items, pair_q, static_cast<const uint8_t*>(Qm.data),
                (int64_t)Qm.dpad * 2, Xm.norm, out, dev_err};
@@ -394,9 +396,9 @@ int launch_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
   if (e != cudaSuccess) {
     cudaFuncAttributes fa{};
     cudaFuncGetAttributes(&fa, kern);
-    set_error("bf_tc_emit_kernel<KB=%d,BN=%d,S=%d> launch failed: %s (regs %d, local %zu, "
+    set_error("bf_tc_emit_kernel<KB=%d,BN=%d,S=%d,QS=%d> launch failed: %s (regs %d, local %zu, "
               "dynamic smem %d)",
-              KB, BN, S, cudaGetErrorString(e), fa.numRegs, fa.localSizeBytes, L::ALLOC);
+              KB, BN, S, QS, cudaGetErrorString(e), fa.numRegs, fa.localSizeBytes, L::ALLOC);
     return RBC_ERR_CUDA;
   }
   return RBC_OK;
@@ -417,10 +419,10 @@ int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* it
   }
   if (max_items <= 0) return RBC_OK;
   switch (Qm.dpad / 64) {
-    case 1: return launch_emit<1, 256, 4, 8>(Qm, Xm, items, num_items_dev, max_items, pair_q, out, grid, st, dev_err);
-    case 2: return launch_emit<2, 128, 3, 8>(Qm, Xm, items, num_items_dev, max_items, pair_q, out, grid, st, dev_err);
-    case 3: return launch_emit<3, 64, 3, 8>(Qm, Xm, items, num_items_dev, max_items, pair_q, out, grid, st, dev_err);
-    case 4: return launch_emit<4, 64, 2, 4>(Qm, Xm, items, num_items_dev, max_items, pair_q, out, grid, st, dev_err);
+    case 1: return launch_emit<1, 256, 4, 8, 4>(Qm, Xm, items, num_items_dev, max_items, pair_q, out, grid, st, dev_err);
+    case 2: return launch_emit<2, 128, 3, 8, 3>(Qm, Xm, items, num_items_dev, max_items, pair_q, out, grid, st, dev_err);
+    case 3: return launch_emit<3, 64, 3, 8, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, out, grid, st, dev_err);
+    case 4: return launch_emit<4, 64, 2, 4, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, out, grid, st, dev_err);
     default: break;
   }
   set_error("tensor-core BF: padded dimension %d unsupported", Qm.dpad);

@@ -115,6 +115,8 @@ struct CandSelectArgs {
   const int* cand_cnt;      // [m] emissions (may exceed cap: overflow)
   int cap;
   int64_t m;
+  const int* rows;   // optional: the queries to finish (nrows of them); else 0 .. m-1
+  int nrows;
   const float* Q32;  // [m, d] queries FP32
   int d;
   int metric;
@@ -139,16 +141,12 @@ int launch_select_cands(const CandSelectArgs& a, cudaStream_t st);
 // k-th nearest-neighbour distance
 int launch_gbound(const float* own, const float* gk, int64_t m, float rel_rep, float* g,
                   cudaStream_t st);
-// own[qout[row]] = the k-th smallest FP32 distance of grouped row `row` from
-// the two sorted sub-lists of the FP32 tile kernel ([tile][TQ][2][C]),
-// rounded up by rel (INF if fewer than k)
-int launch_own_kth(const float* ps, int C, const int* qout, int64_t rows, int k, int metric,
-                   float rel, float* own, cudaStream_t st);
-// the same from the tensor-core top-C lists ([tile][TQ][2][C] unsorted
-// low-precision scores and list-ordered rows, C <= 32): the largest FP32
-// distance of the k best-scored rows, rounded up by rel (Q32: the grouped
-// query rows)
-int launch_own_kth_lp(const float* ps, const int* pi, int C, const int* qout, int64_t rows,
+// Own-list bound of every grouped query row from the tensor-core top-C lists
+// ([tile][TQ][2][C] unsorted low-precision scores and list-ordered rows,
+// C <= 32): own[qsrc[row]] = the largest FP32 distance of the row's k
+// best-scored rows, rounded up by rel (INF if fewer than k); Q32 holds the
+// batch queries, qsrc maps grouped rows to them (-1: padding)
+int launch_own_kth_lp(const float* ps, const int* pi, int C, const int* qsrc, int64_t rows,
                       int k, const float* Q32, const float* X32, int d, int metric, float rel,
                       float* own, cudaStream_t st);
 // Kept (q, r) pairs binned by (r, bucket of rho(q, r)), window_buckets() per
@@ -173,6 +171,15 @@ int launch_window_items(const int* bin_off, int nb, int n_r, const int* pair_q,
                         const float* xdist, float rel, float relx, int* chunk_counts,
                         int* chunk_off, int max_items, EmitItem* items,
                         unsigned long long* stats, cudaStream_t st);
+// Second pass for queries whose candidate buffer overflowed (rows[i], i < n):
+// threshold = score_bound(dist_upper(k-th smallest stored score)), which k
+// stored candidates already meet, and the buffer count reset to zero; then
+// items over the whole list storage (chunks of TQ of these queries x row
+// spans of xspan) for the emission kernel.
+int launch_overflow_rethreshold(const int* rows, int n, const float* cand_score, int* cand_cnt,
+                                int cap, int k, const float* qnorm, const float* qerr,
+                                const unsigned* lp_max, int d, float* thr, cudaStream_t st);
+int launch_dense_emit_items(int n, int64_t x_rows, int xspan, EmitItem* items, cudaStream_t st);
 int launch_score_threshold(const float* g, const float* qnorm, const float* qerr,
                            const unsigned* lp_max, int d, int64_t m, float* thr,
                            cudaStream_t st);
@@ -224,6 +231,11 @@ int launch_gather_rows(const float* src, const int64_t* idx64, const int* idx32,
 int launch_to_lowp(const float* src, int64_t rows, int d, int dpad, int storage, void* dst,
                    float* norm, float* err, unsigned* err_max_bits, unsigned* norm_max_bits,
                    cudaStream_t st);
+// dst row i = src row idx[i] of a bf16 / fp16 [*, dpad] matrix plus its norm
+// and residual; idx[i] < 0 gives a zero row
+int launch_gather_lp_rows(const void* src, const float* snorm, const float* serr, const int* idx,
+                          int64_t rows, int dpad, void* dst, float* dnorm, float* derr,
+                          cudaStream_t st);
 // out[i] = qorig ? qorig[rows[i]] : rows[i], for i < *n_dev (or n when n_dev is null)
 int launch_map_rows(const int* rows, const int* n_dev, int n, const int* qorig, int* out,
                     cudaStream_t st);

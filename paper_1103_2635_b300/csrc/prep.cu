@@ -87,6 +87,25 @@ __global__ void to_lowp_kernel(const float* __restrict__ src, int64_t rows, int 
   }
 }
 
+// dst row i = src row idx[i] of a 16-bit [*, dpad] matrix with its norm and
+// residual; idx[i] < 0 gives a zero row (norm 0, residual 0).  One warp per
+// row, 16-byte copies.
+__global__ void gather_lp_rows_kernel(const uint4* __restrict__ src, const float* __restrict__ snorm,
+                                      const float* __restrict__ serr, const int* __restrict__ idx,
+                                      int64_t rows, int vec_per_row, uint4* __restrict__ dst,
+                                      float* __restrict__ dnorm, float* __restrict__ derr) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= rows) return;
+  const int s = idx[w];
+  for (int j = lane; j < vec_per_row; j += 32)
+    dst[w * vec_per_row + j] = s >= 0 ? src[(int64_t)s * vec_per_row + j] : make_uint4(0, 0, 0, 0);
+  if (lane == 0) {
+    dnorm[w] = s >= 0 ? snorm[s] : 0.0f;
+    derr[w] = s >= 0 ? serr[s] : 0.0f;
+  }
+}
+
 __global__ void map_rows_kernel(const int* __restrict__ rows, const int* __restrict__ n_dev, int n,
                                 const int* __restrict__ qorig, int* __restrict__ out) {
   int lim = n_dev ? *n_dev : n;
@@ -130,6 +149,17 @@ int launch_to_lowp(const float* src, int64_t rows, int d, int dpad, int storage,
                                                    reinterpret_cast<__half*>(dst), norm, err,
                                                    err_max_bits, norm_max_bits);
   RBC_LAUNCH_CHECK("to_lowp_kernel");
+  return RBC_OK;
+}
+
+int launch_gather_lp_rows(const void* src, const float* snorm, const float* serr, const int* idx,
+                          int64_t rows, int dpad, void* dst, float* dnorm, float* derr,
+                          cudaStream_t st) {
+  if (rows <= 0) return RBC_OK;
+  gather_lp_rows_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(
+      static_cast<const uint4*>(src), snorm, serr, idx, rows, dpad * 2 / 16,
+      static_cast<uint4*>(dst), dnorm, derr);
+  RBC_LAUNCH_CHECK("gather_lp_rows_kernel");
   return RBC_OK;
 }
 

@@ -131,7 +131,12 @@ __global__ void list_radii_kernel(const float* __restrict__ dist_by_id, const in
   if (lane == 0) psi_plus[w] = mx * (1.0f + rel);
 }
 
-template <int KW>
+// One warp per query row of D (distances >= 0, so their bit patterns order
+// like their values): gamma_1 and the nearest column by a warp arg-min
+// (ties to the smaller column); gamma_k by a bitwise search for the k-th
+// smallest bit pattern, counting with the whole warp (rows of up to 1024
+// values are held in registers).
+template <bool CACHED>
 __global__ void row_stats_kernel(const float* __restrict__ D, int64_t m, int n_r, int k,
                                  float* __restrict__ g1, float* __restrict__ gk,
                                  int64_t* __restrict__ nearest) {
@@ -139,49 +144,60 @@ __global__ void row_stats_kernel(const float* __restrict__ D, int64_t m, int n_r
   const int lane = threadIdx.x & 31;
   if (w >= m) return;
   const float* row = D + w * n_r;
-  TopList<KW> lst;
-  lst.init();
-  for (int c = lane; c < n_r; c += 32) {
-    float v = row[c];
-    if (lst.admits(v, c)) lst.insert(v, c);
+  unsigned vals[CACHED ? 32 : 1];
+  float bv = INFINITY;
+  int bi = INT32_MAX;
+  if (CACHED) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int c = lane + 32 * j;
+      const float v = c < n_r ? row[c] : INFINITY;
+      vals[j] = __float_as_uint(v);
+      if (v < bv) {
+        bv = v;
+        bi = c;
+      }
+    }
+  } else {
+    for (int c = lane; c < n_r; c += 32) {
+      const float v = row[c];
+      if (v < bv) {
+        bv = v;
+        bi = c;
+      }
+    }
   }
-  // k rounds of warp arg-min over the lane heads (lists live in registers:
-  // the head is selected with a fully unrolled scan)
-  int head = 0;
-  float first = INFINITY, kth = INFINITY;
-  int first_id = 0;
-  const int rounds = min(k, n_r);
-  for (int j = 0; j < rounds; ++j) {
-    float hv = INFINITY;
-    int hi = INT32_MAX;
 #pragma unroll
-    for (int t = 0; t < KW; ++t)
-      if (t == head) {
-        hv = lst.s[t];
-        hi = lst.i[t];
-      }
-    float bv = hv;
-    int bi = hi;
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov < bv || (ov == bv && oi < bi)) {
+      bv = ov;
+      bi = oi;
+    }
+  }
+  float kth = INFINITY;
+  if (k <= n_r) {
+    unsigned res = 0;
+    for (int bit = 31; bit >= 0; --bit) {
+      const unsigned t = res | (1u << bit);
+      int cnt = 0;
+      if (CACHED) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (pair_lt(ov, oi, bv, bi)) {
-        bv = ov;
-        bi = oi;
+        for (int j = 0; j < 32; ++j) cnt += vals[j] < t;
+      } else {
+        for (int c = lane; c < n_r; c += 32) cnt += __float_as_uint(row[c]) < t;
       }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+      if (cnt < k) res = t;
     }
-    if (hi == bi && hv == bv) ++head;
-    if (j == 0) {
-      first = bv;
-      first_id = bi;
-    }
-    kth = bv;
+    kth = __uint_as_float(res);
   }
   if (lane == 0) {
-    g1[w] = first;
-    gk[w] = (k <= n_r) ? kth : INFINITY;
-    nearest[w] = first_id;
+    g1[w] = bv;
+    gk[w] = kth;
+    nearest[w] = bi;
   }
 }
 
@@ -478,26 +494,12 @@ int launch_list_radii(const float* dist_by_id, const int* perm, const int* offse
 int launch_row_stats(const float* D, int64_t m, int n_r, int k, float* g1, float* gk,
                      int64_t* nearest, cudaStream_t st) {
   if (m <= 0) return RBC_OK;
-  unsigned blocks = (unsigned)((m * 32 + 255) / 256);
-  int kk = k < n_r ? k : n_r;
-  if (kk <= 1)
-    row_stats_kernel<1><<<blocks, 256, 0, st>>>(D, m, n_r, k, g1, gk, nearest);
-  else if (kk <= 2)
-    row_stats_kernel<2><<<blocks, 256, 0, st>>>(D, m, n_r, k, g1, gk, nearest);
-  else if (kk <= 4)
-    row_stats_kernel<4><<<blocks, 256, 0, st>>>(D, m, n_r, k, g1, gk, nearest);
-  else if (kk <= 8)
-    row_stats_kernel<8><<<blocks, 256, 0, st>>>(D, m, n_r, k, g1, gk, nearest);
-  else if (kk <= 16)
-    row_stats_kernel<16><<<blocks, 256, 0, st>>>(D, m, n_r, k, g1, gk, nearest);
-  else if (kk <= 32)
-    row_stats_kernel<32><<<blocks, 256, 0, st>>>(D, m, n_r, k, g1, gk, nearest);
-  else {
-    set_error("row_stats: k = %d too large", k);
-    return RBC_ERR_UNSUPPORTED;
-  }
+  const unsigned blocks = (unsigned)((m * 32 + 255) / 256);
+  if (n_r <= 1024)
+    row_stats_kernel<true><<<blocks, 256, 0, st>>>(D, m, n_r, k, g1, gk, nearest);
+  else
+    row_stats_kernel<false><<<blocks, 256, 0, st>>>(D, m, n_r, k, g1, gk, nearest);
   RBC_LAUNCH_CHECK("row_stats_kernel");
-  // when n_r < k every representative is kept: gamma_k = +inf
   return RBC_OK;
 }
 

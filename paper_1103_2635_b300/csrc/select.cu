@@ -327,8 +327,9 @@ __global__ void __launch_bounds__(WARPS * 32) select_cands_kernel(CandSelectArgs
   __shared__ int stage[WARPS][RERANK_MAX];
   const int wib = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int64_t q = (int64_t)blockIdx.x * WARPS + wib;
-  if (q >= a.m) return;
+  const int64_t wi = (int64_t)blockIdx.x * WARPS + wib;
+  if (wi >= (a.rows ? (int64_t)a.nrows : a.m)) return;
+  const int64_t q = a.rows ? (int64_t)a.rows[wi] : wi;
   const int cnt = a.cand_cnt[q];
   const int k = a.k;
   auto to_research = [&]() {
@@ -468,7 +469,8 @@ int launch_select_cands(const CandSelectArgs& a, cudaStream_t st) {
     set_error("select_cands: bad k=%d c_out=%d cap=%d", a.k, a.c_out, a.cap);
     return RBC_ERR_ARG;
   }
-  const int64_t blocks = (a.m + WARPS - 1) / WARPS;
+  const int64_t nw = a.rows ? (int64_t)a.nrows : a.m;
+  const int64_t blocks = (nw + WARPS - 1) / WARPS;
   if (blocks == 0) return RBC_OK;
   select_cands_kernel<<<(unsigned)blocks, WARPS * 32, 0, st>>>(a);
   RBC_LAUNCH_CHECK("select_cands_kernel");

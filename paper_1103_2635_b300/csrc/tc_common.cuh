@@ -57,6 +57,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
   return ok != 0;
 }
 
+// The same with a suspend-time hint: a thread whose phase is not complete
+// may sleep up to `ns` nanoseconds (it wakes when the phase completes), so
+// waiting warps leave the issue slots to the working ones.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* b, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait for the phase with the given parity.  Returns false (and sets
 // the CTA's abort flag and the device error word) if the wait expired or
 // another role already aborted.
@@ -65,8 +80,8 @@ static __device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, vola
   if (mbar_try_wait(b, parity)) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t i = 0;; ++i) {
-    if (mbar_try_wait(b, parity)) return true;
-    if ((i & 63) == 63) {
+    if (mbar_try_wait_sleep(b, parity, 1000)) return true;
+    if ((i & 15) == 15) {
       if (*abort_flag) return false;
       if (global_ns() - t0 > WAIT_NS) {
         *abort_flag = 1;

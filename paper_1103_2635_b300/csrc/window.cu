@@ -24,6 +24,8 @@
 // warp walks the representatives: bin counters are then updated once per
 // (warp, representative, bucket) and the scattered pairs of one bin land in
 // consecutive slots.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -50,47 +52,19 @@ __global__ void gbound_kernel(const float* __restrict__ own, const float* __rest
   g[q] = fminf(gk[q] * (1.0f + rel_rep) * SLACK, own[q]);
 }
 
-// k-th smallest FP32 distance of every grouped query row from the two sorted
-// sub-lists its tile kernel left (scores are rho^2 for l2), rounded up by the
-// kernel's bound: an upper bound of the k-th distance inside its list
-__global__ void own_kth_kernel(const float* __restrict__ ps, int C, const int* __restrict__ qout,
-                               int64_t rows, int k, int l2, float rel, float* __restrict__ own) {
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= rows) return;
-  const int q = qout[row];
-  if (q < 0) return;
-  const int64_t b0 = row * 2 * (int64_t)C;  // slot = tile, [slot][TQ][2][C]
-  const float* a = ps + b0;
-  const float* b = a + C;
-  int i = 0, j = 0;
-  float v = INFINITY;
-  for (int t = 0; t < k; ++t) {
-    const float x = i < C ? a[i] : INFINITY;
-    const float y = j < C ? b[j] : INFINITY;
-    if (x <= y) {
-      v = x;
-      ++i;
-    } else {
-      v = y;
-      ++j;
-    }
-  }
-  own[q] = v < INFINITY ? (l2 ? sqrtf(v) : v) * (1.0f + rel) * SLACK : INFINITY;
-}
-
 // Own-list bound from the tensor-core top-C lists of the grouped rows, one
 // warp per row: the k best-scored candidates of the row's two sub-lists are
 // k distinct points of its list, so the largest of their FP32 distances
 // (rounded up by the re-rank bound) bounds the row's k-th distance.  If the
 // lists hold fewer than k points the bound is infinite.
 __global__ void own_kth_lp_kernel(const float* __restrict__ ps, const int* __restrict__ pi, int C,
-                                  const int* __restrict__ qout, int64_t rows, int k,
+                                  const int* __restrict__ qsrc, int64_t rows, int k,
                                   const float* __restrict__ Q32, const float* __restrict__ X32,
                                   int d, int metric, float rel, float* __restrict__ own) {
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= rows) return;
-  const int q = qout[row];
+  const int q = qsrc[row];  // the batch query of this grouped row
   if (q < 0) return;
   const int64_t base = row * 2 * (int64_t)C;  // [slot = tile][TQ][2][C]
   // up to 2C <= 64 entries, two per lane
@@ -137,7 +111,7 @@ __global__ void own_kth_lp_kernel(const float* __restrict__ ps, const int* __res
   float rho = 0.0f;
   bool missing = lane < k && mine < 0;
   if (lane < k && mine >= 0) {
-    const float* qr = Q32 + row * d;
+    const float* qr = Q32 + (int64_t)q * d;
     const float* xr = X32 + (int64_t)mine * d;
     float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
     int i = 0;
@@ -228,10 +202,14 @@ wrange_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __re
       const int nr = min(WT, re - r0);
       for (int rr = 0; rr < nr; ++rr) {
         const float v = tiles[wid][lane][rr];
-        if (c.live && keep_pair(v, c.lo, c.gh, psi_plus[r0 + rr], c.lemma)) {
-          ++kept;
-          atomicMin(&smin[r0 + rr - rb], __float_as_uint(v));
-          atomicMax(&smax[r0 + rr - rb], __float_as_uint(v));
+        const bool kp = c.live && keep_pair(v, c.lo, c.gh, psi_plus[r0 + rr], c.lemma);
+        kept += kp;
+        // warp reductions first: one shared-memory update per (warp, r)
+        const unsigned vmin = __reduce_min_sync(0xffffffffu, kp ? __float_as_uint(v) : 0xffffffffu);
+        const unsigned vmax = __reduce_max_sync(0xffffffffu, kp ? __float_as_uint(v) : 0u);
+        if (lane == 0 && vmin != 0xffffffffu) {
+          atomicMin(&smin[r0 + rr - rb], vmin);
+          atomicMax(&smax[r0 + rr - rb], vmax);
         }
       }
       __syncwarp();
@@ -267,10 +245,10 @@ wbin_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __rest
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rb = blockIdx.y * RSPAN, re = min(n_r, rb + RSPAN);
   const int64_t nbins = (int64_t)n_r * NBK;
-  const int64_t crow = (int64_t)blockIdx.x * nbins;  // this block's row of counts
+  const int64_t nqb = gridDim.x;  // counts are [bin][query block]
   for (int i = threadIdx.x; i < RSPAN * NBK; i += blockDim.x) {
     const int64_t bin = (int64_t)rb * NBK + i;
-    h[i] = SCATTER ? (bin < nbins ? bin_off[bin] + counts[crow + bin] : 0) : 0;
+    h[i] = SCATTER ? (bin < nbins ? bin_off[bin] + counts[bin * nqb + blockIdx.x] : 0) : 0;
   }
   for (int i = threadIdx.x; i < re - rb; i += blockDim.x) {
     const float blo = __uint_as_float(rmin[rb + i]);
@@ -303,23 +281,32 @@ wbin_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __rest
   if (!SCATTER) {
     __syncthreads();
     for (int i = threadIdx.x; i < (re - rb) * NBK; i += blockDim.x)
-      counts[crow + (int64_t)rb * NBK + i] = h[i];
+      counts[((int64_t)rb * NBK + i) * nqb + blockIdx.x] = h[i];
   }
 }
 
-// per bin: exclusive prefix over the query blocks in place, totals[bin] = sum
-__global__ void bin_colscan_kernel(int* __restrict__ counts, int nblocks, int64_t nbins,
+// per bin (one warp): exclusive prefix over the query blocks in place
+// (counts are [bin][query block]), totals[bin] = sum
+__global__ void bin_colscan_kernel(int* __restrict__ counts, int nqb, int64_t nbins,
                                    int* __restrict__ totals) {
-  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (b >= nbins) return;
-  int run = 0;
-  for (int k = 0; k < nblocks; ++k) {
-    const int64_t o = (int64_t)k * nbins + b;
-    const int c = counts[o];
-    counts[o] = run;
-    run += c;
+  int* col = counts + b * nqb;
+  int carry = 0;
+  for (int i0 = 0; i0 < nqb; i0 += 32) {
+    const int i = i0 + lane;
+    const int v = i < nqb ? col[i] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (i < nqb) col[i] = carry + x - v;
+    carry += __shfl_sync(0xffffffffu, x, 31);
   }
-  totals[b] = run;
+  if (lane == 0) totals[b] = carry;
 }
 
 // per representative: chunks of TQ pairs in its group
@@ -329,70 +316,142 @@ __global__ void chunk_count_kernel(const int* __restrict__ bin_off, int nb, int 
   if (r < n_r) out[r] = (bin_off[(r + 1) * nb] - bin_off[r * nb] + TQ - 1) / TQ;
 }
 
-// first index i in [0, n) with a[i] >= v (n if none)
-__device__ __forceinline__ int lower_bound_f(const float* a, int n, float v) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (a[mid] < v) lo = mid + 1; else hi = mid;
+// Warp-cooperative search in a sorted array: the first index i in [0, n)
+// with a[i] >= v (LOWER) or a[i] > v (!LOWER), n if none.  Each round probes
+// 32 evenly spaced positions at once and keeps the gap holding the answer,
+// so a list of N entries costs about log_32(N) dependent loads.
+template <bool LOWER>
+__device__ __forceinline__ int warp_bound(const float* __restrict__ a, int n, float v, int lane) {
+  int lo = 0, hi = n;  // the answer lies in [lo, hi]
+  while (hi - lo > 32) {
+    const int64_t len = hi - lo;
+    const int p = lo + (int)((len * lane) >> 5);
+    const bool before = LOWER ? a[p] < v : a[p] <= v;
+    const int c = __popc(__ballot_sync(0xffffffffu, before));  // probes before the answer
+    const int nlo = c == 0 ? lo : lo + (int)((len * (c - 1)) >> 5) + 1;
+    const int nhi = c == 32 ? hi : lo + (int)((len * c) >> 5);
+    lo = nlo;
+    hi = nhi;
   }
-  return lo;
-}
-// first index i in [0, n) with a[i] > v (n if none)
-__device__ __forceinline__ int upper_bound_f(const float* a, int n, float v) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (a[mid] <= v) lo = mid + 1; else hi = mid;
-  }
-  return lo;
+  const int p = lo + lane;
+  const bool before = p < hi && (LOWER ? a[p] < v : a[p] <= v);
+  return lo + __popc(__ballot_sync(0xffffffffu, before));
 }
 
-// One warp per chunk: the union of its queries' windows, cut from the sorted
-// list by binary search.
-__global__ void window_items_kernel(const int* __restrict__ chunk_off, int n_r,
-                                    const int* __restrict__ bin_off, int nb,
-                                    const int* __restrict__ pair_q, const float* __restrict__ pair_d,
-                                    const float* __restrict__ g, const int* __restrict__ offsets,
-                                    const float* __restrict__ xdist, float rel, float relx,
-                                    int max_items, EmitItem* __restrict__ items,
-                                    unsigned long long* __restrict__ stats) {
-  const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  const int total = chunk_off[n_r];
-  if (c >= total || c >= max_items) return;
-  // the group holding chunk c: last r with chunk_off[r] <= c
-  int lo_r = 0, hi_r = n_r;  // invariant: chunk_off[lo_r] <= c < chunk_off[hi_r]
-  while (hi_r - lo_r > 1) {
-    const int mid = (lo_r + hi_r) >> 1;
-    if (chunk_off[mid] <= c) lo_r = mid; else hi_r = mid;
-  }
-  const int r = lo_r;
-  const int begin = bin_off[r * nb] + ((int)c - chunk_off[r]) * TQ;
-  const int end = min(begin + TQ, bin_off[(r + 1) * nb]);
-  float wlo = INFINITY, whi = -INFINITY;
+// Warps loop over chunks: the union of each chunk's windows, cut from the
+// sorted list by a cooperative binary search.  Statistics are summed per
+// block and added once per block.
+__global__ void __launch_bounds__(256)
+window_items_kernel(const int* __restrict__ chunk_off, int n_r, const int* __restrict__ bin_off,
+                    int nb, const int* __restrict__ pair_q, const float* __restrict__ pair_d,
+                    const float* __restrict__ g, const int* __restrict__ offsets,
+                    const float* __restrict__ xdist, float rel, float relx, int max_items,
+                    EmitItem* __restrict__ items, unsigned long long* __restrict__ stats) {
+  __shared__ unsigned long long part[2][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int total = min(chunk_off[n_r], max_items);
   const float dlo = 1.0f - rel, dup = 1.0f + rel;
   const float xlo = (1.0f - relx) * (1.0f - 2.4e-7f), xup = (1.0f + relx) * SLACK;
-  for (int i = begin + lane; i < end; i += 32) {
-    const float d = pair_d[i];
-    const float gq = g[pair_q[i]];
-    wlo = fminf(wlo, (d * dlo - gq * SLACK) * xlo);
-    whi = fmaxf(whi, (d * dup + gq) * xup);
-  }
+  unsigned long long rows_sum = 0, pairs_sum = 0;
+  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total;
+       c += (gridDim.x * blockDim.x) >> 5) {
+    // the group holding chunk c: last r with chunk_off[r] <= c
+    int lo_r = 0, hi_r = n_r;  // invariant: chunk_off[lo_r] <= c < chunk_off[hi_r]
+    while (hi_r - lo_r > 1) {
+      const int mid = (lo_r + hi_r) >> 1;
+      if (chunk_off[mid] <= c) lo_r = mid; else hi_r = mid;
+    }
+    const int r = lo_r;
+    const int begin = bin_off[r * nb] + (c - chunk_off[r]) * TQ;
+    const int end = min(begin + TQ, bin_off[(r + 1) * nb]);
+    float wlo = INFINITY, whi = -INFINITY;
+    for (int i = begin + lane; i < end; i += 32) {
+      const float d = pair_d[i];
+      const float gq = g[pair_q[i]];
+      wlo = fminf(wlo, (d * dlo - gq * SLACK) * xlo);
+      whi = fmaxf(whi, (d * dup + gq) * xup);
+    }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    wlo = fminf(wlo, __shfl_xor_sync(0xffffffffu, wlo, o));
-    whi = fmaxf(whi, __shfl_xor_sync(0xffffffffu, whi, o));
+    for (int o = 16; o > 0; o >>= 1) {
+      wlo = fminf(wlo, __shfl_xor_sync(0xffffffffu, wlo, o));
+      whi = fmaxf(whi, __shfl_xor_sync(0xffffffffu, whi, o));
+    }
+    const int ob = offsets[r], oe = offsets[r + 1];
+    const int xb = ob + warp_bound<true>(xdist + ob, oe - ob, wlo, lane);
+    const int xe = ob + warp_bound<false>(xdist + ob, oe - ob, whi, lane);
+    if (lane == 0) {
+      items[c] = EmitItem{begin, end - begin, xb, xe > xb ? xe : xb};
+      if (xe > xb) {
+        rows_sum += (unsigned long long)(xe - xb);
+        pairs_sum += (unsigned long long)(end - begin) * (unsigned long long)(xe - xb);
+      }
+    }
   }
   if (lane == 0) {
-    const int ob = offsets[r], oe = offsets[r + 1];
-    const int xb = ob + lower_bound_f(xdist + ob, oe - ob, wlo);
-    const int xe = ob + upper_bound_f(xdist + ob, oe - ob, whi);
-    items[c] = EmitItem{begin, end - begin, xb, xe > xb ? xe : xb};
-    if (stats && xe > xb) {
-      atomicAdd(&stats[0], (unsigned long long)(xe - xb));
-      atomicAdd(&stats[1], (unsigned long long)(end - begin) * (unsigned long long)(xe - xb));
+    part[0][wid] = rows_sum;
+    part[1][wid] = pairs_sum;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && stats) {
+    unsigned long long a = 0, b = 0;
+    for (int w = 0; w < 8; ++w) {
+      a += part[0][w];
+      b += part[1][w];
     }
+    if (a) atomicAdd(&stats[0], a);
+    if (b) atomicAdd(&stats[1], b);
+  }
+}
+
+// One warp per overflowing query: the k-th smallest of its stored scores
+// (bitwise search over order-preserving keys) -> a tighter threshold.
+__global__ void overflow_rethreshold_kernel(const int* __restrict__ rows, int n,
+                                            const float* __restrict__ cand_score,
+                                            int* __restrict__ cand_cnt, int cap, int k,
+                                            const float* __restrict__ qnorm,
+                                            const float* __restrict__ qerr,
+                                            const unsigned* __restrict__ lp_max, int d,
+                                            float* __restrict__ thr) {
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  const int q = rows[i];
+  const int stored = min(cand_cnt[q], cap);
+  float t = INFINITY;
+  if (stored >= k) {
+    const float* sc = cand_score + (int64_t)q * cap;
+    unsigned res = 0;
+    for (int bit = 31; bit >= 0; --bit) {
+      const unsigned tt = res | (1u << bit);
+      int c = 0;
+      for (int e = lane; e < stored; e += 32) {
+        const unsigned b = __float_as_uint(sc[e]);
+        const unsigned key = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+        c += key < tt;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+      if (c < k) res = tt;
+    }
+    const float sk = __uint_as_float((res & 0x80000000u) ? (res & 0x7fffffffu) : ~res);
+    const float xe = __uint_as_float(lp_max[0]), xn = __uint_as_float(lp_max[1]);
+    t = score_bound(dist_upper(sk, qnorm[q], qerr[q], xe, xn, d), qnorm[q], qerr[q], xe, xn, d);
+  }
+  if (lane == 0) {
+    thr[q] = t;
+    cand_cnt[q] = 0;
+  }
+}
+
+__global__ void dense_emit_items_kernel(int n, int64_t x_rows, int xspan, int nsplit,
+                                        EmitItem* __restrict__ items) {
+  const int nchunk = (n + TQ - 1) / TQ;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nchunk * nsplit;
+       i += gridDim.x * blockDim.x) {
+    const int c = i / nsplit, sp = i - c * nsplit;
+    const int64_t xb = (int64_t)sp * xspan;
+    const int64_t xe = xb + xspan < x_rows ? xb + xspan : x_rows;
+    items[i] = EmitItem{c * TQ, min(TQ, n - c * TQ), (int)xb, (int)xe};
   }
 }
 
@@ -417,21 +476,12 @@ int launch_gbound(const float* own, const float* gk, int64_t m, float rel_rep, f
   return RBC_OK;
 }
 
-int launch_own_kth(const float* ps, int C, const int* qout, int64_t rows, int k, int metric,
-                   float rel, float* own, cudaStream_t st) {
-  if (rows <= 0) return RBC_OK;
-  own_kth_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(ps, C, qout, rows, k,
-                                                                 metric == RBC_L2, rel, own);
-  RBC_LAUNCH_CHECK("own_kth_kernel");
-  return RBC_OK;
-}
-
-int launch_own_kth_lp(const float* ps, const int* pi, int C, const int* qout, int64_t rows,
+int launch_own_kth_lp(const float* ps, const int* pi, int C, const int* qsrc, int64_t rows,
                       int k, const float* Q32, const float* X32, int d, int metric, float rel,
                       float* own, cudaStream_t st) {
   if (rows <= 0) return RBC_OK;
   own_kth_lp_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(
-      ps, pi, C, qout, rows, k, Q32, X32, d, metric, rel, own);
+      ps, pi, C, qsrc, rows, k, Q32, X32, d, metric, rel, own);
   RBC_LAUNCH_CHECK("own_kth_lp_kernel");
   return RBC_OK;
 }
@@ -454,8 +504,8 @@ int launch_window_pairs_count(const float* D, int64_t m, int n_r, const float* g
     wbin_kernel<false><<<grid, WW * 32, 0, st>>>(D, m, n_r, g, g1, psi_plus, rel, rmin, rmax,
                                                  counts, nullptr, nullptr, nullptr);
     RBC_LAUNCH_CHECK("wbin_kernel");
-    bin_colscan_kernel<<<(unsigned)((nbins + 255) / 256), 256, 0, st>>>(counts, (int)qblocks,
-                                                                        nbins, totals);
+    bin_colscan_kernel<<<(unsigned)((nbins * 32 + 255) / 256), 256, 0, st>>>(
+        counts, (int)qblocks, nbins, totals);
     RBC_LAUNCH_CHECK("bin_colscan_kernel");
   } else {
     RBC_CUDA(cudaMemsetAsync(totals, 0, nbins * sizeof(int), st));
@@ -488,7 +538,8 @@ int launch_window_items(const int* bin_off, int nb, int n_r, const int* pair_q,
   int rc = launch_exclusive_scan(chunk_counts, n_r, chunk_off, st);
   if (rc != RBC_OK) return rc;
   if (max_items <= 0) return RBC_OK;
-  window_items_kernel<<<(unsigned)(((int64_t)max_items * 32 + 255) / 256), 256, 0, st>>>(
+  const int64_t want = ((int64_t)max_items * 32 + 255) / 256;
+  window_items_kernel<<<(unsigned)std::min<int64_t>(want, 148 * 16), 256, 0, st>>>(
       chunk_off, n_r, bin_off, nb, pair_q, pair_d, g, offsets, xdist, rel, relx, max_items,
       items, stats);
   RBC_LAUNCH_CHECK("window_items_kernel");
@@ -502,6 +553,24 @@ int launch_score_threshold(const float* g, const float* qnorm, const float* qerr
   score_threshold_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(g, qnorm, qerr, lp_max, d,
                                                                       m, thr);
   RBC_LAUNCH_CHECK("score_threshold_kernel");
+  return RBC_OK;
+}
+
+int launch_overflow_rethreshold(const int* rows, int n, const float* cand_score, int* cand_cnt,
+                                int cap, int k, const float* qnorm, const float* qerr,
+                                const unsigned* lp_max, int d, float* thr, cudaStream_t st) {
+  if (n <= 0) return RBC_OK;
+  overflow_rethreshold_kernel<<<(unsigned)(((int64_t)n * 32 + 255) / 256), 256, 0, st>>>(
+      rows, n, cand_score, cand_cnt, cap, k, qnorm, qerr, lp_max, d, thr);
+  RBC_LAUNCH_CHECK("overflow_rethreshold_kernel");
+  return RBC_OK;
+}
+
+int launch_dense_emit_items(int n, int64_t x_rows, int xspan, EmitItem* items, cudaStream_t st) {
+  if (n <= 0) return RBC_OK;
+  const int nsplit = (int)((x_rows + xspan - 1) / xspan);
+  dense_emit_items_kernel<<<64, 256, 0, st>>>(n, x_rows, xspan, nsplit, items);
+  RBC_LAUNCH_CHECK("dense_emit_items_kernel");
   return RBC_OK;
 }
 
