@@ -265,6 +265,16 @@ int rbc_last_stats(rbc_search_stats* out);
  * the previous setting. */
 int rbc_set_timing(int on);
 
+/*
+ * rbc_trim_workspace -- returns the search workspace cached for the current
+ *   device to the driver.  Search calls take their scratch (distance rows,
+ *   work items, candidate buffers: a few GB for large batches) from a
+ *   library-owned stream-ordered pool that keeps freed memory mapped for the
+ *   next call; this call synchronises the device and releases all of it.
+ *   Errors: RBC_ERR_CUDA.  No counterpart in the paper (memory management).
+ */
+int rbc_trim_workspace(void);
+
 /* rbc_free -- releases the index (waits for its outstanding work). NULL ok. */
 void rbc_free(rbc_index* idx);
 

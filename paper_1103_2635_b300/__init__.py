@@ -26,7 +26,7 @@ import numpy as np
 __all__ = [
     "L2", "L1", "EXACT", "ONESHOT", "F32", "BF16", "F16", "PLAN_WINDOW", "PLAN_TILE_UNION",
     "RbcError", "bf_search", "bf_search_noalloc", "rbc_build", "rbc_search", "rbc_sample_reps",
-    "RbcIndex", "last_stats", "set_timing", "library_path", "load",
+    "RbcIndex", "last_stats", "set_timing", "trim_workspace", "library_path", "load",
 ]
 
 L2, L1 = 0, 1
@@ -95,6 +95,7 @@ def load():
     lib.rbc_set_timing.restype = ctypes.c_int
     lib.rbc_free.argtypes = [P]
     lib.rbc_free.restype = None
+    lib.rbc_trim_workspace.argtypes = []
     lib.rbc_last_error.restype = ctypes.c_char_p
     lib.rbc_default_opts.argtypes = [ctypes.POINTER(_Opts)]
     lib.rbc_default_opts.restype = None
@@ -263,6 +264,11 @@ def rbc_search(index: RbcIndex, Q, k: int, out_ids=None, out_dist=None, stream=N
     st = _stream_of(stream, qdev or idev)
     _check(load().rbc_search(index.handle, qp, m, k, ip, dp, st))
     return out_ids, out_dist
+
+
+def trim_workspace() -> None:
+    """Release the search workspace cached for the current device."""
+    _check(load().rbc_trim_workspace())
 
 
 def set_timing(on: bool) -> bool:

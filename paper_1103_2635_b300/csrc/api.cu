@@ -15,6 +15,7 @@
 #include <cstring>
 #include <new>
 #include <unordered_map>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -167,11 +168,43 @@ int sm_count() {
   return cached[dev];
 }
 
+// Workspace memory comes from a library-owned stream-ordered pool per device
+// whose release threshold is unlimited: freed blocks stay mapped and are
+// reused by the next call instead of being unmapped at every
+// synchronisation (a search's workspace is a few GB).  rbc_trim_workspace()
+// hands the cached memory back.
+constexpr int MAX_POOL_DEVICES = 64;
+cudaMemPool_t g_pools[MAX_POOL_DEVICES] = {};
+std::mutex g_pool_mu;
+
+cudaMemPool_t workspace_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_POOL_DEVICES) return nullptr;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = pool;
+  }
+  return g_pools[dev];
+}
+
 // Stream-ordered scratch released when the arena goes out of scope.
 struct Arena {
   cudaStream_t st;
+  cudaMemPool_t pool;
   std::vector<void*> ptrs;
-  explicit Arena(cudaStream_t s) : st(s) {}
+  explicit Arena(cudaStream_t s) : st(s), pool(workspace_pool()) {}
   ~Arena() {
     for (void* p : ptrs) cudaFreeAsync(p, st);
   }
@@ -180,7 +213,8 @@ struct Arena {
     *out = nullptr;
     if (count <= 0) count = 1;
     void* p = nullptr;
-    cudaError_t e = cudaMallocAsync(&p, (size_t)count * sizeof(T), st);
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, (size_t)count * sizeof(T), pool, st)
+                         : cudaMallocAsync(&p, (size_t)count * sizeof(T), st);
     if (e != cudaSuccess) {
       cudaGetLastError();
       set_error("workspace allocation of %lld bytes failed: %s",
@@ -682,6 +716,7 @@ int build_exact(rbc_index* ix, const float* Xdev, const std::vector<int64_t>& re
 // exact search (Section 5.2)
 // ---------------------------------------------------------------------------
 constexpr int64_t MAX_BATCH = 131072;  // queries per internal batch (bounds workspace)
+constexpr int64_t WINDOW_MAX_PAIRS = 1LL << 28;  // windowed search: batch x n_r bound
 
 int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, int64_t* ids,
                        float* dist, const Counters& cn, int64_t* items_total, Arena& ar,
@@ -1211,17 +1246,17 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   RBC_TRY(launch_window_pairs_count(D, mb, n_r, g, g1, ix->psi, simt_eps(d), rmin, rmax, qkept,
                                     counts, totals, bin_off, st));
   RBC_TRY(launch_sum_i32(qkept, mb, cn.sums, st));
-  int npairs = 0;
-  RBC_CUDA(cudaMemcpyAsync(&npairs, bin_off + nbins, sizeof(int), cudaMemcpyDeviceToHost, st));
-  RBC_CUDA(cudaStreamSynchronize(st));
+  // pair arrays sized by the bound mb x n_r (batches are cut so that it stays
+  // within WINDOW_MAX_PAIRS), so no count needs to come back to the host
+  const int64_t pair_cap = mb * n_r;
   int* pq;
   float* pd;
-  RBC_TRY(ar.alloc(&pq, npairs));
-  RBC_TRY(ar.alloc(&pd, npairs));
+  RBC_TRY(ar.alloc(&pq, pair_cap));
+  RBC_TRY(ar.alloc(&pd, pair_cap));
   RBC_TRY(launch_window_pairs_scatter(D, mb, n_r, g, g1, ix->psi, simt_eps(d), rmin, rmax, counts,
                                       bin_off, pq, pd, st));
   // work items: chunks of TQ pairs, each with the union of its windows
-  const int max_items = (int)std::min<int64_t>((int64_t)npairs / TQ + n_r, INT32_MAX);
+  const int max_items = (int)std::min<int64_t>(pair_cap / TQ + n_r, INT32_MAX);
   int *ccount, *choff;
   EmitItem* items;
   RBC_TRY(ar.alloc(&ccount, n_r));
@@ -1277,57 +1312,52 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   RBC_TRY(launch_select_cands(a, st));
   tmark(3, st);
   RBC_TRY(launch_add_ints(cn.c, lc, 3, st));
-  int nfb = 0;
+  // Queries whose candidate buffer overflowed (count in lc[0], on the device):
+  // k of their stored candidates give a much tighter threshold; emit again
+  // for them alone against the whole list storage and finish them.  Launched
+  // unconditionally with device-side counts (empty when nothing overflowed),
+  // so the batch needs one synchronisation, at its end.
+  RBC_TRY(launch_overflow_rethreshold(fb_rows, lc, mb, cs, cc, CAND_CAP, k, ql.norm, ql.err,
+                                      ix->lp_max, d, thr, st));
+  const int xspan = (int)std::max<int64_t>(4096, (n + 2 * sms - 1) / (2 * sms) / 256 * 256);
+  const int nsplit = (int)((n + xspan - 1) / xspan);
+  const int max2 = (int)std::min<int64_t>((mb + TQ - 1) / TQ * nsplit, INT32_MAX);
+  EmitItem* items2;
+  int* n_items2;
+  RBC_TRY(ar.alloc(&items2, max2));
+  RBC_TRY(ar.alloc(&n_items2, 1));
+  RBC_TRY(launch_dense_emit_items(lc, n, xspan, max2, items2, n_items2, st));
+  RBC_TRY(launch_bf_tc_emit(Qm, Xm, items2, n_items2, max2, fb_rows, eo, sms, st, dev_err));
+  int* fb2;
+  int* lc2;
+  RBC_TRY(ar.alloc(&fb2, mb));
+  RBC_TRY(ar.alloc(&lc2, 8));
+  RBC_CUDA(cudaMemsetAsync(lc2, 0, 8 * sizeof(int), st));
+  CandSelectArgs a2 = a;
+  a2.rows = fb_rows;
+  a2.nrows_dev = lc;
+  a2.nrows = (int)mb;
+  a2.fallback_rows = fb2;
+  a2.counters = lc2;
+  RBC_TRY(launch_select_cands(a2, st));
+  RBC_TRY(launch_add_ints(cn.c + 4, lc2, 3, st));
+  int nfb2 = 0;
   uint32_t herr = 0;
-  RBC_CUDA(cudaMemcpyAsync(&nfb, lc, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RBC_CUDA(cudaMemcpyAsync(&nfb2, lc2, sizeof(int), cudaMemcpyDeviceToHost, st));
   RBC_CUDA(cudaMemcpyAsync(&herr, dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   RBC_CUDA(cudaStreamSynchronize(st));
   if (herr) {
     set_error("windowed stage two reported device error flags 0x%x", herr);
     return (herr & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
   }
-  if (nfb > 0) {
-    // Queries whose candidate buffer overflowed: k of the stored candidates
-    // give a much tighter threshold; emit again for them alone against the
-    // whole list storage, then finish them.  Whatever still overflows (more
-    // than the buffer of points tied within rounding) goes to the FP32 BF.
-    RBC_TRY(launch_overflow_rethreshold(fb_rows, nfb, cs, cc, CAND_CAP, k, ql.norm, ql.err,
-                                        ix->lp_max, d, thr, st));
-    const int xspan = (int)std::max<int64_t>(4096, (n + 2 * sms - 1) / (2 * sms) / 256 * 256);
-    const int64_t nsplit = (n + xspan - 1) / xspan;
-    const int n2 = (int)(((int64_t)nfb + TQ - 1) / TQ * nsplit);
-    EmitItem* items2;
-    RBC_TRY(ar.alloc(&items2, n2));
-    RBC_TRY(launch_dense_emit_items(nfb, n, xspan, items2, st));
-    RBC_TRY(launch_bf_tc_emit(Qm, Xm, items2, nullptr, n2, fb_rows, eo, sms, st, dev_err));
-    int* fb2;
-    int* lc2;
-    RBC_TRY(ar.alloc(&fb2, nfb));
-    RBC_TRY(ar.alloc(&lc2, 8));
-    RBC_CUDA(cudaMemsetAsync(lc2, 0, 8 * sizeof(int), st));
-    CandSelectArgs a2 = a;
-    a2.rows = fb_rows;
-    a2.nrows = nfb;
-    a2.fallback_rows = fb2;
-    a2.counters = lc2;
-    RBC_TRY(launch_select_cands(a2, st));
-    RBC_TRY(launch_add_ints(cn.c + 4, lc2, 3, st));
-    int nfb2 = 0;
-    RBC_CUDA(cudaMemcpyAsync(&nfb2, lc2, sizeof(int), cudaMemcpyDeviceToHost, st));
-    RBC_CUDA(cudaMemcpyAsync(&herr, dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    RBC_CUDA(cudaStreamSynchronize(st));
-    if (herr) {
-      set_error("windowed stage two (overflow pass) reported device error flags 0x%x", herr);
-      return (herr & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
-    }
-    if (nfb2 > 0) {
-      DbView db;
-      db.X32 = ix->X32;
-      db.xid = ix->members;
-      db.rows = n;
-      RBC_TRY(fallback_f32(Qb, fb2, nfb2, nullptr, db, d, k, ix->metric, ids, dist, cn.c + 4, ar,
-                           st));
-    }
+  if (nfb2 > 0) {
+    // more points than a buffer holds tie within rounding: FP32 brute force
+    DbView db;
+    db.X32 = ix->X32;
+    db.xid = ix->members;
+    db.rows = n;
+    RBC_TRY(fallback_f32(Qb, fb2, nfb2, nullptr, db, d, k, ix->metric, ids, dist, cn.c + 4, ar,
+                         st));
   }
   tmark(4, st);
   taccumulate();
@@ -1561,13 +1591,19 @@ int rbc_search(const rbc_index* ix, const float* Q, int64_t m, int32_t k, int64_
   Counters cn;
   RBC_TRY(counters_alloc(cn, ar, st));
   int64_t items = 0;
-  for (int64_t b0 = 0; b0 < m; b0 += MAX_BATCH) {
-    int64_t mb = std::min<int64_t>(MAX_BATCH, m - b0);
+  const bool window = ix->mode == RBC_EXACT && ix->plan == RBC_PLAN_WINDOW &&
+                      uses_lp(ix->storage, ix->metric) && ix->Xlp;
+  // the windowed search sizes its pair arrays by batch x n_r
+  const int64_t batch =
+      window ? std::max<int64_t>(TQ, std::min<int64_t>(MAX_BATCH, WINDOW_MAX_PAIRS / ix->n_r))
+             : MAX_BATCH;
+  for (int64_t b0 = 0; b0 < m; b0 += batch) {
+    int64_t mb = std::min<int64_t>(batch, m - b0);
     Arena bar(st);
     if (ix->mode == RBC_ONESHOT)
       RBC_TRY(search_oneshot_batch(ix, io.Qdev + b0 * ix->d, mb, k, io.ids_dev + b0 * k,
                                    io.dist_dev + b0 * k, cn, &items, bar, st));
-    else if (ix->plan == RBC_PLAN_WINDOW && uses_lp(ix->storage, ix->metric) && ix->Xlp)
+    else if (window)
       RBC_TRY(search_window_batch(ix, io.Qdev + b0 * ix->d, mb, k, io.ids_dev + b0 * k,
                                   io.dist_dev + b0 * k, cn, &items, bar, st));
     else
@@ -1619,6 +1655,24 @@ int rbc_index_export(const rbc_index* ix, int64_t* reps, int64_t* offsets, int64
     for (size_t i = 0; i < mm.size(); ++i) members[i] = mm[i];
   }
   if (psi) RBC_CUDA(cudaMemcpy(psi, ix->psi, ix->n_r * sizeof(float), cudaMemcpyDeviceToHost));
+  return RBC_OK;
+}
+
+int rbc_trim_workspace(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_POOL_DEVICES) {
+    cudaGetLastError();
+    set_error("rbc_trim_workspace: no current device");
+    return RBC_ERR_CUDA;
+  }
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    pool = g_pools[dev];
+  }
+  if (!pool) return RBC_OK;
+  RBC_CUDA(cudaDeviceSynchronize());
+  RBC_CUDA(cudaMemPoolTrimTo(pool, 0));
   return RBC_OK;
 }
 

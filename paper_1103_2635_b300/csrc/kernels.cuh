@@ -115,8 +115,9 @@ struct CandSelectArgs {
   const int* cand_cnt;      // [m] emissions (may exceed cap: overflow)
   int cap;
   int64_t m;
-  const int* rows;   // optional: the queries to finish (nrows of them); else 0 .. m-1
-  int nrows;
+  const int* rows;      // optional: the queries to finish; else 0 .. m-1
+  const int* nrows_dev; // with rows: device-side count (else nrows)
+  int nrows;            // with rows: the count, or the bound of *nrows_dev
   const float* Q32;  // [m, d] queries FP32
   int d;
   int metric;
@@ -176,10 +177,13 @@ int launch_window_items(const int* bin_off, int nb, int n_r, const int* pair_q,
 // stored candidates already meet, and the buffer count reset to zero; then
 // items over the whole list storage (chunks of TQ of these queries x row
 // spans of xspan) for the emission kernel.
-int launch_overflow_rethreshold(const int* rows, int n, const float* cand_score, int* cand_cnt,
-                                int cap, int k, const float* qnorm, const float* qerr,
-                                const unsigned* lp_max, int d, float* thr, cudaStream_t st);
-int launch_dense_emit_items(int n, int64_t x_rows, int xspan, EmitItem* items, cudaStream_t st);
+// (the number of rows is read from n_dev on the device; at most max_rows)
+int launch_overflow_rethreshold(const int* rows, const int* n_dev, int64_t max_rows,
+                                const float* cand_score, int* cand_cnt, int cap, int k,
+                                const float* qnorm, const float* qerr, const unsigned* lp_max,
+                                int d, float* thr, cudaStream_t st);
+int launch_dense_emit_items(const int* n_dev, int64_t x_rows, int xspan, int max_items,
+                            EmitItem* items, int* num_items, cudaStream_t st);
 int launch_score_threshold(const float* g, const float* qnorm, const float* qerr,
                            const unsigned* lp_max, int d, int64_t m, float* thr,
                            cudaStream_t st);

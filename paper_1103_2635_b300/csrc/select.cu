@@ -328,7 +328,8 @@ __global__ void __launch_bounds__(WARPS * 32) select_cands_kernel(CandSelectArgs
   const int wib = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int64_t wi = (int64_t)blockIdx.x * WARPS + wib;
-  if (wi >= (a.rows ? (int64_t)a.nrows : a.m)) return;
+  const int64_t nw = a.rows ? (a.nrows_dev ? (int64_t)*a.nrows_dev : (int64_t)a.nrows) : a.m;
+  if (wi >= nw) return;
   const int64_t q = a.rows ? (int64_t)a.rows[wi] : wi;
   const int cnt = a.cand_cnt[q];
   const int k = a.k;

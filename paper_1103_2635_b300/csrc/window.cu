@@ -405,16 +405,18 @@ window_items_kernel(const int* __restrict__ chunk_off, int n_r, const int* __res
 
 // One warp per overflowing query: the k-th smallest of its stored scores
 // (bitwise search over order-preserving keys) -> a tighter threshold.
-__global__ void overflow_rethreshold_kernel(const int* __restrict__ rows, int n,
+__global__ void overflow_rethreshold_kernel(const int* __restrict__ rows,
+                                            const int* __restrict__ n_dev,
                                             const float* __restrict__ cand_score,
                                             int* __restrict__ cand_cnt, int cap, int k,
                                             const float* __restrict__ qnorm,
                                             const float* __restrict__ qerr,
                                             const unsigned* __restrict__ lp_max, int d,
                                             float* __restrict__ thr) {
-  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (i >= n) return;
+  const int n = *n_dev;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n;
+       i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
   const int q = rows[i];
   const int stored = min(cand_cnt[q], cap);
   float t = INFINITY;
@@ -441,12 +443,17 @@ __global__ void overflow_rethreshold_kernel(const int* __restrict__ rows, int n,
     thr[q] = t;
     cand_cnt[q] = 0;
   }
+  }
 }
 
-__global__ void dense_emit_items_kernel(int n, int64_t x_rows, int xspan, int nsplit,
-                                        EmitItem* __restrict__ items) {
+__global__ void dense_emit_items_kernel(const int* __restrict__ n_dev, int64_t x_rows, int xspan,
+                                        int nsplit, int max_items, EmitItem* __restrict__ items,
+                                        int* __restrict__ num_items) {
+  const int n = *n_dev;
   const int nchunk = (n + TQ - 1) / TQ;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nchunk * nsplit;
+  const int total = min(nchunk * nsplit, max_items);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *num_items = total;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += gridDim.x * blockDim.x) {
     const int c = i / nsplit, sp = i - c * nsplit;
     const int64_t xb = (int64_t)sp * xspan;
@@ -556,20 +563,23 @@ int launch_score_threshold(const float* g, const float* qnorm, const float* qerr
   return RBC_OK;
 }
 
-int launch_overflow_rethreshold(const int* rows, int n, const float* cand_score, int* cand_cnt,
-                                int cap, int k, const float* qnorm, const float* qerr,
-                                const unsigned* lp_max, int d, float* thr, cudaStream_t st) {
-  if (n <= 0) return RBC_OK;
-  overflow_rethreshold_kernel<<<(unsigned)(((int64_t)n * 32 + 255) / 256), 256, 0, st>>>(
-      rows, n, cand_score, cand_cnt, cap, k, qnorm, qerr, lp_max, d, thr);
+int launch_overflow_rethreshold(const int* rows, const int* n_dev, int64_t max_rows,
+                                const float* cand_score, int* cand_cnt, int cap, int k,
+                                const float* qnorm, const float* qerr, const unsigned* lp_max,
+                                int d, float* thr, cudaStream_t st) {
+  if (max_rows <= 0) return RBC_OK;
+  const int64_t want = (max_rows * 32 + 255) / 256;
+  overflow_rethreshold_kernel<<<(unsigned)std::min<int64_t>(want, 148 * 4), 256, 0, st>>>(
+      rows, n_dev, cand_score, cand_cnt, cap, k, qnorm, qerr, lp_max, d, thr);
   RBC_LAUNCH_CHECK("overflow_rethreshold_kernel");
   return RBC_OK;
 }
 
-int launch_dense_emit_items(int n, int64_t x_rows, int xspan, EmitItem* items, cudaStream_t st) {
-  if (n <= 0) return RBC_OK;
+int launch_dense_emit_items(const int* n_dev, int64_t x_rows, int xspan, int max_items,
+                            EmitItem* items, int* num_items, cudaStream_t st) {
   const int nsplit = (int)((x_rows + xspan - 1) / xspan);
-  dense_emit_items_kernel<<<64, 256, 0, st>>>(n, x_rows, xspan, nsplit, items);
+  dense_emit_items_kernel<<<64, 256, 0, st>>>(n_dev, x_rows, xspan, nsplit, max_items, items,
+                                              num_items);
   RBC_LAUNCH_CHECK("dense_emit_items_kernel");
   return RBC_OK;
 }
