@@ -1249,12 +1249,17 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   // pair arrays sized by the bound mb x n_r (batches are cut so that it stays
   // within WINDOW_MAX_PAIRS), so no count needs to come back to the host
   const int64_t pair_cap = mb * n_r;
+  // score thresholds first: every pair carries its query's
+  float* thr;
+  RBC_TRY(ar.alloc(&thr, mb));
+  RBC_TRY(launch_score_threshold(g, ql.norm, ql.err, ix->lp_max, d, mb, thr, st));
   int* pq;
-  float* pd;
+  float *pd, *pt;
   RBC_TRY(ar.alloc(&pq, pair_cap));
   RBC_TRY(ar.alloc(&pd, pair_cap));
+  RBC_TRY(ar.alloc(&pt, pair_cap));
   RBC_TRY(launch_window_pairs_scatter(D, mb, n_r, g, g1, ix->psi, simt_eps(d), rmin, rmax, counts,
-                                      bin_off, pq, pd, st));
+                                      bin_off, thr, pq, pd, pt, st));
   // work items: chunks of TQ pairs, each with the union of its windows
   const int max_items = (int)std::min<int64_t>(pair_cap / TQ + n_r, INT32_MAX);
   int *ccount, *choff;
@@ -1266,10 +1271,7 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
                               2.0f * rerank_eps_host(d) + 8.0f * U32, ccount, choff, max_items,
                               items, cn.sums + 1, st));
   *items_total += max_items;
-  // thresholds, then the tensor-core pass emitting candidates
-  float* thr;
-  RBC_TRY(ar.alloc(&thr, mb));
-  RBC_TRY(launch_score_threshold(g, ql.norm, ql.err, ix->lp_max, d, mb, thr, st));
+  // the tensor-core pass emitting candidates
   float* cs;
   int *cr, *cc;
   RBC_TRY(ar.alloc(&cs, mb * CAND_CAP));
@@ -1280,7 +1282,7 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   LpMatrix Xm{ix->Xlp, ix->xnorm, n, ix->dpad, ix->storage};
   EmitOut eo{thr, cs, cr, cc, CAND_CAP};
   tmark(1, st);
-  RBC_TRY(launch_bf_tc_emit(Qm, Xm, items, choff + n_r, max_items, pq, eo, sms, st, dev_err));
+  RBC_TRY(launch_bf_tc_emit(Qm, Xm, items, choff + n_r, max_items, pq, pt, eo, sms, st, dev_err));
   tmark(2, st);
   // exact re-rank of the candidates; overflowing queries go to the FP32 re-search
   int* fb_rows;
@@ -1327,7 +1329,8 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   RBC_TRY(ar.alloc(&items2, max2));
   RBC_TRY(ar.alloc(&n_items2, 1));
   RBC_TRY(launch_dense_emit_items(lc, n, xspan, max2, items2, n_items2, st));
-  RBC_TRY(launch_bf_tc_emit(Qm, Xm, items2, n_items2, max2, fb_rows, eo, sms, st, dev_err));
+  RBC_TRY(launch_bf_tc_emit(Qm, Xm, items2, n_items2, max2, fb_rows, nullptr, eo, sms, st,
+                            dev_err));
   int* fb2;
   int* lc2;
   RBC_TRY(ar.alloc(&fb2, mb));

@@ -19,8 +19,9 @@
 //
 //   warp 0      TMA producer: database tiles of BN rows + their norms
 //   warp 1      tensor-memory allocation, MMA issue (M = 128, N = BN, K = 16)
-//   warp 2      query gather (cp.async), per-row query id and threshold
-//   warp 3      idle (keeps the epilogue warps aligned to TMEM lane quarters)
+//   warps 2-3   query gather (cp.async), per-row query id and threshold;
+//               the two warps take alternate items (a short window leaves
+//               an item little more time than one gather takes)
 //   warps 4-    epilogue: TMEM lane quarter (warp % 4) x column slice; with
 //               no candidate lists to keep, a thread needs ~90 registers, so
 //               up to 16 epilogue warps (four per scheduler) hide the TMEM
@@ -37,8 +38,9 @@ namespace {
 
 using namespace tc;
 
-constexpr int E_GATHER = 2;     // query-gather warp
-constexpr int E_EPI0 = 4;       // first epilogue warp (warp 3 idles)
+constexpr int E_GATHER = 2;     // first query-gather warp
+constexpr int E_NGATHER = 2;    // query-gather warps (alternate items)
+constexpr int E_EPI0 = 4;       // first epilogue warp
 
 // Epilogue parts: the tile's columns are split into NPART slices of BN/NPART
 // (at least 32) columns; each (TMEM lane quarter, slice) is one warp.
@@ -56,6 +58,7 @@ struct EmitParams {
   const int* num_items_dev;
   int max_items;
   const int* pair_q;
+  const float* pair_t;  // threshold of each pair's query (nullptr: read out.thr)
   const uint8_t* qlp;  // [q_rows, dpad] 16-bit rows
   int64_t q_row_bytes;
   const float* xnorm;  // [rows + pad]
@@ -82,6 +85,7 @@ struct EmitSmem {
   static constexpr int ALLOC = BYTES + 1024;  // slack for 1024-byte alignment
   static_assert(ALLOC <= 232448, "shared memory budget");
   static_assert(OFF_X % 1024 == 0 && X_STAGE % 1024 == 0, "swizzled tiles need 1024-byte alignment");
+  static_assert(QSTAGES % 2 == 0, "query stages alternate between two gather warps");
 };
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
@@ -93,8 +97,9 @@ __device__ __forceinline__ void st_shared_zero16(uint32_t dst) {
   asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(dst), "r"(0) : "memory");
 }
 
-// QSTAGES query stages: the gather of an item's rows takes a few
-// microseconds, longer than a one-tile item, so several are kept in flight.
+// QSTAGES query stages (even: the two gather warps alternate over them): the
+// gather of an item's rows takes a few microseconds, longer than a one-tile
+// item, so several are kept in flight.
 template <int KB, int BN, int S, int NR, int QSTAGES>
 __global__ void __launch_bounds__(EpiShape<BN>::THREADS, 1)
 bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32_t idesc) {
@@ -196,22 +201,37 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32
       for (uint32_t j = (it > (uint32_t)NR ? it - NR : 0); j < it; ++j)
         mbar_wait(&nfull[j % NR], (j / NR) & 1, sAbort, p.dev_err);
     }
-  } else if (warp == E_GATHER) {
-    // ---------------- query gather ----------------
+  } else if (warp >= E_GATHER && warp < E_GATHER + E_NGATHER) {
+    // ---------------- query gather (warp gw takes items qi = gw mod 2) ----------------
+    const uint32_t gw = warp - E_GATHER;
     uint32_t qi = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
       const EmitItem e = p.items[item];
       if (e.x_end <= e.x_begin) continue;
+      if (qi % E_NGATHER != gw) {
+        ++qi;
+        continue;
+      }
       const int qs = qi % QSTAGES;
       const uint32_t qph = (qi / QSTAGES) & 1;
+      // the item's query ids and thresholds: independent loads, issued
+      // before the wait for the stage
+      int srcs[BM / 32];
+      float thrs[BM / 32];
+#pragma unroll
+      for (int t = 0; t < BM / 32; ++t) {
+        const int row = lane + 32 * t;
+        srcs[t] = row < e.nq ? p.pair_q[e.pair_begin + row] : -1;
+        thrs[t] = row < e.nq && p.pair_t ? p.pair_t[e.pair_begin + row] : -INFINITY;
+      }
       if (!__all_sync(0xffffffffu, mbar_wait(&qempty[qs], qph ^ 1, sAbort, p.dev_err))) break;
       const uint32_t qbase = smem_u32(sQ + qs * L::Q_BYTES);
 #pragma unroll
       for (int t = 0; t < BM / 32; ++t) {
         const int row = lane + 32 * t;
-        const int src = row < e.nq ? p.pair_q[e.pair_begin + row] : -1;
+        const int src = srcs[t];
         sRowQ[qs * BM + row] = src;
-        sRowT[qs * BM + row] = src >= 0 ? p.out.thr[src] : -INFINITY;
+        sRowT[qs * BM + row] = src < 0 ? -INFINITY : (p.pair_t ? thrs[t] : p.out.thr[src]);
         const uint8_t* g = p.qlp + (int64_t)(src >= 0 ? src : 0) * p.q_row_bytes;
 #pragma unroll
         for (int kb = 0; kb < KB; ++kb)
@@ -380,15 +400,15 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32
 
 template <int KB, int BN, int S, int NR, int QS>
 int launch_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
-                const int* num_items_dev, int max_items, const int* pair_q, const EmitOut& out,
-                int grid, cudaStream_t st, uint32_t* dev_err) {
+                const int* num_items_dev, int max_items, const int* pair_q, const float* pair_t,
+                const EmitOut& out, int grid, cudaStream_t st, uint32_t* dev_err) {
   using L = EmitSmem<KB, BN, S, NR, QS>;
   CUtensorMap xmap;
   RBC_TRY_TC(encode_map(&xmap, Xm.data, Xm.rows, Xm.dpad, Xm.storage, BN));
   auto kern = bf_tc_emit_kernel<KB, BN, S, NR, QS>;
   RBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC));
-  EmitParams p{items,   num_items_dev, max_items, pair_q, static_cast<const uint8_t*>(Qm.data),
-               (int64_t)Qm.dpad * 2, Xm.norm, out, dev_err};
+  EmitParams p{items,  num_items_dev, max_items, pair_q, pair_t,
+               static_cast<const uint8_t*>(Qm.data), (int64_t)Qm.dpad * 2, Xm.norm, out, dev_err};
   const uint32_t idesc = idesc_f16(Qm.storage == RBC_BF16 ? 1 : 0, BM, BN);
   kern<<<grid, EpiShape<BN>::THREADS, L::ALLOC, st>>>(xmap, p, idesc);
   ++t_launches;
@@ -408,7 +428,8 @@ int launch_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
 
 int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
                       const int* num_items_dev, int max_items, const int* pair_q,
-                      const EmitOut& out, int grid, cudaStream_t st, uint32_t* dev_err) {
+                      const float* pair_t, const EmitOut& out, int grid, cudaStream_t st,
+                      uint32_t* dev_err) {
   if (!tc_available()) {
     set_error("tensor-core BF kernel needs an sm_103 device");
     return RBC_ERR_UNSUPPORTED;
@@ -419,10 +440,10 @@ int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* it
   }
   if (max_items <= 0) return RBC_OK;
   switch (Qm.dpad / 64) {
-    case 1: return launch_emit<1, 256, 4, 8, 4>(Qm, Xm, items, num_items_dev, max_items, pair_q, out, grid, st, dev_err);
-    case 2: return launch_emit<2, 128, 3, 8, 3>(Qm, Xm, items, num_items_dev, max_items, pair_q, out, grid, st, dev_err);
-    case 3: return launch_emit<3, 64, 3, 8, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, out, grid, st, dev_err);
-    case 4: return launch_emit<4, 64, 2, 4, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, out, grid, st, dev_err);
+    case 1: return launch_emit<1, 256, 4, 8, 4>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_t, out, grid, st, dev_err);
+    case 2: return launch_emit<2, 128, 3, 8, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_t, out, grid, st, dev_err);
+    case 3: return launch_emit<3, 64, 3, 8, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_t, out, grid, st, dev_err);
+    case 4: return launch_emit<4, 64, 2, 4, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_t, out, grid, st, dev_err);
     default: break;
   }
   set_error("tensor-core BF: padded dimension %d unsupported", Qm.dpad);

@@ -69,9 +69,12 @@ struct EmitOut {
   int* cand_cnt;     // [m]
   int cap;
 };
+// pair_t (optional): the threshold of each pair's query, read alongside
+// pair_q instead of through out.thr
 int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
                       const int* num_items_dev, int max_items, const int* pair_q,
-                      const EmitOut& out, int grid, cudaStream_t st, uint32_t* dev_err);
+                      const float* pair_t, const EmitOut& out, int grid, cudaStream_t st,
+                      uint32_t* dev_err);
 
 // ---- merge + re-rank + certification ----
 struct SelectArgs {
@@ -150,11 +153,12 @@ int launch_gbound(const float* own, const float* gk, int64_t m, float rel_rep, f
 int launch_own_kth_lp(const float* ps, const int* pi, int C, const int* qsrc, int64_t rows,
                       int k, const float* Q32, const float* X32, int d, int metric, float rel,
                       float* own, cudaStream_t st);
-// Kept (q, r) pairs binned by (r, bucket of rho(q, r)), window_buckets() per
-// r: rmin/rmax [n_r] (float bits), q_kept [m], counts
+// Kept (q, r) pairs binned by (r, bucket of the window start rho(q, r) - g(q)),
+// window_buckets() per r: rmin/rmax [n_r] (order-preserving keys of the
+// extreme window starts), q_kept [m], counts
 // [window_pair_blocks(m)][n_r nb] (per query block, then its prefix within
 // each bin), totals [n_r nb], bin_off [n_r nb + 1]; then the pairs
-// themselves (pair_q, pair_d).
+// themselves (pair_q, pair_d, and pair_t = thr of the pair's query).
 int window_buckets();
 int64_t window_pair_blocks(int64_t m);
 int launch_window_pairs_count(const float* D, int64_t m, int n_r, const float* g,
@@ -164,7 +168,8 @@ int launch_window_pairs_count(const float* D, int64_t m, int n_r, const float* g
 int launch_window_pairs_scatter(const float* D, int64_t m, int n_r, const float* g,
                                 const float* g1, const float* psi_plus, float rel,
                                 const unsigned* rmin, const unsigned* rmax, int* counts,
-                                const int* bin_off, int* pair_q, float* pair_d, cudaStream_t st);
+                                const int* bin_off, const float* thr, int* pair_q,
+                                float* pair_d, float* pair_t, cudaStream_t st);
 // chunks of TQ pairs per representative -> items (the chunk's window in the
 // sorted list); stats[0] += window rows, stats[1] += query x row pairs
 int launch_window_items(const int* bin_off, int nb, int n_r, const int* pair_q,

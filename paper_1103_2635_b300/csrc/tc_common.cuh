@@ -74,10 +74,10 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* b, uint32_t parity
 
 // Bounded wait for the phase with the given parity.  Returns false (and sets
 // the CTA's abort flag and the device error word) if the wait expired or
-// another role already aborted.
-static __device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag,
-                                       uint32_t* dev_err) {
-  if (mbar_try_wait(b, parity)) return true;
+// another role already aborted.  The first probe is inline; only a phase that
+// is not complete yet pays for the call into the bounded loop.
+static __device__ __noinline__ bool mbar_wait_slow(uint64_t* b, uint32_t parity,
+                                                   volatile int* abort_flag, uint32_t* dev_err) {
   const uint64_t t0 = global_ns();
   for (uint32_t i = 0;; ++i) {
     if (mbar_try_wait_sleep(b, parity, 1000)) return true;
@@ -90,6 +90,12 @@ static __device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, vola
       }
     }
   }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag,
+                                          uint32_t* dev_err) {
+  if (mbar_try_wait(b, parity)) return true;
+  return mbar_wait_slow(b, parity, abort_flag, dev_err);
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,

@@ -12,12 +12,15 @@
 // rho(q, r) - g and rho(q, r) + g.  All comparisons carry the FP32 rounding
 // bounds of the values involved, so no needed point is ever cut.
 //
-// The surviving (q, r) pairs are binned by (r, bucket of rho(q, r)) -- NB
-// buckets between the smallest and largest kept rho(q, r) of each r -- with a
-// counting sort over the implicit pair list, so each r's group comes out
-// ordered by rho(q, r) up to the bucket width.  Each group is cut into chunks
-// of up to TQ queries: one work item per chunk, against the union of its
-// queries' windows -- queries with close rho(q, r) have close windows.
+// The surviving (q, r) pairs are binned by (r, bucket of rho(q, r) - g(q)),
+// the lower end of the query's window -- NB buckets between the smallest and
+// largest of them for each r -- with a counting sort over the implicit pair
+// list, so each r's group comes out ordered by the window start up to the
+// bucket width.  Each group is cut into chunks of up to TQ queries: one work
+// item per chunk, against the union of its queries' windows.  Ordered by
+// window start, consecutive windows overlap almost entirely (ordering by
+// rho(q, r) alone would mix queries of very different g and about double the
+// union).
 //
 // The pair passes read D [m, n_r] in warp tiles of 32 queries x 32
 // representatives through shared memory, so that a lane owns a query and the
@@ -35,8 +38,8 @@ namespace {
 
 constexpr int WT = 32;           // queries per warp tile
 constexpr int WW = 8;            // warps per block of the pair passes
-constexpr int RSPAN = 64;        // representatives per block (grid.y splits the rest)
-constexpr int NBK = 32;          // distance buckets per representative
+constexpr int RSPAN = 32;        // representatives per block (grid.y splits the rest)
+constexpr int NBK = 64;          // window buckets per representative
 constexpr float SLACK = 1.0f + 2.4e-7f;
 
 __device__ __forceinline__ bool keep_pair(float d, float lo, float gh, float psi, float lemma) {
@@ -155,6 +158,18 @@ __device__ __forceinline__ void load_tile(const float* __restrict__ D, int64_t m
   __syncwarp();
 }
 
+// integer key with the order of the float (negative values included)
+__device__ __forceinline__ unsigned fkey(float v) {
+  const unsigned b = __float_as_uint(v);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// the binning key of a kept pair: the window's lower end rho(q, r) - g(q)
+__device__ __forceinline__ float window_key(float d, float gh) { return d - gh; }
+
 // The pair passes: block (x, y) covers queries [x * 256, +256) (one warp tile
 // of 32 queries per warp) and representatives [y * RSPAN, +RSPAN); per-block
 // reductions go through shared memory, so global memory sees one update per
@@ -177,9 +192,8 @@ __device__ __forceinline__ PairCtx pair_ctx(int64_t q0, int lane, int64_t m,
   return c;
 }
 
-// Pass 1: per representative, the smallest and largest kept rho(q, r) (float
-// bits: distances are >= 0, so integer order is value order); per query its
-// kept count.
+// Pass 1: per representative, the smallest and largest binning key of its
+// kept pairs (as order-preserving integer keys); per query its kept count.
 __global__ void __launch_bounds__(WW * 32)
 wrange_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __restrict__ g,
               const float* __restrict__ g1, const float* __restrict__ psi_plus, float rel,
@@ -189,7 +203,7 @@ wrange_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __re
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rb = blockIdx.y * RSPAN, re = min(n_r, rb + RSPAN);
   for (int i = threadIdx.x; i < RSPAN; i += blockDim.x) {
-    smin[i] = 0x7f7f7f7fu;
+    smin[i] = 0xffffffffu;
     smax[i] = 0u;
   }
   __syncthreads();
@@ -205,8 +219,9 @@ wrange_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __re
         const bool kp = c.live && keep_pair(v, c.lo, c.gh, psi_plus[r0 + rr], c.lemma);
         kept += kp;
         // warp reductions first: one shared-memory update per (warp, r)
-        const unsigned vmin = __reduce_min_sync(0xffffffffu, kp ? __float_as_uint(v) : 0xffffffffu);
-        const unsigned vmax = __reduce_max_sync(0xffffffffu, kp ? __float_as_uint(v) : 0u);
+        const unsigned key = fkey(window_key(v, c.gh));
+        const unsigned vmin = __reduce_min_sync(0xffffffffu, kp ? key : 0xffffffffu);
+        const unsigned vmax = __reduce_max_sync(0xffffffffu, kp ? key : 0u);
         if (lane == 0 && vmin != 0xffffffffu) {
           atomicMin(&smin[r0 + rr - rb], vmin);
           atomicMax(&smax[r0 + rr - rb], vmax);
@@ -218,7 +233,7 @@ wrange_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __re
   }
   __syncthreads();
   for (int i = threadIdx.x; i < re - rb; i += blockDim.x) {
-    if (smin[i] != 0x7f7f7f7fu) {  // some pair of r kept in this block
+    if (smin[i] != 0xffffffffu) {  // some pair of r kept in this block
       atomicMin(&rmin[rb + i], smin[i]);
       atomicMax(&rmax[rb + i], smax[i]);
     }
@@ -226,8 +241,9 @@ wrange_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __re
 }
 
 __device__ __forceinline__ int bucket_of(float v, float lo, float scale) {
-  return min(NBK - 1, (int)((v - lo) * scale));
+  return min(NBK - 1, max(0, (int)((v - lo) * scale)));
 }
+
 
 // Passes 2 and 3.  Count: every (r, bucket) bin of the block's pairs ->
 // counts[block x][bin].  Scatter: the pairs, at the bins' offsets plus the
@@ -237,8 +253,9 @@ __global__ void __launch_bounds__(WW * 32)
 wbin_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __restrict__ g,
             const float* __restrict__ g1, const float* __restrict__ psi_plus, float rel,
             const unsigned* __restrict__ rmin, const unsigned* __restrict__ rmax,
-            int* __restrict__ counts, const int* __restrict__ bin_off, int* __restrict__ pair_q,
-            float* __restrict__ pair_d) {
+            int* __restrict__ counts, const int* __restrict__ bin_off,
+            const float* __restrict__ thr, int* __restrict__ pair_q, float* __restrict__ pair_d,
+            float* __restrict__ pair_t) {
   __shared__ float tiles[WW][WT][WT + 1];
   __shared__ int h[RSPAN * NBK];
   __shared__ float sblo[RSPAN], sscale[RSPAN];
@@ -251,8 +268,8 @@ wbin_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __rest
     h[i] = SCATTER ? (bin < nbins ? bin_off[bin] + counts[bin * nqb + blockIdx.x] : 0) : 0;
   }
   for (int i = threadIdx.x; i < re - rb; i += blockDim.x) {
-    const float blo = __uint_as_float(rmin[rb + i]);
-    const float bhi = __uint_as_float(rmax[rb + i]);
+    const float blo = fkey_inv(rmin[rb + i]);
+    const float bhi = fkey_inv(rmax[rb + i]);
     sblo[i] = blo;
     sscale[i] = bhi > blo ? (float)NBK / (bhi - blo) : 0.0f;
   }
@@ -260,6 +277,7 @@ wbin_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __rest
   const int64_t q0 = ((int64_t)blockIdx.x * WW + wid) * WT;
   if (q0 < m) {
     const PairCtx c = pair_ctx(q0, lane, m, g, g1, rel);
+    const float my_thr = SCATTER && c.live ? thr[c.q] : 0.0f;
     for (int r0 = rb; r0 < re; r0 += WT) {
       load_tile(D, m, n_r, q0, r0, tiles[wid], lane);
       const int nr = min(WT, re - r0);
@@ -267,11 +285,12 @@ wbin_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __rest
         const int rl = r0 + rr - rb;
         const float v = tiles[wid][lane][rr];
         if (c.live && keep_pair(v, c.lo, c.gh, psi_plus[r0 + rr], c.lemma)) {
-          const int slot = rl * NBK + bucket_of(v, sblo[rl], sscale[rl]);
+          const int slot = rl * NBK + bucket_of(window_key(v, c.gh), sblo[rl], sscale[rl]);
           const int pos = atomicAdd(&h[slot], 1);
           if (SCATTER) {
             pair_q[pos] = (int)c.q;
             pair_d[pos] = v;
+            pair_t[pos] = my_thr;
           }
         }
       }
@@ -503,13 +522,14 @@ int launch_window_pairs_count(const float* D, int64_t m, int n_r, const float* g
   const int64_t qblocks = window_pair_blocks(m);
   if (qblocks > 0) {
     const dim3 grid((unsigned)qblocks, (n_r + RSPAN - 1) / RSPAN);
-    RBC_CUDA(cudaMemsetAsync(rmin, 0x7f, n_r * sizeof(unsigned), st));  // above any distance
+    RBC_CUDA(cudaMemsetAsync(rmin, 0xff, n_r * sizeof(unsigned), st));  // above any key
     RBC_CUDA(cudaMemsetAsync(rmax, 0, n_r * sizeof(unsigned), st));
     RBC_CUDA(cudaMemsetAsync(q_kept, 0, m * sizeof(int), st));
     wrange_kernel<<<grid, WW * 32, 0, st>>>(D, m, n_r, g, g1, psi_plus, rel, rmin, rmax, q_kept);
     RBC_LAUNCH_CHECK("wrange_kernel");
     wbin_kernel<false><<<grid, WW * 32, 0, st>>>(D, m, n_r, g, g1, psi_plus, rel, rmin, rmax,
-                                                 counts, nullptr, nullptr, nullptr);
+                                                 counts, nullptr, nullptr, nullptr, nullptr,
+                                                 nullptr);
     RBC_LAUNCH_CHECK("wbin_kernel");
     bin_colscan_kernel<<<(unsigned)((nbins * 32 + 255) / 256), 256, 0, st>>>(
         counts, (int)qblocks, nbins, totals);
@@ -523,12 +543,13 @@ int launch_window_pairs_count(const float* D, int64_t m, int n_r, const float* g
 int launch_window_pairs_scatter(const float* D, int64_t m, int n_r, const float* g,
                                 const float* g1, const float* psi_plus, float rel,
                                 const unsigned* rmin, const unsigned* rmax, int* counts,
-                                const int* bin_off, int* pair_q, float* pair_d, cudaStream_t st) {
+                                const int* bin_off, const float* thr, int* pair_q,
+                                float* pair_d, float* pair_t, cudaStream_t st) {
   const int64_t qblocks = window_pair_blocks(m);
   if (qblocks == 0) return RBC_OK;
   const dim3 grid((unsigned)qblocks, (n_r + RSPAN - 1) / RSPAN);
   wbin_kernel<true><<<grid, WW * 32, 0, st>>>(D, m, n_r, g, g1, psi_plus, rel, rmin, rmax, counts,
-                                              bin_off, pair_q, pair_d);
+                                              bin_off, thr, pair_q, pair_d, pair_t);
   RBC_LAUNCH_CHECK("wbin_kernel");
   return RBC_OK;
 }
