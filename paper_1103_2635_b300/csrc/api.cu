@@ -64,6 +64,7 @@ struct rbc_index {
   int dpad = 0;               // low-precision row length (multiple of 64)
   void* Xlp = nullptr;        // [list_entries, dpad]
   float* xnorm = nullptr;     // [list_entries] |x~|^2
+  void* xnblock = nullptr;    // [list_entries + NORM_PAD, 16] bf16 norm block (high, low)
   unsigned* lp_max = nullptr; // [4] float bits: max|x-x~|, max|x~|, max|r-r~|, max|r~|
   void* Rlp = nullptr;        // [n_r, dpad]
   float* rnorm = nullptr;     // [n_r]
@@ -661,6 +662,10 @@ int make_lp_copies(rbc_index* ix, cudaStream_t st) {
   RBC_CUDA(cudaMemsetAsync(ix->lp_max, 0, 4 * sizeof(unsigned), st));
   RBC_TRY(launch_to_lowp(ix->X32, n, d, ix->dpad, ix->storage, xl, ix->xnorm, nullptr,
                          ix->lp_max, ix->lp_max + 1, st));
+  // -|x~|^2 / 2 as a bf16 (high, low) block: the windowed kernel adds it to
+  // its accumulators with one extra MMA instead of a per-column FMA
+  RBC_TRY(ix->alloc(reinterpret_cast<uint16_t**>(&ix->xnblock), (n + NORM_PAD) * NBLOCK_COLS));
+  RBC_TRY(launch_norm_block(ix->xnorm, n, n + NORM_PAD, ix->xnblock, st));
   RBC_TRY(launch_to_lowp(ix->R32, n_r, d, ix->dpad, ix->storage, rl, ix->rnorm, nullptr,
                          ix->lp_max + 2, ix->lp_max + 3, st));
   ix->Xlp = xl;
@@ -1279,7 +1284,7 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   RBC_TRY(ar.alloc(&cc, mb));
   RBC_CUDA(cudaMemsetAsync(cc, 0, mb * sizeof(int), st));
   LpMatrix Qm{ql.lp, ql.norm, mb, ix->dpad, ix->storage};
-  LpMatrix Xm{ix->Xlp, ix->xnorm, n, ix->dpad, ix->storage};
+  LpMatrix Xm{ix->Xlp, ix->xnorm, n, ix->dpad, ix->storage, ix->xnblock};
   EmitOut eo{thr, cs, cr, cc, CAND_CAP};
   tmark(1, st);
   RBC_TRY(launch_bf_tc_emit(Qm, Xm, items, choff + n_r, max_items, pq, pt, eo, sms, st, dev_err));

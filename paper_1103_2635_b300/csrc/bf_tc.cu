@@ -468,6 +468,27 @@ int encode_map(CUtensorMap* map, const void* base, int64_t rows, int dpad, int s
   return RBC_OK;
 }
 
+int encode_nblock_map(CUtensorMap* map, const void* base, int64_t rows, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return RBC_ERR_CUDA;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)NBLOCK_COLS, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)NBLOCK_COLS * 2};
+  cuuint32_t box[2] = {(cuuint32_t)NBLOCK_COLS, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (norm block) failed (%d): rows=%lld", (int)r,
+              (long long)rows);
+    return RBC_ERR_CUDA;
+  }
+  return RBC_OK;
+}
+
 }  // namespace tc
 
 namespace {

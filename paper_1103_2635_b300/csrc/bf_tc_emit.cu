@@ -11,13 +11,18 @@
 //
 // Every query q carries a score threshold T(q) (window.cu): no point whose
 // score |x~|^2 - 2 q~.x~ exceeds T(q) can be within g(q) of q, the bound of
-// its k-th neighbour distance.  So the epilogue keeps no lists at all: per
-// 32-column chunk it forms the scores, takes their minimum, and only when
-// that minimum is <= T(q) appends the qualifying (score, row) pairs to q's
-// candidate buffer in global memory.  The candidates are re-ranked exactly
-// afterwards (select.cu).
+// its k-th neighbour distance.  The norm term is folded into the MMA: next to
+// each database tile the stage holds the tile's norm block (-|x~|^2 / 2 as a
+// bf16 high and low part, 16 columns), and one extra bf16 MMA of an all-ones
+// A operand against it adds -|x~|^2 / 2 to every accumulator, which then
+// holds q~.x~ - |x~|^2 / 2 = -s / 2.  So the epilogue keeps no lists, loads
+// no norms and does no arithmetic per score: per 32-column chunk it takes
+// the maximum of the raw accumulators, and only when that reaches -T(q) / 2
+// appends the qualifying (score, row) pairs to q's candidate buffer in
+// global memory.  The candidates are re-ranked exactly afterwards
+// (select.cu).
 //
-//   warp 0      TMA producer: database tiles of BN rows + their norms
+//   warp 0      TMA producer: database tiles of BN rows + their norm blocks
 //   warp 1      tensor-memory allocation, MMA issue (M = 128, N = BN, K = 16)
 //   warps 2-3   query gather (cp.async), per-row query id and threshold;
 //               the two warps take alternate items (a short window leaves
@@ -66,27 +71,54 @@ struct EmitParams {
   uint32_t* dev_err;
 };
 
-template <int KB, int BN, int S, int NR, int QSTAGES>
+template <int KB, int BN, int S, int QSTAGES>
 struct EmitSmem {
   static constexpr int NBUF = (512 / BN) < 4 ? (512 / BN) : 4;  // TMEM accumulator buffers
   static constexpr int Q_BYTES = KB * BM * 128;
   static constexpr int X_STAGE = KB * BN * 128;
-  static constexpr int NORM_STAGE = BN * 4;
+  static constexpr int NB_STAGE = BN * NBLOCK_COLS * 2;          // a tile's norm block
+  static constexpr int ONES_BYTES = BM * NBLOCK_COLS * 2;        // the all-ones A block
   static constexpr int OFF_Q = 0;
   static constexpr int OFF_X = OFF_Q + QSTAGES * Q_BYTES;
-  static constexpr int OFF_NORM = OFF_X + S * X_STAGE;
-  static constexpr int OFF_ROWQ = OFF_NORM + NR * NORM_STAGE;  // [QSTAGES][BM] query id or -1
-  static constexpr int OFF_ROWT = OFF_ROWQ + QSTAGES * BM * 4;  // [QSTAGES][BM] threshold
+  static constexpr int OFF_NB = OFF_X + S * X_STAGE;
+  static constexpr int OFF_ONES = OFF_NB + S * NB_STAGE;
+  static constexpr int OFF_ROWQ = OFF_ONES + ONES_BYTES;        // [QSTAGES][BM] query id or -1
+  static constexpr int OFF_ROWT = OFF_ROWQ + QSTAGES * BM * 4;  // [QSTAGES][BM] -T / 2
   static constexpr int OFF_BAR = OFF_ROWT + QSTAGES * BM * 4;
-  // full[S], empty[S], nfull[NR], nempty[NR], tfull[NBUF], tempty[NBUF], qfull[QS], qempty[QS]
-  static constexpr int NBAR = 2 * S + 2 * NR + 2 * NBUF + 2 * QSTAGES;
+  // full[S], empty[S], tfull[NBUF], tempty[NBUF], qfull[QS], qempty[QS]
+  static constexpr int NBAR = 2 * S + 2 * NBUF + 2 * QSTAGES;
   static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;  // tmem base, abort flag
   static constexpr int BYTES = OFF_MISC + 16;
   static constexpr int ALLOC = BYTES + 1024;  // slack for 1024-byte alignment
   static_assert(ALLOC <= 232448, "shared memory budget");
   static_assert(OFF_X % 1024 == 0 && X_STAGE % 1024 == 0, "swizzled tiles need 1024-byte alignment");
+  static_assert(OFF_NB % 1024 == 0 && NB_STAGE % 1024 == 0 && OFF_ONES % 1024 == 0,
+                "norm blocks need 1024-byte alignment");
   static_assert(QSTAGES % 2 == 0, "query stages alternate between two gather warps");
 };
+
+// Shared-memory descriptor of a K-major operand with 32-byte rows (16 bf16)
+// and 32-byte swizzle: 8-row groups 256 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(256 >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)6 << 61;                   // 32-byte swizzle
+  return d;
+}
+
+// Largest of 32 values as a depth-4 tree of three-input maxima.
+__device__ __forceinline__ float max_of32(const float (&u)[32]) {
+  float a[11];
+#pragma unroll
+  for (int j = 0; j < 10; ++j) a[j] = max3f(u[3 * j], u[3 * j + 1], u[3 * j + 2]);
+  a[10] = fmaxf(u[30], u[31]);
+  const float b0 = max3f(a[0], a[1], a[2]), b1 = max3f(a[3], a[4], a[5]);
+  const float b2 = max3f(a[6], a[7], a[8]), b3 = fmaxf(a[9], a[10]);
+  return fmaxf(max3f(b0, b1, b2), b3);
+}
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
@@ -100,10 +132,11 @@ __device__ __forceinline__ void st_shared_zero16(uint32_t dst) {
 // QSTAGES query stages (even: the two gather warps alternate over them): the
 // gather of an item's rows takes a few microseconds, longer than a one-tile
 // item, so several are kept in flight.
-template <int KB, int BN, int S, int NR, int QSTAGES>
+template <int KB, int BN, int S, int QSTAGES>
 __global__ void __launch_bounds__(EpiShape<BN>::THREADS, 1)
-bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32_t idesc) {
-  using L = EmitSmem<KB, BN, S, NR, QSTAGES>;
+bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap nbmap,
+                  EmitParams p, uint32_t idesc, uint32_t idesc_norm) {
+  using L = EmitSmem<KB, BN, S, QSTAGES>;
   using E = EpiShape<BN>;
   constexpr int E_NEPI = E::NEPI;
   extern __shared__ uint8_t smem_raw[];
@@ -111,16 +144,15 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32
                                              ~(uintptr_t)1023);
   uint8_t* sQ = smem + L::OFF_Q;
   uint8_t* sX = smem + L::OFF_X;
-  float* sNorm = reinterpret_cast<float*>(smem + L::OFF_NORM);
+  uint8_t* sNB = smem + L::OFF_NB;
+  uint32_t* sOnes = reinterpret_cast<uint32_t*>(smem + L::OFF_ONES);
   int* sRowQ = reinterpret_cast<int*>(smem + L::OFF_ROWQ);
   float* sRowT = reinterpret_cast<float*>(smem + L::OFF_ROWT);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
   constexpr int NBUF = L::NBUF;
   uint64_t* full = bars;
   uint64_t* empty = full + S;
-  uint64_t* nfull = empty + S;
-  uint64_t* nempty = nfull + NR;
-  uint64_t* tfull = nempty + NR;
+  uint64_t* tfull = empty + S;
   uint64_t* tempty = tfull + NBUF;
   uint64_t* qfull = tempty + NBUF;
   uint64_t* qempty = qfull + QSTAGES;
@@ -135,10 +167,6 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int r = 0; r < NR; ++r) {
-      mbar_init(&nfull[r], 1);
-      mbar_init(&nempty[r], E_NEPI);
-    }
     for (int b = 0; b < NBUF; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], E_NEPI);
@@ -151,6 +179,10 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
+  // the all-ones A block of the norm MMA (bf16 1.0 pairs; every layout of an
+  // all-ones block reads the same)
+  for (int i = threadIdx.x; i < L::ONES_BYTES / 4; i += blockDim.x) sOnes[i] = 0x3F803F80u;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(sTmem)),
@@ -176,21 +208,16 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32
       for (int x = e.x_begin & ~3; x < e.x_end; x += BN, ++it) {
         const int s = it % S;
         const uint32_t ph = (it / S) & 1;
-        const int r = it % NR;
-        const uint32_t nph = (it / NR) & 1;
-        bool got = mbar_wait(&empty[s], ph ^ 1, sAbort, p.dev_err) &&
-                   mbar_wait(&nempty[r], nph ^ 1, sAbort, p.dev_err);
-        if (!__all_sync(0xffffffffu, got)) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&empty[s], ph ^ 1, sAbort, p.dev_err))) {
           ok = false;
           break;
         }
         if (lane == 0) {
-          mbar_arrive_expect_tx(&full[s], L::X_STAGE);
+          mbar_arrive_expect_tx(&full[s], L::X_STAGE + L::NB_STAGE);
 #pragma unroll
           for (int kb = 0; kb < KB; ++kb)
             tma_load_2d(sX + s * L::X_STAGE + kb * BN * 128, &xmap, &full[s], kb * 64, x);
-          mbar_arrive_expect_tx(&nfull[r], L::NORM_STAGE);
-          bulk_load(sNorm + r * BN, p.xnorm + x, L::NORM_STAGE, &nfull[r]);
+          tma_load_2d(sNB + s * L::NB_STAGE, &nbmap, &full[s], 0, x);
         }
         __syncwarp();
       }
@@ -198,8 +225,6 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32
     if (lane == 0) {
       for (uint32_t j = (it > (uint32_t)S ? it - S : 0); j < it; ++j)
         mbar_wait(&full[j % S], (j / S) & 1, sAbort, p.dev_err);
-      for (uint32_t j = (it > (uint32_t)NR ? it - NR : 0); j < it; ++j)
-        mbar_wait(&nfull[j % NR], (j / NR) & 1, sAbort, p.dev_err);
     }
   } else if (warp >= E_GATHER && warp < E_GATHER + E_NGATHER) {
     // ---------------- query gather (warp gw takes items qi = gw mod 2) ----------------
@@ -231,7 +256,7 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32
         const int row = lane + 32 * t;
         const int src = srcs[t];
         sRowQ[qs * BM + row] = src;
-        sRowT[qs * BM + row] = src < 0 ? -INFINITY : (p.pair_t ? thrs[t] : p.out.thr[src]);
+        sRowT[qs * BM + row] = src < 0 ? INFINITY : -0.5f * (p.pair_t ? thrs[t] : p.out.thr[src]);
         const uint8_t* g = p.qlp + (int64_t)(src >= 0 ? src : 0) * p.q_row_bytes;
 #pragma unroll
         for (int kb = 0; kb < KB; ++kb)
@@ -286,6 +311,9 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32
               uint64_t bd = smem_desc_sw128(xb + kb * BN * 128 + k16 * 32);
               mma_f16(d_tmem, ad, bd, idesc, (kb | k16) != 0);
             }
+          // + (-|x~|^2 / 2) in every row: ones x norm block (bf16, K = 16)
+          mma_f16(d_tmem, smem_desc_sw32(smem_u32(sOnes)),
+                  smem_desc_sw32(smem_u32(sNB + s * L::NB_STAGE)), idesc_norm, 1u);
           mma_commit(&empty[s]);
           mma_commit(&tfull[buf]);
         }
@@ -315,7 +343,7 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32
       const uint32_t qph = (qi / QSTAGES) & 1;
       if (!__all_sync(0xffffffffu, mbar_wait(&qfull[qs], qph, sAbort, p.dev_err))) break;
       const int myq = sRowQ[qs * BM + row];
-      const float myT = sRowT[qs * BM + row];
+      const float myT = sRowT[qs * BM + row];  // -T(q) / 2: emit where the accumulator reaches it
       __syncwarp();
       if (lane == 0) mbar_arrive(&qempty[qs]);
       ++qi;
@@ -323,13 +351,9 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32
       int* cr = p.out.cand_row + (int64_t)(myq >= 0 ? myq : 0) * cap;
       int* cc = p.out.cand_cnt + (myq >= 0 ? myq : 0);
       for (int x = e.x_begin & ~3; x < e.x_end; x += BN, ++it) {
-        const int r = it % NR;
-        const uint32_t nph = (it / NR) & 1;
         const int buf = it % NBUF;
         const uint32_t aph = (it / NBUF) & 1;
-        bool got = mbar_wait(&nfull[r], nph, sAbort, p.dev_err) &&
-                   mbar_wait(&tfull[buf], aph, sAbort, p.dev_err);
-        if (!__all_sync(0xffffffffu, got)) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&tfull[buf], aph, sAbort, p.dev_err))) {
           ok = false;
           break;
         }
@@ -343,25 +367,17 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[buf]);
-        const float* nrm = sNorm + r * BN + part * COLS;
         const int lo = e.x_begin - x - part * COLS;  // first valid column of the slice
         const int hi = e.x_end - x - part * COLS;    // one past the last valid column
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
-          float u[32];
-          const float4* n4 = reinterpret_cast<const float4*>(nrm + c * 32);
+          float u[32];  // -s / 2 per column
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const float4 nn = n4[j];
-            fma2(u[4 * j], u[4 * j + 1], __uint_as_float(raw[c][4 * j]),
-                 __uint_as_float(raw[c][4 * j + 1]), -2.0f, nn.x, nn.y);
-            fma2(u[4 * j + 2], u[4 * j + 3], __uint_as_float(raw[c][4 * j + 2]),
-                 __uint_as_float(raw[c][4 * j + 3]), -2.0f, nn.z, nn.w);
-          }
-          // The minimum runs over all 32 columns, including any outside the
+          for (int j = 0; j < 32; ++j) u[j] = __uint_as_float(raw[c][j]);
+          // The maximum runs over all 32 columns, including any outside the
           // window (real rows, or zero rows past the matrix end): a false
           // alarm only costs the slow path, where the in-window mask decides.
-          const bool hit = min_of32(u) <= myT;
+          const bool hit = max_of32(u) >= myT;
           if (__any_sync(0xffffffffu, hit)) {  // warp-uniform: the rare path
             if (hit) {
               const int clo = lo - c * 32, chi = hi - c * 32;
@@ -371,10 +387,10 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32
               const int cb = x + part * COLS + c * 32;
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
-                if (((valid >> j) & 1u) && u[j] <= myT) {
+                if (((valid >> j) & 1u) && u[j] >= myT) {
                   const int pos = atomicAdd(cc, 1);
                   if (pos < cap) {
-                    cs[pos] = u[j];
+                    cs[pos] = -2.0f * u[j];
                     cr[pos] = cb + j;
                   }
                 }
@@ -383,8 +399,6 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32
             __syncwarp();
           }
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&nempty[r]);
       }
     }
   }
@@ -398,19 +412,21 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, EmitParams p, uint32
   }
 }
 
-template <int KB, int BN, int S, int NR, int QS>
+template <int KB, int BN, int S, int QS>
 int launch_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
                 const int* num_items_dev, int max_items, const int* pair_q, const float* pair_t,
                 const EmitOut& out, int grid, cudaStream_t st, uint32_t* dev_err) {
-  using L = EmitSmem<KB, BN, S, NR, QS>;
-  CUtensorMap xmap;
+  using L = EmitSmem<KB, BN, S, QS>;
+  CUtensorMap xmap, nbmap;
   RBC_TRY_TC(encode_map(&xmap, Xm.data, Xm.rows, Xm.dpad, Xm.storage, BN));
-  auto kern = bf_tc_emit_kernel<KB, BN, S, NR, QS>;
+  RBC_TRY_TC(encode_nblock_map(&nbmap, Xm.nblock, Xm.rows, BN));
+  auto kern = bf_tc_emit_kernel<KB, BN, S, QS>;
   RBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC));
   EmitParams p{items,  num_items_dev, max_items, pair_q, pair_t,
                static_cast<const uint8_t*>(Qm.data), (int64_t)Qm.dpad * 2, Xm.norm, out, dev_err};
   const uint32_t idesc = idesc_f16(Qm.storage == RBC_BF16 ? 1 : 0, BM, BN);
-  kern<<<grid, EpiShape<BN>::THREADS, L::ALLOC, st>>>(xmap, p, idesc);
+  const uint32_t idesc_norm = idesc_f16(1, BM, BN);  // the norm block is bf16 for any storage
+  kern<<<grid, EpiShape<BN>::THREADS, L::ALLOC, st>>>(xmap, nbmap, p, idesc, idesc_norm);
   ++t_launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -439,11 +455,15 @@ int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* it
     return RBC_ERR_ARG;
   }
   if (max_items <= 0) return RBC_OK;
+  if (!Xm.nblock) {
+    set_error("tensor-core emission: the database has no norm block");
+    return RBC_ERR_ARG;
+  }
   switch (Qm.dpad / 64) {
-    case 1: return launch_emit<1, 256, 4, 8, 4>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_t, out, grid, st, dev_err);
-    case 2: return launch_emit<2, 128, 3, 8, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_t, out, grid, st, dev_err);
-    case 3: return launch_emit<3, 64, 3, 8, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_t, out, grid, st, dev_err);
-    case 4: return launch_emit<4, 64, 2, 4, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_t, out, grid, st, dev_err);
+    case 1: return launch_emit<1, 256, 3, 4>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_t, out, grid, st, dev_err);
+    case 2: return launch_emit<2, 128, 3, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_t, out, grid, st, dev_err);
+    case 3: return launch_emit<3, 64, 3, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_t, out, grid, st, dev_err);
+    case 4: return launch_emit<4, 64, 2, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_t, out, grid, st, dev_err);
     default: break;
   }
   set_error("tensor-core BF: padded dimension %d unsupported", Qm.dpad);

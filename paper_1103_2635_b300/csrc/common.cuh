@@ -79,7 +79,10 @@ __host__ __device__ __forceinline__ float score_bound(float g, float qn, float q
   if (!(g < INFINITY)) return INFINITY;
   const float G = (g + qerr + xerr) * (1.0f + 4.8e-7f);
   const float span = (sqrtf(qn) + xnmax) * (1.0f + 4.8e-7f);
-  const float ef = 2.0f * (float)(d + 4) * 1.9073486e-06f * span * span;
+  // doubled FP32 evaluation bound, plus 2^-16 max|x~|^2 for a norm term that
+  // enters as a bf16 (high, low) pair (error <= 2^-17 |x~|^2)
+  const float ef = 2.0f * (float)(d + 4) * 1.9073486e-06f * span * span +
+                   1.5258789e-05f * xnmax * xnmax;
   return (G * G * (1.0f + 4.8e-7f) - qn * (1.0f - 4.8e-7f) + ef) * (1.0f + 4.8e-7f) + 1e-30f;
 }
 

@@ -43,7 +43,11 @@ struct LpMatrix {
   int64_t rows;
   int dpad;          // multiple of 64
   int storage;       // RBC_BF16 / RBC_F16
+  const void* nblock = nullptr;  // optional [rows, 16] bf16: -|x~|^2 / 2 as (high, low, 0 ...)
 };
+
+// columns of a norm block row, and the rows past the end that stay readable
+constexpr int NBLOCK_COLS = 16;
 
 bool tc_available();
 int launch_bf_tc_topc(const LpMatrix& Qm, const LpMatrix& Xm, int C, const TileWork& w,
@@ -245,6 +249,12 @@ int launch_to_lowp(const float* src, int64_t rows, int d, int dpad, int storage,
 int launch_gather_lp_rows(const void* src, const float* snorm, const float* serr, const int* idx,
                           int64_t rows, int dpad, void* dst, float* dnorm, float* derr,
                           cudaStream_t st);
+// Norm block of a low-precision matrix: row i = (h, l, 0, ..., 0) in bf16
+// with h = bf16(-norm[i] / 2), l = bf16(-norm[i] / 2 - h), so that an MMA of
+// an all-ones row against it adds -|x~|^2 / 2 to every accumulator of column
+// i (to about 2^-17 relative).  rows_out >= rows; rows past `rows` are zero.
+int launch_norm_block(const float* norm, int64_t rows, int64_t rows_out, void* dst,
+                      cudaStream_t st);
 // out[i] = qorig ? qorig[rows[i]] : rows[i], for i < *n_dev (or n when n_dev is null)
 int launch_map_rows(const int* rows, const int* n_dev, int n, const int* qorig, int* out,
                     cudaStream_t st);

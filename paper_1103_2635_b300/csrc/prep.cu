@@ -10,6 +10,8 @@
 //   can move under rounding (triangle inequality of the metric:
 //   |rho(q~, x~) - rho(q, x)| <= |q - q~| + |x - x~|), which the exact search
 //   needs to stay exact with low-precision storage.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -106,6 +108,21 @@ __global__ void gather_lp_rows_kernel(const uint4* __restrict__ src, const float
   }
 }
 
+__global__ void norm_block_kernel(const float* __restrict__ norm, int64_t rows, int64_t rows_out,
+                                  __nv_bfloat16* __restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows_out;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = i < rows ? -0.5f * norm[i] : 0.0f;  // exact: a power-of-two scale
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));  // v - h exact
+    __nv_bfloat16* row = dst + i * NBLOCK_COLS;
+    row[0] = h;
+    row[1] = l;
+#pragma unroll
+    for (int j = 2; j < NBLOCK_COLS; ++j) row[j] = __float2bfloat16_rn(0.0f);
+  }
+}
+
 __global__ void map_rows_kernel(const int* __restrict__ rows, const int* __restrict__ n_dev, int n,
                                 const int* __restrict__ qorig, int* __restrict__ out) {
   int lim = n_dev ? *n_dev : n;
@@ -160,6 +177,16 @@ int launch_gather_lp_rows(const void* src, const float* snorm, const float* serr
       static_cast<const uint4*>(src), snorm, serr, idx, rows, dpad * 2 / 16,
       static_cast<uint4*>(dst), dnorm, derr);
   RBC_LAUNCH_CHECK("gather_lp_rows_kernel");
+  return RBC_OK;
+}
+
+int launch_norm_block(const float* norm, int64_t rows, int64_t rows_out, void* dst,
+                      cudaStream_t st) {
+  if (rows_out <= 0) return RBC_OK;
+  const unsigned blocks = (unsigned)std::min<int64_t>((rows_out + 255) / 256, 148 * 16);
+  norm_block_kernel<<<blocks, 256, 0, st>>>(norm, rows, rows_out,
+                                            static_cast<__nv_bfloat16*>(dst));
+  RBC_LAUNCH_CHECK("norm_block_kernel");
   return RBC_OK;
 }
 

@@ -270,6 +270,9 @@ __device__ __forceinline__ uint32_t hit_mask32(const float (&u)[32], float t) {
 // 64 columns x box_rows rows, 128-byte swizzle (defined in bf_tc.cu).
 int encode_map(CUtensorMap* map, const void* base, int64_t rows, int dpad, int storage,
                int box_rows);
+// The same for a [rows, NBLOCK_COLS] bf16 norm block: boxes of 16 columns
+// (32 bytes) x box_rows rows, 32-byte swizzle.
+int encode_nblock_map(CUtensorMap* map, const void* base, int64_t rows, int box_rows);
 
 }  // namespace tc
 }  // namespace rbc
