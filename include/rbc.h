@@ -253,6 +253,8 @@ typedef struct {
   double stage2_ms;          /*   stage one / the main BF distance kernel / */
   double select_ms;          /*   merge + re-rank + certification / */
   double fallback_ms;        /*   FP32 re-search of uncertified queries */
+  int64_t candidates;        /* windowed search: points emitted by the tensor-core
+                                pass for the exact re-rank (summed over queries) */
 } rbc_search_stats;
 
 /* rbc_last_stats -- statistics of this thread's last search call (host only;

@@ -64,7 +64,8 @@ class _Stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "queries", "kept_reps", "tile_points", "stage2_items", "uncertified", "fp64_ties",
         "boundary_ties", "pairs", "kernel_launches")] + [
-        (name, ctypes.c_double) for name in ("stage1_ms", "stage2_ms", "select_ms", "fallback_ms")]
+        (name, ctypes.c_double) for name in ("stage1_ms", "stage2_ms", "select_ms", "fallback_ms")] + [
+        ("candidates", ctypes.c_int64)]
 
 
 def library_path() -> str:

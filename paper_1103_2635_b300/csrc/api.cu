@@ -248,7 +248,8 @@ thread_local rbc_search_stats t_stats_fixed;
 
 // device counters: ints [0] uncertified [1] fp64 ties [2] boundary ties,
 // [4..6] the same for the FP32 re-search; u64 sums [0] kept reps
-// [1] tile points [2] (query, point) pairs of the main pass
+// [1] tile points [2] (query, point) pairs of the main pass [3] emitted
+// candidates (windowed search)
 struct Counters {
   int* c = nullptr;
   unsigned long long* sums = nullptr;
@@ -296,15 +297,15 @@ __global__ void stats_pack_kernel(const int* c, const unsigned long long* sums,
     out[4] = (unsigned long long)(c[2] + c[6]);
     out[5] = (unsigned long long)c[4];
     out[6] = sums[2];
-    out[7] = 0;
+    out[7] = sums[3];
   }
 }
 
 int counters_alloc(Counters& cn, Arena& ar, cudaStream_t st) {
   RBC_TRY(ar.alloc(&cn.c, 8));
-  RBC_TRY(ar.alloc(&cn.sums, 3));
+  RBC_TRY(ar.alloc(&cn.sums, 4));
   RBC_CUDA(cudaMemsetAsync(cn.c, 0, 8 * sizeof(int), st));
-  RBC_CUDA(cudaMemsetAsync(cn.sums, 0, 3 * sizeof(unsigned long long), st));
+  RBC_CUDA(cudaMemsetAsync(cn.sums, 0, 4 * sizeof(unsigned long long), st));
   t_launches = 0;
   for (double& v : t_timing.ms) v = 0;
   return RBC_OK;
@@ -1282,19 +1283,35 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   RBC_TRY(ar.alloc(&cs, mb * CAND_CAP));
   RBC_TRY(ar.alloc(&cr, mb * CAND_CAP));
   RBC_TRY(ar.alloc(&cc, mb));
-  RBC_CUDA(cudaMemsetAsync(cc, 0, mb * sizeof(int), st));
   LpMatrix Qm{ql.lp, ql.norm, mb, ix->dpad, ix->storage};
   LpMatrix Xm{ix->Xlp, ix->xnorm, n, ix->dpad, ix->storage, ix->xnblock};
-  EmitOut eo{thr, cs, cr, cc, CAND_CAP};
-  tmark(1, st);
-  RBC_TRY(launch_bf_tc_emit(Qm, Xm, items, choff + n_r, max_items, pq, pt, eo, sms, st, dev_err));
-  tmark(2, st);
-  // exact re-rank of the candidates; overflowing queries go to the FP32 re-search
+  // hit arena: each CTA appends its emissions to its own segment (a shared
+  // counter, no global atomics in the kernel); a post-pass fills the
+  // per-query buffers.  The segments hold 4x the hits of this workload; if
+  // one overflows, the batch is emitted again with direct per-query appends.
+  const int arena_sub = (int)std::min<int64_t>(
+      INT32_MAX / (4 * ARENA_SUBSEG),
+      std::max<int64_t>(512, (mb * 128 + sms * ARENA_SUBSEG - 1) / (sms * ARENA_SUBSEG)));
+  const int arena_seg = arena_sub * ARENA_SUBSEG;  // per CTA
+  int4* arena;
+  int *arena_cnt, *arena_ovf;
+  RBC_TRY(ar.alloc(&arena, (int64_t)sms * arena_seg));
+  RBC_TRY(ar.alloc(&arena_cnt, sms * ARENA_SUBSEG));
+  RBC_CUDA(cudaMemsetAsync(arena_cnt, 0, sms * ARENA_SUBSEG * sizeof(int), st));
+  RBC_TRY(ar.alloc(&arena_ovf, 1));
   int* fb_rows;
-  int* lc;
+  int *lc, *lc2, *fb2;
   RBC_TRY(ar.alloc(&fb_rows, mb));
   RBC_TRY(ar.alloc(&lc, 8));
-  RBC_CUDA(cudaMemsetAsync(lc, 0, 8 * sizeof(int), st));
+  RBC_TRY(ar.alloc(&fb2, mb));
+  RBC_TRY(ar.alloc(&lc2, 8));
+  const int xspan = (int)std::max<int64_t>(4096, (n + 2 * sms - 1) / (2 * sms) / 256 * 256);
+  const int nsplit = (int)((n + xspan - 1) / xspan);
+  const int max2 = (int)std::min<int64_t>((mb + TQ - 1) / TQ * nsplit, INT32_MAX);
+  EmitItem* items2;
+  int* n_items2;
+  RBC_TRY(ar.alloc(&items2, max2));
+  RBC_TRY(ar.alloc(&n_items2, 1));
   CandSelectArgs a{};
   a.cand_score = cs;
   a.cand_row = cr;
@@ -1316,56 +1333,70 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   a.out_dist = dist;
   a.fallback_rows = fb_rows;
   a.counters = lc;
-  RBC_TRY(launch_select_cands(a, st));
-  tmark(3, st);
-  RBC_TRY(launch_add_ints(cn.c, lc, 3, st));
-  // Queries whose candidate buffer overflowed (count in lc[0], on the device):
-  // k of their stored candidates give a much tighter threshold; emit again
-  // for them alone against the whole list storage and finish them.  Launched
-  // unconditionally with device-side counts (empty when nothing overflowed),
-  // so the batch needs one synchronisation, at its end.
-  RBC_TRY(launch_overflow_rethreshold(fb_rows, lc, mb, cs, cc, CAND_CAP, k, ql.norm, ql.err,
-                                      ix->lp_max, d, thr, st));
-  const int xspan = (int)std::max<int64_t>(4096, (n + 2 * sms - 1) / (2 * sms) / 256 * 256);
-  const int nsplit = (int)((n + xspan - 1) / xspan);
-  const int max2 = (int)std::min<int64_t>((mb + TQ - 1) / TQ * nsplit, INT32_MAX);
-  EmitItem* items2;
-  int* n_items2;
-  RBC_TRY(ar.alloc(&items2, max2));
-  RBC_TRY(ar.alloc(&n_items2, 1));
-  RBC_TRY(launch_dense_emit_items(lc, n, xspan, max2, items2, n_items2, st));
-  RBC_TRY(launch_bf_tc_emit(Qm, Xm, items2, n_items2, max2, fb_rows, nullptr, eo, sms, st,
-                            dev_err));
-  int* fb2;
-  int* lc2;
-  RBC_TRY(ar.alloc(&fb2, mb));
-  RBC_TRY(ar.alloc(&lc2, 8));
-  RBC_CUDA(cudaMemsetAsync(lc2, 0, 8 * sizeof(int), st));
-  CandSelectArgs a2 = a;
-  a2.rows = fb_rows;
-  a2.nrows_dev = lc;
-  a2.nrows = (int)mb;
-  a2.fallback_rows = fb2;
-  a2.counters = lc2;
-  RBC_TRY(launch_select_cands(a2, st));
-  RBC_TRY(launch_add_ints(cn.c + 4, lc2, 3, st));
-  int nfb2 = 0;
-  uint32_t herr = 0;
-  RBC_CUDA(cudaMemcpyAsync(&nfb2, lc2, sizeof(int), cudaMemcpyDeviceToHost, st));
-  RBC_CUDA(cudaMemcpyAsync(&herr, dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-  RBC_CUDA(cudaStreamSynchronize(st));
-  if (herr) {
-    set_error("windowed stage two reported device error flags 0x%x", herr);
-    return (herr & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
-  }
-  if (nfb2 > 0) {
-    // more points than a buffer holds tie within rounding: FP32 brute force
-    DbView db;
-    db.X32 = ix->X32;
-    db.xid = ix->members;
-    db.rows = n;
-    RBC_TRY(fallback_f32(Qb, fb2, nfb2, nullptr, db, d, k, ix->metric, ids, dist, cn.c + 4, ar,
-                         st));
+  for (int attempt = 0;; ++attempt) {
+    const bool direct = attempt > 0;
+    RBC_CUDA(cudaMemsetAsync(cc, 0, mb * sizeof(int), st));
+    RBC_CUDA(cudaMemsetAsync(arena_ovf, 0, sizeof(int), st));
+    RBC_CUDA(cudaMemsetAsync(lc, 0, 8 * sizeof(int), st));
+    RBC_CUDA(cudaMemsetAsync(lc2, 0, 8 * sizeof(int), st));
+    EmitOut eo{thr, cs, cr, cc, CAND_CAP};
+    EmitOut eo_arena = eo;
+    if (!direct) {
+      eo_arena.arena = arena;
+      eo_arena.arena_seg = arena_seg;
+      eo_arena.arena_cnt = arena_cnt;
+      eo_arena.arena_ovf = arena_ovf;
+    }
+    tmark(1, st);
+    RBC_TRY(launch_bf_tc_emit(Qm, Xm, items, choff + n_r, max_items, pq, pt, eo_arena, sms, st,
+                              dev_err));
+    if (!direct)
+      RBC_TRY(launch_scatter_hits(arena, arena_sub, arena_cnt, sms * ARENA_SUBSEG, cs, cr, cc,
+                                  CAND_CAP, st));
+    tmark(2, st);
+    // exact re-rank of the candidates; overflowing queries are collected
+    RBC_TRY(launch_select_cands(a, st));
+    tmark(3, st);
+    // Queries whose candidate buffer overflowed (count in lc[0], on the
+    // device): k of their stored candidates give a much tighter threshold;
+    // emit again for them alone against the whole list storage (direct
+    // appends) and finish them.  Launched unconditionally with device-side
+    // counts (empty when nothing overflowed), so the batch synchronises once.
+    RBC_TRY(launch_overflow_rethreshold(fb_rows, lc, mb, cs, cc, CAND_CAP, k, ql.norm, ql.err,
+                                        ix->lp_max, d, thr, st));
+    RBC_TRY(launch_dense_emit_items(lc, n, xspan, max2, items2, n_items2, st));
+    RBC_TRY(launch_bf_tc_emit(Qm, Xm, items2, n_items2, max2, fb_rows, nullptr, eo, sms, st,
+                              dev_err));
+    CandSelectArgs a2 = a;
+    a2.rows = fb_rows;
+    a2.nrows_dev = lc;
+    a2.nrows = (int)mb;
+    a2.fallback_rows = fb2;
+    a2.counters = lc2;
+    RBC_TRY(launch_select_cands(a2, st));
+    int host[3] = {0, 0, 0};  // rows left for the FP32 BF, device error flags, arena overflow
+    RBC_CUDA(cudaMemcpyAsync(&host[0], lc2, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBC_CUDA(cudaMemcpyAsync(&host[1], dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    RBC_CUDA(cudaMemcpyAsync(&host[2], arena_ovf, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBC_CUDA(cudaStreamSynchronize(st));
+    if (host[1]) {
+      set_error("windowed stage two reported device error flags 0x%x", (unsigned)host[1]);
+      return (host[1] & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
+    }
+    if (!direct && host[2]) continue;  // an arena segment overflowed: emit again directly
+    RBC_TRY(launch_add_ints(cn.c, lc, 3, st));
+    RBC_TRY(launch_add_ints(cn.c + 4, lc2, 3, st));
+    RBC_TRY(launch_sum_i32(cc, mb, cn.sums + 3, st));
+    if (host[0] > 0) {
+      // more points than a buffer holds tie within rounding: FP32 brute force
+      DbView db;
+      db.X32 = ix->X32;
+      db.xid = ix->members;
+      db.rows = n;
+      RBC_TRY(fallback_f32(Qb, fb2, host[0], nullptr, db, d, k, ix->metric, ids, dist, cn.c + 4,
+                           ar, st));
+    }
+    break;
   }
   tmark(4, st);
   taccumulate();
@@ -1410,6 +1441,7 @@ int rbc_last_stats(rbc_search_stats* out) {
     const unsigned long long* v = t_stats_host->v;
     t_stats_fixed.kept_reps = t_stats_host_kept >= 0 ? t_stats_host_kept : (int64_t)v[0];
     t_stats_fixed.tile_points = (int64_t)v[1];
+    t_stats_fixed.candidates = (int64_t)v[7];
     t_stats_fixed.uncertified = (int64_t)v[2];
     t_stats_fixed.fp64_ties = (int64_t)v[3];
     t_stats_fixed.boundary_ties = (int64_t)v[4];

@@ -87,7 +87,7 @@ struct EmitSmem {
   static constexpr int OFF_BAR = OFF_ROWT + QSTAGES * BM * 4;
   // full[S], empty[S], tfull[NBUF], tempty[NBUF], qfull[QS], qempty[QS]
   static constexpr int NBAR = 2 * S + 2 * NBUF + 2 * QSTAGES;
-  static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;  // tmem base, abort flag
+  static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;  // tmem base, abort flag, hit count
   static constexpr int BYTES = OFF_MISC + 16;
   static constexpr int ALLOC = BYTES + 1024;  // slack for 1024-byte alignment
   static_assert(ALLOC <= 232448, "shared memory budget");
@@ -158,6 +158,7 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
   uint64_t* qempty = qfull + QSTAGES;
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(smem + L::OFF_MISC);
   volatile int* sAbort = reinterpret_cast<volatile int*>(smem + L::OFF_MISC + 4);
+  int* sHits = reinterpret_cast<int*>(smem + L::OFF_MISC + 8);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -176,6 +177,7 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
       mbar_init(&qempty[q], 1 + E_NEPI);     // MMA commit + every epilogue warp
     }
     *sAbort = 0;
+    *sHits = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -336,6 +338,14 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
     uint32_t it = 0, qi = 0;
     bool ok = true;
     const int cap = p.out.cap;
+    // hit arena: this warp's private sub-segment and its fill count (kept
+    // identical in every lane, so no atomics are needed)
+    const int esub = p.out.arena_seg / ARENA_SUBSEG;
+    const int ew = warp - E_EPI0;
+    int4* hits = p.out.arena
+                     ? p.out.arena + (int64_t)blockIdx.x * p.out.arena_seg + (int64_t)ew * esub
+                     : nullptr;
+    int nhits = 0;
     for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
       const EmitItem e = p.items[item];
       if (e.x_end <= e.x_begin) continue;
@@ -379,15 +389,39 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
           // alarm only costs the slow path, where the in-window mask decides.
           const bool hit = max_of32(u) >= myT;
           if (__any_sync(0xffffffffu, hit)) {  // warp-uniform: the rare path
+            const int cb = x + part * COLS + c * 32;
+            uint32_t hm = 0;  // this row's emitted columns of the chunk
             if (hit) {
               const int clo = lo - c * 32, chi = hi - c * 32;
               const uint32_t below_hi = chi >= 32 ? 0xffffffffu : (chi <= 0 ? 0u : (1u << chi) - 1u);
               const uint32_t below_lo = clo >= 32 ? 0xffffffffu : (clo <= 0 ? 0u : (1u << clo) - 1u);
               const uint32_t valid = below_hi & ~below_lo;
-              const int cb = x + part * COLS + c * 32;
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (((valid >> j) & 1u) && u[j] >= myT) hm |= 1u << j;
+            }
+            if (hits) {
+              // positions inside the warp's sub-segment: a prefix sum
+              const int nh = __popc(hm);
+              int incl = nh;
+#pragma unroll
+              for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+              }
+              int pos = nhits + incl - nh;
+              nhits += __shfl_sync(0xffffffffu, incl, 31);
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
-                if (((valid >> j) & 1u) && u[j] >= myT) {
+                if ((hm >> j) & 1u) {
+                  if (pos < esub) hits[pos] = make_int4(myq, cb + j, __float_as_int(-2.0f * u[j]), 0);
+                  ++pos;
+                }
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                if ((hm >> j) & 1u) {
                   const int pos = atomicAdd(cc, 1);
                   if (pos < cap) {
                     cs[pos] = -2.0f * u[j];
@@ -400,6 +434,10 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
           }
         }
       }
+    }
+    if (hits && lane == 0) {
+      p.out.arena_cnt[blockIdx.x * ARENA_SUBSEG + ew] = nhits < esub ? nhits : esub;
+      if (nhits > esub) atomicOr(p.out.arena_ovf, 1);
     }
   }
 

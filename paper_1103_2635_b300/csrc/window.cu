@@ -481,6 +481,24 @@ __global__ void dense_emit_items_kernel(const int* __restrict__ n_dev, int64_t x
   }
 }
 
+// Hit arena -> per-query candidate buffers: one thread per record.
+__global__ void scatter_hits_kernel(const int4* __restrict__ arena, int arena_seg,
+                                    const int* __restrict__ arena_cnt,
+                                    float* __restrict__ cand_score, int* __restrict__ cand_row,
+                                    int* __restrict__ cand_cnt, int cap) {
+  const int seg = blockIdx.x;  // one sub-segment of arena_seg records
+  const int n = arena_cnt[seg];
+  const int4* a = arena + (int64_t)seg * arena_seg;
+  for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x) {
+    const int4 h = a[i];
+    const int pos = atomicAdd(&cand_cnt[h.x], 1);
+    if (pos < cap) {
+      cand_score[(int64_t)h.x * cap + pos] = __int_as_float(h.z);
+      cand_row[(int64_t)h.x * cap + pos] = h.y;
+    }
+  }
+}
+
 // Score threshold of every query: no point within g(q) of q scores above it.
 __global__ void score_threshold_kernel(const float* __restrict__ g, const float* __restrict__ qnorm,
                                        const float* __restrict__ qerr,
@@ -602,6 +620,16 @@ int launch_dense_emit_items(const int* n_dev, int64_t x_rows, int xspan, int max
   dense_emit_items_kernel<<<64, 256, 0, st>>>(n_dev, x_rows, xspan, nsplit, max_items, items,
                                               num_items);
   RBC_LAUNCH_CHECK("dense_emit_items_kernel");
+  return RBC_OK;
+}
+
+int launch_scatter_hits(const int4* arena, int arena_seg, const int* arena_cnt, int nseg,
+                        float* cand_score, int* cand_row, int* cand_cnt, int cap,
+                        cudaStream_t st) {
+  if (nseg <= 0) return RBC_OK;
+  scatter_hits_kernel<<<dim3(nseg, 4), 256, 0, st>>>(arena, arena_seg, arena_cnt, cand_score,
+                                                     cand_row, cand_cnt, cap);
+  RBC_LAUNCH_CHECK("scatter_hits_kernel");
   return RBC_OK;
 }
 
