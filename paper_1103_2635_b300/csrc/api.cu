@@ -1255,17 +1255,14 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   // pair arrays sized by the bound mb x n_r (batches are cut so that it stays
   // within WINDOW_MAX_PAIRS), so no count needs to come back to the host
   const int64_t pair_cap = mb * n_r;
-  // score thresholds first: every pair carries its query's
+  // score thresholds of the queries
   float* thr;
   RBC_TRY(ar.alloc(&thr, mb));
   RBC_TRY(launch_score_threshold(g, ql.norm, ql.err, ix->lp_max, d, mb, thr, st));
-  int* pq;
-  float *pd, *pt;
-  RBC_TRY(ar.alloc(&pq, pair_cap));
-  RBC_TRY(ar.alloc(&pd, pair_cap));
-  RBC_TRY(ar.alloc(&pt, pair_cap));
+  int2* pairs;  // (query, rho(q, r) bits)
+  RBC_TRY(ar.alloc(&pairs, pair_cap));
   RBC_TRY(launch_window_pairs_scatter(D, mb, n_r, g, g1, ix->psi, simt_eps(d), rmin, rmax, counts,
-                                      bin_off, thr, pq, pd, pt, st));
+                                      bin_off, pairs, st));
   // work items: chunks of TQ pairs, each with the union of its windows
   const int max_items = (int)std::min<int64_t>(pair_cap / TQ + n_r, INT32_MAX);
   int *ccount, *choff;
@@ -1273,7 +1270,7 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   RBC_TRY(ar.alloc(&ccount, n_r));
   RBC_TRY(ar.alloc(&choff, n_r + 1));
   RBC_TRY(ar.alloc(&items, std::max(max_items, 1)));
-  RBC_TRY(launch_window_items(bin_off, NB, n_r, pq, pd, g, ix->offsets, ix->xdist, simt_eps(d),
+  RBC_TRY(launch_window_items(bin_off, NB, n_r, pairs, g, ix->offsets, ix->xdist, simt_eps(d),
                               2.0f * rerank_eps_host(d) + 8.0f * U32, ccount, choff, max_items,
                               items, cn.sums + 1, st));
   *items_total += max_items;
@@ -1348,8 +1345,8 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
       eo_arena.arena_ovf = arena_ovf;
     }
     tmark(1, st);
-    RBC_TRY(launch_bf_tc_emit(Qm, Xm, items, choff + n_r, max_items, pq, pt, eo_arena, sms, st,
-                              dev_err));
+    RBC_TRY(launch_bf_tc_emit(Qm, Xm, items, choff + n_r, max_items,
+                              reinterpret_cast<const int*>(pairs), 2, eo_arena, sms, st, dev_err));
     if (!direct)
       RBC_TRY(launch_scatter_hits(arena, arena_sub, arena_cnt, sms * ARENA_SUBSEG, cs, cr, cc,
                                   CAND_CAP, st));
@@ -1365,8 +1362,7 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
     RBC_TRY(launch_overflow_rethreshold(fb_rows, lc, mb, cs, cc, CAND_CAP, k, ql.norm, ql.err,
                                         ix->lp_max, d, thr, st));
     RBC_TRY(launch_dense_emit_items(lc, n, xspan, max2, items2, n_items2, st));
-    RBC_TRY(launch_bf_tc_emit(Qm, Xm, items2, n_items2, max2, fb_rows, nullptr, eo, sms, st,
-                              dev_err));
+    RBC_TRY(launch_bf_tc_emit(Qm, Xm, items2, n_items2, max2, fb_rows, 1, eo, sms, st, dev_err));
     CandSelectArgs a2 = a;
     a2.rows = fb_rows;
     a2.nrows_dev = lc;

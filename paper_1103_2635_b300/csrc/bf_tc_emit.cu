@@ -63,7 +63,7 @@ struct EmitParams {
   const int* num_items_dev;
   int max_items;
   const int* pair_q;
-  const float* pair_t;  // threshold of each pair's query (nullptr: read out.thr)
+  int pair_stride;      // the query of pair i is pair_q[i * pair_stride]
   const uint8_t* qlp;  // [q_rows, dpad] 16-bit rows
   int64_t q_row_bytes;
   const float* xnorm;  // [rows + pad]
@@ -248,9 +248,10 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
 #pragma unroll
       for (int t = 0; t < BM / 32; ++t) {
         const int row = lane + 32 * t;
-        srcs[t] = row < e.nq ? p.pair_q[e.pair_begin + row] : -1;
-        thrs[t] = row < e.nq && p.pair_t ? p.pair_t[e.pair_begin + row] : -INFINITY;
+        srcs[t] = row < e.nq ? p.pair_q[(int64_t)(e.pair_begin + row) * p.pair_stride] : -1;
       }
+#pragma unroll
+      for (int t = 0; t < BM / 32; ++t) thrs[t] = srcs[t] >= 0 ? p.out.thr[srcs[t]] : 0.0f;
       if (!__all_sync(0xffffffffu, mbar_wait(&qempty[qs], qph ^ 1, sAbort, p.dev_err))) break;
       const uint32_t qbase = smem_u32(sQ + qs * L::Q_BYTES);
 #pragma unroll
@@ -258,7 +259,7 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
         const int row = lane + 32 * t;
         const int src = srcs[t];
         sRowQ[qs * BM + row] = src;
-        sRowT[qs * BM + row] = src < 0 ? INFINITY : -0.5f * (p.pair_t ? thrs[t] : p.out.thr[src]);
+        sRowT[qs * BM + row] = src < 0 ? INFINITY : -0.5f * thrs[t];
         const uint8_t* g = p.qlp + (int64_t)(src >= 0 ? src : 0) * p.q_row_bytes;
 #pragma unroll
         for (int kb = 0; kb < KB; ++kb)
@@ -452,7 +453,7 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
 
 template <int KB, int BN, int S, int QS>
 int launch_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
-                const int* num_items_dev, int max_items, const int* pair_q, const float* pair_t,
+                const int* num_items_dev, int max_items, const int* pair_q, int pair_stride,
                 const EmitOut& out, int grid, cudaStream_t st, uint32_t* dev_err) {
   using L = EmitSmem<KB, BN, S, QS>;
   CUtensorMap xmap, nbmap;
@@ -460,7 +461,7 @@ int launch_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
   RBC_TRY_TC(encode_nblock_map(&nbmap, Xm.nblock, Xm.rows, BN));
   auto kern = bf_tc_emit_kernel<KB, BN, S, QS>;
   RBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC));
-  EmitParams p{items,  num_items_dev, max_items, pair_q, pair_t,
+  EmitParams p{items,  num_items_dev, max_items, pair_q, pair_stride,
                static_cast<const uint8_t*>(Qm.data), (int64_t)Qm.dpad * 2, Xm.norm, out, dev_err};
   const uint32_t idesc = idesc_f16(Qm.storage == RBC_BF16 ? 1 : 0, BM, BN);
   const uint32_t idesc_norm = idesc_f16(1, BM, BN);  // the norm block is bf16 for any storage
@@ -482,7 +483,7 @@ int launch_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
 
 int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
                       const int* num_items_dev, int max_items, const int* pair_q,
-                      const float* pair_t, const EmitOut& out, int grid, cudaStream_t st,
+                      int pair_stride, const EmitOut& out, int grid, cudaStream_t st,
                       uint32_t* dev_err) {
   if (!tc_available()) {
     set_error("tensor-core BF kernel needs an sm_103 device");
@@ -498,10 +499,10 @@ int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* it
     return RBC_ERR_ARG;
   }
   switch (Qm.dpad / 64) {
-    case 1: return launch_emit<1, 256, 3, 4>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_t, out, grid, st, dev_err);
-    case 2: return launch_emit<2, 128, 3, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_t, out, grid, st, dev_err);
-    case 3: return launch_emit<3, 64, 3, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_t, out, grid, st, dev_err);
-    case 4: return launch_emit<4, 64, 2, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_t, out, grid, st, dev_err);
+    case 1: return launch_emit<1, 256, 3, 4>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_stride, out, grid, st, dev_err);
+    case 2: return launch_emit<2, 128, 3, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_stride, out, grid, st, dev_err);
+    case 3: return launch_emit<3, 64, 3, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_stride, out, grid, st, dev_err);
+    case 4: return launch_emit<4, 64, 2, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_stride, out, grid, st, dev_err);
     default: break;
   }
   set_error("tensor-core BF: padded dimension %d unsupported", Qm.dpad);

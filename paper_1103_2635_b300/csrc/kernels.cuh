@@ -90,11 +90,10 @@ constexpr int ARENA_SUBSEG = 16;  // arena parts per CTA (at least its epilogue 
 int launch_scatter_hits(const int4* arena, int arena_seg, const int* arena_cnt, int nseg,
                         float* cand_score, int* cand_row, int* cand_cnt, int cap,
                         cudaStream_t st);
-// pair_t (optional): the threshold of each pair's query, read alongside
-// pair_q instead of through out.thr
+// the query of an item's row i is pair_q[(pair_begin + i) * pair_stride]
 int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
                       const int* num_items_dev, int max_items, const int* pair_q,
-                      const float* pair_t, const EmitOut& out, int grid, cudaStream_t st,
+                      int pair_stride, const EmitOut& out, int grid, cudaStream_t st,
                       uint32_t* dev_err);
 
 // ---- merge + re-rank + certification ----
@@ -179,7 +178,7 @@ int launch_own_kth_lp(const float* ps, const int* pi, int C, const int* qsrc, in
 // extreme window starts), q_kept [m], counts
 // [window_pair_blocks(m)][n_r nb] (per query block, then its prefix within
 // each bin), totals [n_r nb], bin_off [n_r nb + 1]; then the pairs
-// themselves (pair_q, pair_d, and pair_t = thr of the pair's query).
+// themselves: pairs[i] = (query, rho(q, r) as float bits).
 int window_buckets();
 int64_t window_pair_blocks(int64_t m);
 int launch_window_pairs_count(const float* D, int64_t m, int n_r, const float* g,
@@ -189,12 +188,11 @@ int launch_window_pairs_count(const float* D, int64_t m, int n_r, const float* g
 int launch_window_pairs_scatter(const float* D, int64_t m, int n_r, const float* g,
                                 const float* g1, const float* psi_plus, float rel,
                                 const unsigned* rmin, const unsigned* rmax, int* counts,
-                                const int* bin_off, const float* thr, int* pair_q,
-                                float* pair_d, float* pair_t, cudaStream_t st);
+                                const int* bin_off, int2* pairs, cudaStream_t st);
 // chunks of TQ pairs per representative -> items (the chunk's window in the
 // sorted list); stats[0] += window rows, stats[1] += query x row pairs
-int launch_window_items(const int* bin_off, int nb, int n_r, const int* pair_q,
-                        const float* pair_d, const float* g, const int* offsets,
+int launch_window_items(const int* bin_off, int nb, int n_r, const int2* pairs,
+                        const float* g, const int* offsets,
                         const float* xdist, float rel, float relx, int* chunk_counts,
                         int* chunk_off, int max_items, EmitItem* items,
                         unsigned long long* stats, cudaStream_t st);

@@ -254,8 +254,7 @@ wbin_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __rest
             const float* __restrict__ g1, const float* __restrict__ psi_plus, float rel,
             const unsigned* __restrict__ rmin, const unsigned* __restrict__ rmax,
             int* __restrict__ counts, const int* __restrict__ bin_off,
-            const float* __restrict__ thr, int* __restrict__ pair_q, float* __restrict__ pair_d,
-            float* __restrict__ pair_t) {
+            int2* __restrict__ pairs) {
   __shared__ float tiles[WW][WT][WT + 1];
   __shared__ int h[RSPAN * NBK];
   __shared__ float sblo[RSPAN], sscale[RSPAN];
@@ -277,7 +276,6 @@ wbin_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __rest
   const int64_t q0 = ((int64_t)blockIdx.x * WW + wid) * WT;
   if (q0 < m) {
     const PairCtx c = pair_ctx(q0, lane, m, g, g1, rel);
-    const float my_thr = SCATTER && c.live ? thr[c.q] : 0.0f;
     for (int r0 = rb; r0 < re; r0 += WT) {
       load_tile(D, m, n_r, q0, r0, tiles[wid], lane);
       const int nr = min(WT, re - r0);
@@ -287,11 +285,7 @@ wbin_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __rest
         if (c.live && keep_pair(v, c.lo, c.gh, psi_plus[r0 + rr], c.lemma)) {
           const int slot = rl * NBK + bucket_of(window_key(v, c.gh), sblo[rl], sscale[rl]);
           const int pos = atomicAdd(&h[slot], 1);
-          if (SCATTER) {
-            pair_q[pos] = (int)c.q;
-            pair_d[pos] = v;
-            pair_t[pos] = my_thr;
-          }
+          if (SCATTER) pairs[pos] = make_int2((int)c.q, __float_as_int(v));
         }
       }
       __syncwarp();
@@ -362,7 +356,7 @@ __device__ __forceinline__ int warp_bound(const float* __restrict__ a, int n, fl
 // block and added once per block.
 __global__ void __launch_bounds__(256)
 window_items_kernel(const int* __restrict__ chunk_off, int n_r, const int* __restrict__ bin_off,
-                    int nb, const int* __restrict__ pair_q, const float* __restrict__ pair_d,
+                    int nb, const int2* __restrict__ pairs,
                     const float* __restrict__ g, const int* __restrict__ offsets,
                     const float* __restrict__ xdist, float rel, float relx, int max_items,
                     EmitItem* __restrict__ items, unsigned long long* __restrict__ stats) {
@@ -385,8 +379,9 @@ window_items_kernel(const int* __restrict__ chunk_off, int n_r, const int* __res
     const int end = min(begin + TQ, bin_off[(r + 1) * nb]);
     float wlo = INFINITY, whi = -INFINITY;
     for (int i = begin + lane; i < end; i += 32) {
-      const float d = pair_d[i];
-      const float gq = g[pair_q[i]];
+      const int2 pr = pairs[i];
+      const float d = __int_as_float(pr.y);
+      const float gq = g[pr.x];
       wlo = fminf(wlo, (d * dlo - gq * SLACK) * xlo);
       whi = fmaxf(whi, (d * dup + gq) * xup);
     }
@@ -546,8 +541,7 @@ int launch_window_pairs_count(const float* D, int64_t m, int n_r, const float* g
     wrange_kernel<<<grid, WW * 32, 0, st>>>(D, m, n_r, g, g1, psi_plus, rel, rmin, rmax, q_kept);
     RBC_LAUNCH_CHECK("wrange_kernel");
     wbin_kernel<false><<<grid, WW * 32, 0, st>>>(D, m, n_r, g, g1, psi_plus, rel, rmin, rmax,
-                                                 counts, nullptr, nullptr, nullptr, nullptr,
-                                                 nullptr);
+                                                 counts, nullptr, nullptr);
     RBC_LAUNCH_CHECK("wbin_kernel");
     bin_colscan_kernel<<<(unsigned)((nbins * 32 + 255) / 256), 256, 0, st>>>(
         counts, (int)qblocks, nbins, totals);
@@ -561,21 +555,20 @@ int launch_window_pairs_count(const float* D, int64_t m, int n_r, const float* g
 int launch_window_pairs_scatter(const float* D, int64_t m, int n_r, const float* g,
                                 const float* g1, const float* psi_plus, float rel,
                                 const unsigned* rmin, const unsigned* rmax, int* counts,
-                                const int* bin_off, const float* thr, int* pair_q,
-                                float* pair_d, float* pair_t, cudaStream_t st) {
+                                const int* bin_off, int2* pairs, cudaStream_t st) {
   const int64_t qblocks = window_pair_blocks(m);
   if (qblocks == 0) return RBC_OK;
   const dim3 grid((unsigned)qblocks, (n_r + RSPAN - 1) / RSPAN);
   wbin_kernel<true><<<grid, WW * 32, 0, st>>>(D, m, n_r, g, g1, psi_plus, rel, rmin, rmax, counts,
-                                              bin_off, thr, pair_q, pair_d, pair_t);
+                                              bin_off, pairs);
   RBC_LAUNCH_CHECK("wbin_kernel");
   return RBC_OK;
 }
 
 int window_buckets() { return NBK; }
 
-int launch_window_items(const int* bin_off, int nb, int n_r, const int* pair_q,
-                        const float* pair_d, const float* g, const int* offsets,
+int launch_window_items(const int* bin_off, int nb, int n_r, const int2* pairs,
+                        const float* g, const int* offsets,
                         const float* xdist, float rel, float relx, int* chunk_counts,
                         int* chunk_off, int max_items, EmitItem* items,
                         unsigned long long* stats, cudaStream_t st) {
@@ -586,8 +579,8 @@ int launch_window_items(const int* bin_off, int nb, int n_r, const int* pair_q,
   if (max_items <= 0) return RBC_OK;
   const int64_t want = ((int64_t)max_items * 32 + 255) / 256;
   window_items_kernel<<<(unsigned)std::min<int64_t>(want, 148 * 16), 256, 0, st>>>(
-      chunk_off, n_r, bin_off, nb, pair_q, pair_d, g, offsets, xdist, rel, relx, max_items,
-      items, stats);
+      chunk_off, n_r, bin_off, nb, pairs, g, offsets, xdist, rel, relx, max_items, items,
+      stats);
   RBC_LAUNCH_CHECK("window_items_kernel");
   return RBC_OK;
 }
