@@ -38,6 +38,10 @@ import synth  # noqa: E402
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 METRIC = "exact k-NN queries/s (RBC BF16+rerank vs FP32 brute force), p50/p99 latency"
 FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
+# DRAM bytes (read + write) of one main-pass launch of the emission kernel on
+# the default workload, from ncu (profiles/bf_tc_emit_kernel_subspace8-n512k-m50k.md);
+# re-measured whenever the kernel changes.
+EMIT_TRAFFIC_BYTES = 723.7e6 + 77.5e6
 
 
 def parse():
@@ -322,7 +326,10 @@ def run_ours(args, rank, world, local):
     dense_tflops = m * len(X) * flops_per_pair / (bst["stage2_ms"] / 1000.0) / 1e12 if bst["stage2_ms"] else None
     roofline = {
         "bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
-        "frac": (tflops / peak) if tflops else None, "traffic": None,
+        "frac": (tflops / peak) if tflops else None,
+        "traffic": EMIT_TRAFFIC_BYTES if (args.workload == "subspace8-n1m-d64" and args.n is None
+                                          and args.m is None and args.storage == "bf16"
+                                          and args.plan == "window" and k == 10) else None,
         "kernel": "bf_tc_emit_kernel (stage two: query chunks x sorted-list windows)",
         "peak_source": f"{peak_src} bf16 sustained (cuBLAS), of {peak_src}",
         "flops_per_launch": pairs * flops_per_pair, "launch_ms": ph["stage2_ms"],
