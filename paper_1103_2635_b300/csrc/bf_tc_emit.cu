@@ -16,8 +16,9 @@
 // bf16 high and low part, 16 columns), and one extra bf16 MMA of an all-ones
 // A operand against it adds -|x~|^2 / 2 to every accumulator, which then
 // holds q~.x~ - |x~|^2 / 2 = -s / 2.  So the epilogue keeps no lists, loads
-// no norms and does no arithmetic per score: per 32-column chunk it takes
-// the maximum of the raw accumulators, and only when that reaches -T(q) / 2
+// no norms and does no arithmetic per score: per 32-column chunk the TMEM load
+// itself returns the maximum of the raw accumulators (tcgen05.ld.red), and
+// only when that reaches -T(q) / 2
 // appends the qualifying (score, row) pairs to q's candidate buffer in
 // global memory.  The candidates are re-ranked exactly afterwards
 // (select.cu).
@@ -371,8 +372,9 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
         tc_fence_after();
         const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + buf * BN + part * COLS;
         uint32_t raw[CH][32];
+        float cmax[CH];  // per chunk: the largest accumulator, from the load itself
 #pragma unroll
-        for (int c = 0; c < CH; ++c) tmem_ld_x32(tbase + c * 32, raw[c]);
+        for (int c = 0; c < CH; ++c) tmem_ld_x32_max(tbase + c * 32, raw[c], cmax[c]);
         tmem_wait_ld();
         // every column of this slice is in registers: hand the accumulator back
         tc_fence_before();
@@ -382,13 +384,14 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
         const int hi = e.x_end - x - part * COLS;    // one past the last valid column
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
+          if (!(c * 32 < hi && c * 32 + 32 > lo)) continue;  // no window column in the chunk
           float u[32];  // -s / 2 per column
 #pragma unroll
           for (int j = 0; j < 32; ++j) u[j] = __uint_as_float(raw[c][j]);
           // The maximum runs over all 32 columns, including any outside the
           // window (real rows, or zero rows past the matrix end): a false
           // alarm only costs the slow path, where the in-window mask decides.
-          const bool hit = max_of32(u) >= myT;
+          const bool hit = cmax[c] >= myT;
           if (__any_sync(0xffffffffu, hit)) {  // warp-uniform: the rare path
             const int cb = x + part * COLS + c * 32;
             uint32_t hm = 0;  // this row's emitted columns of the chunk
