@@ -1282,19 +1282,20 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   RBC_TRY(ar.alloc(&cc, mb));
   LpMatrix Qm{ql.lp, ql.norm, mb, ix->dpad, ix->storage};
   LpMatrix Xm{ix->Xlp, ix->xnorm, n, ix->dpad, ix->storage, ix->xnblock};
-  // hit arena: each CTA appends its emissions to its own segment (a shared
-  // counter, no global atomics in the kernel); a post-pass fills the
-  // per-query buffers.  The segments hold 4x the hits of this workload; if
-  // one overflows, the batch is emitted again with direct per-query appends.
-  const int arena_sub = (int)std::min<int64_t>(
-      INT32_MAX / (4 * ARENA_SUBSEG),
-      std::max<int64_t>(512, (mb * 128 + sms * ARENA_SUBSEG - 1) / (sms * ARENA_SUBSEG)));
-  const int arena_seg = arena_sub * ARENA_SUBSEG;  // per CTA
+  // hit arena: each epilogue thread appends its emissions to its own slice
+  // (no atomics in the kernel); a post-pass fills the per-query buffers.  The
+  // slices together hold 256 records per query of the batch (about 5x the
+  // candidates of clustered 64-d data); if one overflows, the batch is
+  // emitted again with direct per-query appends.
+  const int64_t nslices = (int64_t)sms * ARENA_SUBSEG * 32;
+  const int arena_lane = (int)std::min<int64_t>(
+      INT32_MAX / (4 * ARENA_SUBSEG * 32), std::max<int64_t>(64, (mb * 256 + nslices - 1) / nslices));
+  const int arena_seg = arena_lane * 32 * ARENA_SUBSEG;  // per CTA
   int4* arena;
   int *arena_cnt, *arena_ovf;
   RBC_TRY(ar.alloc(&arena, (int64_t)sms * arena_seg));
-  RBC_TRY(ar.alloc(&arena_cnt, sms * ARENA_SUBSEG));
-  RBC_CUDA(cudaMemsetAsync(arena_cnt, 0, sms * ARENA_SUBSEG * sizeof(int), st));
+  RBC_TRY(ar.alloc(&arena_cnt, nslices));
+  RBC_CUDA(cudaMemsetAsync(arena_cnt, 0, nslices * sizeof(int), st));
   RBC_TRY(ar.alloc(&arena_ovf, 1));
   int* fb_rows;
   int *lc, *lc2, *fb2;
@@ -1348,7 +1349,7 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
     RBC_TRY(launch_bf_tc_emit(Qm, Xm, items, choff + n_r, max_items,
                               reinterpret_cast<const int*>(pairs), 2, eo_arena, sms, st, dev_err));
     if (!direct)
-      RBC_TRY(launch_scatter_hits(arena, arena_sub, arena_cnt, sms * ARENA_SUBSEG, cs, cr, cc,
+      RBC_TRY(launch_scatter_hits(arena, arena_lane, arena_cnt, (int)nslices, cs, cr, cc,
                                   CAND_CAP, st));
     tmark(2, st);
     // exact re-rank of the candidates; overflowing queries are collected

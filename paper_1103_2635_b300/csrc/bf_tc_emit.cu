@@ -340,13 +340,14 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
     uint32_t it = 0, qi = 0;
     bool ok = true;
     const int cap = p.out.cap;
-    // hit arena: this warp's private sub-segment and its fill count (kept
-    // identical in every lane, so no atomics are needed)
+    // hit arena: this thread's private slice (segment of its warp, split by
+    // lane) and its own fill count: no atomics, no cross-lane traffic
     const int esub = p.out.arena_seg / ARENA_SUBSEG;
+    const int lsub = esub / 32;
     const int ew = warp - E_EPI0;
-    int4* hits = p.out.arena
-                     ? p.out.arena + (int64_t)blockIdx.x * p.out.arena_seg + (int64_t)ew * esub
-                     : nullptr;
+    int4* hits = p.out.arena ? p.out.arena + (int64_t)blockIdx.x * p.out.arena_seg +
+                                   (int64_t)ew * esub + (int64_t)lane * lsub
+                             : nullptr;
     int nhits = 0;
     for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
       const EmitItem e = p.items[item];
@@ -392,40 +393,25 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
           // window (real rows, or zero rows past the matrix end): a false
           // alarm only costs the slow path, where the in-window mask decides.
           const bool hit = cmax[c] >= myT;
-          if (__any_sync(0xffffffffu, hit)) {  // warp-uniform: the rare path
+          if (hit) {  // the rare path: this row has columns at or over its threshold
             const int cb = x + part * COLS + c * 32;
-            uint32_t hm = 0;  // this row's emitted columns of the chunk
-            if (hit) {
-              const int clo = lo - c * 32, chi = hi - c * 32;
-              const uint32_t below_hi = chi >= 32 ? 0xffffffffu : (chi <= 0 ? 0u : (1u << chi) - 1u);
-              const uint32_t below_lo = clo >= 32 ? 0xffffffffu : (clo <= 0 ? 0u : (1u << clo) - 1u);
-              const uint32_t valid = below_hi & ~below_lo;
-#pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (((valid >> j) & 1u) && u[j] >= myT) hm |= 1u << j;
-            }
+            const int clo = lo - c * 32, chi = hi - c * 32;
+            const uint32_t below_hi = chi >= 32 ? 0xffffffffu : (chi <= 0 ? 0u : (1u << chi) - 1u);
+            const uint32_t below_lo = clo >= 32 ? 0xffffffffu : (clo <= 0 ? 0u : (1u << clo) - 1u);
+            const uint32_t valid = below_hi & ~below_lo;
             if (hits) {
-              // positions inside the warp's sub-segment: a prefix sum
-              const int nh = __popc(hm);
-              int incl = nh;
-#pragma unroll
-              for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-              }
-              int pos = nhits + incl - nh;
-              nhits += __shfl_sync(0xffffffffu, incl, 31);
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
-                if ((hm >> j) & 1u) {
-                  if (pos < esub) hits[pos] = make_int4(myq, cb + j, __float_as_int(-2.0f * u[j]), 0);
-                  ++pos;
+                if (((valid >> j) & 1u) && u[j] >= myT) {
+                  if (nhits < lsub)
+                    hits[nhits] = make_int4(myq, cb + j, __float_as_int(-2.0f * u[j]), 0);
+                  ++nhits;
                 }
               }
             } else {
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
-                if ((hm >> j) & 1u) {
+                if (((valid >> j) & 1u) && u[j] >= myT) {
                   const int pos = atomicAdd(cc, 1);
                   if (pos < cap) {
                     cs[pos] = -2.0f * u[j];
@@ -434,14 +420,13 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
                 }
               }
             }
-            __syncwarp();
           }
         }
       }
     }
-    if (hits && lane == 0) {
-      p.out.arena_cnt[blockIdx.x * ARENA_SUBSEG + ew] = nhits < esub ? nhits : esub;
-      if (nhits > esub) atomicOr(p.out.arena_ovf, 1);
+    if (hits) {
+      p.out.arena_cnt[(blockIdx.x * ARENA_SUBSEG + ew) * 32 + lane] = nhits < lsub ? nhits : lsub;
+      if (nhits > lsub) atomicOr(p.out.arena_ovf, 1);
     }
   }
 

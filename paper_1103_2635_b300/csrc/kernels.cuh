@@ -73,20 +73,20 @@ struct EmitOut {
   int* cand_cnt;     // [m]
   int cap;
   // Optional hit arena: CTA b owns arena[b * arena_seg, +arena_seg), split
-  // into ARENA_SUBSEG equal parts, one per epilogue warp; a warp appends
-  // (query, row, score bits, 0) records to its part with a count kept in a
-  // register (no atomics), writes the count to arena_cnt[b * ARENA_SUBSEG +
-  // warp] and sets *arena_ovf if its part overflowed; launch_scatter_hits
-  // then fills the per-query buffers.  arena == nullptr: append to them
-  // directly.
+  // into ARENA_SUBSEG equal parts, one per epilogue warp, and each of those
+  // into 32 lane slices; a thread appends (query, row, score bits, 0) records
+  // to its slice with a count kept in a register (no atomics), writes the
+  // count to arena_cnt[(b * ARENA_SUBSEG + warp) * 32 + lane] and sets
+  // *arena_ovf if its slice overflowed; launch_scatter_hits then fills the
+  // per-query buffers.  arena == nullptr: append to them directly.
   int4* arena = nullptr;
   int arena_seg = 0;
   int* arena_cnt = nullptr;
   int* arena_ovf = nullptr;
 };
 constexpr int ARENA_SUBSEG = 16;  // arena parts per CTA (at least its epilogue warps)
-// per-query buffers from the hit arena of an emission pass with `nseg`
-// sub-segments of arena_seg / ARENA_SUBSEG records each
+// per-query buffers from the hit arena of an emission pass: `nseg` slices of
+// arena_seg records each, counts in arena_cnt[slice]
 int launch_scatter_hits(const int4* arena, int arena_seg, const int* arena_cnt, int nseg,
                         float* cand_score, int* cand_row, int* cand_cnt, int cap,
                         cudaStream_t st);

@@ -476,15 +476,17 @@ __global__ void dense_emit_items_kernel(const int* __restrict__ n_dev, int64_t x
   }
 }
 
-// Hit arena -> per-query candidate buffers: one thread per record.
+// Hit arena -> per-query candidate buffers.
 __global__ void scatter_hits_kernel(const int4* __restrict__ arena, int arena_seg,
-                                    const int* __restrict__ arena_cnt,
+                                    const int* __restrict__ arena_cnt, int64_t nseg,
                                     float* __restrict__ cand_score, int* __restrict__ cand_row,
                                     int* __restrict__ cand_cnt, int cap) {
-  const int seg = blockIdx.x;  // one sub-segment of arena_seg records
+  // one thread per slice, looping over its records
+  const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (seg >= nseg) return;
   const int n = arena_cnt[seg];
-  const int4* a = arena + (int64_t)seg * arena_seg;
-  for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < n; i += gridDim.y * blockDim.x) {
+  const int4* a = arena + seg * arena_seg;
+  for (int i = 0; i < n; ++i) {
     const int4 h = a[i];
     const int pos = atomicAdd(&cand_cnt[h.x], 1);
     if (pos < cap) {
@@ -620,8 +622,8 @@ int launch_scatter_hits(const int4* arena, int arena_seg, const int* arena_cnt, 
                         float* cand_score, int* cand_row, int* cand_cnt, int cap,
                         cudaStream_t st) {
   if (nseg <= 0) return RBC_OK;
-  scatter_hits_kernel<<<dim3(nseg, 4), 256, 0, st>>>(arena, arena_seg, arena_cnt, cand_score,
-                                                     cand_row, cand_cnt, cap);
+  scatter_hits_kernel<<<(unsigned)((nseg + 255) / 256), 256, 0, st>>>(
+      arena, arena_seg, arena_cnt, nseg, cand_score, cand_row, cand_cnt, cap);
   RBC_LAUNCH_CHECK("scatter_hits_kernel");
   return RBC_OK;
 }
