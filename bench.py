@@ -16,6 +16,18 @@ cpu_baseline = the FP64 CPU oracle on a bounded query sample; the FP32
 CUDA-core brute force over the same queries for comparison.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Serving mode (--serve): a resident index over the 12-dim sin/cos embedding
+workload (n = 8,388,608 points in R^96, fp16 storage, n_r = 2896, k = 10)
+behind the library's continuous-batching engine (rbc_server_*).  First the
+engine's capacity is measured with a closed loop (64 requests outstanding),
+then a Poisson stream of requests of log-uniform size in [1, 4096] queries
+is offered at --serve-load (0.7) of that capacity for --serve-seconds (60).
+The line reports the served queries/s and the p50 / p99 request latency
+(submit to results in pinned host buffers), and checks sampled results
+against the FP64 oracle and against the same requests searched alone.
+
+    python bench.py --serve [--serve-seconds S] [--serve-load L]
 """
 from __future__ import annotations
 
@@ -62,6 +74,14 @@ def parse():
                     help="search: only the timed exact-search steps (for profiler launch lists)")
     ap.add_argument("--n", type=int, default=None, help="override the database size")
     ap.add_argument("--m", type=int, default=None, help="override the query batch size")
+    ap.add_argument("--serve", action="store_true", help="serving measurement instead of batch search")
+    ap.add_argument("--serve-workload", default="sincos12-n8m-d96")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-capacity-seconds", type=float, default=8.0)
+    ap.add_argument("--serve-load", type=float, default=0.7)
+    ap.add_argument("--serve-workers", type=int, default=3)
+    ap.add_argument("--serve-max-batch", type=int, default=16384)
+    ap.add_argument("--serve-check", type=int, default=24, help="rows checked against the oracle")
     return ap.parse_args()
 
 
@@ -396,9 +416,170 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# serving: continuous batching under a Poisson request stream
+# ---------------------------------------------------------------------------
+def run_serve(args, rank, world, local):
+    if rank != 0:
+        return
+    import threading
+
+    import torch
+
+    import paper_1103_2635_b300 as rbc
+
+    torch.cuda.set_device(local)
+    k = args.k
+    w = synth.WORKLOADS[args.serve_workload]
+    pool_m = 1 << 18
+    X, Qpool = synth.make_workload(w, seed=0, n=args.n, m=pool_m)
+    n = len(X)
+    t0 = time.perf_counter()
+    idx = rbc.rbc_build(torch.from_numpy(X).cuda(), w.n_r, seed=2, storage=rbc.F16)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    Qpin = torch.from_numpy(Qpool).pin_memory()
+    ring = 1 << 22
+    ids_ring = torch.empty((ring, k), dtype=torch.int64).pin_memory()
+    dist_ring = torch.empty((ring, k), dtype=torch.float32).pin_memory()
+    rng = np.random.default_rng(11)
+
+    def draw_size():
+        return int(min(4096, max(1, np.exp(rng.uniform(0.0, np.log(4097.0))))))
+
+    mean_size = 4096 / np.log(4097.0)  # E[exp(U(0, ln 4097))] - 1/2 flooring, about 492
+    srv = rbc.Server(idx, workers=args.serve_workers, max_batch=args.serve_max_batch, k_max=k)
+    state = {"off": 0}
+    pending = []
+    lock = threading.Condition()
+    kept = []  # (qstart, m, ticket-result slice) of a few requests for checks
+
+    def submit(m):
+        s = int(rng.integers(0, pool_m - m + 1))
+        off = state["off"]
+        if off + m > ring:
+            off = 0
+        state["off"] = off + m
+        t = srv.submit(Qpin[s : s + m], k, ids_ring[off : off + m], dist_ring[off : off + m])
+        return t, s, off, m
+
+    def collector(stop):
+        while True:
+            with lock:
+                while not pending and not stop["v"]:
+                    lock.wait()
+                if not pending and stop["v"]:
+                    return
+                t, s, off, m = pending.pop(0)
+            ids, dist, info = srv.wait(t)
+            if len(kept) < 64 and info["batch_requests"] > 1:
+                kept.append((s, m, ids.numpy().copy(), dist.numpy().copy()))
+
+    def run_phase(seconds, rate=None, depth=64):
+        stop = {"v": False}
+        th = threading.Thread(target=collector, args=(stop,))
+        th.start()
+        srv.stats(reset=True)
+        t_start = time.perf_counter()
+        submitted = q_sub = 0
+        next_t = t_start
+        while True:
+            now = time.perf_counter()
+            if now - t_start >= seconds:
+                break
+            if rate is None:  # closed loop: keep `depth` requests outstanding
+                with lock:
+                    backlog = len(pending)
+                if backlog >= depth:
+                    time.sleep(0.0002)
+                    continue
+            else:
+                if now < next_t:
+                    dt = next_t - now
+                    if dt > 0.001:
+                        time.sleep(dt - 0.0005)
+                    continue
+                next_t += rng.exponential(1.0 / rate)
+            m = draw_size()
+            item = submit(m)
+            with lock:
+                pending.append(item)
+                lock.notify()
+            submitted += 1
+            q_sub += m
+        offered_s = time.perf_counter() - t_start
+        with lock:
+            stop["v"] = True
+            lock.notify()
+        th.join()
+        st = srv.stats(reset=False)
+        return st, submitted, q_sub, offered_s
+
+    # warm-up, then capacity (closed loop), then the Poisson stream
+    run_phase(2.0)
+    cap, _, _, _ = run_phase(args.serve_capacity_seconds)
+    capacity = cap["queries_per_s"]
+    rate = args.serve_load * capacity / mean_size  # requests per second
+    dev = torch.cuda.current_device()
+    with ClockSampler(dev) as clk:
+        st, submitted, q_sub, offered_s = run_phase(args.serve_seconds, rate=rate)
+    clocks = clk.summary()
+    srv.close()
+
+    # checks: sampled rows against the FP64 oracle; merged requests against
+    # the same queries searched alone
+    import oracle
+
+    bad_alone = 0
+    for s, m, ids, dist in kept[:16]:
+        ia, da = rbc.rbc_search(idx, Qpin[s : s + m].cuda(), k)
+        torch.cuda.synchronize()
+        ia, da = ia.cpu().numpy(), da.cpu().numpy()
+        same = np.array_equal(ids, ia) and np.allclose(dist, da, rtol=1e-5, atol=0)
+        bad_alone += 0 if same else 1
+    rows, got_i, got_d = [], [], []
+    for s, m, ids, dist in kept:
+        if len(rows) >= args.serve_check:
+            break
+        j = m // 2
+        rows.append(s + j)
+        got_i.append(ids[j])
+        got_d.append(dist[j])
+    parity = {"checked_rows": len(rows), "alone_vs_mix_requests": min(16, len(kept)),
+              "alone_vs_mix_mismatch": bad_alone}
+    if rows:
+        o_ids, o_rho = oracle.bf(Qpool[rows], X, k)
+        gi, gd = np.array(got_i), np.array(got_d, dtype=np.float64)
+        parity["ids_equal_rows"] = int(np.sum(np.all(gi == o_ids, axis=1)))
+        parity["max_rel_dist_err"] = float(np.max(np.abs(gd - o_rho) / np.maximum(o_rho, 1e-30)))
+    line = {
+        "metric": "serving: queries/s with p50/p99 request latency under a Poisson stream of "
+                  "1-4096-query requests (exact k-NN, RBC fp16 + rerank)",
+        "value": st["queries_per_s"], "unit": "queries/s", "higher_is_better": True,
+        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
+        "queue_p50_ms": st["queue_p50_ms"], "queue_p99_ms": st["queue_p99_ms"],
+        "capacity_qps": capacity, "capacity_p50_ms": cap["p50_ms"], "capacity_p99_ms": cap["p99_ms"],
+        "offered_qps": q_sub / offered_s, "load": args.serve_load,
+        "requests": st["requests"], "queries": st["queries"], "batches": st["batches"],
+        "mean_batch_queries": st["mean_batch_queries"], "max_in_flight": st["max_in_flight"],
+        "peak_reserved_bytes": st["peak_reserved_bytes"], "hbm_budget": st["hbm_budget"],
+        "n_gpus": 1, "dtype": "f16", "data": "synthetic", "clocks": clocks, "parity": parity,
+        "config": {"workload": args.serve_workload, "n": n, "d": w.d, "n_r": w.n_r, "k": k,
+                   "storage": "f16", "workers": args.serve_workers,
+                   "max_batch": args.serve_max_batch, "seconds": args.serve_seconds,
+                   "request_sizes": "log-uniform [1, 4096]", "arrivals": "Poisson",
+                   "build_s": build_s, "host_buffers": "pinned"},
+    }
+    print(json.dumps(line), flush=True)
+    idx.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.serve:
+        run_serve(args, rank, world, local)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

@@ -165,6 +165,22 @@ int rbc_search(const rbc_index* idx, const float* Q, int64_t m, int32_t k, int64
                float* out_dist, void* stream);
 
 /*
+ * rbc_search_workspace -- upper bound of the device workspace (bytes
+ *   requested from the library's workspace pool) that one rbc_search(idx, Q,
+ *   m, k, ...) call holds at any time: the sum of every request the search may
+ *   make, with each data-dependent size at its maximum (every candidate list
+ *   at full width, every query falling back to the FP32 re-search) and host
+ *   I/O copies included.  A call over more queries than one internal batch
+ *   (131,072, or 2^28 / n_r for the windowed plan) holds one batch's
+ *   workspace at a time, so the bound stops growing there except for the
+ *   I/O copies.  Host only; no device work.  rbc_last_stats reports the
+ *   measured peak of a call (workspace_bytes).  Used for admission by memory
+ *   in the serving engine (rbc_server_*).  No counterpart in the paper.
+ *   Errors: RBC_ERR_ARG on NULL idx / bytes, m < 0 or k < 1.
+ */
+int rbc_search_workspace(const rbc_index* idx, int64_t m, int32_t k, int64_t* bytes);
+
+/*
  * bf_search -- the brute-force primitive BF(Q, X) (Section 3): all m x n
  *   distances fused with a per-query top-k; no distance matrix is stored.
  *   storage RBC_F32: FP32 CUDA-core kernel.  RBC_BF16 / RBC_F16 with RBC_L2:
@@ -212,6 +228,7 @@ typedef struct {
   int32_t storage;
   int64_t list_entries;  /* total entries over all lists (n in exact mode) */
   int64_t device_bytes;  /* device memory held by the index */
+  int32_t device;        /* CUDA device the index was built on */
 } rbc_index_desc;
 
 /* rbc_index_info -- fills *out.  Errors: RBC_ERR_ARG on NULL. */
@@ -255,6 +272,8 @@ typedef struct {
   double fallback_ms;        /*   FP32 re-search of uncertified queries */
   int64_t candidates;        /* windowed search: points emitted by the tensor-core
                                 pass for the exact re-rank (summed over queries) */
+  int64_t workspace_bytes;   /* rbc_search: peak device workspace the call held
+                                (bytes requested from the workspace pool) */
 } rbc_search_stats;
 
 /* rbc_last_stats -- statistics of this thread's last search call (host only;
@@ -276,6 +295,113 @@ int rbc_set_timing(int on);
  *   Errors: RBC_ERR_CUDA.  No counterpart in the paper (memory management).
  */
 int rbc_trim_workspace(void);
+
+/* ---------------------------------------------------------------------------
+ * Serving engine: continuous batching over a resident index.  No counterpart
+ * in the paper, whose experiments search each data set's queries as one
+ * batch (Section 7); this is the request loop a deployment puts around
+ * rbc_search.
+ *
+ * A server owns `workers` worker threads, each with its own CUDA stream and
+ * resident device buffers for one merged batch (max_batch queries).  A free
+ * worker takes the requests waiting at the head of the queue, in arrival
+ * order, as many as fit within max_batch queries, shrinking the batch until
+ * its workspace bound (rbc_search_workspace with the batch's largest k)
+ * fits the HBM budget left by the batches already in flight -- or waits for
+ * memory to be released.  It copies the requests' queries into its batch
+ * buffer, runs one rbc_search over the batch, and copies each request's
+ * first k columns into that request's own output buffers.  Batches of
+ * different workers run concurrently on the device.  Each query's result
+ * depends only on that query, so a request gets the same answer alone and
+ * in any mix.
+ * ------------------------------------------------------------------------- */
+typedef struct rbc_server rbc_server; /* opaque; owned by the library */
+
+typedef struct {
+  int32_t workers;    /* batches in flight at once (threads + streams); 0 = 2; <= 16 */
+  int32_t max_batch;  /* queries per merged batch and per request; 0 = 16384 */
+  int32_t k_max;      /* largest k a request may ask for; 0 = 10; <= 31 */
+  int32_t reserved;   /* must be 0 */
+  int64_t hbm_budget; /* device bytes the in-flight batches' search workspace
+                         may take (sum of their rbc_search_workspace bounds);
+                         0 = half the free device memory at creation */
+} rbc_server_opts;
+
+/* What happened to one request (times from a steady clock, nanoseconds). */
+typedef struct {
+  int64_t t_submit_ns;    /* rbc_server_submit */
+  int64_t t_start_ns;     /* its batch was admitted */
+  int64_t t_done_ns;      /* its results were in its host buffers */
+  int64_t batch;          /* sequence number of the batch that served it (-1: m = 0) */
+  int64_t batch_queries;  /* queries in that batch */
+  int32_t batch_requests; /* requests in that batch */
+  int32_t status;         /* RBC_OK or the search's error code */
+} rbc_request_info;
+
+/* Aggregate over the requests collected since creation or the last reset. */
+typedef struct {
+  int64_t requests, queries, batches;
+  double p50_ms, p99_ms, mean_ms, max_ms; /* latency: submit -> results on the host */
+  double queue_p50_ms, queue_p99_ms;      /* submit -> batch admitted */
+  double wall_s;                          /* first submit -> last completion */
+  double queries_per_s;                   /* queries / wall_s */
+  double mean_batch_queries;
+  int64_t peak_reserved_bytes;            /* largest workspace bound held at once */
+  int64_t hbm_budget;
+  int32_t max_in_flight;                  /* most batches on the device at once */
+  int32_t workers;
+} rbc_serving_stats;
+
+/*
+ * rbc_server_create -- starts a server over `idx`, which must stay alive and
+ *   unchanged until rbc_server_destroy.  opts may be NULL (defaults above).
+ *   Errors: RBC_ERR_ARG (NULL, workers > 16, max_batch > 2^24, k_max > 31,
+ *   k_max > n, one-shot k_max > s), RBC_ERR_CUDA / RBC_ERR_OOM (streams,
+ *   buffers).
+ */
+int rbc_server_create(const rbc_index* idx, const rbc_server_opts* opts, rbc_server** out);
+
+/*
+ * rbc_server_submit -- queues a request of m queries Q [m, d] float32 and
+ *   returns at once with its ticket.  out_ids [m, k] int64 and out_dist
+ *   [m, k] float32 receive the results as rbc_search would (host or device
+ *   pointers; pinned host memory gives asynchronous copies).  Q and the
+ *   outputs must stay valid until rbc_server_wait reports the request done.
+ *   Errors: RBC_ERR_ARG (NULL, m < 0, m > max_batch, k outside [1, k_max],
+ *   server stopping); RBC_ERR_OOM if the workspace bound of a batch of this
+ *   request alone exceeds the HBM budget (it could never be admitted).
+ */
+int rbc_server_submit(rbc_server* s, const float* Q, int64_t m, int32_t k, int64_t* out_ids,
+                      float* out_dist, uint64_t* ticket);
+
+/*
+ * rbc_server_wait -- waits until request `ticket` is done (timeout_us < 0:
+ *   no limit), fills *info (may be NULL) and releases the ticket.  Returns
+ *   the request's status (the error of the batch's search, message in
+ *   rbc_last_error), or RBC_ERR_TIMEOUT if still running after timeout_us
+ *   (the ticket stays valid), or RBC_ERR_ARG for an unknown ticket.
+ */
+int rbc_server_wait(rbc_server* s, uint64_t ticket, int64_t timeout_us, rbc_request_info* info);
+
+/* rbc_server_stats -- fills *out; reset != 0 then starts a new window. */
+int rbc_server_stats(rbc_server* s, int32_t reset, rbc_serving_stats* out);
+
+/* rbc_server_destroy -- finishes every queued request, stops the workers and
+ * frees the server (not the index).  No other call on `s` may be running. */
+void rbc_server_destroy(rbc_server* s);
+
+/*
+ * rbc_plan_batch -- the admission rule of the server's workers, exposed for
+ *   tests with a linear workspace model: of n queued requests (m[i] queries,
+ *   k[i] neighbours, in arrival order) a batch takes the first c, the largest
+ *   c whose queries sum to at most max_batch and whose bound
+ *   fixed_bytes + queries * (bytes_per_query + max k * bytes_per_query_k)
+ *   is at most mem_left.  Returns c (0: nothing fits).  Host only.
+ *   Errors: RBC_ERR_ARG (n < 0, NULL arrays, max_batch < 1).
+ */
+int rbc_plan_batch(const int64_t* m, const int32_t* k, int32_t n, int64_t max_batch,
+                   int64_t mem_left, int64_t fixed_bytes, int64_t bytes_per_query,
+                   int64_t bytes_per_query_k);
 
 /* rbc_free -- releases the index (waits for its outstanding work). NULL ok. */
 void rbc_free(rbc_index* idx);

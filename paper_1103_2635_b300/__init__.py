@@ -27,6 +27,7 @@ __all__ = [
     "L2", "L1", "EXACT", "ONESHOT", "F32", "BF16", "F16", "PLAN_WINDOW", "PLAN_TILE_UNION",
     "RbcError", "bf_search", "bf_search_noalloc", "rbc_build", "rbc_search", "rbc_sample_reps",
     "RbcIndex", "last_stats", "set_timing", "trim_workspace", "library_path", "load",
+    "search_workspace", "plan_batch", "Server",
 ]
 
 L2, L1 = 0, 1
@@ -57,7 +58,7 @@ class _Desc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("n_r", ctypes.c_int32),
                 ("s", ctypes.c_int32), ("metric", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("list_entries", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("device", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -65,7 +66,29 @@ class _Stats(ctypes.Structure):
         "queries", "kept_reps", "tile_points", "stage2_items", "uncertified", "fp64_ties",
         "boundary_ties", "pairs", "kernel_launches")] + [
         (name, ctypes.c_double) for name in ("stage1_ms", "stage2_ms", "select_ms", "fallback_ms")] + [
-        ("candidates", ctypes.c_int64)]
+        ("candidates", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64)]
+
+
+class _ServerOpts(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("k_max", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("hbm_budget", ctypes.c_int64)]
+
+
+class _RequestInfo(ctypes.Structure):
+    _fields_ = [("t_submit_ns", ctypes.c_int64), ("t_start_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64), ("batch", ctypes.c_int64),
+                ("batch_queries", ctypes.c_int64), ("batch_requests", ctypes.c_int32),
+                ("status", ctypes.c_int32)]
+
+
+class _ServingStats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in ("requests", "queries", "batches")] + [
+        (name, ctypes.c_double) for name in (
+            "p50_ms", "p99_ms", "mean_ms", "max_ms", "queue_p50_ms", "queue_p99_ms", "wall_s",
+            "queries_per_s", "mean_batch_queries")] + [
+        ("peak_reserved_bytes", ctypes.c_int64), ("hbm_budget", ctypes.c_int64),
+        ("max_in_flight", ctypes.c_int32), ("workers", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -100,8 +123,17 @@ def load():
     lib.rbc_last_error.restype = ctypes.c_char_p
     lib.rbc_default_opts.argtypes = [ctypes.POINTER(_Opts)]
     lib.rbc_default_opts.restype = None
+    lib.rbc_search_workspace.argtypes = [P, I64, I32, ctypes.POINTER(I64)]
+    lib.rbc_plan_batch.argtypes = [P, P, I32, I64, I64, I64, I64, I64]
+    lib.rbc_server_create.argtypes = [P, ctypes.POINTER(_ServerOpts), ctypes.POINTER(ctypes.c_void_p)]
+    lib.rbc_server_submit.argtypes = [P, P, I64, I32, P, P, ctypes.POINTER(U64)]
+    lib.rbc_server_wait.argtypes = [P, U64, I64, ctypes.POINTER(_RequestInfo)]
+    lib.rbc_server_stats.argtypes = [P, I32, ctypes.POINTER(_ServingStats)]
+    lib.rbc_server_destroy.argtypes = [P]
+    lib.rbc_server_destroy.restype = None
     for f in ("rbc_sample_reps", "bf_search", "bf_search_noalloc", "rbc_build", "rbc_search", "rbc_index_info",
-              "rbc_index_export", "rbc_last_stats"):
+              "rbc_index_export", "rbc_last_stats", "rbc_search_workspace", "rbc_plan_batch",
+              "rbc_server_create", "rbc_server_submit", "rbc_server_wait", "rbc_server_stats"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -282,3 +314,91 @@ def last_stats() -> dict:
     s = _Stats()
     _check(load().rbc_last_stats(ctypes.byref(s)))
     return {f: getattr(s, f) for f, _ in _Stats._fields_}
+
+
+def search_workspace(index: RbcIndex, m: int, k: int) -> int:
+    """Upper bound of the device workspace bytes one rbc_search of m queries holds."""
+    b = ctypes.c_int64(0)
+    _check(load().rbc_search_workspace(index.handle, m, k, ctypes.byref(b)))
+    return b.value
+
+
+def plan_batch(m, k, max_batch: int, mem_left: int, fixed_bytes: int = 0,
+               bytes_per_query: int = 0, bytes_per_query_k: int = 0) -> int:
+    """The serving engine's admission rule (host only): how many of the queued
+    requests (sizes m, neighbour counts k, arrival order) one batch takes."""
+    ma = np.ascontiguousarray(m, dtype=np.int64)
+    ka = np.ascontiguousarray(k, dtype=np.int32)
+    rc = load().rbc_plan_batch(ma.ctypes.data, ka.ctypes.data, len(ma), max_batch, mem_left,
+                               fixed_bytes, bytes_per_query, bytes_per_query_k)
+    if rc < 0:
+        _check(rc)
+    return rc
+
+
+class Server:
+    """Continuous-batching request loop over a resident index (rbc_server_*).
+
+    ``submit`` queues a request and returns a ticket at once; the library's
+    worker threads merge waiting requests into batches admitted by an HBM
+    budget and run them concurrently on their own CUDA streams.  Inputs and
+    outputs of a request must stay alive until ``wait`` returns for it; the
+    object keeps references to them until then.
+    """
+
+    def __init__(self, index: RbcIndex, workers: int = 2, max_batch: int = 16384,
+                 k_max: int = 10, hbm_budget: int = 0):
+        o = _ServerOpts(workers, max_batch, k_max, 0, hbm_budget)
+        h = ctypes.c_void_p()
+        _check(load().rbc_server_create(index.handle, ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self._index = index  # the index must outlive the server
+        self._keep = {}
+        self.d = index.info()["d"]
+
+    def submit(self, Q, k: int, out_ids=None, out_dist=None) -> int:
+        """Queue the queries Q [m, d]; results go to out_ids / out_dist [m, k]
+        (allocated as host arrays when omitted).  Returns the ticket."""
+        qp, qk, _ = _arg(Q, np.float32)
+        m = qk.shape[0] if qk.ndim == 2 else 0
+        out_ids, out_dist = _outputs(m, k, None, out_ids, out_dist)
+        ip, ik, _ = _arg(out_ids, np.int64)
+        dp, dk, _ = _arg(out_dist, np.float32)
+        t = ctypes.c_uint64(0)
+        _check(load().rbc_server_submit(self._h, qp, m, k, ip, dp, ctypes.byref(t)))
+        self._keep[t.value] = (qk, ik, dk)
+        return t.value
+
+    def wait(self, ticket: int, timeout_us: int = -1):
+        """(out_ids, out_dist, info) of a finished request; raises RbcError on
+        its error or when it is still running after timeout_us."""
+        info = _RequestInfo()
+        rc = load().rbc_server_wait(self._h, ticket, timeout_us, ctypes.byref(info))
+        if rc == -4 and timeout_us >= 0:
+            _check(rc)
+        _, ik, dk = self._keep.pop(ticket, (None, None, None))
+        _check(rc)
+        return ik, dk, {f: getattr(info, f) for f, _ in _RequestInfo._fields_}
+
+    def stats(self, reset: bool = False) -> dict:
+        st = _ServingStats()
+        _check(load().rbc_server_stats(self._h, int(reset), ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in _ServingStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().rbc_server_destroy(self._h)
+        self._h = None
+        self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -52,6 +52,7 @@ struct rbc_index {
   int64_t n = 0;
   int32_t d = 0, n_r = 0, s = 0, metric = 0, mode = 0, storage = 0, rerank_c = 0, plan = 0;
   int64_t list_entries = 0;
+  int device = 0;             // CUDA device the index lives on
   std::vector<void*> allocs;
   int64_t bytes = 0;
   int64_t* reps = nullptr;    // [n_r] representative ids
@@ -201,13 +202,20 @@ cudaMemPool_t workspace_pool() {
 }
 
 // Stream-ordered scratch released when the arena goes out of scope.
+// Workspace bytes this thread's arenas hold, and the peak since the last
+// reset (reported per search as rbc_search_stats::workspace_bytes).
+thread_local int64_t t_ws_cur = 0;
+thread_local int64_t t_ws_peak = 0;
+
 struct Arena {
   cudaStream_t st;
   cudaMemPool_t pool;
   std::vector<void*> ptrs;
+  int64_t held = 0;
   explicit Arena(cudaStream_t s) : st(s), pool(workspace_pool()) {}
   ~Arena() {
     for (void* p : ptrs) cudaFreeAsync(p, st);
+    t_ws_cur -= held;
   }
   template <typename T>
   int alloc(T** out, int64_t count) {
@@ -223,6 +231,9 @@ struct Arena {
       return RBC_ERR_OOM;
     }
     ptrs.push_back(p);
+    held += count * (int64_t)sizeof(T);
+    t_ws_cur += count * (int64_t)sizeof(T);
+    if (t_ws_cur > t_ws_peak) t_ws_peak = t_ws_cur;
     *out = static_cast<T*>(p);
     return RBC_OK;
   }
@@ -723,6 +734,7 @@ int build_exact(rbc_index* ix, const float* Xdev, const std::vector<int64_t>& re
 // ---------------------------------------------------------------------------
 constexpr int64_t MAX_BATCH = 131072;  // queries per internal batch (bounds workspace)
 constexpr int64_t WINDOW_MAX_PAIRS = 1LL << 28;  // windowed search: batch x n_r bound
+constexpr int64_t ARENA_MIN_LANE = 256;  // hit records per epilogue thread, at least
 
 int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, int64_t* ids,
                        float* dist, const Counters& cn, int64_t* items_total, Arena& ar,
@@ -1285,11 +1297,13 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   // hit arena: each epilogue thread appends its emissions to its own slice
   // (no atomics in the kernel); a post-pass fills the per-query buffers.  The
   // slices together hold 256 records per query of the batch (about 5x the
-  // candidates of clustered 64-d data); if one overflows, the batch is
-  // emitted again with direct per-query appends.
+  // candidates of clustered 64-d data) and at least ARENA_MIN_LANE each: in
+  // a small batch a chunk holds few queries, so a query with thousands of
+  // candidates fills the slices of the few rows it occupies.  If one
+  // overflows, the batch is emitted again with direct per-query appends.
   const int64_t nslices = (int64_t)sms * ARENA_SUBSEG * 32;
   const int arena_lane = (int)std::min<int64_t>(
-      INT32_MAX / (4 * ARENA_SUBSEG * 32), std::max<int64_t>(64, (mb * 256 + nslices - 1) / nslices));
+      INT32_MAX / (4 * ARENA_SUBSEG * 32), std::max<int64_t>(ARENA_MIN_LANE, (mb * 256 + nslices - 1) / nslices));
   const int arena_seg = arena_lane * 32 * ARENA_SUBSEG;  // per CTA
   int4* arena;
   int *arena_cnt, *arena_ovf;
@@ -1398,6 +1412,146 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   tmark(4, st);
   taccumulate();
   return RBC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace upper bound of rbc_search: the sum of every workspace request a
+// call may make, term by term as the batch functions above allocate, with
+// every data-dependent size at its maximum (all candidate lists MAX_C wide,
+// every query of a batch falling back to the FP32 search).  A call holds the
+// I/O copies and counters for its duration and one batch's arena at a time.
+// ---------------------------------------------------------------------------
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// bf_dense_f32 over `rows` queries (items = tiles x splits <= tiles + 8 SMs)
+int64_t bound_dense_f32(int64_t rows, int sms) {
+  if (rows <= 0) return 0;
+  return (cdiv(rows, TQ) + 8LL * sms) * TQ * 2 * MAX_C * 8;
+}
+// fallback_f32: gathered rows + their dense FP32 search
+int64_t bound_fallback_f32(int64_t rows, int d, int sms) {
+  if (rows <= 0) return 0;
+  return rows * ((int64_t)d * 4 + 4) + bound_dense_f32(rows, sms);
+}
+// bf_dense_lp at the nested level: low-precision copy, partial lists, its
+// select and the FP32 fallback of its uncertified rows
+int64_t bound_dense_lp(int64_t rows, int d, int dpad, int sms) {
+  if (rows <= 0) return 0;
+  const int64_t items = cdiv(rows, TQ) + 16LL * sms;
+  return rows * ((int64_t)dpad * 2 + 8) + items * TQ * 2 * MAX_C * 8 + items * 4 + 4 +
+         rows * 4 + 32 + bound_fallback_f32(rows, d, sms);
+}
+// select_lp_and_fallback at level 0 over `rows` rows
+int64_t bound_select_lp(int64_t rows, int d, int dpad, int sms) {
+  return rows * 4 + 32 + rows * ((int64_t)d * 4 + 4) + bound_dense_lp(rows, d, dpad, sms);
+}
+// group_queries over mq rows
+int64_t bound_group(const rbc_index* ix, int64_t mq, bool gather_fp32) {
+  const int64_t n_r = ix->n_r;
+  const int64_t max_tiles = cdiv(mq, TQ) + std::min<int64_t>(n_r, mq);
+  const int64_t rows_cap = max_tiles * TQ;
+  return mq * 4 + (n_r + 1) * 4 + counting_sort_scratch_ints(mq, (int)n_r) * 4 + n_r * 4 +
+         (n_r + 1) * 4 + rows_cap * 8 + max_tiles * 4 + (gather_fp32 ? rows_cap * ix->d * 4 : 0) +
+         max_tiles * (int64_t)(sizeof(WorkItem) + sizeof(Seg)) + 4;
+}
+
+int64_t bound_window_batch(const rbc_index* ix, int64_t mb) {
+  const int d = ix->d, dpad = ix->dpad, sms = sm_count();
+  const int64_t n_r = ix->n_r, n = ix->list_entries;
+  const int64_t max_tiles = cdiv(mb, TQ) + std::min<int64_t>(n_r, mb);
+  const int64_t rows_cap = max_tiles * TQ;
+  const int64_t nbins = n_r * window_buckets();
+  const int64_t nslices = (int64_t)sms * ARENA_SUBSEG * 32;
+  const int64_t arena_lane = std::max<int64_t>(ARENA_MIN_LANE, cdiv(mb * 256, nslices));
+  const int64_t xspan = std::max<int64_t>(4096, cdiv(n, 2LL * sms) / 256 * 256);
+  const int64_t max2 = cdiv(mb, TQ) * cdiv(n, xspan);
+  int64_t b = mb * n_r * 4;                                  // D
+  b += mb * 16 + 4;                                          // g1, gk, nearest, dev_err
+  b += mb * ((int64_t)dpad * 2 + 8);                         // low-precision batch
+  b += mb * 4;                                               // own
+  b += bound_group(ix, mb, false);                           // pass A grouping
+  b += rows_cap * ((int64_t)dpad * 2 + 8);                   // pass A rows
+  b += rows_cap * 2 * MAX_C * 8;                             // pass A partial lists
+  b += mb * 4 + n_r * 8 + mb * 4;                            // g, rmin, rmax, qkept
+  b += window_pair_blocks(mb) * nbins * 4 + nbins * 8 + 4;   // bin counts, totals, offsets
+  b += mb * 4 + mb * n_r * 8;                                // thr, pairs
+  b += n_r * 8 + 4 + (mb * n_r / TQ + n_r) * (int64_t)sizeof(EmitItem);  // chunks, items
+  b += mb * (int64_t)CAND_CAP * 8 + mb * 4;                  // candidate buffers
+  b += nslices * arena_lane * 16 + nslices * 4 + 4;          // hit arena
+  b += mb * 8 + 64;                                          // fallback rows, counters
+  b += max2 * (int64_t)sizeof(EmitItem) + 4;                 // overflow items
+  b += bound_fallback_f32(mb, d, sms);                       // FP32 last resort
+  return b;
+}
+
+int64_t bound_exact_batch(const rbc_index* ix, int64_t mb) {
+  const int d = ix->d, dpad = ix->dpad, sms = sm_count();
+  const int64_t n_r = ix->n_r, n = ix->list_entries;
+  const int64_t tiles = cdiv(mb, TQ);
+  int64_t W = (tiles * n + 16LL * sms - 1) / (16LL * sms);
+  W = std::max<int64_t>(W, 4096);
+  W = std::min<int64_t>(W, std::max<int64_t>(n, 1));
+  W = (W + 255) / 256 * 256;
+  const int64_t item_cap = cdiv(n, W) + 1, seg_cap = n_r + item_cap + 1;
+  const int64_t cap_items = tiles * item_cap;
+  int64_t b = mb * n_r * 4 + mb * 16;                        // D, g1, gk, nearest
+  b += mb * 4 + (n_r + 1) * 4 + counting_sort_scratch_ints(mb, (int)n_r) * 4;
+  b += mb * (int64_t)d * 4;                                  // ordered queries
+  b += tiles * cdiv(n_r, 32) * 4 + tiles * 8 + mb * 4;       // masks, points, kept
+  b += (tiles + 1) * 4 + tiles * 4;                          // item offsets
+  b += cap_items * (int64_t)sizeof(WorkItem) + tiles * seg_cap * (int64_t)sizeof(Seg) + 4;
+  b += cap_items * TQ * 2 * MAX_C * 8 + cap_items * 4;       // partial lists
+  if (uses_lp(ix->storage, ix->metric) && ix->Xlp) {
+    b += mb * ((int64_t)dpad * 2 + 8);                       // low-precision batch
+    b += bound_select_lp(mb, d, dpad, sms);
+  }
+  return b;
+}
+
+int64_t bound_oneshot_stage2(const rbc_index* ix, int64_t mq, bool lp, int level) {
+  if (mq <= 0) return 0;
+  const int d = ix->d, dpad = ix->dpad, sms = sm_count();
+  const int64_t max_tiles = cdiv(mq, TQ) + std::min<int64_t>(ix->n_r, mq);
+  const int64_t rows_cap = max_tiles * TQ;
+  int64_t b = bound_group(ix, mq, true);
+  b += max_tiles * TQ * 2 * MAX_C * 8 + max_tiles * 4 + 4;   // partial lists, valid, dev_err
+  if (lp) {
+    b += rows_cap * ((int64_t)dpad * 2 + 8);                 // low-precision rows
+    b += rows_cap * 4 + 32;                                  // fallback rows, counters
+    b += rows_cap * (8 + 4 + (int64_t)d * 4);                // fallback gather
+    if (level == 0) b += bound_oneshot_stage2(ix, rows_cap, false, 1);
+  }
+  (void)sms;
+  return b;
+}
+
+int64_t bound_oneshot_batch(const rbc_index* ix, int64_t mb) {
+  const bool lp = uses_lp(ix->storage, ix->metric) && ix->Xlp != nullptr;
+  return mb * 12 + 32 + bound_dense_f32(mb, sm_count()) + bound_oneshot_stage2(ix, mb, lp, 0);
+}
+
+// the batch size rbc_search cuts a call into
+int64_t search_batch_size(const rbc_index* ix, bool window) {
+  return window ? std::max<int64_t>(TQ, std::min<int64_t>(MAX_BATCH, WINDOW_MAX_PAIRS / ix->n_r))
+                : MAX_BATCH;
+}
+bool search_uses_window(const rbc_index* ix) {
+  return ix->mode == RBC_EXACT && ix->plan == RBC_PLAN_WINDOW && uses_lp(ix->storage, ix->metric) &&
+         ix->Xlp;
+}
+
+int64_t search_workspace_bound(const rbc_index* ix, int64_t m, int k) {
+  const bool window = search_uses_window(ix);
+  const int64_t mb = std::min<int64_t>(std::max<int64_t>(m, 1), search_batch_size(ix, window));
+  int64_t b = m * ((int64_t)ix->d * 4 + (int64_t)k * 12);   // host I/O copies
+  b += 64 + 64;                                              // counters, packed statistics
+  if (ix->mode == RBC_ONESHOT)
+    b += bound_oneshot_batch(ix, mb);
+  else if (window)
+    b += bound_window_batch(ix, mb);
+  else
+    b += bound_exact_batch(ix, mb);
+  return b;
 }
 
 }  // namespace
@@ -1575,6 +1729,7 @@ int rbc_build(const float* X, int64_t n, int32_t d, int32_t n_r, int32_t s, int3
   ix->storage = o.storage;
   ix->rerank_c = o.rerank_c;
   ix->plan = o.plan;
+  cudaGetDevice(&ix->device);
   int rc;
   {
     Arena ar(st);
@@ -1622,36 +1777,51 @@ int rbc_search(const rbc_index* ix, const float* Q, int64_t m, int32_t k, int64_
     set_error("rbc_search: k=%d exceeds the supported maximum %d", k, MAX_C - 1);
     return RBC_ERR_UNSUPPORTED;
   }
-  Arena ar(st);
-  IoPlan io;
-  RBC_TRY(io_prepare(Q, m, ix->d, k, out_ids, out_dist, io, ar, st));
-  Counters cn;
-  RBC_TRY(counters_alloc(cn, ar, st));
+  const int64_t ws0 = t_ws_cur;
+  t_ws_peak = t_ws_cur;
   int64_t items = 0;
-  const bool window = ix->mode == RBC_EXACT && ix->plan == RBC_PLAN_WINDOW &&
-                      uses_lp(ix->storage, ix->metric) && ix->Xlp;
+  const bool window = search_uses_window(ix);
   // the windowed search sizes its pair arrays by batch x n_r
-  const int64_t batch =
-      window ? std::max<int64_t>(TQ, std::min<int64_t>(MAX_BATCH, WINDOW_MAX_PAIRS / ix->n_r))
-             : MAX_BATCH;
-  for (int64_t b0 = 0; b0 < m; b0 += batch) {
-    int64_t mb = std::min<int64_t>(batch, m - b0);
-    Arena bar(st);
-    if (ix->mode == RBC_ONESHOT)
-      RBC_TRY(search_oneshot_batch(ix, io.Qdev + b0 * ix->d, mb, k, io.ids_dev + b0 * k,
+  const int64_t batch = search_batch_size(ix, window);
+  {
+    Arena ar(st);
+    IoPlan io;
+    RBC_TRY(io_prepare(Q, m, ix->d, k, out_ids, out_dist, io, ar, st));
+    Counters cn;
+    RBC_TRY(counters_alloc(cn, ar, st));
+    for (int64_t b0 = 0; b0 < m; b0 += batch) {
+      int64_t mb = std::min<int64_t>(batch, m - b0);
+      Arena bar(st);
+      if (ix->mode == RBC_ONESHOT)
+        RBC_TRY(search_oneshot_batch(ix, io.Qdev + b0 * ix->d, mb, k, io.ids_dev + b0 * k,
+                                     io.dist_dev + b0 * k, cn, &items, bar, st));
+      else if (window)
+        RBC_TRY(search_window_batch(ix, io.Qdev + b0 * ix->d, mb, k, io.ids_dev + b0 * k,
+                                    io.dist_dev + b0 * k, cn, &items, bar, st));
+      else
+        RBC_TRY(search_exact_batch(ix, io.Qdev + b0 * ix->d, mb, k, io.ids_dev + b0 * k,
                                    io.dist_dev + b0 * k, cn, &items, bar, st));
-    else if (window)
-      RBC_TRY(search_window_batch(ix, io.Qdev + b0 * ix->d, mb, k, io.ids_dev + b0 * k,
-                                  io.dist_dev + b0 * k, cn, &items, bar, st));
+    }
+    if (ix->mode == RBC_ONESHOT)
+      RBC_TRY(stats_publish(cn, m, items, m * (int64_t)ix->s, ar, st, m));
     else
-      RBC_TRY(search_exact_batch(ix, io.Qdev + b0 * ix->d, mb, k, io.ids_dev + b0 * k,
-                                 io.dist_dev + b0 * k, cn, &items, bar, st));
+      RBC_TRY(stats_publish(cn, m, items, 0, ar, st));
+    RBC_TRY(io_finish(m, k, out_ids, out_dist, io, st));
   }
-  if (ix->mode == RBC_ONESHOT)
-    RBC_TRY(stats_publish(cn, m, items, m * (int64_t)ix->s, ar, st, m));
-  else
-    RBC_TRY(stats_publish(cn, m, items, 0, ar, st));
-  RBC_TRY(io_finish(m, k, out_ids, out_dist, io, st));
+  t_stats_fixed.workspace_bytes = t_ws_peak - ws0;
+  return RBC_OK;
+}
+
+int rbc_search_workspace(const rbc_index* ix, int64_t m, int32_t k, int64_t* bytes) {
+  if (!ix || !bytes || m < 0 || k < 1) {
+    set_error("rbc_search_workspace: NULL pointer or bad sizes (m=%lld k=%d)", (long long)m, k);
+    return RBC_ERR_ARG;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != ix->device) cudaSetDevice(ix->device);  // the bound reads this device's SM count
+  *bytes = search_workspace_bound(ix, m, k);
+  if (dev != ix->device) cudaSetDevice(dev);
   return RBC_OK;
 }
 
@@ -1669,6 +1839,7 @@ int rbc_index_info(const rbc_index* ix, rbc_index_desc* out) {
   out->storage = ix->storage;
   out->list_entries = ix->list_entries;
   out->device_bytes = ix->bytes;
+  out->device = ix->device;
   return RBC_OK;
 }
 
