@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="subspace8-n1m-d64")
     ap.add_argument("--k", type=int, default=10)
-    ap.add_argument("--storage", default="bf16", choices=["bf16", "f16", "f32"])
+    ap.add_argument("--storage", default="bf16", choices=["bf16", "f16", "f32", "fp8"])
     ap.add_argument("--plan", default="window", choices=["window", "tile_union"],
                     help="exact-search stage two (bf16 / fp16 storage)")
     ap.add_argument("--cpu-sample", type=int, default=1000)
@@ -216,7 +216,7 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=dev)
-    storage = {"bf16": rbc.BF16, "f16": rbc.F16, "f32": rbc.F32}[args.storage]
+    storage = {"bf16": rbc.BF16, "f16": rbc.F16, "f32": rbc.F32, "fp8": rbc.FP8E4M3}[args.storage]
     # each rank holds its own replica and its own query batch (weak scaling)
     w, X, Q = workload_arrays(args.workload, 0, query_seed=1 + 1000 * rank, n=args.n, m=args.m)
     Xd = torch.from_numpy(X).to(dev)

@@ -24,7 +24,7 @@
  *   the smaller database id.  out_dist holds rho itself (Euclidean distance,
  *   not its square, for RBC_L2; the l1 sum for RBC_L1).  When k exceeds the
  *   number of points the tail holds id -1 and distance +inf.
- * Exactness.  Low-precision storage (RBC_BF16 / RBC_F16) is used for the
+ * Exactness.  Low-precision storage (RBC_BF16 / RBC_F16 / RBC_FP8E4M3) is used for the
  *   tensor-core distance pass only; candidates are re-ranked in FP32
  *   difference form, the candidate set is certified with a rounding-error
  *   bound, queries that fail certification are re-searched in FP32, and
@@ -66,9 +66,15 @@ typedef enum {
 } rbc_mode;
 
 typedef enum {
-  RBC_F32 = 0,  /* FP32 CUDA-core distance kernels throughout */
-  RBC_BF16 = 1, /* bf16 tensor-core pass (L2), FP32 re-rank, FP64 ties */
-  RBC_F16 = 2   /* fp16 tensor-core pass (L2), FP32 re-rank, FP64 ties */
+  RBC_F32 = 0,     /* FP32 CUDA-core distance kernels throughout */
+  RBC_BF16 = 1,    /* bf16 tensor-core pass (L2), FP32 re-rank, FP64 ties */
+  RBC_F16 = 2,     /* fp16 tensor-core pass (L2), FP32 re-rank, FP64 ties */
+  RBC_FP8E4M3 = 3  /* FP8 E4M3 with a per-vector scale (the vector's max |x_i| / 448
+                      rounded up to a power of two), tcgen05 kind::f8f6f4 pass with
+                      FP32 accumulation (L2), FP32 re-rank, FP64 ties; the residual
+                      |x - x~| of the scaled dequantisation enters the certification.
+                      Exact search uses the tile-union plan.  Rows are padded to a
+                      multiple of 128 elements. */
 } rbc_storage;
 
 /* Stage two of the exact search with bf16 / fp16 storage (L2).

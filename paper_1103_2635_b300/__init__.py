@@ -24,7 +24,7 @@ import os
 import numpy as np
 
 __all__ = [
-    "L2", "L1", "EXACT", "ONESHOT", "F32", "BF16", "F16", "PLAN_WINDOW", "PLAN_TILE_UNION",
+    "L2", "L1", "EXACT", "ONESHOT", "F32", "BF16", "F16", "FP8E4M3", "PLAN_WINDOW", "PLAN_TILE_UNION",
     "RbcError", "bf_search", "bf_search_noalloc", "rbc_build", "rbc_search", "rbc_sample_reps",
     "RbcIndex", "last_stats", "set_timing", "trim_workspace", "library_path", "load",
     "search_workspace", "plan_batch", "Server",
@@ -32,7 +32,7 @@ __all__ = [
 
 L2, L1 = 0, 1
 EXACT, ONESHOT = 0, 1
-F32, BF16, F16 = 0, 1, 2
+F32, BF16, F16, FP8E4M3 = 0, 1, 2, 3
 PLAN_WINDOW, PLAN_TILE_UNION = 0, 1
 _STATUS = {0: "ok", -1: "invalid argument", -2: "out of device memory", -3: "CUDA error",
            -4: "device wait timed out", -5: "unsupported"}

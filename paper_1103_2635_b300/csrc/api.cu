@@ -69,6 +69,8 @@ struct rbc_index {
   unsigned* lp_max = nullptr; // [4] float bits: max|x-x~|, max|x~|, max|r-r~|, max|r~|
   void* Rlp = nullptr;        // [n_r, dpad]
   float* rnorm = nullptr;     // [n_r]
+  float* xscale = nullptr;    // FP8: [list_entries + NORM_PAD] per-row power-of-two scales
+  float* rscale = nullptr;    // FP8: [n_r]
 
   template <typename T>
   int alloc(T** out, int64_t count) {
@@ -245,6 +247,10 @@ float simt_eps(int d) { return (float)(d + 8) * U32; }
 // relative bound of rho from the FP32 re-rank (interleaved partial sums)
 float rerank_eps_host(int d) { return (0.25f * d + 8.0f) * U32; }
 int pad64(int d) { return (d + 63) / 64 * 64; }
+// low-precision row length: 128-byte K blocks of 64 16-bit or 128 FP8 elements
+int lp_pad(int d, int storage) {
+  return storage == RBC_FP8E4M3 ? (d + 127) / 128 * 128 : pad64(d);
+}
 // the tensor-core kernel reads whole tiles of norms past the last row
 constexpr int64_t NORM_PAD = 512;
 
@@ -403,7 +409,8 @@ int valid_enums(int metric, int storage) {
     set_error("unknown metric %d", metric);
     return RBC_ERR_ARG;
   }
-  if (storage != RBC_F32 && storage != RBC_BF16 && storage != RBC_F16) {
+  if (storage != RBC_F32 && storage != RBC_BF16 && storage != RBC_F16 &&
+      storage != RBC_FP8E4M3) {
     set_error("unknown storage %d", storage);
     return RBC_ERR_ARG;
   }
@@ -432,6 +439,7 @@ struct DbView {
   int64_t rows = 0;
   const void* Xlp = nullptr;   // [rows, dpad]
   const float* xnorm = nullptr;
+  const float* xscale = nullptr;  // FP8: per-row scales
   int dpad = 0;
   const unsigned* lp_max = nullptr;  // [0] max |x - x~|, [1] max |x~| (float bits)
 };
@@ -514,18 +522,21 @@ struct LpQueries {
   void* lp = nullptr;
   float* norm = nullptr;
   float* err = nullptr;
+  float* scale = nullptr;  // FP8 only
   int storage = RBC_BF16;
 };
 
 int lp_queries(const float* Qdev, int64_t m, int d, int dpad, int storage, LpQueries& q,
                Arena& ar, cudaStream_t st) {
-  uint16_t* buf;
-  RBC_TRY(ar.alloc(&buf, std::max<int64_t>(m, 1) * dpad));
+  uint8_t* buf;
+  RBC_TRY(ar.alloc(&buf, std::max<int64_t>(m, 1) * dpad * lp_elem_bytes(storage)));
   RBC_TRY(ar.alloc(&q.norm, m));
   RBC_TRY(ar.alloc(&q.err, m));
+  if (storage == RBC_FP8E4M3) RBC_TRY(ar.alloc(&q.scale, m));
   q.lp = buf;
   q.storage = storage;
-  return launch_to_lowp(Qdev, m, d, dpad, storage, buf, q.norm, q.err, nullptr, nullptr, st);
+  return launch_to_lowp(Qdev, m, d, dpad, storage, buf, q.norm, q.err, nullptr, nullptr, st,
+                        q.scale);
 }
 
 int bf_dense_lp(const float* Qdev, int64_t m, const DbView& db, int d, int k, int storage,
@@ -536,12 +547,16 @@ int bf_dense_lp(const float* Qdev, int64_t m, const DbView& db, int d, int k, in
 // the re-search of uncertified rows (one host read of their count): first on
 // the tensor cores with the widest candidate lists (level 0 only), then, for
 // rows that still fail, with the FP32 kernel over every row of `db`.
+int fallback_rbc_f32(const rbc_index* ix, const float* Qbuf, const int* rows_dev, int nrows,
+                     const int* qorig, int k, int64_t* out_ids, float* out_dist, int* cnt,
+                     Arena& ar, cudaStream_t st, const float* g_rows = nullptr);
+
 int select_lp_and_fallback(const float* ps, const int* pi, const int* pv, int C,
                            const int* tile_slot_off,
                            int dense_splits, int64_t m, const float* Qbuf, const LpQueries& ql,
                            const DbView& db, int d, int k, int c_out, const int* qorig,
                            int64_t* out_ids, float* out_dist, int* cnt, Arena& ar,
-                           cudaStream_t st, int level = 0) {
+                           cudaStream_t st, int level = 0, const rbc_index* rbc_ix = nullptr) {
   int* fb_rows;
   int* lc;  // this call's counters: [0] rows appended to fb_rows, [1..2] ties
   RBC_TRY(ar.alloc(&fb_rows, m));
@@ -581,7 +596,11 @@ int select_lp_and_fallback(const float* ps, const int* pi, const int* pv, int C,
   RBC_CUDA(cudaMemcpyAsync(&nfb, lc, sizeof(int), cudaMemcpyDeviceToHost, st));
   RBC_CUDA(cudaStreamSynchronize(st));
   if (nfb > 0) {
-    if (level == 0 && db.Xlp) {
+    if (rbc_ix) {
+      // exact RBC: the FP32 exact search over the rows' surviving lists
+      RBC_TRY(fallback_rbc_f32(rbc_ix, Qbuf, fb_rows, nfb, qorig, k, out_ids, out_dist, cnt + 4,
+                               ar, st));
+    } else if (level == 0 && db.Xlp) {
       float* Qf;
       int* forig;
       RBC_TRY(ar.alloc(&Qf, (int64_t)nfb * d));
@@ -633,8 +652,8 @@ int bf_dense_lp(const float* Qdev, int64_t m, const DbView& db, int d, int k, in
   w.n = db.rows;
   w.dense_splits = (int)splits;
   w.dense_chunk = chunk;
-  LpMatrix Qm{ql.lp, ql.norm, m, db.dpad, storage};
-  LpMatrix Xm{db.Xlp, db.xnorm, db.rows, db.dpad, storage};
+  LpMatrix Qm{ql.lp, ql.norm, m, db.dpad, storage, nullptr, ql.scale};
+  LpMatrix Xm{db.Xlp, db.xnorm, db.rows, db.dpad, storage, nullptr, db.xscale};
   uint32_t* dev_err;
   RBC_TRY(ar.alloc(&dev_err, 1));
   RBC_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(uint32_t), st));
@@ -662,24 +681,33 @@ int make_lp_copies(rbc_index* ix, cudaStream_t st) {
   if (ix->storage == RBC_F32 || ix->metric != RBC_L2) return RBC_OK;
   const int64_t n = ix->list_entries;
   const int d = ix->d, n_r = ix->n_r;
-  ix->dpad = pad64(d);
-  uint16_t* xl;
-  uint16_t* rl;
-  RBC_TRY(ix->alloc(&xl, n * ix->dpad));
+  const bool fp8 = ix->storage == RBC_FP8E4M3;
+  const int eb = lp_elem_bytes(ix->storage);
+  ix->dpad = lp_pad(d, ix->storage);
+  uint8_t* xl;
+  uint8_t* rl;
+  RBC_TRY(ix->alloc(&xl, n * ix->dpad * eb));
   RBC_TRY(ix->alloc(&ix->xnorm, n + NORM_PAD));
   RBC_CUDA(cudaMemsetAsync(ix->xnorm + n, 0, NORM_PAD * sizeof(float), st));
   RBC_TRY(ix->alloc(&ix->lp_max, 4));
-  RBC_TRY(ix->alloc(&rl, (int64_t)n_r * ix->dpad));
+  RBC_TRY(ix->alloc(&rl, (int64_t)n_r * ix->dpad * eb));
   RBC_TRY(ix->alloc(&ix->rnorm, n_r));
+  if (fp8) {
+    RBC_TRY(ix->alloc(&ix->xscale, n + NORM_PAD));
+    RBC_CUDA(cudaMemsetAsync(ix->xscale + n, 0, NORM_PAD * sizeof(float), st));
+    RBC_TRY(ix->alloc(&ix->rscale, n_r));
+  }
   RBC_CUDA(cudaMemsetAsync(ix->lp_max, 0, 4 * sizeof(unsigned), st));
   RBC_TRY(launch_to_lowp(ix->X32, n, d, ix->dpad, ix->storage, xl, ix->xnorm, nullptr,
-                         ix->lp_max, ix->lp_max + 1, st));
-  // -|x~|^2 / 2 as a bf16 (high, low) block: the windowed kernel adds it to
-  // its accumulators with one extra MMA instead of a per-column FMA
-  RBC_TRY(ix->alloc(reinterpret_cast<uint16_t**>(&ix->xnblock), (n + NORM_PAD) * NBLOCK_COLS));
-  RBC_TRY(launch_norm_block(ix->xnorm, n, n + NORM_PAD, ix->xnblock, st));
+                         ix->lp_max, ix->lp_max + 1, st, ix->xscale));
+  if (!fp8) {
+    // -|x~|^2 / 2 as a bf16 (high, low) block: the windowed kernel adds it to
+    // its accumulators with one extra MMA instead of a per-column FMA
+    RBC_TRY(ix->alloc(reinterpret_cast<uint16_t**>(&ix->xnblock), (n + NORM_PAD) * NBLOCK_COLS));
+    RBC_TRY(launch_norm_block(ix->xnorm, n, n + NORM_PAD, ix->xnblock, st));
+  }
   RBC_TRY(launch_to_lowp(ix->R32, n_r, d, ix->dpad, ix->storage, rl, ix->rnorm, nullptr,
-                         ix->lp_max + 2, ix->lp_max + 3, st));
+                         ix->lp_max + 2, ix->lp_max + 3, st, ix->rscale));
   ix->Xlp = xl;
   ix->Rlp = rl;
   return RBC_OK;
@@ -738,11 +766,11 @@ constexpr int64_t ARENA_MIN_LANE = 256;  // hit records per epilogue thread, at 
 
 int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, int64_t* ids,
                        float* dist, const Counters& cn, int64_t* items_total, Arena& ar,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool f32_only = false, const float* g_cap = nullptr) {
   const int d = ix->d, n_r = ix->n_r, metric = ix->metric;
   const int64_t n = ix->list_entries;
   const int sms = sm_count();
-  const bool lp = uses_lp(ix->storage, metric) && ix->Xlp != nullptr;
+  const bool lp = !f32_only && uses_lp(ix->storage, metric) && ix->Xlp != nullptr;
   const int64_t tiles = (mb + TQ - 1) / TQ;
 
   tmark(0, st);
@@ -763,6 +791,9 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
   RBC_TRY(ar.alloc(&gk, mb));
   RBC_TRY(ar.alloc(&nearest, mb));
   RBC_TRY(launch_row_stats(D, mb, n_r, k, g1, gk, nearest, st));
+  // a caller that already knows an upper bound of each query's k-th neighbour
+  // distance (the windowed search's own-list bound) tightens gamma_k with it
+  if (g_cap) RBC_TRY(launch_gbound(g_cap, gk, mb, 0.0f, gk, st));
   // queries ordered by nearest representative, so each tile holds nearby queries
   int *qperm, *qoff, *scratch;
   RBC_TRY(ar.alloc(&qperm, mb));
@@ -819,6 +850,7 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
   db.rows = n;
   db.Xlp = ix->Xlp;
   db.xnorm = ix->xnorm;
+  db.xscale = ix->xscale;
   db.dpad = ix->dpad;
   db.lp_max = ix->lp_max;
   const int64_t cap_items = tiles * item_cap;
@@ -866,12 +898,12 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
     RBC_TRY(ar.alloc(&ps, cap_items * TQ * 2 * C));
     RBC_TRY(ar.alloc(&pi, cap_items * TQ * 2 * C));
     RBC_TRY(ar.alloc(&pv, cap_items));
-    LpMatrix Qm{ql.lp, ql.norm, mb, ix->dpad, ix->storage};
-    LpMatrix Xm{ix->Xlp, ix->xnorm, n, ix->dpad, ix->storage};
+    LpMatrix Qm{ql.lp, ql.norm, mb, ix->dpad, ix->storage, nullptr, ql.scale};
+    LpMatrix Xm{ix->Xlp, ix->xnorm, n, ix->dpad, ix->storage, nullptr, ix->xscale};
     tmark(1, st);
     RBC_TRY(launch_bf_tc_topc(Qm, Xm, C, w2, TopOut{ps, pi, pv}, sms, st, dev_err));
     RBC_TRY(select_lp_and_fallback(ps, pi, pv, C, toff, 0, mb, Qp, ql, db, d, k, c_out, qperm,
-                                   ids, dist, cn.c, ar, st));
+                                   ids, dist, cn.c, ar, st, 0, ix));
   }
   uint32_t herr = 0;
   RBC_CUDA(cudaMemcpyAsync(&herr, dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -882,6 +914,49 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
     return (herr & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
   }
   return RBC_OK;
+}
+
+// Rows of a query buffer whose low-precision candidates could not be
+// certified in an exact search are searched again by the FP32 exact search
+// (CUDA cores) over the union of their own surviving lists -- a superset of
+// what they need, and far less than every point of the index.  Row i's
+// result goes to output row qorig[rows_dev[i]] (rows_dev[i] when qorig is
+// null).  g_rows (optional, per row of the query buffer) bounds each
+// query's k-th neighbour distance and tightens the pruning.  The nested
+// search's phases count as the caller's re-search phase.
+int fallback_rbc_f32(const rbc_index* ix, const float* Qbuf, const int* rows_dev, int nrows,
+                     const int* qorig, int k, int64_t* out_ids, float* out_dist, int* cnt,
+                     Arena& ar, cudaStream_t st, const float* g_rows) {
+  if (nrows <= 0) return RBC_OK;
+  const int d = ix->d;
+  float* Qf;
+  int* forig;
+  int64_t* tid;
+  float* tds;
+  RBC_TRY(ar.alloc(&Qf, (int64_t)nrows * d));
+  RBC_TRY(ar.alloc(&forig, nrows));
+  RBC_TRY(ar.alloc(&tid, (int64_t)nrows * k));
+  RBC_TRY(ar.alloc(&tds, (int64_t)nrows * k));
+  RBC_TRY(launch_gather_rows(Qbuf, nullptr, rows_dev, nrows, d, Qf, st));
+  RBC_TRY(launch_map_rows(rows_dev, nullptr, nrows, qorig, forig, st));
+  float* gsub = nullptr;
+  if (g_rows) {
+    RBC_TRY(ar.alloc(&gsub, nrows));
+    RBC_TRY(launch_gather_rows(g_rows, nullptr, rows_dev, nrows, 1, gsub, st));
+  }
+  Counters c2;
+  RBC_TRY(ar.alloc(&c2.c, 8));
+  RBC_TRY(ar.alloc(&c2.sums, 4));
+  RBC_CUDA(cudaMemsetAsync(c2.c, 0, 8 * sizeof(int), st));
+  RBC_CUDA(cudaMemsetAsync(c2.sums, 0, 4 * sizeof(unsigned long long), st));
+  int64_t items = 0;
+  const bool timing = t_timing.on;
+  t_timing.on = false;
+  const int rc = search_exact_batch(ix, Qf, nrows, k, tid, tds, c2, &items, ar, st, true, gsub);
+  t_timing.on = timing;
+  RBC_TRY(rc);
+  RBC_TRY(launch_add_ints(cnt, c2.c, 3, st));
+  return launch_scatter_result_rows(tid, tds, forig, nrows, k, out_ids, out_dist, st);
 }
 
 
@@ -1109,8 +1184,8 @@ int oneshot_stage2(const rbc_index* ix, const float* Qsrc, int64_t mq, const int
   uint32_t* dev_err;
   RBC_TRY(ar.alloc(&dev_err, 1));
   RBC_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(uint32_t), st));
-  LpMatrix Qm{ql.lp, ql.norm, rows_cap, ix->dpad, ix->storage};
-  LpMatrix Xm{ix->Xlp, ix->xnorm, entries, ix->dpad, ix->storage};
+  LpMatrix Qm{ql.lp, ql.norm, rows_cap, ix->dpad, ix->storage, nullptr, ql.scale};
+  LpMatrix Xm{ix->Xlp, ix->xnorm, entries, ix->dpad, ix->storage, nullptr, ix->xscale};
   if (marks) tmark(1, st);
   RBC_TRY(launch_bf_tc_topc(Qm, Xm, C, w, TopOut{ps, pi, pv}, sms, st, dev_err));
   if (marks) tmark(2, st);
@@ -1369,11 +1444,29 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
     // exact re-rank of the candidates; overflowing queries are collected
     RBC_TRY(launch_select_cands(a, st));
     tmark(3, st);
-    // Queries whose candidate buffer overflowed (count in lc[0], on the
-    // device): k of their stored candidates give a much tighter threshold;
-    // emit again for them alone against the whole list storage (direct
-    // appends) and finish them.  Launched unconditionally with device-side
-    // counts (empty when nothing overflowed), so the batch synchronises once.
+    int early[3] = {0, 0, 0};  // overflowing rows, device error flags, arena overflow
+    RBC_CUDA(cudaMemcpyAsync(&early[0], lc, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBC_CUDA(cudaMemcpyAsync(&early[1], dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    RBC_CUDA(cudaMemcpyAsync(&early[2], arena_ovf, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBC_CUDA(cudaStreamSynchronize(st));
+    if (early[1]) {
+      set_error("windowed stage two reported device error flags 0x%x", (unsigned)early[1]);
+      return (early[1] & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
+    }
+    if (!direct && early[2]) continue;  // an arena slice overflowed: emit again directly
+    if (early[0] > mb / 16 + 64) {
+      // Many overflowing queries (clustered data whose points tie within the
+      // rounding slack by the thousand): a dense pass would overflow again,
+      // so they go straight to the FP32 exact search over their own lists.
+      RBC_TRY(launch_add_ints(cn.c, lc, 3, st));
+      RBC_TRY(launch_sum_i32(cc, mb, cn.sums + 3, st));
+      RBC_TRY(fallback_rbc_f32(ix, Qb, fb_rows, early[0], nullptr, k, ids, dist, cn.c + 4, ar,
+                               st, g));
+      break;
+    }
+    // Few overflowing queries (count in lc[0], on the device): k of their
+    // stored candidates give a much tighter threshold; emit again for them
+    // alone against the whole list storage (direct appends) and finish them.
     RBC_TRY(launch_overflow_rethreshold(fb_rows, lc, mb, cs, cc, CAND_CAP, k, ql.norm, ql.err,
                                         ix->lp_max, d, thr, st));
     RBC_TRY(launch_dense_emit_items(lc, n, xspan, max2, items2, n_items2, st));
@@ -1385,28 +1478,21 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
     a2.fallback_rows = fb2;
     a2.counters = lc2;
     RBC_TRY(launch_select_cands(a2, st));
-    int host[3] = {0, 0, 0};  // rows left for the FP32 BF, device error flags, arena overflow
+    int host[2] = {0, 0};  // rows left for the FP32 search, device error flags
     RBC_CUDA(cudaMemcpyAsync(&host[0], lc2, sizeof(int), cudaMemcpyDeviceToHost, st));
     RBC_CUDA(cudaMemcpyAsync(&host[1], dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    RBC_CUDA(cudaMemcpyAsync(&host[2], arena_ovf, sizeof(int), cudaMemcpyDeviceToHost, st));
     RBC_CUDA(cudaStreamSynchronize(st));
     if (host[1]) {
       set_error("windowed stage two reported device error flags 0x%x", (unsigned)host[1]);
       return (host[1] & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
     }
-    if (!direct && host[2]) continue;  // an arena segment overflowed: emit again directly
     RBC_TRY(launch_add_ints(cn.c, lc, 3, st));
     RBC_TRY(launch_add_ints(cn.c + 4, lc2, 3, st));
     RBC_TRY(launch_sum_i32(cc, mb, cn.sums + 3, st));
-    if (host[0] > 0) {
-      // more points than a buffer holds tie within rounding: FP32 brute force
-      DbView db;
-      db.X32 = ix->X32;
-      db.xid = ix->members;
-      db.rows = n;
-      RBC_TRY(fallback_f32(Qb, fb2, host[0], nullptr, db, d, k, ix->metric, ids, dist, cn.c + 4,
-                           ar, st));
-    }
+    // more points than a buffer holds tie within rounding: the FP32 exact
+    // search over those queries' surviving lists
+    if (host[0] > 0)
+      RBC_TRY(fallback_rbc_f32(ix, Qb, fb2, host[0], nullptr, k, ids, dist, cn.c + 4, ar, st, g));
     break;
   }
   tmark(4, st);
@@ -1428,22 +1514,17 @@ int64_t bound_dense_f32(int64_t rows, int sms) {
   if (rows <= 0) return 0;
   return (cdiv(rows, TQ) + 8LL * sms) * TQ * 2 * MAX_C * 8;
 }
-// fallback_f32: gathered rows + their dense FP32 search
-int64_t bound_fallback_f32(int64_t rows, int d, int sms) {
+int64_t bound_exact_batch(const rbc_index* ix, int64_t mb, int k, bool f32_only = false);
+// fallback_rbc_f32 over `rows` rows: gathered rows, results, counters and the
+// FP32 exact search
+int64_t bound_fallback_rbc(const rbc_index* ix, int64_t rows, int k) {
   if (rows <= 0) return 0;
-  return rows * ((int64_t)d * 4 + 4) + bound_dense_f32(rows, sms);
+  return rows * ((int64_t)ix->d * 4 + 8 + (int64_t)k * 12) + 96 +
+         bound_exact_batch(ix, rows, k, true);
 }
-// bf_dense_lp at the nested level: low-precision copy, partial lists, its
-// select and the FP32 fallback of its uncertified rows
-int64_t bound_dense_lp(int64_t rows, int d, int dpad, int sms) {
-  if (rows <= 0) return 0;
-  const int64_t items = cdiv(rows, TQ) + 16LL * sms;
-  return rows * ((int64_t)dpad * 2 + 8) + items * TQ * 2 * MAX_C * 8 + items * 4 + 4 +
-         rows * 4 + 32 + bound_fallback_f32(rows, d, sms);
-}
-// select_lp_and_fallback at level 0 over `rows` rows
-int64_t bound_select_lp(int64_t rows, int d, int dpad, int sms) {
-  return rows * 4 + 32 + rows * ((int64_t)d * 4 + 4) + bound_dense_lp(rows, d, dpad, sms);
+// select_lp_and_fallback at level 0 over `rows` rows of an exact search
+int64_t bound_select_lp(const rbc_index* ix, int64_t rows, int k) {
+  return rows * 4 + 32 + bound_fallback_rbc(ix, rows, k);
 }
 // group_queries over mq rows
 int64_t bound_group(const rbc_index* ix, int64_t mq, bool gather_fp32) {
@@ -1455,7 +1536,7 @@ int64_t bound_group(const rbc_index* ix, int64_t mq, bool gather_fp32) {
          max_tiles * (int64_t)(sizeof(WorkItem) + sizeof(Seg)) + 4;
 }
 
-int64_t bound_window_batch(const rbc_index* ix, int64_t mb) {
+int64_t bound_window_batch(const rbc_index* ix, int64_t mb, int k) {
   const int d = ix->d, dpad = ix->dpad, sms = sm_count();
   const int64_t n_r = ix->n_r, n = ix->list_entries;
   const int64_t max_tiles = cdiv(mb, TQ) + std::min<int64_t>(n_r, mb);
@@ -1467,10 +1548,10 @@ int64_t bound_window_batch(const rbc_index* ix, int64_t mb) {
   const int64_t max2 = cdiv(mb, TQ) * cdiv(n, xspan);
   int64_t b = mb * n_r * 4;                                  // D
   b += mb * 16 + 4;                                          // g1, gk, nearest, dev_err
-  b += mb * ((int64_t)dpad * 2 + 8);                         // low-precision batch
+  b += mb * ((int64_t)dpad * 2 + 12);                         // low-precision batch
   b += mb * 4;                                               // own
   b += bound_group(ix, mb, false);                           // pass A grouping
-  b += rows_cap * ((int64_t)dpad * 2 + 8);                   // pass A rows
+  b += rows_cap * ((int64_t)dpad * 2 + 12);                   // pass A rows
   b += rows_cap * 2 * MAX_C * 8;                             // pass A partial lists
   b += mb * 4 + n_r * 8 + mb * 4;                            // g, rmin, rmax, qkept
   b += window_pair_blocks(mb) * nbins * 4 + nbins * 8 + 4;   // bin counts, totals, offsets
@@ -1480,11 +1561,11 @@ int64_t bound_window_batch(const rbc_index* ix, int64_t mb) {
   b += nslices * arena_lane * 16 + nslices * 4 + 4;          // hit arena
   b += mb * 8 + 64;                                          // fallback rows, counters
   b += max2 * (int64_t)sizeof(EmitItem) + 4;                 // overflow items
-  b += bound_fallback_f32(mb, d, sms);                       // FP32 last resort
+  b += bound_fallback_rbc(ix, mb, k);                       // FP32 exact search of the rest
   return b;
 }
 
-int64_t bound_exact_batch(const rbc_index* ix, int64_t mb) {
+int64_t bound_exact_batch(const rbc_index* ix, int64_t mb, int k, bool f32_only) {
   const int d = ix->d, dpad = ix->dpad, sms = sm_count();
   const int64_t n_r = ix->n_r, n = ix->list_entries;
   const int64_t tiles = cdiv(mb, TQ);
@@ -1501,9 +1582,9 @@ int64_t bound_exact_batch(const rbc_index* ix, int64_t mb) {
   b += (tiles + 1) * 4 + tiles * 4;                          // item offsets
   b += cap_items * (int64_t)sizeof(WorkItem) + tiles * seg_cap * (int64_t)sizeof(Seg) + 4;
   b += cap_items * TQ * 2 * MAX_C * 8 + cap_items * 4;       // partial lists
-  if (uses_lp(ix->storage, ix->metric) && ix->Xlp) {
-    b += mb * ((int64_t)dpad * 2 + 8);                       // low-precision batch
-    b += bound_select_lp(mb, d, dpad, sms);
+  if (!f32_only && uses_lp(ix->storage, ix->metric) && ix->Xlp) {
+    b += mb * ((int64_t)dpad * 2 + 12);                       // low-precision batch
+    b += bound_select_lp(ix, mb, k);
   }
   return b;
 }
@@ -1516,7 +1597,7 @@ int64_t bound_oneshot_stage2(const rbc_index* ix, int64_t mq, bool lp, int level
   int64_t b = bound_group(ix, mq, true);
   b += max_tiles * TQ * 2 * MAX_C * 8 + max_tiles * 4 + 4;   // partial lists, valid, dev_err
   if (lp) {
-    b += rows_cap * ((int64_t)dpad * 2 + 8);                 // low-precision rows
+    b += rows_cap * ((int64_t)dpad * 2 + 12);                 // low-precision rows
     b += rows_cap * 4 + 32;                                  // fallback rows, counters
     b += rows_cap * (8 + 4 + (int64_t)d * 4);                // fallback gather
     if (level == 0) b += bound_oneshot_stage2(ix, rows_cap, false, 1);
@@ -1535,9 +1616,12 @@ int64_t search_batch_size(const rbc_index* ix, bool window) {
   return window ? std::max<int64_t>(TQ, std::min<int64_t>(MAX_BATCH, WINDOW_MAX_PAIRS / ix->n_r))
                 : MAX_BATCH;
 }
+// the windowed plan's emission kernel folds -|x~|^2/2 into the MMA and tests
+// row maxima, which needs one scale per row: FP8 (a scale per column too)
+// takes the tile-union plan
 bool search_uses_window(const rbc_index* ix) {
   return ix->mode == RBC_EXACT && ix->plan == RBC_PLAN_WINDOW && uses_lp(ix->storage, ix->metric) &&
-         ix->Xlp;
+         ix->Xlp && ix->storage != RBC_FP8E4M3;
 }
 
 int64_t search_workspace_bound(const rbc_index* ix, int64_t m, int k) {
@@ -1548,9 +1632,9 @@ int64_t search_workspace_bound(const rbc_index* ix, int64_t m, int k) {
   if (ix->mode == RBC_ONESHOT)
     b += bound_oneshot_batch(ix, mb);
   else if (window)
-    b += bound_window_batch(ix, mb);
+    b += bound_window_batch(ix, mb, k);
   else
-    b += bound_exact_batch(ix, mb);
+    b += bound_exact_batch(ix, mb, k);
   return b;
 }
 
@@ -1644,18 +1728,24 @@ int bf_search(const float* Q, int64_t m, const float* X, int64_t n, int32_t d, i
                          ar, st));
     taccumulate();
   } else {
-    db.dpad = pad64(d);
-    uint16_t* xl;
+    db.dpad = lp_pad(d, storage);
+    uint8_t* xl;
     float* xn;
+    float* xs = nullptr;
     unsigned* mx;
-    RBC_TRY(ar.alloc(&xl, n * db.dpad));
+    RBC_TRY(ar.alloc(&xl, n * db.dpad * lp_elem_bytes(storage)));
     RBC_TRY(ar.alloc(&xn, n + NORM_PAD));
     RBC_CUDA(cudaMemsetAsync(xn + n, 0, NORM_PAD * sizeof(float), st));
+    if (storage == RBC_FP8E4M3) {
+      RBC_TRY(ar.alloc(&xs, n + NORM_PAD));
+      RBC_CUDA(cudaMemsetAsync(xs + n, 0, NORM_PAD * sizeof(float), st));
+    }
     RBC_TRY(ar.alloc(&mx, 2));
     RBC_CUDA(cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned), st));
-    RBC_TRY(launch_to_lowp(Xdev, n, d, db.dpad, storage, xl, xn, nullptr, mx, mx + 1, st));
+    RBC_TRY(launch_to_lowp(Xdev, n, d, db.dpad, storage, xl, xn, nullptr, mx, mx + 1, st, xs));
     db.Xlp = xl;
     db.xnorm = xn;
+    db.xscale = xs;
     db.lp_max = mx;
     RBC_TRY(bf_dense_lp(io.Qdev, m, db, d, k, storage, 0, io.ids_dev, io.dist_dev, cn.c, ar, st));
   }

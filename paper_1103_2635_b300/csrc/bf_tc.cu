@@ -48,6 +48,8 @@ struct TcParams {
   int64_t x_rows;
   int q_rows;
   uint32_t* dev_err;
+  const float* xscale;  // FP8: [rows + pad] per-row scales, readable like xnorm
+  const float* qscale;  // FP8: [q_rows] per-row scales of the queries
 };
 
 __device__ __forceinline__ void item_info(const TileWork& w, int item, int& q0, int& nq, int& sb,
@@ -83,19 +85,21 @@ __device__ __forceinline__ Seg seg_at(const TileWork& w, int si) {
 // past its end are masked to +inf in the epilogue.
 // Each (row, half) keeps C candidates (C = 8, 16 or 32).
 
-template <int C, int KB, int BN, int S, int NR>
+template <int C, int KB, int BN, int S, int NR, bool FP8>
 struct TcSmem {
   static constexpr int NBUF = (512 / BN) < 4 ? (512 / BN) : 4;  // TMEM accumulator buffers
-  static constexpr int Q_BYTES = KB * BM * 128;  // query tile, KB K-blocks of 64 elements
+  static constexpr int Q_BYTES = KB * BM * 128;  // query tile, KB K-blocks of 128 bytes
   static constexpr int X_STAGE = KB * BN * 128;  // one database tile
   static constexpr int NORM_STAGE = BN * 4;
   static constexpr int NEPI_WARPS = NUM_THREADS / 32 - EPI_WARP0;
   static constexpr int OFF_Q = 0;
   static constexpr int OFF_X = OFF_Q + Q_BYTES;
   static constexpr int OFF_NORM = OFF_X + S * X_STAGE;
+  // FP8: the tile's per-row scales, a ring beside the norms
+  static constexpr int OFF_SCALE = OFF_NORM + NR * NORM_STAGE;
   static constexpr int NEPI_THREADS = NEPI_WARPS * 32;
   // per epilogue thread: the columns of its C list entries, entry j at [j][thread]
-  static constexpr int OFF_IDS = OFF_NORM + NR * NORM_STAGE;
+  static constexpr int OFF_IDS = OFF_SCALE + (FP8 ? NR * NORM_STAGE : 0);
   // per epilogue thread: one spilled 32-column chunk
   static constexpr int OFF_SCR = OFF_IDS + C * NEPI_THREADS * 4;
   // per (half, query row): the root score of that half's heap
@@ -111,17 +115,19 @@ struct TcSmem {
 
 // 10 warps: one SM sub-partition hosts three of them, so its 16K-register
 // slice caps a thread at 168 registers (enforced by the launch bound).
-template <int C, int KB, int BN, int S, int NRING>
+template <int C, int KB, int BN, int S, int NRING, bool FP8>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap xmap,
              TcParams p, uint32_t idesc) {
-  using L = TcSmem<C, KB, BN, S, NRING>;
+  using L = TcSmem<C, KB, BN, S, NRING, FP8>;
+  constexpr int KBLOCK = FP8 ? 128 : 64;  // elements per 128-byte K block
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
   uint8_t* sQ = smem + L::OFF_Q;
   uint8_t* sX = smem + L::OFF_X;
   float* sNorm = reinterpret_cast<float*>(smem + L::OFF_NORM);
+  float* sScale = reinterpret_cast<float*>(smem + L::OFF_SCALE);
   int* sIds = reinterpret_cast<int*>(smem + L::OFF_IDS);
   float* sScr = reinterpret_cast<float*>(smem + L::OFF_SCR);
   float* sRoot = reinterpret_cast<float*>(smem + L::OFF_ROOT);
@@ -195,7 +201,8 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
       if (lane == 0) {
         mbar_arrive_expect_tx(qfull, L::Q_BYTES);
 #pragma unroll
-        for (int kb = 0; kb < KB; ++kb) tma_load_2d(sQ + kb * BM * 128, &qmap, qfull, kb * 64, q0);
+        for (int kb = 0; kb < KB; ++kb)
+          tma_load_2d(sQ + kb * BM * 128, &qmap, qfull, kb * KBLOCK, q0);
       }
       for (int si = sb; ok && si < se; ++si) {
         const Seg sg = seg_at(w, si);
@@ -214,9 +221,10 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
             mbar_arrive_expect_tx(&full[s], L::X_STAGE);
 #pragma unroll
             for (int kb = 0; kb < KB; ++kb)
-              tma_load_2d(sX + s * L::X_STAGE + kb * BN * 128, &xmap, &full[s], kb * 64, x);
-            mbar_arrive_expect_tx(&nfull[r], L::NORM_STAGE);
+              tma_load_2d(sX + s * L::X_STAGE + kb * BN * 128, &xmap, &full[s], kb * KBLOCK, x);
+            mbar_arrive_expect_tx(&nfull[r], (FP8 ? 2 : 1) * L::NORM_STAGE);
             bulk_load(sNorm + r * BN, p.xnorm + x, L::NORM_STAGE, &nfull[r]);
+            if (FP8) bulk_load(sScale + r * BN, p.xscale + x, L::NORM_STAGE, &nfull[r]);
           }
           __syncwarp();
         }
@@ -262,9 +270,13 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
             for (int kb = 0; kb < KB; ++kb)
 #pragma unroll
               for (int k16 = 0; k16 < 4; ++k16) {
+                // one K step = 32 bytes (16 bf16 / fp16 or 32 e4m3 elements)
                 uint64_t ad = smem_desc_sw128(qa + kb * BM * 128 + k16 * 32);
                 uint64_t bd = smem_desc_sw128(xb + kb * BN * 128 + k16 * 32);
-                mma_f16(d_tmem, ad, bd, idesc, (kb | k16) != 0);
+                if (FP8)
+                  mma_f8(d_tmem, ad, bd, idesc, (kb | k16) != 0);
+                else
+                  mma_f16(d_tmem, ad, bd, idesc, (kb | k16) != 0);
               }
             mma_commit(&empty[s]);
             mma_commit(&tfull[buf]);
@@ -312,6 +324,8 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
       if (item > ib) item_info(w, item - 1, pq0, pnq, psb, pse, pslot);
       int nq0 = -1, nnq, nsb, nse, nslot;
       if (item + 1 < ie) item_info(w, item + 1, nq0, nnq, nsb, nse, nslot);
+      // FP8: score = |x~|^2 - 2 s_q s_x (a.b); cq = -2 s_q for this row
+      const float cq = FP8 ? (row < nq ? -2.0f * p.qscale[q0 + row] : 0.0f) : -2.0f;
       if (pq0 != q0) {  // first item of a run of the same query tile
 #pragma unroll
         for (int j = 0; j < C; ++j) {
@@ -356,11 +370,25 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
               if (lane == 0) mbar_arrive(&tempty[buf]);
             }
             const float4* n4 = reinterpret_cast<const float4*>(nrm + c0);
+            if (FP8) {
+              // per-column scale: cq * s_x is a power of two times cq, exact
+              const float4* s4 =
+                  reinterpret_cast<const float4*>(sScale + r * BN + half * HALF + c0);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              float4 nn = n4[j];
-              fma2(u[4 * j], u[4 * j + 1], u[4 * j], u[4 * j + 1], -2.0f, nn.x, nn.y);
-              fma2(u[4 * j + 2], u[4 * j + 3], u[4 * j + 2], u[4 * j + 3], -2.0f, nn.z, nn.w);
+              for (int j = 0; j < 8; ++j) {
+                const float4 nn = n4[j], ss = s4[j];
+                u[4 * j] = fmaf(cq * ss.x, u[4 * j], nn.x);
+                u[4 * j + 1] = fmaf(cq * ss.y, u[4 * j + 1], nn.y);
+                u[4 * j + 2] = fmaf(cq * ss.z, u[4 * j + 2], nn.z);
+                u[4 * j + 3] = fmaf(cq * ss.w, u[4 * j + 3], nn.w);
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                float4 nn = n4[j];
+                fma2(u[4 * j], u[4 * j + 1], u[4 * j], u[4 * j + 1], -2.0f, nn.x, nn.y);
+                fma2(u[4 * j + 2], u[4 * j + 3], u[4 * j + 2], u[4 * j + 3], -2.0f, nn.z, nn.w);
+              }
             }
             if (partial) {
 #pragma unroll
@@ -451,12 +479,17 @@ int encode_map(CUtensorMap* map, const void* base, int64_t rows, int dpad, int s
     set_error("cuTensorMapEncodeTiled is not available from the driver");
     return RBC_ERR_CUDA;
   }
+  // 128-byte K blocks: 64 16-bit or 128 FP8 elements
+  const int eb = lp_elem_bytes(storage);
   cuuint64_t dims[2] = {(cuuint64_t)dpad, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)dpad * 2};
-  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)dpad * eb};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / eb), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapDataType ty = storage == RBC_BF16   ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                 : storage == RBC_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                      : CU_TENSOR_MAP_DATA_TYPE_UINT8;
   CUresult r = enc(
-      map, storage == RBC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+      map, ty,
       2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
       CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -493,16 +526,17 @@ int encode_nblock_map(CUtensorMap* map, const void* base, int64_t rows, int box_
 
 namespace {
 
-template <int C, int KB, int BN, int S, int NR>
+template <int C, int KB, int BN, int S, int NR, bool FP8 = false>
 int launch_tc(const LpMatrix& Qm, const LpMatrix& Xm, const TileWork& w, const TopOut& out,
               int grid, cudaStream_t st, uint32_t* dev_err) {
-  using L = TcSmem<C, KB, BN, S, NR>;
+  using L = TcSmem<C, KB, BN, S, NR, FP8>;
   CUtensorMap qmap, xmap;
   RBC_TRY_TC(encode_map(&qmap, Qm.data, Qm.rows, Qm.dpad, Qm.storage, BM));
   RBC_TRY_TC(encode_map(&xmap, Xm.data, Xm.rows, Xm.dpad, Xm.storage, BN));
-  auto kern = bf_tc_kernel<C, KB, BN, S, NR>;
+  auto kern = bf_tc_kernel<C, KB, BN, S, NR, FP8>;
   RBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC));
-  TcParams p{w, out, Xm.norm, Xm.rows, (int)Qm.rows, dev_err};
+  TcParams p{w, out, Xm.norm, Xm.rows, (int)Qm.rows, dev_err, Xm.scale, Qm.scale};
+  // kind::f16: format 1 = bf16, 0 = fp16; kind::f8f6f4: format 0 = E4M3
   uint32_t idesc = idesc_f16(Qm.storage == RBC_BF16 ? 1 : 0, BM, BN);
   kern<<<grid, NUM_THREADS, L::ALLOC, st>>>(qmap, xmap, p, idesc);
   ++t_launches;
@@ -538,6 +572,21 @@ int launch_bf_tc_topc(const LpMatrix& Qm, const LpMatrix& Xm, int C, const TileW
   if (Qm.dpad != Xm.dpad || Qm.storage != Xm.storage) {
     set_error("tensor-core BF: operand layouts differ");
     return RBC_ERR_ARG;
+  }
+  if (Qm.storage == RBC_FP8E4M3) {
+    if (!Qm.scale || !Xm.scale) {
+      set_error("tensor-core BF: FP8 operands need per-row scales");
+      return RBC_ERR_ARG;
+    }
+    const int kb = Qm.dpad / 128;
+    if (C == 8 && kb == 1) return launch_tc<8, 1, 256, 3, 8, true>(Qm, Xm, w, out, grid, st, dev_err);
+    if (C == 8 && kb == 2) return launch_tc<8, 2, 128, 3, 8, true>(Qm, Xm, w, out, grid, st, dev_err);
+    if (C == 16 && kb == 1) return launch_tc<16, 1, 256, 3, 8, true>(Qm, Xm, w, out, grid, st, dev_err);
+    if (C == 16 && kb == 2) return launch_tc<16, 2, 128, 3, 8, true>(Qm, Xm, w, out, grid, st, dev_err);
+    if (C == 32 && kb == 1) return launch_tc<32, 1, 256, 3, 8, true>(Qm, Xm, w, out, grid, st, dev_err);
+    if (C == 32 && kb == 2) return launch_tc<32, 2, 128, 2, 8, true>(Qm, Xm, w, out, grid, st, dev_err);
+    set_error("tensor-core BF: FP8 list width %d / padded dimension %d unsupported", C, Qm.dpad);
+    return RBC_ERR_UNSUPPORTED;
   }
   if (C == 8) {
     switch (Qm.dpad / 64) {

@@ -38,13 +38,17 @@ int launch_bf_simt_store(const float* Q, const float* X, int d, int metric, cons
 
 // ---- low-precision (tensor-core) path ----
 struct LpMatrix {
-  const void* data;  // [rows, dpad] bf16 / f16, row-major, rows 16-byte aligned
+  const void* data;  // [rows, dpad] bf16 / f16 / e4m3, row-major, rows 16-byte aligned
   const float* norm; // [rows] |x~|^2 in FP32
   int64_t rows;
-  int dpad;          // multiple of 64
-  int storage;       // RBC_BF16 / RBC_F16
+  int dpad;          // elements per row: multiple of 64 (16-bit) or 128 (FP8)
+  int storage;       // RBC_BF16 / RBC_F16 / RBC_FP8E4M3
   const void* nblock = nullptr;  // optional [rows, 16] bf16: -|x~|^2 / 2 as (high, low, 0 ...)
+  const float* scale = nullptr;  // FP8: [rows] power-of-two scale, x~ = scale * e4m3 row
 };
+
+// bytes per stored element of a low-precision row
+inline int lp_elem_bytes(int storage) { return storage == RBC_FP8E4M3 ? 1 : 2; }
 
 // columns of a norm block row, and the rows past the end that stay readable
 constexpr int NBLOCK_COLS = 16;
@@ -258,7 +262,7 @@ int launch_gather_rows(const float* src, const int64_t* idx64, const int* idx32,
 // (FP64, rounded up); global maxima of |x - x~| and |x~| as float bits.
 int launch_to_lowp(const float* src, int64_t rows, int d, int dpad, int storage, void* dst,
                    float* norm, float* err, unsigned* err_max_bits, unsigned* norm_max_bits,
-                   cudaStream_t st);
+                   cudaStream_t st, float* scale = nullptr);  // scale: [rows], FP8 only
 // dst row i = src row idx[i] of a bf16 / fp16 [*, dpad] matrix plus its norm
 // and residual; idx[i] < 0 gives a zero row
 int launch_gather_lp_rows(const void* src, const float* snorm, const float* serr, const int* idx,
@@ -273,6 +277,10 @@ int launch_norm_block(const float* norm, int64_t rows, int64_t rows_out, void* d
 // out[i] = qorig ? qorig[rows[i]] : rows[i], for i < *n_dev (or n when n_dev is null)
 int launch_map_rows(const int* rows, const int* n_dev, int n, const int* qorig, int* out,
                     cudaStream_t st);
+// out_ids / out_dist row dst_rows[i] = row i of ids / dist ([rows, k])
+int launch_scatter_result_rows(const int64_t* ids, const float* dist, const int* dst_rows,
+                               int64_t rows, int k, int64_t* out_ids, float* out_dist,
+                               cudaStream_t st);
 
 // ---- index construction / exact-search helpers (rbc_kernels.cu) ----
 // counting sort of `key[i]` in [0, nbins): stable positions.  perm[pos] = i,

@@ -10,10 +10,15 @@
 //   can move under rounding (triangle inequality of the metric:
 //   |rho(q~, x~) - rho(q, x)| <= |q - q~| + |x - x~|), which the exact search
 //   needs to stay exact with low-precision storage.
+// to_fp8: FP32 rows -> FP8 E4M3 rows padded to `dpad` (a multiple of 128) with
+//   a per-row scale s (the row's max |x_i| / 448 rounded up to a power of two,
+//   so x / s and s * e4m3 are exact): x~ = s * e4m3(x / s).  Norm and residual
+//   as above, of the dequantised row x~.
 #include <algorithm>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -89,6 +94,69 @@ __global__ void to_lowp_kernel(const float* __restrict__ src, int64_t rows, int 
   }
 }
 
+// E4M3 rows with a per-row power-of-two scale.  One warp per row.
+__global__ void to_fp8_kernel(const float* __restrict__ src, int64_t rows, int d, int dpad,
+                              uint8_t* __restrict__ dst, float* __restrict__ norm,
+                              float* __restrict__ err, float* __restrict__ scale,
+                              unsigned* err_max_bits, unsigned* norm_max_bits) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= rows) return;
+  const float* a = src + w * d;
+  uint8_t* b = dst + w * dpad;
+  float amax = 0.f;
+  for (int i = lane; i < d; i += 32) amax = fmaxf(amax, fabsf(a[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  // s = 2^ceil(log2(amax / 448)): |x_i| / s <= 448, the largest finite E4M3
+  // (a row whose quotient rounds below a power of two saturates at 448; the
+  // residual below records that error like any other)
+  int e = 0;
+  const float f = frexpf(amax * (1.0f / 448.0f), &e);
+  if (f == 0.5f) e -= 1;
+  const float sc = amax > 0.f ? ldexpf(1.0f, e) : 1.0f;
+  const float inv = 1.0f / sc;  // a power of two: exact
+  float nrm = 0.f;
+  double e2 = 0.0;
+  for (int i = lane; i < dpad; i += 32) {
+    const float v = i < d ? a[i] : 0.f;
+    const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(v * inv, __NV_SATFINITE, __NV_E4M3);
+    b[i] = (uint8_t)q;
+    const float r = sc * __half2float(__half(__nv_cvt_fp8_to_halfraw(q, __NV_E4M3)));
+    nrm = fmaf(r, r, nrm);
+    const double diff = (double)v - (double)r;
+    e2 += diff * diff;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+  }
+  if (lane == 0) {
+    const float er = __double2float_ru(sqrt(e2));
+    norm[w] = nrm;
+    scale[w] = sc;
+    if (err) err[w] = er;
+    if (err_max_bits) atomicMax(err_max_bits, __float_as_uint(er));
+    if (norm_max_bits) atomicMax(norm_max_bits, __float_as_uint(__fsqrt_ru(nrm)));
+  }
+}
+
+// Result rows i of a search over gathered queries go to output row dst[i].
+__global__ void scatter_result_rows_kernel(const int64_t* __restrict__ ids,
+                                           const float* __restrict__ dist,
+                                           const int* __restrict__ dst, int64_t rows, int k,
+                                           int64_t* __restrict__ out_ids,
+                                           float* __restrict__ out_dist) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * k) return;
+  const int64_t r = i / k;
+  const int j = (int)(i - r * k);
+  const int64_t o = (int64_t)dst[r] * k + j;
+  out_ids[o] = ids[i];
+  out_dist[o] = dist[i];
+}
+
 // dst row i = src row idx[i] of a 16-bit [*, dpad] matrix with its norm and
 // residual; idx[i] < 0 gives a zero row (norm 0, residual 0).  One warp per
 // row, 16-byte copies.
@@ -153,11 +221,18 @@ int launch_gather_rows(const float* src, const int64_t* idx64, const int* idx32,
 
 int launch_to_lowp(const float* src, int64_t rows, int d, int dpad, int storage, void* dst,
                    float* norm, float* err, unsigned* err_max_bits, unsigned* norm_max_bits,
-                   cudaStream_t st) {
+                   cudaStream_t st, float* scale) {
   if (rows <= 0) return RBC_OK;
   int64_t threads = rows * 32;
   unsigned blocks = (unsigned)((threads + 255) / 256);
-  if (storage == RBC_BF16)
+  if (storage == RBC_FP8E4M3) {
+    if (!scale || dpad % 128) {
+      set_error("to_lowp: FP8 rows need a scale array and dpad %% 128 == 0 (dpad=%d)", dpad);
+      return RBC_ERR_ARG;
+    }
+    to_fp8_kernel<<<blocks, 256, 0, st>>>(src, rows, d, dpad, static_cast<uint8_t*>(dst), norm,
+                                          err, scale, err_max_bits, norm_max_bits);
+  } else if (storage == RBC_BF16)
     to_lowp_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(
         src, rows, d, dpad, reinterpret_cast<__nv_bfloat16*>(dst), norm, err, err_max_bits,
         norm_max_bits);
@@ -166,6 +241,17 @@ int launch_to_lowp(const float* src, int64_t rows, int d, int dpad, int storage,
                                                    reinterpret_cast<__half*>(dst), norm, err,
                                                    err_max_bits, norm_max_bits);
   RBC_LAUNCH_CHECK("to_lowp_kernel");
+  return RBC_OK;
+}
+
+int launch_scatter_result_rows(const int64_t* ids, const float* dist, const int* dst_rows,
+                               int64_t rows, int k, int64_t* out_ids, float* out_dist,
+                               cudaStream_t st) {
+  if (rows <= 0) return RBC_OK;
+  const int64_t total = rows * k;
+  scatter_result_rows_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+      ids, dist, dst_rows, rows, k, out_ids, out_dist);
+  RBC_LAUNCH_CHECK("scatter_result_rows_kernel");
   return RBC_OK;
 }
 

@@ -101,12 +101,12 @@ def test_bf_on_a_side_stream():
     check_knn(Q, X, ids.cpu().numpy(), dist.cpu().numpy(), o_ids, o_rho)
 
 
-# ---- tensor-core (tcgen05) path: bf16 / fp16 storage, FP32 re-rank, certified ----
+# ---- tensor-core (tcgen05) path: bf16 / fp16 / FP8 E4M3 storage, FP32 re-rank, certified ----
 
-LP = {"bf16": rbc.BF16, "f16": rbc.F16}
+LP = {"bf16": rbc.BF16, "f16": rbc.F16, "fp8": rbc.FP8E4M3}
 
 
-@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("storage", ["bf16", "f16", "fp8"])
 @pytest.mark.parametrize("k", [1, 10])
 def test_bf_tc_iid_n16k_d16(storage, k):
     X, Q = synth.make_workload("iid-n16k-d16", seed=0)
@@ -115,7 +115,7 @@ def test_bf_tc_iid_n16k_d16(storage, k):
     check_knn(Q, X, ids, dist, o_ids, o_rho)
 
 
-@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("storage", ["bf16", "f16", "fp8"])
 @pytest.mark.parametrize("n,m,d,k", [(1000, 1, 3, 1), (4099, 129, 33, 5), (3000, 127, 100, 31), (2500, 257, 128, 3), (70000, 300, 64, 10), (5000, 200, 200, 4), (600, 130, 256, 2)])
 def test_bf_tc_ragged(storage, n, m, d, k):
     X = synth.iid_normal(n, d, 3000 + n)
@@ -135,6 +135,21 @@ def test_bf_tc_subspace_workload():
         o_ids, o_rho = oracle.bf(Q, X, k, "l2")
         check_knn(Q, X, ids, dist, o_ids, o_rho)
         assert st["uncertified"] <= 0.05 * len(Q), st
+
+
+def test_bf_fp8_clusters_scales_and_certification():
+    # clustered rows of very different magnitudes: each row gets its own
+    # power-of-two scale; the scaled dequantisation error enters the bound,
+    # uncertified queries are searched again in FP32, the answer stays exact
+    mod = synth.ClusterModel(d=128, n_clusters=50, seed=3)
+    X = mod.sample(30000, 0)
+    X[:5000] *= 40.0
+    X[5000:10000] *= 0.01
+    Q = np.concatenate([mod.sample(300, 1), X[:50] * 1.001, X[5000:5050] * 0.999]).astype(np.float32)
+    for k in (1, 10):
+        ids, dist = run_bf(Q, X, k, "l2", rbc.FP8E4M3)
+        o_ids, o_rho = oracle.bf(Q, X, k, "l2")
+        check_knn(Q, X, ids, dist, o_ids, o_rho)
 
 
 def test_bf_tc_duplicates_and_ties():

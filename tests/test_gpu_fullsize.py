@@ -109,6 +109,7 @@ def test_fullsize_oneshot(data, metric, storage):
 
 @pytest.mark.parametrize("wl,storage,rerank_c,m,sample", [
     ("clusters1000-n4m-d128", "bf16", 32, None, 500),
+    ("clusters1000-n4m-d128", "fp8", 32, None, 500),
     ("sincos12-n8m-d96", "f16", 0, 20000, 300),
 ])
 def test_fullsize_exact_large(wl, storage, rerank_c, m, sample):
@@ -116,7 +117,7 @@ def test_fullsize_exact_large(wl, storage, rerank_c, m, sample):
     X, Q = synth.make_workload(w, seed=0, m=m)
     sel = np.sort(np.random.default_rng(11).choice(len(Q), sample, replace=False))
     Xd = torch.from_numpy(X).cuda()
-    st = {"bf16": rbc.BF16, "f16": rbc.F16}[storage]
+    st = {"bf16": rbc.BF16, "f16": rbc.F16, "fp8": rbc.FP8E4M3}[storage]
     idx = rbc.rbc_build(Xd, w.n_r, metric=rbc.L2, seed=2, storage=st, rerank_c=rerank_c)
     del Xd
     ids, dist = rbc.rbc_search(idx, torch.from_numpy(Q).cuda(), 10)

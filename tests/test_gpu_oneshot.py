@@ -165,14 +165,15 @@ def test_oneshot_duplicates_exceed_candidate_capacity():
     check_search(X, Q, o, ids, dist, 5, "l2")
 
 
-@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("storage", ["bf16", "f16", "fp8"])
 @pytest.mark.parametrize("k", [1, 10])
 def test_oneshot_search_tensor_cores(storage, k):
     mod = synth.SubspaceModel(d=64, k=8, noise_var=0.01, seed=0)
     X = mod.sample(60000, 0)
     Q = mod.sample(3000, 1)
     n_r, s = 245, 700
-    idx = build(X, n_r, s, storage={"bf16": rbc.BF16, "f16": rbc.F16}[storage], seed=4)
+    idx = build(X, n_r, s, storage={"bf16": rbc.BF16, "f16": rbc.F16, "fp8": rbc.FP8E4M3}[storage],
+                seed=4)
     ids, dist = search(idx, Q, k)
     o = oracle.build_oneshot(X, oracle.sample_reps(len(X), n_r, 4), s)
     check_search(X, Q, o, ids, dist, k, "l2")

@@ -128,7 +128,7 @@ PLANS = [rbc.PLAN_WINDOW, rbc.PLAN_TILE_UNION]
 
 
 @pytest.mark.parametrize("plan", PLANS)
-@pytest.mark.parametrize("storage", [rbc.BF16, rbc.F16])
+@pytest.mark.parametrize("storage", [rbc.BF16, rbc.F16, rbc.FP8E4M3])
 @pytest.mark.parametrize("k", [1, 10])
 def test_exact_search_tc_iid_n16k_d16(storage, k, plan):
     X, Q = synth.make_workload("iid-n16k-d16", seed=0)
@@ -147,6 +147,18 @@ def test_exact_search_tc_ragged(n, m, d, n_r, k, plan):
     ids, dist = search(idx, Q, k)
     o_ids, o_rho = oracle.bf(Q, X, k, "l2")
     check_knn(Q, X, ids, dist, o_ids, o_rho)
+
+
+@pytest.mark.parametrize("n,m,d,n_r,k", [(5000, 300, 5, 71, 3), (3001, 77, 12, 3001, 4), (20000, 513, 100, 141, 7), (1000, 1, 64, 30, 31), (9000, 700, 250, 90, 10)])
+def test_exact_search_fp8_ragged(n, m, d, n_r, k):
+    # FP8 storage always takes the tile-union plan (per-column scales)
+    X = synth.iid_normal(n, d, 10 + n)
+    Q = synth.iid_normal(m, d, 20 + m)
+    idx = build(X, n_r, seed=n_r, storage=rbc.FP8E4M3)
+    ids, dist = search(idx, Q, k)
+    o_ids, o_rho = oracle.bf(Q, X, k, "l2")
+    check_knn(Q, X, ids, dist, o_ids, o_rho)
+    assert idx.info()["storage"] == rbc.FP8E4M3
 
 
 @pytest.mark.parametrize("plan", PLANS)
