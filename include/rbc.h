@@ -409,6 +409,78 @@ int rbc_plan_batch(const int64_t* m, const int32_t* k, int32_t n, int64_t max_ba
                    int64_t mem_left, int64_t fixed_bytes, int64_t bytes_per_query,
                    int64_t bytes_per_query_k);
 
+/* ---------------------------------------------------------------------------
+ * Grouped multi-index search.  No counterpart in the paper, which searches
+ * one database at a time (Sections 5, 7): a group holds many independent
+ * exact indexes (one per tenant, shard, category ...) and searches a batch
+ * of queries for every one of them together.  The indexes' rows, lists,
+ * representatives and radii are concatenated into one resident layout (rows
+ * zero-padded to the widest dimension, which changes no distance), and every
+ * step of the exact search runs once for all indexes: stage one against each
+ * query's own representatives, pruning and work generation per 128-query tile
+ * of one index, ONE persistent tensor-core launch over the work items of all
+ * indexes, one merge / re-rank / certification launch, and an FP32 brute
+ * force over the query's own index for uncertified queries.  No count is read
+ * back to the host inside the search, so each batch shape (the per-index
+ * query counts and k) is captured once as a CUDA graph and replayed.
+ * Results equal those of rbc_search on each index alone.
+ * ------------------------------------------------------------------------- */
+typedef struct rbc_group rbc_group; /* opaque; owned by the library */
+
+typedef struct {
+  int64_t indexes, rows, representatives;
+  int32_t dim;               /* common (padded) row length */
+  int32_t work_item_points;  /* stage-two work-item size of the last search */
+  int64_t queries;           /* queries of the last search */
+  int64_t tiles, work_items; /* its 128-query tiles and stage-two work items */
+  int64_t uncertified;       /* its queries searched again by FP32 brute force */
+  int64_t fp64_ties;         /* its queries whose order needed FP64 */
+  int64_t graph_replays;     /* launches of the batch shape's CUDA graph */
+  uint32_t device_errors;    /* device error flags of the last search (0 = none) */
+} rbc_grouped_stats;
+
+/*
+ * rbc_group_create -- copies `count` built indexes into a new group (the
+ *   indexes may be freed afterwards).  Every index must be exact-mode L2 with
+ *   the same bf16 or fp16 storage, on the same device, d <= 256; the group's
+ *   rows and representatives must each number < 2^31.  Synchronises `stream`.
+ *   Errors: RBC_ERR_ARG (NULL, count < 1, mismatched storage / device),
+ *   RBC_ERR_UNSUPPORTED (mode, metric, FP32 / FP8 storage, sizes), RBC_ERR_OOM.
+ */
+int rbc_group_create(const rbc_index* const* indexes, int32_t count, void* stream,
+                     rbc_group** out);
+
+/*
+ * rbc_group_search -- k nearest neighbours of every query of every index.
+ *   m [count]: HOST array, queries per index (0 allowed).  Q: the queries
+ *   packed index after index, index i's m[i] rows of its own d_i floats
+ *   (sum m_i d_i floats, host or device).  out_ids / out_dist: [sum m_i, k]
+ *   in the same order, ids within each query's own index (host or device).
+ *   The first search of a batch shape builds its workspace and CUDA graph;
+ *   later searches of the same shape replay the graph (inputs and outputs are
+ *   copied through the group's buffers).  Synchronises `stream` once (device
+ *   error flags).  Errors: RBC_ERR_ARG (NULL, m out of range, k outside
+ *   [1, 31], k above an index's size), RBC_ERR_OOM, RBC_ERR_CUDA,
+ *   RBC_ERR_TIMEOUT.
+ */
+int rbc_group_search(rbc_group* g, const float* Q, const int64_t* m, int32_t k, int64_t* out_ids,
+                     float* out_dist, void* stream);
+
+/*
+ * rbc_group_tune -- autotuner: times the search of this batch (3 graph
+ *   replays each, CUDA events) for stage-two work-item sizes of 1024 to
+ *   32768 points and keeps the fastest for later searches; *chosen (may be
+ *   NULL) receives it.  Errors as rbc_group_search.
+ */
+int rbc_group_tune(rbc_group* g, const float* Q, const int64_t* m, int32_t k, void* stream,
+                   int32_t* chosen);
+
+/* rbc_group_stats -- fills *out (reads the last search's device counters). */
+int rbc_group_stats(rbc_group* g, rbc_grouped_stats* out);
+
+/* rbc_group_free -- waits for the device and releases the group. NULL ok. */
+void rbc_group_free(rbc_group* g);
+
 /* rbc_free -- releases the index (waits for its outstanding work). NULL ok. */
 void rbc_free(rbc_index* idx);
 

@@ -27,7 +27,7 @@ __all__ = [
     "L2", "L1", "EXACT", "ONESHOT", "F32", "BF16", "F16", "FP8E4M3", "PLAN_WINDOW", "PLAN_TILE_UNION",
     "RbcError", "bf_search", "bf_search_noalloc", "rbc_build", "rbc_search", "rbc_sample_reps",
     "RbcIndex", "last_stats", "set_timing", "trim_workspace", "library_path", "load",
-    "search_workspace", "plan_batch", "Server",
+    "search_workspace", "plan_batch", "Server", "Group",
 ]
 
 L2, L1 = 0, 1
@@ -67,6 +67,15 @@ class _Stats(ctypes.Structure):
         "boundary_ties", "pairs", "kernel_launches")] + [
         (name, ctypes.c_double) for name in ("stage1_ms", "stage2_ms", "select_ms", "fallback_ms")] + [
         ("candidates", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64)]
+
+
+class _GroupedStats(ctypes.Structure):
+    _fields_ = [("indexes", ctypes.c_int64), ("rows", ctypes.c_int64),
+                ("representatives", ctypes.c_int64), ("dim", ctypes.c_int32),
+                ("work_item_points", ctypes.c_int32), ("queries", ctypes.c_int64),
+                ("tiles", ctypes.c_int64), ("work_items", ctypes.c_int64),
+                ("uncertified", ctypes.c_int64), ("fp64_ties", ctypes.c_int64),
+                ("graph_replays", ctypes.c_int64), ("device_errors", ctypes.c_uint32)]
 
 
 class _ServerOpts(ctypes.Structure):
@@ -131,9 +140,16 @@ def load():
     lib.rbc_server_stats.argtypes = [P, I32, ctypes.POINTER(_ServingStats)]
     lib.rbc_server_destroy.argtypes = [P]
     lib.rbc_server_destroy.restype = None
+    lib.rbc_group_create.argtypes = [P, I32, P, ctypes.POINTER(ctypes.c_void_p)]
+    lib.rbc_group_search.argtypes = [P, P, P, I32, P, P, P]
+    lib.rbc_group_tune.argtypes = [P, P, P, I32, P, ctypes.POINTER(I32)]
+    lib.rbc_group_stats.argtypes = [P, ctypes.POINTER(_GroupedStats)]
+    lib.rbc_group_free.argtypes = [P]
+    lib.rbc_group_free.restype = None
     for f in ("rbc_sample_reps", "bf_search", "bf_search_noalloc", "rbc_build", "rbc_search", "rbc_index_info",
               "rbc_index_export", "rbc_last_stats", "rbc_search_workspace", "rbc_plan_batch",
-              "rbc_server_create", "rbc_server_submit", "rbc_server_wait", "rbc_server_stats"):
+              "rbc_server_create", "rbc_server_submit", "rbc_server_wait", "rbc_server_stats",
+              "rbc_group_create", "rbc_group_search", "rbc_group_tune", "rbc_group_stats"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -390,6 +406,79 @@ class Server:
             load().rbc_server_destroy(self._h)
         self._h = None
         self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Group:
+    """Many exact indexes searched together (rbc_group_*): one resident
+    concatenated layout, one persistent tensor-core launch for the stage two
+    of every index, each batch shape captured once as a CUDA graph."""
+
+    def __init__(self, indexes, stream=None):
+        arr = (ctypes.c_void_p * len(indexes))(*[ix.handle.value for ix in indexes])
+        h = ctypes.c_void_p()
+        _check(load().rbc_group_create(arr, len(indexes), _stream_of(stream, True), ctypes.byref(h)))
+        self._h = h
+        self.dims = [ix.info()["d"] for ix in indexes]
+
+    def _pack(self, Qs):
+        if len(Qs) != len(self.dims):
+            raise ValueError("one query array per index")
+        m = np.array([q.shape[0] for q in Qs], dtype=np.int64)
+        if all(_is_torch(q) and q.is_cuda for q in Qs):
+            import torch
+
+            flat = torch.cat([q.reshape(-1) for q in Qs]).contiguous()
+            dev = flat.device
+        else:
+            flat = np.ascontiguousarray(np.concatenate([np.asarray(q, np.float32).reshape(-1) for q in Qs]))
+            dev = None
+        return flat, m, dev
+
+    def search(self, Qs, k: int, stream=None):
+        """Qs: one [m_i, d_i] float32 array per index (all CUDA tensors, or
+        host arrays).  Returns ([m_i, k] ids, [m_i, k] rho) per index."""
+        flat, m, dev = self._pack(Qs)
+        M = int(m.sum())
+        ids, dist = _outputs(M, k, dev, None, None)
+        fp = flat.data_ptr() if dev is not None else flat.ctypes.data
+        ip = ids.data_ptr() if dev is not None else ids.ctypes.data
+        dp = dist.data_ptr() if dev is not None else dist.ctypes.data
+        _check(load().rbc_group_search(self._h, fp, m.ctypes.data, k, ip, dp,
+                                       _stream_of(stream, dev is not None)))
+        cut = np.concatenate([[0], np.cumsum(m)])
+        return ([ids[cut[i]:cut[i + 1]] for i in range(len(m))],
+                [dist[cut[i]:cut[i + 1]] for i in range(len(m))])
+
+    def tune(self, Qs, k: int, stream=None) -> int:
+        """Autotune the stage-two work-item size on this batch; returns it."""
+        flat, m, dev = self._pack(Qs)
+        fp = flat.data_ptr() if dev is not None else flat.ctypes.data
+        w = ctypes.c_int32(0)
+        _check(load().rbc_group_tune(self._h, fp, m.ctypes.data, k, _stream_of(stream, dev is not None),
+                                     ctypes.byref(w)))
+        return w.value
+
+    def stats(self) -> dict:
+        st = _GroupedStats()
+        _check(load().rbc_group_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in _GroupedStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().rbc_group_free(self._h)
+        self._h = None
 
     def __enter__(self):
         return self

@@ -134,6 +134,28 @@ struct SelectArgs {
 };
 int launch_select(const SelectArgs& a, cudaStream_t st);
 
+// Grouped multi-index search: uncertified rows (padded rows of the grouped
+// query buffer, device-side count) searched by FP32 brute force over their
+// own index, written to output row qorig[row].
+struct GroupFallbackArgs {
+  const int* rows;           // [*num_rows_dev] padded rows
+  const int* num_rows_dev;
+  const float* Q32;          // [padded rows, d] FP32 queries (zero-padded columns)
+  int d;                     // common row length of Q32 and X32
+  const int* qorig;          // padded row -> output row (or -1)
+  const int* tile_index;     // padded row / TQ -> index
+  const int64_t* row_base;   // index -> first row in X32
+  const int64_t* n_of;       // index -> rows
+  const float* X32;          // grouped FP32 rows (list order per index)
+  const int* xid;            // row -> database id within its index
+  int k;
+  int c_out;                 // k + 1 (at most 32)
+  int64_t* out_ids;
+  float* out_dist;
+  int* counters;             // [1] FP64 ties (optional)
+};
+int launch_group_fallback(const GroupFallbackArgs& a, int grid, cudaStream_t st);
+
 // Candidate buffers of the windowed search -> exact k-NN per query.
 constexpr int CAND_CAP = 2048;  // candidates per query
 struct CandSelectArgs {

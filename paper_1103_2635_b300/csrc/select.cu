@@ -463,7 +463,133 @@ int launch_cw(const SelectArgs& a, int64_t grid_rows, cudaStream_t st) {
   return RBC_OK;
 }
 
+// Grouped search fallback: FP32 brute force of each uncertified row over its
+// own index (rows [row_base, row_base + n) of the grouped FP32 matrix), with
+// the re-rank's distance formula, (rho, id) order and FP64 near-ties, so the
+// row's answer has the same form as every certified row's.  One block per
+// row, rows taken from a device-side list.
+constexpr int GFB_THREADS = 128;
+template <int CW>
+__global__ void __launch_bounds__(GFB_THREADS) group_fallback_kernel(GroupFallbackArgs a) {
+  __shared__ float sh_s[CW][GFB_THREADS];
+  __shared__ int sh_i[CW][GFB_THREADS];
+  __shared__ float sq[MAX_D];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nrows = *a.num_rows_dev;
+  const float eps = rerank_eps(a.d);
+  for (int fi = blockIdx.x; fi < nrows; fi += gridDim.x) {
+    const int p = a.rows[fi];  // padded row of the grouped query buffer
+    const int q = a.qorig[p];
+    const int g = a.tile_index[p / TQ];
+    const int64_t rb = a.row_base[g], n = a.n_of[g];
+    for (int i = tid; i < a.d; i += GFB_THREADS) sq[i] = a.Q32[(int64_t)p * a.d + i];
+    __syncthreads();
+    TopList<CW> lst;
+    lst.init();
+    for (int64_t x = tid; x < n; x += GFB_THREADS) {
+      const int row = (int)(rb + x);
+      const float rho = rerank_rho(sq, a.X32 + (int64_t)row * a.d, a.d, RBC_L2);
+      if (lst.admits(rho, row)) lst.insert(rho, row);
+    }
+#pragma unroll
+    for (int j = 0; j < CW; ++j) {
+      sh_s[j][tid] = lst.s[j];
+      sh_i[j][tid] = lst.i[j];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // lane l merges the lists of threads l, l + 32, l + 64, l + 96 ...
+      TopList<CW> m;
+      m.init();
+      for (int t = lane; t < GFB_THREADS; t += 32)
+#pragma unroll
+        for (int j = 0; j < CW; ++j)
+          if (sh_i[j][t] != INT32_MAX && m.admits(sh_s[j][t], sh_i[j][t]))
+            m.insert(sh_s[j][t], sh_i[j][t]);
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < CW; ++j) {
+        sh_s[j][lane] = m.s[j];
+        sh_i[j][lane] = m.i[j];
+      }
+      __syncwarp();
+      // ... then c_out rounds of a warp minimum over the lists' heads
+      int head = 0;
+      float cs = INFINITY;
+      int ci = INT32_MAX;
+      for (int j = 0; j < a.c_out; ++j) {
+        float bv = head < CW ? sh_s[head][lane] : INFINITY;
+        int bi = head < CW ? sh_i[head][lane] : INT32_MAX;
+        int bl = lane;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+          int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+          if (key_lt(ov, oi, ol, bv, bi, bl)) {
+            bv = ov;
+            bi = oi;
+            bl = ol;
+          }
+        }
+        if (lane == bl) ++head;
+        if (lane == j) {
+          cs = bv;
+          ci = bi;
+        }
+      }
+      const bool valid = lane < a.c_out && ci != INT32_MAX && cs != INFINITY;
+      float rho = valid ? cs : INFINITY;
+      int brow = valid ? ci : -1;
+      int oid = valid ? a.xid[ci] : INT32_MAX;
+      // order by (rho, id) with the database ids
+#pragma unroll
+      for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+          float ov = __shfl_xor_sync(0xffffffffu, rho, stride);
+          int oi = __shfl_xor_sync(0xffffffffu, oid, stride);
+          int ob = __shfl_xor_sync(0xffffffffu, brow, stride);
+          bool up = (lane & size) == 0 || size == 32;
+          bool lower = (lane & stride) == 0;
+          bool other_less = pair_lt(ov, oi, rho, oid);
+          bool take = (lower == up) ? other_less : (!other_less && !(ov == rho && oi == oid));
+          if (take) {
+            rho = ov;
+            oid = oi;
+            brow = ob;
+          }
+        }
+      }
+      const unsigned ties = fp64_ties(sq, a.X32, a.d, RBC_L2, a.k, a.c_out, eps, lane, rho, oid, brow);
+      if (lane < a.k && q >= 0) {
+        const bool ok = rho != INFINITY && brow >= 0;
+        a.out_ids[(int64_t)q * a.k + lane] = ok ? (int64_t)oid : (int64_t)-1;
+        a.out_dist[(int64_t)q * a.k + lane] = ok ? rho : INFINITY;
+      }
+      if (lane == 0 && ties && a.counters) atomicAdd(&a.counters[1], 1);
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+int launch_group_fallback(const GroupFallbackArgs& a, int grid, cudaStream_t st) {
+  if (a.k < 1 || a.c_out < a.k || a.c_out > 32 || a.d > MAX_D) {
+    set_error("group fallback: bad k=%d c_out=%d d=%d", a.k, a.c_out, a.d);
+    return RBC_ERR_ARG;
+  }
+  if (grid <= 0) return RBC_OK;
+  if (a.c_out <= 8)
+    group_fallback_kernel<8><<<grid, GFB_THREADS, 0, st>>>(a);
+  else if (a.c_out <= 16)
+    group_fallback_kernel<16><<<grid, GFB_THREADS, 0, st>>>(a);
+  else
+    group_fallback_kernel<32><<<grid, GFB_THREADS, 0, st>>>(a);
+  RBC_LAUNCH_CHECK("group_fallback_kernel");
+  return RBC_OK;
+}
 
 int launch_select_cands(const CandSelectArgs& a, cudaStream_t st) {
   if (a.k < 1 || a.c_out < a.k || a.c_out > 32 || a.cap != CAND_CAP) {
