@@ -645,8 +645,11 @@ def run_group(args, rank, world, local):
     Qh = [np.ascontiguousarray(Q) for Q in Qs]
     t_e2e = timed(lambda: g.search(Qh, k), max(3, args.steps // 3), 1)
     # parity: every index alone on the GPU, and the FP64 oracle on sampled rows
+    # (this search is marked as an NVTX range, for profiler launch lists)
+    torch.cuda.nvtx.range_push("group_search")
     ids, dist = g.search(Qd, k)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     import oracle
 
     alone_equal = 0

@@ -72,6 +72,14 @@ __device__ __forceinline__ void item_info(const TileWork& w, int item, int& q0, 
   }
 }
 
+// K blocks the item multiplies: all KB unless the work names fewer per tile
+template <int KB>
+__device__ __forceinline__ int item_kb(const TileWork& w, int item) {
+  if (!w.tile_kb || !w.items) return KB;
+  const int v = w.tile_kb[w.items[item].tile];
+  return v < 1 ? 1 : (v > KB ? KB : v);
+}
+
 __device__ __forceinline__ Seg seg_at(const TileWork& w, int si) {
   if (w.segs) return w.segs[si];
   int64_t b = (int64_t)si * w.dense_chunk;
@@ -198,11 +206,12 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
         ok = false;
         break;
       }
+      const int kbn = item_kb<KB>(w, item);
       if (lane == 0) {
-        mbar_arrive_expect_tx(qfull, L::Q_BYTES);
+        mbar_arrive_expect_tx(qfull, kbn * BM * 128);
 #pragma unroll
         for (int kb = 0; kb < KB; ++kb)
-          tma_load_2d(sQ + kb * BM * 128, &qmap, qfull, kb * KBLOCK, q0);
+          if (kb < kbn) tma_load_2d(sQ + kb * BM * 128, &qmap, qfull, kb * KBLOCK, q0);
       }
       for (int si = sb; ok && si < se; ++si) {
         const Seg sg = seg_at(w, si);
@@ -218,10 +227,11 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
             break;
           }
           if (lane == 0) {
-            mbar_arrive_expect_tx(&full[s], L::X_STAGE);
+            mbar_arrive_expect_tx(&full[s], kbn * BN * 128);
 #pragma unroll
             for (int kb = 0; kb < KB; ++kb)
-              tma_load_2d(sX + s * L::X_STAGE + kb * BN * 128, &xmap, &full[s], kb * KBLOCK, x);
+              if (kb < kbn)
+                tma_load_2d(sX + s * L::X_STAGE + kb * BN * 128, &xmap, &full[s], kb * KBLOCK, x);
             mbar_arrive_expect_tx(&nfull[r], (FP8 ? 2 : 1) * L::NORM_STAGE);
             bulk_load(sNorm + r * BN, p.xnorm + x, L::NORM_STAGE, &nfull[r]);
             if (FP8) bulk_load(sScale + r * BN, p.xscale + x, L::NORM_STAGE, &nfull[r]);
@@ -248,6 +258,7 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
         ok = false;
         break;
       }
+      const int kbn = item_kb<KB>(w, item);
       for (int si = sb; ok && si < se; ++si) {
         const Seg sg = seg_at(w, si);
         for (int x = sg.x_begin & ~3; x < sg.x_end; x += BN, ++it) {
@@ -270,6 +281,7 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
             for (int kb = 0; kb < KB; ++kb)
 #pragma unroll
               for (int k16 = 0; k16 < 4; ++k16) {
+                if (kb >= kbn) continue;
                 // one K step = 32 bytes (16 bf16 / fp16 or 32 e4m3 elements)
                 uint64_t ad = smem_desc_sw128(qa + kb * BM * 128 + k16 * 32);
                 uint64_t bd = smem_desc_sw128(xb + kb * BN * 128 + k16 * 32);

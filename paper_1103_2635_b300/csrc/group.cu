@@ -12,8 +12,9 @@
 //     representatives, list offsets and radii are concatenated, each row
 //     zero-padded to the group's widest dimension (zeros change no distance);
 //     list offsets are global rows, representative ids global ordinals;
-//   * stage one, BF(Q_i, R_i): one kernel over all queries, each against its
-//     own index's representatives only; gamma_1, gamma_k, nearest rep;
+//   * stage one, BF(Q_i, R_i): one launch of the register-tiled FP32 kernel
+//     over work items of 128 queries of one index against that index's
+//     representatives; gamma_1, gamma_k, nearest rep;
 //   * queries ordered by (index, nearest representative), each index's run
 //     padded to whole 128-query tiles, so a tile never mixes indexes;
 //   * pruning (Section 5.2, generalised to k) and work generation per tile
@@ -46,7 +47,6 @@
 namespace rbc {
 namespace {
 
-constexpr int GROUP_STAGE1_THREADS = 128;
 constexpr int GROUP_PRUNE_WARPS = 8;
 constexpr int64_t GROUP_NORM_PAD = 512;  // rows past the end the tensor-core kernel may read
 
@@ -77,33 +77,16 @@ __global__ void group_pad_queries_kernel(const float* __restrict__ Q, const int*
   for (int i = lane; i < DG; i += 32) Qp[w * DG + i] = i < d ? src[i] : 0.f;
 }
 
-// Stage one for every query: D[q, r] = rho(q, r) over its own index's
-// representatives (FP32, sequential sums over the index's d coordinates),
-// +inf past the index's n_r.  One block per query.
-__global__ void __launch_bounds__(GROUP_STAGE1_THREADS)
-group_stage1_kernel(const float* __restrict__ Qp, const int* __restrict__ row_index,
-                    const float* __restrict__ R32, const int* __restrict__ rep_base,
-                    const int* __restrict__ nr_of, const int* __restrict__ d_of, int DG, int NRMAX,
-                    float* __restrict__ D) {
-  __shared__ float sq[MAX_D];
-  const int64_t q = blockIdx.x;
-  const int g = row_index[q];
-  const int d = d_of[g], nr = nr_of[g], rb = rep_base[g];
-  for (int i = threadIdx.x; i < d; i += blockDim.x) sq[i] = Qp[q * DG + i];
-  __syncthreads();
-  for (int r = threadIdx.x; r < NRMAX; r += blockDim.x) {
-    float v = INFINITY;
-    if (r < nr) {
-      const float* x = R32 + (int64_t)(rb + r) * DG;
-      float s = 0.f;
-      for (int i = 0; i < d; ++i) {
-        const float t = sq[i] - x[i];
-        s = fmaf(t, t, s);
-      }
-      v = sqrtf(s);
-    }
-    D[q * NRMAX + r] = v;
-  }
+// Stage one runs as the register-tiled FP32 kernel over work items (one per
+// 128 packed queries of an index, against that index's representatives: one
+// segment), which writes D[q, local r]; the columns past the index's n_r are
+// set to +inf here.
+__global__ void group_fill_pad_kernel(const int* __restrict__ row_index, const int* __restrict__ nr_of,
+                                      int64_t M, int NRMAX, float* __restrict__ D) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= M) return;
+  for (int r = nr_of[row_index[w]] + lane; r < NRMAX; r += 32) D[w * NRMAX + r] = INFINITY;
 }
 
 // Queries ordered by (index, nearest representative): a stable counting sort
@@ -260,6 +243,10 @@ struct Plan {
   std::vector<void*> dev;  // device allocations
   // device arrays
   int *row_index = nullptr, *tile_index = nullptr, *tile_item_cap = nullptr;
+  int8_t* tile_kb = nullptr;   // per tile: 64-column K blocks holding its index's columns
+  WorkItem* items1 = nullptr;  // stage one: 128 packed queries of one index x its reps
+  Seg* segs1 = nullptr;        // stage one: index i's representatives
+  int64_t items1_n = 0;
   int64_t *q_row_base = nullptr, *q_elem_base = nullptr, *pad_base = nullptr, *m_of = nullptr;
   float *Qin = nullptr, *Qp = nullptr, *D = nullptr, *g1 = nullptr, *gk = nullptr, *Qs = nullptr;
   int64_t *nearest = nullptr, *key = nullptr;
@@ -379,8 +366,17 @@ int make_plan(rbc_group* g, const std::vector<int64_t>& m, int k, int W, cudaStr
   const int n = g->count;
   std::vector<int64_t> q_row_base(n), q_elem_base(n), pad_base(n);
   std::vector<int> row_index, tile_index, tile_cap;
+  std::vector<int8_t> tile_kb;
+  std::vector<WorkItem> items1;
+  std::vector<Seg> segs1;
   int64_t M = 0, E = 0, MP = 0, cap_total = 0, cap_max = 1;
   for (int i = 0; i < n; ++i) {
+    segs1.push_back(Seg{g->rep_base[i], g->rep_base[i] + g->nr_of[i]});
+    for (int64_t j = 0; j < m[i]; j += TQ) {
+      const int it = (int)items1.size();
+      items1.push_back(WorkItem{(int32_t)(M + j), (int32_t)std::min<int64_t>(TQ, m[i] - j), i, i + 1,
+                                it, it});
+    }
     q_row_base[i] = M;
     q_elem_base[i] = E;
     pad_base[i] = MP;
@@ -389,6 +385,7 @@ int make_plan(rbc_group* g, const std::vector<int64_t>& m, int k, int W, cudaStr
     for (int64_t t = 0; t < ti; ++t) {
       tile_index.push_back(i);
       tile_cap.push_back((int)cap);
+      tile_kb.push_back((int8_t)((g->d_of[i] + 63) / 64));
     }
     for (int64_t r = 0; r < m[i]; ++r) row_index.push_back(i);
     cap_total += ti * cap;
@@ -414,8 +411,12 @@ int make_plan(rbc_group* g, const std::vector<int64_t>& m, int k, int W, cudaStr
   Plan& p = *P;
   std::vector<int64_t> m64(m.begin(), m.end());
   G_TRY(upload(p, &p.row_index, row_index, st));
+  G_TRY(upload(p, &p.items1, items1, st));
+  G_TRY(upload(p, &p.segs1, segs1, st));
+  p.items1_n = (int64_t)items1.size();
   G_TRY(upload(p, &p.tile_index, tile_index, st));
   G_TRY(upload(p, &p.tile_item_cap, tile_cap, st));
+  G_TRY(upload(p, &p.tile_kb, tile_kb, st));
   G_TRY(upload(p, &p.q_row_base, q_row_base, st));
   G_TRY(upload(p, &p.q_elem_base, q_elem_base, st));
   G_TRY(upload(p, &p.pad_base, pad_base, st));
@@ -471,9 +472,20 @@ int run_plan(rbc_group* g, Plan& p, cudaStream_t st) {
   group_pad_queries_kernel<<<(unsigned)cdiv64(M * 32, 256), 256, 0, st>>>(
       p.Qin, p.row_index, p.q_row_base, p.q_elem_base, g->d_of_d, M, DG, p.Qp);
   RBC_LAUNCH_CHECK("group_pad_queries_kernel");
-  group_stage1_kernel<<<(unsigned)M, GROUP_STAGE1_THREADS, 0, st>>>(
-      p.Qp, p.row_index, g->R32, g->rep_base_d, g->nr_of_d, g->d_of_d, DG, NRMAX, p.D);
-  RBC_LAUNCH_CHECK("group_stage1_kernel");
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+  // stage one, BF(Q_i, R_i) for every index: FP32, every distance kept
+  group_fill_pad_kernel<<<(unsigned)cdiv64(M * 32, 256), 256, 0, st>>>(p.row_index, g->nr_of_d, M,
+                                                                       NRMAX, p.D);
+  RBC_LAUNCH_CHECK("group_fill_pad_kernel");
+  TileWork w1{};
+  w1.items = p.items1;
+  w1.num_items = (int)p.items1_n;
+  w1.segs = p.segs1;
+  w1.m = M;
+  w1.n = g->R;
+  G_TRY(launch_bf_simt_store(p.Qp, g->R32, DG, RBC_L2, w1, p.D, NRMAX,
+                             (int)std::min<int64_t>(p.items1_n, (int64_t)sms * 2 * 16), st));
   G_TRY(launch_row_stats(p.D, M, NRMAX, p.k, p.g1, p.gk, p.nearest, st));
   G_TRY(launch_counting_sort(p.nearest, M, NRMAX, p.perm1, p.qoff, p.scratch, st));
   group_key2_kernel<<<(unsigned)cdiv64(M, 256), 256, 0, st>>>(p.perm1, p.row_index, M, p.key);
@@ -506,10 +518,9 @@ int run_plan(rbc_group* g, Plan& p, cudaStream_t st) {
   w.segs = p.segs;
   w.m = MP;
   w.n = g->N;
+  w.tile_kb = p.tile_kb;  // an index of d <= 64 multiplies one K block, not two
   LpMatrix Qm{p.qlp, p.qnorm, MP, g->dpad, g->storage};
   LpMatrix Xm{g->Xlp, g->xnorm, g->N, g->dpad, g->storage};
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
   G_TRY(launch_bf_tc_topc(Qm, Xm, p.C, w, TopOut{p.ps, p.pi, p.pv}, sms, st, p.dev_err));
   // merge + FP32 re-rank + certification + FP64 ties for every query
   SelectArgs a{};

@@ -21,6 +21,9 @@ struct TileWork {
   int64_t n;
   int dense_splits;
   int64_t dense_chunk;
+  // optional (tensor-core kernels, list form): K blocks of 64 columns that
+  // item tile t multiplies (the rest of its rows are zero); nullptr = all
+  const int8_t* tile_kb = nullptr;
 };
 
 // Per-(slot, query row, sub-list) top-C output of a tile kernel.
