@@ -1342,11 +1342,13 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   RBC_CUDA(cudaMemsetAsync(arena_cnt, 0, nslices * sizeof(int), st));
   RBC_TRY(ar.alloc(&arena_ovf, 1));
   int* fb_rows;
-  int *lc, *lc2, *fb2;
+  int *lc, *lc2, *fb2, *srows, *srows2;
   RBC_TRY(ar.alloc(&fb_rows, mb));
   RBC_TRY(ar.alloc(&lc, 8));
   RBC_TRY(ar.alloc(&fb2, mb));
   RBC_TRY(ar.alloc(&lc2, 8));
+  RBC_TRY(ar.alloc(&srows, mb));  // queries whose survivors are re-ranked in a stream
+  RBC_TRY(ar.alloc(&srows2, mb));
   const int xspan = (int)std::max<int64_t>(4096, (n + 2 * sms - 1) / (2 * sms) / 256 * 256);
   const int nsplit = (int)((n + xspan - 1) / xspan);
   const int max2 = (int)std::min<int64_t>((mb + TQ - 1) / TQ * nsplit, INT32_MAX);
@@ -1375,6 +1377,8 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   a.out_dist = dist;
   a.fallback_rows = fb_rows;
   a.counters = lc;
+  a.stream_rows = srows;
+  a.stream_count = lc + 4;
   for (int attempt = 0;; ++attempt) {
     const bool direct = attempt > 0;
     RBC_CUDA(cudaMemsetAsync(cc, 0, mb * sizeof(int), st));
@@ -1396,8 +1400,10 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
       RBC_TRY(launch_scatter_hits(arena, arena_lane, arena_cnt, (int)nslices, cs, cr, cc,
                                   CAND_CAP, st));
     tmark(2, st);
-    // exact re-rank of the candidates; overflowing queries are collected
+    // exact re-rank of the candidates; overflowing queries are collected,
+    // queries with more survivors than shared memory holds are streamed
     RBC_TRY(launch_select_cands(a, st));
+    RBC_TRY(launch_select_stream(a, (int)mb, st));
     tmark(3, st);
     int early[3] = {0, 0, 0};  // overflowing rows, device error flags, arena overflow
     RBC_CUDA(cudaMemcpyAsync(&early[0], lc, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1432,7 +1438,10 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
     a2.nrows = (int)mb;
     a2.fallback_rows = fb2;
     a2.counters = lc2;
+    a2.stream_rows = srows2;
+    a2.stream_count = lc2 + 4;
     RBC_TRY(launch_select_cands(a2, st));
+    RBC_TRY(launch_select_stream(a2, (int)mb, st));
     int host[2] = {0, 0};  // rows left for the FP32 search, device error flags
     RBC_CUDA(cudaMemcpyAsync(&host[0], lc2, sizeof(int), cudaMemcpyDeviceToHost, st));
     RBC_CUDA(cudaMemcpyAsync(&host[1], dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -1514,7 +1523,7 @@ int64_t bound_window_batch(const rbc_index* ix, int64_t mb, int k) {
   b += n_r * 8 + 4 + (mb * n_r / TQ + n_r) * (int64_t)sizeof(EmitItem);  // chunks, items
   b += mb * (int64_t)CAND_CAP * 8 + mb * 4;                  // candidate buffers
   b += nslices * arena_lane * 16 + nslices * 4 + 4;          // hit arena
-  b += mb * 8 + 64;                                          // fallback rows, counters
+  b += mb * 16 + 64;                                         // fallback / stream rows, counters
   b += max2 * (int64_t)sizeof(EmitItem) + 4;                 // overflow items
   b += bound_fallback_rbc(ix, mb, k);                       // FP32 exact search of the rest
   return b;

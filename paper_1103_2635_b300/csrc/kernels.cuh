@@ -160,7 +160,7 @@ struct GroupFallbackArgs {
 int launch_group_fallback(const GroupFallbackArgs& a, int grid, cudaStream_t st);
 
 // Candidate buffers of the windowed search -> exact k-NN per query.
-constexpr int CAND_CAP = 2048;  // candidates per query
+constexpr int CAND_CAP = 8192;  // candidates per query
 struct CandSelectArgs {
   const float* cand_score;  // [m, cap]
   const int* cand_row;      // [m, cap] list-ordered database rows
@@ -185,8 +185,17 @@ struct CandSelectArgs {
   float* out_dist;
   int* fallback_rows;  // queries sent to the FP32 re-search are appended here
   int* counters;       // [0] such queries, [1] fp64 ties, [2] boundary ties
+  // optional: queries with more survivors than the shared-memory re-rank
+  // holds are appended here (count in *stream_count) for launch_select_stream
+  // instead of going to the re-search
+  int* stream_rows = nullptr;
+  int* stream_count = nullptr;
 };
 int launch_select_cands(const CandSelectArgs& a, cudaStream_t st);
+// The queries a.stream_rows[0 .. *a.stream_count) of a launch_select_cands:
+// every survivor re-ranked in FP32 in a stream (one warp per query, k + 1
+// best kept per lane), FP64 ties, output.  max_rows bounds the count.
+int launch_select_stream(const CandSelectArgs& a, int max_rows, cudaStream_t st);
 
 
 // ---- windowed exact search (window.cu) ----

@@ -372,7 +372,11 @@ __global__ void __launch_bounds__(WARPS * 32) select_cands_kernel(CandSelectArgs
     nre += __popc(bal);
   }
   if (nre > RERANK_MAX) {
-    to_research();
+    if (a.stream_rows) {
+      if (lane == 0) a.stream_rows[atomicAdd(a.stream_count, 1)] = (int)q;
+    } else {
+      to_research();
+    }
     return;
   }
   __syncwarp();
@@ -573,7 +577,136 @@ __global__ void __launch_bounds__(GFB_THREADS) group_fallback_kernel(GroupFallba
   }
 }
 
+// Queries whose survivors (candidates scoring <= score_bound(U)) outnumber
+// the shared-memory re-rank: one warp per query streams every survivor
+// through the FP32 re-rank.  Each lane keeps its CW best (CW >= c_out, so
+// the lanes together hold the query's c_out best for sure), then c_out
+// rounds of a warp minimum rank them, then FP64 ties and the output as in
+// select_cands.
+template <int CW>
+__global__ void __launch_bounds__(WARPS * 32) select_stream_kernel(CandSelectArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = *a.stream_count;
+  const int k = a.k, d = a.d;
+  const float xe = __uint_as_float(*a.x_err_max_bits), xn = __uint_as_float(*a.x_norm_max_bits);
+  for (int64_t wi = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5); wi < nw;
+       wi += (int64_t)gridDim.x * WARPS) {
+    const int64_t q = a.stream_rows[wi];
+    const int cnt = min(a.cand_cnt[q], a.cap);
+    const float* sc = a.cand_score + q * a.cap;
+    const int* cr = a.cand_row + q * a.cap;
+    // k-th smallest score -> survivor bound (as in select_cands)
+    unsigned kth = 0;
+    for (int bit = 31; bit >= 0; --bit) {
+      const unsigned t = kth | (1u << bit);
+      int c = 0;
+      for (int e = lane; e < cnt; e += 32) c += score_key(sc[e]) < t;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+      if (c < k) kth = t;
+    }
+    const float qn = a.q_lpnorm[q], qe = a.q_err[q];
+    const float smax =
+        score_bound(dist_upper(key_score(kth), qn, qe, xe, xn, d), qn, qe, xe, xn, d);
+    const float* qr = a.Q32 + q * d;
+    float ls[CW];
+    int li[CW], lr[CW];
+#pragma unroll
+    for (int j = 0; j < CW; ++j) {
+      ls[j] = INFINITY;
+      li[j] = INT32_MAX;
+      lr[j] = -1;
+    }
+    for (int e = lane; e < cnt; e += 32) {
+      if (!(sc[e] <= smax)) continue;
+      const int row = cr[e];
+      float v = rerank_rho(qr, a.X32 + (int64_t)row * d, d, a.metric);
+      int id = a.xid ? a.xid[row] : row;
+      if (!pair_lt(v, id, ls[CW - 1], li[CW - 1])) continue;
+      int rw = row;
+#pragma unroll
+      for (int j = 0; j < CW; ++j) {
+        const bool lt2 = pair_lt(v, id, ls[j], li[j]);
+        const float ts = lt2 ? ls[j] : v;
+        const int ti = lt2 ? li[j] : id;
+        const int tr = lt2 ? lr[j] : rw;
+        ls[j] = lt2 ? v : ls[j];
+        li[j] = lt2 ? id : li[j];
+        lr[j] = lt2 ? rw : lr[j];
+        v = ts;
+        id = ti;
+        rw = tr;
+      }
+    }
+    int head = 0;
+    float rho = INFINITY;
+    int oid = INT32_MAX, brow = -1;
+    for (int j = 0; j < a.c_out; ++j) {
+      float hv = INFINITY;
+      int hi = INT32_MAX, hr = -1;
+#pragma unroll
+      for (int t = 0; t < CW; ++t)
+        if (t == head) {
+          hv = ls[t];
+          hi = li[t];
+          hr = lr[t];
+        }
+      float bv = hv;
+      int bi = hi, bl = lane;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+        if (key_lt(ov, oi, ol, bv, bi, bl)) {
+          bv = ov;
+          bi = oi;
+          bl = ol;
+        }
+      }
+      const int br = __shfl_sync(0xffffffffu, hr, bl);
+      if (lane == bl) ++head;
+      if (lane == j) {
+        rho = bv;
+        oid = bi;
+        brow = bv == INFINITY ? -1 : br;
+      }
+    }
+    const float eps = rerank_eps(d);
+    const unsigned tie_mask = fp64_ties(qr, a.X32, d, a.metric, k, a.c_out, eps, lane, rho, oid,
+                                        brow);
+    if (lane < k) {
+      const bool ok = rho != INFINITY && brow >= 0;
+      a.out_ids[q * k + lane] = ok ? (int64_t)oid : (int64_t)-1;
+      a.out_dist[q * k + lane] = ok ? rho : INFINITY;
+    }
+    if (lane == 0) {
+      if (tie_mask) atomicAdd(&a.counters[1], 1);
+      if (tie_mask & (1u << (k - 1))) atomicAdd(&a.counters[2], 1);
+    }
+  }
+}
+
 }  // namespace
+
+int launch_select_stream(const CandSelectArgs& a, int max_rows, cudaStream_t st) {
+  if (!a.stream_rows || !a.stream_count || max_rows <= 0) return RBC_OK;
+  if (a.k < 1 || a.c_out < a.k || a.c_out > 32) {
+    set_error("select_stream: bad k=%d c_out=%d", a.k, a.c_out);
+    return RBC_ERR_ARG;
+  }
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // device-side count: a grid that covers the SMs, each warp striding over rows
+  const int grid = (int)std::min<int64_t>((max_rows + WARPS - 1) / WARPS, (int64_t)sms * 8);
+  if (a.c_out <= 16)
+    select_stream_kernel<16><<<grid, WARPS * 32, 0, st>>>(a);
+  else
+    select_stream_kernel<32><<<grid, WARPS * 32, 0, st>>>(a);
+  RBC_LAUNCH_CHECK("select_stream_kernel");
+  return RBC_OK;
+}
 
 int launch_group_fallback(const GroupFallbackArgs& a, int grid, cudaStream_t st) {
   if (a.k < 1 || a.c_out < a.k || a.c_out > 32 || a.d > MAX_D) {

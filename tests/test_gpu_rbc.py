@@ -216,13 +216,28 @@ def test_exact_search_multi_batch_with_recheck(plan):
     np.testing.assert_array_equal(ids[on[:300]], o_ids[np.searchsorted(sel, on[:300])])
 
 
-def test_window_candidate_overflow_goes_to_fp32_research():
-    # 700 copies of one point: a query on it has 700 points at distance 0,
-    # more than a candidate buffer holds, so it is searched again in FP32
+def test_window_many_tied_candidates_are_streamed():
+    # 700 copies of one point: a query on it has 700 survivors at distance 0,
+    # more than the shared-memory re-rank holds; they are re-ranked in a
+    # stream (no FP32 re-search) and the ties go to the smallest ids
     X = synth.iid_normal(20000, 24, 3)
     X[5000:5700] = X[5000]
     Q = np.concatenate([X[5000:5001].repeat(3, 0), synth.iid_normal(300, 24, 4)]).astype(np.float32)
     idx = build(X, 140, storage=rbc.BF16, seed=6)
+    ids, dist = search(idx, Q, 10)
+    assert rbc.last_stats()["uncertified"] == 0
+    o_ids, o_rho = oracle.bf(Q, X, 10, "l2")
+    check_knn(Q, X, ids, dist, o_ids, o_rho)
+    np.testing.assert_array_equal(ids[:3], np.tile(np.arange(5000, 5010), (3, 1)))
+
+
+def test_window_candidate_overflow_goes_to_fp32_research():
+    # 9000 copies of one point: more candidates than a query's buffer holds
+    # (8192), so those queries are searched again in FP32
+    X = synth.iid_normal(30000, 24, 3)
+    X[5000:14000] = X[5000]
+    Q = np.concatenate([X[5000:5001].repeat(3, 0), synth.iid_normal(300, 24, 4)]).astype(np.float32)
+    idx = build(X, 170, storage=rbc.BF16, seed=6)
     ids, dist = search(idx, Q, 10)
     assert rbc.last_stats()["uncertified"] >= 3
     o_ids, o_rho = oracle.bf(Q, X, 10, "l2")
