@@ -481,12 +481,13 @@ __global__ void scatter_hits_kernel(const int4* __restrict__ arena, int arena_se
                                     const int* __restrict__ arena_cnt, int64_t nseg,
                                     float* __restrict__ cand_score, int* __restrict__ cand_row,
                                     int* __restrict__ cand_cnt, int cap) {
-  // one thread per slice, looping over its records
-  const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per slice, its lanes over the slice's records
+  const int64_t seg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (seg >= nseg) return;
   const int n = arena_cnt[seg];
   const int4* a = arena + seg * arena_seg;
-  for (int i = 0; i < n; ++i) {
+  for (int i = lane; i < n; i += 32) {
     const int4 h = a[i];
     const int pos = atomicAdd(&cand_cnt[h.x], 1);
     if (pos < cap) {
@@ -622,7 +623,7 @@ int launch_scatter_hits(const int4* arena, int arena_seg, const int* arena_cnt, 
                         float* cand_score, int* cand_row, int* cand_cnt, int cap,
                         cudaStream_t st) {
   if (nseg <= 0) return RBC_OK;
-  scatter_hits_kernel<<<(unsigned)((nseg + 255) / 256), 256, 0, st>>>(
+  scatter_hits_kernel<<<(unsigned)((nseg * 32 + 255) / 256), 256, 0, st>>>(
       arena, arena_seg, arena_cnt, nseg, cand_score, cand_row, cand_cnt, cap);
   RBC_LAUNCH_CHECK("scatter_hits_kernel");
   return RBC_OK;
