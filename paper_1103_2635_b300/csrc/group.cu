@@ -244,6 +244,7 @@ struct Plan {
   // device arrays
   int *row_index = nullptr, *tile_index = nullptr, *tile_item_cap = nullptr;
   int8_t* tile_kb = nullptr;   // per tile: 64-column K blocks holding its index's columns
+  int16_t* tile_dim = nullptr; // per tile: its index's dimension
   WorkItem* items1 = nullptr;  // stage one: 128 packed queries of one index x its reps
   Seg* segs1 = nullptr;        // stage one: index i's representatives
   int64_t items1_n = 0;
@@ -367,6 +368,7 @@ int make_plan(rbc_group* g, const std::vector<int64_t>& m, int k, int W, cudaStr
   std::vector<int64_t> q_row_base(n), q_elem_base(n), pad_base(n);
   std::vector<int> row_index, tile_index, tile_cap;
   std::vector<int8_t> tile_kb;
+  std::vector<int16_t> tile_dim;
   std::vector<WorkItem> items1;
   std::vector<Seg> segs1;
   int64_t M = 0, E = 0, MP = 0, cap_total = 0, cap_max = 1;
@@ -386,6 +388,7 @@ int make_plan(rbc_group* g, const std::vector<int64_t>& m, int k, int W, cudaStr
       tile_index.push_back(i);
       tile_cap.push_back((int)cap);
       tile_kb.push_back((int8_t)((g->d_of[i] + 63) / 64));
+      tile_dim.push_back((int16_t)g->d_of[i]);
     }
     for (int64_t r = 0; r < m[i]; ++r) row_index.push_back(i);
     cap_total += ti * cap;
@@ -417,6 +420,7 @@ int make_plan(rbc_group* g, const std::vector<int64_t>& m, int k, int W, cudaStr
   G_TRY(upload(p, &p.tile_index, tile_index, st));
   G_TRY(upload(p, &p.tile_item_cap, tile_cap, st));
   G_TRY(upload(p, &p.tile_kb, tile_kb, st));
+  G_TRY(upload(p, &p.tile_dim, tile_dim, st));
   G_TRY(upload(p, &p.q_row_base, q_row_base, st));
   G_TRY(upload(p, &p.q_elem_base, q_elem_base, st));
   G_TRY(upload(p, &p.pad_base, pad_base, st));
@@ -548,6 +552,7 @@ int run_plan(rbc_group* g, Plan& p, cudaStream_t st) {
   a.out_dist = p.out_dist;
   a.fallback_rows = p.fb_rows;
   a.counters = p.counters;
+  a.tile_dim = p.tile_dim;  // re-rank over each index's own columns
   G_TRY(launch_select(a, st));
   // uncertified rows: FP32 brute force over their own index
   GroupFallbackArgs f{};

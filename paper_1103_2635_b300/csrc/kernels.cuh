@@ -134,6 +134,10 @@ struct SelectArgs {
   float* out_dist;
   int* fallback_rows;        // uncertified rows are appended here (lp)
   int* counters;             // [0] uncertified, [1] fp64 ties, [2] boundary ties
+  // optional: per tile (row / TQ) the number of leading columns that can be
+  // nonzero (rows of Q32 / X32 stay d apart); sets the re-rank length and its
+  // rounding bounds
+  const int16_t* tile_dim = nullptr;
 };
 int launch_select(const SelectArgs& a, cudaStream_t st);
 

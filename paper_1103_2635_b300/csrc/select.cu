@@ -73,9 +73,9 @@ __device__ __forceinline__ float rerank_rho(const float* qr, const float* xr, in
 // lane, sorted by (rho, id)) lie within the FP32 bound of each other, every
 // candidate is recomputed in FP64 and the lanes re-sorted by (rho64, id).
 // Returns the ballot of tied ranks (0: nothing recomputed).
-__device__ __forceinline__ unsigned fp64_ties(const float* qr, const float* X32, int d, int metric,
-                                              int k, int c_out, float eps, int lane, float& rho,
-                                              int& oid, int& brow) {
+__device__ __forceinline__ unsigned fp64_ties(const float* qr, const float* X32, int ld, int d,
+                                              int metric, int k, int c_out, float eps, int lane,
+                                              float& rho, int& oid, int& brow) {
   float nxt = __shfl_down_sync(0xffffffffu, rho, 1);
   bool tie = lane < k && lane + 1 < c_out && rho != INFINITY && nxt != INFINITY &&
              (nxt - rho) <= eps * (nxt + rho) * 2.0f;
@@ -83,7 +83,7 @@ __device__ __forceinline__ unsigned fp64_ties(const float* qr, const float* X32,
   if (tie_mask) {
     double r64 = INFINITY;
     if (brow >= 0) {
-      const float* xr = X32 + (int64_t)brow * d;
+      const float* xr = X32 + (int64_t)brow * ld;
       double s = 0.0;
       for (int i = 0; i < d; ++i) {
         double t0 = (double)qr[i] - (double)xr[i];
@@ -214,12 +214,15 @@ __global__ void __launch_bounds__(WARPS * 32) select_kernel(SelectArgs a) {
   const bool valid = lane < a.c_out && ci != INT32_MAX && cs != INFINITY;
 
   // ---- 2. FP32 re-rank ----
-  const int d = a.d;
-  const float* qr = a.Q32 + (int64_t)row * d;
+  // rows are ld floats apart; the tile's own dimension (zero columns past it)
+  // sets the loop length and the rounding bounds
+  const int ld = a.d;
+  const int d = a.tile_dim ? (int)a.tile_dim[tile] : a.d;
+  const float* qr = a.Q32 + (int64_t)row * ld;
   float rho = INFINITY;
   int oid = INT32_MAX;
   if (valid) {
-    rho = rerank_rho(qr, a.X32 + (int64_t)ci * d, d, a.metric);
+    rho = rerank_rho(qr, a.X32 + (int64_t)ci * ld, d, a.metric);
     oid = a.xid ? a.xid[ci] : ci;
   }
   int brow = valid ? ci : -1;  // buffer row carried through the sort
@@ -276,7 +279,7 @@ __global__ void __launch_bounds__(WARPS * 32) select_kernel(SelectArgs a) {
   }
 
   // ---- 5. near-ties among the first k+1 ranks -> FP64 ----
-  const unsigned tie_mask = fp64_ties(qr, a.X32, d, a.metric, a.k, a.c_out, eps, lane, rho, oid,
+  const unsigned tie_mask = fp64_ties(qr, a.X32, ld, d, a.metric, a.k, a.c_out, eps, lane, rho, oid,
                                       brow);
 
   // ---- 6. output ----
@@ -445,7 +448,7 @@ __global__ void __launch_bounds__(WARPS * 32) select_cands_kernel(CandSelectArgs
     }
   }
   const float eps = rerank_eps(d);
-  const unsigned tie_mask = fp64_ties(qr, a.X32, d, a.metric, k, a.c_out, eps, lane, rho, oid,
+  const unsigned tie_mask = fp64_ties(qr, a.X32, d, d, a.metric, k, a.c_out, eps, lane, rho, oid,
                                       brow);
   if (lane < k) {
     const bool ok = rho != INFINITY && brow >= 0;
@@ -565,7 +568,8 @@ __global__ void __launch_bounds__(GFB_THREADS) group_fallback_kernel(GroupFallba
           }
         }
       }
-      const unsigned ties = fp64_ties(sq, a.X32, a.d, RBC_L2, a.k, a.c_out, eps, lane, rho, oid, brow);
+      const unsigned ties =
+          fp64_ties(sq, a.X32, a.d, a.d, RBC_L2, a.k, a.c_out, eps, lane, rho, oid, brow);
       if (lane < a.k && q >= 0) {
         const bool ok = rho != INFINITY && brow >= 0;
         a.out_ids[(int64_t)q * a.k + lane] = ok ? (int64_t)oid : (int64_t)-1;
@@ -673,8 +677,8 @@ __global__ void __launch_bounds__(WARPS * 32) select_stream_kernel(CandSelectArg
       }
     }
     const float eps = rerank_eps(d);
-    const unsigned tie_mask = fp64_ties(qr, a.X32, d, a.metric, k, a.c_out, eps, lane, rho, oid,
-                                        brow);
+    const unsigned tie_mask = fp64_ties(qr, a.X32, d, d, a.metric, k, a.c_out, eps, lane, rho,
+                                        oid, brow);
     if (lane < k) {
       const bool ok = rho != INFINITY && brow >= 0;
       a.out_ids[q * k + lane] = ok ? (int64_t)oid : (int64_t)-1;
