@@ -105,6 +105,30 @@ def dist_env():
     return rank, world, local
 
 
+def rank_query_seed(rank: int) -> int:
+    """Each rank searches its own query batch of the workload (weak scaling)."""
+    return 1 + 1000 * rank
+
+
+def ranks_max(value: float, device=None) -> float:
+    """The largest value over the ranks of the default process group (the
+    slowest rank's time); the value itself without one."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_qps(world: int, m: int, steps: int, elapsed_ms: float) -> float:
+    """Whole-job queries/s: every rank searched m queries per step, the job
+    took the slowest rank's time."""
+    return world * m * steps / (elapsed_ms / 1000.0)
+
+
 def load_peaks():
     try:
         with open(PEAKS_PATH) as f:
@@ -231,7 +255,7 @@ def run_ours(args, rank, world, local):
         dist.init_process_group("nccl", device_id=dev)
     storage = {"bf16": rbc.BF16, "f16": rbc.F16, "f32": rbc.F32, "fp8": rbc.FP8E4M3}[args.storage]
     # each rank holds its own replica and its own query batch (weak scaling)
-    w, X, Q = workload_arrays(args.workload, 0, query_seed=1 + 1000 * rank, n=args.n, m=args.m)
+    w, X, Q = workload_arrays(args.workload, 0, query_seed=rank_query_seed(rank), n=args.n, m=args.m)
     Xd = torch.from_numpy(X).to(dev)
     Qd = torch.from_numpy(Q).to(dev)
     m, d, k = Q.shape[0], Q.shape[1], args.k
@@ -277,13 +301,9 @@ def run_ours(args, rank, world, local):
     lat = {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
            "unit": "ms per batch of %d queries" % m}
     if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+        elapsed_ms = ranks_max(elapsed_ms, dev)
     stats = rbc.last_stats()
-    qps = world * m * args.steps / (elapsed_ms / 1000.0)
+    qps = weak_scaling_qps(world, m, args.steps, elapsed_ms)
     if args.legs == "search":
         if rank == 0:
             print(json.dumps({"legs": "search", "value": qps, "unit": "queries/s",
@@ -318,7 +338,8 @@ def run_ours(args, rank, world, local):
         rbc.rbc_search(idx, Qh_np, k, out_ids=ids_np, out_dist=dist_np)
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
-    e2e_qps = world * m * e2e_steps / e2e_s
+    e2e_s = ranks_max(e2e_s, dev)  # the slowest rank
+    e2e_qps = weak_scaling_qps(world, m, e2e_steps, e2e_s * 1e3)
     same = bool((ids_h.numpy() == ids.cpu().numpy()).all())
 
     # ---- plain FP32 CUDA-core brute force on the same queries ----
