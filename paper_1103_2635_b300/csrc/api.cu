@@ -202,6 +202,19 @@ float simt_eps(int d) { return (float)(d + 8) * U32; }
 // relative bound of rho from the FP32 re-rank (interleaved partial sums)
 float rerank_eps_host(int d) { return (0.25f * d + 8.0f) * U32; }
 int pad64(int d) { return (d + 63) / 64 * 64; }
+
+// Stage one BF(Q, R) as dense work items: a batch of few 128-query tiles
+// splits the representatives into column chunks (at least 256 each) so that
+// every SM gets about two items; a large batch keeps one item per tile.
+void set_stage1_splits(TileWork& w, int64_t tiles, int n_r, int sms) {
+  int64_t splits = tiles > 0 ? (2LL * sms + tiles - 1) / tiles : 1;
+  splits = std::max<int64_t>(1, std::min<int64_t>(splits, (n_r + 255) / 256));
+  int64_t chunk = (n_r + splits - 1) / splits;
+  splits = (n_r + chunk - 1) / chunk;
+  w.dense_splits = (int)splits;
+  w.dense_chunk = chunk;
+  w.num_items = (int)(tiles * splits);
+}
 // low-precision row length: 128-byte K blocks of 64 16-bit or 128 FP8 elements
 int lp_pad(int d, int storage) {
   return storage == RBC_FP8E4M3 ? (d + 127) / 128 * 128 : pad64(d);
@@ -736,10 +749,9 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
   w1.num_items = (int)tiles;
   w1.m = mb;
   w1.n = n_r;
-  w1.dense_splits = 1;
-  w1.dense_chunk = n_r;
+  set_stage1_splits(w1, tiles, n_r, sms);
   RBC_TRY(launch_bf_simt_store(Qb, ix->R32, d, metric, w1, D, n_r,
-                               (int)std::min<int64_t>(tiles, (int64_t)sms * 2 * 16), st));
+                               (int)std::min<int64_t>(w1.num_items, (int64_t)sms * 2 * 16), st));
   float *g1, *gk;
   int64_t* nearest;
   RBC_TRY(ar.alloc(&g1, mb));
@@ -1234,10 +1246,9 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   w1.num_items = (int)tiles;
   w1.m = mb;
   w1.n = n_r;
-  w1.dense_splits = 1;
-  w1.dense_chunk = n_r;
+  set_stage1_splits(w1, tiles, n_r, sms);
   RBC_TRY(launch_bf_simt_store(Qb, ix->R32, d, ix->metric, w1, D, n_r,
-                               (int)std::min<int64_t>(tiles, (int64_t)sms * 2 * 16), st));
+                               (int)std::min<int64_t>(w1.num_items, (int64_t)sms * 2 * 16), st));
   float *g1, *gk;
   int64_t* nearest;
   RBC_TRY(ar.alloc(&g1, mb));
@@ -1291,8 +1302,10 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   RBC_TRY(ar.alloc(&counts, window_pair_blocks(mb) * nbins));
   RBC_TRY(ar.alloc(&totals, nbins));
   RBC_TRY(ar.alloc(&bin_off, nbins + 1));
+  int* scan_scratch;
+  RBC_TRY(ar.alloc(&scan_scratch, exclusive_scan_scratch_ints((int)nbins)));
   RBC_TRY(launch_window_pairs_count(D, mb, n_r, g, g1, ix->psi, simt_eps(d), rmin, rmax, qkept,
-                                    counts, totals, bin_off, st));
+                                    counts, totals, bin_off, st, scan_scratch));
   RBC_TRY(launch_sum_i32(qkept, mb, cn.sums, st));
   // pair arrays sized by the bound mb x n_r (batches are cut so that it stays
   // within WINDOW_MAX_PAIRS), so no count needs to come back to the host
@@ -1519,6 +1532,7 @@ int64_t bound_window_batch(const rbc_index* ix, int64_t mb, int k) {
   b += rows_cap * 2 * MAX_C * 8;                             // pass A partial lists
   b += mb * 4 + n_r * 8 + mb * 4;                            // g, rmin, rmax, qkept
   b += window_pair_blocks(mb) * nbins * 4 + nbins * 8 + 4;   // bin counts, totals, offsets
+  b += ((int64_t)exclusive_scan_scratch_ints((int)nbins)) * 4; // their scan
   b += mb * 4 + mb * n_r * 8;                                // thr, pairs
   b += n_r * 8 + 4 + (mb * n_r / TQ + n_r) * (int64_t)sizeof(EmitItem);  // chunks, items
   b += mb * (int64_t)CAND_CAP * 8 + mb * 4;                  // candidate buffers

@@ -226,7 +226,7 @@ int64_t window_pair_blocks(int64_t m);
 int launch_window_pairs_count(const float* D, int64_t m, int n_r, const float* g,
                               const float* g1, const float* psi_plus, float rel, unsigned* rmin,
                               unsigned* rmax, int* q_kept, int* counts, int* totals, int* bin_off,
-                              cudaStream_t st);
+                              cudaStream_t st, int* scan_scratch = nullptr);
 int launch_window_pairs_scatter(const float* D, int64_t m, int n_r, const float* g,
                                 const float* g1, const float* psi_plus, float rel,
                                 const unsigned* rmin, const unsigned* rmax, int* counts,
@@ -360,7 +360,10 @@ int launch_workgen_items(const uint32_t* tile_mask, const int* offsets, int n_r,
 int launch_sum_i32(const int* v, int64_t n, unsigned long long* out, cudaStream_t st);
 int launch_sum_i64(const int64_t* v, int64_t n, unsigned long long* out, cudaStream_t st);
 // out[i] = sum_{j<i} in[j] for i <= n (out[n] = total), one block
-int launch_exclusive_scan(const int* in, int n, int* out, cudaStream_t st);
+// out[0 .. n] = exclusive prefix sums of in[0 .. n) and the total; with a
+// scratch of exclusive_scan_scratch_ints(n) ints long arrays scan on many blocks
+int exclusive_scan_scratch_ints(int n);
+int launch_exclusive_scan(const int* in, int n, int* out, cudaStream_t st, int* scratch = nullptr);
 // dst[i] += src[i] for i < n (n <= 32)
 int launch_add_ints(int* dst, const int* src, int n, cudaStream_t st);
 // sum over query tiles of (tile rows) x (tile union points)

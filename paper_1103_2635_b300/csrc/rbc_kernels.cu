@@ -89,6 +89,65 @@ __global__ void exclusive_scan_kernel(const int* __restrict__ in, int n, int* __
   if (threadIdx.x == 0) out[n] = carry;
 }
 
+// Two-level exclusive scan for long arrays: per tile of SCAN_TILE elements a
+// sum, a scan of the sums (the single-block kernel), then each tile scanned
+// from its offset.  out[n] = total.
+constexpr int SCAN_TILE = 4096;
+__global__ void scan_tile_sums_kernel(const int* __restrict__ in, int n, int* __restrict__ sums) {
+  __shared__ int part[32];
+  const int base = blockIdx.x * SCAN_TILE;
+  int s = 0;
+  for (int i = base + threadIdx.x; i < min(n, base + SCAN_TILE); i += blockDim.x) s += in[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int v = threadIdx.x < (int)(blockDim.x >> 5) ? part[threadIdx.x] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) sums[blockIdx.x] = v;
+  }
+}
+__global__ void scan_tiles_kernel(const int* __restrict__ in, int n, const int* __restrict__ off,
+                                  int* __restrict__ out) {
+  __shared__ int warp_sums[32];
+  __shared__ int carry;
+  const int base = blockIdx.x * SCAN_TILE;
+  const int end = min(n, base + SCAN_TILE);
+  if (threadIdx.x == 0) carry = off[blockIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int b0 = base; b0 < end; b0 += blockDim.x) {
+    const int i = b0 + threadIdx.x;
+    const int v = i < end ? in[i] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int s = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += y;
+      }
+      warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const int warp_off = wid ? warp_sums[wid - 1] : 0;
+    if (i < end) out[i] = carry + warp_off + x - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = off[gridDim.x];
+}
+
 // one warp per block walks its chunk in order; equal keys within a group of
 // 32 are ranked by lane, so the scatter is stable
 __global__ void cs_scatter_kernel(const int64_t* __restrict__ key, int64_t n, int nbins,
@@ -386,9 +445,23 @@ __global__ void gather_f32_kernel(const float* __restrict__ val, const int* __re
 
 }  // namespace
 
-int launch_exclusive_scan(const int* in, int n, int* out, cudaStream_t st) {
-  exclusive_scan_kernel<<<1, 1024, 0, st>>>(in, n, out);
+int exclusive_scan_scratch_ints(int n) { return 2 * ((n + SCAN_TILE - 1) / SCAN_TILE) + 2; }
+
+int launch_exclusive_scan(const int* in, int n, int* out, cudaStream_t st, int* scratch) {
+  if (!scratch || n <= 2 * SCAN_TILE) {
+    exclusive_scan_kernel<<<1, 1024, 0, st>>>(in, n, out);
+    RBC_LAUNCH_CHECK("exclusive_scan_kernel");
+    return RBC_OK;
+  }
+  const int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+  int* sums = scratch;
+  int* off = scratch + nb + 1;
+  scan_tile_sums_kernel<<<nb, 1024, 0, st>>>(in, n, sums);
+  RBC_LAUNCH_CHECK("scan_tile_sums_kernel");
+  exclusive_scan_kernel<<<1, 1024, 0, st>>>(sums, nb, off);
   RBC_LAUNCH_CHECK("exclusive_scan_kernel");
+  scan_tiles_kernel<<<nb, 1024, 0, st>>>(in, n, off, out);
+  RBC_LAUNCH_CHECK("scan_tiles_kernel");
   return RBC_OK;
 }
 

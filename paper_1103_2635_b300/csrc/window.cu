@@ -533,7 +533,7 @@ int64_t window_pair_blocks(int64_t m) { return (m + WW * WT - 1) / (WW * WT); }
 int launch_window_pairs_count(const float* D, int64_t m, int n_r, const float* g,
                               const float* g1, const float* psi_plus, float rel, unsigned* rmin,
                               unsigned* rmax, int* q_kept, int* counts, int* totals, int* bin_off,
-                              cudaStream_t st) {
+                              cudaStream_t st, int* scan_scratch) {
   const int64_t nbins = (int64_t)n_r * NBK;
   const int64_t qblocks = window_pair_blocks(m);
   if (qblocks > 0) {
@@ -552,7 +552,7 @@ int launch_window_pairs_count(const float* D, int64_t m, int n_r, const float* g
   } else {
     RBC_CUDA(cudaMemsetAsync(totals, 0, nbins * sizeof(int), st));
   }
-  return launch_exclusive_scan(totals, (int)nbins, bin_off, st);
+  return launch_exclusive_scan(totals, (int)nbins, bin_off, st, scan_scratch);
 }
 
 int launch_window_pairs_scatter(const float* D, int64_t m, int n_r, const float* g,
