@@ -142,6 +142,8 @@ def test_request_validation_and_empty_request(served):
         ("subspace", rbc.F32, rbc.L1, rbc.EXACT, rbc.PLAN_WINDOW),
         ("subspace", rbc.BF16, rbc.L2, rbc.ONESHOT, rbc.PLAN_WINDOW),
         ("subspace", rbc.F32, rbc.L2, rbc.ONESHOT, rbc.PLAN_WINDOW),
+        ("subspace", rbc.FP8E4M3, rbc.L2, rbc.EXACT, rbc.PLAN_WINDOW),
+        ("subspace", rbc.FP8E4M3, rbc.L2, rbc.ONESHOT, rbc.PLAN_WINDOW),
     ],
 )
 def test_workspace_bound_holds(gen, storage, metric, mode, plan):
