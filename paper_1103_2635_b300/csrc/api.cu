@@ -226,9 +226,19 @@ constexpr int64_t NORM_PAD = 512;
 struct StatsBlock {
   unsigned long long v[8];
 };
-thread_local StatsBlock* t_stats_host = nullptr;
 thread_local cudaStream_t t_stats_stream = nullptr;
 thread_local bool t_stats_pending = false;
+// pinned landing block of a thread's statistics, freed when the thread ends
+// (serving workers come and go with their servers)
+struct StatsHost {
+  StatsBlock* p = nullptr;
+  ~StatsHost() {
+    if (!p) return;
+    if (t_stats_pending && t_stats_stream) cudaStreamSynchronize(t_stats_stream);
+    cudaFreeHost(p);
+  }
+};
+thread_local StatsHost t_stats_holder;
 thread_local rbc_search_stats t_stats_fixed;
 
 // device counters: ints [0] uncertified [1] fp64 ties [2] boundary ties,
@@ -300,6 +310,7 @@ thread_local int64_t t_stats_host_kept = -1;  // >= 0: kept_reps known on the ho
 
 int stats_publish(const Counters& cn, int64_t queries, int64_t items, int64_t host_pairs, Arena& ar,
                   cudaStream_t st, int64_t host_kept = -1) {
+  StatsBlock*& t_stats_host = t_stats_holder.p;
   if (!t_stats_host) {
     void* p = nullptr;
     RBC_CUDA(cudaMallocHost(&p, sizeof(StatsBlock)));
@@ -1651,7 +1662,7 @@ int rbc_last_stats(rbc_search_stats* out) {
   if (t_stats_pending) {
     cudaError_t e = cudaStreamSynchronize(t_stats_stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
-    const unsigned long long* v = t_stats_host->v;
+    const unsigned long long* v = t_stats_holder.p->v;
     t_stats_fixed.kept_reps = t_stats_host_kept >= 0 ? t_stats_host_kept : (int64_t)v[0];
     t_stats_fixed.tile_points = (int64_t)v[1];
     t_stats_fixed.candidates = (int64_t)v[7];

@@ -359,7 +359,6 @@ int launch_workgen_items(const uint32_t* tile_mask, const int* offsets, int n_r,
 // reduce helpers for statistics
 int launch_sum_i32(const int* v, int64_t n, unsigned long long* out, cudaStream_t st);
 int launch_sum_i64(const int64_t* v, int64_t n, unsigned long long* out, cudaStream_t st);
-// out[i] = sum_{j<i} in[j] for i <= n (out[n] = total), one block
 // out[0 .. n] = exclusive prefix sums of in[0 .. n) and the total; with a
 // scratch of exclusive_scan_scratch_ints(n) ints long arrays scan on many blocks
 int exclusive_scan_scratch_ints(int n);
@@ -370,40 +369,5 @@ int launch_add_ints(int* dst, const int* src, int n, cudaStream_t st);
 int launch_sum_pairs(const int64_t* tile_points, int64_t m, unsigned long long* out,
                      cudaStream_t st);
 
-
-// ---- one-shot RBC (oneshot.cu) ----
-// candidate capacity per representative for a list of s points
-int oneshot_candidate_cap(int s);
-// per row r < reps of D [reps, ld] (distances to n points): the s-th smallest
-// value t and every column with D <= t (1 + 3 eps) -> cand[r][0 .. cand_cnt[r])
-int launch_oneshot_select(const float* D, int64_t ld, int64_t n, int reps, int s, float eps,
-                          int cap, int* cand, int* cand_cnt, uint32_t* dev_err, cudaStream_t st);
-// FP64 distances of the candidates of representatives r0 .. r0 + reps - 1,
-// sorted by (rho, id): the first s ids -> members[r][0 .. s), psi[r] = the
-// s-th distance rounded to float; DEV_ERR_BOUNDS when a representative had
-// fewer than s candidates (non-finite distances)
-int launch_oneshot_refine(const float* X, const float* R, int d, int metric, int s, int cap,
-                          const int* cand, const int* cand_cnt, int r0, int reps, int* members,
-                          float* psi, uint32_t* dev_err, cudaStream_t st);
-// queries grouped by representative (qperm, qoff from a counting sort), each
-// group padded to a multiple of TQ rows: pad_off [n_r + 1], per padded row
-// the source row (qsrc_pad) and the output row (qout_pad, through `orig` when
-// given), -1 on padding, and per tile its representative
-int launch_oneshot_layout(const int* qoff, int n_r, const int* qperm, const int* orig,
-                          int* counts_scratch, int* pad_off, int* qsrc_pad, int* qout_pad,
-                          int* tile_rep, cudaStream_t st);
-// one work item per padded tile: its rows against list r = [r s, (r + 1) s),
-// or [list_off[r], list_off[r + 1]) when list_off is given; adds each tile's
-// list length to *points_sum when given
-int launch_oneshot_items(const int* pad_off, int n_r, const int* tile_rep, const int* qoff, int s,
-                         const int* list_off, WorkItem* items, Seg* segs, int* num_items,
-                         int max_tiles, unsigned long long* points_sum, cudaStream_t st);
-// out[i] = Q[src[i]] (zero row where src[i] < 0), i < rows
-int launch_gather_padded(const float* Q, const int* src, int64_t rows, int d, float* out,
-                         cudaStream_t st);
-// rows[i] (i < n) of a padded layout -> rep64[i] = tile_rep[rows[i] / TQ],
-// out_row[i] = qout_pad[rows[i]]
-int launch_oneshot_fallback_map(const int* rows, int n, const int* tile_rep, const int* qout_pad,
-                                int64_t* rep64, int* out_row, cudaStream_t st);
 
 }  // namespace rbc
