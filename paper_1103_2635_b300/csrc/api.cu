@@ -535,7 +535,8 @@ int select_lp_and_fallback(const float* ps, const int* pi, const int* pv, int C,
                            int dense_splits, int64_t m, const float* Qbuf, const LpQueries& ql,
                            const DbView& db, int d, int k, int c_out, const int* qorig,
                            int64_t* out_ids, float* out_dist, int* cnt, Arena& ar,
-                           cudaStream_t st, int level = 0, const rbc_index* rbc_ix = nullptr) {
+                           cudaStream_t st, int level = 0, const rbc_index* rbc_ix = nullptr,
+                           const float* g_rows = nullptr) {
   int* fb_rows;
   int* lc;  // this call's counters: [0] rows appended to fb_rows, [1..2] ties
   RBC_TRY(ar.alloc(&fb_rows, m));
@@ -578,7 +579,7 @@ int select_lp_and_fallback(const float* ps, const int* pi, const int* pv, int C,
     if (rbc_ix) {
       // exact RBC: the FP32 exact search over the rows' surviving lists
       RBC_TRY(fallback_rbc_f32(rbc_ix, Qbuf, fb_rows, nfb, qorig, k, out_ids, out_dist, cnt + 4,
-                               ar, st));
+                               ar, st, g_rows));
     } else if (level == 0 && db.Xlp) {
       float* Qf;
       int* forig;
@@ -743,6 +744,10 @@ constexpr int64_t MAX_BATCH = 131072;  // queries per internal batch (bounds wor
 constexpr int64_t WINDOW_MAX_PAIRS = 1LL << 28;  // windowed search: batch x n_r bound
 constexpr int64_t ARENA_MIN_LANE = 256;  // hit records per epilogue thread, at least
 
+int own_list_bound(const rbc_index* ix, const float* Qb, int64_t mb, const int64_t* nearest,
+                   const LpQueries& ql, int k, float* own, uint32_t* dev_err, Arena& ar,
+                   cudaStream_t st);
+
 int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, int64_t* ids,
                        float* dist, const Counters& cn, int64_t* items_total, Arena& ar,
                        cudaStream_t st, bool f32_only = false, const float* g_cap = nullptr) {
@@ -772,6 +777,20 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
   // a caller that already knows an upper bound of each query's k-th neighbour
   // distance (the windowed search's own-list bound) tightens gamma_k with it
   if (g_cap) RBC_TRY(launch_gbound(g_cap, gk, mb, 0.0f, gk, st));
+  // low-precision search: the own-list bound g = min(gamma_k, the k-th
+  // distance inside the nearest representative's list) prunes more
+  // surviving lists and bounds the FP32 re-search of uncertified queries
+  uint32_t* dev_err;
+  RBC_TRY(ar.alloc(&dev_err, 1));
+  RBC_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(uint32_t), st));
+  if (lp) {
+    LpQueries qb;
+    RBC_TRY(lp_queries(Qb, mb, d, ix->dpad, ix->storage, qb, ar, st));
+    float* own;
+    RBC_TRY(ar.alloc(&own, mb));
+    RBC_TRY(own_list_bound(ix, Qb, mb, nearest, qb, k, own, dev_err, ar, st));
+    RBC_TRY(launch_gbound(own, gk, mb, simt_eps(d), gk, st));
+  }
   // queries ordered by nearest representative, so each tile holds nearby queries
   int *qperm, *qoff, *scratch;
   RBC_TRY(ar.alloc(&qperm, mb));
@@ -807,11 +826,8 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
   RBC_TRY(launch_item_offsets(tpts, (int)tiles, (int)W, tcnt, toff, st));
   WorkItem* items;
   Seg* segs;
-  uint32_t* dev_err;
   RBC_TRY(ar.alloc(&items, tiles * item_cap));
   RBC_TRY(ar.alloc(&segs, tiles * seg_cap));
-  RBC_TRY(ar.alloc(&dev_err, 1));
-  RBC_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(uint32_t), st));
   RBC_TRY(launch_workgen_items(tmask, ix->offsets, n_r, mb, (int)W, item_cap, seg_cap, toff, items,
                                segs, dev_err, st));
   *items_total += tiles * item_cap;
@@ -880,8 +896,12 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
     LpMatrix Xm{ix->Xlp, ix->xnorm, n, ix->dpad, ix->storage, nullptr, ix->xscale};
     tmark(1, st);
     RBC_TRY(launch_bf_tc_topc(Qm, Xm, C, w2, TopOut{ps, pi, pv}, sms, st, dev_err));
+    // the bound g of each sorted row, for the re-search of uncertified rows
+    float* gp;
+    RBC_TRY(ar.alloc(&gp, mb));
+    RBC_TRY(launch_gather_rows(gk, nullptr, qperm, mb, 1, gp, st));
     RBC_TRY(select_lp_and_fallback(ps, pi, pv, C, toff, 0, mb, Qp, ql, db, d, k, c_out, qperm,
-                                   ids, dist, cn.c, ar, st, 0, ix));
+                                   ids, dist, cn.c, ar, st, 0, ix, gp));
   }
   uint32_t herr = 0;
   RBC_CUDA(cudaMemcpyAsync(&herr, dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -1096,6 +1116,38 @@ int group_queries(const rbc_index* ix, const float* Qsrc, int64_t mq, const int6
   return RBC_OK;
 }
 
+// own[q] = the k-th smallest FP32 distance among the k best low-precision
+// scores of q inside its nearest representative's list -- the distances of
+// k actual points, so an upper bound of q's k-th neighbour distance (INF if
+// that list holds fewer than k points).  Queries grouped by nearest
+// representative, one tensor-core top-C pass over the own lists, FP32
+// distances of the selected rows.  ql holds the batch's low-precision rows.
+int own_list_bound(const rbc_index* ix, const float* Qb, int64_t mb, const int64_t* nearest,
+                   const LpQueries& ql, int k, float* own, uint32_t* dev_err, Arena& ar,
+                   cudaStream_t st) {
+  Grouped gq;
+  RBC_TRY(group_queries(ix, Qb, mb, nearest, nullptr, ix->offsets, nullptr, gq, ar, st, false));
+  const int row_bytes = ix->dpad * lp_elem_bytes(ix->storage);
+  uint8_t* alp;
+  float *anorm, *aerr, *ascale = nullptr;
+  RBC_TRY(ar.alloc(&alp, gq.rows_cap * row_bytes));
+  RBC_TRY(ar.alloc(&anorm, gq.rows_cap));
+  RBC_TRY(ar.alloc(&aerr, gq.rows_cap));
+  if (ql.scale) RBC_TRY(ar.alloc(&ascale, gq.rows_cap));
+  RBC_TRY(launch_gather_lp_rows(ql.lp, ql.norm, ql.err, gq.qsrc, gq.rows_cap, row_bytes, alp,
+                                anorm, aerr, st, ql.scale, ascale));
+  const int C = k <= 8 ? 8 : (k <= 16 ? 16 : 32);
+  float* ps;
+  int* pi;
+  RBC_TRY(ar.alloc(&ps, gq.max_tiles * TQ * 2 * C));
+  RBC_TRY(ar.alloc(&pi, gq.max_tiles * TQ * 2 * C));
+  LpMatrix Qm{alp, anorm, gq.rows_cap, ix->dpad, ix->storage, nullptr, ascale};
+  LpMatrix Xm{ix->Xlp, ix->xnorm, ix->list_entries, ix->dpad, ix->storage, nullptr, ix->xscale};
+  RBC_TRY(launch_bf_tc_topc(Qm, Xm, C, gq.w, TopOut{ps, pi, nullptr}, sm_count(), st, dev_err));
+  return launch_own_kth_lp(ps, pi, C, gq.qsrc, gq.rows_cap, k, Qb, ix->X32, ix->d, ix->metric,
+                           rerank_eps_host(ix->d) + 8.0f * U32, own, st);
+}
+
 int oneshot_stage2(const rbc_index* ix, const float* Qsrc, int64_t mq, const int64_t* rep_of,
                    const int* orig, bool lp, int k, int64_t* ids, float* dist, int* cnt,
                    unsigned long long* points_sum, int64_t* items_total, Arena& ar,
@@ -1274,31 +1326,9 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   LpQueries ql;
   RBC_TRY(lp_queries(Qb, mb, d, ix->dpad, ix->storage, ql, ar, st));
   // pass A: the k-th distance inside the nearest representative's own list
-  // (tensor-core top-C kernel over the grouped queries, then the FP32
-  // distances of each row's k best-scored candidates)
   float* own;
   RBC_TRY(ar.alloc(&own, mb));
-  {
-    Grouped gq;
-    RBC_TRY(group_queries(ix, Qb, mb, nearest, nullptr, ix->offsets, nullptr, gq, ar, st, false));
-    uint16_t* alp;
-    float *anorm, *aerr;
-    RBC_TRY(ar.alloc(&alp, gq.rows_cap * ix->dpad));
-    RBC_TRY(ar.alloc(&anorm, gq.rows_cap));
-    RBC_TRY(ar.alloc(&aerr, gq.rows_cap));
-    RBC_TRY(launch_gather_lp_rows(ql.lp, ql.norm, ql.err, gq.qsrc, gq.rows_cap, ix->dpad, alp, anorm,
-                                  aerr, st));
-    const int C = k <= 8 ? 8 : (k <= 16 ? 16 : 32);
-    float* ps;
-    int* pi;
-    RBC_TRY(ar.alloc(&ps, gq.max_tiles * TQ * 2 * C));
-    RBC_TRY(ar.alloc(&pi, gq.max_tiles * TQ * 2 * C));
-    LpMatrix QmA{alp, anorm, gq.rows_cap, ix->dpad, ix->storage};
-    LpMatrix XmA{ix->Xlp, ix->xnorm, n, ix->dpad, ix->storage};
-    RBC_TRY(launch_bf_tc_topc(QmA, XmA, C, gq.w, TopOut{ps, pi, nullptr}, sms, st, dev_err));
-    RBC_TRY(launch_own_kth_lp(ps, pi, C, gq.qsrc, gq.rows_cap, k, Qb, ix->X32, d, ix->metric,
-                              rerank_eps_host(d) + 8.0f * U32, own, st));
-  }
+  RBC_TRY(own_list_bound(ix, Qb, mb, nearest, ql, k, own, dev_err, ar, st));
   float* g;
   RBC_TRY(ar.alloc(&g, mb));
   RBC_TRY(launch_gbound(own, gk, mb, simt_eps(d), g, st));
@@ -1524,6 +1554,14 @@ int64_t bound_group(const rbc_index* ix, int64_t mq, bool gather_fp32) {
          max_tiles * (int64_t)(sizeof(WorkItem) + sizeof(Seg)) + 4;
 }
 
+// own_list_bound over mb queries (with its output own[mb])
+int64_t bound_own_list(const rbc_index* ix, int64_t mb) {
+  const int64_t max_tiles = cdiv(mb, TQ) + std::min<int64_t>(ix->n_r, mb);
+  const int64_t rows_cap = max_tiles * TQ;
+  return mb * 4 + bound_group(ix, mb, false) + rows_cap * ((int64_t)ix->dpad * 2 + 12) +
+         rows_cap * 2 * MAX_C * 8;
+}
+
 int64_t bound_window_batch(const rbc_index* ix, int64_t mb, int k) {
   const int d = ix->d, dpad = ix->dpad, sms = sm_count();
   const int64_t n_r = ix->n_r, n = ix->list_entries;
@@ -1537,10 +1575,7 @@ int64_t bound_window_batch(const rbc_index* ix, int64_t mb, int k) {
   int64_t b = mb * n_r * 4;                                  // D
   b += mb * 16 + 4;                                          // g1, gk, nearest, dev_err
   b += mb * ((int64_t)dpad * 2 + 12);                         // low-precision batch
-  b += mb * 4;                                               // own
-  b += bound_group(ix, mb, false);                           // pass A grouping
-  b += rows_cap * ((int64_t)dpad * 2 + 12);                   // pass A rows
-  b += rows_cap * 2 * MAX_C * 8;                             // pass A partial lists
+  b += bound_own_list(ix, mb);                               // pass A
   b += mb * 4 + n_r * 8 + mb * 4;                            // g, rmin, rmax, qkept
   b += window_pair_blocks(mb) * nbins * 4 + nbins * 8 + 4;   // bin counts, totals, offsets
   b += ((int64_t)exclusive_scan_scratch_ints((int)nbins)) * 4; // their scan
@@ -1572,7 +1607,8 @@ int64_t bound_exact_batch(const rbc_index* ix, int64_t mb, int k, bool f32_only)
   b += cap_items * (int64_t)sizeof(WorkItem) + tiles * seg_cap * (int64_t)sizeof(Seg) + 4;
   b += cap_items * TQ * 2 * MAX_C * 8 + cap_items * 4;       // partial lists
   if (!f32_only && uses_lp(ix->storage, ix->metric) && ix->Xlp) {
-    b += mb * ((int64_t)dpad * 2 + 12);                       // low-precision batch
+    b += 2 * mb * ((int64_t)dpad * 2 + 12);                   // low-precision batch, twice
+    b += bound_own_list(ix, mb) + mb * 4;                      // own-list bound, sorted g
     b += bound_select_lp(ix, mb, k);
   }
   return b;

@@ -304,8 +304,8 @@ int launch_to_lowp(const float* src, int64_t rows, int d, int dpad, int storage,
 // dst row i = src row idx[i] of a bf16 / fp16 [*, dpad] matrix plus its norm
 // and residual; idx[i] < 0 gives a zero row
 int launch_gather_lp_rows(const void* src, const float* snorm, const float* serr, const int* idx,
-                          int64_t rows, int dpad, void* dst, float* dnorm, float* derr,
-                          cudaStream_t st);
+                          int64_t rows, int row_bytes, void* dst, float* dnorm, float* derr,
+                          cudaStream_t st, const float* sscale = nullptr, float* dscale = nullptr);
 // Norm block of a low-precision matrix: row i = (h, l, 0, ..., 0) in bf16
 // with h = bf16(-norm[i] / 2), l = bf16(-norm[i] / 2 - h), so that an MMA of
 // an all-ones row against it adds -|x~|^2 / 2 to every accumulator of column

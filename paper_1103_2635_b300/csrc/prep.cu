@@ -157,13 +157,14 @@ __global__ void scatter_result_rows_kernel(const int64_t* __restrict__ ids,
   out_dist[o] = dist[i];
 }
 
-// dst row i = src row idx[i] of a 16-bit [*, dpad] matrix with its norm and
-// residual; idx[i] < 0 gives a zero row (norm 0, residual 0).  One warp per
-// row, 16-byte copies.
+// dst row i = src row idx[i] of a low-precision matrix (rows of row_bytes)
+// with its norm, residual and (FP8) scale; idx[i] < 0 gives a zero row (norm
+// 0, residual 0, scale 1).  One warp per row, 16-byte copies.
 __global__ void gather_lp_rows_kernel(const uint4* __restrict__ src, const float* __restrict__ snorm,
                                       const float* __restrict__ serr, const int* __restrict__ idx,
                                       int64_t rows, int vec_per_row, uint4* __restrict__ dst,
-                                      float* __restrict__ dnorm, float* __restrict__ derr) {
+                                      float* __restrict__ dnorm, float* __restrict__ derr,
+                                      const float* __restrict__ sscale, float* __restrict__ dscale) {
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= rows) return;
@@ -173,6 +174,7 @@ __global__ void gather_lp_rows_kernel(const uint4* __restrict__ src, const float
   if (lane == 0) {
     dnorm[w] = s >= 0 ? snorm[s] : 0.0f;
     derr[w] = s >= 0 ? serr[s] : 0.0f;
+    if (dscale) dscale[w] = s >= 0 ? sscale[s] : 1.0f;
   }
 }
 
@@ -256,12 +258,12 @@ int launch_scatter_result_rows(const int64_t* ids, const float* dist, const int*
 }
 
 int launch_gather_lp_rows(const void* src, const float* snorm, const float* serr, const int* idx,
-                          int64_t rows, int dpad, void* dst, float* dnorm, float* derr,
-                          cudaStream_t st) {
+                          int64_t rows, int row_bytes, void* dst, float* dnorm, float* derr,
+                          cudaStream_t st, const float* sscale, float* dscale) {
   if (rows <= 0) return RBC_OK;
   gather_lp_rows_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(
-      static_cast<const uint4*>(src), snorm, serr, idx, rows, dpad * 2 / 16,
-      static_cast<uint4*>(dst), dnorm, derr);
+      static_cast<const uint4*>(src), snorm, serr, idx, rows, row_bytes / 16,
+      static_cast<uint4*>(dst), dnorm, derr, sscale, dscale);
   RBC_LAUNCH_CHECK("gather_lp_rows_kernel");
   return RBC_OK;
 }
