@@ -63,8 +63,8 @@ METRIC = "exact k-NN queries/s (RBC BF16+rerank vs FP32 brute force), p50/p99 la
 FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
 # DRAM bytes (read + write) of one main-pass launch of the emission kernel on
 # the default workload, from ncu (profiles/bf_tc_emit_kernel_subspace8-n512k-m50k.md);
-# re-measured whenever the kernel changes.
-EMIT_TRAFFIC_BYTES = 735.9e6 + 86.1e6
+# re-measured whenever the kernel changes (None until then).
+EMIT_TRAFFIC_BYTES = None
 
 
 def parse():

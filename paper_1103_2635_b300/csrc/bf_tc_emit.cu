@@ -4,10 +4,12 @@
 // A work item is (a chunk of up to 128 queries that all kept representative
 // r, a window [x_begin, x_end) of r's sorted list).  The queries of a chunk
 // are arbitrary rows of the query matrix, so they are gathered, not tiled:
-// a dedicated warp copies them with 16-byte cp.async into the 128-byte-swizzled
-// K-major layout the MMA reads (two query stages, so the next item's rows
-// arrive while the current one computes).  Database windows are contiguous
-// rows and come by TMA as in the top-C kernel.
+// two warps copy them with 16-byte cp.async (eight lanes per row, so every
+// instruction reads whole rows) into the 128-byte-swizzled K-major layout the
+// MMA reads, several query stages ahead of the MMA.  A query stage also
+// carries its item's window, so the MMA and epilogue warps never read the
+// item list.  Database windows are contiguous rows and come by TMA as in the
+// top-C kernel.
 //
 // Every query q carries a score threshold T(q) (window.cu): no point whose
 // score |x~|^2 - 2 q~.x~ exceeds T(q) can be within g(q) of q, the bound of
@@ -25,9 +27,9 @@
 //
 //   warp 0      TMA producer: database tiles of BN rows + their norm blocks
 //   warp 1      tensor-memory allocation, MMA issue (M = 128, N = BN, K = 16)
-//   warps 2-3   query gather (cp.async), per-row query id and threshold;
-//               the two warps take alternate items (a short window leaves
-//               an item little more time than one gather takes)
+//   warps 2-3   query gather (cp.async), per-row query id and threshold,
+//               the item's window; the two warps take alternate items and
+//               fetch their next item's ids while the copies are in flight
 //   warps 4-    epilogue: TMEM lane quarter (warp % 4) x column slice; with
 //               no candidate lists to keep, a thread needs ~90 registers, so
 //               up to 16 epilogue warps (four per scheduler) hide the TMEM
@@ -85,7 +87,8 @@ struct EmitSmem {
   static constexpr int OFF_ONES = OFF_NB + S * NB_STAGE;
   static constexpr int OFF_ROWQ = OFF_ONES + ONES_BYTES;        // [QSTAGES][BM] query id or -1
   static constexpr int OFF_ROWT = OFF_ROWQ + QSTAGES * BM * 4;  // [QSTAGES][BM] -T / 2
-  static constexpr int OFF_BAR = OFF_ROWT + QSTAGES * BM * 4;
+  static constexpr int OFF_XWIN = OFF_ROWT + QSTAGES * BM * 4;  // [QSTAGES] item window
+  static constexpr int OFF_BAR = OFF_XWIN + QSTAGES * 8;
   // full[S], empty[S], tfull[NBUF], tempty[NBUF], qfull[QS], qempty[QS]
   static constexpr int NBAR = 2 * S + 2 * NBUF + 2 * QSTAGES;
   static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;  // tmem base, abort flag, hit count
@@ -108,17 +111,6 @@ __device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t addr) {
   d |= (uint64_t)1 << 46;                   // descriptor version
   d |= (uint64_t)6 << 61;                   // 32-byte swizzle
   return d;
-}
-
-// Largest of 32 values as a depth-4 tree of three-input maxima.
-__device__ __forceinline__ float max_of32(const float (&u)[32]) {
-  float a[11];
-#pragma unroll
-  for (int j = 0; j < 10; ++j) a[j] = max3f(u[3 * j], u[3 * j + 1], u[3 * j + 2]);
-  a[10] = fmaxf(u[30], u[31]);
-  const float b0 = max3f(a[0], a[1], a[2]), b1 = max3f(a[3], a[4], a[5]);
-  const float b2 = max3f(a[6], a[7], a[8]), b3 = fmaxf(a[9], a[10]);
-  return fmaxf(max3f(b0, b1, b2), b3);
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
@@ -149,6 +141,7 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
   uint32_t* sOnes = reinterpret_cast<uint32_t*>(smem + L::OFF_ONES);
   int* sRowQ = reinterpret_cast<int*>(smem + L::OFF_ROWQ);
   float* sRowT = reinterpret_cast<float*>(smem + L::OFF_ROWT);
+  int2* sXwin = reinterpret_cast<int2*>(smem + L::OFF_XWIN);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
   constexpr int NBUF = L::NBUF;
   uint64_t* full = bars;
@@ -232,66 +225,108 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
   } else if (warp >= E_GATHER && warp < E_GATHER + E_NGATHER) {
     // ---------------- query gather (warp gw takes items qi = gw mod 2) ----------------
     const uint32_t gw = warp - E_GATHER;
-    uint32_t qi = 0;
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-      const EmitItem e = p.items[item];
-      if (e.x_end <= e.x_begin) continue;
-      if (qi % E_NGATHER != gw) {
-        ++qi;
-        continue;
+    // the first item at or after `it` that is this warp's: empty items are
+    // skipped, q counts the non-empty ones before it
+    auto seek = [&](int& it, uint32_t& q, EmitItem& ee) -> bool {
+      for (; it < n_items; it += gridDim.x) {
+        ee = p.items[it];
+        if (ee.x_end <= ee.x_begin) continue;
+        if (q % E_NGATHER == gw) return true;
+        ++q;
       }
-      const int qs = qi % QSTAGES;
-      const uint32_t qph = (qi / QSTAGES) & 1;
-      // the item's query ids and thresholds: independent loads, issued
-      // before the wait for the stage
-      int srcs[BM / 32];
-      float thrs[BM / 32];
+      return false;
+    };
+    // an item's query ids and thresholds (row lane + 32 t)
+    int srcs[BM / 32];
+    float thrs[BM / 32];
+    auto meta = [&](const EmitItem& ee) {
 #pragma unroll
       for (int t = 0; t < BM / 32; ++t) {
         const int row = lane + 32 * t;
-        srcs[t] = row < e.nq ? p.pair_q[(int64_t)(e.pair_begin + row) * p.pair_stride] : -1;
+        srcs[t] = row < ee.nq ? p.pair_q[(int64_t)(ee.pair_begin + row) * p.pair_stride] : -1;
       }
 #pragma unroll
       for (int t = 0; t < BM / 32; ++t) thrs[t] = srcs[t] >= 0 ? p.out.thr[srcs[t]] : 0.0f;
-      if (!__all_sync(0xffffffffu, mbar_wait(&qempty[qs], qph ^ 1, sAbort, p.dev_err))) break;
+    };
+    int item = blockIdx.x;
+    uint32_t qi = 0;
+    EmitItem e;
+    bool have = seek(item, qi, e);
+    bool ok = true;
+    if (have) meta(e);
+    while (have) {
+      const int qs = qi % QSTAGES;
+      const uint32_t qph = (qi / QSTAGES) & 1;
+      if (!__all_sync(0xffffffffu, mbar_wait(&qempty[qs], qph ^ 1, sAbort, p.dev_err))) {
+        ok = false;
+        break;
+      }
       const uint32_t qbase = smem_u32(sQ + qs * L::Q_BYTES);
 #pragma unroll
       for (int t = 0; t < BM / 32; ++t) {
         const int row = lane + 32 * t;
-        const int src = srcs[t];
-        sRowQ[qs * BM + row] = src;
-        sRowT[qs * BM + row] = src < 0 ? INFINITY : -0.5f * thrs[t];
-        const uint8_t* g = p.qlp + (int64_t)(src >= 0 ? src : 0) * p.q_row_bytes;
+        sRowQ[qs * BM + row] = srcs[t];
+        sRowT[qs * BM + row] = srcs[t] < 0 ? INFINITY : -0.5f * thrs[t];
+      }
+      // the copies: eight consecutive lanes move the eight 16-byte chunks of
+      // one 128-byte K block of a row, so one instruction reads four whole
+      // rows (row 4i + lane / 8, whose id lane (4i + lane / 8) mod 32 holds)
+      const int c = lane & 7;
 #pragma unroll
-        for (int kb = 0; kb < KB; ++kb)
+      for (int i = 0; i < BM / 4; ++i) {
+        const int row = 4 * i + (lane >> 3);
+        const int src = __shfl_sync(0xffffffffu, srcs[i >> 3], (4 * i + (lane >> 3)) & 31);
+        const uint8_t* g = p.qlp + (int64_t)(src >= 0 ? src : 0) * p.q_row_bytes + c * 16;
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const uint32_t dst = qbase + kb * BM * 128 + row * 128 + ((c ^ (row & 7)) << 4);
-            if (src >= 0)
-              cp_async16(dst, g + kb * 128 + c * 16);
-            else
-              st_shared_zero16(dst);
-          }
+        for (int kb = 0; kb < KB; ++kb) {
+          const uint32_t dst = qbase + kb * BM * 128 + row * 128 + ((c ^ (row & 7)) << 4);
+          if (src >= 0)
+            cp_async16(dst, g + kb * 128);
+          else
+            st_shared_zero16(dst);
+        }
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
+      if (lane == 0) sXwin[qs] = make_int2(e.x_begin, e.x_end);
+      // the next item's descriptor, query ids and thresholds are fetched
+      // while the copies are in flight
+      int item2 = item + gridDim.x;
+      uint32_t qi2 = qi + 1;
+      EmitItem e2;
+      const bool have2 = seek(item2, qi2, e2);
+      if (have2) meta(e2);
       asm volatile("cp.async.wait_group 0;" ::: "memory");
       // this lane's rows are in shared memory: make them visible to the
       // tensor core (async proxy), then release the stage
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&qfull[qs]);
-      ++qi;
+      item = item2;
+      e = e2;
+      qi = qi2;
+      have = have2;
+    }
+    // stage qi (the number of non-empty items) carries the end mark, an
+    // empty window; the gather warp whose turn it is writes it
+    if (ok && qi % E_NGATHER == gw) {
+      const int qs = qi % QSTAGES;
+      if (__all_sync(0xffffffffu, mbar_wait(&qempty[qs], ((qi / QSTAGES) & 1) ^ 1, sAbort, p.dev_err))) {
+        if (lane == 0) sXwin[qs] = make_int2(0, 0);
+        mbar_arrive(&qfull[qs]);
+      }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
-    uint32_t it = 0, qi = 0;
+    // items in query-stage order; each stage carries its window (an empty
+    // window marks the end)
+    uint32_t it = 0;
     bool ok = true;
-    for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
-      const EmitItem e = p.items[item];
-      if (e.x_end <= e.x_begin) continue;
+    for (uint32_t qi = 0; ok; ++qi) {
       const int qs = qi % QSTAGES;
       const uint32_t qph = (qi / QSTAGES) & 1;
       if (!__all_sync(0xffffffffu, mbar_wait(&qfull[qs], qph, sAbort, p.dev_err))) break;
-      for (int x = e.x_begin & ~3; x < e.x_end; x += BN, ++it) {
+      const int2 xw = sXwin[qs];
+      if (xw.y <= xw.x) break;
+      for (int x = xw.x & ~3; x < xw.y; x += BN, ++it) {
         const int s = it % S;
         const uint32_t ph = (it / S) & 1;
         const int buf = it % NBUF;
@@ -325,7 +360,6 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
       }
       if (lane == 0) mma_commit(&qempty[qs]);
       __syncwarp();
-      ++qi;
     }
   } else if (warp >= E_EPI0) {
     // ---------------- epilogue ----------------
@@ -349,21 +383,20 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
                                    (int64_t)ew * esub + (int64_t)lane * lsub
                              : nullptr;
     int nhits = 0;
-    for (int item = blockIdx.x; ok && item < n_items; item += gridDim.x) {
-      const EmitItem e = p.items[item];
-      if (e.x_end <= e.x_begin) continue;
+    for (; ok; ++qi) {
       const int qs = qi % QSTAGES;
       const uint32_t qph = (qi / QSTAGES) & 1;
       if (!__all_sync(0xffffffffu, mbar_wait(&qfull[qs], qph, sAbort, p.dev_err))) break;
+      const int2 xw = sXwin[qs];
       const int myq = sRowQ[qs * BM + row];
       const float myT = sRowT[qs * BM + row];  // -T(q) / 2: emit where the accumulator reaches it
       __syncwarp();
       if (lane == 0) mbar_arrive(&qempty[qs]);
-      ++qi;
+      if (xw.y <= xw.x) break;  // the end mark
       float* cs = p.out.cand_score + (int64_t)(myq >= 0 ? myq : 0) * cap;
       int* cr = p.out.cand_row + (int64_t)(myq >= 0 ? myq : 0) * cap;
       int* cc = p.out.cand_cnt + (myq >= 0 ? myq : 0);
-      for (int x = e.x_begin & ~3; x < e.x_end; x += BN, ++it) {
+      for (int x = xw.x & ~3; x < xw.y; x += BN, ++it) {
         const int buf = it % NBUF;
         const uint32_t aph = (it / NBUF) & 1;
         if (!__all_sync(0xffffffffu, mbar_wait(&tfull[buf], aph, sAbort, p.dev_err))) {
@@ -381,8 +414,8 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[buf]);
-        const int lo = e.x_begin - x - part * COLS;  // first valid column of the slice
-        const int hi = e.x_end - x - part * COLS;    // one past the last valid column
+        const int lo = xw.x - x - part * COLS;  // first valid column of the slice
+        const int hi = xw.y - x - part * COLS;    // one past the last valid column
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
           if (!(c * 32 < hi && c * 32 + 32 > lo)) continue;  // no window column in the chunk
