@@ -304,13 +304,16 @@ __global__ void __launch_bounds__(WARPS * 32) select_kernel(SelectArgs a) {
 // every point whose low-precision score passed the query's threshold, which
 // includes every point within g(q) >= its k-th neighbour distance -- so the
 // true k nearest are among the candidates and no certificate is needed.
-//  1. s_k = the k-th smallest candidate score (bitwise search over the
-//     order-preserving integer keys of the scores, counting with ballots);
+//  1. s_k = the k-th smallest candidate score (up to 64 candidates and
+//     k <= 16: k rounds of warp minimum over keys held in registers; else a
+//     bitwise search over the order-preserving integer keys of the scores);
 //     k distinct points score <= s_k, so U = dist_upper(s_k) bounds the k-th
 //     neighbour distance, and only candidates scoring <= score_bound(U) can
 //     be among the k nearest;
-//  2. those (normally k plus a few) are compacted into shared memory,
-//     re-ranked in FP32 and kept per lane sorted by (rho, id);
+//  2. those (normally k plus a few) are compacted into shared memory and
+//     re-ranked in FP32, eight lanes per candidate row (coalesced reads,
+//     partial sums of d / 8 terms, a three-level tree), then kept per lane
+//     sorted by (rho, id);
 //  3. c_out rounds of warp arg-min give ranks 0 .. c_out - 1, one per lane;
 //     near-ties go through the FP64 step.
 // A buffer that overflowed, holds fewer than k entries, or leaves more than
@@ -326,8 +329,94 @@ __device__ __forceinline__ float key_score(unsigned k) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
+// rho(q, x) of a candidate row by the eight lanes of a group (g8 = lane % 8):
+// lane g8 sums elements g8, g8 + 8, ... (float4 steps when rows allow it),
+// then the group adds its eight partial sums as a tree; every lane of the
+// group returns the result.  FP32 error: d / 8 + 3 roundings of the sum.
+__device__ __forceinline__ float rerank_rho8(const float* qr, const float* xr, int d, int metric,
+                                             int g8) {
+  float p = 0.f;
+  if ((d & 3) == 0 && ((reinterpret_cast<uintptr_t>(qr) | reinterpret_cast<uintptr_t>(xr)) & 15) == 0) {
+    const float4* q4 = reinterpret_cast<const float4*>(qr);
+    const float4* x4 = reinterpret_cast<const float4*>(xr);
+    for (int i = g8; i < d / 4; i += 8) {
+      const float4 a = q4[i], b = x4[i];
+      const float t0 = a.x - b.x, t1 = a.y - b.y, t2 = a.z - b.z, t3 = a.w - b.w;
+      if (metric == RBC_L2) {
+        p = fmaf(t0, t0, p);
+        p = fmaf(t1, t1, p);
+        p = fmaf(t2, t2, p);
+        p = fmaf(t3, t3, p);
+      } else {
+        p += fabsf(t0) + fabsf(t1) + fabsf(t2) + fabsf(t3);
+      }
+    }
+  } else {
+    for (int i = g8; i < d; i += 8) {
+      const float t = qr[i] - xr[i];
+      p = metric == RBC_L2 ? fmaf(t, t, p) : p + fabsf(t);
+    }
+  }
+  p += __shfl_xor_sync(0xffffffffu, p, 1);
+  p += __shfl_xor_sync(0xffffffffu, p, 2);
+  p += __shfl_xor_sync(0xffffffffu, p, 4);
+  return metric == RBC_L2 ? sqrtf(p) : p;
+}
+
+// The k-th smallest (k <= 16) of the n keys key(e), e < n, in one pass: each
+// lane keeps the 16 smallest of its keys sorted, then k rounds of a warp
+// minimum over the lists' heads (a lane holds at most k of the k smallest).
+template <typename KeyFn>
+__device__ __forceinline__ unsigned kth_smallest16(int n, int k, int lane, KeyFn key) {
+  unsigned t[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) t[j] = 0xffffffffu;
+  for (int e = lane; e < n; e += 32) {
+    unsigned v = key(e);
+    if (v < t[15]) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const unsigned lo = min(t[j], v);
+        v = max(t[j], v);
+        t[j] = lo;
+      }
+    }
+  }
+  int head = 0;
+  unsigned res = 0xffffffffu;
+  for (int r = 0; r < k; ++r) {
+    unsigned h = 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (j == head) h = t[j];
+    unsigned mn = h;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    res = mn;
+    const unsigned holders = __ballot_sync(0xffffffffu, h == mn);
+    if (lane == __ffs(holders) - 1) ++head;
+  }
+  return res;
+}
+
+// The k-th smallest candidate score key of a query's buffer (cnt >= k).
+__device__ __forceinline__ unsigned kth_score_key(const float* sc, int cnt, int k, int lane) {
+  if (k <= 16) return kth_smallest16(cnt, k, lane, [&](int e) { return score_key(sc[e]); });
+  unsigned kth = 0;
+  for (int bit = 31; bit >= 0; --bit) {
+    const unsigned t = kth | (1u << bit);
+    int c = 0;
+    for (int e = lane; e < cnt; e += 32) c += score_key(sc[e]) < t;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (c < k) kth = t;
+  }
+  return kth;
+}
+
 __global__ void __launch_bounds__(WARPS * 32) select_cands_kernel(CandSelectArgs a) {
   __shared__ int stage[WARPS][RERANK_MAX];
+  __shared__ float dstage[WARPS][RERANK_MAX];
   const int wib = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int64_t wi = (int64_t)blockIdx.x * WARPS + wib;
@@ -350,13 +439,25 @@ __global__ void __launch_bounds__(WARPS * 32) select_cands_kernel(CandSelectArgs
   const int* cr = a.cand_row + q * a.cap;
   // ---- 1. k-th smallest score ----
   unsigned kth = 0;
-  for (int bit = 31; bit >= 0; --bit) {
-    const unsigned t = kth | (1u << bit);
-    int c = 0;
-    for (int e = lane; e < cnt; e += 32) c += score_key(sc[e]) < t;
+  if (cnt <= 64 && k <= 16) {
+    unsigned k0 = lane < cnt ? score_key(sc[lane]) : 0xffffffffu;
+    unsigned k1 = lane + 32 < cnt ? score_key(sc[lane + 32]) : 0xffffffffu;
+    for (int r = 0; r < k; ++r) {
+      unsigned mn = min(k0, k1);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (c < k) kth = t;
+      for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      kth = mn;
+      // take one copy of the minimum out: the lowest lane holding it
+      const unsigned holders = __ballot_sync(0xffffffffu, k0 == mn || k1 == mn);
+      if (lane == __ffs(holders) - 1) {
+        if (k0 == mn)
+          k0 = 0xffffffffu;
+        else
+          k1 = 0xffffffffu;
+      }
+    }
+  } else {
+    kth = kth_score_key(sc, cnt, k, lane);
   }
   const float qn = a.q_lpnorm[q], qe = a.q_err[q];
   const float xe = __uint_as_float(*a.x_err_max_bits), xn = __uint_as_float(*a.x_norm_max_bits);
@@ -385,6 +486,15 @@ __global__ void __launch_bounds__(WARPS * 32) select_cands_kernel(CandSelectArgs
   __syncwarp();
   const int d = a.d;
   const float* qr = a.Q32 + q * d;
+  // FP32 distances of the survivors, four rows at a time
+  float* dst = dstage[wib];
+  for (int e0 = 0; e0 < nre; e0 += 4) {
+    const int e = e0 + (lane >> 3);
+    const int row = e < nre ? stg[e] : stg[0];
+    const float v = rerank_rho8(qr, a.X32 + (int64_t)row * d, d, a.metric, lane & 7);
+    if ((lane & 7) == 0 && e < nre) dst[e] = v;
+  }
+  __syncwarp();
   float ls[RERANK_PL];
   int li[RERANK_PL], lr[RERANK_PL];
 #pragma unroll
@@ -395,7 +505,7 @@ __global__ void __launch_bounds__(WARPS * 32) select_cands_kernel(CandSelectArgs
   }
   for (int e = lane; e < nre; e += 32) {
     const int row = stg[e];
-    float v = rerank_rho(qr, a.X32 + (int64_t)row * d, d, a.metric);
+    float v = dst[e];
     int id = a.xid ? a.xid[row] : row;
     int rw = row;
 #pragma unroll
@@ -589,7 +699,12 @@ __global__ void __launch_bounds__(GFB_THREADS) group_fallback_kernel(GroupFallba
 // select_cands.
 template <int CW>
 __global__ void __launch_bounds__(WARPS * 32) select_stream_kernel(CandSelectArgs a) {
-  const int lane = threadIdx.x & 31;
+  constexpr int BATCH = 256;  // survivors re-ranked together
+  __shared__ int s_row[WARPS][BATCH];
+  __shared__ float s_rho[WARPS][BATCH];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int* srow = s_row[wib];
+  float* srho = s_rho[wib];
   const int64_t nw = *a.stream_count;
   const int k = a.k, d = a.d;
   const float xe = __uint_as_float(*a.x_err_max_bits), xn = __uint_as_float(*a.x_norm_max_bits);
@@ -600,15 +715,7 @@ __global__ void __launch_bounds__(WARPS * 32) select_stream_kernel(CandSelectArg
     const float* sc = a.cand_score + q * a.cap;
     const int* cr = a.cand_row + q * a.cap;
     // k-th smallest score -> survivor bound (as in select_cands)
-    unsigned kth = 0;
-    for (int bit = 31; bit >= 0; --bit) {
-      const unsigned t = kth | (1u << bit);
-      int c = 0;
-      for (int e = lane; e < cnt; e += 32) c += score_key(sc[e]) < t;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-      if (c < k) kth = t;
-    }
+    const unsigned kth = kth_score_key(sc, cnt, k, lane);
     const float qn = a.q_lpnorm[q], qe = a.q_err[q];
     const float smax =
         score_bound(dist_upper(key_score(kth), qn, qe, xe, xn, d), qn, qe, xe, xn, d);
@@ -621,10 +728,30 @@ __global__ void __launch_bounds__(WARPS * 32) select_stream_kernel(CandSelectArg
       li[j] = INT32_MAX;
       lr[j] = -1;
     }
-    for (int e = lane; e < cnt; e += 32) {
-      if (!(sc[e] <= smax)) continue;
-      const int row = cr[e];
-      float v = rerank_rho(qr, a.X32 + (int64_t)row * d, d, a.metric);
+    // survivors in batches: compacted into shared memory, FP32 distances by
+    // groups of eight lanes (four rows at a time), then inserted per lane
+    const unsigned lt = (1u << lane) - 1u;
+    for (int b0 = 0; b0 < cnt; b0 += BATCH) {
+      const int b1 = min(cnt, b0 + BATCH);
+      int ns = 0;
+      for (int e0 = b0; e0 < b1; e0 += 32) {
+        const int e = e0 + lane;
+        const bool pass = e < b1 && sc[e] <= smax;
+        const unsigned bal = __ballot_sync(0xffffffffu, pass);
+        if (pass) srow[ns + __popc(bal & lt)] = cr[e];
+        ns += __popc(bal);
+      }
+      __syncwarp();
+      for (int e0 = 0; e0 < ns; e0 += 4) {
+        const int e = e0 + (lane >> 3);
+        const int row = srow[e < ns ? e : 0];
+        const float v = rerank_rho8(qr, a.X32 + (int64_t)row * d, d, a.metric, lane & 7);
+        if ((lane & 7) == 0 && e < ns) srho[e] = v;
+      }
+      __syncwarp();
+      for (int e = lane; e < ns; e += 32) {
+      const int row = srow[e];
+      float v = srho[e];
       int id = a.xid ? a.xid[row] : row;
       if (!pair_lt(v, id, ls[CW - 1], li[CW - 1])) continue;
       int rw = row;
@@ -641,6 +768,8 @@ __global__ void __launch_bounds__(WARPS * 32) select_stream_kernel(CandSelectArg
         id = ti;
         rw = tr;
       }
+      }
+      __syncwarp();
     }
     int head = 0;
     float rho = INFINITY;
