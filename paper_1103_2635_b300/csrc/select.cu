@@ -702,9 +702,11 @@ __global__ void __launch_bounds__(WARPS * 32) select_stream_kernel(CandSelectArg
   constexpr int BATCH = 256;  // survivors re-ranked together
   __shared__ int s_row[WARPS][BATCH];
   __shared__ float s_rho[WARPS][BATCH];
+  __shared__ int s_id[WARPS][BATCH];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int* srow = s_row[wib];
   float* srho = s_rho[wib];
+  int* sid = s_id[wib];
   const int64_t nw = *a.stream_count;
   const int k = a.k, d = a.d;
   const float xe = __uint_as_float(*a.x_err_max_bits), xn = __uint_as_float(*a.x_norm_max_bits);
@@ -742,17 +744,21 @@ __global__ void __launch_bounds__(WARPS * 32) select_stream_kernel(CandSelectArg
         ns += __popc(bal);
       }
       __syncwarp();
-      for (int e0 = 0; e0 < ns; e0 += 4) {
-        const int e = e0 + (lane >> 3);
-        const int row = srow[e < ns ? e : 0];
+      // ids first (independent loads), then distances two rounds at a time
+      for (int e = lane; e < ns; e += 32) sid[e] = a.xid ? a.xid[srow[e]] : srow[e];
+      for (int e0 = 0; e0 < ns; e0 += 8) {
+        const int e = e0 + (lane >> 3), f = e + 4;
+        const int row = srow[e < ns ? e : 0], row2 = srow[f < ns ? f : 0];
         const float v = rerank_rho8(qr, a.X32 + (int64_t)row * d, d, a.metric, lane & 7);
+        const float v2 = rerank_rho8(qr, a.X32 + (int64_t)row2 * d, d, a.metric, lane & 7);
         if ((lane & 7) == 0 && e < ns) srho[e] = v;
+        if ((lane & 7) == 0 && f < ns) srho[f] = v2;
       }
       __syncwarp();
       for (int e = lane; e < ns; e += 32) {
       const int row = srow[e];
       float v = srho[e];
-      int id = a.xid ? a.xid[row] : row;
+      int id = sid[e];
       if (!pair_lt(v, id, ls[CW - 1], li[CW - 1])) continue;
       int rw = row;
 #pragma unroll
