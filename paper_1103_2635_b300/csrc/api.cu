@@ -1563,10 +1563,8 @@ int64_t bound_own_list(const rbc_index* ix, int64_t mb) {
 }
 
 int64_t bound_window_batch(const rbc_index* ix, int64_t mb, int k) {
-  const int d = ix->d, dpad = ix->dpad, sms = sm_count();
+  const int dpad = ix->dpad, sms = sm_count();
   const int64_t n_r = ix->n_r, n = ix->list_entries;
-  const int64_t max_tiles = cdiv(mb, TQ) + std::min<int64_t>(n_r, mb);
-  const int64_t rows_cap = max_tiles * TQ;
   const int64_t nbins = n_r * window_buckets();
   const int64_t nslices = (int64_t)sms * ARENA_SUBSEG * 32;
   const int64_t arena_lane = std::max<int64_t>(ARENA_MIN_LANE, cdiv(mb * 256, nslices));
