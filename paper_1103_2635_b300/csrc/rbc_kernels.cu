@@ -192,9 +192,13 @@ __global__ void list_radii_kernel(const float* __restrict__ dist_by_id, const in
 
 // One warp per query row of D (distances >= 0, so their bit patterns order
 // like their values): gamma_1 and the nearest column by a warp arg-min
-// (ties to the smaller column); gamma_k by a bitwise search for the k-th
-// smallest bit pattern, counting with the whole warp (rows of up to 1024
-// values are held in registers).
+// (ties to the smaller column); gamma_k, the k-th smallest value.  Rows of up
+// to 1024 values are held in registers, 32 per lane, and gamma_k is found in
+// two short selections: T = the k-th smallest of the 32 lane minima bounds
+// gamma_k from above (k lanes hold a value <= T), the values <= T (normally
+// a few more than k) are compacted one per lane, and k rounds of a warp
+// minimum over them give gamma_k exactly.  Rows with more than 32 values <= T,
+// and longer rows, use a bitwise search for the k-th smallest bit pattern.
 template <bool CACHED>
 __global__ void row_stats_kernel(const float* __restrict__ D, int64_t m, int n_r, int k,
                                  float* __restrict__ g1, float* __restrict__ gk,
@@ -236,7 +240,52 @@ __global__ void row_stats_kernel(const float* __restrict__ D, int64_t m, int n_r
     }
   }
   float kth = INFINITY;
-  if (k <= n_r) {
+  bool done = false;
+  if constexpr (CACHED) {
+  if (k <= n_r && k <= 32) {
+    // the k-th smallest of {vals[j] ... } by k rounds of a warp minimum over
+    // one value per lane (x); the lane holding the minimum drops it
+    auto kth_of_lanes = [&](unsigned x) {
+      unsigned res = 0xffffffffu;
+      for (int r = 0; r < k; ++r) {
+        unsigned mn = x;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        res = mn;
+        const unsigned holders = __ballot_sync(0xffffffffu, x == mn);
+        if (lane == __ffs(holders) - 1) x = 0xffffffffu;
+      }
+      return res;
+    };
+    unsigned lmin = vals[0];
+#pragma unroll
+    for (int j = 1; j < 32; ++j) lmin = min(lmin, vals[j]);
+    const unsigned T = kth_of_lanes(lmin);
+    int c = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) c += vals[j] <= T;
+    int pre = c;  // inclusive prefix over lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, pre, o);
+      if (lane >= o) pre += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, pre, 31);
+    if (total <= 32) {
+      __shared__ unsigned cand[8][32];  // one slot row per warp of the block
+      unsigned* cw = cand[(threadIdx.x >> 5) & 7];
+      int pos = pre - c;
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (vals[j] <= T) cw[pos++] = vals[j];
+      __syncwarp();
+      const unsigned x = lane < total ? cw[lane] : 0xffffffffu;
+      kth = __uint_as_float(kth_of_lanes(x));
+      done = true;
+    }
+  }
+  }
+  if (!done && k <= n_r) {
     unsigned res = 0;
     for (int bit = 31; bit >= 0; --bit) {
       const unsigned t = res | (1u << bit);

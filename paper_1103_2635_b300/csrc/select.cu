@@ -329,40 +329,6 @@ __device__ __forceinline__ float key_score(unsigned k) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-// rho(q, x) of a candidate row by the eight lanes of a group (g8 = lane % 8):
-// lane g8 sums elements g8, g8 + 8, ... (float4 steps when rows allow it),
-// then the group adds its eight partial sums as a tree; every lane of the
-// group returns the result.  FP32 error: d / 8 + 3 roundings of the sum.
-__device__ __forceinline__ float rerank_rho8(const float* qr, const float* xr, int d, int metric,
-                                             int g8) {
-  float p = 0.f;
-  if ((d & 3) == 0 && ((reinterpret_cast<uintptr_t>(qr) | reinterpret_cast<uintptr_t>(xr)) & 15) == 0) {
-    const float4* q4 = reinterpret_cast<const float4*>(qr);
-    const float4* x4 = reinterpret_cast<const float4*>(xr);
-    for (int i = g8; i < d / 4; i += 8) {
-      const float4 a = q4[i], b = x4[i];
-      const float t0 = a.x - b.x, t1 = a.y - b.y, t2 = a.z - b.z, t3 = a.w - b.w;
-      if (metric == RBC_L2) {
-        p = fmaf(t0, t0, p);
-        p = fmaf(t1, t1, p);
-        p = fmaf(t2, t2, p);
-        p = fmaf(t3, t3, p);
-      } else {
-        p += fabsf(t0) + fabsf(t1) + fabsf(t2) + fabsf(t3);
-      }
-    }
-  } else {
-    for (int i = g8; i < d; i += 8) {
-      const float t = qr[i] - xr[i];
-      p = metric == RBC_L2 ? fmaf(t, t, p) : p + fabsf(t);
-    }
-  }
-  p += __shfl_xor_sync(0xffffffffu, p, 1);
-  p += __shfl_xor_sync(0xffffffffu, p, 2);
-  p += __shfl_xor_sync(0xffffffffu, p, 4);
-  return metric == RBC_L2 ? sqrtf(p) : p;
-}
-
 // The k-th smallest (k <= 16) of the n keys key(e), e < n, in one pass: each
 // lane keeps the 16 smallest of its keys sorted, then k rounds of a warp
 // minimum over the lists' heads (a lane holds at most k of the k smallest).

@@ -111,34 +111,16 @@ __global__ void own_kth_lp_kernel(const float* __restrict__ ps, const int* __res
       c1 = -1;
     }
   }
+  // FP32 distances of the k chosen rows, four at a time by groups of eight
+  // lanes (coalesced row reads); group g of round r takes lane 4r + g's row
   float rho = 0.0f;
-  bool missing = lane < k && mine < 0;
-  if (lane < k && mine >= 0) {
-    const float* qr = Q32 + (int64_t)q * d;
-    const float* xr = X32 + (int64_t)mine * d;
-    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
-    int i = 0;
-    for (; i + 4 <= d; i += 4) {
-      const float t0 = qr[i] - xr[i], t1 = qr[i + 1] - xr[i + 1];
-      const float t2 = qr[i + 2] - xr[i + 2], t3 = qr[i + 3] - xr[i + 3];
-      if (metric == RBC_L2) {
-        p0 = fmaf(t0, t0, p0);
-        p1 = fmaf(t1, t1, p1);
-        p2 = fmaf(t2, t2, p2);
-        p3 = fmaf(t3, t3, p3);
-      } else {
-        p0 += fabsf(t0);
-        p1 += fabsf(t1);
-        p2 += fabsf(t2);
-        p3 += fabsf(t3);
-      }
-    }
-    for (; i < d; ++i) {
-      const float t0 = qr[i] - xr[i];
-      if (metric == RBC_L2) p0 = fmaf(t0, t0, p0); else p0 += fabsf(t0);
-    }
-    const float sum = (p0 + p1) + (p2 + p3);
-    rho = metric == RBC_L2 ? sqrtf(sum) : sum;
+  const bool missing = lane < k && mine < 0;
+  const float* qr = Q32 + (int64_t)q * d;
+  for (int r0 = 0; r0 < k; r0 += 4) {
+    const int src = r0 + (lane >> 3);
+    const int col = __shfl_sync(0xffffffffu, mine, src & 31);
+    const float v = rerank_rho8(qr, X32 + (int64_t)(col >= 0 ? col : 0) * d, d, metric, lane & 7);
+    if (src < k && col >= 0) rho = fmaxf(rho, v);
   }
   const bool any_missing = __any_sync(0xffffffffu, missing);
 #pragma unroll
