@@ -1143,7 +1143,9 @@ int own_list_bound(const rbc_index* ix, const float* Qb, int64_t mb, const int64
   RBC_TRY(ar.alloc(&pi, gq.max_tiles * TQ * 2 * C));
   LpMatrix Qm{alp, anorm, gq.rows_cap, ix->dpad, ix->storage, nullptr, ascale};
   LpMatrix Xm{ix->Xlp, ix->xnorm, ix->list_entries, ix->dpad, ix->storage, nullptr, ix->xscale};
-  RBC_TRY(launch_bf_tc_topc(Qm, Xm, C, gq.w, TopOut{ps, pi, nullptr}, sm_count(), st, dev_err));
+  TileWork wo = gq.w;
+  wo.strided = true;  // one item per query tile: a popular list's tiles spread over CTAs
+  RBC_TRY(launch_bf_tc_topc(Qm, Xm, C, wo, TopOut{ps, pi, nullptr}, sm_count(), st, dev_err));
   return launch_own_kth_lp(ps, pi, C, gq.qsrc, gq.rows_cap, k, Qb, ix->X32, ix->d, ix->metric,
                            rerank_eps_host(ix->d) + 8.0f * U32, own, st);
 }

@@ -191,15 +191,18 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
   const TileWork& w = p.w;
   const int n_items = w.num_items_dev ? *w.num_items_dev : w.num_items;
   // a contiguous range of items per CTA, so that consecutive items of one
-  // query tile stay on one CTA and the epilogue can carry its lists across them
-  const int ib = (int)((int64_t)blockIdx.x * n_items / gridDim.x);
-  const int ie = (int)((int64_t)(blockIdx.x + 1) * n_items / gridDim.x);
+  // query tile stay on one CTA and the epilogue can carry its lists across
+  // them; work whose query tiles are single items may take them strided
+  // instead (neighbouring items, often of similar size, spread over CTAs)
+  const int ib = w.strided ? (int)blockIdx.x : (int)((int64_t)blockIdx.x * n_items / gridDim.x);
+  const int ie = w.strided ? n_items : (int)((int64_t)(blockIdx.x + 1) * n_items / gridDim.x);
+  const int istep = w.strided ? (int)gridDim.x : 1;
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     uint32_t it = 0, qi = 0;
     bool ok = true;
-    for (int item = ib; ok && item < ie; ++item, ++qi) {
+    for (int item = ib; ok && item < ie; item += istep, ++qi) {
       int q0, nq, sb, se, slot;
       item_info(w, item, q0, nq, sb, se, slot);
       if (!__all_sync(0xffffffffu, mbar_wait(qempty, (qi & 1) ^ 1, sAbort, p.dev_err))) {
@@ -251,7 +254,7 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
     // ---------------- MMA issuer ----------------
     uint32_t it = 0, qi = 0;
     bool ok = true;
-    for (int item = ib; ok && item < ie; ++item, ++qi) {
+    for (int item = ib; ok && item < ie; item += istep, ++qi) {
       int q0, nq, sb, se, slot;
       item_info(w, item, q0, nq, sb, se, slot);
       if (!__all_sync(0xffffffffu, mbar_wait(qfull, qi & 1, sAbort, p.dev_err))) {
@@ -329,13 +332,13 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
     int lpos = 0;              // position of the largest entry of ls
     float tau_own = INFINITY;  // = ls[lpos]
     float tau = INFINITY;      // effective threshold: min(own max, other half's max)
-    for (int item = ib; ok && item < ie; ++item) {
+    for (int item = ib; ok && item < ie; item += istep) {
       int q0, nq, sb, se, slot;
       item_info(w, item, q0, nq, sb, se, slot);
       int pq0 = -1, pnq, psb, pse, pslot;
-      if (item > ib) item_info(w, item - 1, pq0, pnq, psb, pse, pslot);
+      if (item - istep >= ib) item_info(w, item - istep, pq0, pnq, psb, pse, pslot);
       int nq0 = -1, nnq, nsb, nse, nslot;
-      if (item + 1 < ie) item_info(w, item + 1, nq0, nnq, nsb, nse, nslot);
+      if (item + istep < ie) item_info(w, item + istep, nq0, nnq, nsb, nse, nslot);
       // FP8: score = |x~|^2 - 2 s_q s_x (a.b); cq = -2 s_q for this row
       const float cq = FP8 ? (row < nq ? -2.0f * p.qscale[q0 + row] : 0.0f) : -2.0f;
       if (pq0 != q0) {  // first item of a run of the same query tile

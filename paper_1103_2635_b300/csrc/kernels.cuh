@@ -24,6 +24,9 @@ struct TileWork {
   // optional (tensor-core kernels, list form): K blocks of 64 columns that
   // item tile t multiplies (the rest of its rows are zero); nullptr = all
   const int8_t* tile_kb = nullptr;
+  // tensor-core top-C kernel: every query tile is one item, so CTAs may take
+  // items strided (balances runs of large items) instead of in ranges
+  bool strided = false;
 };
 
 // Per-(slot, query row, sub-list) top-C output of a tile kernel.
