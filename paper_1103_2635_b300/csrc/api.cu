@@ -1383,10 +1383,11 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   // hit arena: each epilogue thread appends its emissions to its own slice
   // (no atomics in the kernel); a post-pass fills the per-query buffers.  The
   // slices together hold 256 records per query of the batch (about 5x the
-  // candidates of clustered 64-d data) and at least ARENA_MIN_LANE each: in
-  // a small batch a chunk holds few queries, so a query with thousands of
+  // candidates of clustered 64-d data) and at least ARENA_MIN_LANE each: in a
+  // small batch a chunk holds few queries, so a query with thousands of
   // candidates fills the slices of the few rows it occupies.  If one
-  // overflows, the batch is emitted again with direct per-query appends.
+  // overflows, the batch is emitted again with direct per-query appends, and
+  // so are the index's next few searches.
   const int64_t nslices = (int64_t)sms * ARENA_SUBSEG * 32;
   const int arena_lane = (int)std::min<int64_t>(
       INT32_MAX / (4 * ARENA_SUBSEG * 32), std::max<int64_t>(ARENA_MIN_LANE, (mb * 256 + nslices - 1) / nslices));
@@ -1435,7 +1436,12 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   a.counters = lc;
   a.stream_rows = srows;
   a.stream_count = lc + 4;
-  for (int attempt = 0;; ++attempt) {
+  int left = ix->emit_direct_left.load(std::memory_order_relaxed);
+  bool skip_arena = false;
+  while (left > 0 && !skip_arena) {
+    skip_arena = const_cast<rbc_index*>(ix)->emit_direct_left.compare_exchange_weak(left, left - 1);
+  }
+  for (int attempt = skip_arena ? 1 : 0;; ++attempt) {
     const bool direct = attempt > 0;
     RBC_CUDA(cudaMemsetAsync(cc, 0, mb * sizeof(int), st));
     RBC_CUDA(cudaMemsetAsync(arena_ovf, 0, sizeof(int), st));
@@ -1470,7 +1476,15 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
       set_error("windowed stage two reported device error flags 0x%x", (unsigned)early[1]);
       return (early[1] & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
     }
-    if (!direct && early[2]) continue;  // an arena slice overflowed: emit again directly
+    if (!direct && early[2]) {
+      // an arena slice overflowed: emit again directly, and so do the
+      // index's next searches (a run twice as long as the last one)
+      rbc_index* mix = const_cast<rbc_index*>(ix);
+      const int run = std::min(1024, std::max(8, 2 * mix->emit_direct_run.load()));
+      mix->emit_direct_run.store(run, std::memory_order_relaxed);
+      mix->emit_direct_left.store(run, std::memory_order_relaxed);
+      continue;
+    }
     if (early[0] > mb / 16 + 64) {
       // Many overflowing queries (clustered data whose points tie within the
       // rounding slack by the thousand): a dense pass would overflow again,

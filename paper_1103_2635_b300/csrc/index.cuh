@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <vector>
 
 #include "common.cuh"
@@ -32,6 +33,14 @@ struct rbc_index {
   float* rnorm = nullptr;     // [n_r]
   float* xscale = nullptr;    // FP8: [list_entries + NORM_PAD] per-row power-of-two scales
   float* rscale = nullptr;    // FP8: [n_r]
+  // windowed search: searches left that emit their candidates directly into
+  // the per-query buffers instead of through the hit arena.  A batch whose
+  // arena overflowed (a data set that emits thousands of candidates per
+  // query, unevenly over the arena's per-thread slices) sets it to a run
+  // length that starts at 8 and doubles with every further overflow (at most
+  // 1024), so the next searches skip the arena attempt that would fail again.
+  std::atomic<int> emit_direct_left{0};
+  std::atomic<int> emit_direct_run{0};
 
   template <typename T>
   int alloc(T** out, int64_t count) {

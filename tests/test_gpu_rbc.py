@@ -245,6 +245,28 @@ def test_window_candidate_overflow_goes_to_fp32_research():
     np.testing.assert_array_equal(ids[:3], np.tile(np.arange(5000, 5010), (3, 1)))
 
 
+def test_searches_after_an_arena_overflow_agree():
+    # the 9000 copies overflow the emission's hit arena: that batch is emitted
+    # again with direct appends, the index's next searches emit directly (a
+    # run of 8, then 16 after the retry overflows again), and every one of
+    # them gives the same answer
+    X = synth.iid_normal(30000, 24, 3)
+    X[5000:14000] = X[5000]
+    Q = np.concatenate([X[5000:5001].repeat(3, 0), synth.iid_normal(300, 24, 4)]).astype(np.float32)
+    idx = build(X, 170, storage=rbc.BF16, seed=6)
+    ids0, dist0 = search(idx, Q, 10)
+    for _ in range(12):
+        ids, dist = search(idx, Q, 10)
+        np.testing.assert_array_equal(ids, ids0)
+        np.testing.assert_array_equal(dist, dist0)
+    o_ids, o_rho = oracle.bf(Q, X, 10, "l2")
+    check_knn(Q, X, ids0, dist0, o_ids, o_rho)
+    Q2 = synth.iid_normal(500, 24, 5)
+    ids2, dist2 = search(idx, Q2, 5)
+    o_ids, o_rho = oracle.bf(Q2, X, 5, "l2")
+    check_knn(Q2, X, ids2, dist2, o_ids, o_rho)
+
+
 def test_window_stats_count_fewer_pairs_than_tile_union():
     mod = synth.SubspaceModel(d=64, k=8, noise_var=0.01, seed=0)
     X = mod.sample(120000, 0)
