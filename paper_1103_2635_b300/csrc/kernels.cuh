@@ -221,8 +221,8 @@ int launch_own_kth_lp(const float* ps, const int* pi, int C, const int* qsrc, in
 // Kept (q, r) pairs binned by (r, bucket of the window start rho(q, r) - g(q)),
 // window_buckets() per r: rmin/rmax [n_r] (order-preserving keys of the
 // extreme window starts), q_kept [m], counts
-// [window_pair_blocks(m)][n_r nb] (per query block, then its prefix within
-// each bin), totals [n_r nb], bin_off [n_r nb + 1]; then the pairs
+// [n_r nb][window_pair_blocks(m)] (per bin and query block, then the block's
+// prefix within the bin), totals [n_r nb], bin_off [n_r nb + 1]; then the pairs
 // themselves: pairs[i] = (query, rho(q, r) as float bits).
 int window_buckets();
 int64_t window_pair_blocks(int64_t m);

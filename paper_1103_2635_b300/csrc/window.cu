@@ -228,8 +228,8 @@ __device__ __forceinline__ int bucket_of(float v, float lo, float scale) {
 
 
 // Passes 2 and 3.  Count: every (r, bucket) bin of the block's pairs ->
-// counts[block x][bin].  Scatter: the pairs, at the bins' offsets plus the
-// block's prefix (off[block x][bin], from the column scan).
+// counts[bin][block x].  Scatter: the pairs, at the bins' offsets plus the
+// block's prefix (counts[bin][block x] after the column scan).
 template <bool SCATTER>
 __global__ void __launch_bounds__(WW * 32)
 wbin_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __restrict__ g,
@@ -311,26 +311,55 @@ __global__ void chunk_count_kernel(const int* __restrict__ bin_off, int nb, int 
   if (r < n_r) out[r] = (bin_off[(r + 1) * nb] - bin_off[r * nb] + TQ - 1) / TQ;
 }
 
-// Warp-cooperative search in a sorted array: the first index i in [0, n)
-// with a[i] >= v (LOWER) or a[i] > v (!LOWER), n if none.  Each round probes
-// 32 evenly spaced positions at once and keeps the gap holding the answer,
-// so a list of N entries costs about log_32(N) dependent loads.
-template <bool LOWER>
-__device__ __forceinline__ int warp_bound(const float* __restrict__ a, int n, float v, int lane) {
-  int lo = 0, hi = n;  // the answer lies in [lo, hi]
+// Warp-cooperative searches in sorted arrays: each round probes 32 evenly
+// spaced positions at once and keeps the gap holding the answer, so an array
+// of N entries costs about log_32(N) dependent loads.
+// The two searches of a window at once: the first index with a[i] >= vlo and
+// the first with a[i] > vhi, each n if none; both probes of a round are issued
+// together, so the pair costs the dependent loads of one search.
+__device__ __forceinline__ void warp_bounds2(const float* __restrict__ a, int n, float vlo,
+                                             float vhi, int lane, int& blo, int& bhi) {
+  int lo0 = 0, hi0 = n, lo1 = 0, hi1 = n;
+  while (hi0 - lo0 > 32 || hi1 - lo1 > 32) {
+    const int64_t len0 = hi0 - lo0, len1 = hi1 - lo1;
+    const bool act0 = len0 > 32, act1 = len1 > 32;
+    const int p0 = lo0 + (int)((len0 * lane) >> 5), p1 = lo1 + (int)((len1 * lane) >> 5);
+    const float a0 = act0 ? a[p0] : 0.0f, a1 = act1 ? a[p1] : 0.0f;
+    if (act0) {
+      const int c = __popc(__ballot_sync(0xffffffffu, a0 < vlo));
+      const int nlo = c == 0 ? lo0 : lo0 + (int)((len0 * (c - 1)) >> 5) + 1;
+      hi0 = c == 32 ? hi0 : lo0 + (int)((len0 * c) >> 5);
+      lo0 = nlo;
+    }
+    if (act1) {
+      const int c = __popc(__ballot_sync(0xffffffffu, a1 <= vhi));
+      const int nlo = c == 0 ? lo1 : lo1 + (int)((len1 * (c - 1)) >> 5) + 1;
+      hi1 = c == 32 ? hi1 : lo1 + (int)((len1 * c) >> 5);
+      lo1 = nlo;
+    }
+  }
+  const int q0 = lo0 + lane, q1 = lo1 + lane;
+  const float a0 = q0 < hi0 ? a[q0] : 0.0f, a1 = q1 < hi1 ? a[q1] : 0.0f;
+  blo = lo0 + __popc(__ballot_sync(0xffffffffu, q0 < hi0 && a0 < vlo));
+  bhi = lo1 + __popc(__ballot_sync(0xffffffffu, q1 < hi1 && a1 <= vhi));
+}
+
+// The last r in [0, n_r) with off[r] <= c (off ascending, off[0] <= c),
+// probing 32 positions per round.
+__device__ __forceinline__ int warp_group_of(const int* __restrict__ off, int n_r, int c,
+                                             int lane) {
+  int lo = 0, hi = n_r;  // the answer lies in [lo, hi)
   while (hi - lo > 32) {
     const int64_t len = hi - lo;
     const int p = lo + (int)((len * lane) >> 5);
-    const bool before = LOWER ? a[p] < v : a[p] <= v;
-    const int c = __popc(__ballot_sync(0xffffffffu, before));  // probes before the answer
-    const int nlo = c == 0 ? lo : lo + (int)((len * (c - 1)) >> 5) + 1;
-    const int nhi = c == 32 ? hi : lo + (int)((len * c) >> 5);
-    lo = nlo;
+    const int cnt = __popc(__ballot_sync(0xffffffffu, off[p] <= c));  // >= 1: off[lo] <= c
+    const int nhi = cnt == 32 ? hi : lo + (int)((len * cnt) >> 5);
+    lo = lo + (int)((len * (cnt - 1)) >> 5);
     hi = nhi;
   }
   const int p = lo + lane;
-  const bool before = p < hi && (LOWER ? a[p] < v : a[p] <= v);
-  return lo + __popc(__ballot_sync(0xffffffffu, before));
+  const bool le = p < hi && off[p] <= c;
+  return lo + __popc(__ballot_sync(0xffffffffu, le)) - 1;
 }
 
 // Warps loop over chunks: the union of each chunk's windows, cut from the
@@ -351,12 +380,7 @@ window_items_kernel(const int* __restrict__ chunk_off, int n_r, const int* __res
   for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total;
        c += (gridDim.x * blockDim.x) >> 5) {
     // the group holding chunk c: last r with chunk_off[r] <= c
-    int lo_r = 0, hi_r = n_r;  // invariant: chunk_off[lo_r] <= c < chunk_off[hi_r]
-    while (hi_r - lo_r > 1) {
-      const int mid = (lo_r + hi_r) >> 1;
-      if (chunk_off[mid] <= c) lo_r = mid; else hi_r = mid;
-    }
-    const int r = lo_r;
+    const int r = warp_group_of(chunk_off, n_r, c, lane);
     const int begin = bin_off[r * nb] + (c - chunk_off[r]) * TQ;
     const int end = min(begin + TQ, bin_off[(r + 1) * nb]);
     float wlo = INFINITY, whi = -INFINITY;
@@ -373,8 +397,10 @@ window_items_kernel(const int* __restrict__ chunk_off, int n_r, const int* __res
       whi = fmaxf(whi, __shfl_xor_sync(0xffffffffu, whi, o));
     }
     const int ob = offsets[r], oe = offsets[r + 1];
-    const int xb = ob + warp_bound<true>(xdist + ob, oe - ob, wlo, lane);
-    const int xe = ob + warp_bound<false>(xdist + ob, oe - ob, whi, lane);
+    int xb, xe;
+    warp_bounds2(xdist + ob, oe - ob, wlo, whi, lane, xb, xe);
+    xb += ob;
+    xe += ob;
     if (lane == 0) {
       items[c] = EmitItem{begin, end - begin, xb, xe > xb ? xe : xb};
       if (xe > xb) {
