@@ -95,6 +95,10 @@ def parse():
     ap.add_argument("--serve-check", type=int, default=24, help="rows checked against the oracle")
     ap.add_argument("--group", action="store_true", help="grouped multi-index search measurement")
     ap.add_argument("--group-count", type=int, default=256)
+    ap.add_argument("--variants", action="store_true",
+                    help="the other search modes on the same workload: exact L1 (CUDA cores) and "
+                         "one-shot L2 (recall against the exact answer)")
+    ap.add_argument("--oneshot-s", type=int, default=0, help="one-shot list size s (0: n_r)")
     return ap.parse_args()
 
 
@@ -714,9 +718,103 @@ def run_group(args, rank, world, local):
         ix.close()
 
 
+# ---------------------------------------------------------------------------
+# the other search modes: exact L1 search and one-shot search
+# ---------------------------------------------------------------------------
+def run_variants(args, rank, world, local):
+    """Exact L1 RBC (FP32, CUDA cores) against the L1 FP32 brute force, and
+    one-shot RBC (Section 5.1, bf16) with its recall against the exact
+    answer, on the same workload and query batch as the main bench line."""
+    if rank != 0:
+        return
+    import torch
+
+    import oracle
+    import paper_1103_2635_b300 as rbc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w, X, Q = workload_arrays(args.workload, 0, query_seed=rank_query_seed(rank), n=args.n, m=args.m)
+    Xd, Qd = torch.from_numpy(X).to(dev), torch.from_numpy(Q).to(dev)
+    m, k = len(Q), args.k
+    st = torch.cuda.current_stream(dev)
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            out = fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            out = fn()
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        return out, e0.elapsed_time(e1) / steps
+
+    g = np.random.default_rng(11)
+    sel = np.sort(g.choice(m, min(m, 200), replace=False))
+    res = {}
+    with ClockSampler(local) as clk:
+        # exact L1
+        idx1 = rbc.rbc_build(Xd, w.n_r, metric=rbc.L1, seed=2, storage=rbc.F32)
+        (ids1, d1), ms1 = timed(lambda: rbc.rbc_search(idx1, Qd, k), args.steps)
+        st1 = rbc.last_stats()
+        bf_m = min(m, 20000)
+        (bids, _), msb = timed(lambda: rbc.bf_search(Qd[:bf_m], Xd, k, metric=rbc.L1, storage=rbc.F32), 1)
+        o_ids, o_rho = oracle.bf(Q[sel], X, k, "l1")
+        g1 = ids1.cpu().numpy()
+        rel = np.abs(d1.cpu().numpy()[sel].astype(np.float64) - o_rho) / np.maximum(o_rho, 1e-30)
+        res["l1_exact"] = {
+            "value": m / (ms1 / 1e3), "unit": "queries/s", "ms_per_step": ms1, "storage": "f32",
+            "kept_reps_per_query": st1["kept_reps"] / m, "pairs_per_query": st1["pairs"] / m,
+            "fp32_bruteforce_qps": bf_m / (msb / 1e3),
+            "speedup_vs_fp32_bruteforce": (m / ms1) / (bf_m / msb),
+            "rows_equal_to_bruteforce": float((bids.cpu().numpy() == g1[:bf_m]).all(axis=1).mean()),
+            "oracle_sample": {"rows": len(sel), "rows_ids_equal": float((g1[sel] == o_ids).all(axis=1).mean()),
+                              "max_rel_dist_err": float(rel.max())}}
+        idx1.close()
+        # one-shot L2 (and the exact answer it is compared with)
+        s_ = args.oneshot_s or w.n_r
+        idxe = rbc.rbc_build(Xd, w.n_r, metric=rbc.L2, seed=2, storage=rbc.BF16)
+        ids_e, _ = rbc.rbc_search(idxe, Qd, k)
+        ids_e = ids_e.cpu().numpy()
+        idxe.close()
+        t0 = time.perf_counter()
+        idxo = rbc.rbc_build(Xd, w.n_r, metric=rbc.L2, seed=2, storage=rbc.BF16, mode=rbc.ONESHOT, s=s_)
+        torch.cuda.synchronize(dev)
+        build_s = time.perf_counter() - t0
+        (ids_o, d_o), mso = timed(lambda: rbc.rbc_search(idxo, Qd, k), args.steps)
+        go = ids_o.cpu().numpy()
+        hits = sum(len(np.intersect1d(a, b)) for a, b in zip(go, ids_e))
+        # parity of the one-shot answer with the oracle's one-shot search on the sample
+        reps = oracle.sample_reps(len(X), w.n_r, 2)
+        oo = oracle.build_oneshot(X, reps, s_, "l2")
+        oo_ids, oo_rho = oracle.search_oneshot(oo, Q[sel], k)[:2]
+        rel = np.abs(d_o.cpu().numpy()[sel].astype(np.float64) - oo_rho) / np.maximum(oo_rho, 1e-30)
+        # Section 7.2's quality measure: the rank of the returned nearest
+        # neighbour among all database points (0 = the true nearest)
+        ranks = oracle.rank_of(Q[sel], X, go[sel, 0], "l2")
+        res["oneshot"] = {
+            "value": m / (mso / 1e3), "unit": "queries/s", "ms_per_step": mso, "storage": "bf16", "s": s_,
+            "build_s": build_s, "recall_at_k_vs_exact": hits / (m * k),
+            "rows_equal_to_exact": float((go == ids_e).all(axis=1).mean()),
+            "rank_of_first_on_sample": {"mean": float(ranks.mean()), "exact_fraction": float((ranks == 0).mean())},
+            "oracle_oneshot_sample": {"rows": len(sel),
+                                      "rows_ids_equal": float((go[sel] == oo_ids).all(axis=1).mean()),
+                                      "max_rel_dist_err": float(rel.max())}}
+        idxo.close()
+    line = {"mode": "variants", "workload": args.workload, "n": len(X), "m": m, "d": w.d, "n_r": w.n_r,
+            "k": k, "steps": args.steps, "warmup": args.warmup, "n_gpus": 1, "data": "synthetic",
+            "clocks": clk.summary(), **res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.variants:
+        run_variants(args, rank, world, local)
+        return
     if args.group:
         run_group(args, rank, world, local)
         return
