@@ -1495,6 +1495,11 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
                                st, g));
       break;
     }
+    if (early[0] == 0) {  // no query overflowed its candidate buffer: done
+      RBC_TRY(launch_add_ints(cn.c, lc, 3, st));
+      RBC_TRY(launch_sum_i32(cc, mb, cn.sums + 3, st));
+      break;
+    }
     // Few overflowing queries (count in lc[0], on the device): k of their
     // stored candidates give a much tighter threshold; emit again for them
     // alone against the whole list storage (direct appends) and finish them.
