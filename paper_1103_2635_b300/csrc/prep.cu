@@ -5,8 +5,8 @@
 //   row length allows it.
 // to_lowp: FP32 rows -> bf16 / fp16 rows padded with zeros to `dpad` columns
 //   (a multiple of 64, the tensor-core K block), plus per row the FP32 norm
-//   |x~|^2 of the rounded row and the rounding residual |x - x~| computed in
-//   FP64 and rounded up to float.  The residual bounds how far any distance
+//   |x~|^2 of the rounded row and an upper bound of the rounding residual
+//   |x - x~| (FP32 with every operation rounded up).  The residual bounds how far any distance
 //   can move under rounding (triangle inequality of the metric:
 //   |rho(q~, x~) - rho(q, x)| <= |q - q~| + |x - x~|), which the exact search
 //   needs to stay exact with low-precision storage.
@@ -68,24 +68,27 @@ __global__ void to_lowp_kernel(const float* __restrict__ src, int64_t rows, int 
   if (w >= rows) return;
   const float* a = src + w * d;
   T* b = dst + w * dpad;
-  float nrm = 0.f;
-  double e2 = 0.0;
+  // |x - x~| as an upper bound in FP32: v - r is exact (r is v rounded to
+  // fewer significant bits, so within a factor 2 of v, or 0), and every
+  // square, sum and the root round upward (a nonzero square never rounds to
+  // zero), so e >= the exact residual
+  float nrm = 0.f, e2 = 0.f;
   for (int i = lane; i < dpad; i += 32) {
     float v = i < d ? a[i] : 0.f;
     T lv = to_lp<T>(v);
     b[i] = lv;
     float r = from_lp(lv);
     nrm = fmaf(r, r, nrm);
-    double diff = (double)v - (double)r;
-    e2 += diff * diff;
+    const float diff = v - r;
+    e2 = __fadd_ru(e2, __fmul_ru(diff, diff));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-    e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+    e2 = __fadd_ru(e2, __shfl_xor_sync(0xffffffffu, e2, o));
   }
   if (lane == 0) {
-    float e = __double2float_ru(sqrt(e2));
+    float e = __fsqrt_ru(e2);
     norm[w] = nrm;
     if (err) err[w] = e;
     // non-negative floats order like their bit patterns
