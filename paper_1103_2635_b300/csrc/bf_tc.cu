@@ -96,6 +96,8 @@ __device__ __forceinline__ Seg seg_at(const TileWork& w, int si) {
 template <int C, int KB, int BN, int S, int NR, bool FP8>
 struct TcSmem {
   static constexpr int NBUF = (512 / BN) < 4 ? (512 / BN) : 4;  // TMEM accumulator buffers
+  static_assert(NBUF * BN >= 32 && (NBUF * BN & (NBUF * BN - 1)) == 0,
+                "tcgen05.alloc takes a power of two columns (>= 32)");
   static constexpr int Q_BYTES = KB * BM * 128;  // query tile, KB K-blocks of 128 bytes
   static constexpr int X_STAGE = KB * BN * 128;  // one database tile
   static constexpr int NORM_STAGE = BN * 4;

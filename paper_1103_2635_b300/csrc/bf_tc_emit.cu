@@ -77,6 +77,8 @@ struct EmitParams {
 template <int KB, int BN, int S, int QSTAGES>
 struct EmitSmem {
   static constexpr int NBUF = (512 / BN) < 4 ? (512 / BN) : 4;  // TMEM accumulator buffers
+  static_assert(NBUF * BN >= 32 && (NBUF * BN & (NBUF * BN - 1)) == 0,
+                "tcgen05.alloc takes a power of two columns (>= 32)");
   static constexpr int Q_BYTES = KB * BM * 128;
   static constexpr int X_STAGE = KB * BN * 128;
   static constexpr int NB_STAGE = BN * NBLOCK_COLS * 2;          // a tile's norm block
