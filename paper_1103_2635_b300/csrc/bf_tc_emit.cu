@@ -507,7 +507,7 @@ int launch_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
 int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
                       const int* num_items_dev, int max_items, const int* pair_q,
                       int pair_stride, const EmitOut& out, int grid, cudaStream_t st,
-                      uint32_t* dev_err) {
+                      uint32_t* dev_err, bool many_hits) {
   if (!tc_available()) {
     set_error("tensor-core BF kernel needs an sm_103 device");
     return RBC_ERR_UNSUPPORTED;
@@ -523,7 +523,10 @@ int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* it
   }
   switch (Qm.dpad / 64) {
     case 1: return launch_emit<1, 256, 3, 4>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_stride, out, grid, st, dev_err);
-    case 2: return launch_emit<2, 128, 3, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_stride, out, grid, st, dev_err);
+    case 2:
+      if (many_hits)
+        return launch_emit<2, 128, 3, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_stride, out, grid, st, dev_err);
+      return launch_emit<2, 256, 2, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_stride, out, grid, st, dev_err);
     case 3: return launch_emit<3, 64, 3, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_stride, out, grid, st, dev_err);
     case 4: return launch_emit<4, 64, 2, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_stride, out, grid, st, dev_err);
     default: break;

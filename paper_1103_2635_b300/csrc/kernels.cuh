@@ -100,11 +100,15 @@ constexpr int ARENA_SUBSEG = 16;  // arena parts per CTA (at least its epilogue 
 int launch_scatter_hits(const int4* arena, int arena_seg, const int* arena_cnt, int nseg,
                         float* cand_score, int* cand_row, int* cand_cnt, int cap,
                         cudaStream_t st);
-// the query of an item's row i is pair_q[(pair_begin + i) * pair_stride]
+// the query of an item's row i is pair_q[(pair_begin + i) * pair_stride].
+// many_hits: the pass emits many candidates per query (direct appends after
+// an arena overflow); for 128-column K (d in (64, 128]) it then takes
+// 128-row database tiles, whose epilogue keeps up with the hits, instead of
+// 256-row ones, which issue half the MMAs
 int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
                       const int* num_items_dev, int max_items, const int* pair_q,
                       int pair_stride, const EmitOut& out, int grid, cudaStream_t st,
-                      uint32_t* dev_err);
+                      uint32_t* dev_err, bool many_hits = false);
 
 // ---- merge + re-rank + certification ----
 struct SelectArgs {
