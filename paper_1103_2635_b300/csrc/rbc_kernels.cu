@@ -193,13 +193,13 @@ __global__ void list_radii_kernel(const float* __restrict__ dist_by_id, const in
 // One warp per query row of D (distances >= 0, so their bit patterns order
 // like their values): gamma_1 and the nearest column by a warp arg-min
 // (ties to the smaller column); gamma_k, the k-th smallest value.  Rows of up
-// to 1024 values are held in registers, 32 per lane, and gamma_k is found in
+// to 2048 values are held in registers, 32 or 64 per lane, and gamma_k is found in
 // two short selections: T = the k-th smallest of the 32 lane minima bounds
 // gamma_k from above (k lanes hold a value <= T), the values <= T (normally
 // a few more than k) are compacted one per lane, and k rounds of a warp
 // minimum over them give gamma_k exactly.  Rows with more than 32 values <= T,
 // and longer rows, use a bitwise search for the k-th smallest bit pattern.
-template <bool CACHED>
+template <int VPL>  // values per lane held in registers (0: none)
 __global__ void row_stats_kernel(const float* __restrict__ D, int64_t m, int n_r, int k,
                                  float* __restrict__ g1, float* __restrict__ gk,
                                  int64_t* __restrict__ nearest) {
@@ -207,12 +207,13 @@ __global__ void row_stats_kernel(const float* __restrict__ D, int64_t m, int n_r
   const int lane = threadIdx.x & 31;
   if (w >= m) return;
   const float* row = D + w * n_r;
-  unsigned vals[CACHED ? 32 : 1];
+  constexpr bool CACHED = VPL > 0;
+  unsigned vals[CACHED ? VPL : 1];
   float bv = INFINITY;
   int bi = INT32_MAX;
   if (CACHED) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
+    for (int j = 0; j < VPL; ++j) {
       const int c = lane + 32 * j;
       const float v = c < n_r ? row[c] : INFINITY;
       vals[j] = __float_as_uint(v);
@@ -259,11 +260,11 @@ __global__ void row_stats_kernel(const float* __restrict__ D, int64_t m, int n_r
     };
     unsigned lmin = vals[0];
 #pragma unroll
-    for (int j = 1; j < 32; ++j) lmin = min(lmin, vals[j]);
+    for (int j = 1; j < VPL; ++j) lmin = min(lmin, vals[j]);
     const unsigned T = kth_of_lanes(lmin);
     int c = 0;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) c += vals[j] <= T;
+    for (int j = 0; j < VPL; ++j) c += vals[j] <= T;
     int pre = c;  // inclusive prefix over lanes
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -276,7 +277,7 @@ __global__ void row_stats_kernel(const float* __restrict__ D, int64_t m, int n_r
       unsigned* cw = cand[(threadIdx.x >> 5) & 7];
       int pos = pre - c;
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
+      for (int j = 0; j < VPL; ++j)
         if (vals[j] <= T) cw[pos++] = vals[j];
       __syncwarp();
       const unsigned x = lane < total ? cw[lane] : 0xffffffffu;
@@ -292,7 +293,7 @@ __global__ void row_stats_kernel(const float* __restrict__ D, int64_t m, int n_r
       int cnt = 0;
       if (CACHED) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) cnt += vals[j] < t;
+        for (int j = 0; j < VPL; ++j) cnt += vals[j] < t;
       } else {
         for (int c = lane; c < n_r; c += 32) cnt += __float_as_uint(row[c]) < t;
       }
@@ -618,9 +619,11 @@ int launch_row_stats(const float* D, int64_t m, int n_r, int k, float* g1, float
   if (m <= 0) return RBC_OK;
   const unsigned blocks = (unsigned)((m * 32 + 255) / 256);
   if (n_r <= 1024)
-    row_stats_kernel<true><<<blocks, 256, 0, st>>>(D, m, n_r, k, g1, gk, nearest);
+    row_stats_kernel<32><<<blocks, 256, 0, st>>>(D, m, n_r, k, g1, gk, nearest);
+  else if (n_r <= 2048)
+    row_stats_kernel<64><<<blocks, 256, 0, st>>>(D, m, n_r, k, g1, gk, nearest);
   else
-    row_stats_kernel<false><<<blocks, 256, 0, st>>>(D, m, n_r, k, g1, gk, nearest);
+    row_stats_kernel<0><<<blocks, 256, 0, st>>>(D, m, n_r, k, g1, gk, nearest);
   RBC_LAUNCH_CHECK("row_stats_kernel");
   return RBC_OK;
 }
