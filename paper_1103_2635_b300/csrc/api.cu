@@ -207,7 +207,9 @@ int pad64(int d) { return (d + 63) / 64 * 64; }
 // splits the representatives into column chunks (at least 256 each) so that
 // every SM gets about two items; a large batch keeps one item per tile.
 void set_stage1_splits(TileWork& w, int64_t tiles, int n_r, int sms) {
-  int64_t splits = tiles > 0 ? (2LL * sms + tiles - 1) / tiles : 1;
+  // at least 6 items per SM (3 per resident CTA): the last wave's tail
+  // stays a small part of the pass
+  int64_t splits = tiles > 0 ? (6LL * sms + tiles - 1) / tiles : 1;
   splits = std::max<int64_t>(1, std::min<int64_t>(splits, (n_r + 255) / 256));
   int64_t chunk = (n_r + splits - 1) / splits;
   splits = (n_r + chunk - 1) / chunk;
