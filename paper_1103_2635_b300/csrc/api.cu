@@ -203,12 +203,11 @@ float simt_eps(int d) { return (float)(d + 8) * U32; }
 float rerank_eps_host(int d) { return (0.25f * d + 8.0f) * U32; }
 int pad64(int d) { return (d + 63) / 64 * 64; }
 
-// Stage one BF(Q, R) as dense work items: a batch of few 128-query tiles
-// splits the representatives into column chunks (at least 256 each) so that
-// every SM gets about two items; a large batch keeps one item per tile.
+// Stage one BF(Q, R) as dense work items: the representatives are split into
+// column chunks (at least 256 each) so that every SM gets at least six items
+// (three per resident CTA), which keeps the last wave's tail a small part of
+// the pass; a batch with that many 128-query tiles keeps one item per tile.
 void set_stage1_splits(TileWork& w, int64_t tiles, int n_r, int sms) {
-  // at least 6 items per SM (3 per resident CTA): the last wave's tail
-  // stays a small part of the pass
   int64_t splits = tiles > 0 ? (6LL * sms + tiles - 1) / tiles : 1;
   splits = std::max<int64_t>(1, std::min<int64_t>(splits, (n_r + 255) / 256));
   int64_t chunk = (n_r + splits - 1) / splits;
