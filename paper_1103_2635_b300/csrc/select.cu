@@ -304,9 +304,10 @@ __global__ void __launch_bounds__(WARPS * 32) select_kernel(SelectArgs a) {
 // every point whose low-precision score passed the query's threshold, which
 // includes every point within g(q) >= its k-th neighbour distance -- so the
 // true k nearest are among the candidates and no certificate is needed.
-//  1. s_k = the k-th smallest candidate score (up to 64 candidates and
-//     k <= 16: k rounds of warp minimum over keys held in registers; else a
-//     bitwise search over the order-preserving integer keys of the scores);
+//  1. s_k = the k-th smallest candidate score (k <= 16: up to 64 candidates
+//     by k rounds of a warp minimum over keys held in registers, more in one
+//     pass keeping each lane's 16 smallest keys; k > 16: a bitwise search
+//     over the order-preserving integer keys of the scores);
 //     k distinct points score <= s_k, so U = dist_upper(s_k) bounds the k-th
 //     neighbour distance, and only candidates scoring <= score_bound(U) can
 //     be among the k nearest;
@@ -659,10 +660,12 @@ __global__ void __launch_bounds__(GFB_THREADS) group_fallback_kernel(GroupFallba
 
 // Queries whose survivors (candidates scoring <= score_bound(U)) outnumber
 // the shared-memory re-rank: one warp per query streams every survivor
-// through the FP32 re-rank.  Each lane keeps its CW best (CW >= c_out, so
-// the lanes together hold the query's c_out best for sure), then c_out
-// rounds of a warp minimum rank them, then FP64 ties and the output as in
-// select_cands.
+// through the FP32 re-rank -- the k-th score in one pass over the buffer,
+// then batches of up to 256 survivors compacted into shared memory, their
+// ids fetched, their distances computed by groups of eight lanes (two rows
+// per group at a time).  Each lane keeps its CW best (CW >= c_out, so the
+// lanes together hold the query's c_out best for sure), then c_out rounds of
+// a warp minimum rank them, then FP64 ties and the output as in select_cands.
 template <int CW>
 __global__ void __launch_bounds__(WARPS * 32) select_stream_kernel(CandSelectArgs a) {
   constexpr int BATCH = 256;  // survivors re-ranked together
