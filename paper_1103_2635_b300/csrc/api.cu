@@ -686,6 +686,20 @@ int make_lp_copies(rbc_index* ix, cudaStream_t st) {
     // its accumulators with one extra MMA instead of a per-column FMA
     RBC_TRY(ix->alloc(reinterpret_cast<uint16_t**>(&ix->xnblock), (n + NORM_PAD) * NBLOCK_COLS));
     RBC_TRY(launch_norm_block(ix->xnorm, n, n + NORM_PAD, ix->xnblock, st));
+    // with two spare padding columns the pair goes into the rows themselves
+    // (an fp16 pair only while -|x~|^2 / 2 stays well inside its range)
+    if (d % 2 == 0 && ix->dpad - d >= 2) {
+      unsigned nmax_bits = 0;
+      RBC_CUDA(cudaMemcpyAsync(&nmax_bits, ix->lp_max + 1, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                               st));
+      RBC_CUDA(cudaStreamSynchronize(st));
+      float nmax = 0.f;
+      std::memcpy(&nmax, &nmax_bits, sizeof(float));
+      if (ix->storage == RBC_BF16 || 0.5 * (double)nmax * nmax < 16384.0) {
+        RBC_TRY(launch_fold_norm(xl, ix->xnorm, n, ix->dpad, d, ix->storage, st));
+        ix->norm_fold_col = d;
+      }
+    }
   }
   RBC_TRY(launch_to_lowp(ix->R32, n_r, d, ix->dpad, ix->storage, rl, ix->rnorm, nullptr,
                          ix->lp_max + 2, ix->lp_max + 3, st, ix->rscale));
@@ -1459,7 +1473,7 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
     tmark(1, st);
     RBC_TRY(launch_bf_tc_emit(Qm, Xm, items, choff + n_r, max_items,
                               reinterpret_cast<const int*>(pairs), 2, eo_arena, sms, st, dev_err,
-                              direct));
+                              direct, ix->norm_fold_col));
     if (!direct)
       RBC_TRY(launch_scatter_hits(arena, arena_lane, arena_cnt, (int)nslices, cs, cr, cc,
                                   CAND_CAP, st));
@@ -1509,7 +1523,7 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
                                         ix->lp_max, d, thr, st));
     RBC_TRY(launch_dense_emit_items(lc, n, xspan, max2, items2, n_items2, st));
     RBC_TRY(launch_bf_tc_emit(Qm, Xm, items2, n_items2, max2, fb_rows, 1, eo, sms, st, dev_err,
-                              true));
+                              true, ix->norm_fold_col));
     CandSelectArgs a2 = a;
     a2.rows = fb_rows;
     a2.nrows_dev = lc;

@@ -36,6 +36,8 @@
 //               load and arithmetic latencies
 // Every mbarrier wait is bounded (2 s); on expiry the kernel raises
 // DEV_ERR_TIMEOUT, stops issuing work, drains its copies and frees TMEM.
+#include <cstring>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "tc_common.cuh"
@@ -72,6 +74,8 @@ struct EmitParams {
   const float* xnorm;  // [rows + pad]
   EmitOut out;
   uint32_t* dev_err;
+  int fold_col;         // FOLD: the row element holding the norm pair (even)
+  uint32_t fold_ones;   // FOLD: the pair (1, 1) in the storage type
 };
 
 template <int KB, int BN, int S, int QSTAGES>
@@ -127,7 +131,11 @@ __device__ __forceinline__ void st_shared_zero16(uint32_t dst) {
 // QSTAGES query stages (even: the two gather warps alternate over them): the
 // gather of an item's rows takes a few microseconds, longer than a one-tile
 // item, so several are kept in flight.
-template <int KB, int BN, int S, int QSTAGES>
+// FOLD: the database rows hold -|x~|^2 / 2 as a (high, low) pair in two of
+// their zero padding columns (fold_col, fold_col + 1), and the gather sets
+// those columns of every query row to 1: the data MMAs then add the norm
+// themselves, and neither the norm block nor its MMA is needed.
+template <int KB, int BN, int S, int QSTAGES, bool FOLD = false>
 __global__ void __launch_bounds__(EpiShape<BN>::THREADS, 1)
 bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap nbmap,
                   EmitParams p, uint32_t idesc, uint32_t idesc_norm) {
@@ -211,11 +219,11 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
           break;
         }
         if (lane == 0) {
-          mbar_arrive_expect_tx(&full[s], L::X_STAGE + L::NB_STAGE);
+          mbar_arrive_expect_tx(&full[s], L::X_STAGE + (FOLD ? 0 : L::NB_STAGE));
 #pragma unroll
           for (int kb = 0; kb < KB; ++kb)
             tma_load_2d(sX + s * L::X_STAGE + kb * BN * 128, &xmap, &full[s], kb * 64, x);
-          tma_load_2d(sNB + s * L::NB_STAGE, &nbmap, &full[s], 0, x);
+          if (!FOLD) tma_load_2d(sNB + s * L::NB_STAGE, &nbmap, &full[s], 0, x);
         }
         __syncwarp();
       }
@@ -298,6 +306,19 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
       const bool have2 = seek(item2, qi2, e2);
       if (have2) meta(e2);
       asm volatile("cp.async.wait_group 0;" ::: "memory");
+      if (FOLD) {
+        // every lane's copies have landed (wait + warp barrier); then the
+        // ones of the folded norm pair go into this lane's rows
+        __syncwarp();
+        const int kbf = p.fold_col >> 6, within = (p.fold_col & 63) * 2;
+#pragma unroll
+        for (int t = 0; t < BM / 32; ++t) {
+          const int row = lane + 32 * t;
+          const uint32_t a = qbase + kbf * BM * 128 + row * 128 +
+                             ((((within >> 4) ^ (row & 7)) << 4) | (within & 15));
+          asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(p.fold_ones) : "memory");
+        }
+      }
       // this lane's rows are in shared memory: make them visible to the
       // tensor core (async proxy), then release the stage
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -353,8 +374,9 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
               mma_f16(d_tmem, ad, bd, idesc, (kb | k16) != 0);
             }
           // + (-|x~|^2 / 2) in every row: ones x norm block (bf16, K = 16)
-          mma_f16(d_tmem, smem_desc_sw32(smem_u32(sOnes)),
-                  smem_desc_sw32(smem_u32(sNB + s * L::NB_STAGE)), idesc_norm, 1u);
+          if (!FOLD)
+            mma_f16(d_tmem, smem_desc_sw32(smem_u32(sOnes)),
+                    smem_desc_sw32(smem_u32(sNB + s * L::NB_STAGE)), idesc_norm, 1u);
           mma_commit(&empty[s]);
           mma_commit(&tfull[buf]);
         }
@@ -474,18 +496,22 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
   }
 }
 
-template <int KB, int BN, int S, int QS>
+template <int KB, int BN, int S, int QS, bool FOLD>
 int launch_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
                 const int* num_items_dev, int max_items, const int* pair_q, int pair_stride,
-                const EmitOut& out, int grid, cudaStream_t st, uint32_t* dev_err) {
+                const EmitOut& out, int grid, cudaStream_t st, uint32_t* dev_err, int fold_col) {
   using L = EmitSmem<KB, BN, S, QS>;
   CUtensorMap xmap, nbmap;
   RBC_TRY_TC(encode_map(&xmap, Xm.data, Xm.rows, Xm.dpad, Xm.storage, BN));
-  RBC_TRY_TC(encode_nblock_map(&nbmap, Xm.nblock, Xm.rows, BN));
-  auto kern = bf_tc_emit_kernel<KB, BN, S, QS>;
+  if (FOLD)
+    memset(&nbmap, 0, sizeof(nbmap));  // not read: the norm is in the rows
+  else
+    RBC_TRY_TC(encode_nblock_map(&nbmap, Xm.nblock, Xm.rows, BN));
+  auto kern = bf_tc_emit_kernel<KB, BN, S, QS, FOLD>;
   RBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC));
   EmitParams p{items,  num_items_dev, max_items, pair_q, pair_stride,
-               static_cast<const uint8_t*>(Qm.data), (int64_t)Qm.dpad * 2, Xm.norm, out, dev_err};
+               static_cast<const uint8_t*>(Qm.data), (int64_t)Qm.dpad * 2, Xm.norm, out, dev_err,
+               fold_col, Qm.storage == RBC_BF16 ? 0x3F803F80u : 0x3C003C00u};
   const uint32_t idesc = idesc_f16(Qm.storage == RBC_BF16 ? 1 : 0, BM, BN);
   const uint32_t idesc_norm = idesc_f16(1, BM, BN);  // the norm block is bf16 for any storage
   kern<<<grid, EpiShape<BN>::THREADS, L::ALLOC, st>>>(xmap, nbmap, p, idesc, idesc_norm);
@@ -507,7 +533,7 @@ int launch_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
 int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
                       const int* num_items_dev, int max_items, const int* pair_q,
                       int pair_stride, const EmitOut& out, int grid, cudaStream_t st,
-                      uint32_t* dev_err, bool many_hits) {
+                      uint32_t* dev_err, bool many_hits, int fold_col) {
   if (!tc_available()) {
     set_error("tensor-core BF kernel needs an sm_103 device");
     return RBC_ERR_UNSUPPORTED;
@@ -517,20 +543,33 @@ int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* it
     return RBC_ERR_ARG;
   }
   if (max_items <= 0) return RBC_OK;
-  if (!Xm.nblock) {
+  if (!Xm.nblock && fold_col < 0) {
     set_error("tensor-core emission: the database has no norm block");
     return RBC_ERR_ARG;
   }
+  if (fold_col >= 0 && (fold_col & 1 || fold_col + 2 > Qm.dpad)) {
+    set_error("tensor-core emission: folded norm column %d invalid", fold_col);
+    return RBC_ERR_ARG;
+  }
+  // d <= 64: 256-row tiles; d in (64, 128]: 256-row tiles, or 128-row tiles
+  // when the pass emits many candidates (many_hits); longer rows: 64
+#define RBC_EMIT(KB, BN, S, QS)                                                             \
+  return fold_col >= 0 ? launch_emit<KB, BN, S, QS, true>(Qm, Xm, items, num_items_dev,        \
+                                                          max_items, pair_q, pair_stride, out, \
+                                                          grid, st, dev_err, fold_col)         \
+                       : launch_emit<KB, BN, S, QS, false>(Qm, Xm, items, num_items_dev,       \
+                                                           max_items, pair_q, pair_stride, out, \
+                                                           grid, st, dev_err, -1)
   switch (Qm.dpad / 64) {
-    case 1: return launch_emit<1, 256, 3, 4>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_stride, out, grid, st, dev_err);
+    case 1: RBC_EMIT(1, 256, 3, 4);
     case 2:
-      if (many_hits)
-        return launch_emit<2, 128, 3, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_stride, out, grid, st, dev_err);
-      return launch_emit<2, 256, 2, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_stride, out, grid, st, dev_err);
-    case 3: return launch_emit<3, 64, 3, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_stride, out, grid, st, dev_err);
-    case 4: return launch_emit<4, 64, 2, 2>(Qm, Xm, items, num_items_dev, max_items, pair_q, pair_stride, out, grid, st, dev_err);
+      if (many_hits) RBC_EMIT(2, 128, 3, 2);
+      RBC_EMIT(2, 256, 2, 2);
+    case 3: RBC_EMIT(3, 64, 3, 2);
+    case 4: RBC_EMIT(4, 64, 2, 2);
     default: break;
   }
+#undef RBC_EMIT
   set_error("tensor-core BF: padded dimension %d unsupported", Qm.dpad);
   return RBC_ERR_UNSUPPORTED;
 }

@@ -31,6 +31,7 @@ struct rbc_index {
   unsigned* lp_max = nullptr; // [4] float bits: max|x-x~|, max|x~|, max|r-r~|, max|r~|
   void* Rlp = nullptr;        // [n_r, dpad]
   float* rnorm = nullptr;     // [n_r]
+  int norm_fold_col = -1;     // >= 0: Xlp carries -|x~|^2 / 2 in columns col, col + 1
   float* xscale = nullptr;    // FP8: [list_entries + NORM_PAD] per-row power-of-two scales
   float* rscale = nullptr;    // FP8: [n_r]
   // windowed search: searches left that emit their candidates directly into

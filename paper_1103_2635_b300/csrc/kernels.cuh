@@ -101,6 +101,9 @@ int launch_scatter_hits(const int4* arena, int arena_seg, const int* arena_cnt, 
                         float* cand_score, int* cand_row, int* cand_cnt, int cap,
                         cudaStream_t st);
 // the query of an item's row i is pair_q[(pair_begin + i) * pair_stride].
+// fold_col >= 0: the database rows carry -|x~|^2 / 2 as a (high, low) pair
+// in padding columns fold_col, fold_col + 1 (launch_fold_norm), so no norm
+// block or norm MMA is used.
 // many_hits: the pass emits many candidates per query (direct appends after
 // an arena overflow); for 128-column K (d in (64, 128]) it then takes
 // 128-row database tiles, whose epilogue keeps up with the hits, instead of
@@ -108,7 +111,7 @@ int launch_scatter_hits(const int4* arena, int arena_seg, const int* arena_cnt, 
 int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
                       const int* num_items_dev, int max_items, const int* pair_q,
                       int pair_stride, const EmitOut& out, int grid, cudaStream_t st,
-                      uint32_t* dev_err, bool many_hits = false);
+                      uint32_t* dev_err, bool many_hits = false, int fold_col = -1);
 
 // ---- merge + re-rank + certification ----
 struct SelectArgs {
@@ -313,6 +316,12 @@ int launch_to_lowp(const float* src, int64_t rows, int d, int dpad, int storage,
 int launch_gather_lp_rows(const void* src, const float* snorm, const float* serr, const int* idx,
                           int64_t rows, int row_bytes, void* dst, float* dnorm, float* derr,
                           cudaStream_t st, const float* sscale = nullptr, float* dscale = nullptr);
+// -|x~[i]|^2 / 2 as a (high, low) pair of the storage type (bf16 / fp16)
+// written into columns col, col + 1 of each row (zero padding until then):
+// a query row with 1 in those columns then picks the norm term up in its
+// ordinary MMA, and one with 0 there (every other use) is unaffected
+int launch_fold_norm(void* lp, const float* norm, int64_t rows, int dpad, int col, int storage,
+                     cudaStream_t st);
 // Norm block of a low-precision matrix: row i = (h, l, 0, ..., 0) in bf16
 // with h = bf16(-norm[i] / 2), l = bf16(-norm[i] / 2 - h), so that an MMA of
 // an all-ones row against it adds -|x~|^2 / 2 to every accumulator of column

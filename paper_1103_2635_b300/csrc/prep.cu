@@ -196,6 +196,19 @@ __global__ void norm_block_kernel(const float* __restrict__ norm, int64_t rows, 
   }
 }
 
+template <typename T>
+__global__ void fold_norm_kernel(T* __restrict__ lp, const float* __restrict__ norm, int64_t rows,
+                                 int dpad, int col) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = -0.5f * norm[i];  // exact: a power-of-two scale
+    const T h = to_lp<T>(v);
+    const T l = to_lp<T>(v - from_lp(h));  // v - h exact
+    lp[i * dpad + col] = h;
+    lp[i * dpad + col + 1] = l;
+  }
+}
+
 __global__ void map_rows_kernel(const int* __restrict__ rows, const int* __restrict__ n_dev, int n,
                                 const int* __restrict__ qorig, int* __restrict__ out) {
   int lim = n_dev ? *n_dev : n;
@@ -268,6 +281,24 @@ int launch_gather_lp_rows(const void* src, const float* snorm, const float* serr
       static_cast<const uint4*>(src), snorm, serr, idx, rows, row_bytes / 16,
       static_cast<uint4*>(dst), dnorm, derr, sscale, dscale);
   RBC_LAUNCH_CHECK("gather_lp_rows_kernel");
+  return RBC_OK;
+}
+
+int launch_fold_norm(void* lp, const float* norm, int64_t rows, int dpad, int col, int storage,
+                     cudaStream_t st) {
+  if (rows <= 0) return RBC_OK;
+  if (col < 0 || col + 2 > dpad || (storage != RBC_BF16 && storage != RBC_F16)) {
+    set_error("fold_norm: column %d of %d, storage %d", col, dpad, storage);
+    return RBC_ERR_ARG;
+  }
+  const unsigned blocks = (unsigned)std::min<int64_t>((rows + 255) / 256, 148 * 16);
+  if (storage == RBC_BF16)
+    fold_norm_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(static_cast<__nv_bfloat16*>(lp), norm,
+                                                             rows, dpad, col);
+  else
+    fold_norm_kernel<__half><<<blocks, 256, 0, st>>>(static_cast<__half*>(lp), norm, rows, dpad,
+                                                     col);
+  RBC_LAUNCH_CHECK("fold_norm_kernel");
   return RBC_OK;
 }
 
