@@ -466,14 +466,20 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
                 }
               }
             } else {
+              // direct appends: one atomic per (lane, chunk) reserves the
+              // row's slots, then the hits fill them in column order
+              int nh = 0;
+#pragma unroll
+              for (int j = 0; j < 32; ++j) nh += (((valid >> j) & 1u) && u[j] >= myT) ? 1 : 0;
+              int pos = atomicAdd(cc, nh);
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
                 if (((valid >> j) & 1u) && u[j] >= myT) {
-                  const int pos = atomicAdd(cc, 1);
                   if (pos < cap) {
                     cs[pos] = -2.0f * u[j];
                     cr[pos] = cb + j;
                   }
+                  ++pos;
                 }
               }
             }
