@@ -1473,7 +1473,7 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
     tmark(1, st);
     RBC_TRY(launch_bf_tc_emit(Qm, Xm, items, choff + n_r, max_items,
                               reinterpret_cast<const int*>(pairs), 2, eo_arena, sms, st, dev_err,
-                              direct, ix->norm_fold_col));
+                              ix->norm_fold_col));
     if (!direct)
       RBC_TRY(launch_scatter_hits(arena, arena_lane, arena_cnt, (int)nslices, cs, cr, cc,
                                   CAND_CAP, st));
@@ -1523,7 +1523,7 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
                                         ix->lp_max, d, thr, st));
     RBC_TRY(launch_dense_emit_items(lc, n, xspan, max2, items2, n_items2, st));
     RBC_TRY(launch_bf_tc_emit(Qm, Xm, items2, n_items2, max2, fb_rows, 1, eo, sms, st, dev_err,
-                              true, ix->norm_fold_col));
+                              ix->norm_fold_col));
     CandSelectArgs a2 = a;
     a2.rows = fb_rows;
     a2.nrows_dev = lc;

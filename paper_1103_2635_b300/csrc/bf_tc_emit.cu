@@ -539,7 +539,7 @@ int launch_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
 int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
                       const int* num_items_dev, int max_items, const int* pair_q,
                       int pair_stride, const EmitOut& out, int grid, cudaStream_t st,
-                      uint32_t* dev_err, bool many_hits, int fold_col) {
+                      uint32_t* dev_err, int fold_col) {
   if (!tc_available()) {
     set_error("tensor-core BF kernel needs an sm_103 device");
     return RBC_ERR_UNSUPPORTED;
@@ -557,8 +557,8 @@ int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* it
     set_error("tensor-core emission: folded norm column %d invalid", fold_col);
     return RBC_ERR_ARG;
   }
-  // d <= 64: 256-row tiles; d in (64, 128]: 256-row tiles, or 128-row tiles
-  // when the pass emits many candidates (many_hits); longer rows: 64
+  // d <= 128: 256-row database tiles (the fewest MMA instructions per
+  // column); longer rows: 64-row tiles
 #define RBC_EMIT(KB, BN, S, QS)                                                             \
   return fold_col >= 0 ? launch_emit<KB, BN, S, QS, true>(Qm, Xm, items, num_items_dev,        \
                                                           max_items, pair_q, pair_stride, out, \
@@ -568,9 +568,7 @@ int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* it
                                                            grid, st, dev_err, -1)
   switch (Qm.dpad / 64) {
     case 1: RBC_EMIT(1, 256, 3, 4);
-    case 2:
-      if (many_hits) RBC_EMIT(2, 128, 3, 2);
-      RBC_EMIT(2, 256, 2, 2);
+    case 2: RBC_EMIT(2, 256, 2, 2);
     case 3: RBC_EMIT(3, 64, 3, 2);
     case 4: RBC_EMIT(4, 64, 2, 2);
     default: break;

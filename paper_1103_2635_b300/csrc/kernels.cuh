@@ -104,14 +104,10 @@ int launch_scatter_hits(const int4* arena, int arena_seg, const int* arena_cnt, 
 // fold_col >= 0: the database rows carry -|x~|^2 / 2 as a (high, low) pair
 // in padding columns fold_col, fold_col + 1 (launch_fold_norm), so no norm
 // block or norm MMA is used.
-// many_hits: the pass emits many candidates per query (direct appends after
-// an arena overflow); for 128-column K (d in (64, 128]) it then takes
-// 128-row database tiles, whose epilogue keeps up with the hits, instead of
-// 256-row ones, which issue half the MMAs
 int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
                       const int* num_items_dev, int max_items, const int* pair_q,
                       int pair_stride, const EmitOut& out, int grid, cudaStream_t st,
-                      uint32_t* dev_err, bool many_hits = false, int fold_col = -1);
+                      uint32_t* dev_err, int fold_col = -1);
 
 // ---- merge + re-rank + certification ----
 struct SelectArgs {
