@@ -135,7 +135,9 @@ __device__ __forceinline__ void st_shared_zero16(uint32_t dst) {
 // their zero padding columns (fold_col, fold_col + 1), and the gather sets
 // those columns of every query row to 1: the data MMAs then add the norm
 // themselves, and neither the norm block nor its MMA is needed.
-template <int KB, int BN, int S, int QSTAGES, bool FOLD = false>
+// DIRECT: hits go straight to the per-query buffers (no hit arena); each
+// instance holds only its own emission path.
+template <int KB, int BN, int S, int QSTAGES, bool FOLD = false, bool DIRECT = false>
 __global__ void __launch_bounds__(EpiShape<BN>::THREADS, 1)
 bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap nbmap,
                   EmitParams p, uint32_t idesc, uint32_t idesc_norm) {
@@ -456,7 +458,7 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
             const uint32_t below_hi = chi >= 32 ? 0xffffffffu : (chi <= 0 ? 0u : (1u << chi) - 1u);
             const uint32_t below_lo = clo >= 32 ? 0xffffffffu : (clo <= 0 ? 0u : (1u << clo) - 1u);
             const uint32_t valid = below_hi & ~below_lo;
-            if (hits) {
+            if (!DIRECT) {
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
                 if (((valid >> j) & 1u) && u[j] >= myT) {
@@ -487,7 +489,7 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
         }
       }
     }
-    if (hits) {
+    if (!DIRECT) {
       p.out.arena_cnt[(blockIdx.x * ARENA_SUBSEG + ew) * 32 + lane] = nhits < lsub ? nhits : lsub;
       if (nhits > lsub) atomicOr(p.out.arena_ovf, 1);
     }
@@ -502,7 +504,7 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
   }
 }
 
-template <int KB, int BN, int S, int QS, bool FOLD>
+template <int KB, int BN, int S, int QS, bool FOLD, bool DIRECT>
 int launch_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
                 const int* num_items_dev, int max_items, const int* pair_q, int pair_stride,
                 const EmitOut& out, int grid, cudaStream_t st, uint32_t* dev_err, int fold_col) {
@@ -513,7 +515,7 @@ int launch_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
     memset(&nbmap, 0, sizeof(nbmap));  // not read: the norm is in the rows
   else
     RBC_TRY_TC(encode_nblock_map(&nbmap, Xm.nblock, Xm.rows, BN));
-  auto kern = bf_tc_emit_kernel<KB, BN, S, QS, FOLD>;
+  auto kern = bf_tc_emit_kernel<KB, BN, S, QS, FOLD, DIRECT>;
   RBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC));
   EmitParams p{items,  num_items_dev, max_items, pair_q, pair_stride,
                static_cast<const uint8_t*>(Qm.data), (int64_t)Qm.dpad * 2, Xm.norm, out, dev_err,
@@ -559,13 +561,15 @@ int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* it
   }
   // d <= 128: 256-row database tiles (the fewest MMA instructions per
   // column); longer rows: 64-row tiles
+#define RBC_EMIT_ONE(KB, BN, S, QS, FOLD, DIRECT)                                         \
+  launch_emit<KB, BN, S, QS, FOLD, DIRECT>(Qm, Xm, items, num_items_dev, max_items, pair_q,   \
+                                           pair_stride, out, grid, st, dev_err, fold_col)
 #define RBC_EMIT(KB, BN, S, QS)                                                             \
-  return fold_col >= 0 ? launch_emit<KB, BN, S, QS, true>(Qm, Xm, items, num_items_dev,        \
-                                                          max_items, pair_q, pair_stride, out, \
-                                                          grid, st, dev_err, fold_col)         \
-                       : launch_emit<KB, BN, S, QS, false>(Qm, Xm, items, num_items_dev,       \
-                                                           max_items, pair_q, pair_stride, out, \
-                                                           grid, st, dev_err, -1)
+  return direct ? (fold_col >= 0 ? RBC_EMIT_ONE(KB, BN, S, QS, true, true)                   \
+                                 : RBC_EMIT_ONE(KB, BN, S, QS, false, true))                 \
+                : (fold_col >= 0 ? RBC_EMIT_ONE(KB, BN, S, QS, true, false)                  \
+                                 : RBC_EMIT_ONE(KB, BN, S, QS, false, false))
+  const bool direct = out.arena == nullptr;
   switch (Qm.dpad / 64) {
     case 1: RBC_EMIT(1, 256, 3, 4);
     case 2: RBC_EMIT(2, 256, 2, 2);
@@ -574,6 +578,7 @@ int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* it
     default: break;
   }
 #undef RBC_EMIT
+#undef RBC_EMIT_ONE
   set_error("tensor-core BF: padded dimension %d unsupported", Qm.dpad);
   return RBC_ERR_UNSUPPORTED;
 }
