@@ -64,7 +64,7 @@ FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustain
 # DRAM bytes (read + write) of one main-pass launch of the emission kernel on
 # the default workload, from ncu (profiles/bf_tc_emit_kernel_subspace8-n512k-m50k.md);
 # re-measured whenever the kernel changes (None until then).
-EMIT_TRAFFIC_BYTES = None
+EMIT_TRAFFIC_BYTES = 733.4e6 + 84.5e6
 
 
 def parse():
