@@ -20,10 +20,13 @@
 // holds q~.x~ - |x~|^2 / 2 = -s / 2.  So the epilogue keeps no lists, loads
 // no norms and does no arithmetic per score: per 32-column chunk the TMEM load
 // itself returns the maximum of the raw accumulators (tcgen05.ld.red), and
-// only when that reaches -T(q) / 2
-// appends the qualifying (score, row) pairs to q's candidate buffer in
-// global memory.  The candidates are re-ranked exactly afterwards
-// (select.cu).
+// only when that reaches -T(q) / 2 does a lane walk the chunk and emit the
+// qualifying (score, row) pairs: into its own slice of a hit arena (no
+// atomics; a post-pass moves them to the per-query buffers), or, in the
+// instance for direct appends, into q's candidate buffer with one atomic per
+// chunk.  When rows have two spare padding columns, the norm pair lives in
+// them instead (FOLD) and no norm block or norm MMA is needed.  The
+// candidates are re-ranked exactly afterwards (select.cu).
 //
 //   warp 0      TMA producer: database tiles of BN rows + their norm blocks
 //   warp 1      tensor-memory allocation, MMA issue (M = 128, N = BN, K = 16)
