@@ -24,9 +24,12 @@
 //
 // The pair passes read D [m, n_r] in warp tiles of 32 queries x 32
 // representatives through shared memory, so that a lane owns a query and the
-// warp walks the representatives: bin counters are then updated once per
-// (warp, representative, bucket) and the scattered pairs of one bin land in
-// consecutive slots.
+// warp walks the representatives.  The range pass reduces over the warp
+// before it touches shared memory; the count and scatter passes keep the
+// block's bin counters in shared memory (a lane's kept pair takes its slot
+// there), so global memory sees one update per (block, bin), and the pairs of
+// one bin from one block land in consecutive slots.  (Warp-aggregated slot
+// claims, and counts stored block-major, were both measured slower.)
 #include <algorithm>
 
 #include "common.cuh"
