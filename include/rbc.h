@@ -28,8 +28,12 @@
  *   tensor-core distance pass only; candidates are re-ranked in FP32
  *   difference form, the candidate set is certified with a rounding-error
  *   bound, queries that fail certification are re-searched in FP32, and
- *   near-ties are decided in FP64.  Results agree with an FP64 brute force up
- *   to ties closer than the FP32 rounding bound (about 1e-6 relative).
+ *   near-ties are decided in FP64.  On every FP32 path (RBC_F32, RBC_L1, the
+ *   re-search itself) a query whose candidate set still fails the
+ *   certificate -- more points than the set holds within the FP32 rounding
+ *   bound of its k-th distance -- is finished by an FP64 pass over every
+ *   point within that band of its database range.  Results are those of an
+ *   FP64 brute force, up to ties closer than its own rounding.
  * Errors.  Every int-returning call returns RBC_OK (0) or a negative code;
  *   rbc_last_error() then returns a message for the calling thread.  On error
  *   no output is guaranteed.  Inputs containing NaN or Inf are undefined.
@@ -208,15 +212,24 @@ int bf_search(const float* Q, int64_t m, const float* X, int64_t n, int32_t d, i
  *   no counterpart: this is a deployment variant of the brute-force search.
  *   It makes no allocation: its scratch is one static device array of 32 MiB
  *   inside the library, held by every GPU that loads the library until the
- *   process exits.  Q, X, out_ids and out_dist must be DEVICE pointers (host
- *   buffers are rejected with RBC_ERR_ARG).  Limit: the per-query candidate
- *   lists of all ceil(m / 128) query tiles must fit in the array, i.e.
- *   ceil(m / 128) * 128 * 2 * C * 8 bytes <= 32 MiB - 256 with C the smallest
- *   of 2, 4, 8, 16, 32 that is >= k + 1 (m <= 130,944 for 8 <= k <= 15,
- *   m <= 65,408 for 16 <= k <= 31); a larger m returns RBC_ERR_UNSUPPORTED with
- *   the limit in the message.  The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress, once per device, with that device current); make
- *   that first call before any stream capture.  All calls share the array:
+ *   process exits.  Q, X, out_ids and out_dist must be DEVICE pointers on the
+ *   current device (host buffers, or buffers of another GPU, are rejected with
+ *   RBC_ERR_ARG).  Limit: the per-query candidate lists of all ceil(m / 128)
+ *   query tiles plus one int per query (rows to finish exactly, rounded up to
+ *   256 bytes) must fit in the array after a 256-byte head, i.e.
+ *   ceil(m / 128) * 128 * 2 * C * 8 + ceil(4 m / 256) * 256 <= 32 MiB - 256
+ *   with C the smallest of 2, 4, 8, 16, 32 that is >= k + 1: m <= 931,968
+ *   for k = 1, 493,440 for k = 2-3, 254,080 for k = 4-7, 129,024 for
+ *   k = 8-15, 65,024 for k = 16-31.  A larger m returns RBC_ERR_UNSUPPORTED
+ *   with the limit in the message.  Queries whose candidate set fails the
+ *   FP32 certificate are finished exactly in the same call (the FP64 band
+ *   pass, working in the same scratch), as in bf_search; rbc_last_stats
+ *   then reports them (uncertified), read from the scratch on demand, so
+ *   call it before the next bf_search_noalloc on that device.  The first call
+ *   on a device looks up the array's device address (cudaGetSymbolAddress,
+ *   once per device, with that device current) and keeps it for the life of
+ *   the process: make that first call before any stream capture, and do not
+ *   use the library across a cudaDeviceReset.  All calls share the array:
  *   calls that overlap on the GPU race and must be serialised by the caller.
  *   Results and errors otherwise as bf_search.
  */
@@ -263,8 +276,9 @@ typedef struct {
                                 union of surviving lists (one-shot: padded
                                 tiles x s) */
   int64_t stage2_items;      /* stage-two work-item capacity launched */
-  int64_t uncertified;       /* queries whose low-precision candidate set failed
-                                certification and were re-searched in FP32 */
+  int64_t uncertified;       /* queries whose candidate set failed certification:
+                                re-searched in FP32 (low-precision pass), or
+                                finished by the FP64 band pass (FP32 paths) */
   int64_t fp64_ties;         /* queries whose order needed the FP64 tie step */
   int64_t boundary_ties;     /* queries with an FP32 near-tie at the k-th place */
   int64_t pairs;             /* (query, point) distances of the main BF pass:
@@ -419,10 +433,11 @@ int rbc_plan_batch(const int64_t* m, const int32_t* k, int32_t n, int64_t max_ba
  * step of the exact search runs once for all indexes: stage one against each
  * query's own representatives, pruning and work generation per 128-query tile
  * of one index, ONE persistent tensor-core launch over the work items of all
- * indexes, one merge / re-rank / certification launch, and an FP32 brute
- * force over the query's own index for uncertified queries.  No count is read
- * back to the host inside the search, so each batch shape (the per-index
- * query counts and k) is captured once as a CUDA graph and replayed.
+ * indexes, one merge / re-rank / certification launch, and an exact finish
+ * over the query's own index (the FP64 band pass) for uncertified queries.
+ * No count is read back to the host inside the search, so each batch shape
+ * (the per-index query counts and k) is captured once as a CUDA graph and
+ * replayed.
  * Results equal those of rbc_search on each index alone.
  * ------------------------------------------------------------------------- */
 typedef struct rbc_group rbc_group; /* opaque; owned by the library */
@@ -433,7 +448,7 @@ typedef struct {
   int32_t work_item_points;  /* stage-two work-item size of the last search */
   int64_t queries;           /* queries of the last search */
   int64_t tiles, work_items; /* its 128-query tiles and stage-two work items */
-  int64_t uncertified;       /* its queries searched again by FP32 brute force */
+  int64_t uncertified;       /* its queries finished by the FP64 band pass */
   int64_t fp64_ties;         /* its queries whose order needed FP64 */
   int64_t graph_replays;     /* launches of the batch shape's CUDA graph */
   uint32_t device_errors;    /* device error flags of the last search (0 = none) */

@@ -308,6 +308,9 @@ int counters_alloc(Counters& cn, Arena& ar, cudaStream_t st) {
 }
 
 thread_local int64_t t_stats_host_kept = -1;  // >= 0: kept_reps known on the host
+// set by bf_search_noalloc: its counters ([0] uncertified, [1] FP64 ties,
+// [2] boundary ties) live in the library's static scratch and are read there
+thread_local const int* t_stats_counters_dev = nullptr;
 
 int stats_publish(const Counters& cn, int64_t queries, int64_t items, int64_t host_pairs, Arena& ar,
                   cudaStream_t st, int64_t host_kept = -1) {
@@ -335,6 +338,7 @@ int stats_publish(const Counters& cn, int64_t queries, int64_t items, int64_t ho
   t_stats_fixed.fallback_ms = t_timing.ms[3];
   t_stats_stream = st;
   t_stats_pending = true;
+  t_stats_counters_dev = nullptr;
   return RBC_OK;
 }
 
@@ -410,6 +414,36 @@ int choose_c(int k, bool lp, int rerank_c) {
 // candidates need not fit in one half.
 int lp_width(int c) { return c <= 16 ? 8 : (c <= 32 ? 16 : 32); }
 
+// FP32 paths: the CUDA-core kernel keeps the C best per (row, half), C the
+// smallest list width >= k + 1, and the select merges up to 2C of them (at
+// most MAX_C): the extra candidates widen the certificate's margin at no
+// cost to the distance kernel.
+int f32_list_width(int k) { return simt_list_width(k + 1); }
+int f32_c_out(int k) { return std::min(2 * f32_list_width(k), MAX_C); }
+
+// The exact finish (band.cu) of the rows a select launch could not certify:
+// rows fb[0 .. *nfb) of the query buffer Qbuf, results at qorig[row].
+BandArgs band_args(const int* fb, const int* nfb, const float* Qbuf, const int* qorig,
+                   const float* X32, const int* xid, int64_t n, int d, int k, int metric,
+                   int64_t* out_ids, float* out_dist) {
+  BandArgs b{};
+  b.rows = fb;
+  b.nrows_dev = nfb;
+  b.Q32 = Qbuf;
+  b.qorig = qorig;
+  b.X32 = X32;
+  b.xid = xid;
+  b.n = n;
+  b.d = d;
+  b.ld = d;
+  b.k = k;
+  b.metric = metric;
+  b.eps = rerank_eps_host(d);
+  b.out_ids = out_ids;
+  b.out_dist = out_dist;
+  return b;
+}
+
 // ---------------------------------------------------------------------------
 // database views for the BF core
 // ---------------------------------------------------------------------------
@@ -422,6 +456,7 @@ struct DbView {
   const float* xscale = nullptr;  // FP8: per-row scales
   int dpad = 0;
   const unsigned* lp_max = nullptr;  // [0] max |x - x~|, [1] max |x~| (float bits)
+  const void* nblock = nullptr;      // bf16 / fp16: [rows + pad, 16] norm block
 };
 
 // Dense BF(Q, DB) with the FP32 CUDA-core kernel; results for query row i go
@@ -430,8 +465,8 @@ int bf_dense_f32(const float* Qdev, int64_t m, const DbView& db, int d, int k, i
                  const int* qorig, int64_t* out_ids, float* out_dist, int* cnt, Arena& ar,
                  cudaStream_t st, bool marks = true) {
   if (m == 0) return RBC_OK;
-  const int c_out = choose_c(k, false, 0);
-  const int C = simt_list_width(c_out);
+  const int C = f32_list_width(k);
+  const int c_out = f32_c_out(k);
   const int64_t tiles = (m + TQ - 1) / TQ;
   const int sms = sm_count();
   int64_t splits = (8LL * sms + tiles - 1) / tiles;
@@ -472,12 +507,20 @@ int bf_dense_f32(const float* Qdev, int64_t m, const DbView& db, int d, int k, i
   a.c_out = c_out;
   a.out_ids = out_ids;
   a.out_dist = out_dist;
-  a.counters = cnt;
+  int* fb;
+  int* lc;  // [0] rows appended to fb, [1..2] ties
+  RBC_TRY(ar.alloc(&fb, m));
+  RBC_TRY(ar.alloc(&lc, 8));
+  RBC_CUDA(cudaMemsetAsync(lc, 0, 8 * sizeof(int), st));
+  a.fallback_rows = fb;
+  a.counters = lc;
   RBC_TRY(launch_select(a, st));
-  if (marks) {
-    tmark(3, st);
-    tmark(4, st);
-  }
+  RBC_TRY(launch_add_ints(cnt, lc, 3, st));
+  if (marks) tmark(3, st);
+  RBC_TRY(launch_band(band_args(fb, lc, Qdev, qorig, db.X32, db.xid, db.rows, d, k, metric,
+                                out_ids, out_dist),
+                      (int)m, st));
+  if (marks) tmark(4, st);
   return RBC_OK;
 }
 
@@ -634,7 +677,7 @@ int bf_dense_lp(const float* Qdev, int64_t m, const DbView& db, int d, int k, in
   w.dense_splits = (int)splits;
   w.dense_chunk = chunk;
   LpMatrix Qm{ql.lp, ql.norm, m, db.dpad, storage, nullptr, ql.scale};
-  LpMatrix Xm{db.Xlp, db.xnorm, db.rows, db.dpad, storage, nullptr, db.xscale};
+  LpMatrix Xm{db.Xlp, db.xnorm, db.rows, db.dpad, storage, db.nblock, db.xscale};
   uint32_t* dev_err;
   RBC_TRY(ar.alloc(&dev_err, 1));
   RBC_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(uint32_t), st));
@@ -862,10 +905,11 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
   db.xscale = ix->xscale;
   db.dpad = ix->dpad;
   db.lp_max = ix->lp_max;
+  db.nblock = ix->xnblock;
   const int64_t cap_items = tiles * item_cap;
   if (!lp) {
-    const int c_out = choose_c(k, false, 0);
-    const int C = simt_list_width(c_out);
+    const int C = f32_list_width(k);
+    const int c_out = f32_c_out(k);
     float* ps;
     int* pi;
     RBC_TRY(ar.alloc(&ps, cap_items * TQ * 2 * C));
@@ -892,9 +936,21 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
     a.c_out = c_out;
     a.out_ids = ids;
     a.out_dist = dist;
-    a.counters = cn.c;
+    int* fb;
+    int* lc;  // [0] rows appended to fb, [1..2] ties
+    RBC_TRY(ar.alloc(&fb, mb));
+    RBC_TRY(ar.alloc(&lc, 8));
+    RBC_CUDA(cudaMemsetAsync(lc, 0, 8 * sizeof(int), st));
+    a.fallback_rows = fb;
+    a.counters = lc;
     RBC_TRY(launch_select(a, st));
+    RBC_TRY(launch_add_ints(cn.c, lc, 3, st));
     tmark(3, st);
+    // uncertified rows: the FP64 band over the whole index (a superset of
+    // their surviving lists)
+    RBC_TRY(launch_band(band_args(fb, lc, Qp, qperm, ix->X32, ix->members, n, d, k, metric, ids,
+                                  dist),
+                        (int)mb, st));
     tmark(4, st);
   } else {
     const int c_out = choose_c(k, true, ix->rerank_c);
@@ -908,7 +964,7 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
     RBC_TRY(ar.alloc(&pi, cap_items * TQ * 2 * C));
     RBC_TRY(ar.alloc(&pv, cap_items));
     LpMatrix Qm{ql.lp, ql.norm, mb, ix->dpad, ix->storage, nullptr, ql.scale};
-    LpMatrix Xm{ix->Xlp, ix->xnorm, n, ix->dpad, ix->storage, nullptr, ix->xscale};
+    LpMatrix Xm{ix->Xlp, ix->xnorm, n, ix->dpad, ix->storage, ix->xnblock, ix->xscale};
     tmark(1, st);
     RBC_TRY(launch_bf_tc_topc(Qm, Xm, C, w2, TopOut{ps, pi, pv}, sms, st, dev_err));
     // the bound g of each sorted row, for the re-search of uncertified rows
@@ -1157,7 +1213,8 @@ int own_list_bound(const rbc_index* ix, const float* Qb, int64_t mb, const int64
   RBC_TRY(ar.alloc(&ps, gq.max_tiles * TQ * 2 * C));
   RBC_TRY(ar.alloc(&pi, gq.max_tiles * TQ * 2 * C));
   LpMatrix Qm{alp, anorm, gq.rows_cap, ix->dpad, ix->storage, nullptr, ascale};
-  LpMatrix Xm{ix->Xlp, ix->xnorm, ix->list_entries, ix->dpad, ix->storage, nullptr, ix->xscale};
+  LpMatrix Xm{ix->Xlp, ix->xnorm, ix->list_entries, ix->dpad, ix->storage, ix->xnblock,
+              ix->xscale};
   TileWork wo = gq.w;
   wo.strided = true;  // one item per query tile: a popular list's tiles spread over CTAs
   RBC_TRY(launch_bf_tc_topc(Qm, Xm, C, wo, TopOut{ps, pi, nullptr}, sm_count(), st, dev_err));
@@ -1195,8 +1252,8 @@ int oneshot_stage2(const rbc_index* ix, const float* Qsrc, int64_t mq, const int
   a.out_ids = ids;
   a.out_dist = dist;
   if (!lp) {
-    const int c_out = choose_c(k, false, 0);
-    const int C = simt_list_width(c_out);
+    const int C = f32_list_width(k);
+    const int c_out = f32_c_out(k);
     float* ps;
     int* pi;
     RBC_TRY(ar.alloc(&ps, max_tiles * TQ * 2 * C));
@@ -1210,12 +1267,24 @@ int oneshot_stage2(const rbc_index* ix, const float* Qsrc, int64_t mq, const int
     a.C = C;
     a.simt_eps = simt_eps(d);
     a.c_out = c_out;
-    a.counters = cnt;
+    int* fb;
+    int* lc;  // [0] rows appended to fb, [1..2] ties
+    RBC_TRY(ar.alloc(&fb, rows_cap));
+    RBC_TRY(ar.alloc(&lc, 8));
+    RBC_CUDA(cudaMemsetAsync(lc, 0, 8 * sizeof(int), st));
+    a.fallback_rows = fb;
+    a.counters = lc;
     RBC_TRY(launch_select(a, st));
-    if (marks) {
-      tmark(3, st);
-      tmark(4, st);
-    }
+    RBC_TRY(launch_add_ints(cnt, lc, 3, st));
+    if (marks) tmark(3, st);
+    // uncertified rows: the FP64 band over the row's own list
+    BandArgs b = band_args(fb, lc, Qp, qout, ix->X32, ix->members, entries, d, k, metric, ids,
+                           dist);
+    b.tile_list = tile_rep;
+    b.list_off = list_off;
+    b.list_len = ix->s;
+    RBC_TRY(launch_band(b, (int)rows_cap, st));
+    if (marks) tmark(4, st);
     return RBC_OK;
   }
   const int c_out = choose_c(k, true, ix->rerank_c);
@@ -1232,7 +1301,7 @@ int oneshot_stage2(const rbc_index* ix, const float* Qsrc, int64_t mq, const int
   RBC_TRY(ar.alloc(&dev_err, 1));
   RBC_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(uint32_t), st));
   LpMatrix Qm{ql.lp, ql.norm, rows_cap, ix->dpad, ix->storage, nullptr, ql.scale};
-  LpMatrix Xm{ix->Xlp, ix->xnorm, entries, ix->dpad, ix->storage, nullptr, ix->xscale};
+  LpMatrix Xm{ix->Xlp, ix->xnorm, entries, ix->dpad, ix->storage, ix->xnblock, ix->xscale};
   if (marks) tmark(1, st);
   RBC_TRY(launch_bf_tc_topc(Qm, Xm, C, w, TopOut{ps, pi, pv}, sms, st, dev_err));
   if (marks) tmark(2, st);
@@ -1700,6 +1769,19 @@ int64_t search_workspace_bound(const rbc_index* ix, int64_t m, int k) {
 }
 
 }  // namespace
+
+void stats_publish_static(const int* counters_dev, int64_t queries, int64_t pairs,
+                          cudaStream_t st) {
+  memset(&t_stats_fixed, 0, sizeof(t_stats_fixed));
+  t_stats_fixed.queries = queries;
+  t_stats_fixed.pairs = pairs;
+  t_stats_fixed.kernel_launches = t_launches;
+  t_stats_host_kept = -1;
+  t_stats_stream = st;
+  t_stats_pending = true;
+  t_stats_counters_dev = counters_dev;
+}
+
 }  // namespace rbc
 
 // ===========================================================================
@@ -1730,6 +1812,18 @@ int rbc_last_stats(rbc_search_stats* out) {
   if (!out) {
     set_error("rbc_last_stats: NULL");
     return RBC_ERR_ARG;
+  }
+  if (t_stats_pending && t_stats_counters_dev) {
+    cudaError_t e = cudaStreamSynchronize(t_stats_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+    int c[8] = {0};
+    e = cudaMemcpy(c, t_stats_counters_dev, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy", __FILE__, __LINE__);
+    t_stats_fixed.uncertified = c[0];
+    t_stats_fixed.fp64_ties = c[1];
+    t_stats_fixed.boundary_ties = c[2];
+    t_stats_pending = false;
+    t_stats_counters_dev = nullptr;
   }
   if (t_stats_pending) {
     cudaError_t e = cudaStreamSynchronize(t_stats_stream);
@@ -1804,6 +1898,14 @@ int bf_search(const float* Q, int64_t m, const float* X, int64_t n, int32_t d, i
     RBC_TRY(ar.alloc(&mx, 2));
     RBC_CUDA(cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned), st));
     RBC_TRY(launch_to_lowp(Xdev, n, d, db.dpad, storage, xl, xn, nullptr, mx, mx + 1, st, xs));
+    if (storage != RBC_FP8E4M3) {
+      // -|x~|^2 / 2 as a bf16 (high, low) block: the tensor-core pass adds it
+      // to its accumulators with one extra MMA
+      uint16_t* nb;
+      RBC_TRY(ar.alloc(&nb, (n + NORM_PAD) * NBLOCK_COLS));
+      RBC_TRY(launch_norm_block(xn, n, n + NORM_PAD, nb, st));
+      db.nblock = nb;
+    }
     db.Xlp = xl;
     db.xnorm = xn;
     db.xscale = xs;

@@ -605,36 +605,8 @@ int launch_bf_tc_topc(const LpMatrix& Qm, const LpMatrix& Xm, int C, const TileW
     set_error("tensor-core BF: FP8 list width %d / padded dimension %d unsupported", C, Qm.dpad);
     return RBC_ERR_UNSUPPORTED;
   }
-  if (C == 8) {
-    switch (Qm.dpad / 64) {
-      case 1: return launch_tc<8, 1, 256, 4, 8>(Qm, Xm, w, out, grid, st, dev_err);
-      case 2: return launch_tc<8, 2, 128, 3, 8>(Qm, Xm, w, out, grid, st, dev_err);
-      case 3: return launch_tc<8, 3, 64, 3, 8>(Qm, Xm, w, out, grid, st, dev_err);
-      case 4: return launch_tc<8, 4, 64, 2, 4>(Qm, Xm, w, out, grid, st, dev_err);
-      default: break;
-    }
-  } else if (C == 16) {
-    switch (Qm.dpad / 64) {
-      case 1: return launch_tc<16, 1, 256, 4, 8>(Qm, Xm, w, out, grid, st, dev_err);
-      case 2: return launch_tc<16, 2, 128, 3, 8>(Qm, Xm, w, out, grid, st, dev_err);
-      case 3: return launch_tc<16, 3, 64, 3, 8>(Qm, Xm, w, out, grid, st, dev_err);
-      case 4: return launch_tc<16, 4, 64, 2, 4>(Qm, Xm, w, out, grid, st, dev_err);
-      default: break;
-    }
-  } else if (C == 32) {
-    switch (Qm.dpad / 64) {
-      case 1: return launch_tc<32, 1, 256, 4, 8>(Qm, Xm, w, out, grid, st, dev_err);
-      case 2: return launch_tc<32, 2, 128, 2, 8>(Qm, Xm, w, out, grid, st, dev_err);
-      case 3: return launch_tc<32, 3, 64, 3, 8>(Qm, Xm, w, out, grid, st, dev_err);
-      case 4: return launch_tc<32, 4, 64, 2, 2>(Qm, Xm, w, out, grid, st, dev_err);
-      default: break;
-    }
-  } else {
-    set_error("tensor-core BF: list width %d unsupported (8, 16 or 32)", C);
-    return RBC_ERR_ARG;
-  }
-  set_error("tensor-core BF: padded dimension %d unsupported", Qm.dpad);
-  return RBC_ERR_UNSUPPORTED;
+  // bf16 / fp16: the norm folded into the MMA (bf_tc_top.cu)
+  return launch_bf_tc_top(Qm, Xm, C, w, out, grid, st, dev_err);
 }
 
 }  // namespace rbc

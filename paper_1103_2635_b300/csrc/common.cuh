@@ -105,6 +105,22 @@ __device__ __forceinline__ float rerank_rho8(const float* qr, const float* xr, i
   return metric == RBC_L2 ? sqrtf(p) : p;
 }
 
+// The same distance in FP64 (from the FP32 inputs), by the eight lanes of a
+// group; every lane of the group returns it.  All 32 lanes of the warp must
+// call it together.
+__device__ __forceinline__ double rho64_8(const float* qr, const float* xr, int d, int metric,
+                                          int g8) {
+  double p = 0.0;
+  for (int i = g8; i < d; i += 8) {
+    const double t = (double)qr[i] - (double)xr[i];
+    p += metric == RBC_L2 ? t * t : fabs(t);
+  }
+  p += __shfl_xor_sync(0xffffffffu, p, 1);
+  p += __shfl_xor_sync(0xffffffffu, p, 2);
+  p += __shfl_xor_sync(0xffffffffu, p, 4);
+  return metric == RBC_L2 ? sqrt(p) : p;
+}
+
 // Largest low-precision score |x~|^2 - 2 q~.x~ that a point within distance
 // g of q can have: (g + |q - q~| + max |x - x~|)^2 - |q~|^2 + E_f, with E_f the
 // FP32 evaluation bound (d + 4) 2^-19 (|q~| + max |x~|)^2 (doubled), rounded up.

@@ -239,7 +239,7 @@ struct Plan {
   int k = 0;
   int W = 0;               // stage-two work-item size (points)
   int64_t M = 0, MP = 0, tiles = 0, item_cap_total = 0;
-  int seg_cap = 0, C = 0, c_out = 0, c_sel = 0;
+  int seg_cap = 0, C = 0, c_sel = 0;
   std::vector<void*> dev;  // device allocations
   // device arrays
   int *row_index = nullptr, *tile_index = nullptr, *tile_item_cap = nullptr;
@@ -306,6 +306,7 @@ struct rbc_group {
       *d_of_d = nullptr;
   int64_t *row_base_d = nullptr, *n_of_d = nullptr;
   void* Xlp = nullptr;
+  void* xnblock = nullptr;  // [N + pad, 16] bf16: -|x~|^2 / 2 as (high, low), the norm MMA's B
   unsigned* lp_max = nullptr;
   int W = 0;  // tuned work-item size (0: default)
   std::mutex mu;
@@ -406,7 +407,6 @@ int make_plan(rbc_group* g, const std::vector<int64_t>& m, int k, int W, cudaStr
   const int c_out = std::min(k <= 1 ? 16 : 32, MAX_C);  // low-precision candidate lists
   P->c_sel = c_out;
   P->C = c_out <= 16 ? 8 : 16;
-  P->c_out = std::min(k + 1, 32);
   if (M == 0) {
     out = std::move(P);
     return RBC_OK;
@@ -524,7 +524,7 @@ int run_plan(rbc_group* g, Plan& p, cudaStream_t st) {
   w.n = g->N;
   w.tile_kb = p.tile_kb;  // an index of d <= 64 multiplies one K block, not two
   LpMatrix Qm{p.qlp, p.qnorm, MP, g->dpad, g->storage};
-  LpMatrix Xm{g->Xlp, g->xnorm, g->N, g->dpad, g->storage};
+  LpMatrix Xm{g->Xlp, g->xnorm, g->N, g->dpad, g->storage, g->xnblock};
   G_TRY(launch_bf_tc_topc(Qm, Xm, p.C, w, TopOut{p.ps, p.pi, p.pv}, sms, st, p.dev_err));
   // merge + FP32 re-rank + certification + FP64 ties for every query
   SelectArgs a{};
@@ -554,24 +554,26 @@ int run_plan(rbc_group* g, Plan& p, cudaStream_t st) {
   a.counters = p.counters;
   a.tile_dim = p.tile_dim;  // re-rank over each index's own columns
   G_TRY(launch_select(a, st));
-  // uncertified rows: FP32 brute force over their own index
-  GroupFallbackArgs f{};
-  f.rows = p.fb_rows;
-  f.num_rows_dev = p.counters;
-  f.Q32 = p.Qs;
-  f.d = DG;
-  f.qorig = p.qsrc;
-  f.tile_index = p.tile_index;
-  f.row_base = g->row_base_d;
-  f.n_of = g->n_of_d;
-  f.X32 = g->X32;
-  f.xid = g->members;
-  f.k = p.k;
-  f.c_out = p.c_out;
-  f.out_ids = p.out_ids;
-  f.out_dist = p.out_dist;
-  f.counters = p.counters + 4;
-  G_TRY(launch_group_fallback(f, sms * 4, st));
+  // uncertified rows: the FP64 band over their own index (band.cu)
+  BandArgs b{};
+  b.rows = p.fb_rows;
+  b.nrows_dev = p.counters;
+  b.Q32 = p.Qs;
+  b.qorig = p.qsrc;
+  b.X32 = g->X32;
+  b.xid = g->members;
+  b.n = g->N;
+  b.tile_grp = p.tile_index;
+  b.grp_base = g->row_base_d;
+  b.grp_len = g->n_of_d;
+  b.d = DG;
+  b.ld = DG;
+  b.k = p.k;
+  b.metric = RBC_L2;
+  b.eps = (0.25f * DG + 8.0f) * 5.9604645e-08f;  // the re-rank's bound at the widest rows
+  b.out_ids = p.out_ids;
+  b.out_dist = p.out_dist;
+  G_TRY(launch_band(b, (int)MP, st));
   return RBC_OK;
 }
 
@@ -736,6 +738,10 @@ int rbc_group_create(const rbc_index* const* indexes, int32_t count, void* strea
   RBC_CUDA(cudaMemsetAsync(g.lp_max, 0, 2 * sizeof(unsigned), st));
   G_TRY(launch_to_lowp(g.X32, g.N, g.DG, g.dpad, g.storage, g.Xlp, g.xnorm, nullptr, g.lp_max,
                        g.lp_max + 1, st));
+  uint16_t* nb;
+  G_TRY(g.alloc(&nb, (g.N + GROUP_NORM_PAD) * NBLOCK_COLS));
+  G_TRY(launch_norm_block(g.xnorm, g.N, g.N + GROUP_NORM_PAD, nb, st));
+  g.xnblock = nb;
   G_TRY(g.alloc(&g.rep_base_d, count));
   G_TRY(g.alloc(&g.nr_of_d, count));
   G_TRY(g.alloc(&g.d_of_d, count));

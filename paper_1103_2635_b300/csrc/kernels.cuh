@@ -60,8 +60,14 @@ inline int lp_elem_bytes(int storage) { return storage == RBC_FP8E4M3 ? 1 : 2; }
 constexpr int NBLOCK_COLS = 16;
 
 bool tc_available();
+// Tensor-core BF fused with a per-query top-C: per (slot, query row) two
+// sub-lists (column halves) of C entries.  FP8 runs bf_tc.cu; bf16 / fp16 run
+// bf_tc_top.cu, which needs Xm.nblock.
 int launch_bf_tc_topc(const LpMatrix& Qm, const LpMatrix& Xm, int C, const TileWork& w,
                       const TopOut& out, int grid, cudaStream_t st, uint32_t* dev_err);
+// the bf16 / fp16 pass itself: cs entries per (row, column half)
+int launch_bf_tc_top(const LpMatrix& Qm, const LpMatrix& Xm, int cs, const TileWork& w,
+                     const TopOut& out, int grid, cudaStream_t st, uint32_t* dev_err);
 
 // ---- windowed stage two: per (representative, query chunk) work items ----
 // Queries pair_q[pair_begin .. pair_begin + nq) (rows of the query buffer)
@@ -147,27 +153,45 @@ struct SelectArgs {
 };
 int launch_select(const SelectArgs& a, cudaStream_t st);
 
-// Grouped multi-index search: uncertified rows (padded rows of the grouped
-// query buffer, device-side count) searched by FP32 brute force over their
-// own index, written to output row qorig[row].
-struct GroupFallbackArgs {
-  const int* rows;           // [*num_rows_dev] padded rows
-  const int* num_rows_dev;
-  const float* Q32;          // [padded rows, d] FP32 queries (zero-padded columns)
-  int d;                     // common row length of Q32 and X32
-  const int* qorig;          // padded row -> output row (or -1)
-  const int* tile_index;     // padded row / TQ -> index
-  const int64_t* row_base;   // index -> first row in X32
-  const int64_t* n_of;       // index -> rows
-  const float* X32;          // grouped FP32 rows (list order per index)
-  const int* xid;            // row -> database id within its index
-  int k;
-  int c_out;                 // k + 1 (at most 32)
+
+// Exact finish of uncertified rows (band.cu): for each buffer row rows[i],
+// i < *nrows_dev, every point of the row's database range whose FP32
+// distance lies within the rounding band of the row's current k-th distance
+// (read from out_dist at the row's output row) is evaluated in FP64, and the
+// row's output is overwritten with the k smallest (rho64, id).
+struct BandArgs {
+  const int* rows;
+  const int* nrows_dev;
+  const float* Q32;          // buffer queries, rows ld floats apart
+  const int* qorig;          // buffer row -> output row (nullptr: identity; < 0: skip)
+  const float* X32;          // database rows, ld floats apart
+  const int* xid;            // row -> database id (nullptr: identity)
+  int64_t n;                 // database rows (default range [0, n))
+  // optional per-row range, grouped layout: g = tile_grp[row / TQ] ->
+  // [grp_base[g], grp_base[g] + grp_len[g])
+  const int* tile_grp;
+  const int64_t* grp_base;
+  const int64_t* grp_len;
+  // optional per-row range, one-shot layout: r = tile_list[row / TQ] ->
+  // [list_off[r], list_off[r + 1]), or [r list_len, (r + 1) list_len)
+  const int* tile_list;
+  const int* list_off;
+  int list_len;
+  int d;                     // columns evaluated
+  int ld;                    // row stride of Q32 and X32 (>= d)
+  int k;                     // <= 32
+  int metric;
+  float eps;                 // relative bound of the FP32 re-rank that wrote out_dist
   int64_t* out_ids;
   float* out_dist;
-  int* counters;             // [1] FP64 ties (optional)
 };
-int launch_group_fallback(const GroupFallbackArgs& a, int grid, cudaStream_t st);
+// grid over at most max_rows rows (the count itself is read on the device)
+int launch_band(const BandArgs& a, int max_rows, cudaStream_t st);
+
+// rbc_last_stats after bf_search_noalloc: queries / pairs from the host, the
+// certification counters read from counters_dev (static scratch) on demand
+void stats_publish_static(const int* counters_dev, int64_t queries, int64_t pairs,
+                          cudaStream_t st);
 
 // Candidate buffers of the windowed search -> exact k-NN per query.
 constexpr int CAND_CAP = 8192;  // candidates per query

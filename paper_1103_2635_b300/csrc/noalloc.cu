@@ -36,10 +36,9 @@ std::mutex g_scratch_mu;
 
 // Device address of the scratch array for the current device.  In host code
 // `g_noalloc_scratch` is only a host-side stand-in for the symbol, so the
-// address is looked up once per device (with that device current) and cached.
-int scratch_for_current_device(void** out) {
-  int dev = 0;
-  RBC_CUDA(cudaGetDevice(&dev));
+// address is looked up once per device (with that device current, on the
+// first call there) and cached for the life of the process.
+int scratch_for_current_device(int dev, void** out) {
   if (dev < 0 || dev >= MAX_DEVICES) {
     set_error("bf_search_noalloc: device ordinal %d out of range", dev);
     return RBC_ERR_UNSUPPORTED;
@@ -55,14 +54,24 @@ int scratch_for_current_device(void** out) {
   return RBC_OK;
 }
 
-bool on_device(const void* p) {
+// A device (or managed) pointer usable on the current device: the scratch
+// belongs to the current device, so buffers of another GPU are refused
+// rather than reached through unified addressing.
+bool on_current_device(const void* p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
+
+// Scratch layout of a call: [256-byte head: 8 int counters] [re-search rows:
+// m ints, rounded up to 256 bytes] [partial candidate lists: items x 128
+// rows x 2 halves x C x (score, column)].
+constexpr size_t NOALLOC_HEAD = 256;
+size_t rows_bytes(int64_t m) { return ((size_t)m * 4 + 255) / 256 * 256; }
 
 }  // namespace
 }  // namespace rbc
@@ -95,32 +104,37 @@ extern "C" int bf_search_noalloc(const float* Q, int64_t m, const float* X, int6
     set_error("bf_search_noalloc: NULL pointer");
     return RBC_ERR_ARG;
   }
-  if (!on_device(Q) || !on_device(X) || !on_device(out_ids) || !on_device(out_dist)) {
-    set_error("bf_search_noalloc: Q, X, out_ids and out_dist must be device pointers "
-              "(host buffers would need device copies, i.e. an allocation)");
+  int dev = 0;
+  RBC_CUDA(cudaGetDevice(&dev));
+  if (!on_current_device(Q, dev) || !on_current_device(X, dev) ||
+      !on_current_device(out_ids, dev) || !on_current_device(out_dist, dev)) {
+    set_error("bf_search_noalloc: Q, X, out_ids and out_dist must be device pointers on the "
+              "current device %d (host buffers would need device copies, i.e. an allocation)",
+              dev);
     return RBC_ERR_ARG;
   }
 
-  // scratch layout: [8 counters (int)] [partial scores] [partial columns]
-  const int c_out = std::min(k + 1, MAX_C);
-  const int C = simt_list_width(c_out);
+  const int C = simt_list_width(k + 1);
+  const int c_out = std::min(2 * C, MAX_C);
   const int64_t tiles = (m + TQ - 1) / TQ;
   const int64_t per_item = (int64_t)TQ * 2 * C;  // entries per work item
-  const size_t head = 256;                        // counters, padded to the alignment
-  const int64_t max_items = (int64_t)((NOALLOC_SCRATCH_BYTES - head) / (per_item * 8));
+  const size_t fixed = NOALLOC_HEAD + rows_bytes(m);
+  const int64_t max_items =
+      fixed < NOALLOC_SCRATCH_BYTES
+          ? (int64_t)((NOALLOC_SCRATCH_BYTES - fixed) / (size_t)(per_item * 8))
+          : 0;
   if (tiles > max_items) {
-    set_error("bf_search_noalloc: m=%lld needs %lld query tiles but the %zu-byte scratch holds "
-              "at most %lld for k=%d (m <= %lld)",
-              (long long)m, (long long)tiles, NOALLOC_SCRATCH_BYTES, (long long)max_items, k,
-              (long long)(max_items * TQ));
+    set_error("bf_search_noalloc: m=%lld needs %lld query tiles of candidate lists plus %zu "
+              "bytes of re-search rows, but the %zu-byte scratch holds only %lld tiles at k=%d",
+              (long long)m, (long long)tiles, rows_bytes(m), NOALLOC_SCRATCH_BYTES,
+              (long long)max_items, k);
     return RBC_ERR_UNSUPPORTED;
   }
   void* base = nullptr;
-  int rc = scratch_for_current_device(&base);
+  int rc = scratch_for_current_device(dev, &base);
   if (rc != RBC_OK) return rc;
 
-  int sms = 1, dev = 0;
-  cudaGetDevice(&dev);
+  int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   // database splits: enough work items for the GPU, within the scratch
   int64_t splits = (8LL * sms + tiles - 1) / tiles;
@@ -130,10 +144,13 @@ extern "C" int bf_search_noalloc(const float* Q, int64_t m, const float* X, int6
   splits = (n + chunk - 1) / chunk;
   const int64_t items = tiles * splits;
 
-  int* counters = static_cast<int*>(base);
-  float* ps = reinterpret_cast<float*>(static_cast<unsigned char*>(base) + head);
+  unsigned char* b8 = static_cast<unsigned char*>(base);
+  int* counters = reinterpret_cast<int*>(b8);
+  int* fb_rows = reinterpret_cast<int*>(b8 + NOALLOC_HEAD);
+  float* ps = reinterpret_cast<float*>(b8 + fixed);
   int* pi = reinterpret_cast<int*>(ps + items * per_item);
   RBC_CUDA(cudaMemsetAsync(counters, 0, 8 * sizeof(int), st));
+  t_launches = 0;
 
   TileWork w{};
   w.num_items = (int)items;
@@ -162,6 +179,27 @@ extern "C" int bf_search_noalloc(const float* Q, int64_t m, const float* X, int6
   a.c_out = c_out;
   a.out_ids = out_ids;
   a.out_dist = out_dist;
+  a.fallback_rows = fb_rows;
   a.counters = counters;
-  return launch_select(a, st);
+  rc = launch_select(a, st);
+  if (rc != RBC_OK) return rc;
+  // rows the certificate could not decide: the FP64 band over X (band.cu),
+  // with the row list and its count in the scratch
+  BandArgs b{};
+  b.rows = fb_rows;
+  b.nrows_dev = counters;
+  b.Q32 = Q;
+  b.X32 = X;
+  b.n = n;
+  b.d = d;
+  b.ld = d;
+  b.k = k;
+  b.metric = metric;
+  b.eps = (0.25f * d + 8.0f) * 5.9604645e-08f;
+  b.out_ids = out_ids;
+  b.out_dist = out_dist;
+  rc = launch_band(b, (int)m, st);
+  if (rc != RBC_OK) return rc;
+  stats_publish_static(counters, m, m * n, st);
+  return RBC_OK;
 }

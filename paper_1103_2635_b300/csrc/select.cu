@@ -265,10 +265,13 @@ __global__ void __launch_bounds__(WARPS * 32) select_kernel(SelectArgs a) {
     } else {
       float qn = a.q_lpnorm[row];
       float nq = sqrtf(qn);
-      float span = nq + __uint_as_float(*a.x_norm_max_bits);
+      const float xn = __uint_as_float(*a.x_norm_max_bits);
+      float span = nq + xn;
       // FP32 evaluation bound of |x~|^2 - 2 q~.x~ (tensor-core products are
-      // exact, accumulation allowed 2^-20 relative per term): (d+4) 2^-19 span^2
-      float ef = (float)(d + 4) * 1.9073486e-06f * span * span;
+      // exact, accumulation allowed 2^-20 relative per term): (d+4) 2^-19 span^2,
+      // plus 2^-16 max|x~|^2 for a norm term that enters the accumulator as a
+      // bf16 (high, low) pair (its error is at most 2^-17 |x~|^2)
+      float ef = (float)(d + 4) * 1.9073486e-06f * span * span + 1.5258789e-05f * xn * xn;
       float t = B + qn - ef;
       lower = (t > 0.f ? sqrtf(t) * (1.0f - 4.0f * U32) : 0.f) - a.q_err[row] -
               __uint_as_float(*a.x_err_max_bits);
@@ -381,9 +384,95 @@ __device__ __forceinline__ unsigned kth_score_key(const float* sc, int cnt, int 
   return kth;
 }
 
+// Band of the k-th place: the largest FP32 distance a point among the k
+// nearest can have, r_k (1 + eps) / (1 - eps) rounded up (the k ranked points
+// are k distinct points within r_k / (1 - eps) of the query).
+__device__ __forceinline__ float kth_band(float rk, float eps) {
+  return rk < INFINITY ? rk * (1.0f + eps) / (1.0f - eps) * (1.0f + 8.0f * U32) : INFINITY;
+}
+
+// Exact finish of a query whose FP32 ranks tie (within the re-rank's rounding
+// band) across the k-th place: the rows of every candidate whose FP32
+// distance is within kth_band -- a set that holds the true k nearest -- are
+// evaluated in FP64 and ranked by (rho64, id).  They come in batches: this
+// merges the batch sr[0 .. ns) (shared memory, ns <= RERANK_MAX; eight lanes
+// per row evaluate it) into the sorted list best_r / best_i [0 .. nbest)
+// (shared memory) by k rounds of a warp arg-min over both, and returns the
+// new list length, min(k, nbest + ns).  sid / s64 are shared scratch of
+// RERANK_MAX entries.  After the last batch, best[0 .. k) is the FP64 brute
+// force's answer over the candidates.
+__device__ int band_merge(const float* qr, const float* X32, const int* xid, int d, int metric,
+                          int k, const int* sr, int ns, int* sid, double* s64, double* best_r,
+                          int* best_i, int nbest, int lane) {
+  for (int e0 = 0; e0 < ns; e0 += 4) {
+    const int e = e0 + (lane >> 3);
+    const int row = sr[e < ns ? e : 0];
+    const double v = rho64_8(qr, X32 + (int64_t)row * d, d, metric, lane & 7);
+    if ((lane & 7) == 0 && e < ns) s64[e] = v;
+  }
+  for (int e = lane; e < ns; e += 32) sid[e] = xid ? xid[sr[e]] : sr[e];
+  __syncwarp();
+  const int nout = min(k, nbest + ns);
+  unsigned taken = 0;            // bit t: batch entry lane + 32 t already ranked
+  bool btaken = lane >= nbest;   // list entry `lane` already ranked (or absent)
+  double myr = INFINITY;
+  int myi = INT32_MAX;
+  for (int j = 0; j < nout; ++j) {
+    double bv = INFINITY;
+    int bi = INT32_MAX, bt = -2;
+    if (!btaken) {
+      bv = best_r[lane];
+      bi = best_i[lane];
+      bt = -1;
+    }
+    for (int t = 0; t < RERANK_MAX / 32; ++t) {
+      const int e = lane + 32 * t;
+      if (e < ns && !((taken >> t) & 1u)) {
+        const double v = s64[e];
+        const int id = sid[e];
+        if (v < bv || (v == bv && id < bi)) {
+          bv = v;
+          bi = id;
+          bt = t;
+        }
+      }
+    }
+    int bl = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+      if (ov < bv || (ov == bv && (oi < bi || (oi == bi && ol < bl)))) {
+        bv = ov;
+        bi = oi;
+        bl = ol;
+      }
+    }
+    if (lane == bl) {
+      if (bt == -1) btaken = true;
+      else if (bt >= 0) taken |= 1u << bt;
+    }
+    if (lane == j) {
+      myr = bv;
+      myi = bi;
+    }
+  }
+  __syncwarp();
+  if (lane < nout) {
+    best_r[lane] = myr;
+    best_i[lane] = myi;
+  }
+  __syncwarp();
+  return nout;
+}
+
 __global__ void __launch_bounds__(WARPS * 32) select_cands_kernel(CandSelectArgs a) {
   __shared__ int stage[WARPS][RERANK_MAX];
   __shared__ float dstage[WARPS][RERANK_MAX];
+  __shared__ double s64[WARPS][RERANK_MAX];
+  __shared__ double best_r[WARPS][32];
+  __shared__ int best_i[WARPS][32];
   const int wib = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int64_t wi = (int64_t)blockIdx.x * WARPS + wib;
@@ -525,8 +614,33 @@ __global__ void __launch_bounds__(WARPS * 32) select_cands_kernel(CandSelectArgs
     }
   }
   const float eps = rerank_eps(d);
-  const unsigned tie_mask = fp64_ties(qr, a.X32, d, d, a.metric, k, a.c_out, eps, lane, rho, oid,
-                                      brow);
+  // A candidate past rank k - 1 within the band of the k-th place: the
+  // lanes' ranks may miss a point of the true k nearest, so every survivor
+  // in the band is decided in FP64 (compacted in place: positions only move
+  // down, and each chunk is read before the ballot that places it).
+  const float band = kth_band(__shfl_sync(0xffffffffu, rho, k - 1), eps);
+  unsigned tie_mask;
+  if (__shfl_sync(0xffffffffu, rho, k) <= band) {
+    int ns = 0;
+    for (int e0 = 0; e0 < nre; e0 += 32) {
+      const int e = e0 + lane;
+      const int row = e < nre ? stg[e] : 0;
+      const bool pass = e < nre && dst[e] <= band;
+      const unsigned bal = __ballot_sync(0xffffffffu, pass);
+      if (pass) stg[ns + __popc(bal & lt)] = row;
+      ns += __popc(bal);
+    }
+    __syncwarp();
+    const int nb = band_merge(qr, a.X32, a.xid, d, a.metric, k, stg, ns,
+                              reinterpret_cast<int*>(dst), s64[wib], best_r[wib], best_i[wib], 0,
+                              lane);
+    rho = lane < nb ? (float)best_r[wib][lane] : INFINITY;
+    oid = lane < nb ? best_i[wib][lane] : INT32_MAX;
+    brow = 0;
+    tie_mask = 1u << (k - 1);
+  } else {
+    tie_mask = fp64_ties(qr, a.X32, d, d, a.metric, k, a.c_out, eps, lane, rho, oid, brow);
+  }
   if (lane < k) {
     const bool ok = rho != INFINITY && brow >= 0;
     a.out_ids[q * k + lane] = ok ? (int64_t)oid : (int64_t)-1;
@@ -547,117 +661,6 @@ int launch_cw(const SelectArgs& a, int64_t grid_rows, cudaStream_t st) {
   return RBC_OK;
 }
 
-// Grouped search fallback: FP32 brute force of each uncertified row over its
-// own index (rows [row_base, row_base + n) of the grouped FP32 matrix), with
-// the re-rank's distance formula, (rho, id) order and FP64 near-ties, so the
-// row's answer has the same form as every certified row's.  One block per
-// row, rows taken from a device-side list.
-constexpr int GFB_THREADS = 128;
-template <int CW>
-__global__ void __launch_bounds__(GFB_THREADS) group_fallback_kernel(GroupFallbackArgs a) {
-  __shared__ float sh_s[CW][GFB_THREADS];
-  __shared__ int sh_i[CW][GFB_THREADS];
-  __shared__ float sq[MAX_D];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nrows = *a.num_rows_dev;
-  const float eps = rerank_eps(a.d);
-  for (int fi = blockIdx.x; fi < nrows; fi += gridDim.x) {
-    const int p = a.rows[fi];  // padded row of the grouped query buffer
-    const int q = a.qorig[p];
-    const int g = a.tile_index[p / TQ];
-    const int64_t rb = a.row_base[g], n = a.n_of[g];
-    for (int i = tid; i < a.d; i += GFB_THREADS) sq[i] = a.Q32[(int64_t)p * a.d + i];
-    __syncthreads();
-    TopList<CW> lst;
-    lst.init();
-    for (int64_t x = tid; x < n; x += GFB_THREADS) {
-      const int row = (int)(rb + x);
-      const float rho = rerank_rho(sq, a.X32 + (int64_t)row * a.d, a.d, RBC_L2);
-      if (lst.admits(rho, row)) lst.insert(rho, row);
-    }
-#pragma unroll
-    for (int j = 0; j < CW; ++j) {
-      sh_s[j][tid] = lst.s[j];
-      sh_i[j][tid] = lst.i[j];
-    }
-    __syncthreads();
-    if (warp == 0) {
-      // lane l merges the lists of threads l, l + 32, l + 64, l + 96 ...
-      TopList<CW> m;
-      m.init();
-      for (int t = lane; t < GFB_THREADS; t += 32)
-#pragma unroll
-        for (int j = 0; j < CW; ++j)
-          if (sh_i[j][t] != INT32_MAX && m.admits(sh_s[j][t], sh_i[j][t]))
-            m.insert(sh_s[j][t], sh_i[j][t]);
-      __syncwarp();
-#pragma unroll
-      for (int j = 0; j < CW; ++j) {
-        sh_s[j][lane] = m.s[j];
-        sh_i[j][lane] = m.i[j];
-      }
-      __syncwarp();
-      // ... then c_out rounds of a warp minimum over the lists' heads
-      int head = 0;
-      float cs = INFINITY;
-      int ci = INT32_MAX;
-      for (int j = 0; j < a.c_out; ++j) {
-        float bv = head < CW ? sh_s[head][lane] : INFINITY;
-        int bi = head < CW ? sh_i[head][lane] : INT32_MAX;
-        int bl = lane;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-          int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          int ol = __shfl_xor_sync(0xffffffffu, bl, o);
-          if (key_lt(ov, oi, ol, bv, bi, bl)) {
-            bv = ov;
-            bi = oi;
-            bl = ol;
-          }
-        }
-        if (lane == bl) ++head;
-        if (lane == j) {
-          cs = bv;
-          ci = bi;
-        }
-      }
-      const bool valid = lane < a.c_out && ci != INT32_MAX && cs != INFINITY;
-      float rho = valid ? cs : INFINITY;
-      int brow = valid ? ci : -1;
-      int oid = valid ? a.xid[ci] : INT32_MAX;
-      // order by (rho, id) with the database ids
-#pragma unroll
-      for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-          float ov = __shfl_xor_sync(0xffffffffu, rho, stride);
-          int oi = __shfl_xor_sync(0xffffffffu, oid, stride);
-          int ob = __shfl_xor_sync(0xffffffffu, brow, stride);
-          bool up = (lane & size) == 0 || size == 32;
-          bool lower = (lane & stride) == 0;
-          bool other_less = pair_lt(ov, oi, rho, oid);
-          bool take = (lower == up) ? other_less : (!other_less && !(ov == rho && oi == oid));
-          if (take) {
-            rho = ov;
-            oid = oi;
-            brow = ob;
-          }
-        }
-      }
-      const unsigned ties =
-          fp64_ties(sq, a.X32, a.d, a.d, RBC_L2, a.k, a.c_out, eps, lane, rho, oid, brow);
-      if (lane < a.k && q >= 0) {
-        const bool ok = rho != INFINITY && brow >= 0;
-        a.out_ids[(int64_t)q * a.k + lane] = ok ? (int64_t)oid : (int64_t)-1;
-        a.out_dist[(int64_t)q * a.k + lane] = ok ? rho : INFINITY;
-      }
-      if (lane == 0 && ties && a.counters) atomicAdd(&a.counters[1], 1);
-    }
-    __syncthreads();
-  }
-}
-
 // Queries whose survivors (candidates scoring <= score_bound(U)) outnumber
 // the shared-memory re-rank: one warp per query streams every survivor
 // through the FP32 re-rank -- the k-th score in one pass over the buffer,
@@ -672,10 +675,15 @@ __global__ void __launch_bounds__(WARPS * 32) select_stream_kernel(CandSelectArg
   __shared__ int s_row[WARPS][BATCH];
   __shared__ float s_rho[WARPS][BATCH];
   __shared__ int s_id[WARPS][BATCH];
+  __shared__ int s_band[WARPS][RERANK_MAX];
+  __shared__ double s_b64[WARPS][RERANK_MAX];
+  __shared__ double s_best_r[WARPS][32];
+  __shared__ int s_best_i[WARPS][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int* srow = s_row[wib];
   float* srho = s_rho[wib];
   int* sid = s_id[wib];
+  int* sband = s_band[wib];
   const int64_t nw = *a.stream_count;
   const int k = a.k, d = a.d;
   const float xe = __uint_as_float(*a.x_err_max_bits), xn = __uint_as_float(*a.x_norm_max_bits);
@@ -781,8 +789,51 @@ __global__ void __launch_bounds__(WARPS * 32) select_stream_kernel(CandSelectArg
       }
     }
     const float eps = rerank_eps(d);
-    const unsigned tie_mask = fp64_ties(qr, a.X32, d, d, a.metric, k, a.c_out, eps, lane, rho,
-                                        oid, brow);
+    // a candidate past rank k - 1 within the band of the k-th place: a
+    // second pass over the survivors collects those in the band, batch by
+    // batch, and merges them into the FP64 (rho, id) order
+    const float band = kth_band(__shfl_sync(0xffffffffu, rho, k - 1), eps);
+    unsigned tie_mask;
+    if (__shfl_sync(0xffffffffu, rho, k) <= band) {
+      int nbest = 0;
+      for (int b0 = 0; b0 < cnt; b0 += BATCH) {
+        const int b1 = min(cnt, b0 + BATCH);
+        int nb = 0;
+        for (int e0 = b0; e0 < b1; e0 += 32) {
+          const int e = e0 + lane;
+          const bool pass = e < b1 && sc[e] <= smax;
+          const unsigned bal = __ballot_sync(0xffffffffu, pass);
+          if (pass) srow[nb + __popc(bal & lt)] = cr[e];
+          nb += __popc(bal);
+        }
+        __syncwarp();
+        for (int e0 = 0; e0 < nb; e0 += 4) {
+          const int e = e0 + (lane >> 3);
+          const int row = srow[e < nb ? e : 0];
+          const float v = rerank_rho8(qr, a.X32 + (int64_t)row * d, d, a.metric, lane & 7);
+          if ((lane & 7) == 0 && e < nb) srho[e] = v;
+        }
+        __syncwarp();
+        int ns = 0;
+        for (int e0 = 0; e0 < nb; e0 += 32) {
+          const int e = e0 + lane;
+          const bool pass = e < nb && srho[e] <= band;
+          const unsigned bal = __ballot_sync(0xffffffffu, pass);
+          if (pass) sband[ns + __popc(bal & lt)] = srow[e];
+          ns += __popc(bal);
+        }
+        __syncwarp();
+        if (ns > 0)
+          nbest = band_merge(qr, a.X32, a.xid, d, a.metric, k, sband, ns, sid, s_b64[wib],
+                             s_best_r[wib], s_best_i[wib], nbest, lane);
+      }
+      rho = lane < nbest ? (float)s_best_r[wib][lane] : INFINITY;
+      oid = lane < nbest ? s_best_i[wib][lane] : INT32_MAX;
+      brow = 0;
+      tie_mask = 1u << (k - 1);
+    } else {
+      tie_mask = fp64_ties(qr, a.X32, d, d, a.metric, k, a.c_out, eps, lane, rho, oid, brow);
+    }
     if (lane < k) {
       const bool ok = rho != INFINITY && brow >= 0;
       a.out_ids[q * k + lane] = ok ? (int64_t)oid : (int64_t)-1;
@@ -813,22 +864,6 @@ int launch_select_stream(const CandSelectArgs& a, int max_rows, cudaStream_t st)
   else
     select_stream_kernel<32><<<grid, WARPS * 32, 0, st>>>(a);
   RBC_LAUNCH_CHECK("select_stream_kernel");
-  return RBC_OK;
-}
-
-int launch_group_fallback(const GroupFallbackArgs& a, int grid, cudaStream_t st) {
-  if (a.k < 1 || a.c_out < a.k || a.c_out > 32 || a.d > MAX_D) {
-    set_error("group fallback: bad k=%d c_out=%d d=%d", a.k, a.c_out, a.d);
-    return RBC_ERR_ARG;
-  }
-  if (grid <= 0) return RBC_OK;
-  if (a.c_out <= 8)
-    group_fallback_kernel<8><<<grid, GFB_THREADS, 0, st>>>(a);
-  else if (a.c_out <= 16)
-    group_fallback_kernel<16><<<grid, GFB_THREADS, 0, st>>>(a);
-  else
-    group_fallback_kernel<32><<<grid, GFB_THREADS, 0, st>>>(a);
-  RBC_LAUNCH_CHECK("group_fallback_kernel");
   return RBC_OK;
 }
 
