@@ -38,6 +38,8 @@
 // Every wait on an mbarrier is bounded; on expiry the kernel raises
 // DEV_ERR_TIMEOUT, stops issuing work, waits (bounded) for its own copies and
 // frees its tensor memory before returning.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "tc_common.cuh"
@@ -59,9 +61,22 @@ struct TopParams {
   uint32_t* dev_err;
 };
 
+// Item `item` of the work.  Paired (cluster) dense form: item = (pair of
+// query tiles, split), and CTA `rank` of the cluster takes tile 2 pair + rank
+// (nq <= 0 for the missing partner of an odd last tile).
+template <bool MC = false>
 __device__ __forceinline__ void top_item(const TileWork& w, int item, int& q0, int& nq, int& sb,
-                                         int& se, int& slot) {
-  if (w.items) {
+                                         int& se, int& slot, int rank = 0) {
+  if (MC) {
+    const int pair = item / w.dense_splits;
+    const int s = item - pair * w.dense_splits;
+    const int tile = 2 * pair + rank;
+    q0 = tile * TQ;
+    nq = (int)min((int64_t)TQ, w.m - (int64_t)q0);
+    sb = s;
+    se = s + 1;
+    slot = tile * w.dense_splits + s;
+  } else if (w.items) {
     const WorkItem it = w.items[item];
     q0 = it.q_row0;
     nq = it.nq;
@@ -140,6 +155,36 @@ __device__ __forceinline__ uint64_t top_desc_sw32(uint32_t addr) {
   return d;
 }
 
+// Cluster helpers for the paired dense pass: the two CTAs of a cluster
+// multiply different query tiles by the same database tiles, and each loads
+// half of every database tile into both CTAs' shared memory (TMA multicast
+// within this GPU's memory), which halves the L2 traffic per SM.
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                               int c0, int c1, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+// arrive on the same mbarrier in every CTA of `mask` when this CTA's MMAs end
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
 // r[j] for a run-time j < 32: a five-level tree of selects on the bits of j
 // (the rare path's way to read a register array without local memory).
 __device__ __forceinline__ uint32_t pick32(const uint32_t (&r)[32], int j) {
@@ -169,8 +214,9 @@ __device__ __forceinline__ uint32_t acc_above_mask(const uint32_t (&r)[32], floa
 
 // CS: list entries per (row, column half); KB: 64-column K blocks; BN:
 // database rows per tile; S: database stages; QS: query-tile stages; PQ:
-// pending inserts per epilogue thread.
-template <int CS, int KB, int BN, int S, int QS, int PQ>
+// pending inserts per epilogue thread; MC: paired dense pass on a cluster of
+// two CTAs sharing the database tiles by multicast.
+template <int CS, int KB, int BN, int S, int QS, int PQ, bool MC>
 __global__ void __launch_bounds__(T_THREADS, 1)
 bf_tc_top_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap xmap,
                  const __grid_constant__ CUtensorMap nbmap, TopParams p, uint32_t idesc,
@@ -178,6 +224,8 @@ bf_tc_top_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant
   using L = TopSmem<CS, KB, BN, S, QS, PQ>;
   constexpr int NBUF = L::NBUF;
   constexpr int NG = CS / 4;  // list groups of four entries
+  static_assert(!MC || BN % 16 == 0, "paired tiles split in two halves of 8-row groups");
+  const int rank = MC ? (int)cluster_rank() : 0;
   constexpr int COLS = BN / 2;     // columns per epilogue thread per tile
   constexpr int CH = COLS / 32;    // 32-column TMEM loads per thread per tile
   constexpr int RC = CH < 2 ? CH : 2;  // loads per round
@@ -209,7 +257,7 @@ bf_tc_top_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], MC ? 2 : 1);  // paired: both CTAs' MMAs must be done with a stage
     }
     for (int b = 0; b < NBUF; ++b) {
       mbar_init(&tfull[b], 1);
@@ -238,6 +286,8 @@ bf_tc_top_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  // paired: the partner's barriers are initialised before any multicast
+  if (MC) cluster_sync();
   const uint32_t tmem = *sTmem;
 
   const TileWork& w = p.w;
@@ -245,9 +295,12 @@ bf_tc_top_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant
   // a contiguous range of items per CTA, so that consecutive items of one
   // query tile stay on one CTA and the epilogue carries its lists across
   // them; work whose query tiles are single items may take them strided
-  const int ib = w.strided ? (int)blockIdx.x : (int)((int64_t)blockIdx.x * n_items / gridDim.x);
-  const int ie = w.strided ? n_items : (int)((int64_t)(blockIdx.x + 1) * n_items / gridDim.x);
-  const int istep = w.strided ? (int)gridDim.x : 1;
+  // paired: the cluster's two CTAs take the same range of (pair, split) items
+  const int cid = MC ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int ncta = MC ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  const int ib = w.strided ? cid : (int)((int64_t)cid * n_items / ncta);
+  const int ie = w.strided ? n_items : (int)((int64_t)(cid + 1) * n_items / ncta);
+  const int istep = w.strided ? ncta : 1;
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -255,7 +308,7 @@ bf_tc_top_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant
     bool ok = true;
     for (int item = ib; ok && item < ie; item += istep, ++qi) {
       int q0, nq, sb, se, slot;
-      top_item(w, item, q0, nq, sb, se, slot);
+      top_item<MC>(w, item, q0, nq, sb, se, slot, rank);
       const int kbn = top_item_kb<KB>(w, item);
       const int qs = qi % QS;
       if (!__all_sync(0xffffffffu,
@@ -281,11 +334,23 @@ bf_tc_top_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant
           }
           if (lane == 0) {
             mbar_arrive_expect_tx(&full[s], kbn * BN * 128 + L::NB_STAGE);
+            if (MC) {
+              // this CTA's half of the tile (rows rank * BN / 2 ...), into both CTAs
+              constexpr int HB = BN / 2;
 #pragma unroll
-            for (int kb = 0; kb < KB; ++kb)
-              if (kb < kbn)
-                tma_load_2d(sX + s * L::X_STAGE + kb * BN * 128, &xmap, &full[s], kb * 64, x);
-            tma_load_2d(sNB + s * L::NB_STAGE, &nbmap, &full[s], 0, x);
+              for (int kb = 0; kb < KB; ++kb)
+                if (kb < kbn)
+                  tma_load_2d_mc(sX + s * L::X_STAGE + kb * BN * 128 + rank * HB * 128, &xmap,
+                                 &full[s], kb * 64, x + rank * HB, (uint16_t)3);
+              tma_load_2d_mc(sNB + s * L::NB_STAGE + rank * HB * NBLOCK_COLS * 2, &nbmap, &full[s],
+                             0, x + rank * HB, (uint16_t)3);
+            } else {
+#pragma unroll
+              for (int kb = 0; kb < KB; ++kb)
+                if (kb < kbn)
+                  tma_load_2d(sX + s * L::X_STAGE + kb * BN * 128, &xmap, &full[s], kb * 64, x);
+              tma_load_2d(sNB + s * L::NB_STAGE, &nbmap, &full[s], 0, x);
+            }
           }
           __syncwarp();
         }
@@ -304,7 +369,7 @@ bf_tc_top_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant
     bool ok = true;
     for (int item = ib; ok && item < ie; item += istep, ++qi) {
       int q0, nq, sb, se, slot;
-      top_item(w, item, q0, nq, sb, se, slot);
+      top_item<MC>(w, item, q0, nq, sb, se, slot, rank);
       const int kbn = top_item_kb<KB>(w, item);
       const int qs = qi % QS;
       if (!__all_sync(0xffffffffu, mbar_wait(&qfull[qs], (qi / QS) & 1, sAbort, p.dev_err))) {
@@ -341,7 +406,10 @@ bf_tc_top_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant
             // + (-|x~|^2 / 2) in every row: ones x norm block (bf16, K = 16)
             mma_f16(d_tmem, top_desc_sw32(smem_u32(sOnes)),
                     top_desc_sw32(smem_u32(sNB + s * L::NB_STAGE)), idesc_norm, 1u);
-            mma_commit(&empty[s]);
+            if (MC)
+              mma_commit_mc(&empty[s], (uint16_t)3);  // the stage is free in both CTAs
+            else
+              mma_commit(&empty[s]);
             mma_commit(&tfull[buf]);
           }
           __syncwarp();
@@ -424,11 +492,11 @@ bf_tc_top_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant
     };
     for (int item = ib; ok && item < ie; item += istep) {
       int q0, nq, sb, se, slot;
-      top_item(w, item, q0, nq, sb, se, slot);
+      top_item<MC>(w, item, q0, nq, sb, se, slot, rank);
       int pq0 = -1, pnq, psb, pse, pslot;
-      if (item - istep >= ib) top_item(w, item - istep, pq0, pnq, psb, pse, pslot);
+      if (item - istep >= ib) top_item<MC>(w, item - istep, pq0, pnq, psb, pse, pslot, rank);
       int nq0 = -1, nnq, nsb, nse, nslot;
-      if (item + istep < ie) top_item(w, item + istep, nq0, nnq, nsb, nse, nslot);
+      if (item + istep < ie) top_item<MC>(w, item + istep, nq0, nnq, nsb, nse, nslot, rank);
       if (pq0 != q0) {  // the first item of a run of one query tile: empty lists
 #pragma unroll
         for (int j = 0; j < CS; ++j) {
@@ -528,7 +596,8 @@ bf_tc_top_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant
         }
       }
       const bool carry = nq0 == q0;  // the next item continues this tile's lists
-      if (p.out.slot_valid && threadIdx.x == T_EPI0 * 32) p.out.slot_valid[slot] = carry ? 0 : 1;
+      if (p.out.slot_valid && threadIdx.x == T_EPI0 * 32 && nq > 0)
+        p.out.slot_valid[slot] = carry ? 0 : 1;
       if (!carry) {
         while (npend > 0) {
           --npend;
@@ -550,6 +619,9 @@ bf_tc_top_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant
 
   tc_fence_before();
   __syncthreads();
+  // paired: no CTA leaves while its partner may still multicast into it or
+  // arrive on its barriers (both have drained their own copies by now)
+  if (MC) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NBUF * BN)
@@ -557,31 +629,75 @@ bf_tc_top_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant
   }
 }
 
-template <int CS, int KB, int BN, int S, int QS, int PQ>
+template <int CS, int KB, int BN, int S, int QS, int PQ, bool MC>
 int launch_top(const LpMatrix& Qm, const LpMatrix& Xm, const TileWork& w, const TopOut& out,
                int grid, cudaStream_t st, uint32_t* dev_err) {
   using L = TopSmem<CS, KB, BN, S, QS, PQ>;
+  // paired: each CTA loads half of every database tile (and of its norm block)
+  constexpr int XBOX = MC ? BN / 2 : BN;
   CUtensorMap qmap, xmap, nbmap;
   RBC_TRY_TC(encode_map(&qmap, Qm.data, Qm.rows, Qm.dpad, Qm.storage, BM));
-  RBC_TRY_TC(encode_map(&xmap, Xm.data, Xm.rows, Xm.dpad, Xm.storage, BN));
-  RBC_TRY_TC(encode_nblock_map(&nbmap, Xm.nblock, Xm.rows, BN));
-  auto kern = bf_tc_top_kernel<CS, KB, BN, S, QS, PQ>;
+  RBC_TRY_TC(encode_map(&xmap, Xm.data, Xm.rows, Xm.dpad, Xm.storage, XBOX));
+  RBC_TRY_TC(encode_nblock_map(&nbmap, Xm.nblock, Xm.rows, XBOX));
+  auto kern = bf_tc_top_kernel<CS, KB, BN, S, QS, PQ, MC>;
   RBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC));
   TopParams p{w, out, dev_err};
   const uint32_t idesc = idesc_f16(Qm.storage == RBC_BF16 ? 1 : 0, BM, BN);
   const uint32_t idesc_norm = idesc_f16(1, BM, BN);  // the norm block is bf16 for any storage
-  kern<<<grid, T_THREADS, L::ALLOC, st>>>(qmap, xmap, nbmap, p, idesc, idesc_norm);
+  cudaError_t e;
+  if (MC) {
+    // items are (pair of query tiles, split); one cluster of two CTAs per
+    // item range, as many clusters as fit on the GPU at once
+    const int64_t tiles = (w.m + TQ - 1) / TQ;
+    p.w.num_items = (int)(((tiles + 1) / 2) * w.dense_splits);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(T_THREADS);
+    cfg.dynamicSmemBytes = L::ALLOC;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(2 * ((grid + 1) / 2));
+    int max_clusters = 0;
+    RBC_CUDA(cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg));
+    if (max_clusters < 1) {
+      set_error("tensor-core BF: no cluster of two CTAs fits (%d bytes of shared memory each)",
+                L::ALLOC);
+      return RBC_ERR_UNSUPPORTED;
+    }
+    const int clusters = (int)std::min<int64_t>(max_clusters, std::max(1, p.w.num_items));
+    cfg.gridDim = dim3(2 * clusters);
+    e = cudaLaunchKernelEx(&cfg, kern, qmap, xmap, nbmap, p, idesc, idesc_norm);
+  } else {
+    kern<<<grid, T_THREADS, L::ALLOC, st>>>(qmap, xmap, nbmap, p, idesc, idesc_norm);
+    e = cudaGetLastError();
+  }
   ++t_launches;
-  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     cudaFuncAttributes fa{};
     cudaFuncGetAttributes(&fa, kern);
-    set_error("bf_tc_top_kernel<CS=%d,KB=%d,BN=%d,S=%d> launch failed: %s (regs %d, local %zu, "
-              "dynamic smem %d)",
-              CS, KB, BN, S, cudaGetErrorString(e), fa.numRegs, fa.localSizeBytes, L::ALLOC);
+    set_error("bf_tc_top_kernel<CS=%d,KB=%d,BN=%d,S=%d,MC=%d> launch failed: %s (regs %d, local "
+              "%zu, dynamic smem %d)",
+              CS, KB, BN, S, (int)MC, cudaGetErrorString(e), fa.numRegs, fa.localSizeBytes,
+              L::ALLOC);
     return RBC_ERR_CUDA;
   }
   return RBC_OK;
+}
+
+template <int CS, int KB, int BN, int S, int QS, int PQ>
+int launch_top2(const LpMatrix& Qm, const LpMatrix& Xm, const TileWork& w, const TopOut& out,
+                int grid, cudaStream_t st, uint32_t* dev_err) {
+  // the dense form (every query tile against the same database ranges) runs
+  // paired on clusters of two; work lists run one CTA per item range
+  if (!w.items && !w.segs)
+    return launch_top<CS, KB, BN, S, QS, PQ, true>(Qm, Xm, w, out, grid, st, dev_err);
+  return launch_top<CS, KB, BN, S, QS, PQ, false>(Qm, Xm, w, out, grid, st, dev_err);
 }
 
 template <int CS>
@@ -592,10 +708,10 @@ int dispatch_kb(const LpMatrix& Qm, const LpMatrix& Xm, const TileWork& w, const
   // stages so that the stages, lists and pending stacks fit in shared memory
   constexpr bool WIDE = CS > 16;
   switch (Qm.dpad / 64) {
-    case 1: return launch_top<CS, 1, 256, WIDE ? 2 : 3, 2, 8>(Qm, Xm, w, out, grid, st, dev_err);
-    case 2: return launch_top<CS, 2, WIDE ? 128 : 256, 2, 1, WIDE ? 8 : 4>(Qm, Xm, w, out, grid, st, dev_err);
-    case 3: return launch_top<CS, 3, WIDE ? 64 : 128, 2, 1, 8>(Qm, Xm, w, out, grid, st, dev_err);
-    case 4: return launch_top<CS, 4, 64, 2, 1, 8>(Qm, Xm, w, out, grid, st, dev_err);
+    case 1: return launch_top2<CS, 1, 256, WIDE ? 2 : 3, 2, 8>(Qm, Xm, w, out, grid, st, dev_err);
+    case 2: return launch_top2<CS, 2, WIDE ? 128 : 256, 2, 1, WIDE ? 8 : 4>(Qm, Xm, w, out, grid, st, dev_err);
+    case 3: return launch_top2<CS, 3, WIDE ? 64 : 128, 2, 1, 8>(Qm, Xm, w, out, grid, st, dev_err);
+    case 4: return launch_top2<CS, 4, 64, 2, 1, 8>(Qm, Xm, w, out, grid, st, dev_err);
     default: break;
   }
   set_error("tensor-core BF: padded dimension %d unsupported", Qm.dpad);
