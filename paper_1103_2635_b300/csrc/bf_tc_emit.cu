@@ -448,9 +448,6 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
           if (!(c * 32 < hi && c * 32 + 32 > lo)) continue;  // no window column in the chunk
-          float u[32];  // -s / 2 per column
-#pragma unroll
-          for (int j = 0; j < 32; ++j) u[j] = __uint_as_float(raw[c][j]);
           // The maximum runs over all 32 columns, including any outside the
           // window (real rows, or zero rows past the matrix end): a false
           // alarm only costs the slow path, where the in-window mask decides.
@@ -461,31 +458,30 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
             const uint32_t below_hi = chi >= 32 ? 0xffffffffu : (chi <= 0 ? 0u : (1u << chi) - 1u);
             const uint32_t below_lo = clo >= 32 ? 0xffffffffu : (clo <= 0 ? 0u : (1u << clo) - 1u);
             const uint32_t valid = below_hi & ~below_lo;
+            // the set bits of the hit mask, one by one (compact code: the
+            // common path stays small in the instruction cache)
+            uint32_t mask = valid & over_mask32<true>(raw[c], myT);
             if (!DIRECT) {
-#pragma unroll
-              for (int j = 0; j < 32; ++j) {
-                if (((valid >> j) & 1u) && u[j] >= myT) {
-                  if (nhits < lsub)
-                    hits[nhits] = make_int4(myq, cb + j, __float_as_int(-2.0f * u[j]), 0);
-                  ++nhits;
-                }
+              while (mask) {
+                const int j = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const float v = __uint_as_float(pick32(raw[c], j));
+                if (nhits < lsub) hits[nhits] = make_int4(myq, cb + j, __float_as_int(-2.0f * v), 0);
+                ++nhits;
               }
             } else {
               // direct appends: one atomic per (lane, chunk) reserves the
               // row's slots, then the hits fill them in column order
-              int nh = 0;
-#pragma unroll
-              for (int j = 0; j < 32; ++j) nh += (((valid >> j) & 1u) && u[j] >= myT) ? 1 : 0;
-              int pos = atomicAdd(cc, nh);
-#pragma unroll
-              for (int j = 0; j < 32; ++j) {
-                if (((valid >> j) & 1u) && u[j] >= myT) {
-                  if (pos < cap) {
-                    cs[pos] = -2.0f * u[j];
-                    cr[pos] = cb + j;
-                  }
-                  ++pos;
+              int pos = atomicAdd(cc, __popc(mask));
+              while (mask) {
+                const int j = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const float v = __uint_as_float(pick32(raw[c], j));
+                if (pos < cap) {
+                  cs[pos] = -2.0f * v;
+                  cr[pos] = cb + j;
                 }
+                ++pos;
               }
             }
           }

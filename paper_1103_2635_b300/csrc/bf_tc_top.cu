@@ -185,33 +185,6 @@ __device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
       : "memory");
 }
 
-// r[j] for a run-time j < 32: a five-level tree of selects on the bits of j
-// (the rare path's way to read a register array without local memory).
-__device__ __forceinline__ uint32_t pick32(const uint32_t (&r)[32], int j) {
-  uint32_t a[16], b[8], c[4], d[2];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) a[i] = (j & 1) ? r[2 * i + 1] : r[2 * i];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) b[i] = (j & 2) ? a[2 * i + 1] : a[2 * i];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) c[i] = (j & 4) ? b[2 * i + 1] : b[2 * i];
-#pragma unroll
-  for (int i = 0; i < 2; ++i) d[i] = (j & 8) ? c[2 * i + 1] : c[2 * i];
-  return (j & 16) ? d[1] : d[0];
-}
-
-// Bit j set iff the accumulator bits r[j] hold a value above t.
-__device__ __forceinline__ uint32_t acc_above_mask(const uint32_t (&r)[32], float t) {
-  uint32_t g[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q)
-    g[q] = (__uint_as_float(r[4 * q]) > t ? 1u : 0u) | (__uint_as_float(r[4 * q + 1]) > t ? 2u : 0u) |
-           (__uint_as_float(r[4 * q + 2]) > t ? 4u : 0u) |
-           (__uint_as_float(r[4 * q + 3]) > t ? 8u : 0u);
-  return (g[0] | (g[1] << 4) | (g[2] << 8) | (g[3] << 12)) |
-         ((g[4] | (g[5] << 4) | (g[6] << 8) | (g[7] << 12)) << 16);
-}
-
 // CS: list entries per (row, column half); KB: 64-column K blocks; BN:
 // database rows per tile; S: database stages; QS: query-tile stages; PQ:
 // pending inserts per epilogue thread; MC: paired dense pass on a cluster of
@@ -578,7 +551,7 @@ bf_tc_top_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant
               if (chi <= 0 || clo >= 32) continue;
               const uint32_t below_hi = chi >= 32 ? 0xffffffffu : (1u << chi) - 1u;
               const uint32_t below_lo = clo <= 0 ? 0u : (1u << clo) - 1u;
-              uint32_t mask = below_hi & ~below_lo & acc_above_mask(raw[c], -0.5f * tau);
+              uint32_t mask = below_hi & ~below_lo & over_mask32<false>(raw[c], -0.5f * tau);
               while (mask) {
                 const int j = __ffs(mask) - 1;
                 mask &= mask - 1;

@@ -273,6 +273,40 @@ __device__ __forceinline__ uint32_t eq_mask(const float (&v)[C], float x) {
   return m;
 }
 
+// r[j] for a run-time j < 32: a five-level tree of selects on the bits of j
+// (a rare path's way to read one of 32 registers without local memory, in a
+// few instructions of code).
+__device__ __forceinline__ uint32_t pick32(const uint32_t (&r)[32], int j) {
+  uint32_t a[16], b[8], c[4], d[2];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i] = (j & 1) ? r[2 * i + 1] : r[2 * i];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) b[i] = (j & 2) ? a[2 * i + 1] : a[2 * i];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) c[i] = (j & 4) ? b[2 * i + 1] : b[2 * i];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) d[i] = (j & 8) ? c[2 * i + 1] : c[2 * i];
+  return (j & 16) ? d[1] : d[0];
+}
+
+// Bit j set iff the float bits r[j] hold a value above t (GE: at least t).
+template <bool GE>
+__device__ __forceinline__ uint32_t over_mask32(const uint32_t (&r)[32], float t) {
+  uint32_t g[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float v = __uint_as_float(r[4 * q + i]);
+      m |= (GE ? v >= t : v > t) ? (1u << i) : 0u;
+    }
+    g[q] = m;
+  }
+  return (g[0] | (g[1] << 4) | (g[2] << 8) | (g[3] << 12)) |
+         ((g[4] | (g[5] << 4) | (g[6] << 8) | (g[7] << 12)) << 16);
+}
+
 // Bit j set iff u[j] < t, for a 32-column chunk.
 __device__ __forceinline__ uint32_t hit_mask32(const float (&u)[32], float t) {
   uint32_t g[8];
