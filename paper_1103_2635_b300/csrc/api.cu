@@ -1222,6 +1222,25 @@ int own_list_bound(const rbc_index* ix, const float* Qb, int64_t mb, const int64
                            rerank_eps_host(ix->d) + 8.0f * U32, own, st);
 }
 
+// The same bound from the FP32 CUDA-core top-C pass (FP32 storage or l1):
+// the k best FP32 values of q inside its nearest representative's list,
+// re-ranked, the largest of them rounded up.
+int own_list_bound_f32(const rbc_index* ix, const float* Qb, int64_t mb, const int64_t* nearest,
+                       int k, float* own, Arena& ar, cudaStream_t st) {
+  Grouped gq;
+  RBC_TRY(group_queries(ix, Qb, mb, nearest, nullptr, ix->offsets, nullptr, gq, ar, st, true));
+  const int C = k <= 8 ? 8 : (k <= 16 ? 16 : 32);
+  float* ps;
+  int* pi;
+  RBC_TRY(ar.alloc(&ps, gq.max_tiles * TQ * 2 * C));
+  RBC_TRY(ar.alloc(&pi, gq.max_tiles * TQ * 2 * C));
+  const int sms = sm_count();
+  RBC_TRY(launch_bf_simt_topc(gq.Qp, ix->X32, ix->d, ix->metric, C, gq.w, TopOut{ps, pi, nullptr},
+                              (int)std::min<int64_t>(gq.max_tiles, (int64_t)sms * 2 * 8), st));
+  return launch_own_kth_lp(ps, pi, C, gq.qsrc, gq.rows_cap, k, Qb, ix->X32, ix->d, ix->metric,
+                           rerank_eps_host(ix->d) + 8.0f * U32, own, st);
+}
+
 int oneshot_stage2(const rbc_index* ix, const float* Qsrc, int64_t mq, const int64_t* rep_of,
                    const int* orig, bool lp, int k, int64_t* ids, float* dist, int* cnt,
                    unsigned long long* points_sum, int64_t* items_total, Arena& ar,
@@ -1408,13 +1427,21 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   uint32_t* dev_err;
   RBC_TRY(ar.alloc(&dev_err, 1));
   RBC_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(uint32_t), st));
+  // bf16 / fp16 storage with l2: tensor-core passes on the low-precision rows;
+  // otherwise (FP32 storage, l1) the same plan on the CUDA cores in FP32
+  const bool lp = uses_lp(ix->storage, ix->metric) && ix->Xlp != nullptr;
+  const int metric = ix->metric;
+  const float f32_eps = simt_eps(d);
   // low-precision copy of the batch (pass A and the emission pass)
   LpQueries ql;
-  RBC_TRY(lp_queries(Qb, mb, d, ix->dpad, ix->storage, ql, ar, st));
+  if (lp) RBC_TRY(lp_queries(Qb, mb, d, ix->dpad, ix->storage, ql, ar, st));
   // pass A: the k-th distance inside the nearest representative's own list
   float* own;
   RBC_TRY(ar.alloc(&own, mb));
-  RBC_TRY(own_list_bound(ix, Qb, mb, nearest, ql, k, own, dev_err, ar, st));
+  if (lp)
+    RBC_TRY(own_list_bound(ix, Qb, mb, nearest, ql, k, own, dev_err, ar, st));
+  else
+    RBC_TRY(own_list_bound_f32(ix, Qb, mb, nearest, k, own, ar, st));
   float* g;
   RBC_TRY(ar.alloc(&g, mb));
   RBC_TRY(launch_gbound(own, gk, mb, simt_eps(d), g, st));
@@ -1440,7 +1467,7 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   // score thresholds of the queries
   float* thr;
   RBC_TRY(ar.alloc(&thr, mb));
-  RBC_TRY(launch_score_threshold(g, ql.norm, ql.err, ix->lp_max, d, mb, thr, st));
+  RBC_TRY(launch_score_threshold(g, ql.norm, ql.err, ix->lp_max, d, mb, thr, st, f32_eps, metric));
   int2* pairs;  // (query, rho(q, r) bits)
   RBC_TRY(ar.alloc(&pairs, pair_cap));
   RBC_TRY(launch_window_pairs_scatter(D, mb, n_r, g, g1, ix->psi, simt_eps(d), rmin, rmax, counts,
@@ -1478,9 +1505,14 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   const int arena_seg = arena_lane * 32 * ARENA_SUBSEG;  // per CTA
   int4* arena;
   int *arena_cnt, *arena_ovf;
-  RBC_TRY(ar.alloc(&arena, (int64_t)sms * arena_seg));
-  RBC_TRY(ar.alloc(&arena_cnt, nslices));
-  RBC_CUDA(cudaMemsetAsync(arena_cnt, 0, nslices * sizeof(int), st));
+  if (lp) {
+    RBC_TRY(ar.alloc(&arena, (int64_t)sms * arena_seg));
+    RBC_TRY(ar.alloc(&arena_cnt, nslices));
+    RBC_CUDA(cudaMemsetAsync(arena_cnt, 0, nslices * sizeof(int), st));
+  } else {
+    arena = nullptr;
+    arena_cnt = nullptr;
+  }
   RBC_TRY(ar.alloc(&arena_ovf, 1));
   int* fb_rows;
   int *lc, *lc2, *fb2, *srows, *srows2;
@@ -1520,8 +1552,11 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   a.counters = lc;
   a.stream_rows = srows;
   a.stream_count = lc + 4;
-  int left = ix->emit_direct_left.load(std::memory_order_relaxed);
-  bool skip_arena = false;
+  a.f32 = lp ? 0 : 1;
+  a.f32_eps = f32_eps;
+  // the CUDA-core emission appends to the per-query buffers directly
+  int left = lp ? ix->emit_direct_left.load(std::memory_order_relaxed) : 0;
+  bool skip_arena = !lp;
   while (left > 0 && !skip_arena) {
     skip_arena = const_cast<rbc_index*>(ix)->emit_direct_left.compare_exchange_weak(left, left - 1);
   }
@@ -1540,9 +1575,13 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
       eo_arena.arena_ovf = arena_ovf;
     }
     tmark(1, st);
-    RBC_TRY(launch_bf_tc_emit(Qm, Xm, items, choff + n_r, max_items,
-                              reinterpret_cast<const int*>(pairs), 2, eo_arena, sms, st, dev_err,
-                              ix->norm_fold_col));
+    if (lp)
+      RBC_TRY(launch_bf_tc_emit(Qm, Xm, items, choff + n_r, max_items,
+                                reinterpret_cast<const int*>(pairs), 2, eo_arena, sms, st, dev_err,
+                                ix->norm_fold_col));
+    else
+      RBC_TRY(launch_bf_simt_emit(Qb, ix->X32, d, metric, items, choff + n_r, max_items,
+                                  reinterpret_cast<const int*>(pairs), 2, eo, 2 * sms, st));
     if (!direct)
       RBC_TRY(launch_scatter_hits(arena, arena_lane, arena_cnt, (int)nslices, cs, cr, cc,
                                   CAND_CAP, st));
@@ -1589,10 +1628,14 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
     // stored candidates give a much tighter threshold; emit again for them
     // alone against the whole list storage (direct appends) and finish them.
     RBC_TRY(launch_overflow_rethreshold(fb_rows, lc, mb, cs, cc, CAND_CAP, k, ql.norm, ql.err,
-                                        ix->lp_max, d, thr, st));
+                                        ix->lp_max, d, thr, st, f32_eps, metric));
     RBC_TRY(launch_dense_emit_items(lc, n, xspan, max2, items2, n_items2, st));
-    RBC_TRY(launch_bf_tc_emit(Qm, Xm, items2, n_items2, max2, fb_rows, 1, eo, sms, st, dev_err,
-                              ix->norm_fold_col));
+    if (lp)
+      RBC_TRY(launch_bf_tc_emit(Qm, Xm, items2, n_items2, max2, fb_rows, 1, eo, sms, st, dev_err,
+                                ix->norm_fold_col));
+    else
+      RBC_TRY(launch_bf_simt_emit(Qb, ix->X32, d, metric, items2, n_items2, max2, fb_rows, 1, eo,
+                                  2 * sms, st));
     CandSelectArgs a2 = a;
     a2.rows = fb_rows;
     a2.nrows_dev = lc;
@@ -1680,7 +1723,9 @@ int64_t bound_window_batch(const rbc_index* ix, int64_t mb, int k) {
   int64_t b = mb * n_r * 4;                                  // D
   b += mb * 16 + 4;                                          // g1, gk, nearest, dev_err
   b += mb * ((int64_t)dpad * 2 + 12);                         // low-precision batch
-  b += bound_own_list(ix, mb);                               // pass A
+  b += bound_own_list(ix, mb);                               // pass A (tensor cores)
+  b += bound_group(ix, mb, true) + cdiv(mb, TQ) * TQ * 2 * MAX_C * 8 +
+       std::min<int64_t>(ix->n_r, mb) * TQ * 2 * MAX_C * 8;  // pass A (CUDA cores)
   b += mb * 4 + n_r * 8 + mb * 4;                            // g, rmin, rmax, qkept
   b += window_pair_blocks(mb) * nbins * 4 + nbins * 8 + 4;   // bin counts, totals, offsets
   b += ((int64_t)exclusive_scan_scratch_ints((int)nbins)) * 4; // their scan
@@ -1750,8 +1795,10 @@ int64_t search_batch_size(const rbc_index* ix, bool window) {
 // row maxima, which needs one scale per row: FP8 (a scale per column too)
 // takes the tile-union plan
 bool search_uses_window(const rbc_index* ix) {
-  return ix->mode == RBC_EXACT && ix->plan == RBC_PLAN_WINDOW && uses_lp(ix->storage, ix->metric) &&
-         ix->Xlp && ix->storage != RBC_FP8E4M3;
+  if (ix->mode != RBC_EXACT || ix->plan != RBC_PLAN_WINDOW) return false;
+  // FP32 storage or l1: the windowed plan on the CUDA cores
+  if (!uses_lp(ix->storage, ix->metric)) return true;
+  return ix->Xlp && ix->storage != RBC_FP8E4M3;
 }
 
 int64_t search_workspace_bound(const rbc_index* ix, int64_t m, int k) {

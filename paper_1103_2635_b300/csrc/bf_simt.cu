@@ -210,6 +210,110 @@ int dispatch_c(int C, const float* Q, const float* X, int d, const TileWork& w, 
   }
 }
 
+// Windowed stage two on CUDA cores (FP32 storage or the l1 metric): the same
+// work items as the tensor-core emission kernel -- a chunk of up to TQ
+// queries that kept representative r, against a window [x_begin, x_end) of
+// r's sorted list (Section 5.2 with sorted lists; the window bound holds for
+// any metric by the triangle inequality).  The chunk's query rows are
+// gathered into shared memory (transposed), the window streams through in
+// tiles of TX rows, each thread accumulates an 8 x 4 block of FP32
+// difference-form distances (squared for l2), and every (query, row) whose
+// value is at most the query's threshold thr[q] is appended to q's candidate
+// buffer (one atomic per hit; cand_cnt counts every emission, so a count
+// above cap marks an overflow).
+template <int METRIC>
+__global__ void __launch_bounds__(NTHREADS, 2)
+bf_simt_emit_kernel(const float* __restrict__ Q, const float* __restrict__ X, int d,
+                    const EmitItem* __restrict__ items, const int* __restrict__ num_items_dev,
+                    int max_items, const int* __restrict__ pair_q, int pair_stride, EmitOut out) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  const int dq = (d + DC - 1) / DC * DC;
+  float* Qs = smem;             // [dq][QS]
+  float* Xs = Qs + dq * QS;     // [DC][XS]
+  __shared__ int s_q[TQ];       // query of each chunk row (-1: none)
+  __shared__ float s_thr[TQ];   // its threshold
+  const int t = threadIdx.x;
+  const int tx = t & 15;
+  const int ty = t >> 4;
+  int n_items = num_items_dev ? *num_items_dev : max_items;
+  if (n_items > max_items) n_items = max_items;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const EmitItem e = items[item];
+    if (e.x_end <= e.x_begin) continue;  // the same for the whole CTA
+    __syncthreads();  // the previous item's readers of Qs / s_q are done
+    if (t < TQ) {
+      const int q = t < e.nq ? pair_q[(int64_t)(e.pair_begin + t) * pair_stride] : -1;
+      s_q[t] = q;
+      s_thr[t] = q >= 0 ? out.thr[q] : -INFINITY;
+    }
+    __syncthreads();
+    // the chunk's query rows, transposed and zero padded: Qs[c][r]
+    for (int idx = t; idx < TQ * dq; idx += NTHREADS) {
+      const int c = idx % dq;
+      const int r = idx / dq;
+      const int q = s_q[r];
+      Qs[c * QS + r] = (q >= 0 && c < d) ? Q[(int64_t)q * d + c] : 0.f;
+    }
+    for (int x0 = e.x_begin; x0 < e.x_end; x0 += TX) {
+      const int nx = min(TX, e.x_end - x0);
+      float acc[8][4];
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+      for (int c0 = 0; c0 < dq; c0 += DC) {
+        __syncthreads();  // Xs free (and Qs complete on the first chunk)
+#pragma unroll
+        for (int j = 0; j < (TX * DC) / NTHREADS; ++j) {
+          const int idx = t + j * NTHREADS;
+          const int c = idx & (DC - 1);
+          const int r = idx / DC;
+          Xs[c * XS + r] = (r < nx && c0 + c < d) ? X[(int64_t)(x0 + r) * d + c0 + c] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int c = 0; c < DC; ++c) {
+          const float4 qa = *reinterpret_cast<const float4*>(&Qs[(c0 + c) * QS + ty * 8]);
+          const float4 qb = *reinterpret_cast<const float4*>(&Qs[(c0 + c) * QS + ty * 8 + 4]);
+          const float qv[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+          float xv[4];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) xv[b] = Xs[c * XS + tx * 4 + b];
+#pragma unroll
+          for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              const float diff = qv[a] - xv[b];
+              if (METRIC == RBC_L2)
+                acc[a][b] = fmaf(diff, diff, acc[a][b]);
+              else
+                acc[a][b] += fabsf(diff);
+            }
+        }
+      }
+      // emission: every value at or under its row's threshold
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int row = ty * 8 + a;
+        const float th = s_thr[row];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int col = tx * 4 + b;
+          if (col < nx && acc[a][b] <= th) {
+            const int q = s_q[row];
+            const int pos = atomicAdd(&out.cand_cnt[q], 1);
+            if (pos < out.cap) {
+              out.cand_score[(int64_t)q * out.cap + pos] = acc[a][b];
+              out.cand_row[(int64_t)q * out.cap + pos] = x0 + col;
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
 }  // namespace
 
 int simt_list_width(int c_needed) {
@@ -226,6 +330,31 @@ int launch_bf_simt_topc(const float* Q, const float* X, int d, int metric, int C
   }
   if (metric == RBC_L2) return dispatch_c<RBC_L2>(C, Q, X, d, w, out, grid, st);
   return dispatch_c<RBC_L1>(C, Q, X, d, w, out, grid, st);
+}
+
+int launch_bf_simt_emit(const float* Q, const float* X, int d, int metric, const EmitItem* items,
+                        const int* num_items_dev, int max_items, const int* pair_q,
+                        int pair_stride, const EmitOut& out, int grid, cudaStream_t st) {
+  if (d > SIMT_MAX_D) {
+    set_error("bf_simt: d = %d exceeds %d", d, SIMT_MAX_D);
+    return RBC_ERR_UNSUPPORTED;
+  }
+  if (max_items <= 0 || grid <= 0) return RBC_OK;
+  const int dq = (d + DC - 1) / DC * DC;
+  const size_t smem = sizeof(float) * ((size_t)dq * QS + DC * XS);
+  if (metric == RBC_L2) {
+    auto kern = bf_simt_emit_kernel<RBC_L2>;
+    RBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, NTHREADS, smem, st>>>(Q, X, d, items, num_items_dev, max_items, pair_q,
+                                       pair_stride, out);
+  } else {
+    auto kern = bf_simt_emit_kernel<RBC_L1>;
+    RBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, NTHREADS, smem, st>>>(Q, X, d, items, num_items_dev, max_items, pair_q,
+                                       pair_stride, out);
+  }
+  RBC_LAUNCH_CHECK("bf_simt_emit_kernel");
+  return RBC_OK;
 }
 
 int launch_bf_simt_store(const float* Q, const float* X, int d, int metric, const TileWork& w,

@@ -147,6 +147,23 @@ __host__ __device__ __forceinline__ float dist_upper(float s, float qn, float qe
   return (sqrtf(fmaxf(t, 0.0f)) * (1.0f + 4.8e-7f) + qerr + xerr) * (1.0f + 4.8e-7f);
 }
 
+// FP32 difference-form values (rho^2 for l2, rho for l1) with relative error
+// at most eps: the largest distance a value s can stand for (s >= v (1 - eps)
+// for the exact value v, so v <= s (1 + 2 eps)), and the largest value a point
+// within distance g can have (g^2 (1 + eps) for l2, g (1 + eps) for l1), both
+// rounded up.
+__host__ __device__ __forceinline__ float f32_dist_upper(float s, float eps, int metric) {
+  if (!(s < INFINITY)) return INFINITY;
+  const float t = fmaxf(s, 0.0f) * (1.0f + 2.0f * eps) * (1.0f + 4.8e-7f);
+  return metric == RBC_L2 ? sqrtf(t) * (1.0f + 4.8e-7f) : t;
+}
+__host__ __device__ __forceinline__ float f32_score_bound(float g, float eps, int metric) {
+  if (!(g < INFINITY)) return INFINITY;
+  const float G = g * (1.0f + 4.8e-7f);
+  const float v = metric == RBC_L2 ? G * G * (1.0f + 4.8e-7f) : G;
+  return v * (1.0f + eps) * (1.0f + 4.8e-7f) + 1e-30f;
+}
+
 // Device-side error flags (bit mask), read back by the host after a call.
 enum : uint32_t {
   DEV_ERR_TIMEOUT = 1u,      // a bounded wait gave up

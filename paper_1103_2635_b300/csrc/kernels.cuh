@@ -115,6 +115,13 @@ int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* it
                       int pair_stride, const EmitOut& out, int grid, cudaStream_t st,
                       uint32_t* dev_err, int fold_col = -1);
 
+// The same windowed stage two on CUDA cores (FP32 rows, l2 or l1): every
+// (query, window row) whose FP32 difference-form value (rho^2 for l2, rho
+// for l1) is at most thr[query] is appended to the query's buffer.
+int launch_bf_simt_emit(const float* Q, const float* X, int d, int metric, const EmitItem* items,
+                        const int* num_items_dev, int max_items, const int* pair_q,
+                        int pair_stride, const EmitOut& out, int grid, cudaStream_t st);
+
 // ---- merge + re-rank + certification ----
 struct SelectArgs {
   const float* part_score;
@@ -224,6 +231,10 @@ struct CandSelectArgs {
   // instead of going to the re-search
   int* stream_rows = nullptr;
   int* stream_count = nullptr;
+  // FP32 candidates (CUDA-core emission): scores are FP32 difference-form
+  // values with relative error <= f32_eps; the low-precision fields are unused
+  int f32 = 0;
+  float f32_eps = 0.0f;
 };
 int launch_select_cands(const CandSelectArgs& a, cudaStream_t st);
 // The queries a.stream_rows[0 .. *a.stream_count) of a launch_select_cands:
@@ -274,15 +285,18 @@ int launch_window_items(const int* bin_off, int nb, int n_r, const int2* pairs,
 // items over the whole list storage (chunks of TQ of these queries x row
 // spans of xspan) for the emission kernel.
 // (the number of rows is read from n_dev on the device; at most max_rows)
+// (qnorm == nullptr: FP32 difference-form scores, bounds from f32_eps / metric)
 int launch_overflow_rethreshold(const int* rows, const int* n_dev, int64_t max_rows,
                                 const float* cand_score, int* cand_cnt, int cap, int k,
                                 const float* qnorm, const float* qerr, const unsigned* lp_max,
-                                int d, float* thr, cudaStream_t st);
+                                int d, float* thr, cudaStream_t st, float f32_eps = 0.0f,
+                                int metric = RBC_L2);
 int launch_dense_emit_items(const int* n_dev, int64_t x_rows, int xspan, int max_items,
                             EmitItem* items, int* num_items, cudaStream_t st);
+// (qnorm == nullptr: thr = f32_score_bound(g, f32_eps, metric))
 int launch_score_threshold(const float* g, const float* qnorm, const float* qerr,
                            const unsigned* lp_max, int d, int64_t m, float* thr,
-                           cudaStream_t st);
+                           cudaStream_t st, float f32_eps = 0.0f, int metric = RBC_L2);
 
 // ---- one-shot RBC (oneshot.cu) ----
 // candidate capacity per representative for a list of s points

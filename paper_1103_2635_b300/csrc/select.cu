@@ -515,10 +515,15 @@ __global__ void __launch_bounds__(WARPS * 32) select_cands_kernel(CandSelectArgs
   } else {
     kth = kth_score_key(sc, cnt, k, lane);
   }
-  const float qn = a.q_lpnorm[q], qe = a.q_err[q];
-  const float xe = __uint_as_float(*a.x_err_max_bits), xn = __uint_as_float(*a.x_norm_max_bits);
-  const float smax = score_bound(dist_upper(key_score(kth), qn, qe, xe, xn, a.d), qn, qe, xe, xn,
-                                 a.d);
+  float smax;
+  if (a.f32) {
+    smax = f32_score_bound(f32_dist_upper(key_score(kth), a.f32_eps, a.metric), a.f32_eps,
+                           a.metric);
+  } else {
+    const float qn = a.q_lpnorm[q], qe = a.q_err[q];
+    const float xe = __uint_as_float(*a.x_err_max_bits), xn = __uint_as_float(*a.x_norm_max_bits);
+    smax = score_bound(dist_upper(key_score(kth), qn, qe, xe, xn, a.d), qn, qe, xe, xn, a.d);
+  }
   // ---- 2. survivors -> shared memory ----
   int* stg = stage[wib];
   int nre = 0;
@@ -686,7 +691,8 @@ __global__ void __launch_bounds__(WARPS * 32) select_stream_kernel(CandSelectArg
   int* sband = s_band[wib];
   const int64_t nw = *a.stream_count;
   const int k = a.k, d = a.d;
-  const float xe = __uint_as_float(*a.x_err_max_bits), xn = __uint_as_float(*a.x_norm_max_bits);
+  const float xe = a.f32 ? 0.0f : __uint_as_float(*a.x_err_max_bits);
+  const float xn = a.f32 ? 0.0f : __uint_as_float(*a.x_norm_max_bits);
   for (int64_t wi = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5); wi < nw;
        wi += (int64_t)gridDim.x * WARPS) {
     const int64_t q = a.stream_rows[wi];
@@ -695,9 +701,14 @@ __global__ void __launch_bounds__(WARPS * 32) select_stream_kernel(CandSelectArg
     const int* cr = a.cand_row + q * a.cap;
     // k-th smallest score -> survivor bound (as in select_cands)
     const unsigned kth = kth_score_key(sc, cnt, k, lane);
-    const float qn = a.q_lpnorm[q], qe = a.q_err[q];
-    const float smax =
-        score_bound(dist_upper(key_score(kth), qn, qe, xe, xn, d), qn, qe, xe, xn, d);
+    float smax;
+    if (a.f32) {
+      smax = f32_score_bound(f32_dist_upper(key_score(kth), a.f32_eps, a.metric), a.f32_eps,
+                             a.metric);
+    } else {
+      const float qn = a.q_lpnorm[q], qe = a.q_err[q];
+      smax = score_bound(dist_upper(key_score(kth), qn, qe, xe, xn, d), qn, qe, xe, xn, d);
+    }
     const float* qr = a.Q32 + q * d;
     float ls[CW];
     int li[CW], lr[CW];

@@ -437,7 +437,7 @@ __global__ void overflow_rethreshold_kernel(const int* __restrict__ rows,
                                             const float* __restrict__ qnorm,
                                             const float* __restrict__ qerr,
                                             const unsigned* __restrict__ lp_max, int d,
-                                            float* __restrict__ thr) {
+                                            float* __restrict__ thr, float f32_eps, int metric) {
   const int lane = threadIdx.x & 31;
   const int n = *n_dev;
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n;
@@ -461,8 +461,12 @@ __global__ void overflow_rethreshold_kernel(const int* __restrict__ rows,
       if (c < k) res = tt;
     }
     const float sk = __uint_as_float((res & 0x80000000u) ? (res & 0x7fffffffu) : ~res);
-    const float xe = __uint_as_float(lp_max[0]), xn = __uint_as_float(lp_max[1]);
-    t = score_bound(dist_upper(sk, qnorm[q], qerr[q], xe, xn, d), qnorm[q], qerr[q], xe, xn, d);
+    if (qnorm) {
+      const float xe = __uint_as_float(lp_max[0]), xn = __uint_as_float(lp_max[1]);
+      t = score_bound(dist_upper(sk, qnorm[q], qerr[q], xe, xn, d), qnorm[q], qerr[q], xe, xn, d);
+    } else {
+      t = f32_score_bound(f32_dist_upper(sk, f32_eps, metric), f32_eps, metric);
+    }
   }
   if (lane == 0) {
     thr[q] = t;
@@ -512,11 +516,12 @@ __global__ void scatter_hits_kernel(const int4* __restrict__ arena, int arena_se
 __global__ void score_threshold_kernel(const float* __restrict__ g, const float* __restrict__ qnorm,
                                        const float* __restrict__ qerr,
                                        const unsigned* __restrict__ lp_max, int d, int64_t m,
-                                       float* __restrict__ thr) {
+                                       float* __restrict__ thr, float f32_eps, int metric) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= m) return;
-  thr[q] = score_bound(g[q], qnorm[q], qerr[q], __uint_as_float(lp_max[0]),
-                       __uint_as_float(lp_max[1]), d);
+  thr[q] = qnorm ? score_bound(g[q], qnorm[q], qerr[q], __uint_as_float(lp_max[0]),
+                               __uint_as_float(lp_max[1]), d)
+                 : f32_score_bound(g[q], f32_eps, metric);
 }
 
 }  // namespace
@@ -601,10 +606,10 @@ int launch_window_items(const int* bin_off, int nb, int n_r, const int2* pairs,
 
 int launch_score_threshold(const float* g, const float* qnorm, const float* qerr,
                            const unsigned* lp_max, int d, int64_t m, float* thr,
-                           cudaStream_t st) {
+                           cudaStream_t st, float f32_eps, int metric) {
   if (m <= 0) return RBC_OK;
   score_threshold_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(g, qnorm, qerr, lp_max, d,
-                                                                      m, thr);
+                                                                      m, thr, f32_eps, metric);
   RBC_LAUNCH_CHECK("score_threshold_kernel");
   return RBC_OK;
 }
@@ -612,11 +617,11 @@ int launch_score_threshold(const float* g, const float* qnorm, const float* qerr
 int launch_overflow_rethreshold(const int* rows, const int* n_dev, int64_t max_rows,
                                 const float* cand_score, int* cand_cnt, int cap, int k,
                                 const float* qnorm, const float* qerr, const unsigned* lp_max,
-                                int d, float* thr, cudaStream_t st) {
+                                int d, float* thr, cudaStream_t st, float f32_eps, int metric) {
   if (max_rows <= 0) return RBC_OK;
   const int64_t want = (max_rows * 32 + 255) / 256;
   overflow_rethreshold_kernel<<<(unsigned)std::min<int64_t>(want, 148 * 4), 256, 0, st>>>(
-      rows, n_dev, cand_score, cand_cnt, cap, k, qnorm, qerr, lp_max, d, thr);
+      rows, n_dev, cand_score, cand_cnt, cap, k, qnorm, qerr, lp_max, d, thr, f32_eps, metric);
   RBC_LAUNCH_CHECK("overflow_rethreshold_kernel");
   return RBC_OK;
 }

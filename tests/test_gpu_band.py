@@ -79,15 +79,22 @@ def test_bf_noalloc_uncertified_rows_match_oracle(metric):
 
 
 @pytest.mark.parametrize("metric", ["l2", "l1"])
-def test_exact_search_f32_uncertified_rows_match_oracle(metric):
+@pytest.mark.parametrize("plan", [rbc.PLAN_WINDOW, rbc.PLAN_TILE_UNION])
+def test_exact_search_f32_uncertified_rows_match_oracle(metric, plan):
+    # tile-union plan: the FP32 certificate fails and the FP64 band pass
+    # finishes the rows; windowed plan: every survivor in the tie band of the
+    # k-th place is decided in FP64 by the select step
     X, Q = shell_inputs(64, metric)
     Xd, Qd = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
-    idx = rbc.rbc_build(Xd, 128, metric=MET[metric], seed=3, storage=rbc.F32)
+    idx = rbc.rbc_build(Xd, 128, metric=MET[metric], seed=3, storage=rbc.F32, plan=plan)
     ids, dist = rbc.rbc_search(idx, Qd, 31)
     ids, dist = _cpu(ids), _cpu(dist)
     st = rbc.last_stats()
     idx.close()
-    assert st["uncertified"] > 0, st
+    if plan == rbc.PLAN_TILE_UNION:
+        assert st["uncertified"] > 0, st
+    else:
+        assert st["boundary_ties"] > 0, st
     o_ids, o_rho = oracle.bf(Q, X, 31, metric)
     check_knn(Q, X, ids, dist, o_ids, o_rho, metric)
 

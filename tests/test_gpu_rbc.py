@@ -63,13 +63,32 @@ def test_exact_search_iid_n16k_d16(metric, k):
 
 @pytest.mark.parametrize("metric", ["l2", "l1"])
 @pytest.mark.parametrize("n,m,d,n_r,k", [(5000, 300, 5, 71, 3), (2049, 129, 33, 1, 2), (3001, 77, 12, 3001, 4), (20000, 513, 8, 141, 7), (1000, 1, 64, 30, 31)])
-def test_exact_search_ragged(metric, n, m, d, n_r, k):
+@pytest.mark.parametrize("plan", [rbc.PLAN_WINDOW, rbc.PLAN_TILE_UNION])
+def test_exact_search_ragged(metric, n, m, d, n_r, k, plan):
+    # FP32 storage: both stage-two plans on the CUDA cores
     X = synth.iid_normal(n, d, 10 + n)
     Q = synth.iid_normal(m, d, 20 + m)
-    idx = build(X, n_r, metric, seed=n_r)
+    idx = build(X, n_r, metric, seed=n_r, plan=plan)
     ids, dist = search(idx, Q, k)
     o_ids, o_rho = oracle.bf(Q, X, k, metric)
     check_knn(Q, X, ids, dist, o_ids, o_rho, metric)
+
+
+@pytest.mark.parametrize("metric", ["l2", "l1"])
+@pytest.mark.parametrize("k", [1, 10])
+def test_exact_search_f32_window_subspace(metric, k):
+    # the windowed plan on the CUDA cores examines fewer (query, point) pairs
+    # than the tile-union plan and returns the same neighbours
+    X, Q = synth.make_workload("subspace8-n1m-d64", seed=0, n=60000, m=700)
+    res = {}
+    for plan in (rbc.PLAN_WINDOW, rbc.PLAN_TILE_UNION):
+        idx = build(X, 245, metric, plan=plan)
+        res[plan] = search(idx, Q, k) + (rbc.last_stats(),)
+        idx.close()
+    o_ids, o_rho = oracle.bf(Q, X, k, metric)
+    for plan, (ids, dist, st) in res.items():
+        check_knn(Q, X, ids, dist, o_ids, o_rho, metric)
+    assert res[rbc.PLAN_WINDOW][2]["pairs"] < res[rbc.PLAN_TILE_UNION][2]["pairs"]
 
 
 def test_exact_search_subspace_workload_small():
