@@ -485,10 +485,32 @@ int bf_dense_f32(const float* Qdev, int64_t m, const DbView& db, int d, int k, i
   w.dense_splits = (int)splits;
   w.dense_chunk = chunk;
   int grid = (int)std::min<int64_t>(items, (int64_t)sms * 2 * 16);
+  // l2: the expansion form |x|^2 - 2 q.x (one FFMA per dimension) with FP32
+  // norms, certified with its absolute rounding bound; l1: the difference form
+  const bool exp32 = metric == RBC_L2;
+  float *xn = nullptr, *qn = nullptr;
+  unsigned* xmax = nullptr;
+  if (exp32) {
+    RBC_TRY(ar.alloc(&xn, db.rows));
+    RBC_TRY(ar.alloc(&qn, m));
+    RBC_TRY(ar.alloc(&xmax, 1));
+    RBC_CUDA(cudaMemsetAsync(xmax, 0, sizeof(unsigned), st));
+    RBC_TRY(launch_row_norms(db.X32, db.rows, d, xn, xmax, st));
+    RBC_TRY(launch_row_norms(Qdev, m, d, qn, nullptr, st));
+  }
   if (marks) tmark(1, st);
-  RBC_TRY(launch_bf_simt_topc(Qdev, db.X32, d, metric, C, w, TopOut{ps, pi, nullptr}, grid, st));
+  if (exp32)
+    RBC_TRY(launch_bf_simt_topc_exp(Qdev, db.X32, xn, d, C, w, TopOut{ps, pi, nullptr}, grid, st));
+  else
+    RBC_TRY(launch_bf_simt_topc(Qdev, db.X32, d, metric, C, w, TopOut{ps, pi, nullptr}, grid, st));
   if (marks) tmark(2, st);
   SelectArgs a{};
+  if (exp32) {
+    a.lp = 1;
+    a.exp32 = 1;
+    a.q_lpnorm = qn;
+    a.x_norm_max_bits = xmax;
+  }
   a.part_score = ps;
   a.part_idx = pi;
   a.C = C;
@@ -501,7 +523,6 @@ int bf_dense_f32(const float* Qdev, int64_t m, const DbView& db, int d, int k, i
   a.qorig = qorig;
   a.X32 = db.X32;
   a.xid = db.xid;
-  a.lp = 0;
   a.simt_eps = simt_eps(d);
   a.k = k;
   a.c_out = c_out;
@@ -1678,9 +1699,11 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // bf_dense_f32 over `rows` queries (items = tiles x splits <= tiles + 8 SMs)
-int64_t bound_dense_f32(int64_t rows, int sms) {
+// bf_dense_f32 over `rows` queries against `db_rows` database rows: partial
+// lists, FP32 norms of both (l2), the rows to finish exactly and counters
+int64_t bound_dense_f32(int64_t rows, int sms, int64_t db_rows) {
   if (rows <= 0) return 0;
-  return (cdiv(rows, TQ) + 8LL * sms) * TQ * 2 * MAX_C * 8;
+  return (cdiv(rows, TQ) + 8LL * sms) * TQ * 2 * MAX_C * 8 + db_rows * 4 + rows * 8 + 64;
 }
 int64_t bound_exact_batch(const rbc_index* ix, int64_t mb, int k, bool f32_only = false);
 // fallback_rbc_f32 over `rows` rows: gathered rows, results, counters and the
@@ -1783,7 +1806,7 @@ int64_t bound_oneshot_stage2(const rbc_index* ix, int64_t mq, bool lp, int level
 
 int64_t bound_oneshot_batch(const rbc_index* ix, int64_t mb) {
   const bool lp = uses_lp(ix->storage, ix->metric) && ix->Xlp != nullptr;
-  return mb * 12 + 32 + bound_dense_f32(mb, sm_count()) + bound_oneshot_stage2(ix, mb, lp, 0);
+  return mb * 12 + 32 + bound_dense_f32(mb, sm_count(), ix->n_r) + bound_oneshot_stage2(ix, mb, lp, 0);
 }
 
 // the batch size rbc_search cuts a call into

@@ -13,7 +13,11 @@
 //
 // Modes: TOPC (the lists above) and STORE (write every distance to a dense
 // [rows, ld] matrix; used for the representative distances of the exact
-// search, Section 5.2, which must be kept).
+// search, Section 5.2, which must be kept).  EXP (l2 top-C only): the
+// expansion |x|^2 - 2 q.x with precomputed FP32 norms instead of the
+// difference form -- one FFMA per dimension instead of a subtraction and an
+// FFMA; its rounding bound is absolute, (d + 4) 2^-23 (|q| + max |x|)^2, and
+// the select step certifies with it (SelectArgs::exp32).
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -57,16 +61,18 @@ __device__ __forceinline__ Seg get_seg(const TileWork& w, int si) {
   return Seg{(int32_t)b, (int32_t)e};
 }
 
-template <int METRIC, int C, bool STORE>
+template <int METRIC, int C, bool STORE, bool EXP = false>
 __global__ void __launch_bounds__(NTHREADS, 2)
 bf_simt_kernel(const float* __restrict__ Q, const float* __restrict__ X, int d, TileWork w,
-               TopOut out, float* __restrict__ store, int64_t store_ld) {
+               TopOut out, float* __restrict__ store, int64_t store_ld,
+               const float* __restrict__ xnorm = nullptr) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   const int dq = (d + DC - 1) / DC * DC;  // query tile rows, padded to the chunk
   float* Qs = smem;                        // [dq][QS]
   float* Xs = Qs + dq * QS;                // [DC][XS]
   float* Ds = Xs + DC * XS;                // [TQ][DS]
+  __shared__ float s_xn[TX];               // EXP: |x|^2 of the tile's rows
 
   const int t = threadIdx.x;
   const int tx = t & 15;
@@ -130,22 +136,29 @@ bf_simt_kernel(const float* __restrict__ Q, const float* __restrict__ X, int d, 
             for (int a = 0; a < 8; ++a)
 #pragma unroll
               for (int b = 0; b < 4; ++b) {
-                float diff = qv[a] - xv[b];
-                if (METRIC == RBC_L2)
-                  acc[a][b] = fmaf(diff, diff, acc[a][b]);
-                else
-                  acc[a][b] += fabsf(diff);
+                if (EXP) {
+                  acc[a][b] = fmaf(qv[a], xv[b], acc[a][b]);
+                } else {
+                  float diff = qv[a] - xv[b];
+                  if (METRIC == RBC_L2)
+                    acc[a][b] = fmaf(diff, diff, acc[a][b]);
+                  else
+                    acc[a][b] += fabsf(diff);
+                }
               }
           }
         }
         // ---- distance tile -> shared memory (columns interleaved for the
         // two selecting threads of a row) ----
+        if (EXP && t < TX) s_xn[t] = t < nx ? xnorm[x0 + t] : 0.f;
+        if (EXP) __syncthreads();
 #pragma unroll
         for (int a = 0; a < 8; ++a)
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
             int col = tx * 4 + b;
-            Ds[(ty * 8 + a) * DS + col] = (col < nx) ? acc[a][b] : INFINITY;
+            const float v = EXP ? fmaf(-2.0f, acc[a][b], s_xn[col]) : acc[a][b];
+            Ds[(ty * 8 + a) * DS + col] = (col < nx) ? v : INFINITY;
           }
         __syncthreads();
         if (STORE) {
@@ -185,14 +198,15 @@ bf_simt_kernel(const float* __restrict__ Q, const float* __restrict__ X, int d, 
   }
 }
 
-template <int METRIC, int C, bool STORE>
+template <int METRIC, int C, bool STORE, bool EXP = false>
 int launch_one(const float* Q, const float* X, int d, const TileWork& w, const TopOut& out,
-               float* store, int64_t store_ld, int grid, cudaStream_t st) {
+               float* store, int64_t store_ld, int grid, cudaStream_t st,
+               const float* xnorm = nullptr) {
   const int dq = (d + DC - 1) / DC * DC;
   size_t smem = sizeof(float) * ((size_t)dq * QS + DC * XS + TQ * DS);
-  auto kern = bf_simt_kernel<METRIC, C, STORE>;
+  auto kern = bf_simt_kernel<METRIC, C, STORE, EXP>;
   RBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<grid, NTHREADS, smem, st>>>(Q, X, d, w, out, store, store_ld);
+  kern<<<grid, NTHREADS, smem, st>>>(Q, X, d, w, out, store, store_ld, xnorm);
   RBC_LAUNCH_CHECK("bf_simt_kernel");
   return RBC_OK;
 }
@@ -330,6 +344,22 @@ int launch_bf_simt_topc(const float* Q, const float* X, int d, int metric, int C
   }
   if (metric == RBC_L2) return dispatch_c<RBC_L2>(C, Q, X, d, w, out, grid, st);
   return dispatch_c<RBC_L1>(C, Q, X, d, w, out, grid, st);
+}
+
+int launch_bf_simt_topc_exp(const float* Q, const float* X, const float* xnorm, int d, int C,
+                            const TileWork& w, const TopOut& out, int grid, cudaStream_t st) {
+  if (d > SIMT_MAX_D) {
+    set_error("bf_simt: d = %d exceeds %d", d, SIMT_MAX_D);
+    return RBC_ERR_UNSUPPORTED;
+  }
+  switch (C) {
+    case 2: return launch_one<RBC_L2, 2, false, true>(Q, X, d, w, out, nullptr, 0, grid, st, xnorm);
+    case 4: return launch_one<RBC_L2, 4, false, true>(Q, X, d, w, out, nullptr, 0, grid, st, xnorm);
+    case 8: return launch_one<RBC_L2, 8, false, true>(Q, X, d, w, out, nullptr, 0, grid, st, xnorm);
+    case 16: return launch_one<RBC_L2, 16, false, true>(Q, X, d, w, out, nullptr, 0, grid, st, xnorm);
+    case 32: return launch_one<RBC_L2, 32, false, true>(Q, X, d, w, out, nullptr, 0, grid, st, xnorm);
+    default: set_error("bf_simt: unsupported list width %d", C); return RBC_ERR_UNSUPPORTED;
+  }
 }
 
 int launch_bf_simt_emit(const float* Q, const float* X, int d, int metric, const EmitItem* items,

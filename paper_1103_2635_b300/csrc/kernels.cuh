@@ -41,6 +41,11 @@ int launch_bf_simt_topc(const float* Q, const float* X, int d, int metric, int C
                         const TileWork& w, const TopOut& out, int grid, cudaStream_t st);
 int launch_bf_simt_store(const float* Q, const float* X, int d, int metric, const TileWork& w,
                          float* store, int64_t store_ld, int grid, cudaStream_t st);
+// l2 top-C in the expansion form |x|^2 - 2 q.x (one FFMA per dimension), with
+// the rows' FP32 squared norms xnorm: scores for the select step's
+// expansion-form certificate (SelectArgs::exp32)
+int launch_bf_simt_topc_exp(const float* Q, const float* X, const float* xnorm, int d, int C,
+                            const TileWork& w, const TopOut& out, int grid, cudaStream_t st);
 
 // ---- low-precision (tensor-core) path ----
 struct LpMatrix {
@@ -157,6 +162,10 @@ struct SelectArgs {
   // nonzero (rows of Q32 / X32 stay d apart); sets the re-rank length and its
   // rounding bounds
   const int16_t* tile_dim = nullptr;
+  // lp with FP32 expansion-form scores (|x|^2 - 2 q.x on CUDA cores): no
+  // rounding residuals (q_err / x_err_max_bits unused), FP32 evaluation bound
+  // (d + 4) 2^-23 (|q| + max |x|)^2, q_lpnorm = |q|^2, x_norm_max_bits = max |x|
+  int exp32 = 0;
 };
 int launch_select(const SelectArgs& a, cudaStream_t st);
 
@@ -362,6 +371,9 @@ int launch_fold_norm(void* lp, const float* norm, int64_t rows, int dpad, int co
 // i (to about 2^-17 relative).  rows_out >= rows; rows past `rows` are zero.
 int launch_norm_block(const float* norm, int64_t rows, int64_t rows_out, void* dst,
                       cudaStream_t st);
+// |x|^2 of FP32 rows [rows, d]; max_bits (optional): the largest |x| rounded up
+int launch_row_norms(const float* X, int64_t rows, int d, float* norm, unsigned* max_bits,
+                     cudaStream_t st);
 // out[i] = qorig ? qorig[rows[i]] : rows[i], for i < *n_dev (or n when n_dev is null)
 int launch_map_rows(const int* rows, const int* n_dev, int n, const int* qorig, int* out,
                     cudaStream_t st);

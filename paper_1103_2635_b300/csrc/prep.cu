@@ -227,6 +227,34 @@ int launch_map_rows(const int* rows, const int* n_dev, int n, const int* qorig, 
   return RBC_OK;
 }
 
+// |x|^2 of FP32 rows (one warp per row, FP32 partial sums) and, when asked,
+// the largest |x| rounded up, as float bits (for the expansion form's bound).
+__global__ void row_norms_kernel(const float* __restrict__ X, int64_t rows, int d,
+                                 float* __restrict__ norm, unsigned* __restrict__ max_bits) {
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  const float* x = X + r * d;
+  float s = 0.f;
+  for (int i = lane; i < d; i += 32) s = fmaf(x[i], x[i], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    norm[r] = s;
+    // sqrt rounded up, and a margin for the sum's own rounding
+    if (max_bits) atomicMax(max_bits, __float_as_uint(__fsqrt_ru(s) * (1.0f + 1e-6f)));
+  }
+}
+
+int launch_row_norms(const float* X, int64_t rows, int d, float* norm, unsigned* max_bits,
+                     cudaStream_t st) {
+  if (rows <= 0) return RBC_OK;
+  const int64_t threads = rows * 32;
+  row_norms_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(X, rows, d, norm, max_bits);
+  RBC_LAUNCH_CHECK("row_norms_kernel");
+  return RBC_OK;
+}
+
 int launch_gather_rows(const float* src, const int64_t* idx64, const int* idx32, int64_t rows,
                        int d, float* dst, cudaStream_t st) {
   if (rows <= 0) return RBC_OK;

@@ -266,15 +266,18 @@ __global__ void __launch_bounds__(WARPS * 32) select_kernel(SelectArgs a) {
       float qn = a.q_lpnorm[row];
       float nq = sqrtf(qn);
       const float xn = __uint_as_float(*a.x_norm_max_bits);
-      float span = nq + xn;
+      float span = (nq + xn) * (1.0f + 4.0f * U32);
       // FP32 evaluation bound of |x~|^2 - 2 q~.x~ (tensor-core products are
       // exact, accumulation allowed 2^-20 relative per term): (d+4) 2^-19 span^2,
       // plus 2^-16 max|x~|^2 for a norm term that enters the accumulator as a
-      // bf16 (high, low) pair (its error is at most 2^-17 |x~|^2)
-      float ef = (float)(d + 4) * 1.9073486e-06f * span * span + 1.5258789e-05f * xn * xn;
+      // bf16 (high, low) pair (its error is at most 2^-17 |x~|^2).  FP32
+      // expansion on CUDA cores: (d+1) 2^-24 span^2 for the dot product, the
+      // norms and the final FMA, taken twice: (d+4) 2^-23 span^2
+      float ef = a.exp32 ? (float)(d + 4) * 1.1920929e-07f * span * span
+                         : (float)(d + 4) * 1.9073486e-06f * span * span + 1.5258789e-05f * xn * xn;
       float t = B + qn - ef;
-      lower = (t > 0.f ? sqrtf(t) * (1.0f - 4.0f * U32) : 0.f) - a.q_err[row] -
-              __uint_as_float(*a.x_err_max_bits);
+      lower = (t > 0.f ? sqrtf(t) * (1.0f - 4.0f * U32) : 0.f);
+      if (!a.exp32) lower -= a.q_err[row] + __uint_as_float(*a.x_err_max_bits);
       lower *= (1.0f - 8.0f * U32);
     }
     float upper = rk * (1.0f + eps) * (1.0f + 4.0f * U32);
