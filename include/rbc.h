@@ -166,13 +166,43 @@ int rbc_build(const float* X, int64_t n, int32_t d, int32_t n_r, int32_t s, int3
  *   k <= s.  Queries are grouped by representative and each group padded to
  *   whole 128-query tiles, so every tile searches exactly one list.
  *   Q [m, d] float32; out_ids [m, k] int64; out_dist [m, k] float32 (device
- *   or host).  m may be 0 (no work).  The call reads back one small counter
- *   (the stage-two work size) and so synchronises `stream` once.
- *   Errors: RBC_ERR_ARG if idx/Q/outputs NULL, m < 0, k < 1, k > n, or
- *   one-shot with k > s; RBC_ERR_OOM; RBC_ERR_CUDA; RBC_ERR_TIMEOUT.
+ *   or host).  m may be 0 (no work).
+ *   Host read-backs: the tile-union plan and one-shot mode read back small
+ *   counters (stage-two work sizes) and so synchronise `stream`.  The
+ *   windowed plan decides its overflow passes on the device and reads back
+ *   once per batch of queries, at its end: the count of rows left for the
+ *   FP32 exact search (rows with more points tying within rounding than a
+ *   candidate buffer holds) and the device error flags.
+ *   Stream capture (windowed plan only): called while `stream` is being
+ *   captured into a CUDA graph, rbc_search reads nothing back and
+ *   synchronises nothing, so the graph replays the whole search.  Rows left
+ *   after the overflow pass are then finished on the device by the FP64
+ *   band pass over the whole database (exact, slow only when thousands of
+ *   points tie); device error flags (a bounded wait that expired) are
+ *   recorded in the index and reported by rbc_search_check.  Requirements:
+ *   Q and the outputs in device memory, rbc_set_timing off, and one call
+ *   with the same batch shape made on this thread before the capture (it
+ *   sets up the kernels' attributes and the pinned statistics block).
+ *   Workspace is then taken from the graph's own memory (stream-ordered
+ *   allocation nodes) instead of the library's pool.
+ *   Errors: RBC_ERR_ARG if idx/Q/outputs NULL, m < 0, k < 1, k > n,
+ *   one-shot with k > s, or host memory under capture; RBC_ERR_UNSUPPORTED
+ *   under capture with a plan other than the windowed one or with timing
+ *   on; RBC_ERR_OOM; RBC_ERR_CUDA; RBC_ERR_TIMEOUT.
  */
 int rbc_search(const rbc_index* idx, const float* Q, int64_t m, int32_t k, int64_t* out_ids,
                float* out_dist, void* stream);
+
+/*
+ * rbc_search_check -- waits for `stream`, then reports and clears the device
+ *   error flags that searches recorded under stream capture left in the
+ *   index (each bounded wait of the tensor-core kernels gives up after
+ *   2 s and sets a flag instead of hanging).  RBC_OK when none is set.
+ *   No counterpart in the paper (error reporting of replayed graphs).
+ *   Errors: RBC_ERR_ARG if idx is NULL; RBC_ERR_TIMEOUT or RBC_ERR_CUDA for
+ *   recorded flags; RBC_ERR_CUDA.
+ */
+int rbc_search_check(const rbc_index* idx, void* stream);
 
 /*
  * rbc_search_workspace -- upper bound of the device workspace (bytes

@@ -121,6 +121,7 @@ def load():
     lib.rbc_build.argtypes = [P, I64, I32, I32, I32, I32, ctypes.POINTER(_Opts), P,
                               ctypes.POINTER(ctypes.c_void_p)]
     lib.rbc_search.argtypes = [P, P, I64, I32, P, P, P]
+    lib.rbc_search_check.argtypes = [P, P]
     lib.rbc_index_info.argtypes = [P, ctypes.POINTER(_Desc)]
     lib.rbc_index_export.argtypes = [P, P, P, P, P]
     lib.rbc_last_stats.argtypes = [ctypes.POINTER(_Stats)]
@@ -146,7 +147,7 @@ def load():
     lib.rbc_group_stats.argtypes = [P, ctypes.POINTER(_GroupedStats)]
     lib.rbc_group_free.argtypes = [P]
     lib.rbc_group_free.restype = None
-    for f in ("rbc_sample_reps", "bf_search", "bf_search_noalloc", "rbc_build", "rbc_search", "rbc_index_info",
+    for f in ("rbc_sample_reps", "bf_search", "bf_search_noalloc", "rbc_build", "rbc_search", "rbc_search_check", "rbc_index_info",
               "rbc_index_export", "rbc_last_stats", "rbc_search_workspace", "rbc_plan_batch",
               "rbc_server_create", "rbc_server_submit", "rbc_server_wait", "rbc_server_stats",
               "rbc_group_create", "rbc_group_search", "rbc_group_tune", "rbc_group_stats"):
@@ -313,6 +314,12 @@ def rbc_search(index: RbcIndex, Q, k: int, out_ids=None, out_dist=None, stream=N
     st = _stream_of(stream, qdev or idev)
     _check(load().rbc_search(index.handle, qp, m, k, ip, dp, st))
     return out_ids, out_dist
+
+
+def search_check(index: RbcIndex, stream=None) -> None:
+    """Wait for the stream, then raise if a search recorded under stream
+    capture (a CUDA graph) left device error flags in the index."""
+    _check(load().rbc_search_check(index.handle, _stream_of(stream, True)))
 
 
 def trim_workspace() -> None:

@@ -159,6 +159,16 @@ cudaMemPool_t workspace_pool() {
 }
 
 // Stream-ordered scratch released when the arena goes out of scope.
+// whether work enqueued on `st` is being recorded into a graph
+bool stream_capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
 // Workspace bytes this thread's arenas hold, and the peak since the last
 // reset (reported per search as rbc_search_stats::workspace_bytes).
 thread_local int64_t t_ws_cur = 0;
@@ -169,7 +179,10 @@ struct Arena {
   cudaMemPool_t pool;
   std::vector<void*> ptrs;
   int64_t held = 0;
-  explicit Arena(cudaStream_t s) : st(s), pool(workspace_pool()) {}
+  // under stream capture the allocations become graph memory nodes of the
+  // default pool
+  explicit Arena(cudaStream_t s)
+      : st(s), pool(stream_capturing(s) ? nullptr : workspace_pool()) {}
   ~Arena() {
     for (void* p : ptrs) cudaFreeAsync(p, st);
     t_ws_cur -= held;
@@ -315,6 +328,17 @@ thread_local const int* t_stats_counters_dev = nullptr;
 int stats_publish(const Counters& cn, int64_t queries, int64_t items, int64_t host_pairs, Arena& ar,
                   cudaStream_t st, int64_t host_kept = -1) {
   StatsBlock*& t_stats_host = t_stats_holder.p;
+  if (!t_stats_host && stream_capturing(st)) {
+    // no pinned landing block yet, and none can be allocated while a graph
+    // is recorded: this search reports host-side statistics only
+    memset(&t_stats_fixed, 0, sizeof(t_stats_fixed));
+    t_stats_fixed.queries = queries;
+    t_stats_fixed.stage2_items = items;
+    t_stats_fixed.kernel_launches = t_launches;
+    t_stats_pending = false;
+    t_stats_counters_dev = nullptr;
+    return RBC_OK;
+  }
   if (!t_stats_host) {
     void* p = nullptr;
     RBC_CUDA(cudaMallocHost(&p, sizeof(StatsBlock)));
@@ -1536,11 +1560,12 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   }
   RBC_TRY(ar.alloc(&arena_ovf, 1));
   int* fb_rows;
-  int *lc, *lc2, *fb2, *srows, *srows2;
+  int *lc, *lc2, *fb2, *srows, *srows2, *n_dense;
   RBC_TRY(ar.alloc(&fb_rows, mb));
   RBC_TRY(ar.alloc(&lc, 8));
   RBC_TRY(ar.alloc(&fb2, mb));
   RBC_TRY(ar.alloc(&lc2, 8));
+  RBC_TRY(ar.alloc(&n_dense, 1));
   RBC_TRY(ar.alloc(&srows, mb));  // queries whose survivors are re-ranked in a stream
   RBC_TRY(ar.alloc(&srows2, mb));
   const int xspan = (int)std::max<int64_t>(4096, (n + 2 * sms - 1) / (2 * sms) / 256 * 256);
@@ -1575,98 +1600,79 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   a.stream_count = lc + 4;
   a.f32 = lp ? 0 : 1;
   a.f32_eps = f32_eps;
-  // the CUDA-core emission appends to the per-query buffers directly
-  int left = lp ? ix->emit_direct_left.load(std::memory_order_relaxed) : 0;
-  bool skip_arena = !lp;
-  while (left > 0 && !skip_arena) {
-    skip_arena = const_cast<rbc_index*>(ix)->emit_direct_left.compare_exchange_weak(left, left - 1);
+  RBC_CUDA(cudaMemsetAsync(cc, 0, mb * sizeof(int), st));
+  RBC_CUDA(cudaMemsetAsync(arena_ovf, 0, sizeof(int), st));
+  RBC_CUDA(cudaMemsetAsync(lc, 0, 8 * sizeof(int), st));
+  RBC_CUDA(cudaMemsetAsync(lc2, 0, 8 * sizeof(int), st));
+  EmitOut eo{thr, cs, cr, cc, CAND_CAP};
+  EmitOut eo_arena = eo;
+  if (lp) {
+    eo_arena.arena = arena;
+    eo_arena.arena_seg = arena_seg;
+    eo_arena.arena_cnt = arena_cnt;
+    eo_arena.arena_ovf = arena_ovf;
   }
-  for (int attempt = skip_arena ? 1 : 0;; ++attempt) {
-    const bool direct = attempt > 0;
-    RBC_CUDA(cudaMemsetAsync(cc, 0, mb * sizeof(int), st));
-    RBC_CUDA(cudaMemsetAsync(arena_ovf, 0, sizeof(int), st));
-    RBC_CUDA(cudaMemsetAsync(lc, 0, 8 * sizeof(int), st));
-    RBC_CUDA(cudaMemsetAsync(lc2, 0, 8 * sizeof(int), st));
-    EmitOut eo{thr, cs, cr, cc, CAND_CAP};
-    EmitOut eo_arena = eo;
-    if (!direct) {
-      eo_arena.arena = arena;
-      eo_arena.arena_seg = arena_seg;
-      eo_arena.arena_cnt = arena_cnt;
-      eo_arena.arena_ovf = arena_ovf;
-    }
-    tmark(1, st);
-    if (lp)
-      RBC_TRY(launch_bf_tc_emit(Qm, Xm, items, choff + n_r, max_items,
-                                reinterpret_cast<const int*>(pairs), 2, eo_arena, sms, st, dev_err,
-                                ix->norm_fold_col));
-    else
-      RBC_TRY(launch_bf_simt_emit(Qb, ix->X32, d, metric, items, choff + n_r, max_items,
-                                  reinterpret_cast<const int*>(pairs), 2, eo, 2 * sms, st));
-    if (!direct)
-      RBC_TRY(launch_scatter_hits(arena, arena_lane, arena_cnt, (int)nslices, cs, cr, cc,
-                                  CAND_CAP, st));
-    tmark(2, st);
-    // exact re-rank of the candidates; overflowing queries are collected,
-    // queries with more survivors than shared memory holds are streamed
-    RBC_TRY(launch_select_cands(a, st));
-    RBC_TRY(launch_select_stream(a, (int)mb, st));
-    tmark(3, st);
-    int early[3] = {0, 0, 0};  // overflowing rows, device error flags, arena overflow
-    RBC_CUDA(cudaMemcpyAsync(&early[0], lc, sizeof(int), cudaMemcpyDeviceToHost, st));
-    RBC_CUDA(cudaMemcpyAsync(&early[1], dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    RBC_CUDA(cudaMemcpyAsync(&early[2], arena_ovf, sizeof(int), cudaMemcpyDeviceToHost, st));
-    RBC_CUDA(cudaStreamSynchronize(st));
-    if (early[1]) {
-      set_error("windowed stage two reported device error flags 0x%x", (unsigned)early[1]);
-      return (early[1] & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
-    }
-    if (!direct && early[2]) {
-      // an arena slice overflowed: emit again directly, and so do the
-      // index's next searches (a run twice as long as the last one)
-      rbc_index* mix = const_cast<rbc_index*>(ix);
-      const int run = std::min(1024, std::max(8, 2 * mix->emit_direct_run.load()));
-      mix->emit_direct_run.store(run, std::memory_order_relaxed);
-      mix->emit_direct_left.store(run, std::memory_order_relaxed);
-      continue;
-    }
-    if (early[0] > mb / 16 + 64) {
-      // Many overflowing queries (clustered data whose points tie within the
-      // rounding slack by the thousand): a dense pass would overflow again,
-      // so they go straight to the FP32 exact search over their own lists.
-      RBC_TRY(launch_add_ints(cn.c, lc, 3, st));
-      RBC_TRY(launch_sum_i32(cc, mb, cn.sums + 3, st));
-      RBC_TRY(fallback_rbc_f32(ix, Qb, fb_rows, early[0], nullptr, k, ids, dist, cn.c + 4, ar,
-                               st, g));
-      break;
-    }
-    if (early[0] == 0) {  // no query overflowed its candidate buffer: done
-      RBC_TRY(launch_add_ints(cn.c, lc, 3, st));
-      RBC_TRY(launch_sum_i32(cc, mb, cn.sums + 3, st));
-      break;
-    }
-    // Few overflowing queries (count in lc[0], on the device): k of their
-    // stored candidates give a much tighter threshold; emit again for them
-    // alone against the whole list storage (direct appends) and finish them.
-    RBC_TRY(launch_overflow_rethreshold(fb_rows, lc, mb, cs, cc, CAND_CAP, k, ql.norm, ql.err,
-                                        ix->lp_max, d, thr, st, f32_eps, metric));
-    RBC_TRY(launch_dense_emit_items(lc, n, xspan, max2, items2, n_items2, st));
-    if (lp)
-      RBC_TRY(launch_bf_tc_emit(Qm, Xm, items2, n_items2, max2, fb_rows, 1, eo, sms, st, dev_err,
-                                ix->norm_fold_col));
-    else
-      RBC_TRY(launch_bf_simt_emit(Qb, ix->X32, d, metric, items2, n_items2, max2, fb_rows, 1, eo,
-                                  2 * sms, st));
-    CandSelectArgs a2 = a;
-    a2.rows = fb_rows;
-    a2.nrows_dev = lc;
-    a2.nrows = (int)mb;
-    a2.fallback_rows = fb2;
-    a2.counters = lc2;
-    a2.stream_rows = srows2;
-    a2.stream_count = lc2 + 4;
-    RBC_TRY(launch_select_cands(a2, st));
-    RBC_TRY(launch_select_stream(a2, (int)mb, st));
+  tmark(1, st);
+  // the CUDA-core emission appends to the per-query buffers directly
+  if (lp)
+    RBC_TRY(launch_bf_tc_emit(Qm, Xm, items, choff + n_r, max_items,
+                              reinterpret_cast<const int*>(pairs), 2, eo_arena, sms, st, dev_err,
+                              ix->norm_fold_col));
+  else
+    RBC_TRY(launch_bf_simt_emit(Qb, ix->X32, d, metric, items, choff + n_r, max_items,
+                                reinterpret_cast<const int*>(pairs), 2, eo, 2 * sms, st));
+  if (lp)
+    RBC_TRY(launch_scatter_hits(arena, arena_lane, arena_cnt, (int)nslices, cs, cr, cc, CAND_CAP,
+                                st));
+  tmark(2, st);
+  // exact re-rank of the candidates; overflowing queries are collected,
+  // queries with more survivors than shared memory holds are streamed
+  RBC_TRY(launch_select_cands(a, st));
+  RBC_TRY(launch_select_stream(a, (int)mb, st));
+  tmark(3, st);
+  // Overflowing queries (count lc[0], on the device).  Up to mb / 16 + 64 of
+  // them: k of their stored candidates give a much tighter threshold; they
+  // are emitted again alone against the whole list storage (direct appends)
+  // and finished.  More than that (clustered data whose points tie within
+  // the rounding slack by the thousand: a dense pass would overflow again)
+  // go straight to the exact finish below.  Every launch here reads its
+  // count on the device, so with no overflow they find no work.
+  RBC_TRY(launch_overflow_split(fb_rows, lc, (int)mb, (int)(mb / 16 + 64), n_dense, fb2, lc2, st));
+  RBC_TRY(launch_overflow_rethreshold(fb_rows, n_dense, mb, cs, cc, CAND_CAP, k, ql.norm, ql.err,
+                                      ix->lp_max, d, thr, st, f32_eps, metric));
+  RBC_TRY(launch_dense_emit_items(n_dense, n, xspan, max2, items2, n_items2, st));
+  if (lp)
+    RBC_TRY(launch_bf_tc_emit(Qm, Xm, items2, n_items2, max2, fb_rows, 1, eo, sms, st, dev_err,
+                              ix->norm_fold_col));
+  else
+    RBC_TRY(launch_bf_simt_emit(Qb, ix->X32, d, metric, items2, n_items2, max2, fb_rows, 1, eo,
+                                2 * sms, st));
+  CandSelectArgs a2 = a;
+  a2.rows = fb_rows;
+  a2.nrows_dev = n_dense;
+  a2.nrows = (int)mb;
+  a2.fallback_rows = fb2;
+  a2.counters = lc2;
+  a2.stream_rows = srows2;
+  a2.stream_count = lc2 + 4;
+  RBC_TRY(launch_select_cands(a2, st));
+  RBC_TRY(launch_select_stream(a2, (int)mb, st));
+  RBC_TRY(launch_add_ints(cn.c, lc, 3, st));
+  RBC_TRY(launch_add_ints(cn.c + 4, lc2, 3, st));
+  RBC_TRY(launch_sum_i32(cc, mb, cn.sums + 3, st));
+  // Rows still left (fb2, count lc2[0]): more points than a buffer holds tie
+  // within rounding.  Outside stream capture the count comes back and they
+  // take the FP32 exact search over their surviving lists; a recorded
+  // search reads nothing back: they are finished on the device by the FP64
+  // band pass over the whole database, with g(q) bounding the band, and the
+  // device error flags go to the index for rbc_search_check.
+  if (stream_capturing(st)) {
+    BandArgs bb = band_args(fb2, lc2, Qb, nullptr, ix->X32, ix->members, n, d, k, metric, ids,
+                            dist);
+    bb.kth_bound = g;
+    RBC_TRY(launch_band(bb, (int)mb, st));
+    RBC_TRY(launch_or_flags(ix->dev_status, dev_err, st));
+  } else {
     int host[2] = {0, 0};  // rows left for the FP32 search, device error flags
     RBC_CUDA(cudaMemcpyAsync(&host[0], lc2, sizeof(int), cudaMemcpyDeviceToHost, st));
     RBC_CUDA(cudaMemcpyAsync(&host[1], dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -1675,14 +1681,8 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
       set_error("windowed stage two reported device error flags 0x%x", (unsigned)host[1]);
       return (host[1] & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
     }
-    RBC_TRY(launch_add_ints(cn.c, lc, 3, st));
-    RBC_TRY(launch_add_ints(cn.c + 4, lc2, 3, st));
-    RBC_TRY(launch_sum_i32(cc, mb, cn.sums + 3, st));
-    // more points than a buffer holds tie within rounding: the FP32 exact
-    // search over those queries' surviving lists
     if (host[0] > 0)
       RBC_TRY(fallback_rbc_f32(ix, Qb, fb2, host[0], nullptr, k, ids, dist, cn.c + 4, ar, st, g));
-    break;
   }
   tmark(4, st);
   taccumulate();
@@ -2057,8 +2057,12 @@ int rbc_build(const float* X, int64_t n, int32_t d, int32_t n_r, int32_t s, int3
   {
     Arena ar(st);
     const float* Xdev = X;
-    rc = RBC_OK;
-    if (!is_device_ptr(X)) {
+    rc = ix->alloc(&ix->dev_status, 1);
+    if (rc == RBC_OK) {
+      cudaError_t e = cudaMemsetAsync(ix->dev_status, 0, sizeof(uint32_t), st);
+      if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemsetAsync", __FILE__, __LINE__);
+    }
+    if (rc == RBC_OK && !is_device_ptr(X)) {
       float* x = nullptr;
       rc = ar.alloc(&x, n * d);
       if (rc == RBC_OK) {
@@ -2104,6 +2108,23 @@ int rbc_search(const rbc_index* ix, const float* Q, int64_t m, int32_t k, int64_
   t_ws_peak = t_ws_cur;
   int64_t items = 0;
   const bool window = search_uses_window(ix);
+  if (stream_capturing(st)) {
+    // a recorded search may read nothing back: the windowed plan only, with
+    // device-resident inputs and outputs and no phase timing
+    if (!window) {
+      set_error("rbc_search: under stream capture the index must use the windowed plan "
+                "(exact mode, FP32 / bf16 / fp16 storage)");
+      return RBC_ERR_UNSUPPORTED;
+    }
+    if (m > 0 && (!is_device_ptr(Q) || !is_device_ptr(out_ids) || !is_device_ptr(out_dist))) {
+      set_error("rbc_search: under stream capture Q and the outputs must be device memory");
+      return RBC_ERR_ARG;
+    }
+    if (t_timing.on) {
+      set_error("rbc_search: phase timing (rbc_set_timing) cannot be recorded in a graph");
+      return RBC_ERR_UNSUPPORTED;
+    }
+  }
   // the windowed search sizes its pair arrays by batch x n_r
   const int64_t batch = search_batch_size(ix, window);
   {
@@ -2133,6 +2154,20 @@ int rbc_search(const rbc_index* ix, const float* Q, int64_t m, int32_t k, int64_
   }
   t_stats_fixed.workspace_bytes = t_ws_peak - ws0;
   return RBC_OK;
+}
+
+int rbc_search_check(const rbc_index* ix, void* stream) {
+  if (!ix) {
+    set_error("rbc_search_check: NULL index");
+    return RBC_ERR_ARG;
+  }
+  RBC_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  uint32_t f = 0;
+  RBC_CUDA(cudaMemcpy(&f, ix->dev_status, sizeof(f), cudaMemcpyDeviceToHost));
+  if (!f) return RBC_OK;
+  RBC_CUDA(cudaMemset(ix->dev_status, 0, sizeof(f)));
+  set_error("a recorded search reported device error flags 0x%x", (unsigned)f);
+  return (f & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
 }
 
 int rbc_search_workspace(const rbc_index* ix, int64_t m, int32_t k, int64_t* bytes) {

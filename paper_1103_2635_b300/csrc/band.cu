@@ -70,11 +70,17 @@ __global__ void __launch_bounds__(BAND_THREADS) band_kernel(BandArgs a) {
     __syncthreads();  // the previous row's readers of sq and the lists are done
     for (int i = tid; i < d; i += BAND_THREADS) sq[i] = a.Q32[(int64_t)p * a.ld + i];
     if (tid < BAND_GROUPS) s_n[tid] = 0;
-    const float rk = a.out_dist[orow * k + k - 1];
-    // the band: FP32 values at most r_k (1 + eps) / (1 - eps), rounded up
-    const float thr = rk < INFINITY
-                          ? rk * (1.0f + a.eps) / (1.0f - a.eps) * (1.0f + 8.0f * BAND_U32)
+    // the band: FP32 values at most r_k (1 + eps) / (1 - eps), rounded up;
+    // given a bound U of the true k-th distance instead: U (1 + eps)
+    float thr;
+    if (a.kth_bound) {
+      const float ub = a.kth_bound[p];
+      thr = ub < INFINITY ? ub * (1.0f + a.eps) * (1.0f + 8.0f * BAND_U32) : INFINITY;
+    } else {
+      const float rk = a.out_dist[orow * k + k - 1];
+      thr = rk < INFINITY ? rk * (1.0f + a.eps) / (1.0f - a.eps) * (1.0f + 8.0f * BAND_U32)
                           : INFINITY;
+    }
     __syncthreads();
     const int64_t iters = (e - b + BAND_GROUPS - 1) / BAND_GROUPS;  // the same for every warp
     for (int64_t it = 0; it < iters; ++it) {

@@ -22,7 +22,8 @@
 // itself returns the maximum of the raw accumulators (tcgen05.ld.red), and
 // only when that reaches -T(q) / 2 does a lane walk the chunk and emit the
 // qualifying (score, row) pairs: into its own slice of a hit arena (no
-// atomics; a post-pass moves them to the per-query buffers), or, in the
+// atomics; a post-pass moves them to the per-query buffers; the hits of a
+// full slice go to the query's buffer directly, one atomic each), or, in the
 // instance for direct appends, into q's candidate buffer with one atomic per
 // chunk.  When rows have two spare padding columns, the norm pair lives in
 // them instead (FOLD) and no norm block or norm MMA is needed.  The
@@ -466,7 +467,16 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
                 const int j = __ffs(mask) - 1;
                 mask &= mask - 1;
                 const float v = __uint_as_float(pick32(raw[c], j));
-                if (nhits < lsub) hits[nhits] = make_int4(myq, cb + j, __float_as_int(-2.0f * v), 0);
+                if (nhits < lsub) {
+                  hits[nhits] = make_int4(myq, cb + j, __float_as_int(-2.0f * v), 0);
+                } else {
+                  // the slice is full: this hit goes straight to the row's buffer
+                  const int pos = atomicAdd(cc, 1);
+                  if (pos < cap) {
+                    cs[pos] = -2.0f * v;
+                    cr[pos] = cb + j;
+                  }
+                }
                 ++nhits;
               }
             } else {

@@ -34,14 +34,10 @@ struct rbc_index {
   int norm_fold_col = -1;     // >= 0: Xlp carries -|x~|^2 / 2 in columns col, col + 1
   float* xscale = nullptr;    // FP8: [list_entries + NORM_PAD] per-row power-of-two scales
   float* rscale = nullptr;    // FP8: [n_r]
-  // windowed search: searches left that emit their candidates directly into
-  // the per-query buffers instead of through the hit arena.  A batch whose
-  // arena overflowed (a data set that emits thousands of candidates per
-  // query, unevenly over the arena's per-thread slices) sets it to a run
-  // length that starts at 8 and doubles with every further overflow (at most
-  // 1024), so the next searches skip the arena attempt that would fail again.
-  std::atomic<int> emit_direct_left{0};
-  std::atomic<int> emit_direct_run{0};
+  // device error flags of searches that could not report them when they
+  // returned (searches recorded under stream capture): OR-ed in on the
+  // device, read and cleared by rbc_search_check
+  uint32_t* dev_status = nullptr;
 
   template <typename T>
   int alloc(T** out, int64_t count) {

@@ -98,8 +98,9 @@ struct EmitOut {
   // into 32 lane slices; a thread appends (query, row, score bits, 0) records
   // to its slice with a count kept in a register (no atomics), writes the
   // count to arena_cnt[(b * ARENA_SUBSEG + warp) * 32 + lane] and sets
-  // *arena_ovf if its slice overflowed; launch_scatter_hits then fills the
-  // per-query buffers.  arena == nullptr: append to them directly.
+  // *arena_ovf if its slice overflowed (the hits past a full slice are
+  // appended to the per-query buffers directly); launch_scatter_hits then
+  // fills the per-query buffers.  arena == nullptr: append to them directly.
   int4* arena = nullptr;
   int arena_seg = 0;
   int* arena_cnt = nullptr;
@@ -111,6 +112,11 @@ constexpr int ARENA_SUBSEG = 16;  // arena parts per CTA (at least its epilogue 
 int launch_scatter_hits(const int4* arena, int arena_seg, const int* arena_cnt, int nseg,
                         float* cand_score, int* cand_row, int* cand_cnt, int cap,
                         cudaStream_t st);
+// overflowing rows[0 .. *n_dev) (at most max_rows): *n_dense = *n_dev if it
+// is at most lim (they take the dense re-emission pass), else 0, with the
+// rows copied to rest and *rest_n = *n_dev (they go to the exact finish)
+int launch_overflow_split(const int* rows, const int* n_dev, int max_rows, int lim, int* n_dense,
+                          int* rest, int* rest_n, cudaStream_t st);
 // the query of an item's row i is pair_q[(pair_begin + i) * pair_stride].
 // fold_col >= 0: the database rows carry -|x~|^2 / 2 as a (high, low) pair
 // in padding columns fold_col, fold_col + 1 (launch_fold_norm), so no norm
@@ -200,6 +206,10 @@ struct BandArgs {
   float eps;                 // relative bound of the FP32 re-rank that wrote out_dist
   int64_t* out_ids;
   float* out_dist;
+  // optional, per buffer row: an upper bound of the row's true k-th
+  // neighbour distance, used instead of the k-th distance in out_dist (rows
+  // for which no select step wrote k points)
+  const float* kth_bound = nullptr;
 };
 // grid over at most max_rows rows (the count itself is read on the device)
 int launch_band(const BandArgs& a, int max_rows, cudaStream_t st);
@@ -427,6 +437,8 @@ int exclusive_scan_scratch_ints(int n);
 int launch_exclusive_scan(const int* in, int n, int* out, cudaStream_t st, int* scratch = nullptr);
 // dst[i] += src[i] for i < n (n <= 32)
 int launch_add_ints(int* dst, const int* src, int n, cudaStream_t st);
+// *dst |= *src (device error flags)
+int launch_or_flags(uint32_t* dst, const uint32_t* src, cudaStream_t st);
 // sum over query tiles of (tile rows) x (tile union points)
 int launch_sum_pairs(const int64_t* tile_points, int64_t m, unsigned long long* out,
                      cudaStream_t st);

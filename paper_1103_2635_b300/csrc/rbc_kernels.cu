@@ -515,6 +515,16 @@ int launch_exclusive_scan(const int* in, int n, int* out, cudaStream_t st, int* 
   return RBC_OK;
 }
 
+__global__ void or_flags_kernel(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src) {
+  if (threadIdx.x == 0 && *src) atomicOr(dst, *src);
+}
+
+int launch_or_flags(uint32_t* dst, const uint32_t* src, cudaStream_t st) {
+  or_flags_kernel<<<1, 32, 0, st>>>(dst, src);
+  RBC_LAUNCH_CHECK("or_flags_kernel");
+  return RBC_OK;
+}
+
 int launch_add_ints(int* dst, const int* src, int n, cudaStream_t st) {
   add_ints_kernel<<<1, 32, 0, st>>>(dst, src, n);
   RBC_LAUNCH_CHECK("add_ints_kernel");

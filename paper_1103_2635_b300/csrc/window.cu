@@ -491,6 +491,25 @@ __global__ void dense_emit_items_kernel(const int* __restrict__ n_dev, int64_t x
   }
 }
 
+// The overflowing queries of the windowed select, rows[0 .. *n): up to lim of
+// them take the dense re-emission pass (*n_dense = *n); more than lim (data
+// whose points tie within the rounding slack by the thousand, where a dense
+// pass would overflow again) go straight on to the exact finish: *n_dense =
+// 0, rest = rows, *rest_n = *n.
+__global__ void overflow_split_kernel(const int* __restrict__ rows, const int* __restrict__ n_dev,
+                                      int lim, int* __restrict__ n_dense, int* __restrict__ rest,
+                                      int* __restrict__ rest_n) {
+  const int n = *n_dev;
+  const bool dense = n <= lim;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *n_dense = dense ? n : 0;
+    if (!dense) *rest_n = n;
+  }
+  if (dense) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    rest[i] = rows[i];
+}
+
 // Hit arena -> per-query candidate buffers.
 __global__ void scatter_hits_kernel(const int4* __restrict__ arena, int arena_seg,
                                     const int* __restrict__ arena_cnt, int64_t nseg,
@@ -632,6 +651,14 @@ int launch_dense_emit_items(const int* n_dev, int64_t x_rows, int xspan, int max
   dense_emit_items_kernel<<<64, 256, 0, st>>>(n_dev, x_rows, xspan, nsplit, max_items, items,
                                               num_items);
   RBC_LAUNCH_CHECK("dense_emit_items_kernel");
+  return RBC_OK;
+}
+
+int launch_overflow_split(const int* rows, const int* n_dev, int max_rows, int lim, int* n_dense,
+                          int* rest, int* rest_n, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>(64, ((int64_t)max_rows + 255) / 256 + 1);
+  overflow_split_kernel<<<blocks, 256, 0, st>>>(rows, n_dev, lim, n_dense, rest, rest_n);
+  RBC_LAUNCH_CHECK("overflow_split_kernel");
   return RBC_OK;
 }
 

@@ -265,10 +265,9 @@ def test_window_candidate_overflow_goes_to_fp32_research():
 
 
 def test_searches_after_an_arena_overflow_agree():
-    # the 9000 copies overflow the emission's hit arena: that batch is emitted
-    # again with direct appends, the index's next searches emit directly (a
-    # run of 8, then 16 after the retry overflows again), and every one of
-    # them gives the same answer
+    # the 9000 copies overflow the emission's hit arena: the hits past a full
+    # slice go to the query buffers directly, and every search gives the
+    # same answer
     X = synth.iid_normal(30000, 24, 3)
     X[5000:14000] = X[5000]
     Q = np.concatenate([X[5000:5001].repeat(3, 0), synth.iid_normal(300, 24, 4)]).astype(np.float32)
