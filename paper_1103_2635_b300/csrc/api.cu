@@ -1493,19 +1493,14 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   // surviving (q, r) pairs binned by (r, bucket of rho(q, r))
   const int NB = window_buckets();
   const int64_t nbins = (int64_t)n_r * NB;
-  unsigned *rmin, *rmax;
-  int *qkept, *counts, *totals, *bin_off;
-  RBC_TRY(ar.alloc(&rmin, n_r));
-  RBC_TRY(ar.alloc(&rmax, n_r));
-  RBC_TRY(ar.alloc(&qkept, mb));
-  RBC_TRY(ar.alloc(&counts, window_pair_blocks(mb) * nbins));
+  int *totals, *bin_off, *blk_off;
   RBC_TRY(ar.alloc(&totals, nbins));
   RBC_TRY(ar.alloc(&bin_off, nbins + 1));
+  RBC_TRY(ar.alloc(&blk_off, window_block_offsets(mb, n_r)));
   int* scan_scratch;
   RBC_TRY(ar.alloc(&scan_scratch, exclusive_scan_scratch_ints((int)nbins)));
-  RBC_TRY(launch_window_pairs_count(D, mb, n_r, g, g1, ix->psi, simt_eps(d), rmin, rmax, qkept,
-                                    counts, totals, bin_off, st, scan_scratch));
-  RBC_TRY(launch_sum_i32(qkept, mb, cn.sums, st));
+  RBC_TRY(launch_window_pairs_count(D, mb, n_r, g, g1, ix->psi, simt_eps(d), totals, bin_off,
+                                    blk_off, cn.sums, st, scan_scratch));
   // pair arrays sized by the bound mb x n_r (batches are cut so that it stays
   // within WINDOW_MAX_PAIRS), so no count needs to come back to the host
   const int64_t pair_cap = mb * n_r;
@@ -1515,8 +1510,8 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   RBC_TRY(launch_score_threshold(g, ql.norm, ql.err, ix->lp_max, d, mb, thr, st, f32_eps, metric));
   int2* pairs;  // (query, rho(q, r) bits)
   RBC_TRY(ar.alloc(&pairs, pair_cap));
-  RBC_TRY(launch_window_pairs_scatter(D, mb, n_r, g, g1, ix->psi, simt_eps(d), rmin, rmax, counts,
-                                      bin_off, pairs, st));
+  RBC_TRY(launch_window_pairs_scatter(D, mb, n_r, g, g1, ix->psi, simt_eps(d), bin_off, blk_off,
+                                      pairs, st));
   // work items: chunks of TQ pairs, each with the union of its windows
   const int max_items = (int)std::min<int64_t>(pair_cap / TQ + n_r, INT32_MAX);
   int *ccount, *choff;
@@ -1749,8 +1744,8 @@ int64_t bound_window_batch(const rbc_index* ix, int64_t mb, int k) {
   b += bound_own_list(ix, mb);                               // pass A (tensor cores)
   b += bound_group(ix, mb, true) + cdiv(mb, TQ) * TQ * 2 * MAX_C * 8 +
        std::min<int64_t>(ix->n_r, mb) * TQ * 2 * MAX_C * 8;  // pass A (CUDA cores)
-  b += mb * 4 + n_r * 8 + mb * 4;                            // g, rmin, rmax, qkept
-  b += window_pair_blocks(mb) * nbins * 4 + nbins * 8 + 4;   // bin counts, totals, offsets
+  b += mb * 4;                                               // g
+  b += nbins * 8 + 4 + window_block_offsets(mb, n_r) * 4;   // totals, offsets, block offsets
   b += ((int64_t)exclusive_scan_scratch_ints((int)nbins)) * 4; // their scan
   b += mb * 4 + mb * n_r * 8;                                // thr, pairs
   b += n_r * 8 + 4 + (mb * n_r / TQ + n_r) * (int64_t)sizeof(EmitItem);  // chunks, items

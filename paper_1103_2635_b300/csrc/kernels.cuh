@@ -276,21 +276,21 @@ int launch_own_kth_lp(const float* ps, const int* pi, int C, const int* qsrc, in
                       int k, const float* Q32, const float* X32, int d, int metric, float rel,
                       float* own, cudaStream_t st);
 // Kept (q, r) pairs binned by (r, bucket of the window start rho(q, r) - g(q)),
-// window_buckets() per r: rmin/rmax [n_r] (order-preserving keys of the
-// extreme window starts), q_kept [m], counts
-// [n_r nb][window_pair_blocks(m)] (per bin and query block, then the block's
-// prefix within the bin), totals [n_r nb], bin_off [n_r nb + 1]; then the pairs
-// themselves: pairs[i] = (query, rho(q, r) as float bits).
+// window_buckets() per r over [0, psi_r]: totals [n_r nb] (pairs per bin),
+// bin_off [n_r nb + 1] (their exclusive prefix), blk_off
+// [window_block_offsets(m, n_r)] (each pass block's offset within each bin),
+// *kept_sum += the kept pairs; then the pairs themselves, each bin's run
+// from bin_off: pairs[i] = (query, rho(q, r) as float bits).
 int window_buckets();
 int64_t window_pair_blocks(int64_t m);
+int64_t window_block_offsets(int64_t m, int n_r);
 int launch_window_pairs_count(const float* D, int64_t m, int n_r, const float* g,
-                              const float* g1, const float* psi_plus, float rel, unsigned* rmin,
-                              unsigned* rmax, int* q_kept, int* counts, int* totals, int* bin_off,
+                              const float* g1, const float* psi_plus, float rel, int* totals,
+                              int* bin_off, int* blk_off, unsigned long long* kept_sum,
                               cudaStream_t st, int* scan_scratch = nullptr);
 int launch_window_pairs_scatter(const float* D, int64_t m, int n_r, const float* g,
                                 const float* g1, const float* psi_plus, float rel,
-                                const unsigned* rmin, const unsigned* rmax, int* counts,
-                                const int* bin_off, int2* pairs, cudaStream_t st);
+                                const int* bin_off, int* blk_off, int2* pairs, cudaStream_t st);
 // chunks of TQ pairs per representative -> items (the chunk's window in the
 // sorted list); stats[0] += window rows, stats[1] += query x row pairs
 int launch_window_items(const int* bin_off, int nb, int n_r, const int2* pairs,

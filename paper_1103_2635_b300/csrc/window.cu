@@ -13,23 +13,23 @@
 // bounds of the values involved, so no needed point is ever cut.
 //
 // The surviving (q, r) pairs are binned by (r, bucket of rho(q, r) - g(q)),
-// the lower end of the query's window -- NB buckets between the smallest and
-// largest of them for each r -- with a counting sort over the implicit pair
-// list, so each r's group comes out ordered by the window start up to the
-// bucket width.  Each group is cut into chunks of up to TQ queries: one work
-// item per chunk, against the union of its queries' windows.  Ordered by
-// window start, consecutive windows overlap almost entirely (ordering by
-// rho(q, r) alone would mix queries of very different g and about double the
-// union).
+// the lower end of the query's window -- NB buckets over [0, psi_r] for each
+// r -- with a counting sort over the implicit pair list, so each r's group
+// comes out ordered by the window start up to the bucket width.  Each group
+// is cut into chunks of up to TQ queries: one work item per chunk, against
+// the union of its queries' windows.  Ordered by window start, consecutive
+// windows overlap almost entirely (ordering by rho(q, r) alone would mix
+// queries of very different g and about double the union).
 //
-// The pair passes read D [m, n_r] in warp tiles of 32 queries x 32
-// representatives through shared memory, so that a lane owns a query and the
-// warp walks the representatives.  The range pass reduces over the warp
-// before it touches shared memory; the count and scatter passes keep the
-// block's bin counters in shared memory (a lane's kept pair takes its slot
-// there), so global memory sees one update per (block, bin), and the pairs of
-// one bin from one block land in consecutive slots.  (Warp-aggregated slot
-// claims, and counts stored block-major, were both measured slower.)
+// The two pair passes (count, scatter) read D [m, n_r] in warp tiles of 32
+// queries x 32 representatives through shared memory, so that a lane owns a
+// query and the warp walks the representatives (a lane per representative,
+// walking the queries, was measured slower: its pair writes scatter over 32
+// bins).  They keep the block's bin counters in shared memory (a lane's kept
+// pair takes its slot there), so global memory sees one atomic per non-empty
+// (block, bin) on an array of n_r NB counters that stays in L2, and the
+// pairs of one bin from one block land in consecutive slots.
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -143,22 +143,11 @@ __device__ __forceinline__ void load_tile(const float* __restrict__ D, int64_t m
   __syncwarp();
 }
 
-// integer key with the order of the float (negative values included)
-__device__ __forceinline__ unsigned fkey(float v) {
-  const unsigned b = __float_as_uint(v);
-  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-__device__ __forceinline__ float fkey_inv(unsigned k) {
-  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
-}
-
 // the binning key of a kept pair: the window's lower end rho(q, r) - g(q)
 __device__ __forceinline__ float window_key(float d, float gh) { return d - gh; }
 
 // The pair passes: block (x, y) covers queries [x * 256, +256) (one warp tile
-// of 32 queries per warp) and representatives [y * RSPAN, +RSPAN); per-block
-// reductions go through shared memory, so global memory sees one update per
-// (block, representative) or (block, bin).
+// of 32 queries per warp) and representatives [y * RSPAN, +RSPAN).
 struct PairCtx {
   int64_t q;
   bool live;
@@ -177,134 +166,87 @@ __device__ __forceinline__ PairCtx pair_ctx(int64_t q0, int lane, int64_t m,
   return c;
 }
 
-// Pass 1: per representative, the smallest and largest binning key of its
-// kept pairs (as order-preserving integer keys); per query its kept count.
-__global__ void __launch_bounds__(WW * 32)
-wrange_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __restrict__ g,
-              const float* __restrict__ g1, const float* __restrict__ psi_plus, float rel,
-              unsigned* __restrict__ rmin, unsigned* __restrict__ rmax, int* __restrict__ q_kept) {
-  __shared__ float tiles[WW][WT][WT + 1];
-  __shared__ unsigned smin[RSPAN], smax[RSPAN];
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rb = blockIdx.y * RSPAN, re = min(n_r, rb + RSPAN);
-  for (int i = threadIdx.x; i < RSPAN; i += blockDim.x) {
-    smin[i] = 0xffffffffu;
-    smax[i] = 0u;
-  }
-  __syncthreads();
-  const int64_t q0 = ((int64_t)blockIdx.x * WW + wid) * WT;
-  if (q0 < m) {
-    const PairCtx c = pair_ctx(q0, lane, m, g, g1, rel);
-    int kept = 0;
-    for (int r0 = rb; r0 < re; r0 += WT) {
-      load_tile(D, m, n_r, q0, r0, tiles[wid], lane);
-      const int nr = min(WT, re - r0);
-      for (int rr = 0; rr < nr; ++rr) {
-        const float v = tiles[wid][lane][rr];
-        const bool kp = c.live && keep_pair(v, c.lo, c.gh, psi_plus[r0 + rr], c.lemma);
-        kept += kp;
-        // warp reductions first: one shared-memory update per (warp, r)
-        const unsigned key = fkey(window_key(v, c.gh));
-        const unsigned vmin = __reduce_min_sync(0xffffffffu, kp ? key : 0xffffffffu);
-        const unsigned vmax = __reduce_max_sync(0xffffffffu, kp ? key : 0u);
-        if (lane == 0 && vmin != 0xffffffffu) {
-          atomicMin(&smin[r0 + rr - rb], vmin);
-          atomicMax(&smax[r0 + rr - rb], vmax);
-        }
-      }
-      __syncwarp();
-    }
-    if (c.live && kept) atomicAdd(&q_kept[c.q], kept);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < re - rb; i += blockDim.x) {
-    if (smin[i] != 0xffffffffu) {  // some pair of r kept in this block
-      atomicMin(&rmin[rb + i], smin[i]);
-      atomicMax(&rmax[rb + i], smax[i]);
-    }
-  }
+__device__ __forceinline__ int bucket_of(float key, float scale) {
+  return min(NBK - 1, max(0, (int)(key * scale)));
 }
 
-__device__ __forceinline__ int bucket_of(float v, float lo, float scale) {
-  return min(NBK - 1, max(0, (int)((v - lo) * scale)));
-}
-
-
-// Passes 2 and 3.  Count: every (r, bucket) bin of the block's pairs ->
-// counts[bin][block x].  Scatter: the pairs, at the bins' offsets plus the
-// block's prefix (counts[bin][block x] after the column scan).
+// The two pair passes.  Count: the block's kept pairs per (r, bucket) bin in
+// shared memory, then one global atomic per non-empty (block, bin) into
+// bin_ctr, whose old value -- the block's offset within the bin -- is kept
+// in blk_off (one contiguous row of n_r NB per block), and the block's kept
+// count into *kept_sum.  Scatter: each bin's slots start at bin_off plus
+// the block's offset, and the pairs go to those slots.  The bins of r cover the
+// window starts rho(q, r) - g(q) in [0, psi_r] (every kept pair has a start
+// of at most psi_r, and all starts below 0 begin the window at the list's
+// first entry).  The order of the blocks' slot runs within a bin is that of
+// their atomics: work items differ between runs, results do not.
 template <bool SCATTER>
 __global__ void __launch_bounds__(WW * 32)
-wbin_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __restrict__ g,
-            const float* __restrict__ g1, const float* __restrict__ psi_plus, float rel,
-            const unsigned* __restrict__ rmin, const unsigned* __restrict__ rmax,
-            int* __restrict__ counts, const int* __restrict__ bin_off,
-            int2* __restrict__ pairs) {
+wpairs_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __restrict__ g,
+              const float* __restrict__ g1, const float* __restrict__ psi_plus, float rel,
+              int* __restrict__ bin_ctr, const int* __restrict__ bin_off,
+              int* __restrict__ blk_off, int2* __restrict__ pairs,
+              unsigned long long* __restrict__ kept_sum) {
   __shared__ float tiles[WW][WT][WT + 1];
   __shared__ int h[RSPAN * NBK];
-  __shared__ float sblo[RSPAN], sscale[RSPAN];
+  __shared__ float spsi[RSPAN], sscale[RSPAN];
+  __shared__ int skept[WW];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rb = blockIdx.y * RSPAN, re = min(n_r, rb + RSPAN);
-  const int64_t nbins = (int64_t)n_r * NBK;
-  const int64_t nqb = gridDim.x;  // counts are [bin][query block]
-  for (int i = threadIdx.x; i < RSPAN * NBK; i += blockDim.x) {
-    const int64_t bin = (int64_t)rb * NBK + i;
-    h[i] = SCATTER ? (bin < nbins ? bin_off[bin] + counts[bin * nqb + blockIdx.x] : 0) : 0;
-  }
+  const int64_t bin0 = (int64_t)rb * NBK;
+  int* brow = blk_off + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * (RSPAN * NBK);
+  for (int i = threadIdx.x; i < RSPAN * NBK; i += blockDim.x)
+    h[i] = SCATTER ? (i < (re - rb) * NBK ? bin_off[bin0 + i] + brow[i] : 0) : 0;
   for (int i = threadIdx.x; i < re - rb; i += blockDim.x) {
-    const float blo = fkey_inv(rmin[rb + i]);
-    const float bhi = fkey_inv(rmax[rb + i]);
-    sblo[i] = blo;
-    sscale[i] = bhi > blo ? (float)NBK / (bhi - blo) : 0.0f;
+    const float ps = psi_plus[rb + i];
+    spsi[i] = ps;
+    sscale[i] = ps > 0.0f ? (float)NBK / ps : 0.0f;
   }
   __syncthreads();
   const int64_t q0 = ((int64_t)blockIdx.x * WW + wid) * WT;
-  if (q0 < m) {
-    const PairCtx c = pair_ctx(q0, lane, m, g, g1, rel);
+  const PairCtx c = pair_ctx(q0, lane, m, g, g1, rel);
+  // one pass over the warp's tiles: count, or (place) take the slots
+  auto walk = [&](bool place) {
+    int kept = 0;
+    if (q0 >= m) return kept;
     for (int r0 = rb; r0 < re; r0 += WT) {
       load_tile(D, m, n_r, q0, r0, tiles[wid], lane);
       const int nr = min(WT, re - r0);
       for (int rr = 0; rr < nr; ++rr) {
         const int rl = r0 + rr - rb;
         const float v = tiles[wid][lane][rr];
-        if (c.live && keep_pair(v, c.lo, c.gh, psi_plus[r0 + rr], c.lemma)) {
-          const int slot = rl * NBK + bucket_of(window_key(v, c.gh), sblo[rl], sscale[rl]);
-          const int pos = atomicAdd(&h[slot], 1);
-          if (SCATTER) pairs[pos] = make_int2((int)c.q, __float_as_int(v));
+        if (c.live && keep_pair(v, c.lo, c.gh, spsi[rl], c.lemma)) {
+          int* hp = &h[rl * NBK + bucket_of(window_key(v, c.gh), sscale[rl])];
+          if (place) {
+            pairs[atomicAdd(hp, 1)] = make_int2((int)c.q, __float_as_int(v));
+          } else {
+            ++kept;
+            atomicAdd(hp, 1);
+          }
         }
       }
       __syncwarp();
     }
+    return kept;
+  };
+  if (SCATTER) {
+    walk(true);
+    return;
   }
-  if (!SCATTER) {
-    __syncthreads();
+  const int kept = walk(false);
+  __syncthreads();
+  {
     for (int i = threadIdx.x; i < (re - rb) * NBK; i += blockDim.x)
-      counts[((int64_t)rb * NBK + i) * nqb + blockIdx.x] = h[i];
-  }
-}
-
-// per bin (one warp): exclusive prefix over the query blocks in place
-// (counts are [bin][query block]), totals[bin] = sum
-__global__ void bin_colscan_kernel(int* __restrict__ counts, int nqb, int64_t nbins,
-                                   int* __restrict__ totals) {
-  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (b >= nbins) return;
-  int* col = counts + b * nqb;
-  int carry = 0;
-  for (int i0 = 0; i0 < nqb; i0 += 32) {
-    const int i = i0 + lane;
-    const int v = i < nqb ? col[i] : 0;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+      brow[i] = h[i] ? atomicAdd(&bin_ctr[bin0 + i], h[i]) : 0;
+    const int wk = __reduce_add_sync(0xffffffffu, kept);
+    if (lane == 0) skept[wid] = wk;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long t = 0;
+      for (int w = 0; w < WW; ++w) t += (unsigned long long)skept[w];
+      if (t) atomicAdd(kept_sum, t);
     }
-    if (i < nqb) col[i] = carry + x - v;
-    carry += __shfl_sync(0xffffffffu, x, 31);
   }
-  if (lane == 0) totals[b] = carry;
 }
 
 // per representative: chunks of TQ pairs in its group
@@ -566,40 +508,34 @@ int launch_own_kth_lp(const float* ps, const int* pi, int C, const int* qsrc, in
 int64_t window_pair_blocks(int64_t m) { return (m + WW * WT - 1) / (WW * WT); }
 
 int launch_window_pairs_count(const float* D, int64_t m, int n_r, const float* g,
-                              const float* g1, const float* psi_plus, float rel, unsigned* rmin,
-                              unsigned* rmax, int* q_kept, int* counts, int* totals, int* bin_off,
+                              const float* g1, const float* psi_plus, float rel, int* totals,
+                              int* bin_off, int* blk_off, unsigned long long* kept_sum,
                               cudaStream_t st, int* scan_scratch) {
   const int64_t nbins = (int64_t)n_r * NBK;
   const int64_t qblocks = window_pair_blocks(m);
+  RBC_CUDA(cudaMemsetAsync(totals, 0, nbins * sizeof(int), st));
   if (qblocks > 0) {
     const dim3 grid((unsigned)qblocks, (n_r + RSPAN - 1) / RSPAN);
-    RBC_CUDA(cudaMemsetAsync(rmin, 0xff, n_r * sizeof(unsigned), st));  // above any key
-    RBC_CUDA(cudaMemsetAsync(rmax, 0, n_r * sizeof(unsigned), st));
-    RBC_CUDA(cudaMemsetAsync(q_kept, 0, m * sizeof(int), st));
-    wrange_kernel<<<grid, WW * 32, 0, st>>>(D, m, n_r, g, g1, psi_plus, rel, rmin, rmax, q_kept);
-    RBC_LAUNCH_CHECK("wrange_kernel");
-    wbin_kernel<false><<<grid, WW * 32, 0, st>>>(D, m, n_r, g, g1, psi_plus, rel, rmin, rmax,
-                                                 counts, nullptr, nullptr);
-    RBC_LAUNCH_CHECK("wbin_kernel");
-    bin_colscan_kernel<<<(unsigned)((nbins * 32 + 255) / 256), 256, 0, st>>>(
-        counts, (int)qblocks, nbins, totals);
-    RBC_LAUNCH_CHECK("bin_colscan_kernel");
-  } else {
-    RBC_CUDA(cudaMemsetAsync(totals, 0, nbins * sizeof(int), st));
+    wpairs_kernel<false><<<grid, WW * 32, 0, st>>>(D, m, n_r, g, g1, psi_plus, rel, totals,
+                                                   nullptr, blk_off, nullptr, kept_sum);
+    RBC_LAUNCH_CHECK("wpairs_kernel");
   }
   return launch_exclusive_scan(totals, (int)nbins, bin_off, st, scan_scratch);
 }
 
+int64_t window_block_offsets(int64_t m, int n_r) {
+  return window_pair_blocks(m) * ((n_r + RSPAN - 1) / RSPAN) * RSPAN * NBK;
+}
+
 int launch_window_pairs_scatter(const float* D, int64_t m, int n_r, const float* g,
                                 const float* g1, const float* psi_plus, float rel,
-                                const unsigned* rmin, const unsigned* rmax, int* counts,
-                                const int* bin_off, int2* pairs, cudaStream_t st) {
+                                const int* bin_off, int* blk_off, int2* pairs, cudaStream_t st) {
   const int64_t qblocks = window_pair_blocks(m);
   if (qblocks == 0) return RBC_OK;
   const dim3 grid((unsigned)qblocks, (n_r + RSPAN - 1) / RSPAN);
-  wbin_kernel<true><<<grid, WW * 32, 0, st>>>(D, m, n_r, g, g1, psi_plus, rel, rmin, rmax, counts,
-                                              bin_off, pairs);
-  RBC_LAUNCH_CHECK("wbin_kernel");
+  wpairs_kernel<true><<<grid, WW * 32, 0, st>>>(D, m, n_r, g, g1, psi_plus, rel, nullptr,
+                                                bin_off, blk_off, pairs, nullptr);
+  RBC_LAUNCH_CHECK("wpairs_kernel");
   return RBC_OK;
 }
 
