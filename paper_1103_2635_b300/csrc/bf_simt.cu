@@ -11,13 +11,15 @@
 // threads per query row merge it into their sorted register lists.  Nothing
 // but the per-(query, thread) top-C lists reaches global memory.
 //
-// Modes: TOPC (the lists above) and STORE (write every distance to a dense
-// [rows, ld] matrix; used for the representative distances of the exact
-// search, Section 5.2, which must be kept).  EXP (l2 top-C only): the
-// expansion |x|^2 - 2 q.x with precomputed FP32 norms instead of the
-// difference form -- one FFMA per dimension instead of a subtraction and an
-// FFMA; its rounding bound is absolute, (d + 4) 2^-23 (|q| + max |x|)^2, and
-// the select step certifies with it (SelectArgs::exp32).
+// EXP (l2 only): the expansion |x|^2 - 2 q.x with precomputed FP32 norms
+// instead of the difference form -- one FFMA per dimension instead of a
+// subtraction and an FFMA; its rounding bound is absolute,
+// (d + 4) 2^-23 (|q| + max |x|)^2, and the select step certifies with it
+// (SelectArgs::exp32).
+//
+// The same file holds the windowed emission kernel on CUDA cores and the
+// distance-matrix kernel of stage one (every distance kept), described
+// where they are defined.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -61,11 +63,10 @@ __device__ __forceinline__ Seg get_seg(const TileWork& w, int si) {
   return Seg{(int32_t)b, (int32_t)e};
 }
 
-template <int METRIC, int C, bool STORE, bool EXP = false>
+template <int METRIC, int C, bool EXP = false>
 __global__ void __launch_bounds__(NTHREADS, 2)
 bf_simt_kernel(const float* __restrict__ Q, const float* __restrict__ X, int d, TileWork w,
-               TopOut out, float* __restrict__ store, int64_t store_ld,
-               const float* __restrict__ xnorm = nullptr) {
+               TopOut out, const float* __restrict__ xnorm = nullptr) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   const int dq = (d + DC - 1) / DC * DC;  // query tile rows, padded to the chunk
@@ -96,11 +97,7 @@ bf_simt_kernel(const float* __restrict__ Q, const float* __restrict__ X, int d, 
     }
 
     TopList<C> top;
-    if (!STORE) top.init();
-
-    // STORE mode: running column of the output matrix (a dense split starts
-    // at its first database row)
-    int store_col = w.items ? 0 : (int)get_seg(w, sb).x_begin;
+    top.init();
     for (int si = sb; si < se; ++si) {
       const Seg sg = get_seg(w, si);
       for (int x0 = sg.x_begin; x0 < sg.x_end; x0 += TX) {
@@ -161,18 +158,7 @@ bf_simt_kernel(const float* __restrict__ Q, const float* __restrict__ X, int d, 
             Ds[(ty * 8 + a) * DS + col] = (col < nx) ? v : INFINITY;
           }
         __syncthreads();
-        if (STORE) {
-          // write rows of the tile to the dense output (coalesced along columns)
-          for (int idx = t; idx < TQ * TX; idx += NTHREADS) {
-            int r = idx / TX;
-            int c = idx % TX;
-            if (r < nq && c < nx) {
-              float v = Ds[r * DS + c];
-              if (METRIC == RBC_L2) v = sqrtf(v);
-              store[(int64_t)(q0 + r) * store_ld + store_col + c] = v;
-            }
-          }
-        } else if (sel_row < nq) {
+        if (sel_row < nq) {
 #pragma unroll 4
           for (int j = 0; j < TX / 2; ++j) {
             int col = 2 * j + sel_half;
@@ -183,10 +169,9 @@ bf_simt_kernel(const float* __restrict__ Q, const float* __restrict__ X, int d, 
             }
           }
         }
-        store_col += nx;
       }
     }
-    if (!STORE && sel_row < nq) {
+    if (sel_row < nq) {
       // partial slot layout: [slot][TQ][NSUB = 2][C]
       int64_t base = (((int64_t)slot * TQ + sel_row) * 2 + sel_half) * C;
 #pragma unroll
@@ -198,15 +183,14 @@ bf_simt_kernel(const float* __restrict__ Q, const float* __restrict__ X, int d, 
   }
 }
 
-template <int METRIC, int C, bool STORE, bool EXP = false>
+template <int METRIC, int C, bool EXP = false>
 int launch_one(const float* Q, const float* X, int d, const TileWork& w, const TopOut& out,
-               float* store, int64_t store_ld, int grid, cudaStream_t st,
-               const float* xnorm = nullptr) {
+               int grid, cudaStream_t st, const float* xnorm = nullptr) {
   const int dq = (d + DC - 1) / DC * DC;
   size_t smem = sizeof(float) * ((size_t)dq * QS + DC * XS + TQ * DS);
-  auto kern = bf_simt_kernel<METRIC, C, STORE, EXP>;
+  auto kern = bf_simt_kernel<METRIC, C, EXP>;
   RBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<grid, NTHREADS, smem, st>>>(Q, X, d, w, out, store, store_ld, xnorm);
+  kern<<<grid, NTHREADS, smem, st>>>(Q, X, d, w, out, xnorm);
   RBC_LAUNCH_CHECK("bf_simt_kernel");
   return RBC_OK;
 }
@@ -215,11 +199,11 @@ template <int METRIC>
 int dispatch_c(int C, const float* Q, const float* X, int d, const TileWork& w, const TopOut& out,
                int grid, cudaStream_t st) {
   switch (C) {
-    case 2: return launch_one<METRIC, 2, false>(Q, X, d, w, out, nullptr, 0, grid, st);
-    case 4: return launch_one<METRIC, 4, false>(Q, X, d, w, out, nullptr, 0, grid, st);
-    case 8: return launch_one<METRIC, 8, false>(Q, X, d, w, out, nullptr, 0, grid, st);
-    case 16: return launch_one<METRIC, 16, false>(Q, X, d, w, out, nullptr, 0, grid, st);
-    case 32: return launch_one<METRIC, 32, false>(Q, X, d, w, out, nullptr, 0, grid, st);
+    case 2: return launch_one<METRIC, 2>(Q, X, d, w, out, grid, st);
+    case 4: return launch_one<METRIC, 4>(Q, X, d, w, out, grid, st);
+    case 8: return launch_one<METRIC, 8>(Q, X, d, w, out, grid, st);
+    case 16: return launch_one<METRIC, 16>(Q, X, d, w, out, grid, st);
+    case 32: return launch_one<METRIC, 32>(Q, X, d, w, out, grid, st);
     default: set_error("bf_simt: unsupported list width %d", C); return RBC_ERR_UNSUPPORTED;
   }
 }
@@ -328,6 +312,163 @@ bf_simt_emit_kernel(const float* __restrict__ Q, const float* __restrict__ X, in
   }
 }
 
+// Distance matrix kernel (STORE): every distance of a query tile against
+// the database rows of the item's segments, written to store[q][col] -- the
+// representative distances of the exact search's stage one (Section 5.2),
+// which are all kept.  A CTA computes 128 x 128 tiles: the query tile stays
+// in shared memory (transposed, [d][TQ]), the database rows pass through in
+// 16-dimension chunks, staged from registers that were loaded while the
+// previous chunk was being used.  Each thread accumulates an 8 x 8 block
+// (rows 4 ty + {0..3} and 64 + 4 ty + {0..3}, the same for columns with tx,
+// so every shared-memory read is one 16-byte load per four values and the
+// two query loads are broadcasts) in the difference form, and writes it
+// from registers (16-byte stores of four consecutive columns).
+constexpr int S_TX = 128;          // database rows per tile
+constexpr int S_DC = 16;           // dimensions per staged chunk
+constexpr int S_QS = TQ + 4;       // row stride of the transposed query tile
+constexpr int S_XS = S_TX + 4;     // row stride of the transposed database chunk
+
+template <int METRIC>
+__global__ void __launch_bounds__(NTHREADS, 2)
+bf_simt_store_kernel(const float* __restrict__ Q, const float* __restrict__ X, int d, TileWork w,
+                     float* __restrict__ store, int64_t store_ld) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  const int dq = (d + S_DC - 1) / S_DC * S_DC;
+  float* Qs = smem;            // [dq][S_QS]
+  float* Xs = Qs + dq * S_QS;  // [S_DC][S_XS]
+  const float4* Q4 = reinterpret_cast<const float4*>(Qs);
+  const float4* X4 = reinterpret_cast<const float4*>(Xs);
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int sc = t & (S_DC - 1);  // staging: dimension of this thread's values
+  const int sr = t >> 4;          // staging: first row (then + 16 j)
+  float xr[8];                    // the next chunk, in flight
+  auto fetch = [&](int fx0, int fnx, int fc0) {
+    const bool cin = fc0 + sc < d;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int r = sr + 16 * j;
+      xr[j] = (cin && r < fnx) ? X[(int64_t)(fx0 + r) * d + fc0 + sc] : 0.f;
+    }
+  };
+  int n_items = w.num_items_dev ? *w.num_items_dev : w.num_items;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    int q0, nq, sb, se, slot;
+    fetch_item(w, item, q0, nq, sb, se, slot);
+    // first non-empty segment
+    int si = sb, x0 = 0, xe = 0;
+    for (; si < se; ++si) {
+      const Seg sg = get_seg(w, si);
+      if (sg.x_end > sg.x_begin) {
+        x0 = sg.x_begin;
+        xe = sg.x_end;
+        break;
+      }
+    }
+    if (si < se) fetch(x0, min(S_TX, xe - x0), 0);
+    __syncthreads();  // the previous item's readers of Qs are done
+    for (int idx = t; idx < TQ * dq; idx += NTHREADS) {
+      const int c = idx % dq;
+      const int r = idx / dq;
+      Qs[c * S_QS + r] = (r < nq && c < d) ? Q[(int64_t)(q0 + r) * d + c] : 0.f;
+    }
+    // running column of the output (a dense split starts at its first row)
+    int store_col = w.items ? 0 : (int)get_seg(w, sb).x_begin;
+    int c0 = 0;
+    float acc[8][8];
+    while (si < se) {
+      const int nx = min(S_TX, xe - x0);
+      // the chunk after this one
+      int nsi = si, nx0 = x0, nxe = xe, nc0 = c0 + S_DC;
+      if (nc0 >= dq) {
+        nc0 = 0;
+        nx0 = x0 + S_TX;
+        if (nx0 >= xe) {
+          for (++nsi; nsi < se; ++nsi) {
+            const Seg sg = get_seg(w, nsi);
+            if (sg.x_end > sg.x_begin) {
+              nx0 = sg.x_begin;
+              nxe = sg.x_end;
+              break;
+            }
+          }
+        }
+      }
+      __syncthreads();  // the previous chunk's readers of Xs are done
+#pragma unroll
+      for (int j = 0; j < 8; ++j) Xs[sc * S_XS + sr + 16 * j] = xr[j];
+      __syncthreads();  // the chunk (and, first, the query tile) is in place
+      if (nsi < se) fetch(nx0, min(S_TX, nxe - nx0), nc0);
+      if (c0 == 0) {
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+      }
+#pragma unroll 4
+      for (int k = 0; k < S_DC; ++k) {
+        const float4 qa = Q4[(c0 + k) * (S_QS / 4) + ty];
+        const float4 qb = Q4[(c0 + k) * (S_QS / 4) + 16 + ty];
+        const float4 xa = X4[k * (S_XS / 4) + tx];
+        const float4 xb = X4[k * (S_XS / 4) + 16 + tx];
+        const float qv[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+        const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) {
+            const float diff = qv[a] - xv[b];
+            if (METRIC == RBC_L2)
+              acc[a][b] = fmaf(diff, diff, acc[a][b]);
+            else
+              acc[a][b] += fabsf(diff);
+          }
+      }
+      if (c0 + S_DC >= dq) {
+        // the tile's distances, straight from registers
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          const int row = 4 * ty + (a & 3) + (a >> 2) * 64;
+          if (row >= nq) continue;
+          float* orow = store + (int64_t)(q0 + row) * store_ld + store_col;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int col = 4 * tx + 64 * h;
+            float v[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+              v[b] = METRIC == RBC_L2 ? sqrtf(acc[a][4 * h + b]) : acc[a][4 * h + b];
+            if (col + 4 <= nx && (reinterpret_cast<uintptr_t>(orow + col) & 15) == 0) {
+              *reinterpret_cast<float4*>(orow + col) = make_float4(v[0], v[1], v[2], v[3]);
+            } else {
+#pragma unroll
+              for (int b = 0; b < 4; ++b)
+                if (col + b < nx) orow[col + b] = v[b];
+            }
+          }
+        }
+        store_col += nx;
+      }
+      si = nsi;
+      x0 = nx0;
+      xe = nxe;
+      c0 = nc0;
+    }
+  }
+}
+
+template <int METRIC>
+int launch_store(const float* Q, const float* X, int d, const TileWork& w, float* store,
+                 int64_t store_ld, int grid, cudaStream_t st) {
+  const int dq = (d + S_DC - 1) / S_DC * S_DC;
+  const size_t smem = sizeof(float) * ((size_t)dq * S_QS + S_DC * S_XS);
+  auto kern = bf_simt_store_kernel<METRIC>;
+  RBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, NTHREADS, smem, st>>>(Q, X, d, w, store, store_ld);
+  RBC_LAUNCH_CHECK("bf_simt_store_kernel");
+  return RBC_OK;
+}
+
 }  // namespace
 
 int simt_list_width(int c_needed) {
@@ -353,11 +494,11 @@ int launch_bf_simt_topc_exp(const float* Q, const float* X, const float* xnorm, 
     return RBC_ERR_UNSUPPORTED;
   }
   switch (C) {
-    case 2: return launch_one<RBC_L2, 2, false, true>(Q, X, d, w, out, nullptr, 0, grid, st, xnorm);
-    case 4: return launch_one<RBC_L2, 4, false, true>(Q, X, d, w, out, nullptr, 0, grid, st, xnorm);
-    case 8: return launch_one<RBC_L2, 8, false, true>(Q, X, d, w, out, nullptr, 0, grid, st, xnorm);
-    case 16: return launch_one<RBC_L2, 16, false, true>(Q, X, d, w, out, nullptr, 0, grid, st, xnorm);
-    case 32: return launch_one<RBC_L2, 32, false, true>(Q, X, d, w, out, nullptr, 0, grid, st, xnorm);
+    case 2: return launch_one<RBC_L2, 2, true>(Q, X, d, w, out, grid, st, xnorm);
+    case 4: return launch_one<RBC_L2, 4, true>(Q, X, d, w, out, grid, st, xnorm);
+    case 8: return launch_one<RBC_L2, 8, true>(Q, X, d, w, out, grid, st, xnorm);
+    case 16: return launch_one<RBC_L2, 16, true>(Q, X, d, w, out, grid, st, xnorm);
+    case 32: return launch_one<RBC_L2, 32, true>(Q, X, d, w, out, grid, st, xnorm);
     default: set_error("bf_simt: unsupported list width %d", C); return RBC_ERR_UNSUPPORTED;
   }
 }
@@ -393,10 +534,8 @@ int launch_bf_simt_store(const float* Q, const float* X, int d, int metric, cons
     set_error("bf_simt: d = %d exceeds %d", d, SIMT_MAX_D);
     return RBC_ERR_UNSUPPORTED;
   }
-  TopOut none{nullptr, nullptr};
-  if (metric == RBC_L2)
-    return launch_one<RBC_L2, 2, true>(Q, X, d, w, none, store, store_ld, grid, st);
-  return launch_one<RBC_L1, 2, true>(Q, X, d, w, none, store, store_ld, grid, st);
+  if (metric == RBC_L2) return launch_store<RBC_L2>(Q, X, d, w, store, store_ld, grid, st);
+  return launch_store<RBC_L1>(Q, X, d, w, store, store_ld, grid, st);
 }
 
 }  // namespace rbc
