@@ -546,7 +546,8 @@ bf_tc_top_kernel(const __grid_constant__ CUtensorMap qmap, const __grid_constant
               // the segment (rows of other segments, or zero rows past the
               // matrix end): a false alarm only costs the walk, where the
               // mask decides.
-              if (!(cmax[c] > -0.5f * tau)) continue;
+              // rows past the tile's queries (zero padding) are never written
+              if (row >= nq || !(cmax[c] > -0.5f * tau)) continue;
               const int clo = lo - (r0 + c) * 32, chi = hi - (r0 + c) * 32;
               if (chi <= 0 || clo >= 32) continue;
               const uint32_t below_hi = chi >= 32 ? 0xffffffffu : (1u << chi) - 1u;

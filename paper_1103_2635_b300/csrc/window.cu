@@ -307,8 +307,11 @@ __device__ __forceinline__ int warp_group_of(const int* __restrict__ off, int n_
   return lo + __popc(__ballot_sync(0xffffffffu, le)) - 1;
 }
 
-// Warps loop over chunks: the union of each chunk's windows, cut from the
-// sorted list by a cooperative binary search.  Statistics are summed per
+// Warps take contiguous runs of chunks: the union of each chunk's windows,
+// cut from the sorted list by a cooperative binary search.  A run finds its
+// first chunk's representative by a search of chunk_off and then steps r
+// forward as the run crosses representatives, so a chunk costs the loads of
+// its pairs, their g, and the window search.  Statistics are summed per
 // block and added once per block.
 __global__ void __launch_bounds__(256)
 window_items_kernel(const int* __restrict__ chunk_off, int n_r, const int* __restrict__ bin_off,
@@ -322,26 +325,40 @@ window_items_kernel(const int* __restrict__ chunk_off, int n_r, const int* __res
   const float dlo = 1.0f - rel, dup = 1.0f + rel;
   const float xlo = (1.0f - relx) * (1.0f - 2.4e-7f), xup = (1.0f + relx) * SLACK;
   unsigned long long rows_sum = 0, pairs_sum = 0;
-  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total;
-       c += (gridDim.x * blockDim.x) >> 5) {
-    // the group holding chunk c: last r with chunk_off[r] <= c
-    const int r = warp_group_of(chunk_off, n_r, c, lane);
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int per = (total + nwarps - 1) / nwarps;
+  const int cb = min(total, gw * per), ce = min(total, cb + per);
+  int r = cb < ce ? warp_group_of(chunk_off, n_r, cb, lane) : 0;
+  int r_end = cb < ce ? chunk_off[r + 1] : 0;  // first chunk past r
+  for (int c = cb; c < ce; ++c) {
+    while (c >= r_end) r_end = chunk_off[++r + 1];  // the run enters the next r
     const int begin = bin_off[r * nb] + (c - chunk_off[r]) * TQ;
     const int end = min(begin + TQ, bin_off[(r + 1) * nb]);
+    const int ob = offsets[r], oe = offsets[r + 1];
+    // the chunk's pairs (up to TQ = 4 x 32) and their g, loads issued together
+    int2 pr[TQ / 32];
+#pragma unroll
+    for (int u = 0; u < TQ / 32; ++u) {
+      const int i = begin + lane + 32 * u;
+      pr[u] = i < end ? pairs[i] : make_int2(-1, 0);
+    }
+    float gq[TQ / 32];
+#pragma unroll
+    for (int u = 0; u < TQ / 32; ++u) gq[u] = pr[u].x >= 0 ? g[pr[u].x] : 0.0f;
     float wlo = INFINITY, whi = -INFINITY;
-    for (int i = begin + lane; i < end; i += 32) {
-      const int2 pr = pairs[i];
-      const float d = __int_as_float(pr.y);
-      const float gq = g[pr.x];
-      wlo = fminf(wlo, (d * dlo - gq * SLACK) * xlo);
-      whi = fmaxf(whi, (d * dup + gq) * xup);
+#pragma unroll
+    for (int u = 0; u < TQ / 32; ++u) {
+      if (pr[u].x < 0) continue;
+      const float d = __int_as_float(pr[u].y);
+      wlo = fminf(wlo, (d * dlo - gq[u] * SLACK) * xlo);
+      whi = fmaxf(whi, (d * dup + gq[u]) * xup);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       wlo = fminf(wlo, __shfl_xor_sync(0xffffffffu, wlo, o));
       whi = fmaxf(whi, __shfl_xor_sync(0xffffffffu, whi, o));
     }
-    const int ob = offsets[r], oe = offsets[r + 1];
     int xb, xe;
     warp_bounds2(xdist + ob, oe - ob, wlo, whi, lane, xb, xe);
     xb += ob;
