@@ -20,7 +20,7 @@ namespace rbc {
 
 namespace {
 
-constexpr int CS_CHUNK = 2048;  // keys per counting-sort block
+constexpr int CS_CHUNK = 512;  // keys per counting-sort block
 
 __global__ void cs_hist_kernel(const int64_t* __restrict__ key, int64_t n, int nbins,
                                int* __restrict__ counts) {
@@ -37,19 +37,28 @@ __global__ void cs_hist_kernel(const int64_t* __restrict__ key, int64_t n, int n
     counts[(int64_t)blockIdx.x * nbins + b] = h[b];
 }
 
-// per bin: exclusive prefix over blocks in place; totals[bin] = sum
+// per bin (one warp, lanes over 32 blocks at a time): exclusive prefix over
+// blocks in place; totals[bin] = sum
 __global__ void cs_colscan_kernel(int* __restrict__ counts, int nblocks, int nbins,
                                   int* __restrict__ totals) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (b >= nbins) return;
-  int run = 0;
-  for (int k = 0; k < nblocks; ++k) {
-    int64_t o = (int64_t)k * nbins + b;
-    int c = counts[o];
-    counts[o] = run;
-    run += c;
+  int carry = 0;
+  for (int k0 = 0; k0 < nblocks; k0 += 32) {
+    const int k = k0 + lane;
+    const int64_t o = (int64_t)k * nbins + b;
+    const int v = k < nblocks ? counts[o] : 0;
+    int x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, off);
+      if (lane >= off) x += y;
+    }
+    if (k < nblocks) counts[o] = carry + x - v;
+    carry += __shfl_sync(0xffffffffu, x, 31);
   }
-  totals[b] = run;
+  if (lane == 0) totals[b] = carry;
 }
 
 // single block exclusive scan of n ints: out[i] = sum_{j<i} in[j], out[n] = total
@@ -556,7 +565,8 @@ int launch_counting_sort(const int64_t* key, int64_t n, int nbins, int* perm, in
   if (blocks > 0) {
     cs_hist_kernel<<<blocks, 256, nbins * sizeof(int), st>>>(key, n, nbins, counts);
     RBC_LAUNCH_CHECK("cs_hist_kernel");
-    cs_colscan_kernel<<<(nbins + 255) / 256, 256, 0, st>>>(counts, blocks, nbins, totals);
+    cs_colscan_kernel<<<(unsigned)(((int64_t)nbins * 32 + 255) / 256), 256, 0, st>>>(
+        counts, blocks, nbins, totals);
     RBC_LAUNCH_CHECK("cs_colscan_kernel");
   } else {
     RBC_CUDA(cudaMemsetAsync(totals, 0, nbins * sizeof(int), st));
