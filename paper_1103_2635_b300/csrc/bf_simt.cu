@@ -17,9 +17,11 @@
 // (d + 4) 2^-23 (|q| + max |x|)^2, and the select step certifies with it
 // (SelectArgs::exp32).
 //
-// The same file holds the windowed emission kernel on CUDA cores and the
-// distance-matrix kernel of stage one (every distance kept), described
-// where they are defined.
+// This 8 x 4 kernel serves 32-wide lists and rows too long for the 8 x 8
+// top-C kernel further down, which takes lists of up to 16.  The same file
+// holds the windowed emission kernel on CUDA cores and the distance-matrix
+// kernel of stage one (every distance kept), described where they are
+// defined.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -195,18 +197,6 @@ int launch_one(const float* Q, const float* X, int d, const TileWork& w, const T
   return RBC_OK;
 }
 
-template <int METRIC>
-int dispatch_c(int C, const float* Q, const float* X, int d, const TileWork& w, const TopOut& out,
-               int grid, cudaStream_t st) {
-  switch (C) {
-    case 2: return launch_one<METRIC, 2>(Q, X, d, w, out, grid, st);
-    case 4: return launch_one<METRIC, 4>(Q, X, d, w, out, grid, st);
-    case 8: return launch_one<METRIC, 8>(Q, X, d, w, out, grid, st);
-    case 16: return launch_one<METRIC, 16>(Q, X, d, w, out, grid, st);
-    case 32: return launch_one<METRIC, 32>(Q, X, d, w, out, grid, st);
-    default: set_error("bf_simt: unsupported list width %d", C); return RBC_ERR_UNSUPPORTED;
-  }
-}
 
 // Windowed stage two on CUDA cores (FP32 storage or the l1 metric): the same
 // work items as the tensor-core emission kernel -- a chunk of up to TQ
@@ -312,31 +302,28 @@ bf_simt_emit_kernel(const float* __restrict__ Q, const float* __restrict__ X, in
   }
 }
 
-// Distance matrix kernel (STORE): every distance of a query tile against
-// the database rows of the item's segments, written to store[q][col] -- the
-// representative distances of the exact search's stage one (Section 5.2),
-// which are all kept.  A CTA computes 128 x 128 tiles: the query tile stays
-// in shared memory (transposed, [d][TQ]), the database rows pass through in
-// 16-dimension chunks, staged from registers that were loaded while the
-// previous chunk was being used.  Each thread accumulates an 8 x 8 block
-// (rows 4 ty + {0..3} and 64 + 4 ty + {0..3}, the same for columns with tx,
-// so every shared-memory read is one 16-byte load per four values and the
-// two query loads are broadcasts) in the difference form, and writes it
-// from registers (16-byte stores of four consecutive columns).
+// 8 x 8 register-tiled kernels: the distance matrix of stage one (STORE,
+// every distance kept) and the top-C pass.  A CTA computes 128 x 128 tiles:
+// the query tile stays in shared memory (transposed, [d][TQ]), the database
+// rows pass through in 16-dimension chunks, staged from registers that were
+// loaded while the previous chunk was being used.  Each thread accumulates an
+// 8 x 8 block (rows 4 ty + {0..3} and 64 + 4 ty + {0..3}, the same for columns
+// with tx, so every shared-memory read is one 16-byte load per four values
+// and the two query loads are broadcasts): the difference form, or (EXP) the
+// product q.x for the expansion |x|^2 - 2 q.x.
 constexpr int S_TX = 128;          // database rows per tile
 constexpr int S_DC = 16;           // dimensions per staged chunk
 constexpr int S_QS = TQ + 4;       // row stride of the transposed query tile
 constexpr int S_XS = S_TX + 4;     // row stride of the transposed database chunk
 
-template <int METRIC>
-__global__ void __launch_bounds__(NTHREADS, 2)
-bf_simt_store_kernel(const float* __restrict__ Q, const float* __restrict__ X, int d, TileWork w,
-                     float* __restrict__ store, int64_t store_ld) {
-  extern __shared__ float4 smem4[];
-  float* smem = reinterpret_cast<float*>(smem4);
-  const int dq = (d + S_DC - 1) / S_DC * S_DC;
-  float* Qs = smem;            // [dq][S_QS]
-  float* Xs = Qs + dq * S_QS;  // [S_DC][S_XS]
+// One work item: load the query tile, then every 128-row tile of the item's
+// segments; on_tile(x0, nx, acc) runs after each tile's last chunk (all
+// threads, acc complete; x0 the tile's first database row, nx its rows).
+template <int METRIC, bool EXP, typename TileFn>
+__device__ __forceinline__ void simt8_item(const float* __restrict__ Q,
+                                           const float* __restrict__ X, int d, int dq,
+                                           const TileWork& w, int q0, int nq, int sb, int se,
+                                           float* Qs, float* Xs, TileFn&& on_tile) {
   const float4* Q4 = reinterpret_cast<const float4*>(Qs);
   const float4* X4 = reinterpret_cast<const float4*>(Xs);
   const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
@@ -351,108 +338,242 @@ bf_simt_store_kernel(const float* __restrict__ Q, const float* __restrict__ X, i
       xr[j] = (cin && r < fnx) ? X[(int64_t)(fx0 + r) * d + fc0 + sc] : 0.f;
     }
   };
-  int n_items = w.num_items_dev ? *w.num_items_dev : w.num_items;
-  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-    int q0, nq, sb, se, slot;
-    fetch_item(w, item, q0, nq, sb, se, slot);
-    // first non-empty segment
-    int si = sb, x0 = 0, xe = 0;
-    for (; si < se; ++si) {
-      const Seg sg = get_seg(w, si);
-      if (sg.x_end > sg.x_begin) {
-        x0 = sg.x_begin;
-        xe = sg.x_end;
-        break;
-      }
+  // first non-empty segment
+  int si = sb, x0 = 0, xe = 0;
+  for (; si < se; ++si) {
+    const Seg sg = get_seg(w, si);
+    if (sg.x_end > sg.x_begin) {
+      x0 = sg.x_begin;
+      xe = sg.x_end;
+      break;
     }
-    if (si < se) fetch(x0, min(S_TX, xe - x0), 0);
-    __syncthreads();  // the previous item's readers of Qs are done
-    for (int idx = t; idx < TQ * dq; idx += NTHREADS) {
-      const int c = idx % dq;
-      const int r = idx / dq;
-      Qs[c * S_QS + r] = (r < nq && c < d) ? Q[(int64_t)(q0 + r) * d + c] : 0.f;
-    }
-    // running column of the output (a dense split starts at its first row)
-    int store_col = w.items ? 0 : (int)get_seg(w, sb).x_begin;
-    int c0 = 0;
-    float acc[8][8];
-    while (si < se) {
-      const int nx = min(S_TX, xe - x0);
-      // the chunk after this one
-      int nsi = si, nx0 = x0, nxe = xe, nc0 = c0 + S_DC;
-      if (nc0 >= dq) {
-        nc0 = 0;
-        nx0 = x0 + S_TX;
-        if (nx0 >= xe) {
-          for (++nsi; nsi < se; ++nsi) {
-            const Seg sg = get_seg(w, nsi);
-            if (sg.x_end > sg.x_begin) {
-              nx0 = sg.x_begin;
-              nxe = sg.x_end;
-              break;
-            }
+  }
+  if (si < se) fetch(x0, min(S_TX, xe - x0), 0);
+  __syncthreads();  // the previous item's readers of Qs are done
+  for (int idx = t; idx < TQ * dq; idx += NTHREADS) {
+    const int c = idx % dq;
+    const int r = idx / dq;
+    Qs[c * S_QS + r] = (r < nq && c < d) ? Q[(int64_t)(q0 + r) * d + c] : 0.f;
+  }
+  int c0 = 0;
+  float acc[8][8];
+  while (si < se) {
+    const int nx = min(S_TX, xe - x0);
+    // the chunk after this one
+    int nsi = si, nx0 = x0, nxe = xe, nc0 = c0 + S_DC;
+    if (nc0 >= dq) {
+      nc0 = 0;
+      nx0 = x0 + S_TX;
+      if (nx0 >= xe) {
+        for (++nsi; nsi < se; ++nsi) {
+          const Seg sg = get_seg(w, nsi);
+          if (sg.x_end > sg.x_begin) {
+            nx0 = sg.x_begin;
+            nxe = sg.x_end;
+            break;
           }
         }
       }
-      __syncthreads();  // the previous chunk's readers of Xs are done
+    }
+    __syncthreads();  // the previous chunk's readers of Xs are done
 #pragma unroll
-      for (int j = 0; j < 8; ++j) Xs[sc * S_XS + sr + 16 * j] = xr[j];
-      __syncthreads();  // the chunk (and, first, the query tile) is in place
-      if (nsi < se) fetch(nx0, min(S_TX, nxe - nx0), nc0);
-      if (c0 == 0) {
+    for (int j = 0; j < 8; ++j) Xs[sc * S_XS + sr + 16 * j] = xr[j];
+    __syncthreads();  // the chunk (and, first, the query tile) is in place
+    if (nsi < se) fetch(nx0, min(S_TX, nxe - nx0), nc0);
+    if (c0 == 0) {
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
+      for (int a = 0; a < 8; ++a)
 #pragma unroll
-          for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
-      }
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+    }
 #pragma unroll 4
-      for (int k = 0; k < S_DC; ++k) {
-        const float4 qa = Q4[(c0 + k) * (S_QS / 4) + ty];
-        const float4 qb = Q4[(c0 + k) * (S_QS / 4) + 16 + ty];
-        const float4 xa = X4[k * (S_XS / 4) + tx];
-        const float4 xb = X4[k * (S_XS / 4) + 16 + tx];
-        const float qv[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
-        const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+    for (int k = 0; k < S_DC; ++k) {
+      const float4 qa = Q4[(c0 + k) * (S_QS / 4) + ty];
+      const float4 qb = Q4[(c0 + k) * (S_QS / 4) + 16 + ty];
+      const float4 xa = X4[k * (S_XS / 4) + tx];
+      const float4 xb = X4[k * (S_XS / 4) + 16 + tx];
+      const float qv[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+      const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
+      for (int a = 0; a < 8; ++a)
 #pragma unroll
-          for (int b = 0; b < 8; ++b) {
+        for (int b = 0; b < 8; ++b) {
+          if (EXP) {
+            acc[a][b] = fmaf(qv[a], xv[b], acc[a][b]);
+          } else {
             const float diff = qv[a] - xv[b];
             if (METRIC == RBC_L2)
               acc[a][b] = fmaf(diff, diff, acc[a][b]);
             else
               acc[a][b] += fabsf(diff);
           }
+        }
+    }
+    if (c0 + S_DC >= dq) on_tile(x0, nx, acc);
+    si = nsi;
+    x0 = nx0;
+    xe = nxe;
+    c0 = nc0;
+  }
+}
+
+// STORE: the tile's distances, straight from registers (16-byte stores of
+// four consecutive columns) to store[q][col], col running over the item's
+// segments (a dense split starts at its first row).
+template <int METRIC>
+__global__ void __launch_bounds__(NTHREADS, 2)
+bf_simt_store_kernel(const float* __restrict__ Q, const float* __restrict__ X, int d, TileWork w,
+                     float* __restrict__ store, int64_t store_ld) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  const int dq = (d + S_DC - 1) / S_DC * S_DC;
+  float* Qs = smem;            // [dq][S_QS]
+  float* Xs = Qs + dq * S_QS;  // [S_DC][S_XS]
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  int n_items = w.num_items_dev ? *w.num_items_dev : w.num_items;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    int q0, nq, sb, se, slot;
+    fetch_item(w, item, q0, nq, sb, se, slot);
+    int store_col = w.items ? 0 : (int)get_seg(w, sb).x_begin;
+    simt8_item<METRIC, false>(Q, X, d, dq, w, q0, nq, sb, se, Qs, Xs,
+                              [&](int x0, int nx, float (&acc)[8][8]) {
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int row = 4 * ty + (a & 3) + (a >> 2) * 64;
+        if (row >= nq) continue;
+        float* orow = store + (int64_t)(q0 + row) * store_ld + store_col;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int col = 4 * tx + 64 * h;
+          float v[4];
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            v[b] = METRIC == RBC_L2 ? sqrtf(acc[a][4 * h + b]) : acc[a][4 * h + b];
+          if (col + 4 <= nx && (reinterpret_cast<uintptr_t>(orow + col) & 15) == 0) {
+            *reinterpret_cast<float4*>(orow + col) = make_float4(v[0], v[1], v[2], v[3]);
+          } else {
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+              if (col + b < nx) orow[col + b] = v[b];
+          }
+        }
       }
-      if (c0 + S_DC >= dq) {
-        // the tile's distances, straight from registers
+      store_col += nx;
+    });
+  }
+}
+
+// TOPC: per (query row, column parity) a sorted list of the C best (score,
+// id), in shared memory, owned by one thread (row t / 2, parity t % 2), whose
+// last entry -- the list's threshold -- is published in shared memory.  A
+// tile goes through a half-width distance buffer in two 64-column halves:
+// the threads that computed the values compare them with the thresholds and
+// flag the (row, parity) lists that one of them may enter; only a flagged
+// owner walks its 32 columns of the half and inserts the ones that beat its
+// list.  Scores: the difference form, or (EXP) |x|^2 - 2 q.x with xnorm =
+// |x|^2.  The lists go to out in the layout [slot][TQ][2][C] at the item's
+// end.
+constexpr int T_DH = 66;  // row stride of the half-tile buffer (owner reads conflict-free)
+
+template <int METRIC, int C, bool EXP>
+__global__ void __launch_bounds__(NTHREADS, 2)
+bf_simt_top8_kernel(const float* __restrict__ Q, const float* __restrict__ X, int d, TileWork w,
+                    TopOut out, const float* __restrict__ xnorm) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  const int dq = (d + S_DC - 1) / S_DC * S_DC;
+  float* Qs = smem;                 // [dq][S_QS]
+  float* Xs = Qs + dq * S_QS;       // [S_DC][S_XS]
+  float* Ds = Xs + S_DC * S_XS;     // [TQ][T_DH]
+  float* Ls = Ds + TQ * T_DH;       // [C][NTHREADS] list scores
+  int* Li = reinterpret_cast<int*>(Ls + C * NTHREADS);  // [C][NTHREADS] list ids
+  __shared__ float s_thr[NTHREADS];  // threshold of list t (row t / 2, parity t % 2)
+  __shared__ int s_flag[NTHREADS];   // list t may take a value of this half
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int orow = t >> 1, osub = t & 1;
+  float* ls = Ls + t;
+  int* li = Li + t;
+  int n_items = w.num_items_dev ? *w.num_items_dev : w.num_items;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    int q0, nq, sb, se, slot;
+    fetch_item(w, item, q0, nq, sb, se, slot);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      ls[j * NTHREADS] = INFINITY;
+      li[j * NTHREADS] = INT32_MAX;
+    }
+    float wv = INFINITY;  // the list's last entry
+    int wi = INT32_MAX;
+    s_thr[t] = INFINITY;  // read by the producers after the item's first barrier
+    s_flag[t] = 0;
+    simt8_item<METRIC, EXP>(Q, X, d, dq, w, q0, nq, sb, se, Qs, Xs,
+                            [&](int x0, int nx, float (&acc)[8][8]) {
+      float xn[8];
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const int col = 4 * tx + (b & 3) + (b >> 2) * 64;
+        xn[b] = (EXP && col < nx) ? xnorm[x0 + col] : 0.f;
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        __syncthreads();  // the previous half's owners are done with Ds
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
           const int row = 4 * ty + (a & 3) + (a >> 2) * 64;
-          if (row >= nq) continue;
-          float* orow = store + (int64_t)(q0 + row) * store_ld + store_col;
+          float v[4];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int col = 4 * tx + 64 * h;
-            float v[4];
+          for (int b = 0; b < 4; ++b) {
+            const float s = EXP ? fmaf(-2.0f, acc[a][4 * h + b], xn[4 * h + b]) : acc[a][4 * h + b];
+            v[b] = (64 * h + 4 * tx + b < nx) ? s : INFINITY;
+          }
+          float2* dp = reinterpret_cast<float2*>(Ds + row * T_DH + 4 * tx);
+          dp[0] = make_float2(v[0], v[1]);
+          dp[1] = make_float2(v[2], v[3]);
+          // columns 4 tx + b have parity b % 2
+          const float t0 = s_thr[2 * row], t1 = s_thr[2 * row + 1];
+          if (v[0] <= t0 || v[2] <= t0) s_flag[2 * row] = 1;
+          if (v[1] <= t1 || v[3] <= t1) s_flag[2 * row + 1] = 1;
+        }
+        __syncthreads();
+        if (orow < nq && s_flag[t]) {
+          s_flag[t] = 0;
+          const float* drow = Ds + orow * T_DH + osub;
+#pragma unroll 4
+          for (int j = 0; j < 32; ++j) {
+            float v = drow[2 * j];
+            if (v <= wv) {
+              int id = x0 + 64 * h + 2 * j + osub;
+              if (pair_lt(v, id, wv, wi)) {
+                // sorted insertion into the owner's list
 #pragma unroll
-            for (int b = 0; b < 4; ++b)
-              v[b] = METRIC == RBC_L2 ? sqrtf(acc[a][4 * h + b]) : acc[a][4 * h + b];
-            if (col + 4 <= nx && (reinterpret_cast<uintptr_t>(orow + col) & 15) == 0) {
-              *reinterpret_cast<float4*>(orow + col) = make_float4(v[0], v[1], v[2], v[3]);
-            } else {
-#pragma unroll
-              for (int b = 0; b < 4; ++b)
-                if (col + b < nx) orow[col + b] = v[b];
+                for (int e = 0; e < C; ++e) {
+                  const float sv = ls[e * NTHREADS];
+                  const int si = li[e * NTHREADS];
+                  if (pair_lt(v, id, sv, si)) {
+                    ls[e * NTHREADS] = v;
+                    li[e * NTHREADS] = id;
+                    v = sv;
+                    id = si;
+                  }
+                }
+                wv = ls[(C - 1) * NTHREADS];
+                wi = li[(C - 1) * NTHREADS];
+              }
             }
           }
+          s_thr[t] = wv;
         }
-        store_col += nx;
       }
-      si = nsi;
-      x0 = nx0;
-      xe = nxe;
-      c0 = nc0;
+    });
+    if (orow < nq) {
+      // partial slot layout: [slot][TQ][NSUB = 2][C]
+      const int64_t base = (((int64_t)slot * TQ + orow) * 2 + osub) * C;
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const float v = ls[j * NTHREADS];
+        out.score[base + j] = v;
+        out.idx[base + j] = v == INFINITY ? -1 : li[j * NTHREADS];
+      }
     }
   }
 }
@@ -469,6 +590,48 @@ int launch_store(const float* Q, const float* X, int d, const TileWork& w, float
   return RBC_OK;
 }
 
+size_t top8_smem(int d, int C) {
+  const int dq = (d + S_DC - 1) / S_DC * S_DC;
+  return sizeof(float) * ((size_t)dq * S_QS + S_DC * S_XS + TQ * T_DH) + (size_t)C * NTHREADS * 8;
+}
+
+template <int METRIC, int C, bool EXP>
+int launch_top8(const float* Q, const float* X, int d, const TileWork& w, const TopOut& out,
+                int grid, cudaStream_t st, const float* xnorm) {
+  const size_t smem = top8_smem(d, C);
+  auto kern = bf_simt_top8_kernel<METRIC, C, EXP>;
+  RBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, NTHREADS, smem, st>>>(Q, X, d, w, out, xnorm);
+  RBC_LAUNCH_CHECK("bf_simt_top8_kernel");
+  return RBC_OK;
+}
+
+// the 8 x 8 kernel for lists of up to 16 (two CTAs per SM at d = 64); the
+// 8 x 4 kernel for 32-wide lists (its lists live in registers, so it keeps
+// two CTAs per SM: measured 22.2 against 18.4 TFLOP/s at k = 31, d = 64) and
+// wherever the 8 x 8 kernel's shared memory would not fit one CTA (227 KB)
+template <int METRIC, bool EXP>
+int dispatch_top8(int C, const float* Q, const float* X, int d, const TileWork& w,
+                  const TopOut& out, int grid, cudaStream_t st, const float* xnorm) {
+  if (C > 16 || top8_smem(d, C) > 227 * 1024) {
+    switch (C) {
+      case 2: return launch_one<METRIC, 2, EXP>(Q, X, d, w, out, grid, st, xnorm);
+      case 4: return launch_one<METRIC, 4, EXP>(Q, X, d, w, out, grid, st, xnorm);
+      case 8: return launch_one<METRIC, 8, EXP>(Q, X, d, w, out, grid, st, xnorm);
+      case 16: return launch_one<METRIC, 16, EXP>(Q, X, d, w, out, grid, st, xnorm);
+      case 32: return launch_one<METRIC, 32, EXP>(Q, X, d, w, out, grid, st, xnorm);
+      default: set_error("bf_simt: unsupported list width %d", C); return RBC_ERR_UNSUPPORTED;
+    }
+  }
+  switch (C) {
+    case 2: return launch_top8<METRIC, 2, EXP>(Q, X, d, w, out, grid, st, xnorm);
+    case 4: return launch_top8<METRIC, 4, EXP>(Q, X, d, w, out, grid, st, xnorm);
+    case 8: return launch_top8<METRIC, 8, EXP>(Q, X, d, w, out, grid, st, xnorm);
+    case 16: return launch_top8<METRIC, 16, EXP>(Q, X, d, w, out, grid, st, xnorm);
+    default: set_error("bf_simt: unsupported list width %d", C); return RBC_ERR_UNSUPPORTED;
+  }
+}
+
 }  // namespace
 
 int simt_list_width(int c_needed) {
@@ -483,8 +646,8 @@ int launch_bf_simt_topc(const float* Q, const float* X, int d, int metric, int C
     set_error("bf_simt: d = %d exceeds %d", d, SIMT_MAX_D);
     return RBC_ERR_UNSUPPORTED;
   }
-  if (metric == RBC_L2) return dispatch_c<RBC_L2>(C, Q, X, d, w, out, grid, st);
-  return dispatch_c<RBC_L1>(C, Q, X, d, w, out, grid, st);
+  if (metric == RBC_L2) return dispatch_top8<RBC_L2, false>(C, Q, X, d, w, out, grid, st, nullptr);
+  return dispatch_top8<RBC_L1, false>(C, Q, X, d, w, out, grid, st, nullptr);
 }
 
 int launch_bf_simt_topc_exp(const float* Q, const float* X, const float* xnorm, int d, int C,
@@ -493,14 +656,7 @@ int launch_bf_simt_topc_exp(const float* Q, const float* X, const float* xnorm, 
     set_error("bf_simt: d = %d exceeds %d", d, SIMT_MAX_D);
     return RBC_ERR_UNSUPPORTED;
   }
-  switch (C) {
-    case 2: return launch_one<RBC_L2, 2, true>(Q, X, d, w, out, grid, st, xnorm);
-    case 4: return launch_one<RBC_L2, 4, true>(Q, X, d, w, out, grid, st, xnorm);
-    case 8: return launch_one<RBC_L2, 8, true>(Q, X, d, w, out, grid, st, xnorm);
-    case 16: return launch_one<RBC_L2, 16, true>(Q, X, d, w, out, grid, st, xnorm);
-    case 32: return launch_one<RBC_L2, 32, true>(Q, X, d, w, out, grid, st, xnorm);
-    default: set_error("bf_simt: unsupported list width %d", C); return RBC_ERR_UNSUPPORTED;
-  }
+  return dispatch_top8<RBC_L2, true>(C, Q, X, d, w, out, grid, st, xnorm);
 }
 
 int launch_bf_simt_emit(const float* Q, const float* X, int d, int metric, const EmitItem* items,
