@@ -65,6 +65,31 @@ __device__ __forceinline__ Seg get_seg(const TileWork& w, int si) {
   return Seg{(int32_t)b, (int32_t)e};
 }
 
+// Two terms of a distance sum, columns x0 and x1 against one query value q:
+// EXP a += q x; l2 a += (q - x)^2; l1 a += |q - x|.  EXP and l2 use the
+// packed two-lane FP32 instructions (fma / sub .f32x2: one issue slot for
+// two terms, the same rounding as the scalar ones).
+template <int METRIC, bool EXP>
+__device__ __forceinline__ void two_terms(float& a0, float& a1, float x0, float x1, float q) {
+  if (EXP) {
+    asm("{\n\t.reg .b64 ac, xx, qq;\n\t"
+        "mov.b64 ac, {%0, %1};\n\tmov.b64 xx, {%2, %3};\n\tmov.b64 qq, {%4, %4};\n\t"
+        "fma.rn.f32x2 ac, xx, qq, ac;\n\tmov.b64 {%0, %1}, ac;\n\t}"
+        : "+f"(a0), "+f"(a1)
+        : "f"(x0), "f"(x1), "f"(q));
+  } else if (METRIC == RBC_L2) {
+    asm("{\n\t.reg .b64 ac, xx, qq, df;\n\t"
+        "mov.b64 ac, {%0, %1};\n\tmov.b64 xx, {%2, %3};\n\tmov.b64 qq, {%4, %4};\n\t"
+        "sub.rn.f32x2 df, qq, xx;\n\tfma.rn.f32x2 ac, df, df, ac;\n\t"
+        "mov.b64 {%0, %1}, ac;\n\t}"
+        : "+f"(a0), "+f"(a1)
+        : "f"(x0), "f"(x1), "f"(q));
+  } else {
+    a0 += fabsf(q - x0);
+    a1 += fabsf(q - x1);
+  }
+}
+
 template <int METRIC, int C, bool EXP = false>
 __global__ void __launch_bounds__(NTHREADS, 2)
 bf_simt_kernel(const float* __restrict__ Q, const float* __restrict__ X, int d, TileWork w,
@@ -134,17 +159,8 @@ bf_simt_kernel(const float* __restrict__ Q, const float* __restrict__ X, int d, 
 #pragma unroll
             for (int a = 0; a < 8; ++a)
 #pragma unroll
-              for (int b = 0; b < 4; ++b) {
-                if (EXP) {
-                  acc[a][b] = fmaf(qv[a], xv[b], acc[a][b]);
-                } else {
-                  float diff = qv[a] - xv[b];
-                  if (METRIC == RBC_L2)
-                    acc[a][b] = fmaf(diff, diff, acc[a][b]);
-                  else
-                    acc[a][b] += fabsf(diff);
-                }
-              }
+              for (int b = 0; b < 4; b += 2)
+                two_terms<METRIC, EXP>(acc[a][b], acc[a][b + 1], xv[b], xv[b + 1], qv[a]);
           }
         }
         // ---- distance tile -> shared memory (columns interleaved for the
@@ -272,6 +288,7 @@ bf_simt_emit_kernel(const float* __restrict__ Q, const float* __restrict__ X, in
           for (int a = 0; a < 8; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
+              // scalar here: the packed form measured 7% slower in this kernel
               const float diff = qv[a] - xv[b];
               if (METRIC == RBC_L2)
                 acc[a][b] = fmaf(diff, diff, acc[a][b]);
@@ -397,17 +414,8 @@ __device__ __forceinline__ void simt8_item(const float* __restrict__ Q,
 #pragma unroll
       for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-          if (EXP) {
-            acc[a][b] = fmaf(qv[a], xv[b], acc[a][b]);
-          } else {
-            const float diff = qv[a] - xv[b];
-            if (METRIC == RBC_L2)
-              acc[a][b] = fmaf(diff, diff, acc[a][b]);
-            else
-              acc[a][b] += fabsf(diff);
-          }
-        }
+        for (int b = 0; b < 8; b += 2)
+          two_terms<METRIC, EXP>(acc[a][b], acc[a][b + 1], xv[b], xv[b + 1], qv[a]);
     }
     if (c0 + S_DC >= dq) on_tile(x0, nx, acc);
     si = nsi;
