@@ -471,9 +471,12 @@ bf_simt_store_kernel(const float* __restrict__ Q, const float* __restrict__ X, i
   }
 }
 
-// TOPC: per (query row, column parity) a sorted list of the C best (score,
-// id), in shared memory, owned by one thread (row t / 2, parity t % 2), whose
-// last entry -- the list's threshold -- is published in shared memory.  A
+// TOPC: per (query row, column parity) a list of the C best (score, id), in
+// shared memory and unsorted, owned by one thread (row t / 2, parity t % 2):
+// a new entry overwrites the largest, whose position the owner finds from
+// the largest entry of each group of four (2-bit positions packed in one
+// register); the largest entry -- the list's threshold -- is published in
+// shared memory.  A
 // tile goes through a half-width distance buffer in two 64-column halves:
 // the threads that computed the values compare them with the thresholds and
 // flag the (row, parity) lists that one of them may enter; only a flagged
@@ -510,8 +513,60 @@ bf_simt_top8_kernel(const float* __restrict__ Q, const float* __restrict__ X, in
       ls[j * NTHREADS] = INFINITY;
       li[j * NTHREADS] = INT32_MAX;
     }
-    float wv = INFINITY;  // the list's last entry
+    float wv = INFINITY;  // the list's largest entry (score, id) ...
     int wi = INT32_MAX;
+    int lpos = 0;         // ... at this position
+    uint32_t gp = 0;      // 2 bits per group of four: its largest entry's position
+    // (v, id) replaces the largest entry; the group's and the list's largest
+    // are found again
+    auto insert = [&](float v, int id) {
+      ls[lpos * NTHREADS] = v;
+      li[lpos * NTHREADS] = id;
+      if (C < 4) {  // two entries: the larger is the other one or the new one
+        const float ov = ls[(1 - lpos) * NTHREADS];
+        const int oi = li[(1 - lpos) * NTHREADS];
+        if (pair_lt(v, id, ov, oi)) {
+          wv = ov;
+          wi = oi;
+          lpos = 1 - lpos;
+        } else {
+          wv = v;
+          wi = id;
+        }
+        return;
+      }
+      const int g = lpos >> 2;
+      float bv = ls[(4 * g) * NTHREADS];
+      int bi = li[(4 * g) * NTHREADS], bp = 0;
+#pragma unroll
+      for (int u = 1; u < 4; ++u) {
+        const float cv = ls[(4 * g + u) * NTHREADS];
+        const int ci = li[(4 * g + u) * NTHREADS];
+        if (pair_lt(bv, bi, cv, ci)) {
+          bv = cv;
+          bi = ci;
+          bp = u;
+        }
+      }
+      gp = (gp & ~(3u << (2 * g))) | ((uint32_t)bp << (2 * g));
+      int P = gp & 3;
+      float M = ls[P * NTHREADS];
+      int I = li[P * NTHREADS];
+#pragma unroll
+      for (int u = 1; u < C / 4; ++u) {
+        const int pu = 4 * u + ((gp >> (2 * u)) & 3);
+        const float cv = ls[pu * NTHREADS];
+        const int ci = li[pu * NTHREADS];
+        if (pair_lt(M, I, cv, ci)) {
+          M = cv;
+          I = ci;
+          P = pu;
+        }
+      }
+      wv = M;
+      wi = I;
+      lpos = P;
+    };
     s_thr[t] = INFINITY;  // read by the producers after the item's first barrier
     s_flag[t] = 0;
     simt8_item<METRIC, EXP>(Q, X, d, dq, w, q0, nq, sb, se, Qs, Xs,
@@ -548,25 +603,10 @@ bf_simt_top8_kernel(const float* __restrict__ Q, const float* __restrict__ X, in
           const float* drow = Ds + orow * T_DH + osub;
 #pragma unroll 4
           for (int j = 0; j < 32; ++j) {
-            float v = drow[2 * j];
+            const float v = drow[2 * j];
             if (v <= wv) {
-              int id = x0 + 64 * h + 2 * j + osub;
-              if (pair_lt(v, id, wv, wi)) {
-                // sorted insertion into the owner's list
-#pragma unroll
-                for (int e = 0; e < C; ++e) {
-                  const float sv = ls[e * NTHREADS];
-                  const int si = li[e * NTHREADS];
-                  if (pair_lt(v, id, sv, si)) {
-                    ls[e * NTHREADS] = v;
-                    li[e * NTHREADS] = id;
-                    v = sv;
-                    id = si;
-                  }
-                }
-                wv = ls[(C - 1) * NTHREADS];
-                wi = li[(C - 1) * NTHREADS];
-              }
+              const int id = x0 + 64 * h + 2 * j + osub;
+              if (pair_lt(v, id, wv, wi)) insert(v, id);
             }
           }
           s_thr[t] = wv;
