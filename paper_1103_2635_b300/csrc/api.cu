@@ -468,6 +468,14 @@ BandArgs band_args(const int* fb, const int* nfb, const float* Qbuf, const int* 
   return b;
 }
 
+// scratch of the band pass's chunked rows (a few hundred KB)
+int band_split_alloc(BandArgs& b, Arena& ar) {
+  const int64_t n = band_split_scratch_entries();
+  RBC_TRY(ar.alloc(&b.split_r, n));
+  RBC_TRY(ar.alloc(&b.split_i, n));
+  return RBC_OK;
+}
+
 // ---------------------------------------------------------------------------
 // database views for the BF core
 // ---------------------------------------------------------------------------
@@ -562,9 +570,10 @@ int bf_dense_f32(const float* Qdev, int64_t m, const DbView& db, int d, int k, i
   RBC_TRY(launch_select(a, st));
   RBC_TRY(launch_add_ints(cnt, lc, 3, st));
   if (marks) tmark(3, st);
-  RBC_TRY(launch_band(band_args(fb, lc, Qdev, qorig, db.X32, db.xid, db.rows, d, k, metric,
-                                out_ids, out_dist),
-                      (int)m, st));
+  BandArgs bb = band_args(fb, lc, Qdev, qorig, db.X32, db.xid, db.rows, d, k, metric, out_ids,
+                          out_dist);
+  RBC_TRY(band_split_alloc(bb, ar));
+  RBC_TRY(launch_band(bb, (int)m, st));
   if (marks) tmark(4, st);
   return RBC_OK;
 }
@@ -993,9 +1002,9 @@ int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, 
     tmark(3, st);
     // uncertified rows: the FP64 band over the whole index (a superset of
     // their surviving lists)
-    RBC_TRY(launch_band(band_args(fb, lc, Qp, qperm, ix->X32, ix->members, n, d, k, metric, ids,
-                                  dist),
-                        (int)mb, st));
+    BandArgs bb = band_args(fb, lc, Qp, qperm, ix->X32, ix->members, n, d, k, metric, ids, dist);
+    RBC_TRY(band_split_alloc(bb, ar));
+    RBC_TRY(launch_band(bb, (int)mb, st));
     tmark(4, st);
   } else {
     const int c_out = choose_c(k, true, ix->rerank_c);
@@ -1347,6 +1356,7 @@ int oneshot_stage2(const rbc_index* ix, const float* Qsrc, int64_t mq, const int
     b.tile_list = tile_rep;
     b.list_off = list_off;
     b.list_len = ix->s;
+    RBC_TRY(band_split_alloc(b, ar));
     RBC_TRY(launch_band(b, (int)rows_cap, st));
     if (marks) tmark(4, st);
     return RBC_OK;
@@ -1665,6 +1675,7 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
     BandArgs bb = band_args(fb2, lc2, Qb, nullptr, ix->X32, ix->members, n, d, k, metric, ids,
                             dist);
     bb.kth_bound = g;
+    RBC_TRY(band_split_alloc(bb, ar));
     RBC_TRY(launch_band(bb, (int)mb, st));
     RBC_TRY(launch_or_flags(ix->dev_status, dev_err, st));
   } else {
@@ -1693,12 +1704,15 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
 // ---------------------------------------------------------------------------
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// bf_dense_f32 over `rows` queries (items = tiles x splits <= tiles + 8 SMs)
-// bf_dense_f32 over `rows` queries against `db_rows` database rows: partial
-// lists, FP32 norms of both (l2), the rows to finish exactly and counters
+// the band pass's chunk scratch, (rho64, id) entries
+int64_t bound_band() { return band_split_scratch_entries() * 12; }
+// bf_dense_f32 over `rows` queries against `db_rows` database rows (items =
+// tiles x splits <= tiles + 8 SMs): partial lists, FP32 norms of both (l2),
+// the rows to finish exactly, counters and the band pass's scratch
 int64_t bound_dense_f32(int64_t rows, int sms, int64_t db_rows) {
   if (rows <= 0) return 0;
-  return (cdiv(rows, TQ) + 8LL * sms) * TQ * 2 * MAX_C * 8 + db_rows * 4 + rows * 8 + 64;
+  return (cdiv(rows, TQ) + 8LL * sms) * TQ * 2 * MAX_C * 8 + db_rows * 4 + rows * 8 + 64 +
+         bound_band();
 }
 int64_t bound_exact_batch(const rbc_index* ix, int64_t mb, int k, bool f32_only = false);
 // fallback_rbc_f32 over `rows` rows: gathered rows, results, counters and the
@@ -1754,6 +1768,7 @@ int64_t bound_window_batch(const rbc_index* ix, int64_t mb, int k) {
   b += mb * 16 + 64;                                         // fallback / stream rows, counters
   b += max2 * (int64_t)sizeof(EmitItem) + 4;                 // overflow items
   b += bound_fallback_rbc(ix, mb, k);                       // FP32 exact search of the rest
+  b += bound_band();                                         // band pass (recorded searches)
   return b;
 }
 
@@ -1774,6 +1789,7 @@ int64_t bound_exact_batch(const rbc_index* ix, int64_t mb, int k, bool f32_only)
   b += (tiles + 1) * 4 + tiles * 4;                          // item offsets
   b += cap_items * (int64_t)sizeof(WorkItem) + tiles * seg_cap * (int64_t)sizeof(Seg) + 4;
   b += cap_items * TQ * 2 * MAX_C * 8 + cap_items * 4;       // partial lists
+  b += bound_band();                                         // band pass (FP32 lists)
   if (!f32_only && uses_lp(ix->storage, ix->metric) && ix->Xlp) {
     b += 2 * mb * ((int64_t)dpad * 2 + 12);                   // low-precision batch, twice
     b += bound_own_list(ix, mb) + mb * 4;                      // own-list bound, sorted g
@@ -1789,6 +1805,7 @@ int64_t bound_oneshot_stage2(const rbc_index* ix, int64_t mq, bool lp, int level
   const int64_t rows_cap = max_tiles * TQ;
   int64_t b = bound_group(ix, mq, true);
   b += max_tiles * TQ * 2 * MAX_C * 8 + max_tiles * 4 + 4;   // partial lists, valid, dev_err
+  b += bound_band();                                         // band pass (FP32 lists)
   if (lp) {
     b += rows_cap * ((int64_t)dpad * 2 + 12);                 // low-precision rows
     b += rows_cap * 4 + 32;                                  // fallback rows, counters

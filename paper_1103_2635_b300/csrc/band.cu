@@ -40,12 +40,63 @@ constexpr int BAND_THREADS = 256;
 constexpr int BAND_GROUPS = BAND_THREADS / 8;  // one point per 8-lane group
 constexpr int BAND_MAXK = 32;
 constexpr float BAND_U32 = 5.9604645e-08f;  // 2^-24
+constexpr int BAND_U = 4;                    // rows per group and step
+// A launch with at most BAND_SPLIT_ROWS rows cuts each into BAND_SPLIT chunks
+// of its range, one CTA each: a few rows over a large database would
+// otherwise each stream it through one SM.
+constexpr int BAND_SPLIT = 16;
+constexpr int BAND_SPLIT_ROWS = 64;
+
+// rerank_rho8 of U rows at once (rows x0 + u * stride, u < U; rows at or past
+// e read row b instead and are ignored by the caller): the eight lanes of a
+// group load all U rows' float4 elements first, then reduce each.  Rows are
+// ld floats apart, ld and d multiples of 4 and X 16-byte aligned.
+template <int U>
+__device__ __forceinline__ void rho8_rows(const float* qr, const float* __restrict__ X, int ld,
+                                          int64_t b, int64_t e, int64_t x0, int stride, int d,
+                                          int metric, int g8, float (&out)[U]) {
+  const float4* q4 = reinterpret_cast<const float4*>(qr);
+  const float4* xr[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t x = x0 + (int64_t)u * stride;
+    xr[u] = reinterpret_cast<const float4*>(X + (x < e ? x : b) * ld);
+    out[u] = 0.f;
+  }
+  for (int i = g8; i < d / 4; i += 8) {
+    const float4 qa = q4[i];
+    float4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = xr[u][i];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const float t0 = qa.x - v[u].x, t1 = qa.y - v[u].y, t2 = qa.z - v[u].z, t3 = qa.w - v[u].w;
+      if (metric == RBC_L2) {
+        out[u] = fmaf(t0, t0, out[u]);
+        out[u] = fmaf(t1, t1, out[u]);
+        out[u] = fmaf(t2, t2, out[u]);
+        out[u] = fmaf(t3, t3, out[u]);
+      } else {
+        out[u] += fabsf(t0) + fabsf(t1) + fabsf(t2) + fabsf(t3);
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    float p = out[u];
+    p += __shfl_xor_sync(0xffffffffu, p, 1);
+    p += __shfl_xor_sync(0xffffffffu, p, 2);
+    p += __shfl_xor_sync(0xffffffffu, p, 4);
+    out[u] = metric == RBC_L2 ? sqrtf(p) : p;
+  }
+}
 
 __device__ __forceinline__ bool lt64(double a, int ia, double b, int ib) {
   return a < b || (a == b && ia < ib);
 }
 
-__global__ void __launch_bounds__(BAND_THREADS) band_kernel(BandArgs a) {
+// two CTAs per SM: up to 128 registers, so the four-row steps do not spill
+__global__ void __launch_bounds__(BAND_THREADS, 2) band_kernel(BandArgs a) {
   __shared__ __align__(16) float sq[MAX_D];
   __shared__ double s_r[BAND_GROUPS][BAND_MAXK];
   __shared__ int s_i[BAND_GROUPS][BAND_MAXK];
@@ -53,7 +104,16 @@ __global__ void __launch_bounds__(BAND_THREADS) band_kernel(BandArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, grp = tid >> 3, g8 = tid & 7;
   const int k = a.k, d = a.d;
   const int nrows = *a.nrows_dev;
-  for (int fi = blockIdx.x; fi < nrows; fi += gridDim.x) {
+  // work units: up to BAND_SPLIT_ROWS rows in BAND_SPLIT chunks of their
+  // range (their chunk lists go to the split scratch, merged by
+  // band_merge_kernel); more rows than that keep every SM busy whole (the
+  // scan is then bound by HBM, not by one SM's reads)
+  const int nsplit = (a.split_r && nrows <= BAND_SPLIT_ROWS) ? nrows : 0;
+  const int units = nsplit * BAND_SPLIT + (nrows - nsplit);
+  for (int un = blockIdx.x; un < units; un += gridDim.x) {
+    const bool split = un < nsplit * BAND_SPLIT;
+    const int fi = split ? un / BAND_SPLIT : nsplit + (un - nsplit * BAND_SPLIT);
+    const int chunk = split ? un % BAND_SPLIT : 0;
     const int p = a.rows[fi];
     const int64_t orow = a.qorig ? (int64_t)a.qorig[p] : (int64_t)p;
     if (orow < 0) continue;  // padding row (the same for every thread)
@@ -66,6 +126,12 @@ __global__ void __launch_bounds__(BAND_THREADS) band_kernel(BandArgs a) {
       const int r = a.tile_list[p / TQ];
       b = a.list_off ? a.list_off[r] : (int64_t)r * a.list_len;
       e = a.list_off ? a.list_off[r + 1] : b + a.list_len;
+    }
+    if (split) {
+      const int64_t len = e - b;
+      const int64_t cb = b + len * chunk / BAND_SPLIT, ce = b + len * (chunk + 1) / BAND_SPLIT;
+      b = cb;
+      e = ce;
     }
     __syncthreads();  // the previous row's readers of sq and the lists are done
     for (int i = tid; i < d; i += BAND_THREADS) sq[i] = a.Q32[(int64_t)p * a.ld + i];
@@ -82,12 +148,29 @@ __global__ void __launch_bounds__(BAND_THREADS) band_kernel(BandArgs a) {
                           : INFINITY;
     }
     __syncthreads();
-    const int64_t iters = (e - b + BAND_GROUPS - 1) / BAND_GROUPS;  // the same for every warp
+    // BAND_U rows per group and step, their loads issued together (the
+    // scan of a whole database is latency-bound otherwise)
+    const bool vec = (d & 3) == 0 && (a.ld & 3) == 0 &&
+                     (reinterpret_cast<uintptr_t>(a.X32) & 15) == 0;
+    const int64_t iters = (e - b + BAND_GROUPS * BAND_U - 1) / (BAND_GROUPS * BAND_U);
     for (int64_t it = 0; it < iters; ++it) {
-      const int64_t x = b + it * BAND_GROUPS + grp;
+      float vu[BAND_U];
+      if (vec) {
+        rho8_rows<BAND_U>(sq, a.X32, a.ld, b, e, b + it * BAND_GROUPS * BAND_U + grp,
+                          BAND_GROUPS, d, a.metric, g8, vu);
+      } else {
+#pragma unroll
+        for (int u = 0; u < BAND_U; ++u) {
+          const int64_t x = b + (it * BAND_U + u) * BAND_GROUPS + grp;
+          vu[u] = rerank_rho8(sq, a.X32 + (x < e ? x : b) * a.ld, d, a.metric, g8);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < BAND_U; ++u) {
+      const int64_t x = b + (it * BAND_U + u) * BAND_GROUPS + grp;
       const bool valid = x < e;
       const float* xr = a.X32 + (valid ? x : b) * a.ld;
-      const float v = rerank_rho8(sq, xr, d, a.metric, g8);
+      const float v = vu[u];
       const bool in = valid && v <= thr;
       if (__any_sync(0xffffffffu, in)) {
         const double r64 = rho64_8(sq, xr, d, a.metric, g8);
@@ -109,6 +192,7 @@ __global__ void __launch_bounds__(BAND_THREADS) band_kernel(BandArgs a) {
             if (nn < k) s_n[grp] = nn + 1;
           }
         }
+      }
       }
     }
     __syncthreads();
@@ -139,7 +223,14 @@ __global__ void __launch_bounds__(BAND_THREADS) band_kernel(BandArgs a) {
           myi = bi;
         }
       }
-      if (lane < k) {
+      if (split) {
+        // this chunk's k best, sorted, to the row's slot of the scratch
+        const int64_t so = ((int64_t)fi * BAND_SPLIT + chunk) * BAND_MAXK;
+        if (lane < k) {
+          a.split_r[so + lane] = myr;
+          a.split_i[so + lane] = myi;
+        }
+      } else if (lane < k) {
         const bool ok = myr < INFINITY;
         a.out_ids[orow * k + lane] = ok ? (int64_t)myi : (int64_t)-1;
         a.out_dist[orow * k + lane] = ok ? (float)myr : INFINITY;
@@ -148,7 +239,58 @@ __global__ void __launch_bounds__(BAND_THREADS) band_kernel(BandArgs a) {
   }
 }
 
+// The split rows: one warp per row merges its BAND_SPLIT sorted chunk lists
+// (lane c holds chunk c's head) by k rounds of a warp arg-min over (rho64, id)
+// and writes the row's answer.
+__global__ void band_merge_kernel(BandArgs a) {
+  const int w = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  const int nrows = *a.nrows_dev;
+  const int nsplit = nrows <= BAND_SPLIT_ROWS ? nrows : 0;
+  if (w >= nsplit) return;
+  const int p = a.rows[w];
+  const int64_t orow = a.qorig ? (int64_t)a.qorig[p] : (int64_t)p;
+  if (orow < 0) return;
+  const int k = a.k;
+  const int64_t so = ((int64_t)w * BAND_SPLIT + lane) * BAND_MAXK;
+  int head = 0;
+  double myr = INFINITY;
+  int myi = INT32_MAX;
+  for (int j = 0; j < k; ++j) {
+    double bv = INFINITY;
+    int bi = INT32_MAX;
+    if (lane < BAND_SPLIT && head < k) {
+      bv = a.split_r[so + head];
+      bi = a.split_i[so + head];
+    }
+    int bl = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+      if (ov < bv || (ov == bv && (oi < bi || (oi == bi && ol < bl)))) {
+        bv = ov;
+        bi = oi;
+        bl = ol;
+      }
+    }
+    if (lane == bl) ++head;
+    if (lane == j) {
+      myr = bv;
+      myi = bi;
+    }
+  }
+  if (lane < k) {
+    const bool ok = myr < INFINITY;
+    a.out_ids[orow * k + lane] = ok ? (int64_t)myi : (int64_t)-1;
+    a.out_dist[orow * k + lane] = ok ? (float)myr : INFINITY;
+  }
+}
+
 }  // namespace
+
+int64_t band_split_scratch_entries() { return (int64_t)BAND_SPLIT_ROWS * BAND_SPLIT * BAND_MAXK; }
 
 int launch_band(const BandArgs& a, int max_rows, cudaStream_t st) {
   if (max_rows <= 0) return RBC_OK;
@@ -160,9 +302,18 @@ int launch_band(const BandArgs& a, int max_rows, cudaStream_t st) {
   int sms = 1, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = (int)std::min<int64_t>(max_rows, (int64_t)sms * 4);
+  const int64_t units =
+      a.split_r ? std::max<int64_t>((int64_t)std::min(max_rows, BAND_SPLIT_ROWS) * BAND_SPLIT,
+                                    max_rows)
+                : max_rows;
+  const int grid = (int)std::min<int64_t>(units, (int64_t)sms * 4);
   band_kernel<<<grid, BAND_THREADS, 0, st>>>(a);
   RBC_LAUNCH_CHECK("band_kernel");
+  if (a.split_r) {
+    const int nw = std::min(max_rows, BAND_SPLIT_ROWS);
+    band_merge_kernel<<<(nw * 32 + 255) / 256, 256, 0, st>>>(a);
+    RBC_LAUNCH_CHECK("band_merge_kernel");
+  }
   return RBC_OK;
 }
 

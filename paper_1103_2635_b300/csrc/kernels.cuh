@@ -210,7 +210,12 @@ struct BandArgs {
   // neighbour distance, used instead of the k-th distance in out_dist (rows
   // for which no select step wrote k points)
   const float* kth_bound = nullptr;
+  // optional scratch of band_split_scratch_entries() (rho64, id) entries: the
+  // first rows of the launch are then scanned in chunks by several CTAs
+  double* split_r = nullptr;
+  int* split_i = nullptr;
 };
+int64_t band_split_scratch_entries();
 // grid over at most max_rows rows (the count itself is read on the device)
 int launch_band(const BandArgs& a, int max_rows, cudaStream_t st);
 
