@@ -105,6 +105,50 @@ __device__ __forceinline__ float rerank_rho8(const float* qr, const float* xr, i
   return metric == RBC_L2 ? sqrtf(p) : p;
 }
 
+// rerank_rho8 of U rows at once (rows x0 + u * stride, u < U; rows at or past
+// e read row b instead and are ignored by the caller): the eight lanes of a
+// group load all U rows' float4 elements first, then reduce each.  Rows are
+// ld floats apart, ld and d multiples of 4 and X 16-byte aligned.
+template <int U>
+__device__ __forceinline__ void rho8_rows(const float* qr, const float* __restrict__ X, int ld,
+                                          int64_t b, int64_t e, int64_t x0, int stride, int d,
+                                          int metric, int g8, float (&out)[U]) {
+  const float4* q4 = reinterpret_cast<const float4*>(qr);
+  const float4* xr[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t x = x0 + (int64_t)u * stride;
+    xr[u] = reinterpret_cast<const float4*>(X + (x < e ? x : b) * ld);
+    out[u] = 0.f;
+  }
+  for (int i = g8; i < d / 4; i += 8) {
+    const float4 qa = q4[i];
+    float4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = xr[u][i];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const float t0 = qa.x - v[u].x, t1 = qa.y - v[u].y, t2 = qa.z - v[u].z, t3 = qa.w - v[u].w;
+      if (metric == RBC_L2) {
+        out[u] = fmaf(t0, t0, out[u]);
+        out[u] = fmaf(t1, t1, out[u]);
+        out[u] = fmaf(t2, t2, out[u]);
+        out[u] = fmaf(t3, t3, out[u]);
+      } else {
+        out[u] += fabsf(t0) + fabsf(t1) + fabsf(t2) + fabsf(t3);
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    float p = out[u];
+    p += __shfl_xor_sync(0xffffffffu, p, 1);
+    p += __shfl_xor_sync(0xffffffffu, p, 2);
+    p += __shfl_xor_sync(0xffffffffu, p, 4);
+    out[u] = metric == RBC_L2 ? sqrtf(p) : p;
+  }
+}
+
 // The same distance in FP64 (from the FP32 inputs), by the eight lanes of a
 // group; every lane of the group returns it.  All 32 lanes of the warp must
 // call it together.

@@ -4,8 +4,8 @@ Each test query gets a shell of points at distances R (1 + j g), j = 0, 1, ...,
 with relative gaps g between the 1e-6 tie threshold of the parity rule and
 the FP32 rounding bound of the select step: the FP64 order of the shell is
 fixed, but the FP32 candidate set cannot certify it, so the query has to be
-finished exactly (the FP64 band pass, or the FP64 band finish of the
-windowed select).  The tests assert that such rows occurred (the
+finished exactly (the FP64 band pass -- a few rows split over several CTAs,
+many rows one CTA each -- or the FP64 band finish of the windowed select).  The tests assert that such rows occurred (the
 `uncertified` / `boundary_ties` counters) and that every answer matches the
 oracle element by element (Section 3: BF returns the k nearest; Section 5.2:
 the exact search is always correct)."""
@@ -62,6 +62,20 @@ def test_bf_f32_uncertified_rows_match_oracle(metric, d, k):
     st = rbc.last_stats()
     assert st["uncertified"] > 0, st
     o_ids, o_rho = oracle.bf(Q, X, k, metric)
+    check_knn(Q, X, ids, dist, o_ids, o_rho, metric)
+
+
+@pytest.mark.parametrize("metric", ["l2", "l1"])
+def test_bf_f32_many_uncertified_rows_match_oracle(metric):
+    # more uncertified rows than the band pass splits across CTAs (64): the
+    # rows are then scanned whole, one CTA each
+    X, Q = shell_inputs(48, metric, n_bg=20000, m=160, shelled=120, seed=9)
+    Qd, Xd = torch.from_numpy(Q).cuda(), torch.from_numpy(X).cuda()
+    ids, dist = rbc.bf_search(Qd, Xd, 31, metric=MET[metric], storage=rbc.F32)
+    ids, dist = _cpu(ids), _cpu(dist)
+    st = rbc.last_stats()
+    assert st["uncertified"] > 64, st
+    o_ids, o_rho = oracle.bf(Q, X, 31, metric)
     check_knn(Q, X, ids, dist, o_ids, o_rho, metric)
 
 

@@ -235,6 +235,19 @@ def test_exact_search_multi_batch_with_recheck(plan):
     np.testing.assert_array_equal(ids[on[:300]], o_ids[np.searchsorted(sel, on[:300])])
 
 
+@pytest.mark.parametrize("storage,metric", [(rbc.BF16, "l2"), (rbc.F32, "l2"), (rbc.F32, "l1")])
+@pytest.mark.parametrize("k", [1, 10, 20])
+def test_exact_search_fewer_queries_than_lists(storage, metric, k):
+    # m <= n_r: most lists hold one query or none, so the own-list tiles are
+    # almost all padding rows
+    X, _ = synth.make_workload("iid-n16k-d16", seed=0)
+    Q = synth.iid_normal(300, 16, 17)
+    idx = build(X, 512, metric, storage=storage)
+    ids, dist = search(idx, Q, k)
+    o_ids, o_rho = oracle.bf(Q, X, k, metric)
+    check_knn(Q, X, ids, dist, o_ids, o_rho, metric)
+
+
 def test_window_many_tied_candidates_are_streamed():
     # 700 copies of one point: a query on it has 700 survivors at distance 0,
     # more than the shared-memory re-rank holds; they are re-ranked in a
