@@ -22,8 +22,9 @@
 // itself returns the maximum of the raw accumulators (tcgen05.ld.red), and
 // only when that reaches -T(q) / 2 does a lane walk the chunk and emit the
 // qualifying (score, row) pairs: into its own slice of a hit arena (no
-// atomics; a post-pass moves them to the per-query buffers; the hits of a
-// full slice go to the query's buffer directly, one atomic each), or, in the
+// atomics; a post-pass moves them to the per-query buffers; a chunk's hits
+// that the slice has no room for go to the query's buffer directly, one
+// atomic per chunk), or, in the
 // instance for direct appends, into q's candidate buffer with one atomic per
 // chunk.  When rows have two spare padding columns, the norm pair lives in
 // them instead (FOLD) and no norm block or norm MMA is needed.  The
@@ -415,7 +416,8 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
     int4* hits = p.out.arena ? p.out.arena + (int64_t)blockIdx.x * p.out.arena_seg +
                                    (int64_t)ew * esub + (int64_t)lane * lsub
                              : nullptr;
-    int nhits = 0;
+    int nhits = 0;         // records in this thread's arena slice
+    bool spilled = false;  // some chunk's hits went to the buffers directly
     for (; ok; ++qi) {
       const int qs = qi % QSTAGES;
       const uint32_t qph = (qi / QSTAGES) & 1;
@@ -465,26 +467,19 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
             // the set bits of the hit mask, one by one (compact code: the
             // common path stays small in the instruction cache)
             uint32_t mask = valid & over_mask32<true>(raw[c], myT);
-            if (!DIRECT) {
+            if (!DIRECT && nhits + __popc(mask) <= lsub) {
               while (mask) {
                 const int j = __ffs(mask) - 1;
                 mask &= mask - 1;
                 const float v = __uint_as_float(pick32(raw[c], j));
-                if (nhits < lsub) {
-                  hits[nhits] = make_int4(myq, cb + j, __float_as_int(-2.0f * v), 0);
-                } else {
-                  // the slice is full: this hit goes straight to the row's buffer
-                  const int pos = atomicAdd(cc, 1);
-                  if (pos < cap) {
-                    cs[pos] = -2.0f * v;
-                    cr[pos] = cb + j;
-                  }
-                }
-                ++nhits;
+                hits[nhits++] = make_int4(myq, cb + j, __float_as_int(-2.0f * v), 0);
               }
             } else {
-              // direct appends: one atomic per (lane, chunk) reserves the
-              // row's slots, then the hits fill them in column order
+              // direct appends (and, in the arena instance, the hits of a
+              // chunk that its slice has no room for): one atomic per (lane,
+              // chunk) reserves the row's slots, then the hits fill them in
+              // column order
+              if (!DIRECT) spilled = true;
               int pos = atomicAdd(cc, __popc(mask));
               while (mask) {
                 const int j = __ffs(mask) - 1;
@@ -502,8 +497,8 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
       }
     }
     if (!DIRECT) {
-      p.out.arena_cnt[(blockIdx.x * ARENA_SUBSEG + ew) * 32 + lane] = nhits < lsub ? nhits : lsub;
-      if (nhits > lsub) atomicOr(p.out.arena_ovf, 1);
+      p.out.arena_cnt[(blockIdx.x * ARENA_SUBSEG + ew) * 32 + lane] = nhits;
+      if (spilled) atomicOr(p.out.arena_ovf, 1);
     }
   }
 
