@@ -858,7 +858,7 @@ constexpr int64_t ARENA_MIN_LANE = 256;  // hit records per epilogue thread, at 
 
 int own_list_bound(const rbc_index* ix, const float* Qb, int64_t mb, const int64_t* nearest,
                    const LpQueries& ql, int k, float* own, uint32_t* dev_err, Arena& ar,
-                   cudaStream_t st);
+                   cudaStream_t st, int** order = nullptr);
 
 int search_exact_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, int64_t* ids,
                        float* dist, const Counters& cn, int64_t* items_total, Arena& ar,
@@ -1199,13 +1199,14 @@ struct Grouped {
 
 int group_queries(const rbc_index* ix, const float* Qsrc, int64_t mq, const int64_t* rep_of,
                   const int* orig, const int* list_off, unsigned long long* points_sum, Grouped& gq,
-                  Arena& ar, cudaStream_t st, bool gather_fp32 = true) {
+                  Arena& ar, cudaStream_t st, bool gather_fp32 = true, int** order = nullptr) {
   const int d = ix->d, n_r = ix->n_r, s = ix->s;
   int *qperm, *qoff, *scratch;
   RBC_TRY(ar.alloc(&qperm, mq));
   RBC_TRY(ar.alloc(&qoff, n_r + 1));
   RBC_TRY(ar.alloc(&scratch, counting_sort_scratch_ints(mq, n_r)));
   RBC_TRY(launch_counting_sort(rep_of, mq, n_r, qperm, qoff, scratch, st));
+  if (order) *order = qperm;
   gq.max_tiles = (mq + TQ - 1) / TQ + std::min<int64_t>(n_r, mq);
   gq.rows_cap = gq.max_tiles * TQ;
   int *pad_cnt, *pad_off;
@@ -1249,9 +1250,10 @@ int group_queries(const rbc_index* ix, const float* Qsrc, int64_t mq, const int6
 // distances of the selected rows.  ql holds the batch's low-precision rows.
 int own_list_bound(const rbc_index* ix, const float* Qb, int64_t mb, const int64_t* nearest,
                    const LpQueries& ql, int k, float* own, uint32_t* dev_err, Arena& ar,
-                   cudaStream_t st) {
+                   cudaStream_t st, int** order) {
   Grouped gq;
-  RBC_TRY(group_queries(ix, Qb, mb, nearest, nullptr, ix->offsets, nullptr, gq, ar, st, false));
+  RBC_TRY(
+      group_queries(ix, Qb, mb, nearest, nullptr, ix->offsets, nullptr, gq, ar, st, false, order));
   const int row_bytes = ix->dpad * lp_elem_bytes(ix->storage);
   uint8_t* alp;
   float *anorm, *aerr, *ascale = nullptr;
@@ -1283,9 +1285,10 @@ int own_list_bound(const rbc_index* ix, const float* Qb, int64_t mb, const int64
 // the k best FP32 values of q inside its nearest representative's list,
 // re-ranked, the largest of them rounded up.
 int own_list_bound_f32(const rbc_index* ix, const float* Qb, int64_t mb, const int64_t* nearest,
-                       int k, float* own, Arena& ar, cudaStream_t st) {
+                       int k, float* own, Arena& ar, cudaStream_t st, int** order = nullptr) {
   Grouped gq;
-  RBC_TRY(group_queries(ix, Qb, mb, nearest, nullptr, ix->offsets, nullptr, gq, ar, st, true));
+  RBC_TRY(
+      group_queries(ix, Qb, mb, nearest, nullptr, ix->offsets, nullptr, gq, ar, st, true, order));
   const int C = simt_list_width((k + 1) / 2);  // half-lists: 2C >= k
   float* ps;
   int* pi;
@@ -1494,12 +1497,14 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   LpQueries ql;
   if (lp) RBC_TRY(lp_queries(Qb, mb, d, ix->dpad, ix->storage, ql, ar, st));
   // pass A: the k-th distance inside the nearest representative's own list
+  // (and the batch's queries ordered by nearest representative)
   float* own;
+  int* qorder = nullptr;
   RBC_TRY(ar.alloc(&own, mb));
   if (lp)
-    RBC_TRY(own_list_bound(ix, Qb, mb, nearest, ql, k, own, dev_err, ar, st));
+    RBC_TRY(own_list_bound(ix, Qb, mb, nearest, ql, k, own, dev_err, ar, st, &qorder));
   else
-    RBC_TRY(own_list_bound_f32(ix, Qb, mb, nearest, k, own, ar, st));
+    RBC_TRY(own_list_bound_f32(ix, Qb, mb, nearest, k, own, ar, st, &qorder));
   float* g;
   RBC_TRY(ar.alloc(&g, mb));
   RBC_TRY(launch_gbound(own, gk, mb, simt_eps(d), g, st));
@@ -1608,6 +1613,10 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   a.stream_count = lc + 4;
   a.f32 = lp ? 0 : 1;
   a.f32_eps = f32_eps;
+  // queries in nearest-representative order: the warps that run together
+  // re-rank points of the same few lists, whose FP32 rows then come from L2
+  a.rows = qorder;
+  a.nrows = (int)mb;
   RBC_CUDA(cudaMemsetAsync(cc, 0, mb * sizeof(int), st));
   RBC_CUDA(cudaMemsetAsync(arena_ovf, 0, sizeof(int), st));
   RBC_CUDA(cudaMemsetAsync(lc, 0, 8 * sizeof(int), st));

@@ -105,6 +105,93 @@ __device__ __forceinline__ float rerank_rho8(const float* qr, const float* xr, i
   return metric == RBC_L2 ? sqrtf(p) : p;
 }
 
+// rerank_rho8 of U gathered rows xr[u] by the eight lanes of a group (d a
+// multiple of 4, rows and query 16-byte aligned): the float4 elements of all
+// U rows, up to four per lane and row (all of a row for d <= 128), are loaded
+// before any is used, so a group keeps up to 4 U loads in flight.  Every sum
+// runs in rerank_rho8's order (ascending element, then the same shuffle
+// tree), so the values are bit-identical to it.
+template <int U>
+__device__ __forceinline__ void rho8_gather(const float* qr, const float* const (&xr)[U], int d,
+                                            int metric, int g8, float (&out)[U]) {
+  const float4* q4 = reinterpret_cast<const float4*>(qr);
+  const int n4 = d / 4;
+#pragma unroll
+  for (int u = 0; u < U; ++u) out[u] = 0.f;
+  for (int i0 = g8; i0 < n4; i0 += 32) {
+    float4 v[4][U];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int i = i0 + 8 * s;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        v[s][u] = i < n4 ? reinterpret_cast<const float4*>(xr[u])[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int i = i0 + 8 * s;
+      if (i < n4) {
+        const float4 qa = q4[i];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const float t0 = qa.x - v[s][u].x, t1 = qa.y - v[s][u].y, t2 = qa.z - v[s][u].z,
+                      t3 = qa.w - v[s][u].w;
+          if (metric == RBC_L2) {
+            out[u] = fmaf(t0, t0, out[u]);
+            out[u] = fmaf(t1, t1, out[u]);
+            out[u] = fmaf(t2, t2, out[u]);
+            out[u] = fmaf(t3, t3, out[u]);
+          } else {
+            out[u] += fabsf(t0) + fabsf(t1) + fabsf(t2) + fabsf(t3);
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    float p = out[u];
+    p += __shfl_xor_sync(0xffffffffu, p, 1);
+    p += __shfl_xor_sync(0xffffffffu, p, 2);
+    p += __shfl_xor_sync(0xffffffffu, p, 4);
+    out[u] = metric == RBC_L2 ? sqrtf(p) : p;
+  }
+}
+
+// FP32 distances of the rows rows[0 .. n) (shared memory) to the query, into
+// out[0 .. n) (shared memory), by the whole warp: 4 U rows per round (U per
+// group of eight lanes, gathered loads; a larger U keeps more loads in flight
+// for long lists, a smaller one fewer registers for short ones), or
+// rerank_rho8 row by row when the layout does not allow 16-byte loads.
+template <int U>
+__device__ __forceinline__ void rerank_rows(const float* qr, const float* X32, int d, int metric,
+                                            const int* rows, int n, float* out, int lane) {
+  const int g = lane >> 3, g8 = lane & 7;
+  if ((d & 3) == 0 && ((reinterpret_cast<uintptr_t>(qr) | reinterpret_cast<uintptr_t>(X32)) & 15) == 0) {
+    for (int e0 = 0; e0 < n; e0 += 4 * U) {
+      const float* xr[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + g + 4 * u;
+        xr[u] = X32 + (int64_t)rows[e < n ? e : 0] * d;
+      }
+      float v[U];
+      rho8_gather<U>(qr, xr, d, metric, g8, v);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + g + 4 * u;
+        if (g8 == 0 && e < n) out[e] = v[u];
+      }
+    }
+  } else {
+    for (int e0 = 0; e0 < n; e0 += 4) {
+      const int e = e0 + g;
+      const float v = rerank_rho8(qr, X32 + (int64_t)rows[e < n ? e : 0] * d, d, metric, g8);
+      if (g8 == 0 && e < n) out[e] = v;
+    }
+  }
+}
+
 // rerank_rho8 of U rows at once (rows x0 + u * stride, u < U; rows at or past
 // e read row b instead and are ignored by the caller): the eight lanes of a
 // group load all U rows' float4 elements first, then reduce each.  Rows are

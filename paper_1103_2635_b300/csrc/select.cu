@@ -552,12 +552,7 @@ __global__ void __launch_bounds__(WARPS * 32) select_cands_kernel(CandSelectArgs
   const float* qr = a.Q32 + q * d;
   // FP32 distances of the survivors, four rows at a time
   float* dst = dstage[wib];
-  for (int e0 = 0; e0 < nre; e0 += 4) {
-    const int e = e0 + (lane >> 3);
-    const int row = e < nre ? stg[e] : stg[0];
-    const float v = rerank_rho8(qr, a.X32 + (int64_t)row * d, d, a.metric, lane & 7);
-    if ((lane & 7) == 0 && e < nre) dst[e] = v;
-  }
+  rerank_rows<1>(qr, a.X32, d, a.metric, stg, nre, dst, lane);
   __syncwarp();
   float ls[RERANK_PL];
   int li[RERANK_PL], lr[RERANK_PL];
@@ -735,16 +730,9 @@ __global__ void __launch_bounds__(WARPS * 32) select_stream_kernel(CandSelectArg
         ns += __popc(bal);
       }
       __syncwarp();
-      // ids first (independent loads), then distances two rounds at a time
+      // ids first (independent loads), then distances sixteen rows at a time
       for (int e = lane; e < ns; e += 32) sid[e] = a.xid ? a.xid[srow[e]] : srow[e];
-      for (int e0 = 0; e0 < ns; e0 += 8) {
-        const int e = e0 + (lane >> 3), f = e + 4;
-        const int row = srow[e < ns ? e : 0], row2 = srow[f < ns ? f : 0];
-        const float v = rerank_rho8(qr, a.X32 + (int64_t)row * d, d, a.metric, lane & 7);
-        const float v2 = rerank_rho8(qr, a.X32 + (int64_t)row2 * d, d, a.metric, lane & 7);
-        if ((lane & 7) == 0 && e < ns) srho[e] = v;
-        if ((lane & 7) == 0 && f < ns) srho[f] = v2;
-      }
+      rerank_rows<4>(qr, a.X32, d, a.metric, srow, ns, srho, lane);
       __syncwarp();
       for (int e = lane; e < ns; e += 32) {
       const int row = srow[e];
@@ -821,12 +809,7 @@ __global__ void __launch_bounds__(WARPS * 32) select_stream_kernel(CandSelectArg
           nb += __popc(bal);
         }
         __syncwarp();
-        for (int e0 = 0; e0 < nb; e0 += 4) {
-          const int e = e0 + (lane >> 3);
-          const int row = srow[e < nb ? e : 0];
-          const float v = rerank_rho8(qr, a.X32 + (int64_t)row * d, d, a.metric, lane & 7);
-          if ((lane & 7) == 0 && e < nb) srho[e] = v;
-        }
+        rerank_rows<4>(qr, a.X32, d, a.metric, srow, nb, srho, lane);
         __syncwarp();
         int ns = 0;
         for (int e0 = 0; e0 < nb; e0 += 32) {
