@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--workload", default="subspace8-n1m-d64")
     ap.add_argument("--k", type=int, default=10)
     ap.add_argument("--storage", default="bf16", choices=["bf16", "f16", "f32", "fp8"])
-    ap.add_argument("--plan", default="window", choices=["window", "tile_union"],
+    ap.add_argument("--plan", default="window", choices=["window", "tile_union", "window_offset"],
                     help="exact-search stage two (bf16 / fp16 storage)")
     ap.add_argument("--cpu-sample", type=int, default=1000)
     ap.add_argument("--no-cpu", action="store_true")
@@ -266,7 +266,8 @@ def run_ours(args, rank, world, local):
     st = torch.cuda.current_stream(dev)
 
     t0 = time.perf_counter()
-    plan = {"window": rbc.PLAN_WINDOW, "tile_union": rbc.PLAN_TILE_UNION}[args.plan]
+    plan = {"window": rbc.PLAN_WINDOW, "tile_union": rbc.PLAN_TILE_UNION,
+            "window_offset": rbc.PLAN_WINDOW_OFFSET}[args.plan]
     idx = rbc.rbc_build(Xd, w.n_r, metric=rbc.L2, seed=2, storage=storage, plan=plan)
     torch.cuda.synchronize(dev)
     build_s = time.perf_counter() - t0

@@ -92,8 +92,24 @@ typedef enum {
  *   RBC_PLAN_TILE_UNION: tiles of 128 queries ordered by nearest
  *     representative search the union of their surviving lists, keeping a
  *     top-c list per query, then re-rank and certify.
- * FP32 and L1 searches always use the tile-union form on CUDA cores. */
-typedef enum { RBC_PLAN_WINDOW = 0, RBC_PLAN_TILE_UNION = 1 } rbc_plan;
+ *   RBC_PLAN_WINDOW_OFFSET: the windowed plan on offsets from the
+ *     representative (bf16 storage, d a multiple of 8; otherwise the same as
+ *     RBC_PLAN_WINDOW): the build also stores every list row as
+ *     y~ = bf16(x - r) of its representative r, and each (query chunk,
+ *     window of r's list) multiplies a~ = bf16(q - r) by those rows.  The
+ *     rounding then scales with |q - r| + |x - r| instead of |q| + |x|, so
+ *     far fewer points fall in the band a candidate must be re-ranked for
+ *     (data far from the origin, tight clusters).  Uses n x dpad more bf16
+ *     of device memory, and per batch one bf16 row per kept (query, list)
+ *     pair, sized by reading the pair count back (so a search on this plan
+ *     cannot be recorded into a CUDA graph).
+ * FP32 and L1 searches run the windowed plan on CUDA cores (the tile-union
+ * plan when asked for). */
+typedef enum {
+  RBC_PLAN_WINDOW = 0,
+  RBC_PLAN_TILE_UNION = 1,
+  RBC_PLAN_WINDOW_OFFSET = 2
+} rbc_plan;
 
 typedef struct rbc_index rbc_index; /* opaque; owned by the library */
 
@@ -105,8 +121,9 @@ typedef struct {
   int32_t storage;        /* rbc_storage used by the search and the build */
   int32_t rerank_c;       /* candidates per query kept by the low-precision
                              pass before re-ranking; 0 = automatic */
-  int32_t plan;           /* exact-search stage two with bf16 / fp16 storage:
-                             RBC_PLAN_WINDOW (0) or RBC_PLAN_TILE_UNION (1) */
+  int32_t plan;           /* exact-search stage two: RBC_PLAN_WINDOW (0),
+                             RBC_PLAN_TILE_UNION (1) or
+                             RBC_PLAN_WINDOW_OFFSET (2) */
   const int64_t* rep_ids; /* optional HOST array of n_r distinct ids in
                              [0, n), ascending; NULL = sample them */
 } rbc_opts;
@@ -187,7 +204,7 @@ int rbc_build(const float* X, int64_t n, int32_t d, int32_t n_r, int32_t s, int3
  *   allocation nodes) instead of the library's pool.
  *   Errors: RBC_ERR_ARG if idx/Q/outputs NULL, m < 0, k < 1, k > n,
  *   one-shot with k > s, or host memory under capture; RBC_ERR_UNSUPPORTED
- *   under capture with a plan other than the windowed one or with timing
+ *   under capture with a plan other than RBC_PLAN_WINDOW or with timing
  *   on; RBC_ERR_OOM; RBC_ERR_CUDA; RBC_ERR_TIMEOUT.
  */
 int rbc_search(const rbc_index* idx, const float* Q, int64_t m, int32_t k, int64_t* out_ids,

@@ -25,6 +25,7 @@ import numpy as np
 
 __all__ = [
     "L2", "L1", "EXACT", "ONESHOT", "F32", "BF16", "F16", "FP8E4M3", "PLAN_WINDOW", "PLAN_TILE_UNION",
+    "PLAN_WINDOW_OFFSET",
     "RbcError", "bf_search", "bf_search_noalloc", "rbc_build", "rbc_search", "rbc_sample_reps",
     "RbcIndex", "last_stats", "set_timing", "trim_workspace", "library_path", "load",
     "search_workspace", "plan_batch", "Server", "Group",
@@ -33,7 +34,7 @@ __all__ = [
 L2, L1 = 0, 1
 EXACT, ONESHOT = 0, 1
 F32, BF16, F16, FP8E4M3 = 0, 1, 2, 3
-PLAN_WINDOW, PLAN_TILE_UNION = 0, 1
+PLAN_WINDOW, PLAN_TILE_UNION, PLAN_WINDOW_OFFSET = 0, 1, 2
 _STATUS = {0: "ok", -1: "invalid argument", -2: "out of device memory", -3: "CUDA error",
            -4: "device wait timed out", -5: "unsupported"}
 

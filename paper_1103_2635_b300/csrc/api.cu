@@ -802,6 +802,38 @@ int make_lp_copies(rbc_index* ix, cudaStream_t st) {
                          ix->lp_max + 2, ix->lp_max + 3, st, ix->rscale));
   ix->Xlp = xl;
   ix->Rlp = rl;
+  if (ix->plan == RBC_PLAN_WINDOW_OFFSET && ix->mode == RBC_EXACT && ix->storage == RBC_BF16 &&
+      d % 8 == 0 && ix->offsets) {
+    // list rows as offsets from their representative: y~ = bf16(x - r)
+    float* y32 = nullptr;
+    RBC_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&y32), (size_t)n * (d + 1) * sizeof(float),
+                             st));
+    float* yerr = y32 + n * d;  // per-row |y - y~|
+    uint8_t* yl;
+    unsigned* ymax;
+    int rc = ix->alloc(&yl, n * ix->dpad * eb);
+    if (rc == RBC_OK) rc = ix->alloc(&ix->ynorm, n + NORM_PAD);
+    if (rc == RBC_OK) rc = ix->alloc(&ix->yerr_list, n_r);
+    if (rc == RBC_OK) rc = ix->alloc(&ymax, 2);
+    if (rc == RBC_OK)
+      rc = ix->alloc(reinterpret_cast<uint16_t**>(&ix->ynblock), (n + NORM_PAD) * NBLOCK_COLS);
+    if (rc == RBC_OK) rc = launch_offset_rows(ix->X32, ix->R32, ix->offsets, n_r, d, y32, st);
+    if (rc == RBC_OK) {
+      cudaError_t e = cudaMemsetAsync(ix->ynorm + n, 0, NORM_PAD * sizeof(float), st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(ymax, 0, 2 * sizeof(unsigned), st);
+      if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemsetAsync", __FILE__, __LINE__);
+    }
+    if (rc == RBC_OK)
+      rc = launch_to_lowp(y32, n, d, ix->dpad, ix->storage, yl, ix->ynorm, yerr, ymax, ymax + 1,
+                          st);
+    if (rc == RBC_OK) rc = launch_list_max(yerr, ix->offsets, n_r, ix->yerr_list, st);
+    if (rc == RBC_OK) rc = launch_norm_block(ix->ynorm, n, n + NORM_PAD, ix->ynblock, st);
+    if (rc == RBC_OK && ix->norm_fold_col >= 0)
+      rc = launch_fold_norm(yl, ix->ynorm, n, ix->dpad, d, ix->storage, st);
+    cudaFreeAsync(y32, st);
+    RBC_TRY(rc);
+    ix->Ylp = yl;
+  }
   return RBC_OK;
 }
 
@@ -1517,8 +1549,21 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   RBC_TRY(ar.alloc(&blk_off, window_block_offsets(mb, n_r)));
   int* scan_scratch;
   RBC_TRY(ar.alloc(&scan_scratch, exclusive_scan_scratch_ints((int)nbins)));
+  // representative offsets (an index built for them, FP32 queries 16-byte
+  // aligned): the count pass also takes each query's largest pair M
+  const bool offs = lp && ix->Ylp != nullptr && (reinterpret_cast<uintptr_t>(Qb) & 15) == 0;
+  if (offs && stream_capturing(st)) {
+    set_error("rbc_search: the offset plan reads its pair count back and cannot be recorded");
+    return RBC_ERR_UNSUPPORTED;
+  }
+  unsigned *mq = nullptr, *meps = nullptr;  // per query: M, and eps of its rows (emission)
+  if (offs) {
+    RBC_TRY(ar.alloc(&mq, 2 * mb));
+    meps = mq + mb;
+    RBC_CUDA(cudaMemsetAsync(mq, 0, 2 * mb * sizeof(unsigned), st));
+  }
   RBC_TRY(launch_window_pairs_count(D, mb, n_r, g, g1, ix->psi, simt_eps(d), totals, bin_off,
-                                    blk_off, cn.sums, st, scan_scratch));
+                                    blk_off, cn.sums, st, scan_scratch, mq));
   // pair arrays sized by the bound mb x n_r (batches are cut so that it stays
   // within WINDOW_MAX_PAIRS), so no count needs to come back to the host
   const int64_t pair_cap = mb * n_r;
@@ -1549,6 +1594,26 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   RBC_TRY(ar.alloc(&cc, mb));
   LpMatrix Qm{ql.lp, ql.norm, mb, ix->dpad, ix->storage};
   LpMatrix Xm{ix->Xlp, ix->xnorm, n, ix->dpad, ix->storage, ix->xnblock};
+  // the main pass's rows and the offsets it forms its query rows from
+  LpMatrix Ym = offs ? LpMatrix{ix->Ylp, ix->ynorm, n, ix->dpad, ix->storage, ix->ynblock} : Xm;
+  EmitOffsets eoff;
+  if (offs) {
+    // the kept pairs' query rows as offsets a~ = bf16(q - r), sized by the
+    // pair count (read back: the one host wait this plan adds)
+    int npairs = 0;
+    RBC_CUDA(cudaMemcpyAsync(&npairs, bin_off + nbins, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBC_CUDA(cudaStreamSynchronize(st));
+    uint8_t* arows;
+    float *rowt, *rown;
+    RBC_TRY(ar.alloc(&arows, (int64_t)std::max(npairs, 1) * ix->dpad * 2));
+    RBC_TRY(ar.alloc(&rowt, npairs));
+    RBC_TRY(ar.alloc(&rown, npairs));
+    RBC_TRY(launch_offset_pair_rows(pairs, bin_off, NB, n_r, Qb, ix->R32, ix->psi, ix->yerr_list,
+                                    g, d, ix->dpad, arows, rowt, rown, meps, st));
+    eoff.a_rows = arows;
+    eoff.row_t = rowt;
+    eoff.row_n = rown;
+  }
   // hit arena: each epilogue thread appends its emissions to its own slice
   // (no atomics in the kernel); a post-pass fills the per-query buffers.  The
   // slices together hold 256 records per query of the batch (about 5x the
@@ -1613,6 +1678,8 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   a.stream_count = lc + 4;
   a.f32 = lp ? 0 : 1;
   a.f32_eps = f32_eps;
+  a.mq_bits = mq;  // offset estimates (the overflow pass's raw scores: a2 clears them)
+  a.eps_bits = meps;
   // queries in nearest-representative order: the warps that run together
   // re-rank points of the same few lists, whose FP32 rows then come from L2
   a.rows = qorder;
@@ -1632,9 +1699,9 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   tmark(1, st);
   // the CUDA-core emission appends to the per-query buffers directly
   if (lp)
-    RBC_TRY(launch_bf_tc_emit(Qm, Xm, items, choff + n_r, max_items,
+    RBC_TRY(launch_bf_tc_emit(Qm, Ym, items, choff + n_r, max_items,
                               reinterpret_cast<const int*>(pairs), 2, eo_arena, sms, st, dev_err,
-                              ix->norm_fold_col));
+                              ix->norm_fold_col, offs ? &eoff : nullptr));
   else
     RBC_TRY(launch_bf_simt_emit(Qb, ix->X32, d, metric, items, choff + n_r, max_items,
                                 reinterpret_cast<const int*>(pairs), 2, eo, 2 * sms, st));
@@ -1656,7 +1723,7 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   // count on the device, so with no overflow they find no work.
   RBC_TRY(launch_overflow_split(fb_rows, lc, (int)mb, (int)(mb / 16 + 64), n_dense, fb2, lc2, st));
   RBC_TRY(launch_overflow_rethreshold(fb_rows, n_dense, mb, cs, cc, CAND_CAP, k, ql.norm, ql.err,
-                                      ix->lp_max, d, thr, st, f32_eps, metric));
+                                      ix->lp_max, d, thr, st, f32_eps, metric, mq, meps));
   RBC_TRY(launch_dense_emit_items(n_dense, n, xspan, max2, items2, n_items2, st));
   if (lp)
     RBC_TRY(launch_bf_tc_emit(Qm, Xm, items2, n_items2, max2, fb_rows, 1, eo, sms, st, dev_err,
@@ -1665,6 +1732,8 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
     RBC_TRY(launch_bf_simt_emit(Qb, ix->X32, d, metric, items2, n_items2, max2, fb_rows, 1, eo,
                                 2 * sms, st));
   CandSelectArgs a2 = a;
+  a2.mq_bits = nullptr;
+  a2.eps_bits = nullptr;
   a2.rows = fb_rows;
   a2.nrows_dev = n_dense;
   a2.nrows = (int)mb;
@@ -1770,7 +1839,8 @@ int64_t bound_window_batch(const rbc_index* ix, int64_t mb, int k) {
   b += bound_own_list(ix, mb);                               // pass A (tensor cores)
   b += bound_group(ix, mb, true) + cdiv(mb, TQ) * TQ * 2 * MAX_C * 8 +
        std::min<int64_t>(ix->n_r, mb) * TQ * 2 * MAX_C * 8;  // pass A (CUDA cores)
-  b += mb * 4;                                               // g
+  b += mb * 4 + (ix->Ylp ? mb * 8 : 0);                      // g, offset M and eps per query
+  if (ix->Ylp) b += mb * n_r * ((int64_t)dpad * 2 + 8) + 256;  // offset rows of the pairs
   b += nbins * 8 + 4 + window_block_offsets(mb, n_r) * 4;   // totals, offsets, block offsets
   b += ((int64_t)exclusive_scan_scratch_ints((int)nbins)) * 4; // their scan
   b += mb * 4 + mb * n_r * 8;                                // thr, pairs
@@ -1842,7 +1912,7 @@ int64_t search_batch_size(const rbc_index* ix, bool window) {
 // row maxima, which needs one scale per row: FP8 (a scale per column too)
 // takes the tile-union plan
 bool search_uses_window(const rbc_index* ix) {
-  if (ix->mode != RBC_EXACT || ix->plan != RBC_PLAN_WINDOW) return false;
+  if (ix->mode != RBC_EXACT || ix->plan == RBC_PLAN_TILE_UNION) return false;
   // FP32 storage or l1: the windowed plan on the CUDA cores
   if (!uses_lp(ix->storage, ix->metric)) return true;
   return ix->Xlp && ix->storage != RBC_FP8E4M3;
@@ -2042,9 +2112,10 @@ int rbc_build(const float* X, int64_t n, int32_t d, int32_t n_r, int32_t s, int3
     return RBC_ERR_ARG;
   }
   if (o.rerank_c < 0 || o.rerank_c > MAX_C ||
-      (o.plan != RBC_PLAN_WINDOW && o.plan != RBC_PLAN_TILE_UNION)) {
-    set_error("rbc_build: rerank_c must be in [0, %d] and plan RBC_PLAN_WINDOW or "
-              "RBC_PLAN_TILE_UNION", MAX_C);
+      (o.plan != RBC_PLAN_WINDOW && o.plan != RBC_PLAN_TILE_UNION &&
+       o.plan != RBC_PLAN_WINDOW_OFFSET)) {
+    set_error("rbc_build: rerank_c must be in [0, %d] and plan RBC_PLAN_WINDOW, "
+              "RBC_PLAN_TILE_UNION or RBC_PLAN_WINDOW_OFFSET", MAX_C);
     return RBC_ERR_ARG;
   }
   if (d > MAX_D) {
@@ -2135,9 +2206,9 @@ int rbc_search(const rbc_index* ix, const float* Q, int64_t m, int32_t k, int64_
   if (stream_capturing(st)) {
     // a recorded search may read nothing back: the windowed plan only, with
     // device-resident inputs and outputs and no phase timing
-    if (!window) {
+    if (!window || ix->Ylp) {
       set_error("rbc_search: under stream capture the index must use the windowed plan "
-                "(exact mode, FP32 / bf16 / fp16 storage)");
+                "without offsets (exact mode, FP32 / bf16 / fp16 storage)");
       return RBC_ERR_UNSUPPORTED;
     }
     if (m > 0 && (!is_device_ptr(Q) || !is_device_ptr(out_ids) || !is_device_ptr(out_dist))) {

@@ -84,6 +84,7 @@ struct EmitParams {
   uint32_t* dev_err;
   int fold_col;         // FOLD: the row element holding the norm pair (even)
   uint32_t fold_ones;   // FOLD: the pair (1, 1) in the storage type
+  EmitOffsets off;      // OFFS: per-pair rows a~ = bf16(q - r), bounds, |a~|^2
 };
 
 template <int KB, int BN, int S, int QSTAGES>
@@ -101,7 +102,8 @@ struct EmitSmem {
   static constexpr int OFF_ONES = OFF_NB + S * NB_STAGE;
   static constexpr int OFF_ROWQ = OFF_ONES + ONES_BYTES;        // [QSTAGES][BM] query id or -1
   static constexpr int OFF_ROWT = OFF_ROWQ + QSTAGES * BM * 4;  // [QSTAGES][BM] -T / 2
-  static constexpr int OFF_XWIN = OFF_ROWT + QSTAGES * BM * 4;  // [QSTAGES] item window
+  static constexpr int OFF_ROWN = OFF_ROWT + QSTAGES * BM * 4;  // [QSTAGES][BM] OFFS: |a~|^2
+  static constexpr int OFF_XWIN = OFF_ROWN + QSTAGES * BM * 4;  // [QSTAGES] item window
   static constexpr int OFF_BAR = OFF_XWIN + QSTAGES * 8;
   // full[S], empty[S], tfull[NBUF], tempty[NBUF], qfull[QS], qempty[QS]
   static constexpr int NBAR = 2 * S + 2 * NBUF + 2 * QSTAGES;
@@ -145,7 +147,12 @@ __device__ __forceinline__ void st_shared_zero16(uint32_t dst) {
 // themselves, and neither the norm block nor its MMA is needed.
 // DIRECT: hits go straight to the per-query buffers (no hit arena); each
 // instance holds only its own emission path.
-template <int KB, int BN, int S, int QSTAGES, bool FOLD = false, bool DIRECT = false>
+// OFFS: representative offsets -- an item's query rows are the rows
+// a~ = bf16(q - r) of its pairs (pair_begin + i), formed beforehand with
+// their emission bounds (accumulator units) and |a~|^2; a hit's value is
+// |a~|^2 - 2 acc, the estimate of |a~ - y~|^2.
+template <int KB, int BN, int S, int QSTAGES, bool FOLD = false, bool DIRECT = false,
+          bool OFFS = false>
 __global__ void __launch_bounds__(EpiShape<KB, BN>::THREADS, 1)
 bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap nbmap,
                   EmitParams p, uint32_t idesc, uint32_t idesc_norm) {
@@ -161,6 +168,7 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
   uint32_t* sOnes = reinterpret_cast<uint32_t*>(smem + L::OFF_ONES);
   int* sRowQ = reinterpret_cast<int*>(smem + L::OFF_ROWQ);
   float* sRowT = reinterpret_cast<float*>(smem + L::OFF_ROWT);
+  float* sRowN = reinterpret_cast<float*>(smem + L::OFF_ROWN);
   int2* sXwin = reinterpret_cast<int2*>(smem + L::OFF_XWIN);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
   constexpr int NBUF = L::NBUF;
@@ -256,17 +264,28 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
       }
       return false;
     };
-    // an item's query ids and thresholds (row lane + 32 t)
+    // an item's query ids and thresholds (row lane + 32 t); OFFS: the rows'
+    // bounds in accumulator units and |a~|^2, per pair
     int srcs[BM / 32];
     float thrs[BM / 32];
+    float nrms[OFFS ? BM / 32 : 1];
     auto meta = [&](const EmitItem& ee) {
 #pragma unroll
       for (int t = 0; t < BM / 32; ++t) {
         const int row = lane + 32 * t;
         srcs[t] = row < ee.nq ? p.pair_q[(int64_t)(ee.pair_begin + row) * p.pair_stride] : -1;
       }
+      if constexpr (OFFS) {
 #pragma unroll
-      for (int t = 0; t < BM / 32; ++t) thrs[t] = srcs[t] >= 0 ? p.out.thr[srcs[t]] : 0.0f;
+        for (int t = 0; t < BM / 32; ++t) {
+          const int64_t i = ee.pair_begin + lane + 32 * t;
+          thrs[t] = srcs[t] >= 0 ? p.off.row_t[i] : INFINITY;
+          nrms[t] = srcs[t] >= 0 ? p.off.row_n[i] : 0.0f;
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < BM / 32; ++t) thrs[t] = srcs[t] >= 0 ? p.out.thr[srcs[t]] : 0.0f;
+      }
     };
     int item = blockIdx.x;
     uint32_t qi = 0;
@@ -286,7 +305,12 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
       for (int t = 0; t < BM / 32; ++t) {
         const int row = lane + 32 * t;
         sRowQ[qs * BM + row] = srcs[t];
-        sRowT[qs * BM + row] = srcs[t] < 0 ? INFINITY : -0.5f * thrs[t];
+        if (OFFS) {
+          sRowT[qs * BM + row] = thrs[t];
+          sRowN[qs * BM + row] = nrms[t];
+        } else {
+          sRowT[qs * BM + row] = srcs[t] < 0 ? INFINITY : -0.5f * thrs[t];
+        }
       }
       // the copies: eight consecutive lanes move the eight 16-byte chunks of
       // one 128-byte K block of a row, so one instruction reads four whole
@@ -296,7 +320,9 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
       for (int i = 0; i < BM / 4; ++i) {
         const int row = 4 * i + (lane >> 3);
         const int src = __shfl_sync(0xffffffffu, srcs[i >> 3], (4 * i + (lane >> 3)) & 31);
-        const uint8_t* g = p.qlp + (int64_t)(src >= 0 ? src : 0) * p.q_row_bytes + c * 16;
+        // OFFS: the row of the item's pair (query rows are per pair)
+        const int64_t srow = OFFS ? (int64_t)e.pair_begin + row : (int64_t)src;
+        const uint8_t* g = (OFFS ? p.off.a_rows : p.qlp) + (src >= 0 ? srow : 0) * p.q_row_bytes + c * 16;
 #pragma unroll
         for (int kb = 0; kb < KB; ++kb) {
           const uint32_t dst = qbase + kb * BM * 128 + row * 128 + ((c ^ (row & 7)) << 4);
@@ -425,6 +451,7 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
       const int2 xw = sXwin[qs];
       const int myq = sRowQ[qs * BM + row];
       const float myT = sRowT[qs * BM + row];  // -T(q) / 2: emit where the accumulator reaches it
+      const float myN = OFFS ? sRowN[qs * BM + row] : 0.0f;  // OFFS: |a~|^2 of the row
       __syncwarp();
       if (lane == 0) mbar_arrive(&qempty[qs]);
       if (xw.y <= xw.x) break;  // the end mark
@@ -472,7 +499,7 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
                 const int j = __ffs(mask) - 1;
                 mask &= mask - 1;
                 const float v = __uint_as_float(pick32(raw[c], j));
-                hits[nhits++] = make_int4(myq, cb + j, __float_as_int(-2.0f * v), 0);
+                hits[nhits++] = make_int4(myq, cb + j, __float_as_int(fmaf(-2.0f, v, myN)), 0);
               }
             } else {
               // direct appends (and, in the arena instance, the hits of a
@@ -486,7 +513,7 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
                 mask &= mask - 1;
                 const float v = __uint_as_float(pick32(raw[c], j));
                 if (pos < cap) {
-                  cs[pos] = -2.0f * v;
+                  cs[pos] = fmaf(-2.0f, v, myN);
                   cr[pos] = cb + j;
                 }
                 ++pos;
@@ -511,10 +538,11 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
   }
 }
 
-template <int KB, int BN, int S, int QS, bool FOLD, bool DIRECT>
+template <int KB, int BN, int S, int QS, bool FOLD, bool DIRECT, bool OFFS = false>
 int launch_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
                 const int* num_items_dev, int max_items, const int* pair_q, int pair_stride,
-                const EmitOut& out, int grid, cudaStream_t st, uint32_t* dev_err, int fold_col) {
+                const EmitOut& out, int grid, cudaStream_t st, uint32_t* dev_err, int fold_col,
+                const EmitOffsets* offs = nullptr) {
   using L = EmitSmem<KB, BN, S, QS>;
   CUtensorMap xmap, nbmap;
   RBC_TRY_TC(encode_map(&xmap, Xm.data, Xm.rows, Xm.dpad, Xm.storage, BN));
@@ -522,11 +550,12 @@ int launch_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
     memset(&nbmap, 0, sizeof(nbmap));  // not read: the norm is in the rows
   else
     RBC_TRY_TC(encode_nblock_map(&nbmap, Xm.nblock, Xm.rows, BN));
-  auto kern = bf_tc_emit_kernel<KB, BN, S, QS, FOLD, DIRECT>;
+  auto kern = bf_tc_emit_kernel<KB, BN, S, QS, FOLD, DIRECT, OFFS>;
   RBC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC));
   EmitParams p{items,  num_items_dev, max_items, pair_q, pair_stride,
                static_cast<const uint8_t*>(Qm.data), (int64_t)Qm.dpad * 2, Xm.norm, out, dev_err,
-               fold_col, Qm.storage == RBC_BF16 ? 0x3F803F80u : 0x3C003C00u};
+               fold_col, Qm.storage == RBC_BF16 ? 0x3F803F80u : 0x3C003C00u,
+               offs ? *offs : EmitOffsets{}};
   const uint32_t idesc = idesc_f16(Qm.storage == RBC_BF16 ? 1 : 0, BM, BN);
   const uint32_t idesc_norm = idesc_f16(1, BM, BN);  // the norm block is bf16 for any storage
   kern<<<grid, EpiShape<KB, BN>::THREADS, L::ALLOC, st>>>(xmap, nbmap, p, idesc, idesc_norm);
@@ -548,7 +577,7 @@ int launch_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
 int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
                       const int* num_items_dev, int max_items, const int* pair_q,
                       int pair_stride, const EmitOut& out, int grid, cudaStream_t st,
-                      uint32_t* dev_err, int fold_col) {
+                      uint32_t* dev_err, int fold_col, const EmitOffsets* offs) {
   if (!tc_available()) {
     set_error("tensor-core BF kernel needs an sm_103 device");
     return RBC_ERR_UNSUPPORTED;
@@ -566,12 +595,23 @@ int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* it
     set_error("tensor-core emission: folded norm column %d invalid", fold_col);
     return RBC_ERR_ARG;
   }
+  if (offs && (Xm.storage != RBC_BF16 || !offs->a_rows || !offs->row_t || !offs->row_n ||
+               out.arena == nullptr || (reinterpret_cast<uintptr_t>(offs->a_rows) & 15))) {
+    set_error("tensor-core emission: offset rows need bf16, the per-pair rows and bounds, and "
+              "the hit arena");
+    return RBC_ERR_ARG;
+  }
   // d <= 128: 256-row database tiles (the fewest MMA instructions per
   // column); longer rows: 64-row tiles
 #define RBC_EMIT_ONE(KB, BN, S, QS, FOLD, DIRECT)                                         \
   launch_emit<KB, BN, S, QS, FOLD, DIRECT>(Qm, Xm, items, num_items_dev, max_items, pair_q,   \
                                            pair_stride, out, grid, st, dev_err, fold_col)
+#define RBC_EMIT_OFFS(KB, BN, S, QS, FOLD)                                                \
+  launch_emit<KB, BN, S, QS, FOLD, false, true>(Qm, Xm, items, num_items_dev, max_items, pair_q, \
+                                               pair_stride, out, grid, st, dev_err, fold_col, offs)
 #define RBC_EMIT(KB, BN, S, QS)                                                             \
+  if (offs)                                                                                 \
+    return fold_col >= 0 ? RBC_EMIT_OFFS(KB, BN, S, QS, true) : RBC_EMIT_OFFS(KB, BN, S, QS, false); \
   return direct ? (fold_col >= 0 ? RBC_EMIT_ONE(KB, BN, S, QS, true, true)                   \
                                  : RBC_EMIT_ONE(KB, BN, S, QS, false, true))                 \
                 : (fold_col >= 0 ? RBC_EMIT_ONE(KB, BN, S, QS, true, false)                  \
@@ -585,6 +625,7 @@ int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* it
     default: break;
   }
 #undef RBC_EMIT
+#undef RBC_EMIT_OFFS
 #undef RBC_EMIT_ONE
   set_error("tensor-core BF: padded dimension %d unsupported", Qm.dpad);
   return RBC_ERR_UNSUPPORTED;

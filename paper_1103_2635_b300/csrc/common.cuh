@@ -278,6 +278,47 @@ __host__ __device__ __forceinline__ float dist_upper(float s, float qn, float qe
   return (sqrtf(fmaxf(t, 0.0f)) * (1.0f + 4.8e-7f) + qerr + xerr) * (1.0f + 4.8e-7f);
 }
 
+// Representative-offset estimates (windowed plan with offset rows, bf16).
+// The query row a = q - r and each list row y = x - r of r's list are formed
+// in FP32 and rounded to bf16; with eps >= |a - a~| + |y - y~| (measured
+// residuals: the query row's from its own rounding, the list's largest from
+// the build, plus the FP32 subtraction's 2^-24 |a|) the exact distance
+// rho = |a - y| is within eps of |a~ - y~|.  The kernel's estimate v of
+// |a~ - y~|^2 (the FP32 |a~|^2 minus twice the accumulator of
+// a~.y~ - |y~|^2 / 2) is within A(M) = (2 (d + 4) 2^-19 + 2^-15) (M (1 + c))^2
+// of |a~ - y~|^2 for M >= |a| + |y| and c = 2^-8 (1 + 2^-7) >= the bf16
+// rounding's relative size: the low-precision score's FP32 evaluation and
+// norm-pair terms as in score_bound, plus the FP32 |a~|^2 and the final
+// subtraction.  Hence rho <= sqrt(max(v, 0) + A) + eps and
+// rho >= sqrt(max(0, v - A)) - eps.
+constexpr float OFF_C = 3.9367676e-03f;  // 2^-8 (1 + 2^-7)
+// M of a (query, representative) pair from rho(q, r) as stage one computed it
+// (relative error below 1e-4) and the list's radius bound psi_r; explicit
+// roundings, so that every kernel computes the same value from the same inputs
+__host__ __device__ __forceinline__ float off_pair_m(float rho_qr, float psi_r) {
+#ifdef __CUDA_ARCH__
+  return __fmul_ru(__fadd_ru(__fmul_ru(rho_qr, 1.0001f), psi_r), 1.0000005f);
+#else
+  return (rho_qr * 1.0001f + psi_r) * 1.0000005f;
+#endif
+}
+__host__ __device__ __forceinline__ float off_arith(float M, int d) {
+  const float s = M * (1.0f + OFF_C) * (1.0f + 4.8e-7f);
+  return ((float)(2 * (d + 4)) * 1.9073486e-06f + 3.0517578e-05f) * s * s * (1.0f + 4.8e-7f);
+}
+// Largest estimate v a point within distance g of q can have.
+__host__ __device__ __forceinline__ float off_value_bound(float g, float M, float eps, int d) {
+  if (!(g < INFINITY)) return INFINITY;
+  const float G = (g + eps) * (1.0f + 4.8e-7f);
+  return (G * G * (1.0f + 4.8e-7f) + off_arith(M, d)) * (1.0f + 4.8e-7f) + 1e-30f;
+}
+// Largest distance a point with estimate v can have from q.
+__host__ __device__ __forceinline__ float off_dist_upper(float v, float M, float eps, int d) {
+  if (!(v < INFINITY)) return INFINITY;
+  const float t = (fmaxf(v, 0.0f) + off_arith(M, d)) * (1.0f + 4.8e-7f);
+  return (sqrtf(t) * (1.0f + 4.8e-7f) + eps) * (1.0f + 4.8e-7f);
+}
+
 // FP32 difference-form values (rho^2 for l2, rho for l1) with relative error
 // at most eps: the largest distance a value s can stand for (s >= v (1 - eps)
 // for the exact value v, so v <= s (1 + 2 eps)), and the largest value a point

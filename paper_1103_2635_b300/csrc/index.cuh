@@ -32,6 +32,13 @@ struct rbc_index {
   void* Rlp = nullptr;        // [n_r, dpad]
   float* rnorm = nullptr;     // [n_r]
   int norm_fold_col = -1;     // >= 0: Xlp carries -|x~|^2 / 2 in columns col, col + 1
+  // windowed plan with representative offsets (bf16, l2): y~ = bf16(x - r)
+  // of every list row (list r), its |y~|^2 and norm block; with
+  // norm_fold_col >= 0 the rows carry -|y~|^2 / 2 in that column pair too
+  void* Ylp = nullptr;        // [list_entries, dpad]
+  float* ynorm = nullptr;     // [list_entries + NORM_PAD]
+  void* ynblock = nullptr;    // [list_entries + NORM_PAD, 16]
+  float* yerr_list = nullptr; // [n_r] largest |y - y~| of each list, rounded up
   float* xscale = nullptr;    // FP8: [list_entries + NORM_PAD] per-row power-of-two scales
   float* rscale = nullptr;    // FP8: [n_r]
   // device error flags of searches that could not report them when they

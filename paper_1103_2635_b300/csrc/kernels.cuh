@@ -82,6 +82,7 @@ struct EmitItem {
   int32_t nq;
   int32_t x_begin;
   int32_t x_end;
+  int32_t rep;  // the representative whose list holds the window (-1: any rows)
 };
 
 // Candidate emission: every (query, row) pair whose score is <= thr[query]
@@ -121,10 +122,20 @@ int launch_overflow_split(const int* rows, const int* n_dev, int max_rows, int l
 // fold_col >= 0: the database rows carry -|x~|^2 / 2 as a (high, low) pair
 // in padding columns fold_col, fold_col + 1 (launch_fold_norm), so no norm
 // block or norm MMA is used.
+// Representative-offset rows (bf16): Xm holds y~ = bf16(x - r) per list
+// row; the query rows of an item are the rows a_rows[pair_begin + i] (one
+// per kept pair, launch_offset_pair_rows) with their emission bounds in
+// accumulator units row_t and |a~|^2 row_n; a hit's value is the estimate
+// |a~|^2 - 2 acc of |a~ - y~|^2.
+struct EmitOffsets {
+  const uint8_t* a_rows = nullptr;  // [pairs, dpad] bf16, 16-byte aligned
+  const float* row_t = nullptr;     // [pairs]
+  const float* row_n = nullptr;     // [pairs]
+};
 int launch_bf_tc_emit(const LpMatrix& Qm, const LpMatrix& Xm, const EmitItem* items,
                       const int* num_items_dev, int max_items, const int* pair_q,
                       int pair_stride, const EmitOut& out, int grid, cudaStream_t st,
-                      uint32_t* dev_err, int fold_col = -1);
+                      uint32_t* dev_err, int fold_col = -1, const EmitOffsets* offs = nullptr);
 
 // The same windowed stage two on CUDA cores (FP32 rows, l2 or l1): every
 // (query, window row) whose FP32 difference-form value (rho^2 for l2, rho
@@ -255,6 +266,11 @@ struct CandSelectArgs {
   // instead of going to the re-search
   int* stream_rows = nullptr;
   int* stream_count = nullptr;
+  // representative-offset values (launch_bf_tc_emit with offsets): [m] M and
+  // eps of each query as float bits; the survivor bound comes from
+  // off_dist_upper
+  const unsigned* mq_bits = nullptr;
+  const unsigned* eps_bits = nullptr;
   // FP32 candidates (CUDA-core emission): scores are FP32 difference-form
   // values with relative error <= f32_eps; the low-precision fields are unused
   int f32 = 0;
@@ -289,10 +305,25 @@ int launch_own_kth_lp(const float* ps, const int* pi, int C, const int* qsrc, in
 int window_buckets();
 int64_t window_pair_blocks(int64_t m);
 int64_t window_block_offsets(int64_t m, int n_r);
+// (mq_bits != nullptr: also mq_bits[q] = max over q's kept pairs of
+// off_pair_m(rho(q, r), psi_r) as float bits; mq_bits zeroed by the caller)
+// Representative offsets of the kept pairs (binned as by the scatter pass,
+// bins of r in bin_off[r nb .. (r + 1) nb]): for pair i = (q, rho(q, r)),
+// a_rows[i] = bf16(fl(q - r)) ([dpad] columns, zero padded), row_n[i] =
+// |a~|^2, row_t[i] = 0.5 (|a~|^2 - T) lowered by a few units in the last
+// place with T = off_value_bound(g(q), M, eps, d), M = off_pair_m(rho, psi_r),
+// eps = |fl(q - r) - a~| (measured) + yerr[r] + 2^-23 M; eps_bits[q] (zeroed
+// by the caller) = the largest eps of q's pairs.  d % 8 == 0, Q32 and R32
+// 16-byte aligned.
+int launch_offset_pair_rows(const int2* pairs, const int* bin_off, int nb, int n_r,
+                            const float* Q32, const float* R32, const float* psi,
+                            const float* yerr, const float* g, int d, int dpad, void* a_rows,
+                            float* row_t, float* row_n, unsigned* eps_bits, cudaStream_t st);
 int launch_window_pairs_count(const float* D, int64_t m, int n_r, const float* g,
                               const float* g1, const float* psi_plus, float rel, int* totals,
                               int* bin_off, int* blk_off, unsigned long long* kept_sum,
-                              cudaStream_t st, int* scan_scratch = nullptr);
+                              cudaStream_t st, int* scan_scratch = nullptr,
+                              unsigned* mq_bits = nullptr);
 int launch_window_pairs_scatter(const float* D, int64_t m, int n_r, const float* g,
                                 const float* g1, const float* psi_plus, float rel,
                                 const int* bin_off, int* blk_off, int2* pairs, cudaStream_t st);
@@ -310,11 +341,14 @@ int launch_window_items(const int* bin_off, int nb, int n_r, const int2* pairs,
 // spans of xspan) for the emission kernel.
 // (the number of rows is read from n_dev on the device; at most max_rows)
 // (qnorm == nullptr: FP32 difference-form scores, bounds from f32_eps / metric)
+// (mq_bits != nullptr: the stored values are representative-offset
+// estimates, bounded with mq_bits[q] as M and eps_bits[q] as eps)
 int launch_overflow_rethreshold(const int* rows, const int* n_dev, int64_t max_rows,
                                 const float* cand_score, int* cand_cnt, int cap, int k,
                                 const float* qnorm, const float* qerr, const unsigned* lp_max,
                                 int d, float* thr, cudaStream_t st, float f32_eps = 0.0f,
-                                int metric = RBC_L2);
+                                int metric = RBC_L2, const unsigned* mq_bits = nullptr,
+                                const unsigned* eps_bits = nullptr);
 int launch_dense_emit_items(const int* n_dev, int64_t x_rows, int xspan, int max_items,
                             EmitItem* items, int* num_items, cudaStream_t st);
 // (qnorm == nullptr: thr = f32_score_bound(g, f32_eps, metric))
@@ -364,6 +398,12 @@ namespace rbc {
 // ---- data movement and preparation (prep.cu) ----
 int launch_gather_rows(const float* src, const int64_t* idx64, const int* idx32, int64_t rows,
                        int d, float* dst, cudaStream_t st);
+// Y rows = X rows of list r minus R row r, for every list r (lists
+// [offsets[r], offsets[r + 1]) of the list-ordered rows), FP32
+int launch_offset_rows(const float* X, const float* R, const int* offsets, int n_r, int d,
+                       float* Y, cudaStream_t st);
+// out[r] = the largest v[i] over list r's rows [offsets[r], offsets[r + 1])
+int launch_list_max(const float* v, const int* offsets, int n_r, float* out, cudaStream_t st);
 // FP32 rows -> low-precision rows [rows, dpad] (zero padded), |x~|^2, |x - x~|
 // (FP64, rounded up); global maxima of |x - x~| and |x~| as float bits.
 int launch_to_lowp(const float* src, int64_t rows, int d, int dpad, int storage, void* dst,

@@ -216,6 +216,32 @@ __global__ void map_rows_kernel(const int* __restrict__ rows, const int* __restr
     out[i] = qorig ? qorig[rows[i]] : rows[i];
 }
 
+// out[r] = max of v over list r's rows (block r; 0 for an empty list).
+__global__ void list_max_kernel(const float* __restrict__ v, const int* __restrict__ offsets,
+                                float* __restrict__ out) {
+  __shared__ float part[8];
+  float m = 0.0f;
+  for (int i = offsets[blockIdx.x] + threadIdx.x; i < offsets[blockIdx.x + 1]; i += blockDim.x)
+    m = fmaxf(m, v[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, part[w]);
+    out[blockIdx.x] = m;
+  }
+}
+
+// Y[i] = X[i] - R[r] for the rows i of list r (block r), FP32.
+__global__ void offset_rows_kernel(const float* __restrict__ X, const float* __restrict__ R,
+                                   const int* __restrict__ offsets, int d, float* __restrict__ Y) {
+  const int r = blockIdx.x;
+  const int64_t b = (int64_t)offsets[r] * d, e = (int64_t)offsets[r + 1] * d;
+  const float* rr = R + (int64_t)r * d;
+  for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) Y[i] = X[i] - rr[(i - b) % d];
+}
+
 }  // namespace
 
 int launch_map_rows(const int* rows, const int* n_dev, int n, const int* qorig, int* out,
@@ -262,6 +288,21 @@ int launch_gather_rows(const float* src, const int64_t* idx64, const int* idx32,
   gather_rows_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(src, idx64, idx32, rows,
                                                                        d, dst);
   RBC_LAUNCH_CHECK("gather_rows_kernel");
+  return RBC_OK;
+}
+
+int launch_list_max(const float* v, const int* offsets, int n_r, float* out, cudaStream_t st) {
+  if (n_r <= 0) return RBC_OK;
+  list_max_kernel<<<n_r, 256, 0, st>>>(v, offsets, out);
+  RBC_LAUNCH_CHECK("list_max_kernel");
+  return RBC_OK;
+}
+
+int launch_offset_rows(const float* X, const float* R, const int* offsets, int n_r, int d,
+                       float* Y, cudaStream_t st) {
+  if (n_r <= 0) return RBC_OK;
+  offset_rows_kernel<<<n_r, 256, 0, st>>>(X, R, offsets, d, Y);
+  RBC_LAUNCH_CHECK("offset_rows_kernel");
   return RBC_OK;
 }
 

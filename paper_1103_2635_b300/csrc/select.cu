@@ -522,6 +522,11 @@ __global__ void __launch_bounds__(WARPS * 32) select_cands_kernel(CandSelectArgs
   if (a.f32) {
     smax = f32_score_bound(f32_dist_upper(key_score(kth), a.f32_eps, a.metric), a.f32_eps,
                            a.metric);
+  } else if (a.mq_bits) {
+    // representative-offset estimates: every candidate's row has M <= M_q
+    // and eps <= eps_q
+    const float M = __uint_as_float(a.mq_bits[q]), eps = __uint_as_float(a.eps_bits[q]);
+    smax = off_value_bound(off_dist_upper(key_score(kth), M, eps, a.d), M, eps, a.d);
   } else {
     const float qn = a.q_lpnorm[q], qe = a.q_err[q];
     const float xe = __uint_as_float(*a.x_err_max_bits), xn = __uint_as_float(*a.x_norm_max_bits);
@@ -703,6 +708,9 @@ __global__ void __launch_bounds__(WARPS * 32) select_stream_kernel(CandSelectArg
     if (a.f32) {
       smax = f32_score_bound(f32_dist_upper(key_score(kth), a.f32_eps, a.metric), a.f32_eps,
                              a.metric);
+    } else if (a.mq_bits) {
+      const float M = __uint_as_float(a.mq_bits[q]), eps = __uint_as_float(a.eps_bits[q]);
+      smax = off_value_bound(off_dist_upper(key_score(kth), M, eps, d), M, eps, d);
     } else {
       const float qn = a.q_lpnorm[q], qe = a.q_err[q];
       smax = score_bound(dist_upper(key_score(kth), qn, qe, xe, xn, d), qn, qe, xe, xn, d);

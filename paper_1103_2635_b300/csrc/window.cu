@@ -30,6 +30,8 @@
 // (block, bin) on an array of n_r NB counters that stays in L2, and the
 // pairs of one bin from one block land in consecutive slots.
 
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -186,7 +188,7 @@ wpairs_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __re
               const float* __restrict__ g1, const float* __restrict__ psi_plus, float rel,
               int* __restrict__ bin_ctr, const int* __restrict__ bin_off,
               int* __restrict__ blk_off, int2* __restrict__ pairs,
-              unsigned long long* __restrict__ kept_sum) {
+              unsigned long long* __restrict__ kept_sum, unsigned* __restrict__ mq_bits) {
   __shared__ float tiles[WW][WT][WT + 1];
   __shared__ int h[RSPAN * NBK];
   __shared__ float spsi[RSPAN], sscale[RSPAN];
@@ -205,6 +207,7 @@ wpairs_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __re
   __syncthreads();
   const int64_t q0 = ((int64_t)blockIdx.x * WW + wid) * WT;
   const PairCtx c = pair_ctx(q0, lane, m, g, g1, rel);
+  float mq = 0.0f;  // count pass with offsets: the largest M of the lane's kept pairs
   // one pass over the warp's tiles: count, or (place) take the slots
   auto walk = [&](bool place) {
     int kept = 0;
@@ -222,6 +225,7 @@ wpairs_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __re
           } else {
             ++kept;
             atomicAdd(hp, 1);
+            if (mq_bits) mq = fmaxf(mq, off_pair_m(v, spsi[rl]));
           }
         }
       }
@@ -234,6 +238,7 @@ wpairs_kernel(const float* __restrict__ D, int64_t m, int n_r, const float* __re
     return;
   }
   const int kept = walk(false);
+  if (mq_bits && mq > 0.0f) atomicMax(mq_bits + c.q, __float_as_uint(mq));
   __syncthreads();
   {
     for (int i = threadIdx.x; i < (re - rb) * NBK; i += blockDim.x)
@@ -364,7 +369,7 @@ window_items_kernel(const int* __restrict__ chunk_off, int n_r, const int* __res
     xb += ob;
     xe += ob;
     if (lane == 0) {
-      items[c] = EmitItem{begin, end - begin, xb, xe > xb ? xe : xb};
+      items[c] = EmitItem{begin, end - begin, xb, xe > xb ? xe : xb, r};
       if (xe > xb) {
         rows_sum += (unsigned long long)(xe - xb);
         pairs_sum += (unsigned long long)(end - begin) * (unsigned long long)(xe - xb);
@@ -396,7 +401,9 @@ __global__ void overflow_rethreshold_kernel(const int* __restrict__ rows,
                                             const float* __restrict__ qnorm,
                                             const float* __restrict__ qerr,
                                             const unsigned* __restrict__ lp_max, int d,
-                                            float* __restrict__ thr, float f32_eps, int metric) {
+                                            float* __restrict__ thr, float f32_eps, int metric,
+                                            const unsigned* __restrict__ mq_bits,
+                                            const unsigned* __restrict__ eps_bits) {
   const int lane = threadIdx.x & 31;
   const int n = *n_dev;
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n;
@@ -421,8 +428,13 @@ __global__ void overflow_rethreshold_kernel(const int* __restrict__ rows,
     }
     const float sk = __uint_as_float((res & 0x80000000u) ? (res & 0x7fffffffu) : ~res);
     if (qnorm) {
+      // stored values: low-precision scores, or offset estimates whose
+      // distance bound the raw scores of the dense pass then use
       const float xe = __uint_as_float(lp_max[0]), xn = __uint_as_float(lp_max[1]);
-      t = score_bound(dist_upper(sk, qnorm[q], qerr[q], xe, xn, d), qnorm[q], qerr[q], xe, xn, d);
+      const float u = mq_bits ? off_dist_upper(sk, __uint_as_float(mq_bits[q]),
+                                               __uint_as_float(eps_bits[q]), d)
+                              : dist_upper(sk, qnorm[q], qerr[q], xe, xn, d);
+      t = score_bound(u, qnorm[q], qerr[q], xe, xn, d);
     } else {
       t = f32_score_bound(f32_dist_upper(sk, f32_eps, metric), f32_eps, metric);
     }
@@ -446,7 +458,7 @@ __global__ void dense_emit_items_kernel(const int* __restrict__ n_dev, int64_t x
     const int c = i / nsplit, sp = i - c * nsplit;
     const int64_t xb = (int64_t)sp * xspan;
     const int64_t xe = xb + xspan < x_rows ? xb + xspan : x_rows;
-    items[i] = EmitItem{c * TQ, min(TQ, n - c * TQ), (int)xb, (int)xe};
+    items[i] = EmitItem{c * TQ, min(TQ, n - c * TQ), (int)xb, (int)xe, -1};
   }
 }
 
@@ -504,6 +516,84 @@ __global__ void score_threshold_kernel(const float* __restrict__ g, const float*
 
 }  // namespace
 
+// One block per representative r, each warp four pairs at a time (eight
+// lanes per pair, lane c holding elements 8 c + 64 kb .. + 7 of every 64).
+__global__ void __launch_bounds__(256)
+offset_pair_rows_kernel(const int2* __restrict__ pairs, const int* __restrict__ bin_off, int nb,
+                        const float* __restrict__ Q32, const float* __restrict__ R32,
+                        const float* __restrict__ psi, const float* __restrict__ yerr,
+                        const float* __restrict__ g, int d, int dpad, uint4* __restrict__ a_rows,
+                        float* __restrict__ row_t, float* __restrict__ row_n,
+                        unsigned* __restrict__ eps_bits) {
+  const int r = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5, c = lane & 7;
+  const int b = bin_off[(int64_t)r * nb], e = bin_off[(int64_t)(r + 1) * nb];
+  if (b >= e) return;
+  const float psi_r = psi[r], yerr_r = yerr[r];
+  const float* rr = R32 + (int64_t)r * d;
+  const int kbs = dpad / 64;
+  for (int i0 = b + 4 * wid; i0 < e; i0 += 32) {
+    const int i = i0 + (lane >> 3);
+    const bool live = i < e;
+    const int2 pr = pairs[live ? i : b];
+    const float* qr = Q32 + (int64_t)pr.x * d;
+    float n2 = 0.0f, e2 = 0.0f;
+    for (int kb = 0; kb < kbs; ++kb) {
+      const int j0 = kb * 64 + 8 * c;
+      uint4 w = make_uint4(0u, 0u, 0u, 0u);
+      if (j0 < d) {
+        const float4 q0 = *reinterpret_cast<const float4*>(qr + j0);
+        const float4 q1 = *reinterpret_cast<const float4*>(qr + j0 + 4);
+        const float4 r0 = *reinterpret_cast<const float4*>(rr + j0);
+        const float4 r1 = *reinterpret_cast<const float4*>(rr + j0 + 4);
+        const float a[8] = {q0.x - r0.x, q0.y - r0.y, q0.z - r0.z, q0.w - r0.w,
+                            q1.x - r1.x, q1.y - r1.y, q1.z - r1.z, q1.w - r1.w};
+        uint32_t ww[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const __nv_bfloat162 bb = __floats2bfloat162_rn(a[2 * u], a[2 * u + 1]);
+          ww[u] = (uint32_t)__bfloat16_as_ushort(bb.x) | ((uint32_t)__bfloat16_as_ushort(bb.y) << 16);
+          const float lo = __uint_as_float(ww[u] << 16), hi = __uint_as_float(ww[u] & 0xffff0000u);
+          n2 = fmaf(hi, hi, fmaf(lo, lo, n2));
+          const float d0 = a[2 * u] - lo, d1 = a[2 * u + 1] - hi;  // exact
+          e2 = fmaf(d1, d1, fmaf(d0, d0, e2));
+        }
+        w = make_uint4(ww[0], ww[1], ww[2], ww[3]);
+      }
+      if (live) a_rows[((int64_t)i * dpad + kb * 64 + 8 * c) / 8] = w;
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+      e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+    }
+    if (live && c == 0) {
+      const float M = off_pair_m(__int_as_float(pr.y), psi_r);
+      const float ea = __fsqrt_ru(e2 * (1.0f + 3.0517578e-05f)) * (1.0f + 2.4e-7f);
+      const float eps = (ea + yerr_r + 1.1920929e-07f * M) * (1.0f + 2.4e-7f);
+      const float T = off_value_bound(g[pr.x], M, eps, d);
+      row_n[i] = n2;
+      row_t[i] = T < INFINITY ? 0.5f * (n2 - T) - 2.4e-7f * (n2 + T) - 1e-30f : -INFINITY;
+      atomicMax(eps_bits + pr.x, __float_as_uint(eps));
+    }
+  }
+}
+
+int launch_offset_pair_rows(const int2* pairs, const int* bin_off, int nb, int n_r,
+                            const float* Q32, const float* R32, const float* psi,
+                            const float* yerr, const float* g, int d, int dpad, void* a_rows,
+                            float* row_t, float* row_n, unsigned* eps_bits, cudaStream_t st) {
+  if (n_r <= 0) return RBC_OK;
+  if (d % 8 != 0 || dpad % 64 != 0 || d > dpad) {
+    set_error("offset rows: d %d must be a multiple of 8 within dpad %d", d, dpad);
+    return RBC_ERR_ARG;
+  }
+  offset_pair_rows_kernel<<<n_r, 256, 0, st>>>(pairs, bin_off, nb, Q32, R32, psi, yerr, g, d,
+                                               dpad, static_cast<uint4*>(a_rows), row_t, row_n,
+                                               eps_bits);
+  RBC_LAUNCH_CHECK("offset_pair_rows_kernel");
+  return RBC_OK;
+}
+
 int launch_gbound(const float* own, const float* gk, int64_t m, float rel_rep, float* g,
                   cudaStream_t st) {
   if (m <= 0) return RBC_OK;
@@ -527,14 +617,14 @@ int64_t window_pair_blocks(int64_t m) { return (m + WW * WT - 1) / (WW * WT); }
 int launch_window_pairs_count(const float* D, int64_t m, int n_r, const float* g,
                               const float* g1, const float* psi_plus, float rel, int* totals,
                               int* bin_off, int* blk_off, unsigned long long* kept_sum,
-                              cudaStream_t st, int* scan_scratch) {
+                              cudaStream_t st, int* scan_scratch, unsigned* mq_bits) {
   const int64_t nbins = (int64_t)n_r * NBK;
   const int64_t qblocks = window_pair_blocks(m);
   RBC_CUDA(cudaMemsetAsync(totals, 0, nbins * sizeof(int), st));
   if (qblocks > 0) {
     const dim3 grid((unsigned)qblocks, (n_r + RSPAN - 1) / RSPAN);
     wpairs_kernel<false><<<grid, WW * 32, 0, st>>>(D, m, n_r, g, g1, psi_plus, rel, totals,
-                                                   nullptr, blk_off, nullptr, kept_sum);
+                                                   nullptr, blk_off, nullptr, kept_sum, mq_bits);
     RBC_LAUNCH_CHECK("wpairs_kernel");
   }
   return launch_exclusive_scan(totals, (int)nbins, bin_off, st, scan_scratch);
@@ -551,7 +641,7 @@ int launch_window_pairs_scatter(const float* D, int64_t m, int n_r, const float*
   if (qblocks == 0) return RBC_OK;
   const dim3 grid((unsigned)qblocks, (n_r + RSPAN - 1) / RSPAN);
   wpairs_kernel<true><<<grid, WW * 32, 0, st>>>(D, m, n_r, g, g1, psi_plus, rel, nullptr,
-                                                bin_off, blk_off, pairs, nullptr);
+                                                bin_off, blk_off, pairs, nullptr, nullptr);
   RBC_LAUNCH_CHECK("wpairs_kernel");
   return RBC_OK;
 }
@@ -589,11 +679,13 @@ int launch_score_threshold(const float* g, const float* qnorm, const float* qerr
 int launch_overflow_rethreshold(const int* rows, const int* n_dev, int64_t max_rows,
                                 const float* cand_score, int* cand_cnt, int cap, int k,
                                 const float* qnorm, const float* qerr, const unsigned* lp_max,
-                                int d, float* thr, cudaStream_t st, float f32_eps, int metric) {
+                                int d, float* thr, cudaStream_t st, float f32_eps, int metric,
+                                const unsigned* mq_bits, const unsigned* eps_bits) {
   if (max_rows <= 0) return RBC_OK;
   const int64_t want = (max_rows * 32 + 255) / 256;
   overflow_rethreshold_kernel<<<(unsigned)std::min<int64_t>(want, 148 * 4), 256, 0, st>>>(
-      rows, n_dev, cand_score, cand_cnt, cap, k, qnorm, qerr, lp_max, d, thr, f32_eps, metric);
+      rows, n_dev, cand_score, cand_cnt, cap, k, qnorm, qerr, lp_max, d, thr, f32_eps, metric,
+      mq_bits, eps_bits);
   RBC_LAUNCH_CHECK("overflow_rethreshold_kernel");
   return RBC_OK;
 }

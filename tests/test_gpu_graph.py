@@ -37,12 +37,14 @@ def record(idx, Qs, k):
 
 
 @pytest.mark.parametrize(
-    "storage,metric", [(rbc.BF16, "l2"), (rbc.F32, "l2"), (rbc.F32, "l1")]
+    "storage,metric,plan",
+    [(rbc.BF16, "l2", rbc.PLAN_WINDOW), (rbc.F32, "l2", rbc.PLAN_WINDOW),
+     (rbc.F32, "l1", rbc.PLAN_WINDOW)],
 )
-def test_replays_match_oracle(storage, metric):
+def test_replays_match_oracle(storage, metric, plan):
     X, _ = synth.make_workload("iid-n16k-d16", seed=0)
     idx = rbc.rbc_build(torch.from_numpy(X).cuda(), 128, metric=MET[metric], seed=2,
-                        storage=storage)
+                        storage=storage, plan=plan)
     m, k = 700, 10  # several 128-query chunks and a ragged tail
     Qs = torch.empty((m, X.shape[1]), dtype=torch.float32, device="cuda")
     Qs.copy_(torch.from_numpy(synth.iid_normal(m, X.shape[1], 11)))
@@ -85,10 +87,11 @@ def test_replay_finishes_rows_that_overflow_twice():
     idx.close()
 
 
-def test_capture_rejects_other_plans_and_host_memory():
+@pytest.mark.parametrize("plan", [rbc.PLAN_TILE_UNION, rbc.PLAN_WINDOW_OFFSET])
+def test_capture_rejects_other_plans_and_host_memory(plan):
+    # the tile-union plan and the offset plan read counts back mid-search
     X, Q = synth.make_workload("iid-n16k-d16", seed=0)
-    idx = rbc.rbc_build(torch.from_numpy(X).cuda(), 128, seed=2, storage=rbc.BF16,
-                        plan=rbc.PLAN_TILE_UNION)
+    idx = rbc.rbc_build(torch.from_numpy(X).cuda(), 128, seed=2, storage=rbc.BF16, plan=plan)
     Qs = torch.from_numpy(Q[:256]).cuda()
     ids = torch.empty((256, 5), dtype=torch.int64, device="cuda")
     dist = torch.empty((256, 5), dtype=torch.float32, device="cuda")

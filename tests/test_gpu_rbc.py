@@ -143,7 +143,8 @@ def test_empty_query_batch():
 # ---- low-precision storage: tensor-core stage two (windowed emission or
 # tile-union top-c lists), exact re-rank ----
 
-PLANS = [rbc.PLAN_WINDOW, rbc.PLAN_TILE_UNION]
+PLANS = [rbc.PLAN_WINDOW, rbc.PLAN_TILE_UNION, rbc.PLAN_WINDOW_OFFSET]
+WINDOW_PLANS = [rbc.PLAN_WINDOW, rbc.PLAN_WINDOW_OFFSET]
 
 
 @pytest.mark.parametrize("plan", PLANS)
@@ -248,14 +249,15 @@ def test_exact_search_fewer_queries_than_lists(storage, metric, k):
     check_knn(Q, X, ids, dist, o_ids, o_rho, metric)
 
 
-def test_window_many_tied_candidates_are_streamed():
+@pytest.mark.parametrize("plan", WINDOW_PLANS)
+def test_window_many_tied_candidates_are_streamed(plan):
     # 700 copies of one point: a query on it has 700 survivors at distance 0,
     # more than the shared-memory re-rank holds; they are re-ranked in a
     # stream (no FP32 re-search) and the ties go to the smallest ids
     X = synth.iid_normal(20000, 24, 3)
     X[5000:5700] = X[5000]
     Q = np.concatenate([X[5000:5001].repeat(3, 0), synth.iid_normal(300, 24, 4)]).astype(np.float32)
-    idx = build(X, 140, storage=rbc.BF16, seed=6)
+    idx = build(X, 140, storage=rbc.BF16, seed=6, plan=plan)
     ids, dist = search(idx, Q, 10)
     assert rbc.last_stats()["uncertified"] == 0
     o_ids, o_rho = oracle.bf(Q, X, 10, "l2")
@@ -263,13 +265,15 @@ def test_window_many_tied_candidates_are_streamed():
     np.testing.assert_array_equal(ids[:3], np.tile(np.arange(5000, 5010), (3, 1)))
 
 
-def test_window_candidate_overflow_goes_to_fp32_research():
+@pytest.mark.parametrize("plan", WINDOW_PLANS)
+def test_window_candidate_overflow_goes_to_fp32_research(plan):
     # 9000 copies of one point: more candidates than a query's buffer holds
-    # (8192), so those queries are searched again in FP32
+    # (8192), so those queries are searched again in FP32 (the offset plan's
+    # stored estimates bound the re-threshold of the dense pass)
     X = synth.iid_normal(30000, 24, 3)
     X[5000:14000] = X[5000]
     Q = np.concatenate([X[5000:5001].repeat(3, 0), synth.iid_normal(300, 24, 4)]).astype(np.float32)
-    idx = build(X, 170, storage=rbc.BF16, seed=6)
+    idx = build(X, 170, storage=rbc.BF16, seed=6, plan=plan)
     ids, dist = search(idx, Q, 10)
     assert rbc.last_stats()["uncertified"] >= 3
     o_ids, o_rho = oracle.bf(Q, X, 10, "l2")
@@ -277,14 +281,15 @@ def test_window_candidate_overflow_goes_to_fp32_research():
     np.testing.assert_array_equal(ids[:3], np.tile(np.arange(5000, 5010), (3, 1)))
 
 
-def test_searches_after_an_arena_overflow_agree():
+@pytest.mark.parametrize("plan", WINDOW_PLANS)
+def test_searches_after_an_arena_overflow_agree(plan):
     # the 9000 copies overflow the emission's hit arena: the hits past a full
     # slice go to the query buffers directly, and every search gives the
     # same answer
     X = synth.iid_normal(30000, 24, 3)
     X[5000:14000] = X[5000]
     Q = np.concatenate([X[5000:5001].repeat(3, 0), synth.iid_normal(300, 24, 4)]).astype(np.float32)
-    idx = build(X, 170, storage=rbc.BF16, seed=6)
+    idx = build(X, 170, storage=rbc.BF16, seed=6, plan=plan)
     ids0, dist0 = search(idx, Q, 10)
     for _ in range(12):
         ids, dist = search(idx, Q, 10)
@@ -309,3 +314,23 @@ def test_window_stats_count_fewer_pairs_than_tile_union():
         res[plan] = (ids, rbc.last_stats())
     np.testing.assert_array_equal(res[rbc.PLAN_WINDOW][0], res[rbc.PLAN_TILE_UNION][0])
     assert res[rbc.PLAN_WINDOW][1]["pairs"] < res[rbc.PLAN_TILE_UNION][1]["pairs"]
+
+
+@pytest.mark.parametrize("d", [64, 96, 128])
+def test_offset_plan_on_tight_clusters(d):
+    """Thirty Gaussian clusters, centres N(0, I), sigma in [0.05, 0.5], two
+    representatives per cluster: the bf16 rounding of x grows with |x| (about
+    sqrt(d)), that of x - r with the cluster's size, so the offset plan emits
+    fewer candidates than the plain windowed plan; both answers match the
+    oracle (d = 96: the norm pair rides in the rows' padding)."""
+    mod = synth.ClusterModel(d=d, n_clusters=30, seed=0)
+    X, Q = mod.sample(60000, 0), mod.sample(600, 1)
+    o_ids, o_rho = oracle.bf(Q, X, 10, "l2")
+    cands = {}
+    for plan in WINDOW_PLANS:
+        idx = build(X, 60, storage=rbc.BF16, seed=3, plan=plan)
+        ids, dist = search(idx, Q, 10)
+        cands[plan] = rbc.last_stats()["candidates"]
+        check_knn(Q, X, ids, dist, o_ids, o_rho)
+        idx.close()
+    assert cands[rbc.PLAN_WINDOW_OFFSET] < cands[rbc.PLAN_WINDOW], cands
