@@ -1608,8 +1608,9 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
     RBC_TRY(ar.alloc(&arows, (int64_t)std::max(npairs, 1) * ix->dpad * 2));
     RBC_TRY(ar.alloc(&rowt, npairs));
     RBC_TRY(ar.alloc(&rown, npairs));
-    RBC_TRY(launch_offset_pair_rows(pairs, bin_off, NB, n_r, Qb, ix->R32, ix->psi, ix->yerr_list,
-                                    g, d, ix->dpad, arows, rowt, rown, meps, st));
+    RBC_TRY(launch_offset_pair_rows(pairs, npairs, bin_off, NB, n_r, Qb, ix->R32, ix->psi,
+                                    ix->yerr_list, g, d, ix->dpad, arows, rowt, rown, meps, sms,
+                                    st));
     eoff.a_rows = arows;
     eoff.row_t = rowt;
     eoff.row_n = rown;

@@ -307,18 +307,20 @@ int64_t window_pair_blocks(int64_t m);
 int64_t window_block_offsets(int64_t m, int n_r);
 // (mq_bits != nullptr: also mq_bits[q] = max over q's kept pairs of
 // off_pair_m(rho(q, r), psi_r) as float bits; mq_bits zeroed by the caller)
-// Representative offsets of the kept pairs (binned as by the scatter pass,
-// bins of r in bin_off[r nb .. (r + 1) nb]): for pair i = (q, rho(q, r)),
+// Representative offsets of the kept pairs [0, npairs) (binned as by the
+// scatter pass, bins of r in bin_off[r nb .. (r + 1) nb]): for pair
+// i = (q, rho(q, r)),
 // a_rows[i] = bf16(fl(q - r)) ([dpad] columns, zero padded), row_n[i] =
 // |a~|^2, row_t[i] = 0.5 (|a~|^2 - T) lowered by a few units in the last
 // place with T = off_value_bound(g(q), M, eps, d), M = off_pair_m(rho, psi_r),
 // eps = |fl(q - r) - a~| (measured) + yerr[r] + 2^-23 M; eps_bits[q] (zeroed
 // by the caller) = the largest eps of q's pairs.  d % 8 == 0, Q32 and R32
 // 16-byte aligned.
-int launch_offset_pair_rows(const int2* pairs, const int* bin_off, int nb, int n_r,
+int launch_offset_pair_rows(const int2* pairs, int npairs, const int* bin_off, int nb, int n_r,
                             const float* Q32, const float* R32, const float* psi,
                             const float* yerr, const float* g, int d, int dpad, void* a_rows,
-                            float* row_t, float* row_n, unsigned* eps_bits, cudaStream_t st);
+                            float* row_t, float* row_n, unsigned* eps_bits, int sms,
+                            cudaStream_t st);
 int launch_window_pairs_count(const float* D, int64_t m, int n_r, const float* g,
                               const float* g1, const float* psi_plus, float rel, int* totals,
                               int* bin_off, int* blk_off, unsigned long long* kept_sum,

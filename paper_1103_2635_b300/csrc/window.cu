@@ -516,80 +516,98 @@ __global__ void score_threshold_kernel(const float* __restrict__ g, const float*
 
 }  // namespace
 
-// One block per representative r, each warp four pairs at a time (eight
-// lanes per pair, lane c holding elements 8 c + 64 kb .. + 7 of every 64).
+// Warps take chunks of OP_CHUNK consecutive pairs (balanced however the
+// pairs spread over the lists), four pairs at a time (eight lanes per pair,
+// lane c holding elements 8 c + 64 kb .. + 7 of every 64); a pair's
+// representative is the last r whose bins start at or before it, found by a
+// binary search at the chunk's start and advanced from there.
+constexpr int OP_CHUNK = 256;
 __global__ void __launch_bounds__(256)
-offset_pair_rows_kernel(const int2* __restrict__ pairs, const int* __restrict__ bin_off, int nb,
-                        const float* __restrict__ Q32, const float* __restrict__ R32,
-                        const float* __restrict__ psi, const float* __restrict__ yerr,
-                        const float* __restrict__ g, int d, int dpad, uint4* __restrict__ a_rows,
-                        float* __restrict__ row_t, float* __restrict__ row_n,
-                        unsigned* __restrict__ eps_bits) {
-  const int r = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5, c = lane & 7;
-  const int b = bin_off[(int64_t)r * nb], e = bin_off[(int64_t)(r + 1) * nb];
-  if (b >= e) return;
-  const float psi_r = psi[r], yerr_r = yerr[r];
-  const float* rr = R32 + (int64_t)r * d;
+offset_pair_rows_kernel(const int2* __restrict__ pairs, int npairs, const int* __restrict__ bin_off,
+                        int nb, int n_r, const float* __restrict__ Q32,
+                        const float* __restrict__ R32, const float* __restrict__ psi,
+                        const float* __restrict__ yerr, const float* __restrict__ g, int d, int dpad,
+                        uint4* __restrict__ a_rows, float* __restrict__ row_t,
+                        float* __restrict__ row_n, unsigned* __restrict__ eps_bits) {
+  const int lane = threadIdx.x & 31, c = lane & 7;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
   const int kbs = dpad / 64;
-  for (int i0 = b + 4 * wid; i0 < e; i0 += 32) {
-    const int i = i0 + (lane >> 3);
-    const bool live = i < e;
-    const int2 pr = pairs[live ? i : b];
-    const float* qr = Q32 + (int64_t)pr.x * d;
-    float n2 = 0.0f, e2 = 0.0f;
-    for (int kb = 0; kb < kbs; ++kb) {
-      const int j0 = kb * 64 + 8 * c;
-      uint4 w = make_uint4(0u, 0u, 0u, 0u);
-      if (j0 < d) {
-        const float4 q0 = *reinterpret_cast<const float4*>(qr + j0);
-        const float4 q1 = *reinterpret_cast<const float4*>(qr + j0 + 4);
-        const float4 r0 = *reinterpret_cast<const float4*>(rr + j0);
-        const float4 r1 = *reinterpret_cast<const float4*>(rr + j0 + 4);
-        const float a[8] = {q0.x - r0.x, q0.y - r0.y, q0.z - r0.z, q0.w - r0.w,
-                            q1.x - r1.x, q1.y - r1.y, q1.z - r1.z, q1.w - r1.w};
-        uint32_t ww[4];
+  for (int c0 = gw * OP_CHUNK; c0 < npairs; c0 += nw * OP_CHUNK) {
+    const int c1 = min(npairs, c0 + OP_CHUNK);
+    // the last r with bin_off[r nb] <= c0 (r < n_r; empty lists share starts)
+    int lo = 0, hi = n_r - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (bin_off[(int64_t)mid * nb] <= c0) lo = mid;
+      else hi = mid - 1;
+    }
+    int r = lo;
+    for (int i0 = c0; i0 < c1; i0 += 4) {
+      const int i = i0 + (lane >> 3);
+      const bool live = i < c1;
+      while (live && r + 1 < n_r && bin_off[(int64_t)(r + 1) * nb] <= i) ++r;
+      const int2 pr = pairs[live ? i : c0];
+      const float* qr = Q32 + (int64_t)pr.x * d;
+      const float* rr = R32 + (int64_t)r * d;
+      float n2 = 0.0f, e2 = 0.0f;
+      for (int kb = 0; kb < kbs; ++kb) {
+        const int j0 = kb * 64 + 8 * c;
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        if (j0 < d) {
+          const float4 q0 = *reinterpret_cast<const float4*>(qr + j0);
+          const float4 q1 = *reinterpret_cast<const float4*>(qr + j0 + 4);
+          const float4 r0 = *reinterpret_cast<const float4*>(rr + j0);
+          const float4 r1 = *reinterpret_cast<const float4*>(rr + j0 + 4);
+          const float a[8] = {q0.x - r0.x, q0.y - r0.y, q0.z - r0.z, q0.w - r0.w,
+                              q1.x - r1.x, q1.y - r1.y, q1.z - r1.z, q1.w - r1.w};
+          uint32_t ww[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const __nv_bfloat162 bb = __floats2bfloat162_rn(a[2 * u], a[2 * u + 1]);
-          ww[u] = (uint32_t)__bfloat16_as_ushort(bb.x) | ((uint32_t)__bfloat16_as_ushort(bb.y) << 16);
-          const float lo = __uint_as_float(ww[u] << 16), hi = __uint_as_float(ww[u] & 0xffff0000u);
-          n2 = fmaf(hi, hi, fmaf(lo, lo, n2));
-          const float d0 = a[2 * u] - lo, d1 = a[2 * u + 1] - hi;  // exact
-          e2 = fmaf(d1, d1, fmaf(d0, d0, e2));
+          for (int u = 0; u < 4; ++u) {
+            const __nv_bfloat162 bb = __floats2bfloat162_rn(a[2 * u], a[2 * u + 1]);
+            ww[u] = (uint32_t)__bfloat16_as_ushort(bb.x) | ((uint32_t)__bfloat16_as_ushort(bb.y) << 16);
+            const float flo = __uint_as_float(ww[u] << 16), fhi = __uint_as_float(ww[u] & 0xffff0000u);
+            n2 = fmaf(fhi, fhi, fmaf(flo, flo, n2));
+            const float d0 = a[2 * u] - flo, d1 = a[2 * u + 1] - fhi;  // exact
+            e2 = fmaf(d1, d1, fmaf(d0, d0, e2));
+          }
+          w = make_uint4(ww[0], ww[1], ww[2], ww[3]);
         }
-        w = make_uint4(ww[0], ww[1], ww[2], ww[3]);
+        if (live) a_rows[((int64_t)i * dpad + kb * 64 + 8 * c) / 8] = w;
       }
-      if (live) a_rows[((int64_t)i * dpad + kb * 64 + 8 * c) / 8] = w;
-    }
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-      n2 += __shfl_xor_sync(0xffffffffu, n2, o);
-      e2 += __shfl_xor_sync(0xffffffffu, e2, o);
-    }
-    if (live && c == 0) {
-      const float M = off_pair_m(__int_as_float(pr.y), psi_r);
-      const float ea = __fsqrt_ru(e2 * (1.0f + 3.0517578e-05f)) * (1.0f + 2.4e-7f);
-      const float eps = (ea + yerr_r + 1.1920929e-07f * M) * (1.0f + 2.4e-7f);
-      const float T = off_value_bound(g[pr.x], M, eps, d);
-      row_n[i] = n2;
-      row_t[i] = T < INFINITY ? 0.5f * (n2 - T) - 2.4e-7f * (n2 + T) - 1e-30f : -INFINITY;
-      atomicMax(eps_bits + pr.x, __float_as_uint(eps));
+      for (int o = 1; o < 8; o <<= 1) {
+        n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+        e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+      }
+      if (live && c == 0) {
+        const float M = off_pair_m(__int_as_float(pr.y), psi[r]);
+        const float ea = __fsqrt_ru(e2 * (1.0f + 3.0517578e-05f)) * (1.0f + 2.4e-7f);
+        const float eps = (ea + yerr[r] + 1.1920929e-07f * M) * (1.0f + 2.4e-7f);
+        const float T = off_value_bound(g[pr.x], M, eps, d);
+        row_n[i] = n2;
+        row_t[i] = T < INFINITY ? 0.5f * (n2 - T) - 2.4e-7f * (n2 + T) - 1e-30f : -INFINITY;
+        atomicMax(eps_bits + pr.x, __float_as_uint(eps));
+      }
     }
   }
 }
 
-int launch_offset_pair_rows(const int2* pairs, const int* bin_off, int nb, int n_r,
+int launch_offset_pair_rows(const int2* pairs, int npairs, const int* bin_off, int nb, int n_r,
                             const float* Q32, const float* R32, const float* psi,
                             const float* yerr, const float* g, int d, int dpad, void* a_rows,
-                            float* row_t, float* row_n, unsigned* eps_bits, cudaStream_t st) {
-  if (n_r <= 0) return RBC_OK;
+                            float* row_t, float* row_n, unsigned* eps_bits, int sms,
+                            cudaStream_t st) {
+  if (npairs <= 0 || n_r <= 0) return RBC_OK;
   if (d % 8 != 0 || dpad % 64 != 0 || d > dpad) {
     set_error("offset rows: d %d must be a multiple of 8 within dpad %d", d, dpad);
     return RBC_ERR_ARG;
   }
-  offset_pair_rows_kernel<<<n_r, 256, 0, st>>>(pairs, bin_off, nb, Q32, R32, psi, yerr, g, d,
-                                               dpad, static_cast<uint4*>(a_rows), row_t, row_n,
-                                               eps_bits);
+  const int chunks = (npairs + OP_CHUNK - 1) / OP_CHUNK;
+  const int grid = std::max(1, std::min((chunks + 7) / 8, sms * 8));
+  offset_pair_rows_kernel<<<grid, 256, 0, st>>>(pairs, npairs, bin_off, nb, n_r, Q32, R32, psi,
+                                                yerr, g, d, dpad, static_cast<uint4*>(a_rows),
+                                                row_t, row_n, eps_bits);
   RBC_LAUNCH_CHECK("offset_pair_rows_kernel");
   return RBC_OK;
 }
