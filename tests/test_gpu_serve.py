@@ -138,6 +138,7 @@ def test_request_validation_and_empty_request(served):
     [
         ("subspace", rbc.BF16, rbc.L2, rbc.EXACT, rbc.PLAN_WINDOW),
         ("subspace", rbc.BF16, rbc.L2, rbc.EXACT, rbc.PLAN_TILE_UNION),
+        ("subspace", rbc.BF16, rbc.L2, rbc.EXACT, rbc.PLAN_WINDOW_OFFSET),
         ("subspace", rbc.F32, rbc.L2, rbc.EXACT, rbc.PLAN_WINDOW),
         ("subspace", rbc.F32, rbc.L1, rbc.EXACT, rbc.PLAN_WINDOW),
         ("subspace", rbc.BF16, rbc.L2, rbc.ONESHOT, rbc.PLAN_WINDOW),
