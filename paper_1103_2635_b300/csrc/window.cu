@@ -394,55 +394,68 @@ window_items_kernel(const int* __restrict__ chunk_off, int n_r, const int* __res
 
 // One warp per overflowing query: the k-th smallest of its stored scores
 // (bitwise search over order-preserving keys) -> a tighter threshold.
-__global__ void overflow_rethreshold_kernel(const int* __restrict__ rows,
-                                            const int* __restrict__ n_dev,
-                                            const float* __restrict__ cand_score,
-                                            int* __restrict__ cand_cnt, int cap, int k,
-                                            const float* __restrict__ qnorm,
-                                            const float* __restrict__ qerr,
-                                            const unsigned* __restrict__ lp_max, int d,
-                                            float* __restrict__ thr, float f32_eps, int metric,
-                                            const unsigned* __restrict__ mq_bits,
-                                            const unsigned* __restrict__ eps_bits) {
-  const int lane = threadIdx.x & 31;
+// One block per overflowing row: the k-th smallest stored key by a radix
+// select over its four bytes (a 256-bin shared histogram per byte, most
+// significant first), the same key the bitwise search over all 32 bits finds.
+__global__ void __launch_bounds__(256)
+overflow_rethreshold_kernel(const int* __restrict__ rows, const int* __restrict__ n_dev,
+                            const float* __restrict__ cand_score, int* __restrict__ cand_cnt,
+                            int cap, int k, const float* __restrict__ qnorm,
+                            const float* __restrict__ qerr, const unsigned* __restrict__ lp_max,
+                            int d, float* __restrict__ thr, float f32_eps, int metric,
+                            const unsigned* __restrict__ mq_bits,
+                            const unsigned* __restrict__ eps_bits) {
+  __shared__ int hist[256];
+  __shared__ unsigned s_prefix;
+  __shared__ int s_rank;
   const int n = *n_dev;
-  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n;
-       i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-  const int q = rows[i];
-  const int stored = min(cand_cnt[q], cap);
-  float t = INFINITY;
-  if (stored >= k) {
-    const float* sc = cand_score + (int64_t)q * cap;
-    unsigned res = 0;
-    for (int bit = 31; bit >= 0; --bit) {
-      const unsigned tt = res | (1u << bit);
-      int c = 0;
-      for (int e = lane; e < stored; e += 32) {
-        const unsigned b = __float_as_uint(sc[e]);
-        const unsigned key = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-        c += key < tt;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const int q = rows[i];
+    const int stored = min(cand_cnt[q], cap);
+    float t = INFINITY;
+    if (stored >= k) {
+      const float* sc = cand_score + (int64_t)q * cap;
+      unsigned prefix = 0, mask = 0;
+      int rank = k;  // 1-based rank of the wanted key among those matching prefix
+      for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        for (int e = threadIdx.x; e < stored; e += blockDim.x) {
+          const unsigned bits = __float_as_uint(sc[e]);
+          const unsigned key = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
+          if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          int cum = 0, b = 0;
+          for (; b < 255 && cum + hist[b] < rank; ++b) cum += hist[b];
+          s_prefix = prefix | ((unsigned)b << shift);
+          s_rank = rank - cum;
+        }
+        __syncthreads();
+        prefix = s_prefix;
+        rank = s_rank;
+        mask |= 255u << shift;
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-      if (c < k) res = tt;
+      const unsigned res = prefix;
+      const float sk = __uint_as_float((res & 0x80000000u) ? (res & 0x7fffffffu) : ~res);
+      if (qnorm) {
+        // stored values: low-precision scores, or offset estimates whose
+        // distance bound the raw scores of the dense pass then use
+        const float xe = __uint_as_float(lp_max[0]), xn = __uint_as_float(lp_max[1]);
+        const float u = mq_bits ? off_dist_upper(sk, __uint_as_float(mq_bits[q]),
+                                                 __uint_as_float(eps_bits[q]), d)
+                                : dist_upper(sk, qnorm[q], qerr[q], xe, xn, d);
+        t = score_bound(u, qnorm[q], qerr[q], xe, xn, d);
+      } else {
+        t = f32_score_bound(f32_dist_upper(sk, f32_eps, metric), f32_eps, metric);
+      }
     }
-    const float sk = __uint_as_float((res & 0x80000000u) ? (res & 0x7fffffffu) : ~res);
-    if (qnorm) {
-      // stored values: low-precision scores, or offset estimates whose
-      // distance bound the raw scores of the dense pass then use
-      const float xe = __uint_as_float(lp_max[0]), xn = __uint_as_float(lp_max[1]);
-      const float u = mq_bits ? off_dist_upper(sk, __uint_as_float(mq_bits[q]),
-                                               __uint_as_float(eps_bits[q]), d)
-                              : dist_upper(sk, qnorm[q], qerr[q], xe, xn, d);
-      t = score_bound(u, qnorm[q], qerr[q], xe, xn, d);
-    } else {
-      t = f32_score_bound(f32_dist_upper(sk, f32_eps, metric), f32_eps, metric);
+    if (threadIdx.x == 0) {
+      thr[q] = t;
+      cand_cnt[q] = 0;
     }
-  }
-  if (lane == 0) {
-    thr[q] = t;
-    cand_cnt[q] = 0;
-  }
+    __syncthreads();  // the histogram is reused by the block's next row
   }
 }
 
@@ -543,51 +556,72 @@ offset_pair_rows_kernel(const int2* __restrict__ pairs, int npairs, const int* _
       else hi = mid - 1;
     }
     int r = lo;
-    for (int i0 = c0; i0 < c1; i0 += 4) {
-      const int i = i0 + (lane >> 3);
-      const bool live = i < c1;
-      while (live && r + 1 < n_r && bin_off[(int64_t)(r + 1) * nb] <= i) ++r;
-      const int2 pr = pairs[live ? i : c0];
-      const float* qr = Q32 + (int64_t)pr.x * d;
-      const float* rr = R32 + (int64_t)r * d;
-      float n2 = 0.0f, e2 = 0.0f;
+    // two pairs per group and round (i and i + 4), their loads issued together
+    for (int i0 = c0; i0 < c1; i0 += 8) {
+      int ii[2], rr_[2];
+      bool live[2];
+      int2 pr[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        ii[u] = i0 + 4 * u + (lane >> 3);
+        live[u] = ii[u] < c1;
+        while (live[u] && r + 1 < n_r && bin_off[(int64_t)(r + 1) * nb] <= ii[u]) ++r;
+        rr_[u] = r;
+        pr[u] = pairs[live[u] ? ii[u] : c0];
+      }
+      float n2[2] = {0.0f, 0.0f}, e2[2] = {0.0f, 0.0f};
       for (int kb = 0; kb < kbs; ++kb) {
         const int j0 = kb * 64 + 8 * c;
-        uint4 w = make_uint4(0u, 0u, 0u, 0u);
-        if (j0 < d) {
-          const float4 q0 = *reinterpret_cast<const float4*>(qr + j0);
-          const float4 q1 = *reinterpret_cast<const float4*>(qr + j0 + 4);
-          const float4 r0 = *reinterpret_cast<const float4*>(rr + j0);
-          const float4 r1 = *reinterpret_cast<const float4*>(rr + j0 + 4);
-          const float a[8] = {q0.x - r0.x, q0.y - r0.y, q0.z - r0.z, q0.w - r0.w,
-                              q1.x - r1.x, q1.y - r1.y, q1.z - r1.z, q1.w - r1.w};
-          uint32_t ww[4];
+        float4 qv[2][2], rv[2][2];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const __nv_bfloat162 bb = __floats2bfloat162_rn(a[2 * u], a[2 * u + 1]);
-            ww[u] = (uint32_t)__bfloat16_as_ushort(bb.x) | ((uint32_t)__bfloat16_as_ushort(bb.y) << 16);
-            const float flo = __uint_as_float(ww[u] << 16), fhi = __uint_as_float(ww[u] & 0xffff0000u);
-            n2 = fmaf(fhi, fhi, fmaf(flo, flo, n2));
-            const float d0 = a[2 * u] - flo, d1 = a[2 * u + 1] - fhi;  // exact
-            e2 = fmaf(d1, d1, fmaf(d0, d0, e2));
-          }
-          w = make_uint4(ww[0], ww[1], ww[2], ww[3]);
+        for (int u = 0; u < 2; ++u) {
+          const int jj = j0 < d ? j0 : 0;  // elements past d are not used
+          const float* qr = Q32 + (int64_t)pr[u].x * d + jj;
+          const float* rr = R32 + (int64_t)rr_[u] * d + jj;
+          qv[u][0] = *reinterpret_cast<const float4*>(qr);
+          qv[u][1] = *reinterpret_cast<const float4*>(qr + 4);
+          rv[u][0] = *reinterpret_cast<const float4*>(rr);
+          rv[u][1] = *reinterpret_cast<const float4*>(rr + 4);
         }
-        if (live) a_rows[((int64_t)i * dpad + kb * 64 + 8 * c) / 8] = w;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          uint4 w = make_uint4(0u, 0u, 0u, 0u);
+          if (j0 < d) {
+            const float4 q0 = qv[u][0], q1 = qv[u][1], r0 = rv[u][0], r1 = rv[u][1];
+            const float a[8] = {q0.x - r0.x, q0.y - r0.y, q0.z - r0.z, q0.w - r0.w,
+                                q1.x - r1.x, q1.y - r1.y, q1.z - r1.z, q1.w - r1.w};
+            uint32_t ww[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const __nv_bfloat162 bb = __floats2bfloat162_rn(a[2 * h], a[2 * h + 1]);
+              ww[h] = (uint32_t)__bfloat16_as_ushort(bb.x) | ((uint32_t)__bfloat16_as_ushort(bb.y) << 16);
+              const float flo = __uint_as_float(ww[h] << 16), fhi = __uint_as_float(ww[h] & 0xffff0000u);
+              n2[u] = fmaf(fhi, fhi, fmaf(flo, flo, n2[u]));
+              const float d0 = a[2 * h] - flo, d1 = a[2 * h + 1] - fhi;  // exact
+              e2[u] = fmaf(d1, d1, fmaf(d0, d0, e2[u]));
+            }
+            w = make_uint4(ww[0], ww[1], ww[2], ww[3]);
+          }
+          if (live[u]) a_rows[((int64_t)ii[u] * dpad + kb * 64 + 8 * c) / 8] = w;
+        }
       }
 #pragma unroll
-      for (int o = 1; o < 8; o <<= 1) {
-        n2 += __shfl_xor_sync(0xffffffffu, n2, o);
-        e2 += __shfl_xor_sync(0xffffffffu, e2, o);
-      }
-      if (live && c == 0) {
-        const float M = off_pair_m(__int_as_float(pr.y), psi[r]);
-        const float ea = __fsqrt_ru(e2 * (1.0f + 3.0517578e-05f)) * (1.0f + 2.4e-7f);
-        const float eps = (ea + yerr[r] + 1.1920929e-07f * M) * (1.0f + 2.4e-7f);
-        const float T = off_value_bound(g[pr.x], M, eps, d);
-        row_n[i] = n2;
-        row_t[i] = T < INFINITY ? 0.5f * (n2 - T) - 2.4e-7f * (n2 + T) - 1e-30f : -INFINITY;
-        atomicMax(eps_bits + pr.x, __float_as_uint(eps));
+      for (int u = 0; u < 2; ++u) {
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+          n2[u] += __shfl_xor_sync(0xffffffffu, n2[u], o);
+          e2[u] += __shfl_xor_sync(0xffffffffu, e2[u], o);
+        }
+        if (live[u] && c == 0) {
+          const float M = off_pair_m(__int_as_float(pr[u].y), psi[rr_[u]]);
+          const float ea = __fsqrt_ru(e2[u] * (1.0f + 3.0517578e-05f)) * (1.0f + 2.4e-7f);
+          const float eps = (ea + yerr[rr_[u]] + 1.1920929e-07f * M) * (1.0f + 2.4e-7f);
+          const float T = off_value_bound(g[pr[u].x], M, eps, d);
+          row_n[ii[u]] = n2[u];
+          row_t[ii[u]] = T < INFINITY ? 0.5f * (n2[u] - T) - 2.4e-7f * (n2[u] + T) - 1e-30f
+                                      : -INFINITY;
+          atomicMax(eps_bits + pr[u].x, __float_as_uint(eps));
+        }
       }
     }
   }
@@ -700,8 +734,7 @@ int launch_overflow_rethreshold(const int* rows, const int* n_dev, int64_t max_r
                                 int d, float* thr, cudaStream_t st, float f32_eps, int metric,
                                 const unsigned* mq_bits, const unsigned* eps_bits) {
   if (max_rows <= 0) return RBC_OK;
-  const int64_t want = (max_rows * 32 + 255) / 256;
-  overflow_rethreshold_kernel<<<(unsigned)std::min<int64_t>(want, 148 * 4), 256, 0, st>>>(
+  overflow_rethreshold_kernel<<<(unsigned)std::min<int64_t>(max_rows, 148 * 4), 256, 0, st>>>(
       rows, n_dev, cand_score, cand_cnt, cap, k, qnorm, qerr, lp_max, d, thr, f32_eps, metric,
       mq_bits, eps_bits);
   RBC_LAUNCH_CHECK("overflow_rethreshold_kernel");
