@@ -476,6 +476,12 @@ bf_tc_emit_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constan
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[buf]);
+        // the common case: no row of the warp reaches its threshold anywhere
+        // in the slice -- one vote instead of a test and a branch per chunk
+        float cm = cmax[0];
+#pragma unroll
+        for (int c = 1; c < CH; ++c) cm = fmaxf(cm, cmax[c]);
+        if (!__any_sync(0xffffffffu, cm >= myT)) continue;
         const int lo = xw.x - x - part * COLS;  // first valid column of the slice
         const int hi = xw.y - x - part * COLS;    // one past the last valid column
 #pragma unroll
