@@ -1594,7 +1594,7 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   RBC_TRY(ar.alloc(&cc, mb));
   LpMatrix Qm{ql.lp, ql.norm, mb, ix->dpad, ix->storage};
   LpMatrix Xm{ix->Xlp, ix->xnorm, n, ix->dpad, ix->storage, ix->xnblock};
-  // the main pass's rows and the offsets it forms its query rows from
+  // the main pass's database rows: the offsets y~ = bf16(x - r) on the offset plan
   LpMatrix Ym = offs ? LpMatrix{ix->Ylp, ix->ynorm, n, ix->dpad, ix->storage, ix->ynblock} : Xm;
   EmitOffsets eoff;
   if (offs) {

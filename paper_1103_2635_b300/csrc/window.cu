@@ -530,8 +530,9 @@ __global__ void score_threshold_kernel(const float* __restrict__ g, const float*
 }  // namespace
 
 // Warps take chunks of OP_CHUNK consecutive pairs (balanced however the
-// pairs spread over the lists), four pairs at a time (eight lanes per pair,
-// lane c holding elements 8 c + 64 kb .. + 7 of every 64); a pair's
+// pairs spread over the lists), eight pairs per round (a group of eight
+// lanes per pair, two pairs per group, lane c holding elements
+// 8 c + 64 kb .. + 7 of every 64); a pair's
 // representative is the last r whose bins start at or before it, found by a
 // binary search at the chunk's start and advanced from there.
 constexpr int OP_CHUNK = 256;
