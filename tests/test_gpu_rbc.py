@@ -334,3 +334,19 @@ def test_offset_plan_on_tight_clusters(d):
         check_knn(Q, X, ids, dist, o_ids, o_rho)
         idx.close()
     assert cands[rbc.PLAN_WINDOW_OFFSET] < cands[rbc.PLAN_WINDOW], cands
+
+
+@pytest.mark.parametrize("n_r", [1, 3, 4000])
+def test_offset_plan_edge_lists(n_r):
+    """Offsets from the representative when one list holds everything (n_r =
+    1), a few long lists, and lists of one point each (every row y = 0 and
+    the query rows a = q - r carry the whole distance); queries that are
+    database points (distance 0) and far ones."""
+    X = synth.iid_normal(4000, 16, 40)
+    Q = np.concatenate([X[:50], synth.iid_normal(200, 16, 41), 30.0 * synth.iid_normal(20, 16, 42)])
+    Q = Q.astype(np.float32)
+    o_ids, o_rho = oracle.bf(Q, X, 10, "l2")
+    idx = build(X, n_r, storage=rbc.BF16, seed=5, plan=rbc.PLAN_WINDOW_OFFSET)
+    ids, dist = search(idx, Q, 10)
+    check_knn(Q, X, ids, dist, o_ids, o_rho)
+    idx.close()
