@@ -232,10 +232,14 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
+        # the same workload and search as the GPU arm's line (its config keys
+        # verbatim); the oracle computes that search's exact answer in FP64
         "config": {"workload": args.workload, "n": w.n, "m": w.m, "d": w.d, "n_r": w.n_r, "k": args.k,
-                   "metric": "l2", "storage": args.storage, "noise_var": w.params.get("noise_var"),
+                   "metric": "l2", "storage": args.storage, "plan": args.plan,
+                   "noise_var": w.params.get("noise_var"),
                    "intrinsic_dim": w.params.get("k"), "parallelism": "replicas1",
-                   "method": "exact RBC search, FP64 CPU oracle"},
+                   "l2_flush": "inputs larger than L2 (bf16 database 128 MiB + FP32 copy 256 MiB)"},
+        "method": "exact RBC search, FP64 CPU oracle",
         "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
                          "sample": f"{S} random queries of {w.m} per step, full {w.n}-point database"},
         "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
