@@ -369,17 +369,23 @@ int stats_publish(const Counters& cn, int64_t queries, int64_t items, int64_t ho
 // ---- inputs / outputs that may live in host memory ----
 struct IoPlan {
   const float* Qdev = nullptr;
+  const float* Qhost = nullptr;  // set when the batches copy their own rows (defer_copy)
   int64_t* ids_dev = nullptr;
   float* dist_dev = nullptr;
   bool ids_host = false, dist_host = false;
 };
 
+// Host query rows: copied here in one piece, or (defer_copy) only given
+// their device buffer, each batch then copying its own rows beside stage 1.
 int io_prepare(const float* Q, int64_t m, int d, int k, int64_t* out_ids, float* out_dist,
-               IoPlan& io, Arena& ar, cudaStream_t st) {
+               IoPlan& io, Arena& ar, cudaStream_t st, bool defer_copy = false) {
   if (m > 0 && !is_device_ptr(Q)) {
     float* q;
     RBC_TRY(ar.alloc(&q, m * d));
-    RBC_CUDA(cudaMemcpyAsync(q, Q, (size_t)m * d * sizeof(float), cudaMemcpyHostToDevice, st));
+    if (defer_copy)
+      io.Qhost = Q;
+    else
+      RBC_CUDA(cudaMemcpyAsync(q, Q, (size_t)m * d * sizeof(float), cudaMemcpyHostToDevice, st));
     io.Qdev = q;
   } else {
     io.Qdev = Q;
@@ -398,6 +404,46 @@ int io_prepare(const float* Q, int64_t m, int d, int k, int64_t* out_ids, float*
   }
   return RBC_OK;
 }
+
+// Query rows from host memory in FEED_CHUNKS row chunks on a second stream
+// (one per thread and device), each chunk's stage 1 waiting only for its own
+// copy: stage 1 is row-independent, so it overlaps the copy of later rows.
+// Batches below FEED_MIN_ROWS copy in one piece on the search's stream.
+constexpr int FEED_CHUNKS = 4;
+constexpr int64_t FEED_MIN_ROWS = 8192;
+constexpr int FEED_MAX_DEVICES = 64;
+
+struct FeedStreams {
+  cudaStream_t s[FEED_MAX_DEVICES] = {};
+  ~FeedStreams() {
+    for (cudaStream_t x : s)
+      if (x) cudaStreamDestroy(x);
+  }
+};
+thread_local FeedStreams t_feed;
+
+cudaStream_t feed_stream() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= FEED_MAX_DEVICES) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (!t_feed.s[dev] &&
+      cudaStreamCreateWithFlags(&t_feed.s[dev], cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    t_feed.s[dev] = nullptr;
+  }
+  return t_feed.s[dev];
+}
+
+// the events of one batch's chunk copies (released once they complete)
+struct FeedEvents {
+  cudaEvent_t ev[FEED_CHUNKS + 1] = {};
+  ~FeedEvents() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
 
 int io_finish(int64_t m, int k, int64_t* out_ids, float* out_dist, const IoPlan& io,
               cudaStream_t st) {
@@ -1492,9 +1538,11 @@ int search_oneshot_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k
 // ---------------------------------------------------------------------------
 // windowed exact search (Section 5.2 with lists sorted by rho(x, r))
 // ---------------------------------------------------------------------------
+// Qhost: the batch's rows in host memory, copied here into Qb (the batch's
+// device buffer) chunk by chunk beside stage 1; null when Qb already holds them.
 int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k, int64_t* ids,
                         float* dist, const Counters& cn, int64_t* items_total, Arena& ar,
-                        cudaStream_t st) {
+                        cudaStream_t st, const float* Qhost = nullptr) {
   const int d = ix->d, n_r = ix->n_r;
   const int64_t n = ix->list_entries;
   const int sms = sm_count();
@@ -1502,14 +1550,37 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   // stage 1: BF(Q, R) keeping every distance; gamma_1, gamma_k, nearest
   float* D;
   RBC_TRY(ar.alloc(&D, mb * n_r));
-  const int64_t tiles = (mb + TQ - 1) / TQ;
-  TileWork w1{};
-  w1.num_items = (int)tiles;
-  w1.m = mb;
-  w1.n = n_r;
-  set_stage1_splits(w1, tiles, n_r, sms);
-  RBC_TRY(launch_bf_simt_store(Qb, ix->R32, d, ix->metric, w1, D, n_r,
-                               (int)std::min<int64_t>(w1.num_items, (int64_t)sms * 2 * 16), st));
+  cudaStream_t side = (Qhost && mb >= FEED_MIN_ROWS) ? feed_stream() : nullptr;
+  const int64_t crows =
+      side ? ((mb + FEED_CHUNKS - 1) / FEED_CHUNKS + TQ - 1) / TQ * TQ : std::max<int64_t>(mb, 1);
+  FeedEvents fe;
+  if (side) {
+    for (cudaEvent_t& e : fe.ev) RBC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    // the copies land in workspace allocated on the search's stream
+    RBC_CUDA(cudaEventRecord(fe.ev[FEED_CHUNKS], st));
+    RBC_CUDA(cudaStreamWaitEvent(side, fe.ev[FEED_CHUNKS], 0));
+  }
+  for (int64_t c0 = 0, ci = 0; c0 < mb; c0 += crows, ++ci) {
+    const int64_t mc = std::min(crows, mb - c0);
+    if (Qhost) {
+      RBC_CUDA(cudaMemcpyAsync(const_cast<float*>(Qb) + c0 * d, Qhost + c0 * d,
+                               (size_t)mc * d * sizeof(float), cudaMemcpyHostToDevice,
+                               side ? side : st));
+      if (side) {
+        RBC_CUDA(cudaEventRecord(fe.ev[ci], side));
+        RBC_CUDA(cudaStreamWaitEvent(st, fe.ev[ci], 0));
+      }
+    }
+    const int64_t tiles = (mc + TQ - 1) / TQ;
+    TileWork w1{};
+    w1.num_items = (int)tiles;
+    w1.m = mc;
+    w1.n = n_r;
+    set_stage1_splits(w1, tiles, n_r, sms);
+    RBC_TRY(launch_bf_simt_store(Qb + c0 * d, ix->R32, d, ix->metric, w1, D + c0 * n_r, n_r,
+                                 (int)std::min<int64_t>(w1.num_items, (int64_t)sms * 2 * 16),
+                                 st));
+  }
   float *g1, *gk;
   int64_t* nearest;
   RBC_TRY(ar.alloc(&g1, mb));
@@ -2226,7 +2297,8 @@ int rbc_search(const rbc_index* ix, const float* Q, int64_t m, int32_t k, int64_
   {
     Arena ar(st);
     IoPlan io;
-    RBC_TRY(io_prepare(Q, m, ix->d, k, out_ids, out_dist, io, ar, st));
+    // the windowed plan copies host query rows batch by batch, beside stage 1
+    RBC_TRY(io_prepare(Q, m, ix->d, k, out_ids, out_dist, io, ar, st, window));
     Counters cn;
     RBC_TRY(counters_alloc(cn, ar, st));
     for (int64_t b0 = 0; b0 < m; b0 += batch) {
@@ -2237,7 +2309,8 @@ int rbc_search(const rbc_index* ix, const float* Q, int64_t m, int32_t k, int64_
                                      io.dist_dev + b0 * k, cn, &items, bar, st));
       else if (window)
         RBC_TRY(search_window_batch(ix, io.Qdev + b0 * ix->d, mb, k, io.ids_dev + b0 * k,
-                                    io.dist_dev + b0 * k, cn, &items, bar, st));
+                                    io.dist_dev + b0 * k, cn, &items, bar, st,
+                                    io.Qhost ? io.Qhost + b0 * ix->d : nullptr));
       else
         RBC_TRY(search_exact_batch(ix, io.Qdev + b0 * ix->d, mb, k, io.ids_dev + b0 * k,
                                    io.dist_dev + b0 * k, cn, &items, bar, st));

@@ -133,6 +133,34 @@ def test_host_buffer_search():
     check_knn(Q, X, ids, dist, o_ids, o_rho)
 
 
+@pytest.mark.parametrize("storage,plan", [(rbc.F32, rbc.PLAN_WINDOW), (rbc.BF16, rbc.PLAN_WINDOW),
+                                          (rbc.BF16, rbc.PLAN_WINDOW_OFFSET)])
+@pytest.mark.parametrize("pinned", [False, True])
+def test_host_rows_copied_beside_stage_one(storage, plan, pinned):
+    # n_r = 4096 cuts 70,001 queries into batches of 65,536 and 4,465 rows:
+    # the first copies its host rows in four chunks on a second stream, each
+    # chunk's stage 1 waiting for its own copy (the last chunk ragged); the
+    # second is below the chunking threshold and copies in one piece.  The
+    # answers must equal those of the same search on device buffers.
+    X = synth.iid_normal(40000, 32, 70)
+    Q = synth.iid_normal(70001, 32, 71)
+    k = 5
+    idx = build(X, 4096, storage=storage, plan=plan)
+    dev_ids, dev_dist = search(idx, Q, k)
+    Qh = torch.from_numpy(Q)
+    ids = torch.empty((Q.shape[0], k), dtype=torch.int64)
+    dist = torch.empty((Q.shape[0], k), dtype=torch.float32)
+    if pinned:
+        Qh, ids, dist = Qh.pin_memory(), ids.pin_memory(), dist.pin_memory()
+    rbc.rbc_search(idx, Qh, k, out_ids=ids, out_dist=dist)
+    np.testing.assert_array_equal(ids.numpy(), dev_ids)
+    np.testing.assert_array_equal(dist.numpy(), dev_dist)
+    sample = np.random.default_rng(72).choice(Q.shape[0], 300, replace=False)
+    sample[:2] = [0, Q.shape[0] - 1]
+    o_ids, o_rho = oracle.bf(Q[sample], X, k, "l2")
+    check_knn(Q[sample], X, ids.numpy()[sample], dist.numpy()[sample], o_ids, o_rho)
+
+
 def test_empty_query_batch():
     X = synth.iid_normal(500, 4, 60)
     idx = build(X, 22)
