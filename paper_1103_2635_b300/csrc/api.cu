@@ -406,10 +406,11 @@ int io_prepare(const float* Q, int64_t m, int d, int k, int64_t* out_ids, float*
 }
 
 // Query rows from host memory in FEED_CHUNKS row chunks on a second stream
-// (one per thread and device), each chunk's stage 1 waiting only for its own
-// copy: stage 1 is row-independent, so it overlaps the copy of later rows.
-// Batches below FEED_MIN_ROWS copy in one piece on the search's stream.
-constexpr int FEED_CHUNKS = 4;
+// (one per thread and device), each chunk's per-row steps (stage 1, row
+// statistics, low-precision copy) waiting only for its own rows: they
+// overlap the copy of later rows.  Batches below FEED_MIN_ROWS copy in one
+// piece on the search's stream.
+constexpr int FEED_CHUNKS = 8;
 constexpr int64_t FEED_MIN_ROWS = 8192;
 constexpr int FEED_MAX_DEVICES = 64;
 
@@ -649,8 +650,7 @@ struct LpQueries {
   int storage = RBC_BF16;
 };
 
-int lp_queries(const float* Qdev, int64_t m, int d, int dpad, int storage, LpQueries& q,
-               Arena& ar, cudaStream_t st) {
+int lp_queries_alloc(int64_t m, int dpad, int storage, LpQueries& q, Arena& ar) {
   uint8_t* buf;
   RBC_TRY(ar.alloc(&buf, std::max<int64_t>(m, 1) * dpad * lp_elem_bytes(storage)));
   RBC_TRY(ar.alloc(&q.norm, m));
@@ -658,8 +658,22 @@ int lp_queries(const float* Qdev, int64_t m, int d, int dpad, int storage, LpQue
   if (storage == RBC_FP8E4M3) RBC_TRY(ar.alloc(&q.scale, m));
   q.lp = buf;
   q.storage = storage;
-  return launch_to_lowp(Qdev, m, d, dpad, storage, buf, q.norm, q.err, nullptr, nullptr, st,
-                        q.scale);
+  return RBC_OK;
+}
+
+// rows [r0, r0 + mr) of Qdev into the same rows of q
+int lp_queries_rows(const float* Qdev, int64_t r0, int64_t mr, int d, int dpad,
+                    const LpQueries& q, cudaStream_t st) {
+  const int64_t rb = (int64_t)dpad * lp_elem_bytes(q.storage);
+  return launch_to_lowp(Qdev + r0 * d, mr, d, dpad, q.storage,
+                        static_cast<uint8_t*>(q.lp) + r0 * rb, q.norm + r0, q.err + r0, nullptr,
+                        nullptr, st, q.scale ? q.scale + r0 : nullptr);
+}
+
+int lp_queries(const float* Qdev, int64_t m, int d, int dpad, int storage, LpQueries& q,
+               Arena& ar, cudaStream_t st) {
+  RBC_TRY(lp_queries_alloc(m, dpad, storage, q, ar));
+  return lp_queries_rows(Qdev, 0, m, d, dpad, q, st);
 }
 
 int bf_dense_lp(const float* Qdev, int64_t m, const DbView& db, int d, int k, int storage,
@@ -1550,6 +1564,21 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
   // stage 1: BF(Q, R) keeping every distance; gamma_1, gamma_k, nearest
   float* D;
   RBC_TRY(ar.alloc(&D, mb * n_r));
+  float *g1, *gk;
+  int64_t* nearest;
+  RBC_TRY(ar.alloc(&g1, mb));
+  RBC_TRY(ar.alloc(&gk, mb));
+  RBC_TRY(ar.alloc(&nearest, mb));
+  // bf16 / fp16 storage with l2: tensor-core passes on the low-precision rows;
+  // otherwise (FP32 storage, l1) the same plan on the CUDA cores in FP32
+  const bool lp = uses_lp(ix->storage, ix->metric) && ix->Xlp != nullptr;
+  const int metric = ix->metric;
+  const float f32_eps = simt_eps(d);
+  // low-precision copy of the batch (pass A and the emission pass)
+  LpQueries ql;
+  if (lp) RBC_TRY(lp_queries_alloc(mb, ix->dpad, ix->storage, ql, ar));
+  // every step up to here is per query row: with host rows, chunk by chunk
+  // behind each chunk's copy
   cudaStream_t side = (Qhost && mb >= FEED_MIN_ROWS) ? feed_stream() : nullptr;
   const int64_t crows =
       side ? ((mb + FEED_CHUNKS - 1) / FEED_CHUNKS + TQ - 1) / TQ * TQ : std::max<int64_t>(mb, 1);
@@ -1580,25 +1609,13 @@ int search_window_batch(const rbc_index* ix, const float* Qb, int64_t mb, int k,
     RBC_TRY(launch_bf_simt_store(Qb + c0 * d, ix->R32, d, ix->metric, w1, D + c0 * n_r, n_r,
                                  (int)std::min<int64_t>(w1.num_items, (int64_t)sms * 2 * 16),
                                  st));
+    RBC_TRY(launch_row_stats(D + c0 * n_r, mc, n_r, k, g1 + c0, gk + c0, nearest + c0, st));
+    if (lp) RBC_TRY(lp_queries_rows(Qb, c0, mc, d, ix->dpad, ql, st));
   }
-  float *g1, *gk;
-  int64_t* nearest;
-  RBC_TRY(ar.alloc(&g1, mb));
-  RBC_TRY(ar.alloc(&gk, mb));
-  RBC_TRY(ar.alloc(&nearest, mb));
-  RBC_TRY(launch_row_stats(D, mb, n_r, k, g1, gk, nearest, st));
   // device error flags of both tensor-core passes
   uint32_t* dev_err;
   RBC_TRY(ar.alloc(&dev_err, 1));
   RBC_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(uint32_t), st));
-  // bf16 / fp16 storage with l2: tensor-core passes on the low-precision rows;
-  // otherwise (FP32 storage, l1) the same plan on the CUDA cores in FP32
-  const bool lp = uses_lp(ix->storage, ix->metric) && ix->Xlp != nullptr;
-  const int metric = ix->metric;
-  const float f32_eps = simt_eps(d);
-  // low-precision copy of the batch (pass A and the emission pass)
-  LpQueries ql;
-  if (lp) RBC_TRY(lp_queries(Qb, mb, d, ix->dpad, ix->storage, ql, ar, st));
   // pass A: the k-th distance inside the nearest representative's own list
   // (and the batch's queries ordered by nearest representative)
   float* own;

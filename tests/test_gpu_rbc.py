@@ -137,13 +137,15 @@ def test_host_buffer_search():
                                           (rbc.BF16, rbc.PLAN_WINDOW_OFFSET)])
 @pytest.mark.parametrize("pinned", [False, True])
 def test_host_rows_copied_beside_stage_one(storage, plan, pinned):
-    # n_r = 4096 cuts 70,001 queries into batches of 65,536 and 4,465 rows:
-    # the first copies its host rows in four chunks on a second stream, each
-    # chunk's stage 1 waiting for its own copy (the last chunk ragged); the
-    # second is below the chunking threshold and copies in one piece.  The
-    # answers must equal those of the same search on device buffers.
+    # n_r = 4096 cuts 74,537 queries into batches of 65,536 and 9,001 rows;
+    # each copies its host rows in eight chunks on a second stream, and each
+    # chunk's per-row steps (stage 1, row statistics, low-precision rows)
+    # wait for its own copy only (the second batch: chunks of 1,152 rows and
+    # a ragged last one of 937).  test_host_buffer_search covers a batch
+    # below the chunking threshold (one copy).  The answers must equal those
+    # of the same search on device buffers.
     X = synth.iid_normal(40000, 32, 70)
-    Q = synth.iid_normal(70001, 32, 71)
+    Q = synth.iid_normal(74537, 32, 71)
     k = 5
     idx = build(X, 4096, storage=storage, plan=plan)
     dev_ids, dev_dist = search(idx, Q, k)
