@@ -529,6 +529,17 @@ int rbc_group_search(rbc_group* g, const float* Q, const int64_t* m, int32_t k, 
                      float* out_dist, void* stream);
 
 /*
+ * rbc_group_search_split -- rbc_group_search with the queries of each index
+ *   in a buffer of its own: Q is a HOST array of `count` pointers, Q[i] index
+ *   i's m[i] rows of d_i floats (host or device; may be NULL when m[i] = 0).
+ *   Each is copied to its place in the group's input buffer, so queries held
+ *   per index need no packing on the host.  Outputs, synchronisation and
+ *   errors as rbc_group_search (RBC_ERR_ARG also for a NULL Q or Q[i]).
+ */
+int rbc_group_search_split(rbc_group* g, const float* const* Q, const int64_t* m, int32_t k,
+                           int64_t* out_ids, float* out_dist, void* stream);
+
+/*
  * rbc_group_tune -- autotuner: times the search of this batch (3 graph
  *   replays each, CUDA events) for stage-two work-item sizes of 1024 to
  *   32768 points and keeps the fastest for later searches; *chosen (may be

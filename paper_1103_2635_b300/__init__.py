@@ -144,6 +144,7 @@ def load():
     lib.rbc_server_destroy.restype = None
     lib.rbc_group_create.argtypes = [P, I32, P, ctypes.POINTER(ctypes.c_void_p)]
     lib.rbc_group_search.argtypes = [P, P, P, I32, P, P, P]
+    lib.rbc_group_search_split.argtypes = [P, P, P, I32, P, P, P]
     lib.rbc_group_tune.argtypes = [P, P, P, I32, P, ctypes.POINTER(I32)]
     lib.rbc_group_stats.argtypes = [P, ctypes.POINTER(_GroupedStats)]
     lib.rbc_group_free.argtypes = [P]
@@ -151,7 +152,8 @@ def load():
     for f in ("rbc_sample_reps", "bf_search", "bf_search_noalloc", "rbc_build", "rbc_search", "rbc_search_check", "rbc_index_info",
               "rbc_index_export", "rbc_last_stats", "rbc_search_workspace", "rbc_plan_batch",
               "rbc_server_create", "rbc_server_submit", "rbc_server_wait", "rbc_server_stats",
-              "rbc_group_create", "rbc_group_search", "rbc_group_tune", "rbc_group_stats"):
+              "rbc_group_create", "rbc_group_search", "rbc_group_search_split", "rbc_group_tune",
+              "rbc_group_stats"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -456,15 +458,30 @@ class Group:
 
     def search(self, Qs, k: int, stream=None):
         """Qs: one [m_i, d_i] float32 array per index (all CUDA tensors, or
-        host arrays).  Returns ([m_i, k] ids, [m_i, k] rho) per index."""
-        flat, m, dev = self._pack(Qs)
-        M = int(m.sum())
-        ids, dist = _outputs(M, k, dev, None, None)
-        fp = flat.data_ptr() if dev is not None else flat.ctypes.data
-        ip = ids.data_ptr() if dev is not None else ids.ctypes.data
-        dp = dist.data_ptr() if dev is not None else dist.ctypes.data
-        _check(load().rbc_group_search(self._h, fp, m.ctypes.data, k, ip, dp,
-                                       _stream_of(stream, dev is not None)))
+        host arrays).  Returns ([m_i, k] ids, [m_i, k] rho) per index.  Host
+        arrays are passed one pointer per index (rbc_group_search_split), so
+        they are copied to the device as they are, with no packing here."""
+        if len(Qs) != len(self.dims):
+            raise ValueError("one query array per index")
+        if all(_is_torch(q) and q.is_cuda for q in Qs):
+            flat, m, dev = self._pack(Qs)
+            M = int(m.sum())
+            ids, dist = _outputs(M, k, dev, None, None)
+            _check(load().rbc_group_search(self._h, flat.data_ptr(), m.ctypes.data, k,
+                                           ids.data_ptr(), dist.data_ptr(), _stream_of(stream, True)))
+        else:
+            keep = [_arg(q, np.float32) for q in Qs]
+            if any(dev for _, _, dev in keep):
+                raise TypeError("queries must be all CUDA tensors or all host arrays")
+            for (_, kq, _), d in zip(keep, self.dims):
+                if len(kq.shape) != 2 or kq.shape[1] != d:
+                    raise ValueError(f"expected [m, {d}] queries, got shape {tuple(kq.shape)}")
+            m = np.array([kq.shape[0] for _, kq, _ in keep], dtype=np.int64)
+            ptrs = (ctypes.c_void_p * len(keep))(*[p for p, _, _ in keep])
+            M = int(m.sum())
+            ids, dist = _outputs(M, k, None, None, None)
+            _check(load().rbc_group_search_split(self._h, ptrs, m.ctypes.data, k, ids.ctypes.data,
+                                                 dist.ctypes.data, _stream_of(stream, False)))
         cut = np.concatenate([[0], np.cumsum(m)])
         return ([ids[cut[i]:cut[i + 1]] for i in range(len(m))],
                 [dist[cut[i]:cut[i + 1]] for i in range(len(m))])

@@ -626,17 +626,86 @@ int launch_plan(rbc_group* g, Plan& p, cudaStream_t st, bool use_graph) {
   return RBC_OK;
 }
 
+// Q: the queries packed index after index; or (Q null) Qs[i]: index i's rows
+// alone, each copied to its place in the plan's input buffer.
 int group_search(rbc_group* g, const float* Q, const int64_t* m, int k, int64_t* out_ids,
-                 float* out_dist, cudaStream_t st, int W, bool use_graph, Plan** used) {
+                 float* out_dist, cudaStream_t st, int W, bool use_graph, Plan** used,
+                 const float* const* Qs = nullptr) {
   std::vector<int64_t> mv(m, m + g->count);
   Plan* p = nullptr;
   G_TRY(plan_for(g, mv, k, W, st, &p));
   if (used) *used = p;
   if (p->M == 0) return RBC_OK;
-  RBC_CUDA(cudaMemcpyAsync(p->Qin, Q, p->in_floats * sizeof(float), cudaMemcpyDefault, st));
+  if (Q) {
+    RBC_CUDA(cudaMemcpyAsync(p->Qin, Q, p->in_floats * sizeof(float), cudaMemcpyDefault, st));
+  } else {
+    int64_t off = 0;
+    for (int i = 0; i < g->count; ++i) {
+      const int64_t f = mv[i] * g->d_of[i];
+      if (f > 0)
+        RBC_CUDA(cudaMemcpyAsync(p->Qin + off, Qs[i], f * sizeof(float), cudaMemcpyDefault, st));
+      off += f;
+    }
+  }
   G_TRY(launch_plan(g, *p, st, use_graph));
   RBC_CUDA(cudaMemcpyAsync(out_ids, p->out_ids, p->M * k * sizeof(int64_t), cudaMemcpyDefault, st));
   RBC_CUDA(cudaMemcpyAsync(out_dist, p->out_dist, p->M * k * sizeof(float), cudaMemcpyDefault, st));
+  return RBC_OK;
+}
+
+// rbc_group_search and rbc_group_search_split: Q packed, or Qs per index
+int group_search_entry(rbc_group* g, const float* Q, const float* const* Qs, const int64_t* m,
+                       int32_t k, int64_t* out_ids, float* out_dist, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!g || !m) {
+    set_error("rbc_group_search: NULL group or m");
+    return RBC_ERR_ARG;
+  }
+  int64_t M = 0;
+  for (int i = 0; i < g->count; ++i) {
+    if (m[i] < 0 || m[i] >= (1LL << 31)) {
+      set_error("rbc_group_search: m[%d] = %lld out of range", i, (long long)m[i]);
+      return RBC_ERR_ARG;
+    }
+    M += m[i];
+  }
+  if (k < 1 || k > MAX_C - 1 || M >= (1LL << 31)) {
+    set_error("rbc_group_search: k=%d must be in [1, %d]; total queries %lld < 2^31", k,
+              MAX_C - 1, (long long)M);
+    return RBC_ERR_ARG;
+  }
+  for (int i = 0; i < g->count; ++i)
+    if (m[i] > 0 && k > g->n_of[i]) {
+      set_error("rbc_group_search: k=%d exceeds the %lld points of index %d", k,
+                (long long)g->n_of[i], i);
+      return RBC_ERR_ARG;
+    }
+  if (M > 0 && ((!Q && !Qs) || !out_ids || !out_dist)) {
+    set_error("rbc_group_search: NULL pointer");
+    return RBC_ERR_ARG;
+  }
+  if (!Q)
+    for (int i = 0; i < g->count; ++i)
+      if (m[i] > 0 && !Qs[i]) {
+        set_error("rbc_group_search_split: NULL query pointer of index %d", i);
+        return RBC_ERR_ARG;
+      }
+  std::lock_guard<std::mutex> lk(g->mu);
+  Plan* p = nullptr;
+  G_TRY(group_search(g, Q, m, k, out_ids, out_dist, st, default_W(g), true, &p, Qs));
+  g->last.queries = M;
+  g->last.work_item_points = p->W;
+  g->last.graph_replays = p->replays;
+  if (M > 0) {
+    // the call's one read-back: the device error flags of the batch
+    uint32_t err = 0;
+    RBC_CUDA(cudaMemcpyAsync(&err, p->dev_err, sizeof(err), cudaMemcpyDeviceToHost, st));
+    RBC_CUDA(cudaStreamSynchronize(st));
+    if (err) {
+      set_error("rbc_group_search: device error flags 0x%x (capacity or bounded wait)", err);
+      return (err & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
+    }
+  }
   return RBC_OK;
 }
 
@@ -760,51 +829,16 @@ int rbc_group_create(const rbc_index* const* indexes, int32_t count, void* strea
 
 int rbc_group_search(rbc_group* g, const float* Q, const int64_t* m, int32_t k, int64_t* out_ids,
                      float* out_dist, void* stream) {
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (!g || !m) {
-    set_error("rbc_group_search: NULL group or m");
+  return rbc::group_search_entry(g, Q, nullptr, m, k, out_ids, out_dist, stream);
+}
+
+int rbc_group_search_split(rbc_group* g, const float* const* Q, const int64_t* m, int32_t k,
+                           int64_t* out_ids, float* out_dist, void* stream) {
+  if (!Q) {
+    rbc::set_error("rbc_group_search_split: NULL query pointer array");
     return RBC_ERR_ARG;
   }
-  int64_t M = 0;
-  for (int i = 0; i < g->count; ++i) {
-    if (m[i] < 0 || m[i] >= (1LL << 31)) {
-      set_error("rbc_group_search: m[%d] = %lld out of range", i, (long long)m[i]);
-      return RBC_ERR_ARG;
-    }
-    M += m[i];
-  }
-  if (k < 1 || k > MAX_C - 1 || M >= (1LL << 31)) {
-    set_error("rbc_group_search: k=%d must be in [1, %d]; total queries %lld < 2^31", k,
-              MAX_C - 1, (long long)M);
-    return RBC_ERR_ARG;
-  }
-  for (int i = 0; i < g->count; ++i)
-    if (m[i] > 0 && k > g->n_of[i]) {
-      set_error("rbc_group_search: k=%d exceeds the %lld points of index %d", k,
-                (long long)g->n_of[i], i);
-      return RBC_ERR_ARG;
-    }
-  if (M > 0 && (!Q || !out_ids || !out_dist)) {
-    set_error("rbc_group_search: NULL pointer");
-    return RBC_ERR_ARG;
-  }
-  std::lock_guard<std::mutex> lk(g->mu);
-  Plan* p = nullptr;
-  G_TRY(group_search(g, Q, m, k, out_ids, out_dist, st, default_W(g), true, &p));
-  g->last.queries = M;
-  g->last.work_item_points = p->W;
-  g->last.graph_replays = p->replays;
-  if (M > 0) {
-    // the call's one read-back: the device error flags of the batch
-    uint32_t err = 0;
-    RBC_CUDA(cudaMemcpyAsync(&err, p->dev_err, sizeof(err), cudaMemcpyDeviceToHost, st));
-    RBC_CUDA(cudaStreamSynchronize(st));
-    if (err) {
-      set_error("rbc_group_search: device error flags 0x%x (capacity or bounded wait)", err);
-      return (err & DEV_ERR_TIMEOUT) ? RBC_ERR_TIMEOUT : RBC_ERR_CUDA;
-    }
-  }
-  return RBC_OK;
+  return rbc::group_search_entry(g, nullptr, Q, m, k, out_ids, out_dist, stream);
 }
 
 int rbc_group_tune(rbc_group* g, const float* Q, const int64_t* m, int32_t k, void* stream,

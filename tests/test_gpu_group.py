@@ -94,6 +94,31 @@ def test_group_graph_replay_and_host_buffers():
         idx.close()
 
 
+def test_group_host_queries_per_index_equal_device():
+    # host queries reach the library one pointer per index
+    # (rbc_group_search_split, no packing on the host): pageable arrays and
+    # pinned CPU tensors give the answers of device tensors (packed on the
+    # device, rbc_group_search), index 1 with no queries at all
+    data = make_indexes(7, seed=9)
+    with rbc.Group([ix for _, _, ix in data]) as g:
+        di, dd = g.search([torch.from_numpy(Q).cuda() for _, Q, _ in data], 5)
+        torch.cuda.synchronize()
+        hi, hd = g.search([Q for _, Q, _ in data], 5)
+        pi, pd = g.search([torch.from_numpy(Q).pin_memory() for _, Q, _ in data], 5)
+        for (_, Q, _), a, b, c, d, e, f in zip(data, di, dd, hi, hd, pi, pd):
+            assert c.shape == (len(Q), 5) and e.shape == (len(Q), 5)
+            np.testing.assert_array_equal(c, a.cpu().numpy())
+            np.testing.assert_array_equal(d, b.cpu().numpy())
+            np.testing.assert_array_equal(e, a.cpu().numpy())
+            np.testing.assert_array_equal(f, b.cpu().numpy())
+        bad = [Q for _, Q, _ in data]
+        bad[0] = np.zeros((3, data[0][1].shape[1] + 1), np.float32)
+        with pytest.raises(ValueError):
+            g.search(bad, 5)
+    for _, _, idx in data:
+        idx.close()
+
+
 def test_group_autotune_keeps_results():
     data = make_indexes(8, seed=5, zero_m=False)
     with rbc.Group([ix for _, _, ix in data]) as g:

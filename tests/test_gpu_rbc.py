@@ -135,8 +135,8 @@ def test_host_buffer_search():
 
 @pytest.mark.parametrize("storage,plan", [(rbc.F32, rbc.PLAN_WINDOW), (rbc.BF16, rbc.PLAN_WINDOW),
                                           (rbc.BF16, rbc.PLAN_WINDOW_OFFSET)])
-@pytest.mark.parametrize("pinned", [False, True])
-def test_host_rows_copied_beside_stage_one(storage, plan, pinned):
+@pytest.mark.parametrize("pinned,own_stream", [(False, False), (True, False), (True, True)])
+def test_host_rows_copied_beside_stage_one(storage, plan, pinned, own_stream):
     # n_r = 4096 cuts 74,537 queries into batches of 65,536 and 9,001 rows;
     # each copies its host rows in eight chunks on a second stream, and each
     # chunk's per-row steps (stage 1, row statistics, low-precision rows)
@@ -154,7 +154,10 @@ def test_host_rows_copied_beside_stage_one(storage, plan, pinned):
     dist = torch.empty((Q.shape[0], k), dtype=torch.float32)
     if pinned:
         Qh, ids, dist = Qh.pin_memory(), ids.pin_memory(), dist.pin_memory()
-    rbc.rbc_search(idx, Qh, k, out_ids=ids, out_dist=dist)
+    # own_stream: the search runs on a stream of its own (not the legacy
+    # default stream), which the copy stream's events must order against
+    rbc.rbc_search(idx, Qh, k, out_ids=ids, out_dist=dist,
+                   stream=torch.cuda.Stream() if own_stream else None)
     np.testing.assert_array_equal(ids.numpy(), dev_ids)
     np.testing.assert_array_equal(dist.numpy(), dev_dist)
     sample = np.random.default_rng(72).choice(Q.shape[0], 300, replace=False)
