@@ -12,7 +12,11 @@
  *   torch CUDA tensor on the current device) or a HOST pointer (pageable or
  *   pinned).  The library inspects each pointer; host inputs are copied to the
  *   device and host outputs are filled by a device-to-host copy, inside the
- *   call, on the given stream.  Arrays are dense row-major: X [n, d],
+ *   call, on the given stream -- except that the windowed exact search copies
+ *   host query rows of batches of 8,192 rows or more in row chunks on a
+ *   library-owned stream (one per calling thread and device), ordered against
+ *   the given stream by events, so that each chunk's first steps start as
+ *   soon as its rows have landed.  Arrays are dense row-major: X [n, d],
  *   Q [m, d] float32; out_ids [m, k] int64; out_dist [m, k] float32.
  * Streams.  `stream` is a cudaStream_t (NULL = the legacy default stream).
  *   With device outputs the call is asynchronous: results are valid once the
