@@ -675,9 +675,12 @@ def run_group(args, rank, world, local):
     clocks = clk.summary()
     st = g.stats()
     t_seq = timed(lambda: [rbc.rbc_search(ix, Q, k) for ix, Q in zip(idxs, Qd)], max(3, args.steps // 3), 2)
-    # e2e: each index's queries in pinned host memory, one pointer per index
+    # e2e: each index's queries in pinned host memory, one pointer per index,
+    # results into pinned host buffers
     Qh = [torch.from_numpy(np.ascontiguousarray(Q)).pin_memory() for Q in Qs]
-    t_e2e = timed(lambda: g.search(Qh, k), max(3, args.steps // 3), 1)
+    oi = torch.empty((M, k), dtype=torch.int64).pin_memory()
+    od = torch.empty((M, k), dtype=torch.float32).pin_memory()
+    t_e2e = timed(lambda: g.search(Qh, k, out_ids=oi, out_dist=od), max(3, args.steps // 3), 1)
     # parity: every index alone on the GPU, and the FP64 oracle on sampled rows
     # (this search is marked as an NVTX range, for profiler launch lists)
     torch.cuda.nvtx.range_push("group_search")

@@ -191,6 +191,16 @@ def _stream_of(stream, device_side: bool):
     return 0
 
 
+def _check_out(a, dtype, m: int, k: int):
+    """Pointer of a caller's [m, k] output, written in place (no copy)."""
+    if tuple(a.shape) != (m, k):
+        raise ValueError(f"expected an [{m}, {k}] output, got shape {tuple(a.shape)}")
+    p, kept, dev = _arg(a, dtype)
+    if kept is not a:
+        raise TypeError(f"outputs must be contiguous {np.dtype(dtype).name} arrays")
+    return p, dev
+
+
 def _outputs(m: int, k: int, like_device, out_ids, out_dist):
     if out_ids is None:
         if like_device is not None:
@@ -456,19 +466,25 @@ class Group:
             dev = None
         return flat, m, dev
 
-    def search(self, Qs, k: int, stream=None):
+    def search(self, Qs, k: int, out_ids=None, out_dist=None, stream=None):
         """Qs: one [m_i, d_i] float32 array per index (all CUDA tensors, or
-        host arrays).  Returns ([m_i, k] ids, [m_i, k] rho) per index.  Host
-        arrays are passed one pointer per index (rbc_group_search_split), so
-        they are copied to the device as they are, with no packing here."""
+        host arrays).  Returns ([m_i, k] ids, [m_i, k] rho) per index: views
+        of one [sum m_i, k] pair, out_ids / out_dist when given (int64 and
+        float32, host or device, e.g. pinned host tensors).  Host arrays are
+        passed one pointer per index (rbc_group_search_split), so they are
+        copied to the device as they are, with no packing here."""
         if len(Qs) != len(self.dims):
             raise ValueError("one query array per index")
+        if (out_ids is None) != (out_dist is None):
+            raise ValueError("give both out_ids and out_dist, or neither")
         if all(_is_torch(q) and q.is_cuda for q in Qs):
             flat, m, dev = self._pack(Qs)
             M = int(m.sum())
-            ids, dist = _outputs(M, k, dev, None, None)
-            _check(load().rbc_group_search(self._h, flat.data_ptr(), m.ctypes.data, k,
-                                           ids.data_ptr(), dist.data_ptr(), _stream_of(stream, True)))
+            ids, dist = _outputs(M, k, dev, out_ids, out_dist)
+            ip, _ = _check_out(ids, np.int64, M, k)
+            dp, _ = _check_out(dist, np.float32, M, k)
+            _check(load().rbc_group_search(self._h, flat.data_ptr(), m.ctypes.data, k, ip, dp,
+                                           _stream_of(stream, True)))
         else:
             keep = [_arg(q, np.float32) for q in Qs]
             if any(dev for _, _, dev in keep):
@@ -479,9 +495,11 @@ class Group:
             m = np.array([kq.shape[0] for _, kq, _ in keep], dtype=np.int64)
             ptrs = (ctypes.c_void_p * len(keep))(*[p for p, _, _ in keep])
             M = int(m.sum())
-            ids, dist = _outputs(M, k, None, None, None)
-            _check(load().rbc_group_search_split(self._h, ptrs, m.ctypes.data, k, ids.ctypes.data,
-                                                 dist.ctypes.data, _stream_of(stream, False)))
+            ids, dist = _outputs(M, k, None, out_ids, out_dist)
+            ip, idev = _check_out(ids, np.int64, M, k)
+            dp, _ = _check_out(dist, np.float32, M, k)
+            _check(load().rbc_group_search_split(self._h, ptrs, m.ctypes.data, k, ip, dp,
+                                                 _stream_of(stream, idev)))
         cut = np.concatenate([[0], np.cumsum(m)])
         return ([ids[cut[i]:cut[i + 1]] for i in range(len(m))],
                 [dist[cut[i]:cut[i + 1]] for i in range(len(m))])

@@ -111,10 +111,22 @@ def test_group_host_queries_per_index_equal_device():
             np.testing.assert_array_equal(d, b.cpu().numpy())
             np.testing.assert_array_equal(e, a.cpu().numpy())
             np.testing.assert_array_equal(f, b.cpu().numpy())
+        # caller-owned pinned outputs are written in place
+        M = sum(len(Q) for _, Q, _ in data)
+        oi = torch.empty((M, 5), dtype=torch.int64).pin_memory()
+        od = torch.empty((M, 5), dtype=torch.float32).pin_memory()
+        qi, qd = g.search([torch.from_numpy(Q).pin_memory() for _, Q, _ in data], 5,
+                          out_ids=oi, out_dist=od)
+        np.testing.assert_array_equal(oi.numpy(), np.concatenate([a.cpu().numpy() for a in di]))
+        np.testing.assert_array_equal(od.numpy(), np.concatenate([b.cpu().numpy() for b in dd]))
+        for a, c in zip(di, qi):
+            np.testing.assert_array_equal(c.numpy(), a.cpu().numpy())
         bad = [Q for _, Q, _ in data]
         bad[0] = np.zeros((3, data[0][1].shape[1] + 1), np.float32)
         with pytest.raises(ValueError):
             g.search(bad, 5)
+        with pytest.raises(ValueError):  # outputs of the wrong size are refused
+            g.search([Q for _, Q, _ in data], 5, out_ids=oi[:-1], out_dist=od[:-1])
     for _, _, idx in data:
         idx.close()
 
