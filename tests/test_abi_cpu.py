@@ -66,3 +66,24 @@ def test_argument_validation_without_device_work():
     with pytest.raises(rbc.RbcError) as e:
         rbc.bf_search(wide[:1], wide, 1)
     assert e.value.code == -5
+
+
+def test_group_entries_reject_null_arguments_without_device_work():
+    lib = rbc.load()
+    # a NULL group, or a NULL array of per-index query pointers: RBC_ERR_ARG
+    # before any CUDA call
+    assert lib.rbc_group_search(None, None, None, 5, None, None, None) == -1
+    assert lib.rbc_group_search_split(None, None, None, 5, None, None, None) == -1
+
+
+def test_caller_output_buffers_are_checked_before_use():
+    # Group.search writes into caller-owned outputs in place: a buffer of the
+    # wrong shape, or one that would need a converted copy, is refused
+    p, dev = rbc._check_out(np.empty((3, 5), np.int64), np.int64, 3, 5)
+    assert p and not dev
+    with pytest.raises(ValueError):
+        rbc._check_out(np.empty((2, 5), np.int64), np.int64, 3, 5)
+    with pytest.raises(TypeError):
+        rbc._check_out(np.empty((3, 5), np.int32), np.int64, 3, 5)
+    with pytest.raises(TypeError):
+        rbc._check_out(np.empty((5, 3), np.int64).T, np.int64, 3, 5)
